@@ -1,0 +1,177 @@
+/*
+ * scff.h -- C ABI of the B300 molecular transition form-factor library.
+ *
+ * The library evaluates, for every excited state s and every point q of a
+ * momentum grid,
+ *
+ *     f_s(q) = scale * sum_{mu,nu} T^s[mu][nu] * Int phi_mu(r) phi_nu(r) e^{+i q.r} d^3r
+ *
+ * over real contracted Cartesian Gaussian basis functions phi (the AO-basis
+ * form factor of Sec. "Analytic Method", from Eqs. fSreal and PhiTDM of
+ * Sec. "FFT Method"; the paper's convention carries scale = sqrt(2) for spin,
+ * Sec. "Electronic Structure Calculation"), together with |f_s(q)|^2.
+ *
+ * The evaluation follows the paper's Cartesian analytic method (Eqs.
+ * sigmaTidbits, positionTidbits, bCoefficients, Mij, CartesianMethod,
+ * DTensor and Ccoefficients): a device pair-prep kernel applies the Gaussian
+ * product theorem to every pair of primitive shells and folds contraction
+ * coefficients, normalisation and T^s into per-pair monomial coefficients;
+ * q-evaluation kernels then sum Gaussian x phase x polynomial terms over the
+ * pairs.
+ *
+ * Units: atomic units throughout (positions in Bohr, q in inverse Bohr).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an scff_status; SCFF_OK is 0.  No call aborts the
+ *   process.  On failure the message of the calling thread's last error is
+ *   available from scff_last_error().
+ * - Input arrays are read during the call and copied; the caller keeps
+ *   ownership and may free them when the call returns.
+ * - Handles (basis, transitions, q-grids) are owned by the context and are
+ *   released with the matching scff_release_* call or by scff_destroy.
+ * - Output buffers are allocated by the caller.
+ * - Device pointers are plain CUDA device addresses on the context's device;
+ *   host pointers are ordinary host memory (pinned memory speeds up copies).
+ * - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef SCFF_H
+#define SCFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t scff_status;
+enum {
+    SCFF_OK = 0,
+    SCFF_ERR_INVALID_ARG = 1,  /* a size, pointer, code or layout is invalid */
+    SCFF_ERR_UNSUPPORTED_L = 2,/* shell angular momentum above Cartesian d */
+    SCFF_ERR_OOM = 3,          /* device or host allocation failed */
+    SCFF_ERR_ADMISSION = 4,    /* job footprint exceeds the context's HBM budget */
+    SCFF_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the name) */
+    SCFF_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    SCFF_ERR_CANCELLED = 7,    /* a queued job was cancelled */
+    SCFF_ERR_NOT_FOUND = 8     /* unknown handle or job id */
+};
+
+/* Arithmetic of the q-evaluation.  Pair-prep, normalisation and the phase
+ * range reduction run in FP64 in every mode. */
+typedef enum {
+    SCFF_FP64 = 0,   /* direct evaluation in FP64: the plain FP64 GPU path */
+    SCFF_FP32 = 1,   /* direct evaluation in FP32 with FP64-accurate phases */
+    SCFF_BF16X3 = 2  /* tensor-core split-BF16 contraction, FP32 accumulate
+                        (product grids; explicit q lists use the FP32 path) */
+} scff_precision;
+
+/* scff_basis flags */
+#define SCFF_RENORM_CONTRACTED 1u /* rescale each contracted function to <phi|phi> = 1 */
+
+typedef struct scff_ctx scff_ctx;
+typedef struct scff_basis_s *scff_basis_h;
+typedef struct scff_trans_s *scff_trans_h;
+typedef struct scff_qgrid_s *scff_qgrid_h;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory that form-factor jobs may hold at once (0 = 90% of the free
+ * memory at creation); it is what admission control checks against. */
+scff_status scff_create(scff_ctx **out, int device, uint64_t hbm_budget_bytes);
+void scff_destroy(scff_ctx *ctx);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *scff_last_error(void);
+
+/*
+ * Basis set (Appendix A, Eq. defprimitive; Sec. "Analytic Method" for the
+ * expansion into Cartesian terms).
+ *   xyz[n_atoms][3]       atom centres, Bohr.
+ *   shell_atom[n_shells]  atom index of each shell.
+ *   shell_l[n_shells]     0 = s, 1 = p, 2 = Cartesian d, -1 = sp (s and p
+ *                         sharing exponents).  Other values give
+ *                         SCFF_ERR_UNSUPPORTED_L (l >= 3) or INVALID_ARG.
+ *   shell_nprim[n_shells] primitives per shell (1..64).
+ *   exponents[]           alpha of exp(-alpha r^2), all shells concatenated
+ *                         (sum of shell_nprim entries), each > 0.
+ *   coefficients[]        contraction coefficients, concatenated; an sp
+ *                         shell stores nprim s coefficients then nprim p
+ *                         coefficients.
+ * Functions are numbered shell by shell; Cartesian components are ordered
+ * x,y,z and xx,xy,xz,yy,yz,zz; an sp shell gives s,px,py,pz.  Each primitive
+ * Cartesian term is normalised to unit norm; with SCFF_RENORM_CONTRACTED the
+ * contracted function is then rescaled to unit norm as well.
+ * On success *out is a new handle and *nbf_out the function count.
+ */
+scff_status scff_basis(scff_ctx *ctx, int n_atoms, const double *xyz, int n_shells,
+                       const int32_t *shell_atom, const int32_t *shell_l,
+                       const int32_t *shell_nprim, const double *exponents,
+                       const double *coefficients, uint32_t flags, scff_basis_h *out,
+                       int32_t *nbf_out);
+
+/*
+ * Transition density matrices T^s (Sec. "Electronic Structure Calculation",
+ * the one-particle TDM in the AO basis).
+ *   T[n_states][nbf][nbf] row-major FP64; T[s][mu][nu] weights phi_mu phi_nu.
+ *   T_on_device: 0 = host pointer, 1 = device pointer (copied device-to-device).
+ * Only the symmetric part of T contributes (the integral is symmetric in
+ * mu, nu for a real basis).
+ */
+scff_status scff_transitions(scff_ctx *ctx, scff_basis_h basis, int n_states,
+                             const double *T, int T_on_device, scff_trans_h *out);
+
+/* Product grid q = (qx[ix], qy[iy], qz[iz]); flat index (ix*ny + iy)*nz + iz
+ * (z fastest).  Host arrays, each length >= 1. */
+scff_status scff_qgrid_product(scff_ctx *ctx, const double *qx, int nx, const double *qy,
+                               int ny, const double *qz, int nz, scff_qgrid_h *out);
+
+/* Explicit list of q vectors, q[n][3] host array, n >= 0. */
+scff_status scff_qgrid_list(scff_ctx *ctx, const double *q, int64_t n, scff_qgrid_h *out);
+
+/* Number of q points of a grid (or -1 for an unknown handle). */
+int64_t scff_qgrid_size(scff_ctx *ctx, scff_qgrid_h grid);
+
+/*
+ * Form factor of every state on every q point (Eq. CartesianMethod evaluated
+ * through its monomial form, Eqs. DTensor and Ccoefficients).
+ *   precision   scff_precision.
+ *   scale       overall factor (1.0 for the bare integral; sqrt(2) for the
+ *               paper's spin-summed convention).
+ *   f_out       [n_states][n_q][2] interleaved (Re, Im); double for SCFF_FP64,
+ *               float otherwise.  Required.
+ *   f2_out      [n_states][n_q] |f|^2 in the same real type, or NULL.
+ *   out_on_device  1: f_out/f2_out are device pointers and the call is
+ *               asynchronous on `stream`; 0: host pointers, the call copies
+ *               the result back and returns after the stream has finished.
+ *   stream      a cudaStream_t (NULL = the legacy default stream).
+ * The pair-prep kernel runs inside every call; intermediate buffers come from
+ * a context-owned workspace that grows as needed.
+ */
+scff_status scff_form_factor(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
+                             scff_qgrid_h grid, int precision, double scale, void *f_out,
+                             void *f2_out, int out_on_device, void *stream);
+
+/* Waits for all work on `stream` and reports the device status word:
+ * SCFF_ERR_TIMEOUT if a device-side wait of an asynchronous call gave up. */
+scff_status scff_sync(scff_ctx *ctx, void *stream);
+
+/* Stage timing.  With timing enabled every scff_form_factor call records
+ * CUDA events on its stream; scff_last_timing then waits for the last call
+ * and writes ms_out[0] = q-evaluation kernel time, ms_out[1] = pair-prep and
+ * table kernels, ms_out[2] = both (milliseconds, device clock). */
+scff_status scff_set_timing(scff_ctx *ctx, int enable);
+scff_status scff_last_timing(scff_ctx *ctx, double *ms_out);
+
+/* Error statistics helper: count of q-evaluation kernel launches made by the
+ * context since creation (for launch accounting in benchmarks). */
+int64_t scff_kernel_launches(scff_ctx *ctx);
+
+void scff_release_basis(scff_ctx *ctx, scff_basis_h h);
+void scff_release_transitions(scff_ctx *ctx, scff_trans_h h);
+void scff_release_qgrid(scff_ctx *ctx, scff_qgrid_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCFF_H */

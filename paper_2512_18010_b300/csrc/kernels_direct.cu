@@ -1,0 +1,473 @@
+// Pair-prep (Gaussian product theorem + monomial coefficients), per-axis
+// Gaussian x phase tables, and the direct q-evaluation kernels (FP64/FP32).
+//
+// Method (Sec. "Analytic Method"): for a pair of primitive shells r1 = (A, alpha),
+// r2 = (B, beta) the Gaussian product theorem (Eqs. sigmaTidbits,
+// positionTidbits) gives p = alpha + beta, P = (alpha A + beta B)/p and the
+// prefactor K = (pi/p)^{3/2} exp(-alpha beta |A-B|^2 / p), which is
+// (2 pi)^{3/2} sigma_ij^3 exp(-r_ij^2 / (2 sigma-bar_ij^2)) of Eq. Mij with
+// sigma^2 = 1/(2 alpha).  Per axis the polynomial (y + P - A)^a (y + P - B)^a'
+// has binomial coefficients b_t (Eq. bCoefficients) and the Fourier integral
+// turns into exp(-q^2/(4p)) sum_u i^u C^u q^u with
+// C^u = sum_m b_{u+2m} sigma^{2(u+m)} (u+2m)! / (m! u! 2^m)  (Eq. Ccoefficients).
+// Folding every function pair of the two shells with its contraction weights
+// and T^s gives one real coefficient per (pair, monomial q_x^u q_y^v q_z^w,
+// state) -- the D-tensor of Eq. DTensor contracted with T -- and
+//     f_s(q) = sum_pairs exp(-q^2/4p) e^{i q.P} sum_uvw i^{u+v+w} D q^u q^v q^w.
+// The factor i^n is stored as a sign in the coefficient; odd n contribute to
+// the imaginary part of the polynomial.
+#include <math.h>
+
+#include "device_common.cuh"
+#include "scff_internal.h"
+
+namespace scff {
+
+// ------------------------------------------------------------------ helpers
+
+// Cartesian exponent of function j of a record type along axis ax.
+__host__ __device__ constexpr int fn_pow(int type, int j, int ax) {
+    // s: (000); p: x,y,z; d: xx,xy,xz,yy,yz,zz; sp: s,x,y,z
+    return type == REC_S   ? 0
+           : type == REC_P ? (j == ax ? 1 : 0)
+           : type == REC_SP
+               ? (j == 0 ? 0 : (j - 1 == ax ? 1 : 0))
+               : /* d */ (ax == 0 ? (j == 0 ? 2 : (j == 1 || j == 2) ? 1 : 0)
+                          : ax == 1 ? (j == 3 ? 2 : (j == 1 || j == 4) ? 1 : 0)
+                                    : (j == 5 ? 2 : (j == 2 || j == 4) ? 1 : 0));
+}
+
+// (u+2m)! / (m! u! 2^m) for u + 2m <= 4.
+__device__ __forceinline__ double herm_mono_factor(int u, int m) {
+    if (m == 0) return 1.0;
+    if (m == 1) return u == 0 ? 1.0 : u == 1 ? 3.0 : 6.0;  // 2!/2, 3!/2, 4!/(2!*2)
+    return 3.0;                                            // u = 0, m = 2: 4!/(2!*4)
+}
+
+// C^u for exponents (a, a2) along one axis, PA = P - A, PB = P - B, s2 = 1/(2p).
+__device__ double c_coef(int a, int a2, int u, double PA, double PB, double s2) {
+    const int deg = a + a2;
+    if (u > deg) return 0.0;
+    // binomial coefficients of (y+PA)^a and (y+PB)^a2 (a, a2 <= 2)
+    double ea[3], eb[3];
+    ea[0] = (a == 0) ? 1.0 : (a == 1) ? PA : PA * PA;
+    ea[1] = (a == 0) ? 0.0 : (a == 1) ? 1.0 : 2.0 * PA;
+    ea[2] = (a == 2) ? 1.0 : 0.0;
+    eb[0] = (a2 == 0) ? 1.0 : (a2 == 1) ? PB : PB * PB;
+    eb[1] = (a2 == 0) ? 0.0 : (a2 == 1) ? 1.0 : 2.0 * PB;
+    eb[2] = (a2 == 2) ? 1.0 : 0.0;
+    double c = 0.0;
+    double s2pow = 1.0;
+    for (int i = 0; i < u; ++i) s2pow *= s2;  // sigma^{2u}
+    for (int m = 0; u + 2 * m <= deg; ++m) {
+        const int t = u + 2 * m;
+        double bt = 0.0;
+        for (int i = 0; i <= a; ++i) {
+            const int j = t - i;
+            if (j >= 0 && j <= a2) bt += ea[i] * eb[j];
+        }
+        c += bt * s2pow * herm_mono_factor(u, m);
+        s2pow *= s2;  // sigma^{2(u+m)} for the next m
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------ pair geometry
+
+__global__ void pair_geom_kernel(PairSetDev ps, double *__restrict__ geom) {
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= ps.n_pair) return;
+    const int2 rr = ps.pair_rec[pr];
+    const double a = ps.rec_alpha[rr.x], b = ps.rec_alpha[rr.y];
+    const double p = a + b;
+    for (int ax = 0; ax < 3; ++ax)
+        geom[4 * pr + ax] = (a * ps.rec_xyz[3 * rr.x + ax] + b * ps.rec_xyz[3 * rr.y + ax]) / p;
+    geom[4 * pr + 3] = 0.25 / p;
+}
+
+cudaError_t launch_pair_geom(const PairSetDev &ps, double *pair_geom, cudaStream_t st) {
+    if (ps.n_pair == 0) return cudaSuccess;
+    pair_geom_kernel<<<(ps.n_pair + 127) / 128, 128, 0, st>>>(ps, pair_geom);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ K1 pair-prep
+
+__global__ void __launch_bounds__(128) pairprep_kernel(PairSetDev ps, const double *__restrict__ T,
+                                                       int S, int SB, double *__restrict__ coef64,
+                                                       float *__restrict__ coef32) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (row >= ps.n_rows) return;
+    int L = 0;
+    while (L < kMaxPairL && row >= ps.row_off[L + 1]) ++L;
+    const int mL = mono_count(L);
+    const int64_t local = row - ps.row_off[L];
+    const int pr = ps.pair_off[L] + (int)(local / mL);
+    const int m = (int)(local % mL);
+    double val = 0.0;
+    if (s < S) {
+        const int2 rr = ps.pair_rec[pr];
+        const double al = ps.rec_alpha[rr.x], be = ps.rec_alpha[rr.y];
+        const double p = al + be;
+        const double s2 = 0.5 / p;
+        double A[3], B[3], PA[3], PB[3], ab2 = 0.0;
+        for (int ax = 0; ax < 3; ++ax) {
+            A[ax] = ps.rec_xyz[3 * rr.x + ax];
+            B[ax] = ps.rec_xyz[3 * rr.y + ax];
+            const double P = (al * A[ax] + be * B[ax]) / p;
+            PA[ax] = P - A[ax];
+            PB[ax] = P - B[ax];
+            ab2 += (A[ax] - B[ax]) * (A[ax] - B[ax]);
+        }
+        const double K = pow(M_PI / p, 1.5) * exp(-al * be * ab2 / p);
+        const int e[3] = {mono_u(m), mono_v(m), mono_w(m)};
+        const int t1 = ps.rec_type[rr.x], t2 = ps.rec_type[rr.y];
+        const int l1 = rec_lmax(t1), l2 = rec_lmax(t2);
+        // C tables for this monomial: C[ax][a][a2]
+        double C[3][3][3];
+        for (int ax = 0; ax < 3; ++ax)
+            for (int a = 0; a <= 2; ++a)
+                for (int a2 = 0; a2 <= 2; ++a2)
+                    C[ax][a][a2] = (a <= l1 && a2 <= l2) ? c_coef(a, a2, e[ax], PA[ax], PB[ax], s2) : 0.0;
+        const int n1 = rec_nfn(t1), n2 = rec_nfn(t2);
+        const int f1 = ps.rec_fn0[rr.x], f2 = ps.rec_fn0[rr.y];
+        const int nbf = ps.nbf;
+        const double *Ts = T + (size_t)s * nbf * nbf;
+        const bool same = (rr.x == rr.y);
+        double acc = 0.0;
+        for (int i = 0; i < n1; ++i) {
+            const double wi = ps.rec_w[6 * rr.x + i];
+            const int ai = fn_pow(t1, i, 0), bi = fn_pow(t1, i, 1), ci = fn_pow(t1, i, 2);
+            for (int j = 0; j < n2; ++j) {
+                const int aj = fn_pow(t2, j, 0), bj = fn_pow(t2, j, 1), cj = fn_pow(t2, j, 2);
+                const double D = C[0][ai][aj] * C[1][bi][bj] * C[2][ci][cj];
+                if (D == 0.0) continue;
+                double tw = Ts[(size_t)(f1 + i) * nbf + (f2 + j)];
+                if (!same) tw += Ts[(size_t)(f2 + j) * nbf + (f1 + i)];
+                acc += tw * wi * ps.rec_w[6 * rr.y + j] * D;
+            }
+        }
+        const int n = e[0] + e[1] + e[2];
+        val = K * acc * ((n & 2) ? -1.0 : 1.0);  // i^n = +1, +i, -1, -i
+    }
+    const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
+    if (coef64) coef64[idx] = val;
+    if (coef32) coef32[idx] = (float)val;
+}
+
+cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB, int S_pad,
+                            double *coef64, float *coef32, int64_t *launches, cudaStream_t st) {
+    if (ps.n_rows == 0) return cudaSuccess;
+    dim3 grid((unsigned)((ps.n_rows + 127) / 128), (unsigned)S_pad);
+    pairprep_kernel<<<grid, 128, 0, st>>>(ps, T, S, SB, coef64, coef32);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ axis tables
+
+template <typename V>
+__global__ void axis_table_kernel(int n_pair, const double *__restrict__ geom,
+                                  const double *__restrict__ qaxis, int n, int axis, V *__restrict__ table) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_pair * n) return;
+    const int pr = (int)(idx / n), i = (int)(idx % n);
+    const double q = qaxis[i];
+    const double P = geom[4 * pr + axis], inv4p = geom[4 * pr + 3];
+    double sn, cs;
+    sincos(q * P, &sn, &cs);  // FP64 range reduction of the phase
+    const double amp = exp(-q * q * inv4p);
+    V v;
+    v.x = amp * cs;
+    v.y = amp * sn;
+    table[idx] = v;
+}
+
+cudaError_t launch_axis_tables(const PairSetDev &ps, const double *pair_geom, const double *qaxis,
+                               int n, int axis, void *table, int fp64, cudaStream_t st) {
+    const int64_t tot = (int64_t)ps.n_pair * n;
+    if (tot == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((tot + 255) / 256);
+    if (fp64)
+        axis_table_kernel<double2><<<blocks, 256, 0, st>>>(ps.n_pair, pair_geom, qaxis, n, axis,
+                                                           (double2 *)table);
+    else
+        axis_table_kernel<float2><<<blocks, 256, 0, st>>>(ps.n_pair, pair_geom, qaxis, n, axis,
+                                                          (float2 *)table);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ K2 direct q-evaluation
+
+template <typename R> struct Cplx;
+template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<float> { using T = float2; };
+
+constexpr int kDirectThreads = 128;
+constexpr int kChunkBytes = 8192;
+
+struct DirectParams {
+    PairSetDev ps;
+    const void *coef;
+    const void *gx, *gy, *gz;
+    const double *qax, *qay, *qaz;
+    int nx, ny, nz;
+    const double *qlist;
+    const double *pair_geom;
+    int64_t nq;
+    int S;
+    double scale;
+    void *f, *f2;
+    int *err;
+};
+
+// Gaussian x phase factor of one pair at this thread's q point.
+template <typename R, bool LIST>
+__device__ __forceinline__ typename Cplx<R>::T pair_factor(const DirectParams &p, int pr, int ix, int iy,
+                                                           int iz, double qx, double qy, double qz, double q2) {
+    using V = typename Cplx<R>::T;
+    V g;
+    if constexpr (!LIST) {
+        const V a = static_cast<const V *>(p.gx)[(int64_t)pr * p.nx + ix];
+        const V b = static_cast<const V *>(p.gy)[(int64_t)pr * p.ny + iy];
+        const V c = static_cast<const V *>(p.gz)[(int64_t)pr * p.nz + iz];
+        const R abx = a.x * b.x - a.y * b.y, aby = a.x * b.y + a.y * b.x;
+        g.x = abx * c.x - aby * c.y;
+        g.y = abx * c.y + aby * c.x;
+    } else {
+        const double2 pxy = reinterpret_cast<const double2 *>(p.pair_geom)[2 * pr];
+        const double2 pzw = reinterpret_cast<const double2 *>(p.pair_geom)[2 * pr + 1];
+        const double ph = qx * pxy.x + qy * pxy.y + qz * pzw.x;
+        if constexpr (sizeof(R) == 8) {
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double amp = exp(-q2 * pzw.y);
+            g.x = amp * cs;
+            g.y = amp * sn;
+        } else {
+            // FP64 range reduction to [-pi, pi], then FP32 evaluation.
+            const double k = rint(ph * 0.15915494309189535);
+            double r = fma(-k, 6.283185307179586, ph);
+            r = fma(-k, 2.4492935982947064e-16, r);
+            float sn, cs;
+            sincosf((float)r, &sn, &cs);
+            const float amp = expf((float)(-q2 * pzw.y));
+            g.x = amp * cs;
+            g.y = amp * sn;
+        }
+    }
+    return g;
+}
+
+template <typename R, int SB, int L, bool LIST>
+__device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf, int pr0,
+                                              int np, const R (&px)[5], const R (&py)[5], const R (&pz)[5],
+                                              int ix, int iy, int iz, double qx, double qy, double qz,
+                                              double q2, R (&fr)[SB], R (&fi)[SB]) {
+    constexpr int mL = mono_count(L);
+    for (int i = 0; i < np; ++i) {
+        const auto g = pair_factor<R, LIST>(p, pr0 + i, ix, iy, iz, qx, qy, qz, q2);
+        R E[SB], O[SB];
+#pragma unroll
+        for (int j = 0; j < SB; ++j) E[j] = O[j] = R(0);
+        const R *c = cbuf + (size_t)i * mL * SB;
+        static_for<mL>([&](auto M) {
+            constexpr int m = decltype(M)::value;
+            constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
+            const R mono = px[u] * py[v] * pz[w];
+#pragma unroll
+            for (int j = 0; j < SB; ++j) {
+                if constexpr (((u + v + w) & 1) != 0)
+                    O[j] = fma(c[m * SB + j], mono, O[j]);
+                else
+                    E[j] = fma(c[m * SB + j], mono, E[j]);
+            }
+        });
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+            fr[j] = fma(g.x, E[j], fr[j]);
+            fr[j] = fma(-g.y, O[j], fr[j]);
+            fi[j] = fma(g.x, O[j], fi[j]);
+            fi[j] = fma(g.y, E[j], fi[j]);
+        }
+    }
+}
+
+// Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
+// false (uniformly across the block) when a wait timed out.
+template <typename R, int SB, int L, bool LIST>
+__device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, uint64_t *bars,
+                                          uint32_t &phase, int sblk, const R (&px)[5], const R (&py)[5],
+                                          const R (&pz)[5], int ix, int iy, int iz, double qx, double qy,
+                                          double qz, double q2, R (&fr)[SB], R (&fi)[SB]) {
+    constexpr int mL = mono_count(L);
+    constexpr int pair_bytes = mL * SB * (int)sizeof(R);
+    constexpr int npc = kChunkBytes / pair_bytes > 0 ? kChunkBytes / pair_bytes : 1;
+    const int pbeg = p.ps.pair_off[L], pend = p.ps.pair_off[L + 1];
+    const int npairs = pend - pbeg;
+    if (npairs <= 0) return true;
+    const int nchunks = (npairs + npc - 1) / npc;
+    const R *base = static_cast<const R *>(p.coef) +
+                    ((size_t)sblk * p.ps.n_rows + (size_t)p.ps.row_off[L]) * SB;
+    R *bufs[2] = {buf0, buf1};
+    auto issue = [&](int c) {
+        const int n = min(npc, npairs - c * npc);
+        const uint32_t bytes = (uint32_t)(n * pair_bytes);
+        mbar_arrive_expect_tx(&bars[c & 1], bytes);
+        bulk_g2s(bufs[c & 1], base + (size_t)c * npc * mL * SB, bytes, &bars[c & 1]);
+    };
+    if (threadIdx.x == 0) {
+        issue(0);
+        if (nchunks > 1) issue(1);
+    }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        const bool got = mbar_wait(&bars[b], (phase >> b) & 1u);
+        phase ^= (1u << b);
+        if (__syncthreads_or(!got)) {
+            ok = false;
+            break;
+        }
+        const int n = min(npc, npairs - c * npc);
+        consume_chunk<R, SB, L, LIST>(p, bufs[b], pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz, q2,
+                                      fr, fi);
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
+    }
+    return ok;
+}
+
+template <typename R, int SB, bool LIST>
+__global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) {
+    __shared__ __align__(128) unsigned char smem[2 * kChunkBytes];
+    __shared__ __align__(8) uint64_t bars[2];
+    R *buf0 = reinterpret_cast<R *>(smem);
+    R *buf1 = reinterpret_cast<R *>(smem + kChunkBytes);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+
+    const int64_t q = (int64_t)blockIdx.x * kDirectThreads + threadIdx.x;
+    const bool valid = q < p.nq;
+    const int64_t qq = valid ? q : 0;
+    const int sblk = blockIdx.y;
+    int ix = 0, iy = 0, iz = 0;
+    double qx, qy, qz;
+    if constexpr (LIST) {
+        qx = p.qlist[3 * qq];
+        qy = p.qlist[3 * qq + 1];
+        qz = p.qlist[3 * qq + 2];
+    } else {
+        const int64_t nyz = (int64_t)p.ny * p.nz;
+        ix = (int)(qq / nyz);
+        iy = (int)((qq / p.nz) % p.ny);
+        iz = (int)(qq % p.nz);
+        qx = p.qax[ix];
+        qy = p.qay[iy];
+        qz = p.qaz[iz];
+    }
+    const double q2 = qx * qx + qy * qy + qz * qz;
+    R px[5], py[5], pz[5];
+    px[0] = py[0] = pz[0] = R(1);
+#pragma unroll
+    for (int k = 1; k < 5; ++k) {
+        px[k] = px[k - 1] * (R)qx;
+        py[k] = py[k - 1] * (R)qy;
+        pz[k] = pz[k - 1] * (R)qz;
+    }
+    R fr[SB], fi[SB];
+#pragma unroll
+    for (int j = 0; j < SB; ++j) fr[j] = fi[j] = R(0);
+
+    uint32_t phase = 0;
+    bool ok = run_class<R, SB, 0, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy,
+                                        qz, q2, fr, fi);
+    if (ok)
+        ok = run_class<R, SB, 1, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
+                                       q2, fr, fi);
+    if (ok)
+        ok = run_class<R, SB, 2, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
+                                       q2, fr, fi);
+    if (ok)
+        ok = run_class<R, SB, 3, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
+                                       q2, fr, fi);
+    if (ok)
+        ok = run_class<R, SB, 4, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
+                                       q2, fr, fi);
+    if (!ok) {
+        if (threadIdx.x == 0) flag_error(p.err, kDevErrTimeout);
+        return;
+    }
+    if (!valid) return;
+    using V = typename Cplx<R>::T;
+    V *f = static_cast<V *>(p.f);
+    R *f2 = static_cast<R *>(p.f2);
+    const R sc = (R)p.scale;
+#pragma unroll
+    for (int j = 0; j < SB; ++j) {
+        const int s = sblk * SB + j;
+        if (s < p.S) {
+            V v;
+            v.x = sc * fr[j];
+            v.y = sc * fi[j];
+            f[(size_t)s * p.nq + q] = v;
+            if (f2) f2[(size_t)s * p.nq + q] = v.x * v.x + v.y * v.y;
+        }
+    }
+}
+
+template <typename R, int SB>
+static cudaError_t launch_direct_t(const DirectArgs &a, bool list, cudaStream_t st) {
+    DirectParams p;
+    p.ps = *a.ps;
+    p.coef = a.coef;
+    p.gx = a.gx;
+    p.gy = a.gy;
+    p.gz = a.gz;
+    p.qax = a.qax;
+    p.qay = a.qay;
+    p.qaz = a.qaz;
+    p.nx = a.nx;
+    p.ny = a.ny;
+    p.nz = a.nz;
+    p.qlist = a.qlist;
+    p.pair_geom = a.pair_geom;
+    p.nq = a.nq;
+    p.S = a.S;
+    p.scale = a.scale;
+    p.f = a.f;
+    p.f2 = a.f2;
+    p.err = a.err_flag;
+    const int nsb = (a.S + SB - 1) / SB;
+    dim3 grid((unsigned)((a.nq + kDirectThreads - 1) / kDirectThreads), (unsigned)nsb);
+    if (list)
+        direct_kernel<R, SB, true><<<grid, kDirectThreads, 0, st>>>(p);
+    else
+        direct_kernel<R, SB, false><<<grid, kDirectThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct(const DirectArgs &a, int fp64, int list_mode, int64_t *launches, cudaStream_t st) {
+    if (a.nq == 0) return cudaSuccess;
+    cudaError_t e;
+    if (fp64) {
+        if (a.SB != 4) return cudaErrorInvalidValue;
+        e = launch_direct_t<double, 4>(a, list_mode != 0, st);
+    } else {
+        if (a.SB == 8)
+            e = launch_direct_t<float, 8>(a, list_mode != 0, st);
+        else if (a.SB == 16)
+            e = launch_direct_t<float, 16>(a, list_mode != 0, st);
+        else
+            return cudaErrorInvalidValue;
+    }
+    if (launches) ++*launches;
+    return e;
+}
+
+}  // namespace scff

@@ -1,0 +1,646 @@
+// Host runtime of the form-factor library: context, handles, validation,
+// basis ingest (normalisation, primitive-shell records, pair list), q-grids
+// and dispatch of the device kernels.  Implements include/scff.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/scff.h"
+#include "scff_internal.h"
+#include "tc_internal.h"
+
+using namespace scff;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static scff_status fail(scff_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            if (e_ == cudaErrorMemoryAllocation)                                              \
+                return fail(SCFF_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));           \
+            return fail(SCFF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));              \
+        }                                                                                     \
+    } while (0)
+
+extern "C" const char *scff_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ objects
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct scff_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    int64_t launches = 0;
+    int *d_err = nullptr;
+    int *h_err = nullptr;  // pinned
+    // workspace slots (grown on demand)
+    DevBuf coef, geom, gx, gy, gz, fstage, f2stage, tc_ws;
+    // stage timing (scff_set_timing): events before pair-prep, before the
+    // q-evaluation, after the q-evaluation
+    int timing = 0;
+    int timed_valid = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::vector<struct scff_basis_s *> bases;
+    std::vector<struct scff_trans_s *> transs;
+    std::vector<struct scff_qgrid_s *> grids;
+};
+
+struct scff_basis_s {
+    scff_ctx *ctx;
+    int nbf;
+    PairSetDev dev;
+};
+
+struct scff_trans_s {
+    scff_ctx *ctx;
+    scff_basis_s *basis;
+    int S;
+    double *d_T;
+};
+
+struct scff_qgrid_s {
+    scff_ctx *ctx;
+    int product;
+    int nx, ny, nz;
+    int64_t n;
+    double *d_qx, *d_qy, *d_qz;  // product grid axes
+    double *d_q;                 // list [n][3]
+    std::vector<double> hx, hy, hz;
+};
+
+static scff_status grow(scff_ctx *c, DevBuf &b, size_t bytes) {
+    if (bytes <= b.cap) return SCFF_OK;
+    // Kernels of earlier calls may still read the old buffer.
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = bytes + bytes / 8 + 256;
+    CUDA_TRY(cudaMalloc(&b.p, want));
+    b.cap = want;
+    (void)c;
+    return SCFF_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        scff_status s_ = (x);           \
+        if (s_ != SCFF_OK) return s_;   \
+    } while (0)
+
+// ------------------------------------------------------------------ context
+
+extern "C" scff_status scff_create(scff_ctx **out, int device, uint64_t hbm_budget_bytes) {
+    if (!out) return fail(SCFF_ERR_INVALID_ARG, "scff_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SCFF_ERR_INVALID_ARG, "scff_create: device %d of %d", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+    scff_ctx *c = new scff_ctx();
+    c->device = device;
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(SCFF_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e));
+    }
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+        if (c->d_err) cudaFree(c->d_err);
+        delete c;
+        return fail(SCFF_ERR_OOM, "scff_create: status word allocation failed");
+    }
+    cudaMemset(c->d_err, 0, sizeof(int));
+    for (auto &ev : c->ev) cudaEventCreate(&ev);
+    *out = c;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_set_timing(scff_ctx *c, int enable) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_timing: NULL context");
+    c->timing = enable ? 1 : 0;
+    c->timed_valid = 0;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_last_timing(scff_ctx *c, double *ms_out) {
+    if (!c || !ms_out) return fail(SCFF_ERR_INVALID_ARG, "scff_last_timing: NULL argument");
+    if (!c->timed_valid) return fail(SCFF_ERR_NOT_FOUND, "scff_last_timing: no timed call since timing was enabled");
+    cudaSetDevice(c->device);
+    CUDA_TRY(cudaEventSynchronize(c->ev[2]));
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+    ms_out[0] = b;        // q-evaluation kernel(s)
+    ms_out[1] = a;        // pair-prep, geometry and tables
+    ms_out[2] = a + b;    // whole device pipeline of the call
+    return SCFF_OK;
+}
+
+static void free_basis(scff_basis_s *b) {
+    PairSetDev &d = b->dev;
+    cudaFree(d.rec_xyz);
+    cudaFree(d.rec_alpha);
+    cudaFree(d.rec_type);
+    cudaFree(d.rec_fn0);
+    cudaFree(d.rec_w);
+    cudaFree(d.pair_rec);
+    delete b;
+}
+static void free_trans(scff_trans_s *t) {
+    cudaFree(t->d_T);
+    delete t;
+}
+static void free_grid(scff_qgrid_s *g) {
+    cudaFree(g->d_qx);
+    cudaFree(g->d_qy);
+    cudaFree(g->d_qz);
+    cudaFree(g->d_q);
+    delete g;
+}
+
+extern "C" void scff_destroy(scff_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto *t : c->transs) free_trans(t);
+    for (auto *b : c->bases) free_basis(b);
+    for (auto *g : c->grids) free_grid(g);
+    DevBuf *bufs[] = {&c->coef, &c->geom, &c->gx, &c->gy, &c->gz, &c->fstage, &c->f2stage, &c->tc_ws};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    cudaFree(c->d_err);
+    cudaFreeHost(c->h_err);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" int64_t scff_kernel_launches(scff_ctx *c) { return c ? c->launches : -1; }
+
+// ------------------------------------------------------------------ basis ingest
+
+namespace {
+
+struct HostRec {
+    int atom;
+    double alpha;
+    int type;
+    int fn0;
+    double w[6];
+};
+
+// (2n-1)!! with (-1)!! = 1
+double dfact_odd(int n) {
+    double r = 1.0;
+    for (int k = 2 * n - 1; k > 1; k -= 2) r *= k;
+    return r;
+}
+
+// Cartesian exponents of the functions of each record type.
+void type_powers(int type, int j, int pw[3]) {
+    static const int P[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    static const int D[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+    pw[0] = pw[1] = pw[2] = 0;
+    if (type == REC_P) memcpy(pw, P[j], sizeof(P[j]));
+    else if (type == REC_D) memcpy(pw, D[j], sizeof(D[j]));
+    else if (type == REC_SP && j > 0) memcpy(pw, P[j - 1], sizeof(P[j - 1]));
+}
+
+// Unit-norm factor of x^a y^b z^c exp(-alpha r^2):
+// N^2 = (2 alpha/pi)^{3/2} (4 alpha)^{a+b+c} / ((2a-1)!! (2b-1)!! (2c-1)!!).
+double prim_norm(double alpha, const int pw[3]) {
+    const int L = pw[0] + pw[1] + pw[2];
+    const double n2 = pow(2.0 * alpha / M_PI, 1.5) * pow(4.0 * alpha, L) /
+                      (dfact_odd(pw[0]) * dfact_odd(pw[1]) * dfact_odd(pw[2]));
+    return sqrt(n2);
+}
+
+// <x^a y^b z^c e^{-a1 r^2} | x^a y^b z^c e^{-a2 r^2}> on one centre:
+// prod_axes (2a-1)!! / (2p)^a * sqrt(pi/p), p = a1 + a2.
+double same_centre_overlap(double p, const int pw[3]) {
+    double v = pow(M_PI / p, 1.5);
+    for (int i = 0; i < 3; ++i) v *= dfact_odd(pw[i]) / pow(2.0 * p, pw[i]);
+    return v;
+}
+
+template <typename T>
+scff_status upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return SCFF_OK;
+    CUDA_TRY(cudaMalloc((void **)dst, sizeof(T) * src.size()));
+    CUDA_TRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return SCFF_OK;
+}
+
+}  // namespace
+
+extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, int n_shells,
+                                  const int32_t *shell_atom, const int32_t *shell_l, const int32_t *shell_nprim,
+                                  const double *exps, const double *coefs, uint32_t flags, scff_basis_h *out,
+                                  int32_t *nbf_out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: NULL context or output");
+    *out = nullptr;
+    if (n_atoms <= 0 || n_shells <= 0 || !xyz || !shell_atom || !shell_l || !shell_nprim || !exps || !coefs)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_basis: empty basis or NULL array");
+    for (int i = 0; i < 3 * n_atoms; ++i)
+        if (!isfinite(xyz[i])) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: non-finite coordinate %d", i);
+    std::vector<HostRec> recs;
+    size_t eoff = 0, coff = 0;
+    int nbf = 0;
+    const bool renorm = (flags & SCFF_RENORM_CONTRACTED) != 0;
+    for (int s = 0; s < n_shells; ++s) {
+        const int l = shell_l[s], np = shell_nprim[s], at = shell_atom[s];
+        if (l > 2) return fail(SCFF_ERR_UNSUPPORTED_L, "scff_basis: shell %d has l=%d (Cartesian d is the maximum)", s, l);
+        if (l < -1) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d has invalid code %d", s, l);
+        if (np < 1 || np > 64) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d has %d primitives", s, np);
+        if (at < 0 || at >= n_atoms) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d on atom %d", s, at);
+        const int type = (l == 0) ? REC_S : (l == 1) ? REC_P : (l == 2) ? REC_D : REC_SP;
+        const int nf = rec_nfn(type);
+        for (int k = 0; k < np; ++k)
+            if (!(exps[eoff + k] > 0.0) || !isfinite(exps[eoff + k]))
+                return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d exponent %d is not positive", s, k);
+        const int ncoef = np * (type == REC_SP ? 2 : 1);
+        for (int k = 0; k < ncoef; ++k)
+            if (!isfinite(coefs[coff + k])) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d coefficient %d", s, k);
+        // weights w[j][k] = c_k N_k(j) R_j
+        std::vector<double> w((size_t)nf * np);
+        for (int j = 0; j < nf; ++j) {
+            int pw[3];
+            type_powers(type, j, pw);
+            const double *c = coefs + coff + ((type == REC_SP && j > 0) ? np : 0);
+            for (int k = 0; k < np; ++k) w[(size_t)j * np + k] = c[k] * prim_norm(exps[eoff + k], pw);
+            if (renorm) {
+                double ov = 0.0;
+                for (int k = 0; k < np; ++k)
+                    for (int kk = 0; kk < np; ++kk)
+                        ov += w[(size_t)j * np + k] * w[(size_t)j * np + kk] *
+                              same_centre_overlap(exps[eoff + k] + exps[eoff + kk], pw);
+                if (!(ov > 0.0)) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d function %d has zero norm", s, j);
+                const double r = 1.0 / sqrt(ov);
+                for (int k = 0; k < np; ++k) w[(size_t)j * np + k] *= r;
+            }
+        }
+        for (int k = 0; k < np; ++k) {
+            HostRec r;
+            r.atom = at;
+            r.alpha = exps[eoff + k];
+            r.type = type;
+            r.fn0 = nbf;
+            for (int j = 0; j < 6; ++j) r.w[j] = j < nf ? w[(size_t)j * np + k] : 0.0;
+            recs.push_back(r);
+        }
+        nbf += nf;
+        eoff += np;
+        coff += ncoef;
+    }
+    // pair list sorted by class L
+    const int nrec = (int)recs.size();
+    std::vector<int2> buckets[kNumClasses];
+    for (int a = 0; a < nrec; ++a)
+        for (int b = a; b < nrec; ++b) {
+            const int L = rec_lmax(recs[a].type) + rec_lmax(recs[b].type);
+            buckets[L].push_back(make_int2(a, b));
+        }
+    scff_basis_s *B = new scff_basis_s();
+    B->ctx = c;
+    B->nbf = nbf;
+    PairSetDev &d = B->dev;
+    d.n_rec = nrec;
+    d.nbf = nbf;
+    std::vector<int2> pairs;
+    d.pair_off[0] = 0;
+    d.row_off[0] = d.krow_off[0] = 0;
+    int64_t axrows = 0;
+    for (int L = 0; L < kNumClasses; ++L) {
+        pairs.insert(pairs.end(), buckets[L].begin(), buckets[L].end());
+        const int64_t np = (int64_t)buckets[L].size();
+        d.pair_off[L + 1] = d.pair_off[L] + (int)np;
+        d.row_off[L + 1] = d.row_off[L] + np * mono_count(L);
+        d.krow_off[L + 1] = d.krow_off[L] + np * vw_count(L);
+        axrows += np * (L + 1);
+    }
+    d.n_pair = (int)pairs.size();
+    d.n_rows = d.row_off[kNumClasses];
+    d.n_krows = d.krow_off[kNumClasses];
+    d.n_axrows = axrows;
+    std::vector<double> rx(3 * (size_t)nrec), ra(nrec), rw(6 * (size_t)nrec);
+    std::vector<int32_t> rt(nrec), rf(nrec);
+    for (int i = 0; i < nrec; ++i) {
+        for (int k = 0; k < 3; ++k) rx[3 * i + k] = xyz[3 * recs[i].atom + k];
+        ra[i] = recs[i].alpha;
+        rt[i] = recs[i].type;
+        rf[i] = recs[i].fn0;
+        for (int j = 0; j < 6; ++j) rw[6 * i + j] = recs[i].w[j];
+    }
+    scff_status st = SCFF_OK;
+    cudaSetDevice(c->device);
+    if ((st = upload(&d.rec_xyz, rx)) || (st = upload(&d.rec_alpha, ra)) || (st = upload(&d.rec_type, rt)) ||
+        (st = upload(&d.rec_fn0, rf)) || (st = upload(&d.rec_w, rw)) || (st = upload(&d.pair_rec, pairs))) {
+        free_basis(B);
+        return st;
+    }
+    c->bases.push_back(B);
+    *out = B;
+    if (nbf_out) *nbf_out = nbf;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_transitions(scff_ctx *c, scff_basis_h b, int n_states, const double *T, int on_dev,
+                                        scff_trans_h *out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_transitions: NULL context or output");
+    *out = nullptr;
+    if (!b || std::find(c->bases.begin(), c->bases.end(), b) == c->bases.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_transitions: unknown basis handle");
+    if (n_states <= 0 || !T) return fail(SCFF_ERR_INVALID_ARG, "scff_transitions: n_states=%d, T=%p", n_states, (const void *)T);
+    const size_t bytes = sizeof(double) * (size_t)n_states * b->nbf * b->nbf;
+    cudaSetDevice(c->device);
+    scff_trans_s *t = new scff_trans_s();
+    t->ctx = c;
+    t->basis = b;
+    t->S = n_states;
+    t->d_T = nullptr;
+    if (cudaMalloc(&t->d_T, bytes) != cudaSuccess) {
+        delete t;
+        return fail(SCFF_ERR_OOM, "scff_transitions: cannot allocate %zu bytes", bytes);
+    }
+    cudaError_t e = cudaMemcpy(t->d_T, T, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_trans(t);
+        return fail(SCFF_ERR_CUDA, "scff_transitions: copy failed: %s", cudaGetErrorString(e));
+    }
+    c->transs.push_back(t);
+    *out = t;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_qgrid_product(scff_ctx *c, const double *qx, int nx, const double *qy, int ny,
+                                          const double *qz, int nz, scff_qgrid_h *out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_product: NULL context or output");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !qx || !qy || !qz)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_product: axis sizes %d %d %d", nx, ny, nz);
+    const double *ax[3] = {qx, qy, qz};
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < n[a]; ++i)
+            if (!isfinite(ax[a][i])) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_product: non-finite q");
+    cudaSetDevice(c->device);
+    scff_qgrid_s *g = new scff_qgrid_s();
+    g->ctx = c;
+    g->product = 1;
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->n = (int64_t)nx * ny * nz;
+    g->d_qx = g->d_qy = g->d_qz = g->d_q = nullptr;
+    g->hx.assign(qx, qx + nx);
+    g->hy.assign(qy, qy + ny);
+    g->hz.assign(qz, qz + nz);
+    scff_status st;
+    if ((st = upload(&g->d_qx, g->hx)) || (st = upload(&g->d_qy, g->hy)) || (st = upload(&g->d_qz, g->hz))) {
+        free_grid(g);
+        return st;
+    }
+    c->grids.push_back(g);
+    *out = g;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_qgrid_list(scff_ctx *c, const double *q, int64_t n, scff_qgrid_h *out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_list: NULL context or output");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && !q)) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_list: n=%lld", (long long)n);
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (!isfinite(q[i])) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_list: non-finite q");
+    cudaSetDevice(c->device);
+    scff_qgrid_s *g = new scff_qgrid_s();
+    g->ctx = c;
+    g->product = 0;
+    g->nx = g->ny = g->nz = 0;
+    g->n = n;
+    g->d_qx = g->d_qy = g->d_qz = g->d_q = nullptr;
+    if (n > 0) {
+        std::vector<double> v(q, q + 3 * n);
+        scff_status st = upload(&g->d_q, v);
+        if (st) {
+            free_grid(g);
+            return st;
+        }
+    }
+    c->grids.push_back(g);
+    *out = g;
+    return SCFF_OK;
+}
+
+extern "C" int64_t scff_qgrid_size(scff_ctx *c, scff_qgrid_h g) {
+    if (!c || !g || std::find(c->grids.begin(), c->grids.end(), g) == c->grids.end()) return -1;
+    return g->n;
+}
+
+template <typename V>
+static void release_from(std::vector<V *> &v, V *h, void (*fr)(V *)) {
+    auto it = std::find(v.begin(), v.end(), h);
+    if (it == v.end()) return;
+    v.erase(it);
+    fr(h);
+}
+
+extern "C" void scff_release_basis(scff_ctx *c, scff_basis_h h) {
+    if (!c || !h) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    // transitions built on this basis go with it
+    for (size_t i = 0; i < c->transs.size();) {
+        if (c->transs[i]->basis == h) {
+            free_trans(c->transs[i]);
+            c->transs.erase(c->transs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+    release_from(c->bases, h, free_basis);
+}
+extern "C" void scff_release_transitions(scff_ctx *c, scff_trans_h h) {
+    if (!c || !h) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    release_from(c->transs, h, free_trans);
+}
+extern "C" void scff_release_qgrid(scff_ctx *c, scff_qgrid_h h) {
+    if (!c || !h) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    release_from(c->grids, h, free_grid);
+}
+
+// ------------------------------------------------------------------ form factor
+
+extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_h t, scff_qgrid_h g, int precision,
+                                        double scale, void *f_out, void *f2_out, int out_on_device, void *stream) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: NULL context");
+    if (!b || std::find(c->bases.begin(), c->bases.end(), b) == c->bases.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown basis handle");
+    if (!t || std::find(c->transs.begin(), c->transs.end(), t) == c->transs.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown transitions handle");
+    if (!g || std::find(c->grids.begin(), c->grids.end(), g) == c->grids.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown q-grid handle");
+    if (t->basis != b) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: transitions belong to another basis");
+    if (precision < SCFF_FP64 || precision > SCFF_BF16X3)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: precision %d", precision);
+    if (!f_out) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: f_out is NULL");
+    if (!isfinite(scale)) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: scale is not finite");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const PairSetDev &ps = b->dev;
+    const int S = t->S;
+    const int64_t nq = g->n;
+    const bool fp64 = precision == SCFF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    const bool use_tc = false && precision == SCFF_BF16X3 && g->product;
+    const int SB = fp64 ? 4 : (use_tc ? 8 : 8);
+    const int S_pad = (S + SB - 1) / SB * SB;
+
+    // footprint check (admission): coefficients + tables + outputs
+    const size_t coef_bytes = (size_t)S_pad * ps.n_rows * rsz;
+    const size_t geom_bytes = (size_t)ps.n_pair * 4 * sizeof(double) + 64;
+    const size_t out_bytes = (size_t)S * nq * rsz * 3;
+    size_t tab_bytes = 0;
+    if (g->product) tab_bytes = (size_t)ps.n_pair * (g->nx + g->ny + g->nz) * 2 * rsz;
+    size_t tc_bytes = use_tc ? tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz) : 0;
+    const size_t foot = coef_bytes + geom_bytes + tab_bytes + tc_bytes + (out_on_device ? 0 : out_bytes);
+    if (foot > c->budget)
+        return fail(SCFF_ERR_ADMISSION, "scff_form_factor: footprint %zu bytes exceeds the budget %llu", foot,
+                    (unsigned long long)c->budget);
+
+    TRY(grow(c, c->coef, coef_bytes + 256));
+    TRY(grow(c, c->geom, geom_bytes));
+    CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], st));
+    CUDA_TRY(launch_pair_geom(ps, (double *)c->geom.p, st));
+    ++c->launches;
+    CUDA_TRY(launch_pairprep(ps, t->d_T, S, SB, S_pad, fp64 ? (double *)c->coef.p : nullptr,
+                             fp64 ? nullptr : (float *)c->coef.p, &c->launches, st));
+
+    void *fdev = f_out, *f2dev = f2_out;
+    if (!out_on_device) {
+        TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
+        fdev = c->fstage.p;
+        if (f2_out) {
+            TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
+            f2dev = c->f2stage.p;
+        }
+    }
+
+    if (use_tc) {
+        TcArgs ta;
+        ta.ps = &ps;
+        ta.coef32 = (const float *)c->coef.p;
+        ta.SB = SB;
+        ta.pair_geom = (const double *)c->geom.p;
+        ta.qx = g->d_qx;
+        ta.qy = g->d_qy;
+        ta.qz = g->d_qz;
+        ta.nx = g->nx;
+        ta.ny = g->ny;
+        ta.nz = g->nz;
+        ta.S = S;
+        ta.scale = scale;
+        ta.f = (float *)fdev;
+        ta.f2 = (float *)f2dev;
+        ta.err = c->d_err;
+        TRY(grow(c, c->tc_ws, tc_bytes + 1024));
+        ta.ws = c->tc_ws.p;
+        ta.ws_bytes = c->tc_ws.cap;
+        ta.ev_mark = c->timing ? c->ev[1] : nullptr;
+        CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
+    } else {
+        DirectArgs a;
+        memset(&a, 0, sizeof(a));
+        a.ps = &ps;
+        a.coef = c->coef.p;
+        a.nq = nq;
+        a.S = S;
+        a.SB = SB;
+        a.scale = scale;
+        a.f = fdev;
+        a.f2 = f2dev;
+        a.err_flag = c->d_err;
+        if (g->product) {
+            const size_t el = 2 * rsz;
+            TRY(grow(c, c->gx, (size_t)ps.n_pair * g->nx * el + 256));
+            TRY(grow(c, c->gy, (size_t)ps.n_pair * g->ny * el + 256));
+            TRY(grow(c, c->gz, (size_t)ps.n_pair * g->nz * el + 256));
+            CUDA_TRY(launch_axis_tables(ps, (double *)c->geom.p, g->d_qx, g->nx, 0, c->gx.p, fp64, st));
+            CUDA_TRY(launch_axis_tables(ps, (double *)c->geom.p, g->d_qy, g->ny, 1, c->gy.p, fp64, st));
+            CUDA_TRY(launch_axis_tables(ps, (double *)c->geom.p, g->d_qz, g->nz, 2, c->gz.p, fp64, st));
+            c->launches += 3;
+            a.gx = c->gx.p;
+            a.gy = c->gy.p;
+            a.gz = c->gz.p;
+            a.qax = g->d_qx;
+            a.qay = g->d_qy;
+            a.qaz = g->d_qz;
+            a.nx = g->nx;
+            a.ny = g->ny;
+            a.nz = g->nz;
+        } else {
+            a.qlist = g->d_q;
+            a.pair_geom = (const double *)c->geom.p;
+        }
+        if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[1], st));
+        CUDA_TRY(launch_direct(a, fp64 ? 1 : 0, g->product ? 0 : 1, &c->launches, st));
+    }
+    if (c->timing) {
+        CUDA_TRY(cudaEventRecord(c->ev[2], st));
+        c->timed_valid = 1;
+    }
+
+    if (!out_on_device) {
+        if (nq > 0) {
+            CUDA_TRY(cudaMemcpyAsync(f_out, fdev, (size_t)S * nq * 2 * rsz, cudaMemcpyDeviceToHost, st));
+            if (f2_out) CUDA_TRY(cudaMemcpyAsync(f2_out, f2dev, (size_t)S * nq * rsz, cudaMemcpyDeviceToHost, st));
+        }
+        CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (*c->h_err) return fail(SCFF_ERR_TIMEOUT, "scff_form_factor: a device-side wait timed out (code %d)", *c->h_err);
+    }
+    return SCFF_OK;
+}
+
+// Reads the device status word after all work on `stream` has finished.
+extern "C" scff_status scff_sync(scff_ctx *c, void *stream) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_sync: NULL context");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (*c->h_err) return fail(SCFF_ERR_TIMEOUT, "scff_sync: a device-side wait timed out (code %d)", *c->h_err);
+    return SCFF_OK;
+}

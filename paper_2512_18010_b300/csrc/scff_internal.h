@@ -1,0 +1,131 @@
+// Internal declarations shared by the host runtime (scff_host.cpp) and the
+// CUDA kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+
+namespace scff {
+
+// Highest total polynomial degree of a pair of primitive shells (d with d).
+constexpr int kMaxPairL = 4;
+constexpr int kNumClasses = kMaxPairL + 1;
+
+// Number of monomials q_x^u q_y^v q_z^w with u+v+w <= L.
+__host__ __device__ constexpr int mono_count(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+// Number of (v, w) with v + w <= L (the contraction index per pair in the
+// tensor-core factorisation).
+__host__ __device__ constexpr int vw_count(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Monomials are ordered by degree n, then u descending, then v descending.
+__host__ __device__ constexpr int mono_u(int m) {
+    int i = 0;
+    for (int n = 0; n <= kMaxPairL; ++n)
+        for (int u = n; u >= 0; --u)
+            for (int v = n - u; v >= 0; --v) {
+                if (i == m) return u;
+                ++i;
+            }
+    return -1;
+}
+__host__ __device__ constexpr int mono_v(int m) {
+    int i = 0;
+    for (int n = 0; n <= kMaxPairL; ++n)
+        for (int u = n; u >= 0; --u)
+            for (int v = n - u; v >= 0; --v) {
+                if (i == m) return v;
+                ++i;
+            }
+    return -1;
+}
+__host__ __device__ constexpr int mono_w(int m) {
+    int i = 0;
+    for (int n = 0; n <= kMaxPairL; ++n)
+        for (int u = n; u >= 0; --u)
+            for (int v = n - u; v >= 0; --v) {
+                if (i == m) return n - u - v;
+                ++i;
+            }
+    return -1;
+}
+__host__ __device__ constexpr int mono_index(int u, int v, int w) {
+    int i = 0;
+    for (int n = 0; n <= kMaxPairL; ++n)
+        for (int uu = n; uu >= 0; --uu)
+            for (int vv = n - uu; vv >= 0; --vv) {
+                if (uu == u && vv == v && n - uu - vv == w) return i;
+                ++i;
+            }
+    return -1;
+}
+
+// Record types of a primitive shell.
+enum RecType : int32_t { REC_S = 0, REC_P = 1, REC_D = 2, REC_SP = 3 };
+__host__ __device__ constexpr int rec_nfn(int t) { return t == REC_S ? 1 : t == REC_P ? 3 : t == REC_D ? 6 : 4; }
+__host__ __device__ constexpr int rec_lmax(int t) { return t == REC_S ? 0 : t == REC_D ? 2 : 1; }
+
+// Device view of one basis: primitive-shell records and the pair list sorted
+// by pair class L = lmax(r1) + lmax(r2).
+struct PairSetDev {
+    int n_rec = 0;
+    int n_pair = 0;
+    int nbf = 0;
+    int pair_off[kNumClasses + 1] = {0};   // pairs of class L: [pair_off[L], pair_off[L+1])
+    int64_t row_off[kNumClasses + 1] = {0};// monomial rows of class L
+    int64_t krow_off[kNumClasses + 1] = {0};// (v,w) rows of class L (tensor-core K index)
+    int64_t n_rows = 0;                    // total monomial rows K
+    int64_t n_krows = 0;                   // total (pair, v, w) rows
+    int64_t n_axrows = 0;                  // total (pair, u) rows = sum (L+1)
+    // device arrays
+    double *rec_xyz = nullptr;   // [n_rec][3]
+    double *rec_alpha = nullptr; // [n_rec]
+    int32_t *rec_type = nullptr; // [n_rec]
+    int32_t *rec_fn0 = nullptr;  // [n_rec] first function index
+    double *rec_w = nullptr;     // [n_rec][6] normalised weights
+    int2 *pair_rec = nullptr;    // [n_pair] (r1, r2), r1 <= r2
+};
+
+// Workspace layout of one form-factor evaluation.
+struct EvalBuffers {
+    double *coef64 = nullptr;    // [n_sblk][n_rows][SB] signed real coefficients
+    float *coef32 = nullptr;     // same, FP32
+    double *pair_geom = nullptr; // [n_pair][4] = P, 1/(4p)
+    void *gx = nullptr, *gy = nullptr, *gz = nullptr; // axis tables (double2 or float2)
+    int *err_flag = nullptr;     // device status word
+};
+
+// ---------------------------------------------------------------- kernels
+// All launchers return the launch status and never synchronise.
+
+cudaError_t launch_pair_geom(const PairSetDev &ps, double *pair_geom, cudaStream_t st);
+
+// coef[(s / SB * n_rows + row) * SB + s % SB] for s < S_pad (zero beyond S).
+cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB, int S_pad,
+                            double *coef64, float *coef32, int64_t *launches, cudaStream_t st);
+
+// Per-axis Gaussian x phase tables g[pair][i] = exp(-q_i^2/(4p)) e^{i q_i P_axis}
+// computed in FP64; stored as double2 (fp64 != 0) or float2.
+cudaError_t launch_axis_tables(const PairSetDev &ps, const double *pair_geom, const double *qaxis,
+                               int n, int axis, void *table, int fp64, cudaStream_t st);
+
+struct DirectArgs {
+    const PairSetDev *ps;
+    const void *coef;        // coef64 or coef32 in [n_sblk][n_rows][SB] layout
+    const void *gx, *gy, *gz;// product-grid axis tables (grid mode)
+    const double *qax, *qay, *qaz; // product-grid axes
+    int nx, ny, nz;
+    const double *qlist;     // [n][3] (list mode)
+    const double *pair_geom; // list mode
+    int64_t nq;
+    int S, SB;
+    double scale;
+    void *f;                 // [S][nq][2]
+    void *f2;                // [S][nq] or null
+    int *err_flag;
+};
+cudaError_t launch_direct(const DirectArgs &a, int fp64, int list_mode, int64_t *launches,
+                          cudaStream_t st);
+
+}  // namespace scff

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of the C ABI in include/scff.h.
+
+Argument marshalling only: every step of the form-factor evaluation runs in
+the CUDA library ``libscff.so``.  Device memory and streams may come from
+PyTorch (CUDA tensors and ``torch.cuda.Stream``); host buffers are numpy
+arrays.  If the library is missing the import of this module fails loudly;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+FP64, FP32, BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+RENORM_CONTRACTED = 1
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_L", 3: "OOM", 4: "ADMISSION", 5: "CUDA",
+          6: "TIMEOUT", 7: "CANCELLED", 8: "NOT_FOUND"}
+
+_SYMBOLS = [
+    "scff_create", "scff_destroy", "scff_last_error", "scff_basis", "scff_transitions",
+    "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
+    "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
+    "scff_set_timing", "scff_last_timing",
+]
+
+
+class ScffError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libscff.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libscff.so not found at {_build.LIB}; build it with "
+                          "`python -m paper_2512_18010_b300.build`")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I32, I64, D, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint32
+    lib.scff_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_uint64]
+    lib.scff_destroy.argtypes = [P]
+    lib.scff_destroy.restype = None
+    lib.scff_last_error.restype = ctypes.c_char_p
+    lib.scff_basis.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, U32, ctypes.POINTER(P),
+                               ctypes.POINTER(I32)]
+    lib.scff_transitions.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.scff_qgrid_product.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.scff_qgrid_list.argtypes = [P, P, I64, ctypes.POINTER(P)]
+    lib.scff_qgrid_size.argtypes = [P, P]
+    lib.scff_qgrid_size.restype = I64
+    lib.scff_form_factor.argtypes = [P, P, P, P, ctypes.c_int, D, P, P, ctypes.c_int, P]
+    lib.scff_sync.argtypes = [P, P]
+    lib.scff_set_timing.argtypes = [P, ctypes.c_int]
+    lib.scff_last_timing.argtypes = [P, P]
+    lib.scff_kernel_launches.argtypes = [P]
+    lib.scff_kernel_launches.restype = I64
+    for n in ("scff_release_basis", "scff_release_transitions", "scff_release_qgrid"):
+        getattr(lib, n).argtypes = [P, P]
+        getattr(lib, n).restype = None
+    for n in ("scff_create", "scff_basis", "scff_transitions", "scff_qgrid_product", "scff_qgrid_list",
+              "scff_form_factor", "scff_sync", "scff_set_timing", "scff_last_timing"):
+        getattr(lib, n).restype = I32
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ScffError(rc, _lib.scff_last_error().decode())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class Basis:
+    def __init__(self, ctx: "Context", handle, nbf: int):
+        self.ctx, self.handle, self.nbf = ctx, handle, nbf
+
+
+class Transitions:
+    def __init__(self, ctx, handle, n_states: int, basis: Basis):
+        self.ctx, self.handle, self.n_states, self.basis = ctx, handle, n_states, basis
+
+
+class QGrid:
+    def __init__(self, ctx, handle, n: int, shape: Optional[Tuple[int, int, int]]):
+        self.ctx, self.handle, self.n, self.shape = ctx, handle, n, shape
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.scff_create(ctypes.byref(h), int(device), int(hbm_budget_bytes)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.scff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inputs ------------------------------------------------------------
+    def basis(self, mol, renorm: bool = True) -> Basis:
+        xyz = _np(mol.xyz, np.float64)
+        sa, sl, sn = _np(mol.shell_atom, np.int32), _np(mol.shell_l, np.int32), _np(mol.shell_nprim, np.int32)
+        ex, co = _np(mol.exponents, np.float64), _np(mol.coefficients, np.float64)
+        h = ctypes.c_void_p()
+        nbf = ctypes.c_int32()
+        _check(self.lib.scff_basis(self.h, int(xyz.shape[0]), _p(xyz), int(sl.shape[0]), _p(sa), _p(sl), _p(sn),
+                                   _p(ex), _p(co), RENORM_CONTRACTED if renorm else 0, ctypes.byref(h),
+                                   ctypes.byref(nbf)))
+        return Basis(self, h, nbf.value)
+
+    def transitions(self, basis: Basis, T) -> Transitions:
+        h = ctypes.c_void_p()
+        if _is_torch_cuda(T):
+            import torch
+            T = T.to(torch.float64).contiguous()
+            if T.dim() == 2:
+                T = T.unsqueeze(0)
+            S = int(T.shape[0])
+            _check(self.lib.scff_transitions(self.h, basis.handle, S, ctypes.c_void_p(T.data_ptr()), 1,
+                                             ctypes.byref(h)))
+        else:
+            T = _np(T, np.float64)
+            if T.ndim == 2:
+                T = T[None]
+            S = int(T.shape[0])
+            if T.shape[1:] != (basis.nbf, basis.nbf):
+                raise ValueError(f"T has shape {T.shape}, basis has {basis.nbf} functions")
+            _check(self.lib.scff_transitions(self.h, basis.handle, S, _p(T), 0, ctypes.byref(h)))
+        return Transitions(self, h, S, basis)
+
+    def qgrid_product(self, qx, qy, qz) -> QGrid:
+        qx, qy, qz = _np(qx, np.float64), _np(qy, np.float64), _np(qz, np.float64)
+        h = ctypes.c_void_p()
+        _check(self.lib.scff_qgrid_product(self.h, _p(qx), len(qx), _p(qy), len(qy), _p(qz), len(qz),
+                                           ctypes.byref(h)))
+        return QGrid(self, h, len(qx) * len(qy) * len(qz), (len(qx), len(qy), len(qz)))
+
+    def qgrid_list(self, q) -> QGrid:
+        q = _np(q, np.float64).reshape(-1, 3)
+        h = ctypes.c_void_p()
+        _check(self.lib.scff_qgrid_list(self.h, _p(q), int(q.shape[0]), ctypes.byref(h)))
+        return QGrid(self, h, int(q.shape[0]), None)
+
+    def release(self, obj):
+        if isinstance(obj, Basis):
+            self.lib.scff_release_basis(self.h, obj.handle)
+        elif isinstance(obj, Transitions):
+            self.lib.scff_release_transitions(self.h, obj.handle)
+        elif isinstance(obj, QGrid):
+            self.lib.scff_release_qgrid(self.h, obj.handle)
+
+    # -- evaluation --------------------------------------------------------
+    def form_factor(self, basis: Basis, trans: Transitions, grid: QGrid, precision=FP32, scale: float = 1.0,
+                    f_out=None, f2_out=None, with_f2: bool = True, stream=None):
+        """Evaluates f_s(q) (and |f_s(q)|^2).
+
+        With torch CUDA tensors as outputs (or ``f_out="cuda"``) the call is
+        asynchronous on ``stream`` (default: torch's current stream) and
+        returns the tensors; otherwise it returns numpy arrays
+        f[S, nq] (complex) and f2[S, nq].
+        """
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        S, nq = trans.n_states, grid.n
+        rdt = np.float64 if precision == FP64 else np.float32
+        if isinstance(f_out, str) and f_out == "cuda":
+            import torch
+            tdt = torch.float64 if precision == FP64 else torch.float32
+            dev = torch.device("cuda", self.device)
+            f_out = torch.empty((S, nq, 2), dtype=tdt, device=dev)
+            f2_out = torch.empty((S, nq), dtype=tdt, device=dev) if with_f2 else None
+        if f_out is not None and _is_torch_cuda(f_out):
+            import torch
+            if stream is None:
+                stream = torch.cuda.current_stream(f_out.device)
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+            _check(self.lib.scff_form_factor(self.h, basis.handle, trans.handle, grid.handle, int(precision),
+                                             float(scale), ctypes.c_void_p(f_out.data_ptr()),
+                                             ctypes.c_void_p(f2_out.data_ptr()) if f2_out is not None else None,
+                                             1, sp))
+            return f_out, f2_out
+        caller_buffers = f_out is not None
+        f = np.empty((S, nq, 2), dtype=rdt) if f_out is None else f_out
+        f2 = (np.empty((S, nq), dtype=rdt) if with_f2 else None) if f2_out is None else f2_out
+        if f.dtype != rdt or f.shape != (S, nq, 2) or not f.flags.c_contiguous:
+            raise ValueError(f"f_out must be a C-contiguous {np.dtype(rdt).name} array of shape {(S, nq, 2)}")
+        if f2 is not None and (f2.dtype != rdt or f2.shape != (S, nq) or not f2.flags.c_contiguous):
+            raise ValueError(f"f2_out must be a C-contiguous {np.dtype(rdt).name} array of shape {(S, nq)}")
+        sp = ctypes.c_void_p(0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                                       else int(stream)))
+        _check(self.lib.scff_form_factor(self.h, basis.handle, trans.handle, grid.handle, int(precision),
+                                         float(scale), _p(f), _p(f2) if f2 is not None else None, 0, sp))
+        if caller_buffers:
+            return f, f2
+        return f[..., 0] + 1j * f[..., 1], f2
+
+    def sync(self, stream=None):
+        sp = ctypes.c_void_p(0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                                       else int(stream)))
+        _check(self.lib.scff_sync(self.h, sp))
+
+    def set_timing(self, enable: bool = True):
+        _check(self.lib.scff_set_timing(self.h, 1 if enable else 0))
+
+    def last_timing(self):
+        """(q-evaluation ms, pair-prep + tables ms, total device ms) of the last call."""
+        out = np.zeros(3, dtype=np.float64)
+        _check(self.lib.scff_last_timing(self.h, _p(out)))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.scff_kernel_launches(self.h))
+
+
+def evaluate_job(ctx: Context, job, precision=FP32, scale: float = 1.0, q_list=None):
+    """Convenience: basis + transitions + grid of a workload job -> host f, f2."""
+    b = ctx.basis(job.mol)
+    t = ctx.transitions(b, job.T)
+    g = ctx.qgrid_list(q_list) if q_list is not None else ctx.qgrid_product(job.qx, job.qy, job.qz)
+    try:
+        return ctx.form_factor(b, t, g, precision=precision, scale=scale)
+    finally:
+        ctx.release(g)
+        ctx.release(b)

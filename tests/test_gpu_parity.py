@@ -1,0 +1,146 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Error metric (per state): max_q |f_gpu - f_oracle| / max_q |f_oracle| over
+the compared points.  Bars: FP64 1e-10, FP32 1e-6, split-BF16 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_18010_b300 import scff
+from paper_2512_18010_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = scff.Context(0)
+    yield c
+    c.close()
+
+
+def rel_err(f, g):
+    f = np.asarray(f)
+    g = np.asarray(g)
+    num = np.max(np.abs(f - g), axis=-1)
+    den = np.max(np.abs(g), axis=-1)
+    return np.max(num / den)
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+def test_config1_full_grid(ctx, prec):
+    job = W.config1()
+    f, f2 = scff.evaluate_job(ctx, job, precision=prec)
+    ref = oracle.grid_form_factor(job)
+    assert rel_err(f, ref) < TOL[prec]
+    assert np.allclose(f2, np.abs(f) ** 2, rtol=1e-5 if prec else 1e-12, atol=0)
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32])
+def test_config1_list_path(ctx, prec):
+    job = W.config1()
+    rng = np.random.default_rng(0)
+    q = np.vstack([np.zeros((1, 3)), rng.uniform(-12, 12, size=(300, 3))])
+    f, _ = scff.evaluate_job(ctx, job, precision=prec, q_list=q)
+    ref = oracle.form_factor(job.mol, job.T, q)
+    assert rel_err(f, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+def test_config2_grid_sampled(ctx, prec):
+    job = W.config2()
+    idx = W.subset_indices(job.nq, 1500, 2002)
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+def test_config3_full_size_sampled(ctx, prec):
+    # Full 128^3 grid, 12 states; the oracle checks a seeded 4096-point subset.
+    job = W.config3()
+    idx = W.subset_indices(job.nq, 4096 if prec != scff.FP64 else 1024, 3003)
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
+def test_hermiticity_on_gpu(ctx):
+    job = W.config2()
+    f, _ = scff.evaluate_job(ctx, job, precision=scff.FP64)
+    n = len(job.qx)
+    g = f.reshape(f.shape[0], n, n, n)
+    mirror = np.conj(g[:, ::-1, ::-1, ::-1])
+    assert np.max(np.abs(g - mirror)) < 1e-12 * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+def test_ragged_grid_and_odd_state_count(ctx, prec):
+    # Non-power-of-two axes (ragged tiles) and 13 states (not a multiple of the state block).
+    base = W.config1()
+    T = W.transition_matrices(77, 13, base.mol.nbf)
+    job = W.Job(base.mol, T, W.axis(5, 6.0), W.axis(7, 9.0), W.axis(131, 11.0))
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 600, 5)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
+def test_degenerate_inputs(ctx):
+    job = W.config1()
+    b = ctx.basis(job.mol)
+    t = ctx.transitions(b, job.T)
+    # empty explicit list
+    g = ctx.qgrid_list(np.zeros((0, 3)))
+    f, f2 = ctx.form_factor(b, t, g, precision=scff.FP64)
+    assert f.shape == (1, 0)
+    # single point grid at q = 0: f(0) = tr(T S) is real
+    g1 = ctx.qgrid_product([0.0], [0.0], [0.0])
+    f, _ = ctx.form_factor(b, t, g1, precision=scff.FP64)
+    ref = oracle.form_factor(job.mol, job.T, np.zeros((1, 3)))
+    assert abs(f[0, 0] - ref[0, 0]) < 1e-12 * abs(ref[0, 0])
+    # zero transition matrix gives exactly zero
+    tz = ctx.transitions(b, np.zeros_like(job.T))
+    fz, _ = ctx.form_factor(b, tz, g1, precision=scff.FP32)
+    assert np.all(fz == 0)
+    # antisymmetric T gives zero to rounding
+    ta = ctx.transitions(b, job.T - np.transpose(job.T, (0, 2, 1)))
+    fa, _ = ctx.form_factor(b, ta, ctx.qgrid_product(job.qx, job.qy, job.qz), precision=scff.FP64)
+    fs, _ = ctx.form_factor(b, t, ctx.qgrid_product(job.qx, job.qy, job.qz), precision=scff.FP64)
+    assert np.max(np.abs(fa)) < 1e-13 * np.max(np.abs(fs)) * 10
+
+
+def test_scale_and_device_outputs(ctx):
+    import torch
+    job = W.config1()
+    b = ctx.basis(job.mol)
+    t = ctx.transitions(b, job.T)
+    g = ctx.qgrid_product(job.qx, job.qy, job.qz)
+    f_host, _ = ctx.form_factor(b, t, g, precision=scff.FP64, scale=np.sqrt(2.0))
+    fd, f2d = ctx.form_factor(b, t, g, precision=scff.FP64, scale=np.sqrt(2.0), f_out="cuda")
+    ctx.sync()
+    fd = fd.cpu().numpy()
+    assert np.array_equal(fd[..., 0] + 1j * fd[..., 1], f_host)
+    ref = oracle.grid_form_factor(job, scale=np.sqrt(2.0))
+    assert rel_err(f_host, ref) < 1e-10
+
+
+def test_invalid_inputs_are_rejected(ctx):
+    job = W.config1()
+    m = job.mol
+    bad = W.Molecule(**{**m.__dict__, "shell_l": np.where(m.shell_l == 2, 3, m.shell_l).astype(np.int32)})
+    with pytest.raises(scff.ScffError) as e:
+        ctx.basis(bad)
+    assert e.value.code == 2  # UNSUPPORTED_L
+    neg = W.Molecule(**{**m.__dict__, "exponents": -m.exponents})
+    with pytest.raises(scff.ScffError) as e:
+        ctx.basis(neg)
+    assert e.value.code == 1
+    b = ctx.basis(m)
+    with pytest.raises(ValueError):
+        ctx.transitions(b, np.zeros((1, 3, 3)))
+    with pytest.raises(scff.ScffError):
+        ctx.qgrid_product([], [0.0], [0.0])
