@@ -260,11 +260,45 @@ __device__ __forceinline__ typename Cplx<R>::T pair_factor(const DirectParams &p
     return g;
 }
 
+// Per-state accumulators.  FP32 sums pairs in short runs of kFlushPairs
+// terms and folds each run into a (hi, lo) double-float pair with the
+// error-free TwoSum transformation (Knuth), which keeps the sum over 10^4
+// pairs at FP64-like accuracy; FP64 accumulates directly.
+constexpr int kFlushPairs = 16;
+
+template <typename R, int SB> struct Acc {
+    R pr[SB], pi[SB];  // running partial sums
+    R hr[SB], hi[SB], lr[SB], li[SB];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int j = 0; j < SB; ++j) pr[j] = pi[j] = hr[j] = hi[j] = lr[j] = li[j] = R(0);
+    }
+    __device__ __forceinline__ static void two_sum(R &h, R &l, R x) {
+        const R s = h + x;
+        const R bb = s - h;
+        const R err = (h - (s - bb)) + (x - bb);
+        h = s;
+        l += err;
+    }
+    __device__ __forceinline__ void flush() {
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int j = 0; j < SB; ++j) {
+                two_sum(hr[j], lr[j], pr[j]);
+                two_sum(hi[j], li[j], pi[j]);
+                pr[j] = pi[j] = R(0);
+            }
+        }
+    }
+    __device__ __forceinline__ R re(int j) const { return sizeof(R) == 4 ? hr[j] + lr[j] : pr[j]; }
+    __device__ __forceinline__ R im(int j) const { return sizeof(R) == 4 ? hi[j] + li[j] : pi[j]; }
+};
+
 template <typename R, int SB, int L, bool LIST>
 __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf, int pr0,
                                               int np, const R (&px)[5], const R (&py)[5], const R (&pz)[5],
                                               int ix, int iy, int iz, double qx, double qy, double qz,
-                                              double q2, R (&fr)[SB], R (&fi)[SB]) {
+                                              double q2, Acc<R, SB> &acc) {
     constexpr int mL = mono_count(L);
     for (int i = 0; i < np; ++i) {
         const auto g = pair_factor<R, LIST>(p, pr0 + i, ix, iy, iz, qx, qy, qz, q2);
@@ -286,12 +320,14 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
         });
 #pragma unroll
         for (int j = 0; j < SB; ++j) {
-            fr[j] = fma(g.x, E[j], fr[j]);
-            fr[j] = fma(-g.y, O[j], fr[j]);
-            fi[j] = fma(g.x, O[j], fi[j]);
-            fi[j] = fma(g.y, E[j], fi[j]);
+            acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
+            acc.pr[j] = fma(-g.y, O[j], acc.pr[j]);
+            acc.pi[j] = fma(g.x, O[j], acc.pi[j]);
+            acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
         }
+        if ((i % kFlushPairs) == kFlushPairs - 1) acc.flush();
     }
+    acc.flush();
 }
 
 // Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
@@ -300,10 +336,12 @@ template <typename R, int SB, int L, bool LIST>
 __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, uint64_t *bars,
                                           uint32_t &phase, int sblk, const R (&px)[5], const R (&py)[5],
                                           const R (&pz)[5], int ix, int iy, int iz, double qx, double qy,
-                                          double qz, double q2, R (&fr)[SB], R (&fi)[SB]) {
+                                          double qz, double q2, Acc<R, SB> &acc) {
     constexpr int mL = mono_count(L);
     constexpr int pair_bytes = mL * SB * (int)sizeof(R);
-    constexpr int npc = kChunkBytes / pair_bytes > 0 ? kChunkBytes / pair_bytes : 1;
+    static_assert(pair_bytes <= kChunkBytes, "one pair's coefficients must fit a staging buffer");
+    static_assert(pair_bytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+    constexpr int npc = kChunkBytes / pair_bytes;
     const int pbeg = p.ps.pair_off[L], pend = p.ps.pair_off[L + 1];
     const int npairs = pend - pbeg;
     if (npairs <= 0) return true;
@@ -332,7 +370,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
         }
         const int n = min(npc, npairs - c * npc);
         consume_chunk<R, SB, L, LIST>(p, bufs[b], pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz, q2,
-                                      fr, fi);
+                                      acc);
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
     }
@@ -380,25 +418,24 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
         py[k] = py[k - 1] * (R)qy;
         pz[k] = pz[k - 1] * (R)qz;
     }
-    R fr[SB], fi[SB];
-#pragma unroll
-    for (int j = 0; j < SB; ++j) fr[j] = fi[j] = R(0);
+    Acc<R, SB> acc;
+    acc.zero();
 
     uint32_t phase = 0;
     bool ok = run_class<R, SB, 0, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy,
-                                        qz, q2, fr, fi);
+                                        qz, q2, acc);
     if (ok)
         ok = run_class<R, SB, 1, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, fr, fi);
+                                       q2, acc);
     if (ok)
         ok = run_class<R, SB, 2, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, fr, fi);
+                                       q2, acc);
     if (ok)
         ok = run_class<R, SB, 3, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, fr, fi);
+                                       q2, acc);
     if (ok)
         ok = run_class<R, SB, 4, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, fr, fi);
+                                       q2, acc);
     if (!ok) {
         if (threadIdx.x == 0) flag_error(p.err, kDevErrTimeout);
         return;
@@ -413,8 +450,8 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
         const int s = sblk * SB + j;
         if (s < p.S) {
             V v;
-            v.x = sc * fr[j];
-            v.y = sc * fi[j];
+            v.x = sc * acc.re(j);
+            v.y = sc * acc.im(j);
             f[(size_t)s * p.nq + q] = v;
             if (f2) f2[(size_t)s * p.nq + q] = v.x * v.x + v.y * v.y;
         }
