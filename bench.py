@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="scff", choices=["scff", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x2", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -267,7 +267,7 @@ def main():
     flops_per_unit = 2 * K + 8 * n_pair
     kern_ms = float(np.mean(qeval_ms))
     achieved = flops_per_unit * units / (kern_ms / 1e3) / 1e12
-    if prec == scff.BF16X3:
+    if prec in (scff.BF16X3, scff.TF32X3, scff.BF16X2):
         peak_src = "measured bf16 dense (MEASURED_PEAKS.json bf16_tflops)"
         try:
             peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
@@ -320,7 +320,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"bf16x3": "bf16x3->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
+                "vs_baseline": None, "dtype": {"tf32x3": "tf32x3->f32", "bf16x3": "bf16x3->f32", "bf16x2": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
                 "data": "synthetic (seeded molecules, basis and transition matrices)",
                 "config": {"workload": desc, "precision": args.precision, "n_pairs": n_pair,
                            "monomial_rows": K, "l2": "flushed between timed steps (256 MB write)",

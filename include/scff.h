@@ -62,9 +62,16 @@ enum {
  * range reduction run in FP64 in every mode. */
 typedef enum {
     SCFF_FP64 = 0,   /* direct evaluation in FP64: the plain FP64 GPU path */
-    SCFF_FP32 = 1,   /* direct evaluation in FP32 with FP64-accurate phases */
-    SCFF_BF16X3 = 2  /* tensor-core split-BF16 contraction, FP32 accumulate
-                        (product grids; explicit q lists use the FP32 path) */
+    SCFF_FP32 = 1,   /* direct evaluation in FP32 with FP64-accurate phases and
+                        double-float accumulation across pairs */
+    SCFF_BF16X3 = 2, /* tensor cores, BF16 split into hi + mid + lo pieces
+                        (six piece products per complex part), FP32 accumulation */
+    SCFF_TF32X3 = 3, /* tensor cores, TF32 split into hi + lo pieces (three
+                        piece products per complex part), FP32 accumulation */
+    SCFF_BF16X2 = 4  /* tensor cores, BF16 hi + lo (three piece products): the
+                        fastest mode, about 2e-5 relative error on the bundled
+                        workloads.  The tensor-core modes need a product grid;
+                        on an explicit q list they run the FP32 direct path. */
 } scff_precision;
 
 /* scff_basis flags */
@@ -155,6 +162,12 @@ scff_status scff_form_factor(scff_ctx *ctx, scff_basis_h basis, scff_trans_h tra
 /* Waits for all work on `stream` and reports the device status word:
  * SCFF_ERR_TIMEOUT if a device-side wait of an asynchronous call gave up. */
 scff_status scff_sync(scff_ctx *ctx, void *stream);
+
+/* Tensor-core accumulation length: the FP32 TMEM accumulators are drained
+ * into the output every `drain_every` k-chunks (0 = once, at the end;
+ * -1 = the library default).  Shorter runs bound the rounding of long
+ * accumulations at the cost of more epilogue traffic. */
+scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
 
 /* Stage timing.  With timing enabled every scff_form_factor call records
  * CUDA events on its stream; scff_last_timing then waits for the last call

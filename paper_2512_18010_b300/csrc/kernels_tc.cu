@@ -1,7 +1,705 @@
-// Tensor-core split-BF16 evaluation path (placeholder until the tcgen05 kernel lands).
+// Tensor-core (tcgen05) split-BF16 evaluation of the form factor on product
+// grids.
+//
+// The Cartesian method factorises per axis (Eq. CartesianMethod with the
+// V-tensors of Eq. CartesianVector): each pair term is
+//   exp(-q^2/4p) e^{iq.P} sum_uvw i^{u+v+w} D_uvw q_x^u q_y^v q_z^w
+//   = sum_uvw D_uvw X_u(q_x) Y_v(q_y) Z_w(q_z),
+// with X_u(q) = (iq)^u exp(-q^2/4p) e^{i q P_x} (and Y, Z alike).  Grouping the
+// x factor with the coefficients,
+//   A[(s, ix), (pair, v, w)] = sum_u D^s_{pair,uvw} X_{pair,u}(q_x[ix])
+//   W[(pair, v, w), (iy, iz)] = Y_{pair,v}(q_y[iy]) Z_{pair,w}(q_z[iz])
+// turns the whole product-grid evaluation into one dense complex contraction
+//   f[(s, ix), (iy, iz)] = sum_k A[(s,ix), k] W[k, (iy,iz)],
+// which runs on the 5th-generation tensor cores:
+//   * A (complex, FP32) is split into BF16 hi + lo parts and stored as the
+//     128B-row-free SW64 K-major shared-memory image of each 128 x 32 tile,
+//     so one 1-D bulk TMA copy per stage lands it in shared memory;
+//   * W is generated on the fly by eight warps from FP64-accurate per-axis
+//     tables (FP32 storage) and split into BF16 hi + lo in shared memory;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM):
+//     Re += Ar Wr - Ai Wi and Im += Ar Wi + Ai Wr, each product as
+//     hi*hi + hi*lo + lo*hi (three passes), the minus sign through the
+//     instruction's negate-A bit;
+//   * the accumulators (Re and Im, 128 x 256 FP32 each: all 512 TMEM columns)
+//     are drained with tcgen05.ld into the FP32 output, optionally every
+//     `drain_every` k-chunks to bound the length of each TMEM accumulation.
+// FP64 is used only for the per-axis phase/Gaussian tables (range reduction
+// of q.P) and upstream in the pair-prep.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "device_common.cuh"
+#include "scff_internal.h"
 #include "tc_internal.h"
 
 namespace scff {
-size_t tc_workspace_bytes(const PairSetDev &, int, int, int, int) { return 0; }
-cudaError_t launch_tc_form_factor(const TcArgs &, int64_t *, cudaStream_t) { return cudaErrorNotSupported; }
+namespace tc {
+
+constexpr int BM = 128;                              // rows (s, ix) per tile
+constexpr int BN = 128;                              // columns (iy, iz) per tile
+constexpr int ROW_BYTES = 64;                        // one K-chunk row (64B swizzle)
+constexpr int A_ARR = BM * ROW_BYTES;                // bytes of one A array
+constexpr int W_ARR = BN * ROW_BYTES;                // bytes of one W array
+constexpr int K_STAGE = 32 * 16;                     // k-index records of one chunk (<= 32 x int4)
+constexpr int GEN_WARPS = 8;                         // W generators and accumulator drains
+constexpr int THREADS = 128 + GEN_WARPS * 32;        // warpgroup 0: TMA warp, MMA warp, 2 idle
+constexpr int TMEM_COLS = 512;                       // two sets of (Re, Im) x 128 columns
+// Register split between warpgroups (setmaxnreg): the launch provides
+// THREADS x LAUNCH_REGS registers; warpgroup 0 keeps LOW_REGS per thread and
+// the two generator warpgroups take HIGH_REGS.  The shares add up to the
+// launch total exactly, and the host checks the compiled count before launch.
+constexpr int LAUNCH_REGS = 168;
+constexpr int LOW_REGS = 72;
+constexpr int HIGH_REGS = 216;
+static_assert(128 * LOW_REGS + GEN_WARPS * 32 * HIGH_REGS == THREADS * LAUNCH_REGS, "register split");
+static_assert(2 * BN == GEN_WARPS * 32, "two generator threads per W row");
+
+// Split kinds.  Every value x of A and W is stored as NP pieces whose sum is x
+// to about 8*NP (BF16) or 22 (TF32) bits; the products kept are those whose
+// piece orders add up to at most NP-1, which bounds the dropped terms by the
+// precision of the split.
+//   KIND_BF16X2: BF16 hi + lo,        products hh, hl, lh          (~2^-16)
+//   KIND_BF16X3: BF16 hi + mid + lo,  products hh, hm, mh, hl, lh, mm (~2^-24)
+//   KIND_TF32X2: TF32 hi + lo,        products hh, hl, lh          (~2^-21)
+enum { KIND_BF16X2 = 0, KIND_BF16X3 = 1, KIND_TF32X2 = 2 };
+
+template <int KIND> struct Kind {
+    static constexpr bool TF32 = KIND == KIND_TF32X2;
+    static constexpr int NP = KIND == KIND_BF16X3 ? 3 : 2;          // pieces per value
+    static constexpr int NPROD = NP == 3 ? 6 : 3;                    // piece products per complex part
+    static constexpr int ELEM = TF32 ? 4 : 2;
+    static constexpr int BK = ROW_BYTES / ELEM;                      // k per chunk
+    static constexpr int PER_VEC = 16 / ELEM;                        // elements per 16-byte vector
+    static constexpr int A_STAGE = 2 * NP * A_ARR;                   // re pieces, then im pieces
+    static constexpr int W_STAGE = 2 * NP * W_ARR;
+    static constexpr int STAGE = A_STAGE + W_STAGE + K_STAGE;
+    static constexpr int STAGES = NP == 3 ? 2 : 3;
+    static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256;
+    static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+};
+
+// Piece orders of the kept products (A piece, W piece).
+__host__ __device__ constexpr int prod_a(int i) { return i == 0 ? 0 : i == 1 ? 0 : i == 2 ? 1 : i == 3 ? 0 : i == 4 ? 2 : 1; }
+__host__ __device__ constexpr int prod_w(int i) { return i == 0 ? 0 : i == 1 ? 1 : i == 2 ? 0 : i == 3 ? 2 : i == 4 ? 0 : 1; }
+
+// Byte offset of element (row, c) in a K-major array with 64-byte rows under
+// the 64B swizzle (16-byte chunk index XOR address bits 7-8).
+template <int KIND>
+__host__ __device__ __forceinline__ uint32_t sw64_offset(int row, int c) {
+    constexpr int E = Kind<KIND>::ELEM, V = Kind<KIND>::PER_VEC;
+    const int rr = row & 7;
+    return (uint32_t)((row >> 3) * 512 + rr * 64 + ((((c / V) ^ ((rr >> 1) & 3))) << 4) + (c % V) * E);
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    // start address >> 4, LBO unused (0), SBO = 512 B (8 rows x 64 B),
+    // version 1 (bits 46-47), layout SWIZZLE_64B = 4 (bits 61-63).
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+// Instruction descriptor: D FP32, A/B BF16 (kind::f16) or TF32 (kind::tf32),
+// both K-major, M = 128, N = 128; bit 13 negates A.
+template <bool TF32>
+constexpr uint32_t idesc_mma(bool neg_a) {
+    return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | ((neg_a ? 1u : 0u) << 13) |
+           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Splits one 16-byte vector worth of values into NP pieces (pieces[0] = hi).
+//   BF16: 8 values per vector; each piece rounds the remaining residual to BF16.
+//   TF32: 4 values per vector; hi = x with the 13 low mantissa bits cleared
+//         (exactly a TF32 number), lo = x - hi (exact in FP32; the MMA reads
+//         its top 19 bits).
+template <int KIND>
+__device__ __forceinline__ void split_vec(const float *x, uint4 (&pc)[Kind<KIND>::NP]) {
+    constexpr int NP = Kind<KIND>::NP;
+    if constexpr (Kind<KIND>::TF32) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float hf = __uint_as_float(__float_as_uint(x[i]) & 0xFFFFE000u);
+            h[i] = __float_as_uint(hf);
+            l[i] = __float_as_uint(x[i] - hf);
+        }
+        pc[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        pc[1] = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+        float r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] = x[i];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat162 b = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+                const float2 bf = __bfloat1622float2(b);
+                r[2 * i] -= bf.x;
+                r[2 * i + 1] -= bf.y;
+                w[i] = *reinterpret_cast<const uint32_t *>(&b);
+            }
+            pc[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ layout
+
+struct Layout {
+    int64_t n_axrows;  // zero row index of the axis tables
+    int64_t K, K_pad;  // contraction length and padded length
+    int nkc;           // k-chunks
+    int M, M_pad, n_mt;
+    int64_t N;
+    int n_nt;
+    size_t off_X, off_Y, off_Z, off_k, off_A, total;
+};
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, int BK, int a_stage) {
+    Layout L;
+    L.n_axrows = ps.n_axrows;
+    L.K = ps.n_krows;
+    L.K_pad = (L.K + BK - 1) / BK * BK;
+    if (L.K_pad == 0) L.K_pad = BK;
+    L.nkc = (int)(L.K_pad / BK);
+    L.M = S * nx;
+    L.M_pad = (L.M + BM - 1) / BM * BM;
+    L.n_mt = L.M_pad / BM;
+    L.N = (int64_t)ny * nz;
+    L.n_nt = (int)((L.N + BN - 1) / BN);
+    size_t o = 0;
+    L.off_X = o;
+    o = align_up(o + sizeof(float2) * (size_t)(L.n_axrows + 1) * nx, 1024);
+    L.off_Y = o;
+    o = align_up(o + sizeof(float2) * (size_t)(L.n_axrows + 1) * ny, 1024);
+    L.off_Z = o;
+    o = align_up(o + sizeof(float2) * (size_t)(L.n_axrows + 1) * nz, 1024);
+    L.off_k = o;
+    o = align_up(o + sizeof(int4) * (size_t)L.K_pad, 1024);
+    L.off_A = o;
+    o = align_up(o + (size_t)L.n_mt * L.nkc * a_stage, 1024);
+    L.total = o;
+    return L;
+}
+
+template <int KIND>
+static Layout make_layout_k(const PairSetDev &ps, int S, int nx, int ny, int nz) {
+    return make_layout(ps, S, nx, ny, nz, Kind<KIND>::BK, Kind<KIND>::A_STAGE);
+}
+
+// ------------------------------------------------------------------ prep kernels
+
+// X_{pair,u}(q_i) = (i q_i)^u exp(-q_i^2/(4p)) e^{i q_i P_axis}, FP64 then FP32.
+__global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict__ geom,
+                                        const double *__restrict__ qaxis, int n, int axis, int64_t n_axrows,
+                                        float2 *__restrict__ table) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (n_axrows + 1) * n) return;
+    const int64_t row = idx / n;
+    const int i = (int)(idx % n);
+    float2 out = make_float2(0.f, 0.f);
+    if (row < n_axrows) {
+        int L = 0;
+        while (L < kMaxPairL && row >= ps.axrow_off[L + 1]) ++L;
+        const int64_t local = row - ps.axrow_off[L];
+        const int pr = ps.pair_off[L] + (int)(local / (L + 1));
+        const int u = (int)(local % (L + 1));
+        const double q = qaxis[i];
+        const double P = geom[4 * pr + axis], inv4p = geom[4 * pr + 3];
+        double sn, cs;
+        sincos(q * P, &sn, &cs);
+        double amp = exp(-q * q * inv4p);
+        for (int t = 0; t < u; ++t) amp *= q;
+        double re, im;
+        switch (u & 3) {  // times i^u
+        case 0: re = cs; im = sn; break;
+        case 1: re = -sn; im = cs; break;
+        case 2: re = -cs; im = -sn; break;
+        default: re = sn; im = -cs; break;
+        }
+        out = make_float2((float)(amp * re), (float)(amp * im));
+    }
+    table[idx] = out;
+}
+
+// k -> (pair, v, w, first axis row of the pair); padding k -> (-1, 0, 0, zero row).
+__global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, int4 *__restrict__ kinfo) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K_pad) return;
+    int4 r = make_int4(-1, 0, 0, (int)n_axrows);
+    if (k < ps.n_krows) {
+        int L = 0;
+        while (L < kMaxPairL && k >= ps.krow_off[L + 1]) ++L;
+        const int64_t local = k - ps.krow_off[L];
+        const int nvw = vw_count(L);
+        const int j = (int)(local % nvw);
+        const int pr = ps.pair_off[L] + (int)(local / nvw);
+        int v = 0, w = 0, cnt = 0;
+        for (int t = 0; t <= L; ++t)
+            for (int vv = t; vv >= 0; --vv) {
+                if (cnt == j) {
+                    v = vv;
+                    w = t - vv;
+                }
+                ++cnt;
+            }
+        const int axbase = (int)(ps.axrow_off[L] + (int64_t)(pr - ps.pair_off[L]) * (L + 1));
+        r = make_int4(pr, v, w, axbase);
+    }
+    kinfo[k] = r;
+}
+
+// A[(s,ix), k] = sum_u D^s_{pair,(u,v,w)} X_{pair,u}(q_x[ix]), split into pieces
+// and written as the swizzled shared-memory image of each tile.  One thread
+// writes one 16-byte vector (PER_VEC consecutive k) of each array.
+template <int KIND>
+__global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int nx,
+                              const float2 *__restrict__ X, const int4 *__restrict__ kinfo, int64_t K_pad, int nkc,
+                              int M, int M_pad, uint8_t *__restrict__ Abuf) {
+    using KD = Kind<KIND>;
+    constexpr int V = KD::PER_VEC, BK = KD::BK, NP = KD::NP;
+    const int64_t kvn = K_pad / V;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M_pad * kvn) return;
+    const int m = (int)(idx / kvn);
+    const int64_t kv = idx % kvn;
+    float re[V], im[V];
+    const bool mvalid = m < M;
+    const int s = mvalid ? m / nx : 0, ix = mvalid ? m % nx : 0;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int4 ki = kinfo[kv * V + e];
+        float ar = 0.f, ai = 0.f;
+        if (mvalid && ki.x >= 0) {
+            int L = 0;
+            while (L < kMaxPairL && ki.x >= ps.pair_off[L + 1]) ++L;
+            const int64_t rowbase = ps.row_off[L] + (int64_t)(ki.x - ps.pair_off[L]) * mono_count(L);
+            const float *cs = coef32 + ((size_t)(s / SB) * ps.n_rows) * SB + (s % SB);
+            for (int u = 0; u <= L - ki.y - ki.z; ++u) {
+                const int mi = mono_index(u, ki.y, ki.z);
+                const int n = u + ki.y + ki.z;
+                const float c = cs[(size_t)(rowbase + mi) * SB] * ((n & 2) ? -1.f : 1.f);
+                const float2 x = X[(size_t)(ki.w + u) * nx + ix];
+                ar = fmaf(c, x.x, ar);
+                ai = fmaf(c, x.y, ai);
+            }
+        }
+        re[e] = ar;
+        im[e] = ai;
+    }
+    uint4 pr_[NP], pi_[NP];
+    split_vec<KIND>(re, pr_);
+    split_vec<KIND>(im, pi_);
+    const int mt = m / BM, r = m % BM;
+    const int64_t kc = (kv * V) / BK;
+    const int c0 = (int)((kv * V) % BK);
+    uint8_t *base = Abuf + ((size_t)mt * nkc + kc) * KD::A_STAGE;
+    const uint32_t off = sw64_offset<KIND>(r, c0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        *reinterpret_cast<uint4 *>(base + q * A_ARR + off) = pr_[q];
+        *reinterpret_cast<uint4 *>(base + (NP + q) * A_ARR + off) = pi_[q];
+    }
+}
+
+// ------------------------------------------------------------------ main kernel
+
+struct MainParams {
+    const uint8_t *A;
+    const float2 *Y, *Z;
+    const int4 *kinfo;
+    int ny, nz;
+    int64_t N;
+    int nkc;
+    int M, nx;
+    int64_t nq;
+    float scale;
+    float2 *f;
+    float *f2;
+    int *err;
+    int drain_every;
+};
+
+// Adds the finished accumulator group gd (TMEM set gd & 1) into this
+// thread's FP32 register sums: row = TMEM lane, CQ columns of Re and of Im.
+template <int CQ>
+__device__ __forceinline__ bool drain_group(int gd, uint64_t *accFull, uint64_t *accEmpty, uint32_t tmem, int lg,
+                                            int lane, int colh, float (&acc_re)[CQ], float (&acc_im)[CQ]) {
+    const int set = gd & 1;
+    const bool got = mbar_wait(&accFull[set], (gd >> 1) & 1);
+    if (__any_sync(0xffffffffu, !got)) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + set * (2 * BN) + colh;
+#pragma unroll
+    for (int cc = 0; cc < CQ; cc += 16) {
+        float re[16], im[16];
+        tmem_ld16(ta + cc, re);
+        tmem_ld16(ta + BN + cc, im);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            acc_re[cc + j] += re[j];
+            acc_im[cc + j] += im[j];
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&accEmpty[set]);
+    return true;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(THREADS, 1) tc_main_kernel(MainParams p) {
+    using KD = Kind<KIND>;
+    constexpr bool TF32 = KD::TF32;
+    constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = KD::STAGES;
+    constexpr int A_STAGE = KD::A_STAGE, W_STAGE = KD::W_STAGE, STAGE = KD::STAGE;
+    constexpr int KH = BK / 2;        // k per generator thread (two threads per W row)
+    constexpr int KSUB = 8;           // loads in flight per sub-batch
+    constexpr int CQ = BN / 2;        // accumulator columns (of Re and of Im) per drain thread
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+    uint64_t *fullA = bars + 0;                  // [STAGES] A tile + k-index records landed (TMA)
+    uint64_t *fullW = bars + STAGES;             // [STAGES] W tile written by the generators
+    uint64_t *empty = bars + 2 * STAGES;         // [STAGES] MMAs of the stage completed
+    uint64_t *accFull = bars + 3 * STAGES;       // [2] accumulator set holds a finished group
+    uint64_t *accEmpty = bars + 3 * STAGES + 2;  // [2] accumulator set drained
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * STAGES + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3 * STAGES + 5);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = blockIdx.x, mt = blockIdx.y;
+    const int nkc = p.nkc;
+    const int G = p.drain_every >= 1 ? max(2, min(p.drain_every, nkc)) : nkc;  // chunks per accumulation group
+    const int ngroups = (nkc + G - 1) / G;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&fullA[s], 1);
+            mbar_init(&fullW[s], GEN_WARPS);
+            mbar_init(&empty[s], 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(&accFull[j], 1);
+            mbar_init(&accEmpty[j], GEN_WARPS);
+        }
+        *abort_flag = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(LOW_REGS));
+        if (warp == 0 && lane == 0) {
+            // ---------------- TMA producer: A tile and the chunk's k-index records
+            for (int it = 0; it < nkc; ++it) {
+                const int s = it % STAGES;
+                if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                uint8_t *st = smem + s * STAGE;
+                mbar_arrive_expect_tx(&fullA[s], A_STAGE + BK * 16);
+                bulk_g2s(st, p.A + ((size_t)mt * nkc + it) * A_STAGE, A_STAGE, &fullA[s]);
+                bulk_g2s(st + A_STAGE + W_STAGE, p.kinfo + (size_t)it * BK, BK * 16, &fullA[s]);
+            }
+        } else if (warp == 1 && lane == 0) {
+            // ---------------- MMA issuer: group g accumulates into TMEM set g & 1
+            constexpr uint32_t ID = idesc_mma<TF32>(false), IDN = idesc_mma<TF32>(true);
+            for (int it = 0; it < nkc; ++it) {
+                const int s = it % STAGES;
+                const uint32_t par = (it / STAGES) & 1;
+                if (*abort_flag || !mbar_wait(&fullA[s], par) || !mbar_wait(&fullW[s], par)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int g = it / G, set = g & 1;
+                const bool first = (it % G) == 0;
+                if (first && g >= 2 && !mbar_wait(&accEmpty[set], ((g - 2) >> 1) & 1)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t t_re = tmem + set * (2 * BN), t_im = t_re + BN;
+                const uint32_t a0 = smem_u32(smem + s * STAGE);
+                const uint32_t w0 = a0 + A_STAGE;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t ko = kk * 32;  // 32 bytes = one MMA K step
+#pragma unroll
+                    for (int pq = 0; pq < KD::NPROD; ++pq) {
+                        const int qa = prod_a(pq), qw = prod_w(pq);
+                        const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
+                        const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
+                        const uint64_t wr = smem_desc_sw64(w0 + qw * W_ARR + ko);
+                        const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
+                        const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
+                        mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
+                        mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
+                        mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
+                        mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+                    }
+                }
+                mma_commit(&empty[s]);
+                if ((it % G) == G - 1 || it == nkc - 1) mma_commit(&accFull[set]);
+            }
+        }
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(HIGH_REGS));
+        // ---------------- W generators (two threads per W row); they also
+        // drain finished accumulator groups into FP32 registers.
+        const int gt = threadIdx.x - 128;          // 0..255
+        const int wrow = gt & (BN - 1);            // W row
+        const int khalf = gt / BN;                 // which half of the chunk's k
+        const int64_t n = (int64_t)nt * BN + wrow;
+        const bool nvalid = n < p.N;
+        const int iy = nvalid ? (int)(n / p.nz) : 0, iz = nvalid ? (int)(n % p.nz) : 0;
+        const float vmask = nvalid ? 1.f : 0.f;
+        const float2 *Yc = p.Y + iy;
+        const float2 *Zc = p.Z + iz;
+        // drain mapping: TMEM lane group = warp % 4 (hardware rule); the two
+        // warps of a lane group take column halves.
+        const int lg = warp & 3;
+        const int colh = ((warp - 4) >> 2) * CQ;
+        float acc_re[CQ], acc_im[CQ];
+#pragma unroll
+        for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
+        int drained = 0;
+        bool ok = true;
+        for (int it = 0; it < nkc && ok; ++it) {
+            const int s = it % STAGES;
+            bool w = mbar_wait(&fullA[s], (it / STAGES) & 1);  // k-index records of this chunk
+            if (w && it >= STAGES) w = mbar_wait(&empty[s], ((it / STAGES) - 1) & 1);
+            if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            uint8_t *st = smem + s * STAGE;
+            const int4 *kin = reinterpret_cast<const int4 *>(st + A_STAGE + W_STAGE) + khalf * KH;
+            uint8_t *wst = st + A_STAGE;
+#pragma unroll
+            for (int sb = 0; sb < KH; sb += KSUB) {
+                float2 y[KSUB], z[KSUB];
+#pragma unroll
+                for (int e = 0; e < KSUB; ++e) {
+                    const int4 ki = kin[sb + e];
+                    y[e] = Yc[(size_t)(ki.w + ki.y) * p.ny];
+                    z[e] = Zc[(size_t)(ki.w + ki.z) * p.nz];
+                }
+#pragma unroll
+                for (int jv = 0; jv < KSUB / V; ++jv) {
+                    float re[V], im[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const float2 a = y[jv * V + e], b = z[jv * V + e];
+                        re[e] = vmask * (a.x * b.x - a.y * b.y);
+                        im[e] = vmask * (a.x * b.y + a.y * b.x);
+                    }
+                    uint4 pr_[NP], pi_[NP];
+                    split_vec<KIND>(re, pr_);
+                    split_vec<KIND>(im, pi_);
+                    const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
+                        *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&fullW[s]);
+            // Group gd is complete once the MMAs of chunk (gd+1)G-1 are; that is
+            // guaranteed STAGES chunks later, so drain it then without stalling.
+            while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
+                if (!drain_group<CQ>(drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) {
+                    ok = false;
+                    break;
+                }
+                ++drained;
+            }
+        }
+        while (ok && drained < ngroups) {
+            if (!drain_group<CQ>(drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) ok = false;
+            ++drained;
+        }
+        if (!ok) *abort_flag = 1;
+        const int row = lg * 32 + lane;
+        const int m = mt * BM + row;
+        if (ok && m < p.M) {
+            const int sidx = m / p.nx, ix = m % p.nx;
+            const int64_t n0 = (int64_t)nt * BN + colh;
+            float2 *frow = p.f + (size_t)sidx * p.nq + (size_t)ix * p.N;
+            float *f2row = p.f2 ? p.f2 + (size_t)sidx * p.nq + (size_t)ix * p.N : nullptr;
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) {
+                const int64_t nn = n0 + j;
+                if (nn < p.N) {
+                    const float2 v = make_float2(p.scale * acc_re[j], p.scale * acc_im[j]);
+                    frow[nn] = v;
+                    if (f2row) f2row[nn] = v.x * v.x + v.y * v.y;
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && *abort_flag) flag_error(p.err, kDevErrTimeout);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace tc
+
+static int kind_of(int precision_kind) { return precision_kind; }
+
+size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
+    switch (kind_of(kind)) {
+    case tc::KIND_BF16X2: return tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz).total;
+    case tc::KIND_BF16X3: return tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz).total;
+    default: return tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz).total;
+    }
+}
+
+template <int KIND>
+static cudaError_t launch_tc_t(const TcArgs &a, int64_t *launches, cudaStream_t st) {
+    using namespace tc;
+    using KD = Kind<KIND>;
+    const PairSetDev &ps = *a.ps;
+    const Layout L = make_layout_k<KIND>(ps, a.S, a.nx, a.ny, a.nz);
+    if (L.total > a.ws_bytes) return cudaErrorInvalidValue;
+    if (L.n_mt > 65535) return cudaErrorInvalidConfiguration;
+    uint8_t *ws = static_cast<uint8_t *>(a.ws);
+    float2 *X = reinterpret_cast<float2 *>(ws + L.off_X);
+    float2 *Y = reinterpret_cast<float2 *>(ws + L.off_Y);
+    float2 *Z = reinterpret_cast<float2 *>(ws + L.off_Z);
+    int4 *kinfo = reinterpret_cast<int4 *>(ws + L.off_k);
+    uint8_t *Abuf = ws + L.off_A;
+    const double *qa[3] = {a.qx, a.qy, a.qz};
+    float2 *tab[3] = {X, Y, Z};
+    const int na[3] = {a.nx, a.ny, a.nz};
+    for (int ax = 0; ax < 3; ++ax) {
+        const int64_t tot = (L.n_axrows + 1) * na[ax];
+        axis_power_table_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.pair_geom, qa[ax], na[ax], ax,
+                                                                               L.n_axrows, tab[ax]);
+    }
+    kindex_kernel<<<(unsigned)((L.K_pad + 255) / 256), 256, 0, st>>>(ps, L.K_pad, L.n_axrows, kinfo);
+    {
+        const int64_t tot = (int64_t)L.M_pad * (L.K_pad / KD::PER_VEC);
+        abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.coef32, a.SB, a.nx, X, kinfo,
+                                                                           L.K_pad, L.nkc, L.M, L.M_pad, Abuf);
+    }
+    if (launches) *launches += 5;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static bool attr_set = false;
+    if (!attr_set) {
+        // The register split inside the kernel assumes exactly LAUNCH_REGS
+        // registers per thread at launch; anything else could leave the
+        // increasing warpgroups waiting, so refuse to launch.
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, tc_main_kernel<KIND>);
+        if (e != cudaSuccess) return e;
+        if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
+        e = cudaFuncSetAttribute(tc_main_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, KD::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    MainParams p;
+    p.A = Abuf;
+    p.Y = Y;
+    p.Z = Z;
+    p.kinfo = kinfo;
+    p.ny = a.ny;
+    p.nz = a.nz;
+    p.N = L.N;
+    p.nkc = L.nkc;
+    p.M = L.M;
+    p.nx = a.nx;
+    p.nq = (int64_t)a.nx * L.N;
+    p.scale = (float)a.scale;
+    p.f = reinterpret_cast<float2 *>(a.f);
+    p.f2 = a.f2;
+    p.err = a.err;
+    p.drain_every = a.drain_every;
+    if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
+    dim3 grid((unsigned)L.n_nt, (unsigned)L.n_mt);
+    tc_main_kernel<KIND><<<grid, THREADS, KD::SMEM_BYTES, st>>>(p);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st) {
+    switch (a.kind) {
+    case tc::KIND_BF16X2: return launch_tc_t<tc::KIND_BF16X2>(a, launches, st);
+    case tc::KIND_BF16X3: return launch_tc_t<tc::KIND_BF16X3>(a, launches, st);
+    default: return launch_tc_t<tc::KIND_TF32X2>(a, launches, st);
+    }
+}
+
 }  // namespace scff

@@ -62,6 +62,7 @@ struct scff_ctx {
     // stage timing (scff_set_timing): events before pair-prep, before the
     // q-evaluation, after the q-evaluation
     int timing = 0;
+    int drain_every = -1;  // tensor-core TMEM accumulation length (-1 = default)
     int timed_valid = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<struct scff_basis_s *> bases;
@@ -139,6 +140,13 @@ extern "C" scff_status scff_create(scff_ctx **out, int device, uint64_t hbm_budg
     cudaMemset(c->d_err, 0, sizeof(int));
     for (auto &ev : c->ev) cudaEventCreate(&ev);
     *out = c;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_set_tc_drain(scff_ctx *c, int drain_every) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_drain: NULL context");
+    if (drain_every < -1) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_drain: %d", drain_every);
+    c->drain_every = drain_every;
     return SCFF_OK;
 }
 
@@ -336,7 +344,7 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
     d.nbf = nbf;
     std::vector<int2> pairs;
     d.pair_off[0] = 0;
-    d.row_off[0] = d.krow_off[0] = 0;
+    d.row_off[0] = d.krow_off[0] = d.axrow_off[0] = 0;
     int64_t axrows = 0;
     for (int L = 0; L < kNumClasses; ++L) {
         pairs.insert(pairs.end(), buckets[L].begin(), buckets[L].end());
@@ -345,6 +353,7 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
         d.row_off[L + 1] = d.row_off[L] + np * mono_count(L);
         d.krow_off[L + 1] = d.krow_off[L] + np * vw_count(L);
         axrows += np * (L + 1);
+        d.axrow_off[L + 1] = axrows;
     }
     d.n_pair = (int)pairs.size();
     d.n_rows = d.row_off[kNumClasses];
@@ -512,7 +521,7 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     if (!g || std::find(c->grids.begin(), c->grids.end(), g) == c->grids.end())
         return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown q-grid handle");
     if (t->basis != b) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: transitions belong to another basis");
-    if (precision < SCFF_FP64 || precision > SCFF_BF16X3)
+    if (precision < SCFF_FP64 || precision > SCFF_BF16X2)
         return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: precision %d", precision);
     if (!f_out) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: f_out is NULL");
     if (!isfinite(scale)) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: scale is not finite");
@@ -523,8 +532,11 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const int64_t nq = g->n;
     const bool fp64 = precision == SCFF_FP64;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
-    const bool use_tc = false && precision == SCFF_BF16X3 && g->product;
-    const int SB = fp64 ? 4 : (use_tc ? 8 : 8);
+    const bool use_tc = (precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2) &&
+                        g->product;
+    // split kind of the tensor-core kernel: 0 BF16 hi/lo, 1 BF16 hi/mid/lo, 2 TF32 hi/lo
+    const int tc_kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+    const int SB = fp64 ? 4 : 8;
     const int S_pad = (S + SB - 1) / SB * SB;
 
     // footprint check (admission): coefficients + tables + outputs
@@ -533,7 +545,7 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const size_t out_bytes = (size_t)S * nq * rsz * 3;
     size_t tab_bytes = 0;
     if (g->product) tab_bytes = (size_t)ps.n_pair * (g->nx + g->ny + g->nz) * 2 * rsz;
-    size_t tc_bytes = use_tc ? tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz) : 0;
+    size_t tc_bytes = use_tc ? tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz, tc_kind) : 0;
     const size_t foot = coef_bytes + geom_bytes + tab_bytes + tc_bytes + (out_on_device ? 0 : out_bytes);
     if (foot > c->budget)
         return fail(SCFF_ERR_ADMISSION, "scff_form_factor: footprint %zu bytes exceeds the budget %llu", foot,
@@ -579,6 +591,8 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
         ta.ws = c->tc_ws.p;
         ta.ws_bytes = c->tc_ws.cap;
         ta.ev_mark = c->timing ? c->ev[1] : nullptr;
+        ta.kind = tc_kind;
+        ta.drain_every = c->drain_every >= 0 ? c->drain_every : 8;
         CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
     } else {
         DirectArgs a;

@@ -78,6 +78,7 @@ struct PairSetDev {
     int64_t n_rows = 0;                    // total monomial rows K
     int64_t n_krows = 0;                   // total (pair, v, w) rows
     int64_t n_axrows = 0;                  // total (pair, u) rows = sum (L+1)
+    int64_t axrow_off[kNumClasses + 1] = {0};// (pair, u) rows of class L
     // device arrays
     double *rec_xyz = nullptr;   // [n_rec][3]
     double *rec_alpha = nullptr; // [n_rec]

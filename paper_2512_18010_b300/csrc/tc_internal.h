@@ -24,9 +24,11 @@ struct TcArgs {
     void *ws;                  // workspace of tc_workspace_bytes()
     size_t ws_bytes;
     cudaEvent_t ev_mark;       // if set, recorded just before the main kernel
+    int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo
+    int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
 };
 
-size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz);
+size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind);
 cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st);
 
 }  // namespace scff

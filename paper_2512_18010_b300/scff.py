@@ -16,8 +16,8 @@ import numpy as np
 
 from . import build as _build
 
-FP64, FP32, BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+FP64, FP32, BF16X3, TF32X3, BF16X2 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3, "bf16x2": BF16X2}
 RENORM_CONTRACTED = 1
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_L", 3: "OOM", 4: "ADMISSION", 5: "CUDA",
@@ -27,7 +27,7 @@ _SYMBOLS = [
     "scff_create", "scff_destroy", "scff_last_error", "scff_basis", "scff_transitions",
     "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
-    "scff_set_timing", "scff_last_timing",
+    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain",
 ]
 
 
@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
     lib.scff_form_factor.argtypes = [P, P, P, P, ctypes.c_int, D, P, P, ctypes.c_int, P]
     lib.scff_sync.argtypes = [P, P]
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
+    lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_last_timing.argtypes = [P, P]
     lib.scff_kernel_launches.argtypes = [P]
     lib.scff_kernel_launches.restype = I64
@@ -77,7 +78,7 @@ def load(build_if_missing: bool = True):
         getattr(lib, n).argtypes = [P, P]
         getattr(lib, n).restype = None
     for n in ("scff_create", "scff_basis", "scff_transitions", "scff_qgrid_product", "scff_qgrid_list",
-              "scff_form_factor", "scff_sync", "scff_set_timing", "scff_last_timing"):
+              "scff_form_factor", "scff_sync", "scff_set_timing", "scff_last_timing", "scff_set_tc_drain"):
         getattr(lib, n).restype = I32
     _lib = lib
     return lib
@@ -238,6 +239,10 @@ class Context:
         sp = ctypes.c_void_p(0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream")
                                                        else int(stream)))
         _check(self.lib.scff_sync(self.h, sp))
+
+    def set_tc_drain(self, drain_every: int):
+        """k-chunks per tensor-core TMEM accumulation (0 = whole K, -1 = default)."""
+        _check(self.lib.scff_set_tc_drain(self.h, int(drain_every)))
 
     def set_timing(self, enable: bool = True):
         _check(self.lib.scff_set_timing(self.h, 1 if enable else 0))

@@ -1,7 +1,10 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Error metric (per state): max_q |f_gpu - f_oracle| / max_q |f_oracle| over
-the compared points.  Bars: FP64 1e-10, FP32 1e-6, split-BF16 1e-5.
+the compared points.  Bars: FP64 1e-10, FP32 1e-6, the 1e-5-grade tensor-core
+splits (BF16 hi/mid/lo, TF32 hi/lo) 1e-5.  The fast BF16 hi/lo split keeps
+three products of two 8-bit pieces, so its per-product error is ~2^-16; it is
+held to its own documented 5e-5 bar.
 """
 import numpy as np
 import pytest
@@ -12,7 +15,8 @@ from paper_2512_18010_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5}
+TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5, scff.TF32X3: 1e-5, scff.BF16X2: 5e-5}
+TC = [scff.BF16X3, scff.TF32X3, scff.BF16X2]
 
 
 @pytest.fixture(scope="module")
@@ -30,13 +34,13 @@ def rel_err(f, g):
     return np.max(num / den)
 
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32] + TC)
 def test_config1_full_grid(ctx, prec):
     job = W.config1()
     f, f2 = scff.evaluate_job(ctx, job, precision=prec)
     ref = oracle.grid_form_factor(job)
     assert rel_err(f, ref) < TOL[prec]
-    assert np.allclose(f2, np.abs(f) ** 2, rtol=1e-5 if prec else 1e-12, atol=0)
+    assert np.allclose(f2, np.abs(f) ** 2, rtol=1e-5 if prec else 1e-12, atol=1e-30)
 
 
 @pytest.mark.parametrize("prec", [scff.FP64, scff.FP32])
@@ -49,7 +53,7 @@ def test_config1_list_path(ctx, prec):
     assert rel_err(f, ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32] + TC)
 def test_config2_grid_sampled(ctx, prec):
     job = W.config2()
     idx = W.subset_indices(job.nq, 1500, 2002)
@@ -58,7 +62,7 @@ def test_config2_grid_sampled(ctx, prec):
     assert rel_err(f[:, idx], ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32] + TC)
 def test_config3_full_size_sampled(ctx, prec):
     # Full 128^3 grid, 12 states; the oracle checks a seeded 4096-point subset.
     job = W.config3()
@@ -77,7 +81,7 @@ def test_hermiticity_on_gpu(ctx):
     assert np.max(np.abs(g - mirror)) < 1e-12 * np.max(np.abs(g))
 
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32] + TC)
 def test_ragged_grid_and_odd_state_count(ctx, prec):
     # Non-power-of-two axes (ragged tiles) and 13 states (not a multiple of the state block).
     base = W.config1()
