@@ -180,6 +180,47 @@ scff_status scff_last_timing(scff_ctx *ctx, double *ms_out);
  * context since creation (for launch accounting in benchmarks). */
 int64_t scff_kernel_launches(scff_ctx *ctx);
 
+/*
+ * Form factor without any device allocation (no counterpart in the paper: it
+ * is a deployment variant of scff_form_factor for callers that cannot
+ * allocate device memory -- a host framework whose caching allocator already
+ * holds nearly all of HBM, a latency-bound serving loop where cudaMalloc and
+ * cudaFree would synchronise the device, or a plugin that must not manage
+ * device memory itself).
+ *
+ * It evaluates f_s(q) in FP64 on an explicit q list, with the same kernels as
+ * scff_form_factor(..., SCFF_FP64, ...) on an scff_qgrid_list grid, but needs
+ * no context or handles.  The basis is given as in scff_basis (host arrays);
+ * T_dev [n_states][nbf][nbf], q_dev [n_q][3], f_dev [n_states][n_q][2] and
+ * f2_dev [n_states][n_q] (or NULL) are caller-owned DEVICE buffers of FP64 on
+ * the current device.  All intermediates live in one fixed 32 MiB device
+ * array that belongs to the library and stays allocated on every GPU that
+ * loaded the library until the process exits; host staging uses static
+ * storage.  On success the call allocates nothing: no cudaMalloc, cudaFree
+ * or other allocating routine (a rejected call stores its message for
+ * scff_last_error()).
+ *
+ * Limits: at most 256 primitive-shell records (one per primitive of every
+ * shell) and n_states x coefficient rows within the scratch (about 3.9 M FP64
+ * coefficients, states padded to a multiple of 4); larger inputs return
+ * SCFF_ERR_INVALID_ARG with the limit in the message.
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same scratch array, which keeps the previous call's
+ * contents: the call rewrites everything it reads and clears its status word
+ * itself.  Calls are serialised on the host, but calls whose GPU work could
+ * overlap (for example on different streams of one device) race on the
+ * scratch array; order them on one stream.  The call returns after `stream`
+ * has finished its work.
+ */
+scff_status scff_form_factor_static(int n_atoms, const double *xyz, int n_shells,
+                                    const int32_t *shell_atom, const int32_t *shell_l,
+                                    const int32_t *shell_nprim, const double *exponents,
+                                    const double *coefficients, uint32_t flags, int n_states,
+                                    const double *T_dev, int64_t n_q, const double *q_dev,
+                                    double scale, double *f_dev, double *f2_dev, void *stream);
+
 void scff_release_basis(scff_ctx *ctx, scff_basis_h h);
 void scff_release_transitions(scff_ctx *ctx, scff_trans_h h);
 void scff_release_qgrid(scff_ctx *ctx, scff_qgrid_h h);

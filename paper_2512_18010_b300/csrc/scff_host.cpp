@@ -44,6 +44,14 @@ static scff_status fail(scff_status code, const char *fmt, ...) {
 
 extern "C" const char *scff_last_error(void) { return g_last_error.c_str(); }
 
+namespace scff {
+// Lets other translation units of the library report an error message.
+scff_status set_last_error(scff_status code, const char *msg) {
+    g_last_error = msg;
+    return code;
+}
+}  // namespace scff
+
 // ------------------------------------------------------------------ objects
 
 struct DevBuf {

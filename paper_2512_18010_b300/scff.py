@@ -27,7 +27,7 @@ _SYMBOLS = [
     "scff_create", "scff_destroy", "scff_last_error", "scff_basis", "scff_transitions",
     "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
-    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain",
+    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_form_factor_static",
 ]
 
 
@@ -69,6 +69,9 @@ def load(build_if_missing: bool = True):
     lib.scff_qgrid_size.restype = I64
     lib.scff_form_factor.argtypes = [P, P, P, P, ctypes.c_int, D, P, P, ctypes.c_int, P]
     lib.scff_sync.argtypes = [P, P]
+    lib.scff_form_factor_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, U32, ctypes.c_int, P,
+                                            I64, P, D, P, P, P]
+    lib.scff_form_factor_static.restype = I32
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_last_timing.argtypes = [P, P]
@@ -255,6 +258,42 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.lib.scff_kernel_launches(self.h))
+
+
+def form_factor_static(mol, T_dev, q_dev, f_dev, f2_dev=None, scale: float = 1.0, renorm: bool = True,
+                       stream=None):
+    """FP64 form factor on an explicit q list without any device allocation.
+
+    For callers that cannot allocate device memory themselves at run time
+    (for example inside a framework whose caching allocator owns the device
+    memory, or a serving loop that must not synchronise on cudaMalloc): T_dev
+    [S, nbf, nbf], q_dev [n, 3], f_dev [S, n, 2] and f2_dev [S, n] are the
+    caller's float64 CUDA tensors; the library's intermediates live in a fixed
+    device array of its own.  Limits and sharing rules are in include/scff.h
+    (scff_form_factor_static).  Blocks until the work on `stream` is done.
+    """
+    lib = load()
+    import torch
+    for name, t in (("T_dev", T_dev), ("q_dev", q_dev), ("f_dev", f_dev)):
+        if not _is_torch_cuda(t) or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    S = int(T_dev.shape[0])
+    n = int(q_dev.shape[0])
+    if tuple(f_dev.shape) != (S, n, 2) or (f2_dev is not None and tuple(f2_dev.shape) != (S, n)):
+        raise ValueError("output shapes must be [S, n, 2] and [S, n]")
+    xyz = _np(mol.xyz, np.float64)
+    sa, sl, sn = _np(mol.shell_atom, np.int32), _np(mol.shell_l, np.int32), _np(mol.shell_nprim, np.int32)
+    ex, co = _np(mol.exponents, np.float64), _np(mol.coefficients, np.float64)
+    if stream is None:
+        stream = torch.cuda.current_stream(f_dev.device)
+    sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib.scff_form_factor_static(int(xyz.shape[0]), _p(xyz), int(sl.shape[0]), _p(sa), _p(sl), _p(sn), _p(ex),
+                                     _p(co), RENORM_CONTRACTED if renorm else 0, S,
+                                     ctypes.c_void_p(T_dev.data_ptr()), n, ctypes.c_void_p(q_dev.data_ptr()),
+                                     float(scale), ctypes.c_void_p(f_dev.data_ptr()),
+                                     ctypes.c_void_p(f2_dev.data_ptr()) if f2_dev is not None else None, sp)
+    _check(rc)
+    return f_dev, f2_dev
 
 
 def evaluate_job(ctx: Context, job, precision=FP32, scale: float = 1.0, q_list=None):
