@@ -159,6 +159,42 @@ scff_status scff_form_factor(scff_ctx *ctx, scff_basis_h basis, scff_trans_h tra
                              scff_qgrid_h grid, int precision, double scale, void *f_out,
                              void *f2_out, int out_on_device, void *stream);
 
+/*
+ * Batches.  A plan evaluates a fixed list of jobs -- each a (basis,
+ * transitions, q-grid) triple with its own scale and caller-owned DEVICE
+ * outputs laid out as in scff_form_factor -- in one precision.  Jobs with a
+ * product grid and a tensor-core precision are grouped so that each group's
+ * tables and A images fit the workspace, and each group runs as ONE
+ * persistent kernel launch over all of its output tiles (one CTA per SM,
+ * tiles ordered by cost).  A tile's arithmetic does not depend on the other
+ * jobs, so a job gives the same result alone and in any batch.  Other jobs
+ * run the direct path.  The handles must stay alive while the plan exists.
+ *   workspace_bytes  bound on the plan's device memory (0 = the context
+ *                    budget, at most 64 GiB); a job that alone exceeds it
+ *                    gives SCFF_ERR_ADMISSION.
+ * scff_plan_run launches the plan's kernels on `stream` (asynchronous; no
+ * allocation and no synchronisation inside, so it may be captured).
+ * scff_plan_run_graph captures one run into a CUDA graph on its first call
+ * and replays that graph on every call (stream must not be NULL).
+ * scff_plan_info: info[0..5] = jobs, tensor-core jobs, groups, tiles,
+ * device bytes, kernel launches per run.
+ */
+typedef struct {
+    scff_basis_h basis;
+    scff_trans_h trans;
+    scff_qgrid_h grid;
+    double scale;
+    void *f_out;   /* device [S][n_q][2] */
+    void *f2_out;  /* device [S][n_q] or NULL */
+} scff_job;
+typedef struct scff_plan_s *scff_plan_h;
+scff_status scff_plan_create(scff_ctx *ctx, int n_jobs, const scff_job *jobs, int precision,
+                             uint64_t workspace_bytes, scff_plan_h *out);
+scff_status scff_plan_run(scff_ctx *ctx, scff_plan_h plan, void *stream);
+scff_status scff_plan_run_graph(scff_ctx *ctx, scff_plan_h plan, void *stream);
+scff_status scff_plan_info(scff_ctx *ctx, scff_plan_h plan, int64_t *info);
+void scff_release_plan(scff_ctx *ctx, scff_plan_h plan);
+
 /* Waits for all work on `stream` and reports the device status word:
  * SCFF_ERR_TIMEOUT if a device-side wait of an asynchronous call gave up. */
 scff_status scff_sync(scff_ctx *ctx, void *stream);

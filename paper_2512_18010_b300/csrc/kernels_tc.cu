@@ -33,6 +33,10 @@
 #include "scff_internal.h"
 #include "tc_internal.h"
 
+#include <algorithm>
+#include <string.h>
+#include <vector>
+
 namespace scff {
 namespace tc {
 
@@ -360,31 +364,16 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
     }
 }
 
-// ------------------------------------------------------------------ main kernel
+// ------------------------------------------------------------------ persistent main kernel
 
-struct MainParams {
-    const uint8_t *A;
-    const float2 *Y, *Z;
-    const int4 *kinfo;
-    int ny, nz;
-    int64_t N;
-    int nkc;
-    int M, nx;
-    int64_t nq;
-    float scale;
-    float2 *f;
-    float *f2;
-    int *err;
-    int drain_every;
-};
-
-// Adds the finished accumulator group gd (TMEM set gd & 1) into this
-// thread's FP32 register sums: row = TMEM lane, CQ columns of Re and of Im.
+// Adds the finished accumulator group with global index gg (TMEM set gg & 1)
+// into this thread's FP32 register sums: row = TMEM lane, CQ columns of Re
+// and of Im.
 template <int CQ>
-__device__ __forceinline__ bool drain_group(int gd, uint64_t *accFull, uint64_t *accEmpty, uint32_t tmem, int lg,
+__device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t *accEmpty, uint32_t tmem, int lg,
                                             int lane, int colh, float (&acc_re)[CQ], float (&acc_im)[CQ]) {
-    const int set = gd & 1;
-    const bool got = mbar_wait(&accFull[set], (gd >> 1) & 1);
+    const int set = gg & 1;
+    const bool got = mbar_wait(&accFull[set], (gg >> 1) & 1);
     if (__any_sync(0xffffffffu, !got)) return false;
     tc_fence_after();
     const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + set * (2 * BN) + colh;
@@ -406,8 +395,17 @@ __device__ __forceinline__ bool drain_group(int gd, uint64_t *accFull, uint64_t 
     return true;
 }
 
+// One CTA per SM walks its share of the work list: items blockIdx.x,
+// blockIdx.x + gridDim.x, ... of a list sorted by cost.  An item is one
+// 128 x 128 output tile of one job; its contraction runs over the job's k
+// chunks.  Stage slots, mbarrier phases and the two TMEM accumulator sets
+// are counted globally across items, so consecutive items pipeline without
+// re-initialisation.  Each tile's reduction order depends only on its own
+// job, never on the rest of the batch.
 template <int KIND>
-__global__ void __launch_bounds__(THREADS, 1) tc_main_kernel(MainParams p) {
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_persistent_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items,
+                         int drain_every, int *err) {
     using KD = Kind<KIND>;
     constexpr bool TF32 = KD::TF32;
     constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = KD::STAGES;
@@ -427,10 +425,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_main_kernel(MainParams p) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3 * STAGES + 5);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nt = blockIdx.x, mt = blockIdx.y;
-    const int nkc = p.nkc;
-    const int G = p.drain_every >= 1 ? max(2, min(p.drain_every, nkc)) : nkc;  // chunks per accumulation group
-    const int ngroups = (nkc + G - 1) / G;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -455,157 +449,189 @@ __global__ void __launch_bounds__(THREADS, 1) tc_main_kernel(MainParams p) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(LOW_REGS));
         if (warp == 0 && lane == 0) {
             // ---------------- TMA producer: A tile and the chunk's k-index records
-            for (int it = 0; it < nkc; ++it) {
-                const int s = it % STAGES;
-                if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1)) {
-                    *abort_flag = 1;
-                    break;
+            int gc = 0;  // global chunk counter
+            for (int idx = blockIdx.x; idx < n_items && !*abort_flag; idx += gridDim.x) {
+                const int4 item = items[idx];
+                const TcJobDev &J = jobs[item.x];
+                const uint8_t *Abase = J.A + (size_t)item.y * J.nkc * A_STAGE;
+                for (int it = 0; it < J.nkc; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    if (gc >= STAGES && !mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *st = smem + s * STAGE;
+                    mbar_arrive_expect_tx(&fullA[s], A_STAGE + BK * 16);
+                    bulk_g2s(st, Abase + (size_t)it * A_STAGE, A_STAGE, &fullA[s]);
+                    bulk_g2s(st + A_STAGE + W_STAGE, J.kinfo + (size_t)it * BK, BK * 16, &fullA[s]);
                 }
-                uint8_t *st = smem + s * STAGE;
-                mbar_arrive_expect_tx(&fullA[s], A_STAGE + BK * 16);
-                bulk_g2s(st, p.A + ((size_t)mt * nkc + it) * A_STAGE, A_STAGE, &fullA[s]);
-                bulk_g2s(st + A_STAGE + W_STAGE, p.kinfo + (size_t)it * BK, BK * 16, &fullA[s]);
             }
         } else if (warp == 1 && lane == 0) {
-            // ---------------- MMA issuer: group g accumulates into TMEM set g & 1
+            // ---------------- MMA issuer: global group gg accumulates into TMEM set gg & 1
             constexpr uint32_t ID = idesc_mma<TF32>(false), IDN = idesc_mma<TF32>(true);
-            for (int it = 0; it < nkc; ++it) {
-                const int s = it % STAGES;
-                const uint32_t par = (it / STAGES) & 1;
-                if (*abort_flag || !mbar_wait(&fullA[s], par) || !mbar_wait(&fullW[s], par)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                const int g = it / G, set = g & 1;
-                const bool first = (it % G) == 0;
-                if (first && g >= 2 && !mbar_wait(&accEmpty[set], ((g - 2) >> 1) & 1)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t t_re = tmem + set * (2 * BN), t_im = t_re + BN;
-                const uint32_t a0 = smem_u32(smem + s * STAGE);
-                const uint32_t w0 = a0 + A_STAGE;
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint32_t ko = kk * 32;  // 32 bytes = one MMA K step
-#pragma unroll
-                    for (int pq = 0; pq < KD::NPROD; ++pq) {
-                        const int qa = prod_a(pq), qw = prod_w(pq);
-                        const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
-                        const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
-                        const uint64_t wr = smem_desc_sw64(w0 + qw * W_ARR + ko);
-                        const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
-                        const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
-                        mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
-                        mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
-                        mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
-                        mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+            int gc = 0, gbase = 0;
+            for (int idx = blockIdx.x; idx < n_items && !*abort_flag; idx += gridDim.x) {
+                const int nkc = items[idx].w;
+                const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
+                bool ok = true;
+                for (int it = 0; it < nkc; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    const uint32_t par = (gc / STAGES) & 1;
+                    if (*abort_flag || !mbar_wait(&fullA[s], par) || !mbar_wait(&fullW[s], par)) {
+                        ok = false;
+                        break;
                     }
+                    const int gg = gbase + it / G, set = gg & 1;
+                    const bool first = (it % G) == 0;
+                    if (first && gg >= 2 && !mbar_wait(&accEmpty[set], ((gg - 2) >> 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t t_re = tmem + set * (2 * BN), t_im = t_re + BN;
+                    const uint32_t a0 = smem_u32(smem + s * STAGE);
+                    const uint32_t w0 = a0 + A_STAGE;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t ko = kk * 32;  // 32 bytes = one MMA K step
+#pragma unroll
+                        for (int pq = 0; pq < KD::NPROD; ++pq) {
+                            const int qa = prod_a(pq), qw = prod_w(pq);
+                            const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
+                            const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
+                            const uint64_t wr = smem_desc_sw64(w0 + qw * W_ARR + ko);
+                            const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
+                            const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
+                            mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
+                            mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
+                            mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
+                            mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    if ((it % G) == G - 1 || it == nkc - 1) mma_commit(&accFull[set]);
                 }
-                mma_commit(&empty[s]);
-                if ((it % G) == G - 1 || it == nkc - 1) mma_commit(&accFull[set]);
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                gbase += (nkc + G - 1) / G;
             }
         }
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(HIGH_REGS));
         // ---------------- W generators (two threads per W row); they also
-        // drain finished accumulator groups into FP32 registers.
+        // drain finished accumulator groups into FP32 registers and write the
+        // finished tile.
         const int gt = threadIdx.x - 128;          // 0..255
         const int wrow = gt & (BN - 1);            // W row
         const int khalf = gt / BN;                 // which half of the chunk's k
-        const int64_t n = (int64_t)nt * BN + wrow;
-        const bool nvalid = n < p.N;
-        const int iy = nvalid ? (int)(n / p.nz) : 0, iz = nvalid ? (int)(n % p.nz) : 0;
-        const float vmask = nvalid ? 1.f : 0.f;
-        const float2 *Yc = p.Y + iy;
-        const float2 *Zc = p.Z + iz;
         // drain mapping: TMEM lane group = warp % 4 (hardware rule); the two
         // warps of a lane group take column halves.
         const int lg = warp & 3;
         const int colh = ((warp - 4) >> 2) * CQ;
-        float acc_re[CQ], acc_im[CQ];
-#pragma unroll
-        for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
-        int drained = 0;
+        int gc = 0, gbase = 0;
         bool ok = true;
-        for (int it = 0; it < nkc && ok; ++it) {
-            const int s = it % STAGES;
-            bool w = mbar_wait(&fullA[s], (it / STAGES) & 1);  // k-index records of this chunk
-            if (w && it >= STAGES) w = mbar_wait(&empty[s], ((it / STAGES) - 1) & 1);
-            if (__any_sync(0xffffffffu, !w) || *abort_flag) {
-                ok = false;
-                break;
-            }
-            uint8_t *st = smem + s * STAGE;
-            const int4 *kin = reinterpret_cast<const int4 *>(st + A_STAGE + W_STAGE) + khalf * KH;
-            uint8_t *wst = st + A_STAGE;
+        for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+            const int4 item = items[idx];
+            const TcJobDev &J = jobs[item.x];
+            const int nkc = item.w;
+            const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
+            const int ngroups = (nkc + G - 1) / G;
+            const int ny = J.ny, nz = J.nz;
+            const int64_t n = (int64_t)item.z * BN + wrow;
+            const bool nvalid = n < J.N;
+            const int iy = nvalid ? (int)(n / nz) : 0, iz = nvalid ? (int)(n % nz) : 0;
+            const float vmask = nvalid ? 1.f : 0.f;
+            const float2 *Yc = J.Y + iy;
+            const float2 *Zc = J.Z + iz;
+            float acc_re[CQ], acc_im[CQ];
 #pragma unroll
-            for (int sb = 0; sb < KH; sb += KSUB) {
-                float2 y[KSUB], z[KSUB];
-#pragma unroll
-                for (int e = 0; e < KSUB; ++e) {
-                    const int4 ki = kin[sb + e];
-                    y[e] = Yc[(size_t)(ki.w + ki.y) * p.ny];
-                    z[e] = Zc[(size_t)(ki.w + ki.z) * p.nz];
-                }
-#pragma unroll
-                for (int jv = 0; jv < KSUB / V; ++jv) {
-                    float re[V], im[V];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const float2 a = y[jv * V + e], b = z[jv * V + e];
-                        re[e] = vmask * (a.x * b.x - a.y * b.y);
-                        im[e] = vmask * (a.x * b.y + a.y * b.x);
-                    }
-                    uint4 pr_[NP], pi_[NP];
-                    split_vec<KIND>(re, pr_);
-                    split_vec<KIND>(im, pi_);
-                    const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
-                        *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
-                    }
-                }
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&fullW[s]);
-            // Group gd is complete once the MMAs of chunk (gd+1)G-1 are; that is
-            // guaranteed STAGES chunks later, so drain it then without stalling.
-            while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
-                if (!drain_group<CQ>(drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) {
+            for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
+            const int gc0 = gc;
+            int drained = 0;
+            for (int it = 0; it < nkc && ok; ++it, ++gc) {
+                const int s = gc % STAGES;
+                bool w = mbar_wait(&fullA[s], (gc / STAGES) & 1);  // k-index records of this chunk
+                if (w && gc >= STAGES) w = mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
+                if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                     ok = false;
                     break;
                 }
+                uint8_t *st = smem + s * STAGE;
+                const int4 *kin = reinterpret_cast<const int4 *>(st + A_STAGE + W_STAGE) + khalf * KH;
+                uint8_t *wst = st + A_STAGE;
+#pragma unroll
+                for (int sb = 0; sb < KH; sb += KSUB) {
+                    float2 y[KSUB], z[KSUB];
+#pragma unroll
+                    for (int e = 0; e < KSUB; ++e) {
+                        const int4 ki = kin[sb + e];
+                        y[e] = Yc[(size_t)(ki.w + ki.y) * ny];
+                        z[e] = Zc[(size_t)(ki.w + ki.z) * nz];
+                    }
+#pragma unroll
+                    for (int jv = 0; jv < KSUB / V; ++jv) {
+                        float re[V], im[V];
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const float2 a = y[jv * V + e], b = z[jv * V + e];
+                            re[e] = vmask * (a.x * b.x - a.y * b.y);
+                            im[e] = vmask * (a.x * b.y + a.y * b.x);
+                        }
+                        uint4 pr_[NP], pi_[NP];
+                        split_vec<KIND>(re, pr_);
+                        split_vec<KIND>(im, pi_);
+                        const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
+                            *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
+                        }
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fullW[s]);
+                // Local group gd is complete once the MMAs of its last chunk
+                // are; that is guaranteed STAGES chunks later, so drain it then
+                // without stalling the tensor pipe.
+                while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
+                    if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) {
+                        ok = false;
+                        break;
+                    }
+                    ++drained;
+                }
+            }
+            while (ok && drained < ngroups) {
+                if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im))
+                    ok = false;
                 ++drained;
             }
-        }
-        while (ok && drained < ngroups) {
-            if (!drain_group<CQ>(drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) ok = false;
-            ++drained;
-        }
-        if (!ok) *abort_flag = 1;
-        const int row = lg * 32 + lane;
-        const int m = mt * BM + row;
-        if (ok && m < p.M) {
-            const int sidx = m / p.nx, ix = m % p.nx;
-            const int64_t n0 = (int64_t)nt * BN + colh;
-            float2 *frow = p.f + (size_t)sidx * p.nq + (size_t)ix * p.N;
-            float *f2row = p.f2 ? p.f2 + (size_t)sidx * p.nq + (size_t)ix * p.N : nullptr;
+            gbase += ngroups;
+            gc = gc0 + nkc;
+            const int m = item.y * BM + lg * 32 + lane;
+            if (ok && m < J.M) {
+                const int sidx = m / J.nx, ix = m % J.nx;
+                const int64_t n0 = (int64_t)item.z * BN + colh;
+                float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
+                float *f2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ix * J.N : nullptr;
+                const float sc = J.scale;
 #pragma unroll
-            for (int j = 0; j < CQ; ++j) {
-                const int64_t nn = n0 + j;
-                if (nn < p.N) {
-                    const float2 v = make_float2(p.scale * acc_re[j], p.scale * acc_im[j]);
-                    frow[nn] = v;
-                    if (f2row) f2row[nn] = v.x * v.x + v.y * v.y;
+                for (int j = 0; j < CQ; ++j) {
+                    const int64_t nn = n0 + j;
+                    if (nn < J.N) {
+                        const float2 v = make_float2(sc * acc_re[j], sc * acc_im[j]);
+                        frow[nn] = v;
+                        if (f2row) f2row[nn] = v.x * v.x + v.y * v.y;
+                    }
                 }
             }
         }
+        if (!ok) *abort_flag = 1;
     }
-    if (threadIdx.x == 0 && *abort_flag) flag_error(p.err, kDevErrTimeout);
+    if (threadIdx.x == 0 && *abort_flag) flag_error(err, kDevErrTimeout);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -616,30 +642,61 @@ __global__ void __launch_bounds__(THREADS, 1) tc_main_kernel(MainParams p) {
 
 }  // namespace tc
 
-static int kind_of(int precision_kind) { return precision_kind; }
+// ------------------------------------------------------------------ host side
 
-size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
-    switch (kind_of(kind)) {
+size_t tc_job_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
+    switch (kind) {
     case tc::KIND_BF16X2: return tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz).total;
     case tc::KIND_BF16X3: return tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz).total;
     default: return tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz).total;
     }
 }
 
+size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
+    const tc::Layout L = kind == tc::KIND_BF16X2   ? tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz)
+                         : kind == tc::KIND_BF16X3 ? tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz)
+                                                   : tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz);
+    return L.total + 1024 + sizeof(TcJobDev) + sizeof(int4) * (size_t)L.n_mt * L.n_nt;
+}
+
+// Descriptor of one job whose tables and A image live in `ws`.
 template <int KIND>
-static cudaError_t launch_tc_t(const TcArgs &a, int64_t *launches, cudaStream_t st) {
+static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
+    using namespace tc;
+    const Layout L = make_layout_k<KIND>(*a.ps, a.S, a.nx, a.ny, a.nz);
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    jd->A = w + L.off_A;
+    jd->Y = reinterpret_cast<float2 *>(w + L.off_Y);
+    jd->Z = reinterpret_cast<float2 *>(w + L.off_Z);
+    jd->kinfo = reinterpret_cast<int4 *>(w + L.off_k);
+    jd->ny = a.ny;
+    jd->nz = a.nz;
+    jd->nx = a.nx;
+    jd->nkc = L.nkc;
+    jd->M = L.M;
+    jd->n_mt = L.n_mt;
+    jd->n_nt = L.n_nt;
+    jd->N = L.N;
+    jd->nq = (int64_t)a.nx * L.N;
+    jd->scale = (float)a.scale;
+    jd->f = reinterpret_cast<float2 *>(a.f);
+    jd->f2 = a.f2;
+}
+
+// Tables, k-index and the A image of one job in `ws` (tc_job_bytes bytes).
+template <int KIND>
+static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launches, cudaStream_t st) {
     using namespace tc;
     using KD = Kind<KIND>;
     const PairSetDev &ps = *a.ps;
     const Layout L = make_layout_k<KIND>(ps, a.S, a.nx, a.ny, a.nz);
-    if (L.total > a.ws_bytes) return cudaErrorInvalidValue;
-    if (L.n_mt > 65535) return cudaErrorInvalidConfiguration;
-    uint8_t *ws = static_cast<uint8_t *>(a.ws);
-    float2 *X = reinterpret_cast<float2 *>(ws + L.off_X);
-    float2 *Y = reinterpret_cast<float2 *>(ws + L.off_Y);
-    float2 *Z = reinterpret_cast<float2 *>(ws + L.off_Z);
-    int4 *kinfo = reinterpret_cast<int4 *>(ws + L.off_k);
-    uint8_t *Abuf = ws + L.off_A;
+    if (L.n_mt > (1 << 24)) return cudaErrorInvalidConfiguration;
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    float2 *X = reinterpret_cast<float2 *>(w + L.off_X);
+    float2 *Y = reinterpret_cast<float2 *>(w + L.off_Y);
+    float2 *Z = reinterpret_cast<float2 *>(w + L.off_Z);
+    int4 *kinfo = reinterpret_cast<int4 *>(w + L.off_k);
+    uint8_t *Abuf = w + L.off_A;
     const double *qa[3] = {a.qx, a.qy, a.qz};
     float2 *tab[3] = {X, Y, Z};
     const int na[3] = {a.nx, a.ny, a.nz};
@@ -655,51 +712,107 @@ static cudaError_t launch_tc_t(const TcArgs &a, int64_t *launches, cudaStream_t 
                                                                            L.K_pad, L.nkc, L.M, L.M_pad, Abuf);
     }
     if (launches) *launches += 5;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (jd) job_desc_t<KIND>(a, ws, jd);
+    return cudaGetLastError();
+}
+
+void tc_job_desc(const TcArgs &a, void *ws, TcJobDev *jd) {
+    switch (a.kind) {
+    case tc::KIND_BF16X2: job_desc_t<tc::KIND_BF16X2>(a, ws, jd); break;
+    case tc::KIND_BF16X3: job_desc_t<tc::KIND_BF16X3>(a, ws, jd); break;
+    default: job_desc_t<tc::KIND_TF32X2>(a, ws, jd); break;
+    }
+}
+
+cudaError_t tc_prep_job(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launches, cudaStream_t st) {
+    switch (a.kind) {
+    case tc::KIND_BF16X2: return prep_job_t<tc::KIND_BF16X2>(a, ws, jd, launches, st);
+    case tc::KIND_BF16X3: return prep_job_t<tc::KIND_BF16X3>(a, ws, jd, launches, st);
+    default: return prep_job_t<tc::KIND_TF32X2>(a, ws, jd, launches, st);
+    }
+}
+
+// Work list of a group of prepared jobs: every (job, m-tile, n-tile), most
+// expensive first (longest k loop), so the static round-robin assignment of
+// items to CTAs balances well.
+void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) {
+    items.clear();
+    for (int j = 0; j < n_jobs; ++j)
+        for (int mt = 0; mt < jobs[j].n_mt; ++mt)
+            for (int nt = 0; nt < jobs[j].n_nt; ++nt) items.push_back(make_int4(j, mt, nt, jobs[j].nkc));
+    std::stable_sort(items.begin(), items.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
+}
+
+template <int KIND>
+static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
+                                int grid_ctas, int64_t *launches, cudaStream_t st) {
+    using namespace tc;
+    using KD = Kind<KIND>;
     static bool attr_set = false;
+    cudaError_t e;
     if (!attr_set) {
         // The register split inside the kernel assumes exactly LAUNCH_REGS
         // registers per thread at launch; anything else could leave the
         // increasing warpgroups waiting, so refuse to launch.
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, tc_main_kernel<KIND>);
+        e = cudaFuncGetAttributes(&fa, tc_persistent_kernel<KIND>);
         if (e != cudaSuccess) return e;
         if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
-        e = cudaFuncSetAttribute(tc_main_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, KD::SMEM_BYTES);
+        e = cudaFuncSetAttribute(tc_persistent_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 KD::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    MainParams p;
-    p.A = Abuf;
-    p.Y = Y;
-    p.Z = Z;
-    p.kinfo = kinfo;
-    p.ny = a.ny;
-    p.nz = a.nz;
-    p.N = L.N;
-    p.nkc = L.nkc;
-    p.M = L.M;
-    p.nx = a.nx;
-    p.nq = (int64_t)a.nx * L.N;
-    p.scale = (float)a.scale;
-    p.f = reinterpret_cast<float2 *>(a.f);
-    p.f2 = a.f2;
-    p.err = a.err;
-    p.drain_every = a.drain_every;
-    if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
-    dim3 grid((unsigned)L.n_nt, (unsigned)L.n_mt);
-    tc_main_kernel<KIND><<<grid, THREADS, KD::SMEM_BYTES, st>>>(p);
+    if (n_items <= 0) return cudaSuccess;
+    const int grid = std::max(1, std::min(grid_ctas, n_items));
+    tc_persistent_kernel<KIND><<<grid, THREADS, KD::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st) {
-    switch (a.kind) {
-    case tc::KIND_BF16X2: return launch_tc_t<tc::KIND_BF16X2>(a, launches, st);
-    case tc::KIND_BF16X3: return launch_tc_t<tc::KIND_BF16X3>(a, launches, st);
-    default: return launch_tc_t<tc::KIND_TF32X2>(a, launches, st);
+cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
+                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st) {
+    switch (kind) {
+    case tc::KIND_BF16X2: return persistent_t<tc::KIND_BF16X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st);
+    case tc::KIND_BF16X3: return persistent_t<tc::KIND_BF16X3>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st);
+    default: return persistent_t<tc::KIND_TF32X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st);
     }
+}
+
+int tc_num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+// Single job: prepare it in the workspace, then one persistent launch over
+// its tiles.  The job descriptor and work list go to the end of the workspace.
+cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st) {
+    const size_t jb = tc_job_bytes(*a.ps, a.S, a.nx, a.ny, a.nz, a.kind);
+    if (jb + 1024 + sizeof(TcJobDev) > a.ws_bytes) return cudaErrorInvalidValue;
+    TcJobDev jd;
+    memset(&jd, 0, sizeof(jd));
+    cudaError_t e = tc_prep_job(a, a.ws, &jd, launches, st);
+    if (e != cudaSuccess) return e;
+    std::vector<int4> items;
+    tc_build_items(&jd, 1, items);
+    uint8_t *tail = static_cast<uint8_t *>(a.ws) + (jb + 255) / 256 * 256;
+    TcJobDev *d_job = reinterpret_cast<TcJobDev *>(tail);
+    int4 *d_items = reinterpret_cast<int4 *>(tail + 256);
+    if ((size_t)(tail + 256 - static_cast<uint8_t *>(a.ws)) + sizeof(int4) * items.size() > a.ws_bytes)
+        return cudaErrorInvalidValue;
+    e = cudaMemcpyAsync(d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
+    return tc_launch_persistent(a.kind, d_job, d_items, (int)items.size(), a.drain_every, a.err, tc_num_sms(),
+                                launches, st);
 }
 
 }  // namespace scff

@@ -76,6 +76,7 @@ struct scff_ctx {
     std::vector<struct scff_basis_s *> bases;
     std::vector<struct scff_trans_s *> transs;
     std::vector<struct scff_qgrid_s *> grids;
+    std::vector<struct scff_plan_s *> plans;
 };
 
 struct scff_basis_s {
@@ -201,6 +202,8 @@ static void free_grid(scff_qgrid_s *g) {
     delete g;
 }
 
+static void free_plan_any(struct scff_plan_s *p);
+
 extern "C" void scff_destroy(scff_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
@@ -208,6 +211,7 @@ extern "C" void scff_destroy(scff_ctx *c) {
     for (auto *t : c->transs) free_trans(t);
     for (auto *b : c->bases) free_basis(b);
     for (auto *g : c->grids) free_grid(g);
+    for (auto *p : c->plans) free_plan_any(p);
     DevBuf *bufs[] = {&c->coef, &c->geom, &c->gx, &c->gy, &c->gz, &c->fstage, &c->f2stage, &c->tc_ws};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -665,4 +669,353 @@ extern "C" scff_status scff_sync(scff_ctx *c, void *stream) {
     CUDA_TRY(cudaStreamSynchronize(st));
     if (*c->h_err) return fail(SCFF_ERR_TIMEOUT, "scff_sync: a device-side wait timed out (code %d)", *c->h_err);
     return SCFF_OK;
+}
+
+// ------------------------------------------------------------------ batches (plans)
+//
+// A plan holds a fixed list of form-factor jobs and every device buffer their
+// evaluation needs.  Tensor-core jobs (product grids, split precisions) are
+// grouped so that each group's tables and A images fit the workspace; a
+// group is evaluated by one persistent launch over all of its tiles.  The
+// other jobs run the direct path one after the other.  scff_plan_run only
+// launches kernels (no allocation, no synchronisation), so it can be
+// captured; scff_plan_run_graph captures it once and replays the graph.
+
+struct PlanJob {
+    scff_job job;
+    int tc;            // tensor-core job
+    int group;         // group index (tensor-core jobs)
+    size_t region;     // offset of the job's tables and A image in the group area
+    int S, S_pad;
+};
+
+struct scff_plan_s {
+    scff_ctx *ctx;
+    int precision;
+    int tc_kind;
+    int SB;
+    std::vector<PlanJob> jobs;
+    std::vector<std::vector<int>> groups;
+    std::vector<size_t> group_desc, group_items;  // offsets in dev
+    std::vector<int> group_nitems;
+    void *dev = nullptr;
+    size_t dev_bytes = 0;
+    size_t off_geom = 0, off_coef = 0, off_tab = 0, off_group = 0;
+    size_t tab_stride = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int64_t launches_per_run = 0;
+};
+
+static size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
+
+extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job *jobs, int precision,
+                                        uint64_t workspace_bytes, scff_plan_h *out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: NULL context or output");
+    *out = nullptr;
+    if (n_jobs <= 0 || !jobs) return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: no jobs");
+    if (precision < SCFF_FP64 || precision > SCFF_BF16X2)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: precision %d", precision);
+    cudaSetDevice(c->device);
+    const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
+    const bool fp64 = precision == SCFF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    scff_plan_s *P = new scff_plan_s();
+    P->ctx = c;
+    P->precision = precision;
+    P->tc_kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+    P->SB = fp64 ? 4 : 8;
+    uint64_t budget = workspace_bytes ? workspace_bytes : std::min<uint64_t>(c->budget, 64ull << 30);
+    size_t geom_max = 256, coef_max = 256, tab_max = 256;
+    for (int i = 0; i < n_jobs; ++i) {
+        const scff_job &j = jobs[i];
+        if (!j.basis || std::find(c->bases.begin(), c->bases.end(), j.basis) == c->bases.end() || !j.trans ||
+            std::find(c->transs.begin(), c->transs.end(), j.trans) == c->transs.end() || !j.grid ||
+            std::find(c->grids.begin(), c->grids.end(), j.grid) == c->grids.end()) {
+            delete P;
+            return fail(SCFF_ERR_NOT_FOUND, "scff_plan_create: job %d has an unknown handle", i);
+        }
+        if (j.trans->basis != j.basis || !j.f_out || !isfinite(j.scale)) {
+            delete P;
+            return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: job %d is inconsistent", i);
+        }
+        PlanJob pj;
+        pj.job = j;
+        pj.tc = tc_prec && j.grid->product;
+        pj.group = -1;
+        pj.region = 0;
+        pj.S = j.trans->S;
+        pj.S_pad = (pj.S + P->SB - 1) / P->SB * P->SB;
+        const PairSetDev &ps = j.basis->dev;
+        geom_max = std::max(geom_max, (size_t)ps.n_pair * 4 * sizeof(double));
+        coef_max = std::max(coef_max, (size_t)pj.S_pad * ps.n_rows * (pj.tc ? sizeof(float) : rsz));
+        if (!pj.tc && j.grid->product)
+            tab_max = std::max(tab_max, (size_t)ps.n_pair * std::max(j.grid->nx, std::max(j.grid->ny, j.grid->nz)) * 2 * rsz);
+        P->jobs.push_back(pj);
+    }
+    // Greedy grouping of tensor-core jobs by footprint, largest first.
+    std::vector<int> order;
+    for (int i = 0; i < n_jobs; ++i)
+        if (P->jobs[i].tc) order.push_back(i);
+    auto bytes_of = [&](int i) {
+        const PlanJob &pj = P->jobs[i];
+        return up1k(tc_job_bytes(pj.job.basis->dev, pj.S, pj.job.grid->nx, pj.job.grid->ny, pj.job.grid->nz,
+                                 P->tc_kind));
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes_of(a) > bytes_of(b); });
+    const size_t fixed = up1k(geom_max) + up1k(coef_max) + 3 * up1k(tab_max);
+    if (fixed >= budget) {
+        delete P;
+        return fail(SCFF_ERR_ADMISSION, "scff_plan_create: workspace budget %llu below the fixed scratch %zu",
+                    (unsigned long long)budget, fixed);
+    }
+    const size_t area_budget = budget - fixed;
+    size_t area_max = 0, cur = 0;
+    for (int i : order) {
+        const size_t b = bytes_of(i);
+        if (b > area_budget) {
+            delete P;
+            return fail(SCFF_ERR_ADMISSION, "scff_plan_create: job %d needs %zu bytes, above the budget %zu", i, b,
+                        area_budget);
+        }
+        if (P->groups.empty() || cur + b > area_budget) {
+            P->groups.emplace_back();
+            cur = 0;
+        }
+        P->jobs[i].group = (int)P->groups.size() - 1;
+        P->jobs[i].region = cur;
+        P->groups.back().push_back(i);
+        cur += b;
+        area_max = std::max(area_max, cur);
+    }
+    // descriptors and work lists of every group (kept for the plan's lifetime)
+    size_t desc_bytes = 0;
+    std::vector<std::vector<TcJobDev>> gdesc(P->groups.size());
+    std::vector<std::vector<int4>> gitems(P->groups.size());
+    P->off_geom = 0;
+    P->off_coef = up1k(geom_max);
+    P->off_tab = P->off_coef + up1k(coef_max);
+    P->tab_stride = up1k(tab_max);
+    P->off_group = P->off_tab + 3 * P->tab_stride;
+    const size_t off_desc = P->off_group + up1k(area_max);
+    for (size_t g = 0; g < P->groups.size(); ++g) {
+        P->group_desc.push_back(off_desc + desc_bytes);
+        desc_bytes += up1k(sizeof(TcJobDev) * P->groups[g].size());
+        P->group_items.push_back(0);
+        P->group_nitems.push_back(0);
+    }
+    // work lists need the descriptors (tile counts), which need addresses: allocate first
+    size_t items_bytes = 0;
+    std::vector<size_t> nitems_est(P->groups.size(), 0);
+    for (size_t g = 0; g < P->groups.size(); ++g) {
+        for (int i : P->groups[g]) {
+            const PlanJob &pj = P->jobs[i];
+            const int64_t M = (int64_t)pj.S * pj.job.grid->nx;
+            const int64_t N = (int64_t)pj.job.grid->ny * pj.job.grid->nz;
+            nitems_est[g] += (size_t)((M + 127) / 128) * (size_t)((N + 127) / 128);
+        }
+        items_bytes += up1k(sizeof(int4) * nitems_est[g]);
+    }
+    P->dev_bytes = off_desc + desc_bytes + items_bytes;
+    if (cudaMalloc(&P->dev, P->dev_bytes) != cudaSuccess) {
+        delete P;
+        return fail(SCFF_ERR_OOM, "scff_plan_create: cannot allocate %zu bytes", P->dev_bytes);
+    }
+    uint8_t *base = static_cast<uint8_t *>(P->dev);
+    size_t ioff = off_desc + desc_bytes;
+    for (size_t g = 0; g < P->groups.size(); ++g) {
+        for (int i : P->groups[g]) {
+            const PlanJob &pj = P->jobs[i];
+            TcArgs ta;
+            memset(&ta, 0, sizeof(ta));
+            ta.ps = &pj.job.basis->dev;
+            ta.S = pj.S;
+            ta.nx = pj.job.grid->nx;
+            ta.ny = pj.job.grid->ny;
+            ta.nz = pj.job.grid->nz;
+            ta.scale = pj.job.scale;
+            ta.f = (float *)pj.job.f_out;
+            ta.f2 = (float *)pj.job.f2_out;
+            ta.kind = P->tc_kind;
+            TcJobDev jd;
+            memset(&jd, 0, sizeof(jd));
+            tc_job_desc(ta, base + P->off_group + pj.region, &jd);
+            gdesc[g].push_back(jd);
+        }
+        tc_build_items(gdesc[g].data(), (int)gdesc[g].size(), gitems[g]);
+        P->group_items[g] = ioff;
+        P->group_nitems[g] = (int)gitems[g].size();
+        ioff += up1k(sizeof(int4) * nitems_est[g]);
+        cudaError_t e1 = cudaMemcpy(base + P->group_desc[g], gdesc[g].data(), sizeof(TcJobDev) * gdesc[g].size(),
+                                    cudaMemcpyHostToDevice);
+        cudaError_t e2 = cudaMemcpy(base + P->group_items[g], gitems[g].data(), sizeof(int4) * gitems[g].size(),
+                                    cudaMemcpyHostToDevice);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            cudaFree(P->dev);
+            delete P;
+            return fail(SCFF_ERR_CUDA, "scff_plan_create: descriptor upload failed");
+        }
+    }
+    // Kernel attributes are set outside any later stream capture.
+    if (!P->groups.empty()) tc_launch_persistent(P->tc_kind, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
+    c->plans.push_back(P);
+    *out = P;
+    return SCFF_OK;
+}
+
+static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launches) {
+    scff_ctx *c = P->ctx;
+    uint8_t *base = static_cast<uint8_t *>(P->dev);
+    double *geom = reinterpret_cast<double *>(base + P->off_geom);
+    void *coef = base + P->off_coef;
+    const bool fp64 = P->precision == SCFF_FP64;
+    CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    for (size_t g = 0; g < P->groups.size(); ++g) {
+        for (int i : P->groups[g]) {
+            const PlanJob &pj = P->jobs[i];
+            const PairSetDev &ps = pj.job.basis->dev;
+            CUDA_TRY(launch_pair_geom(ps, geom, st));
+            ++*launches;
+            CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, P->SB, pj.S_pad, nullptr, (float *)coef, launches, st));
+            TcArgs ta;
+            memset(&ta, 0, sizeof(ta));
+            ta.ps = &ps;
+            ta.coef32 = (const float *)coef;
+            ta.SB = P->SB;
+            ta.pair_geom = geom;
+            ta.qx = pj.job.grid->d_qx;
+            ta.qy = pj.job.grid->d_qy;
+            ta.qz = pj.job.grid->d_qz;
+            ta.nx = pj.job.grid->nx;
+            ta.ny = pj.job.grid->ny;
+            ta.nz = pj.job.grid->nz;
+            ta.S = pj.S;
+            ta.scale = pj.job.scale;
+            ta.f = (float *)pj.job.f_out;
+            ta.f2 = (float *)pj.job.f2_out;
+            ta.kind = P->tc_kind;
+            CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));
+        }
+        const int drain = c->drain_every >= 0 ? c->drain_every : 8;
+        CUDA_TRY(tc_launch_persistent(P->tc_kind, reinterpret_cast<const TcJobDev *>(base + P->group_desc[g]),
+                                      reinterpret_cast<const int4 *>(base + P->group_items[g]), P->group_nitems[g],
+                                      drain, c->d_err, tc_num_sms(), launches, st));
+    }
+    for (const PlanJob &pj : P->jobs) {
+        if (pj.tc) continue;
+        const PairSetDev &ps = pj.job.basis->dev;
+        const scff_qgrid_s *gq = pj.job.grid;
+        CUDA_TRY(launch_pair_geom(ps, geom, st));
+        ++*launches;
+        CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, P->SB, pj.S_pad, fp64 ? (double *)coef : nullptr,
+                                 fp64 ? nullptr : (float *)coef, launches, st));
+        DirectArgs a;
+        memset(&a, 0, sizeof(a));
+        a.ps = &ps;
+        a.coef = coef;
+        a.nq = gq->n;
+        a.S = pj.S;
+        a.SB = P->SB;
+        a.scale = pj.job.scale;
+        a.f = pj.job.f_out;
+        a.f2 = pj.job.f2_out;
+        a.err_flag = c->d_err;
+        if (gq->product) {
+            void *t0 = base + P->off_tab, *t1 = base + P->off_tab + P->tab_stride,
+                 *t2 = base + P->off_tab + 2 * P->tab_stride;
+            CUDA_TRY(launch_axis_tables(ps, geom, gq->d_qx, gq->nx, 0, t0, fp64, st));
+            CUDA_TRY(launch_axis_tables(ps, geom, gq->d_qy, gq->ny, 1, t1, fp64, st));
+            CUDA_TRY(launch_axis_tables(ps, geom, gq->d_qz, gq->nz, 2, t2, fp64, st));
+            *launches += 3;
+            a.gx = t0;
+            a.gy = t1;
+            a.gz = t2;
+            a.qax = gq->d_qx;
+            a.qay = gq->d_qy;
+            a.qaz = gq->d_qz;
+            a.nx = gq->nx;
+            a.ny = gq->ny;
+            a.nz = gq->nz;
+        } else {
+            a.qlist = gq->d_q;
+            a.pair_geom = geom;
+        }
+        CUDA_TRY(launch_direct(a, fp64 ? 1 : 0, gq->product ? 0 : 1, launches, st));
+    }
+    return SCFF_OK;
+}
+
+static bool plan_known(scff_ctx *c, scff_plan_h p) {
+    return c && p && std::find(c->plans.begin(), c->plans.end(), p) != c->plans.end();
+}
+
+extern "C" scff_status scff_plan_run(scff_ctx *c, scff_plan_h p, void *stream) {
+    if (!plan_known(c, p)) return fail(SCFF_ERR_NOT_FOUND, "scff_plan_run: unknown plan");
+    cudaSetDevice(c->device);
+    int64_t n = 0;
+    scff_status s = plan_launch(p, (cudaStream_t)stream, &n);
+    c->launches += n;
+    p->launches_per_run = n;
+    return s;
+}
+
+extern "C" scff_status scff_plan_run_graph(scff_ctx *c, scff_plan_h p, void *stream) {
+    if (!plan_known(c, p)) return fail(SCFF_ERR_NOT_FOUND, "scff_plan_run_graph: unknown plan");
+    if (!stream) return fail(SCFF_ERR_INVALID_ARG, "scff_plan_run_graph: capture needs a non-default stream");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->exec) {
+        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int64_t n = 0;
+        scff_status s = plan_launch(p, st, &n);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (s != SCFF_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(SCFF_ERR_CUDA, "scff_plan_run_graph: capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&p->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            p->exec = nullptr;
+            return fail(SCFF_ERR_CUDA, "scff_plan_run_graph: instantiate failed: %s", cudaGetErrorString(e));
+        }
+        p->graph = g;
+        p->launches_per_run = n;
+    }
+    CUDA_TRY(cudaGraphLaunch(p->exec, st));
+    c->launches += p->launches_per_run;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_plan_info(scff_ctx *c, scff_plan_h p, int64_t *info) {
+    if (!plan_known(c, p) || !info) return fail(SCFF_ERR_NOT_FOUND, "scff_plan_info: unknown plan");
+    int64_t items = 0, tcj = 0;
+    for (int n : p->group_nitems) items += n;
+    for (const PlanJob &pj : p->jobs) tcj += pj.tc;
+    info[0] = (int64_t)p->jobs.size();
+    info[1] = tcj;
+    info[2] = (int64_t)p->groups.size();
+    info[3] = items;
+    info[4] = (int64_t)p->dev_bytes;
+    info[5] = p->launches_per_run;
+    return SCFF_OK;
+}
+
+static void free_plan(scff_plan_s *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->dev);
+    delete p;
+}
+static void free_plan_any(struct scff_plan_s *p) { free_plan(p); }
+
+extern "C" void scff_release_plan(scff_ctx *c, scff_plan_h p) {
+    if (!plan_known(c, p)) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    c->plans.erase(std::find(c->plans.begin(), c->plans.end(), p));
+    free_plan(p);
 }

@@ -7,6 +7,8 @@
 
 #include "scff_internal.h"
 
+#include <vector>
+
 namespace scff {
 
 struct TcArgs {
@@ -28,7 +30,32 @@ struct TcArgs {
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
 };
 
+// Device descriptor of one prepared job (read by the persistent kernel).
+struct TcJobDev {
+    const uint8_t *A;      // swizzled split A tiles [n_mt][nkc][stage bytes]
+    const float2 *Y, *Z;   // per-axis power tables
+    const int4 *kinfo;     // [nkc * BK] k -> (pair, v, w, axis row)
+    int ny, nz, nx, nkc;
+    int M, n_mt, n_nt, pad0;
+    int64_t N, nq;
+    float scale, pad1;
+    float2 *f;             // [S][nq] complex output
+    float *f2;             // [S][nq] or null
+};
+
+// Workspace of one job prepared by tc_prep_job.
+size_t tc_job_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind);
+// Workspace of launch_tc_form_factor (one job plus its descriptor and work list).
 size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind);
+// Single job: prepare and launch.
 cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st);
+// Batch building blocks: per-job tables/k-index/A image, the cost-sorted work
+// list, and the persistent launch over a group of prepared jobs.
+cudaError_t tc_prep_job(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launches, cudaStream_t st);
+void tc_job_desc(const TcArgs &a, void *ws, TcJobDev *jd);
+void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items);
+cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
+                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st);
+int tc_num_sms();
 
 }  // namespace scff

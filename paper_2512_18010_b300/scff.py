@@ -28,7 +28,13 @@ _SYMBOLS = [
     "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
     "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_form_factor_static",
+    "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
 ]
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("basis", ctypes.c_void_p), ("trans", ctypes.c_void_p), ("grid", ctypes.c_void_p),
+                ("scale", ctypes.c_double), ("f_out", ctypes.c_void_p), ("f2_out", ctypes.c_void_p)]
 
 
 class ScffError(RuntimeError):
@@ -72,6 +78,16 @@ def load(build_if_missing: bool = True):
     lib.scff_form_factor_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, U32, ctypes.c_int, P,
                                             I64, P, D, P, P, P]
     lib.scff_form_factor_static.restype = I32
+    lib.scff_plan_create.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(P)]
+    lib.scff_plan_create.restype = I32
+    lib.scff_plan_run.argtypes = [P, P, P]
+    lib.scff_plan_run.restype = I32
+    lib.scff_plan_run_graph.argtypes = [P, P, P]
+    lib.scff_plan_run_graph.restype = I32
+    lib.scff_plan_info.argtypes = [P, P, P]
+    lib.scff_plan_info.restype = I32
+    lib.scff_release_plan.argtypes = [P, P]
+    lib.scff_release_plan.restype = None
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_last_timing.argtypes = [P, P]
@@ -117,6 +133,36 @@ class Transitions:
 class QGrid:
     def __init__(self, ctx, handle, n: int, shape: Optional[Tuple[int, int, int]]):
         self.ctx, self.handle, self.n, self.shape = ctx, handle, n, shape
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Plan:
+    """A fixed batch of jobs evaluated by persistent launches (see scff_plan_create)."""
+
+    def __init__(self, ctx, handle, outputs):
+        self.ctx, self.handle, self.outputs = ctx, handle, outputs
+
+    def run(self, stream=None):
+        _check(self.ctx.lib.scff_plan_run(self.ctx.h, self.handle, _stream_ptr(stream)))
+
+    def run_graph(self, stream):
+        _check(self.ctx.lib.scff_plan_run_graph(self.ctx.h, self.handle, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        out = np.zeros(6, dtype=np.int64)
+        _check(self.ctx.lib.scff_plan_info(self.ctx.h, self.handle, _p(out)))
+        keys = ("jobs", "tc_jobs", "groups", "tiles", "device_bytes", "launches_per_run")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def release(self):
+        if self.handle:
+            self.ctx.lib.scff_release_plan(self.ctx.h, self.handle)
+            self.handle = None
 
 
 class Context:
@@ -237,6 +283,22 @@ class Context:
         if caller_buffers:
             return f, f2
         return f[..., 0] + 1j * f[..., 1], f2
+
+    def plan(self, jobs, precision=TF32X3, workspace_bytes: int = 0) -> Plan:
+        """jobs: list of (basis, transitions, grid, f_out, f2_out_or_None, scale) with CUDA tensor outputs
+        (f_out [S, nq, 2], f2_out [S, nq]; float64 for FP64, float32 otherwise)."""
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        arr = (_Job * len(jobs))()
+        for i, (b, t, g, f, f2, sc) in enumerate(jobs):
+            if not _is_torch_cuda(f) or not f.is_contiguous() or tuple(f.shape) != (t.n_states, g.n, 2):
+                raise ValueError(f"job {i}: f_out must be a contiguous CUDA tensor of shape {(t.n_states, g.n, 2)}")
+            arr[i] = _Job(b.handle.value, t.handle.value, g.handle.value, float(sc), f.data_ptr(),
+                          f2.data_ptr() if f2 is not None else None)
+        h = ctypes.c_void_p()
+        _check(self.lib.scff_plan_create(self.h, len(jobs), ctypes.cast(arr, ctypes.c_void_p), int(precision),
+                                         int(workspace_bytes), ctypes.byref(h)))
+        return Plan(self, h, [(j[3], j[4]) for j in jobs])
 
     def sync(self, stream=None):
         sp = ctypes.c_void_p(0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream")
