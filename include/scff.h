@@ -195,6 +195,64 @@ scff_status scff_plan_run_graph(scff_ctx *ctx, scff_plan_h plan, void *stream);
 scff_status scff_plan_info(scff_ctx *ctx, scff_plan_h plan, int64_t *info);
 void scff_release_plan(scff_ctx *ctx, scff_plan_h plan);
 
+/*
+ * Serving: continuous batching of form-factor jobs (a request loop on a
+ * server thread that owns all of the GPU work).
+ *
+ * A job references a basis and transitions that are already resident on the
+ * device (scff_basis / scff_transitions, registered before submitting and
+ * kept alive until the job finishes), a product q-grid given as host axes
+ * (copied at submit), a scale and output buffers laid out as in
+ * scff_form_factor.  Jobs are admitted in arrival order as soon as a stream
+ * slot is free and their device footprint (tables, A image, axes and
+ * device-side outputs) fits the free part of the server's arena, which is
+ * allocated once at creation; every admitted group of jobs runs as one batch
+ * (one persistent tensor-core launch over all of its tiles).  Jobs arriving
+ * while batches are in flight join the next batch, which may run
+ * concurrently on another slot.  A job's result does not depend on the rest
+ * of its batch.  A job that can never fit the arena fails with
+ * SCFF_ERR_ADMISSION.  Host output buffers that are not pinned are pinned
+ * (cudaHostRegister) for the job's lifetime.
+ *
+ * scff_wait blocks until the job finished, at most timeout_us microseconds
+ * (< 0: no limit), and returns SCFF_OK, SCFF_ERR_TIMEOUT (still running),
+ * SCFF_ERR_CANCELLED or the job's error.  scff_cancel cancels a job that has
+ * not been admitted yet.  scff_job_times writes the host clock (ms) at
+ * submission, admission and completion.  scff_server_stats writes: jobs
+ * submitted, completed, cancelled, failed, batches launched, most jobs in
+ * flight at once, arena bytes.  scff_server_destroy cancels pending jobs,
+ * lets in-flight batches finish, and frees the server (job ids become
+ * invalid).
+ */
+typedef struct scff_server_s *scff_server_h;
+typedef struct {
+    int precision;        /* scff_precision of every job */
+    int slots;            /* batches in flight at once (streams), 1..8 */
+    int max_batch_jobs;   /* jobs per batch */
+    uint64_t arena_bytes; /* device memory for in-flight jobs (0 = half the context budget) */
+} scff_server_options;
+typedef struct {
+    scff_basis_h basis;
+    scff_trans_h trans;
+    const double *qx;
+    int nx;
+    const double *qy;
+    int ny;
+    const double *qz;
+    int nz;
+    double scale;
+    void *f_out;          /* [S][nq][2]: double for SCFF_FP64, float otherwise */
+    void *f2_out;         /* [S][nq] or NULL */
+    int out_on_device;    /* 1: device pointers, 0: host pointers */
+} scff_request;
+scff_status scff_server_create(scff_ctx *ctx, const scff_server_options *opt, scff_server_h *out);
+scff_status scff_submit(scff_server_h server, const scff_request *req, int64_t *job_id);
+scff_status scff_wait(scff_server_h server, int64_t job_id, int64_t timeout_us);
+scff_status scff_cancel(scff_server_h server, int64_t job_id);
+scff_status scff_job_times(scff_server_h server, int64_t job_id, double *ms_submit_admit_done);
+scff_status scff_server_stats(scff_server_h server, int64_t *out);
+void scff_server_destroy(scff_server_h server);
+
 /* Waits for all work on `stream` and reports the device status word:
  * SCFF_ERR_TIMEOUT if a device-side wait of an asynchronous call gave up. */
 scff_status scff_sync(scff_ctx *ctx, void *stream);

@@ -54,53 +54,7 @@ scff_status set_last_error(scff_status code, const char *msg) {
 
 // ------------------------------------------------------------------ objects
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-};
-
-struct scff_ctx {
-    int device = 0;
-    uint64_t budget = 0;
-    int64_t launches = 0;
-    int *d_err = nullptr;
-    int *h_err = nullptr;  // pinned
-    // workspace slots (grown on demand)
-    DevBuf coef, geom, gx, gy, gz, fstage, f2stage, tc_ws;
-    // stage timing (scff_set_timing): events before pair-prep, before the
-    // q-evaluation, after the q-evaluation
-    int timing = 0;
-    int drain_every = -1;  // tensor-core TMEM accumulation length (-1 = default)
-    int timed_valid = 0;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    std::vector<struct scff_basis_s *> bases;
-    std::vector<struct scff_trans_s *> transs;
-    std::vector<struct scff_qgrid_s *> grids;
-    std::vector<struct scff_plan_s *> plans;
-};
-
-struct scff_basis_s {
-    scff_ctx *ctx;
-    int nbf;
-    PairSetDev dev;
-};
-
-struct scff_trans_s {
-    scff_ctx *ctx;
-    scff_basis_s *basis;
-    int S;
-    double *d_T;
-};
-
-struct scff_qgrid_s {
-    scff_ctx *ctx;
-    int product;
-    int nx, ny, nz;
-    int64_t n;
-    double *d_qx, *d_qy, *d_qz;  // product grid axes
-    double *d_q;                 // list [n][3]
-    std::vector<double> hx, hy, hz;
-};
+#include "scff_objects.h"
 
 static scff_status grow(scff_ctx *c, DevBuf &b, size_t bytes) {
     if (bytes <= b.cap) return SCFF_OK;

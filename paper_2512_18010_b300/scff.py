@@ -29,7 +29,21 @@ _SYMBOLS = [
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
     "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_form_factor_static",
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
+    "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
+    "scff_server_destroy",
 ]
+
+
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("slots", ctypes.c_int), ("max_batch_jobs", ctypes.c_int),
+                ("arena_bytes", ctypes.c_uint64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("basis", ctypes.c_void_p), ("trans", ctypes.c_void_p),
+                ("qx", ctypes.c_void_p), ("nx", ctypes.c_int), ("qy", ctypes.c_void_p), ("ny", ctypes.c_int),
+                ("qz", ctypes.c_void_p), ("nz", ctypes.c_int), ("scale", ctypes.c_double),
+                ("f_out", ctypes.c_void_p), ("f2_out", ctypes.c_void_p), ("out_on_device", ctypes.c_int)]
 
 
 class _Job(ctypes.Structure):
@@ -88,6 +102,17 @@ def load(build_if_missing: bool = True):
     lib.scff_plan_info.restype = I32
     lib.scff_release_plan.argtypes = [P, P]
     lib.scff_release_plan.restype = None
+    lib.scff_server_create.argtypes = [P, P, ctypes.POINTER(P)]
+    lib.scff_submit.argtypes = [P, P, ctypes.POINTER(I64)]
+    lib.scff_wait.argtypes = [P, I64, I64]
+    lib.scff_cancel.argtypes = [P, I64]
+    lib.scff_job_times.argtypes = [P, I64, P]
+    lib.scff_server_stats.argtypes = [P, P]
+    for n in ("scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times",
+              "scff_server_stats"):
+        getattr(lib, n).restype = I32
+    lib.scff_server_destroy.argtypes = [P]
+    lib.scff_server_destroy.restype = None
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_last_timing.argtypes = [P, P]
@@ -163,6 +188,68 @@ class Plan:
         if self.handle:
             self.ctx.lib.scff_release_plan(self.ctx.h, self.handle)
             self.handle = None
+
+
+class Server:
+    """Continuous-batching request loop (see scff_server_create)."""
+
+    def __init__(self, ctx: "Context", precision=TF32X3, slots: int = 2, max_batch_jobs: int = 64,
+                 arena_bytes: int = 0):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.ctx = ctx
+        self.precision = precision
+        opt = _ServerOptions(int(precision), int(slots), int(max_batch_jobs), int(arena_bytes))
+        h = ctypes.c_void_p()
+        _check(ctx.lib.scff_server_create(ctx.h, ctypes.byref(opt), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, basis: Basis, trans: Transitions, qx, qy, qz, f_out, f2_out=None, scale: float = 1.0) -> int:
+        """Queues one job; f_out/f2_out are CUDA tensors (device outputs) or numpy/pinned arrays (host)."""
+        qx, qy, qz = _np(qx, np.float64), _np(qy, np.float64), _np(qz, np.float64)
+        dev = _is_torch_cuda(f_out)
+        if dev:
+            fp, f2p = f_out.data_ptr(), (f2_out.data_ptr() if f2_out is not None else None)
+        elif hasattr(f_out, "data_ptr"):
+            fp, f2p = f_out.data_ptr(), (f2_out.data_ptr() if f2_out is not None else None)
+        else:
+            fp = f_out.ctypes.data
+            f2p = f2_out.ctypes.data if f2_out is not None else None
+        req = _Request(basis.handle.value, trans.handle.value, qx.ctypes.data, len(qx), qy.ctypes.data, len(qy),
+                       qz.ctypes.data, len(qz), float(scale), fp, f2p, 1 if dev else 0)
+        jid = ctypes.c_int64()
+        _check(self.ctx.lib.scff_submit(self.h, ctypes.byref(req), ctypes.byref(jid)))
+        self._keep[jid.value] = (f_out, f2_out)
+        return jid.value
+
+    def wait(self, job_id: int, timeout_s: Optional[float] = None):
+        t = -1 if timeout_s is None else int(timeout_s * 1e6)
+        rc = self.ctx.lib.scff_wait(self.h, int(job_id), t)
+        if rc == 0:
+            self._keep.pop(job_id, None)
+        _check(rc)
+
+    def cancel(self, job_id: int):
+        _check(self.ctx.lib.scff_cancel(self.h, int(job_id)))
+
+    def times(self, job_id: int):
+        """Host clock (ms) at submission, admission and completion."""
+        out = np.zeros(3, dtype=np.float64)
+        _check(self.ctx.lib.scff_job_times(self.h, int(job_id), _p(out)))
+        return tuple(float(x) for x in out)
+
+    def stats(self) -> dict:
+        out = np.zeros(7, dtype=np.int64)
+        _check(self.ctx.lib.scff_server_stats(self.h, _p(out)))
+        keys = ("submitted", "completed", "cancelled", "failed", "batches", "max_inflight", "arena_bytes")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.scff_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
 
 
 class Context:
