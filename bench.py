@@ -2,14 +2,17 @@
 """Throughput benchmark of the form-factor hot path on B300.
 
 One step = one full form-factor job on device-resident inputs: pair-prep
-(Gaussian product theorem + coefficient folding), per-axis phase tables and
-the q-evaluation over the whole product grid for every state, with the |f|^2
-epilogue.  Metric: (q-point x state)/s.
+(Gaussian product theorem + coefficient folding), per-axis phase tables, the
+A image and the tensor-core q-evaluation over the whole product grid for
+every state, with the |f|^2 epilogue.  Metric: (q-point x state)/s.
 
 Default workload: the 10-heavy-atom molecule (10 heavy + 10 H, double-zeta +
-d basis, 170 Cartesian functions), 12 states, 128^3 grid on [-20, 20]
-Bohr^-1, evaluated with the split-BF16 tensor-core path; the plain FP64 GPU
-path is timed beside it.
+d basis, 170 Cartesian functions), 12 states, 128^3 grid on [-20, 20] Bohr^-1,
+in the 1e-5-grade TF32 hi/lo tensor-core mode with the autotuner on.  Beside
+it the line reports the plain FP64 GPU path on the same job, the end-to-end
+rate through the C ABI with host buffers, the FP64 oracle on the host cores,
+and (unless --no-serving) a serving run: a Poisson stream of jobs drawn from
+the batched-workload distribution plus 5% large jobs, with p50/p99 latency.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank evaluates its own job (weak scaling, no data-path
@@ -19,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import subprocess
 import sys
@@ -37,6 +41,7 @@ UNIT = "(q-point*state)/s"
 FP32_LANES_PER_SM = 128
 N_SM = 148
 SM_MAX_MHZ = 2032.0
+TF32_PER_BF16 = 0.5   # dense TF32 / dense BF16 tensor rate (nominal 1.1 vs 2.25 PFLOP/s)
 
 
 def parse():
@@ -47,10 +52,14 @@ def parse():
     ap.add_argument("--impl", default="scff", choices=["scff", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x2", "fp32", "fp64"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=0, help="also time a batched plan of this many batched-workload jobs")
     return ap.parse_args()
 
 
@@ -70,19 +79,17 @@ def workload(name: str, rank: int = 0):
 
 
 def pair_stats(mol):
-    """Pair records and monomial rows of a basis (for the algorithmic flop count)."""
-    per_heavy = {0: 1, 1: 3, 2: 6, -1: 4}
+    """Pair records, monomial rows K and (v,w) rows of a basis."""
     lmax = {0: 0, 1: 1, 2: 2, -1: 1}
     recs = []
     for l, n in zip(mol.shell_l, mol.shell_nprim):
         recs += [lmax[int(l)]] * int(n)
     recs = np.array(recs)
-    L = recs[:, None] + recs[None, :]
     iu = np.triu_indices(len(recs))
-    Lp = L[iu]
+    Lp = (recs[:, None] + recs[None, :])[iu]
     K = int(np.sum((Lp + 1) * (Lp + 2) * (Lp + 3) // 6))
-    del per_heavy
-    return len(Lp), K
+    Kvw = int(np.sum((Lp + 1) * (Lp + 2) // 2))
+    return len(Lp), K, Kvw
 
 
 class ClockSampler:
@@ -176,6 +183,114 @@ def run_reference(args):
     return 0
 
 
+def _serving_job(i):
+    return W.config5_job(i)
+
+
+def _batch_job(i):
+    return W.config4_job(i)
+
+
+def make_jobs(fn, n):
+    """Draws jobs in a spawn pool (before any CUDA call in this process).
+
+    Each worker runs single-threaded BLAS: with one BLAS thread pool per core
+    in every worker the QR factorisations oversubscribe the host ~50x."""
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            return pool.map(fn, range(n))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def serving_run(scff, ctx, jobs, precision, rate_factor=0.7):
+    """Saturation throughput, then a Poisson stream at rate_factor x capacity: p50/p99 latency."""
+    import torch
+    handles, outs = [], []
+    for job in jobs:
+        b = ctx.basis(job.mol)
+        t = ctx.transitions(b, job.T)
+        handles.append((b, t))
+        outs.append((torch.empty((job.n_states, job.nq, 2), device="cuda"),
+                     torch.empty((job.n_states, job.nq), device="cuda")))
+    units = sum(j.n_states * j.nq for j in jobs)
+
+    def one_pass(arrivals):
+        srv = scff.Server(ctx, precision=precision, slots=2, max_batch_jobs=16)
+        ids = []
+        t0 = time.perf_counter()
+        for job, (b, t), (f, f2), ta in zip(jobs, handles, outs, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(b, t, job.qx, job.qy, job.qz, f, f2))
+        for i in ids:
+            srv.wait(i, timeout_s=600)
+        wall = time.perf_counter() - t0
+        lat = np.array([srv.times(i)[2] - srv.times(i)[0] for i in ids])
+        st = srv.stats()
+        srv.close()
+        return wall, lat, st
+
+    one_pass([0.0] * len(jobs))                       # warm pass
+    wall_sat, lat_sat, st_sat = one_pass([0.0] * len(jobs))
+    capacity_jobs = len(jobs) / wall_sat
+    rate = rate_factor * capacity_jobs
+    arr = W.poisson_arrivals(len(jobs), rate, seed=5555)
+    wall, lat, st = one_pass(list(arr))
+    for b, _ in handles:
+        ctx.release(b)
+    return {
+        "jobs": len(jobs), "large_jobs": int(sum(1 for j in jobs if j.mol.heavy >= 40)),
+        "saturation": {"value": units / wall_sat, "unit": UNIT, "wall_s": wall_sat, "batches": st_sat["batches"],
+                       "max_inflight": st_sat["max_inflight"]},
+        "poisson": {"rate_jobs_per_s": rate, "rate_factor_of_capacity": rate_factor, "value": units / wall,
+                    "unit": UNIT, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                    "batches": st["batches"], "max_inflight": st["max_inflight"]},
+    }
+
+
+def batch_run(scff, ctx, jobs, precision, steps=2):
+    import torch
+    specs = []
+    for job in jobs:
+        b = ctx.basis(job.mol)
+        t = ctx.transitions(b, job.T)
+        g = ctx.qgrid_product(job.qx, job.qy, job.qz)
+        specs.append((b, t, g, torch.empty((job.n_states, job.nq, 2), device="cuda"),
+                      torch.empty((job.n_states, job.nq), device="cuda"), 1.0))
+    plan = ctx.plan(specs, precision=precision)
+    stream = torch.cuda.Stream()
+    plan.run_graph(stream)               # capture + first replay (warm-up)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.run_graph(stream)
+    e1.record(stream)
+    stream.synchronize()
+    ctx.sync(stream)
+    ms = e0.elapsed_time(e1) / steps
+    units = sum(j.n_states * j.nq for j in jobs)
+    info = plan.info()
+    plan.release()
+    for s in specs:
+        ctx.release(s[2])
+        ctx.release(s[0])
+    return {"jobs": len(jobs), "value": units / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms,
+            "launches_per_run": info["launches_per_run"], "groups": info["groups"], "tiles": info["tiles"],
+            "graph": "one captured CUDA graph per plan, replayed"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -183,6 +298,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    serving_jobs = batch_jobs = None
+    if rank == 0 and world == 1 and not args.no_serving and args.serving_jobs > 0:
+        serving_jobs = make_jobs(_serving_job, args.serving_jobs)
+    if rank == 0 and world == 1 and args.batch > 0:
+        batch_jobs = make_jobs(_batch_job, args.batch)
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -195,6 +315,8 @@ def main():
     S, nq = job.n_states, job.nq
     prec = scff.PRECISIONS[args.precision]
     ctx = scff.Context(local)
+    if not args.no_autotune:
+        ctx.set_autotune(True)
     b = ctx.basis(job.mol)
     t = ctx.transitions(b, job.T)
     g = ctx.qgrid_product(job.qx, job.qy, job.qz)
@@ -213,13 +335,16 @@ def main():
         step()
     torch.cuda.synchronize()
     ctx.sync(stream)
+    choice = None
+    if prec in (scff.TF32X3, scff.BF16X3, scff.BF16X2) and not args.no_autotune:
+        choice = ctx.autotune_choice(b, t, g, prec)
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     l0 = ctx.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    step_ms, qeval_ms = [], []
+    qeval_ms = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -248,8 +373,6 @@ def main():
     fp64 = None
     if args.fp64_steps > 0 and prec != scff.FP64:
         f64 = torch.empty((S, nq, 2), dtype=torch.float64, device=dev)
-        ctx.form_factor(b, t, g, precision=scff.FP64, f_out=f64, stream=stream)  # warm-up
-        torch.cuda.synchronize()
         tms = []
         for _ in range(args.fp64_steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -259,32 +382,41 @@ def main():
             torch.cuda.synchronize()
             tms.append(e0.elapsed_time(e1))
         fms = float(np.mean(tms))
-        fp64 = {"value": units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms, "steps": args.fp64_steps}
+        fp64 = {"value": units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms, "steps": args.fp64_steps,
+                "speedup_of_value": value / (units / (fms / 1e3))}
         del f64
 
     # roofline of the dominant kernel (the q-evaluation)
-    n_pair, K = pair_stats(job.mol)
-    flops_per_unit = 2 * K + 8 * n_pair
+    n_pair, K, Kvw = pair_stats(job.mol)
     kern_ms = float(np.mean(qeval_ms))
-    achieved = flops_per_unit * units / (kern_ms / 1e3) / 1e12
-    if prec in (scff.BF16X3, scff.TF32X3, scff.BF16X2):
-        peak_src = "measured bf16 dense (MEASURED_PEAKS.json bf16_tflops)"
-        try:
-            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
-        except Exception:
-            peak, peak_src = 1800.0, "fallback bf16 1.8 PFLOP/s"
-        roof = {"bound": "tensor", "kernel": "tc_form_factor", "achieved": achieved, "peak": peak,
+    direct_flops = 2 * K + 8 * n_pair           # per (q, state): polynomial + complex phase multiply-add
+    used_tc = prec in (scff.BF16X3, scff.TF32X3, scff.BF16X2) and (choice is None or choice["tensor_cores"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if used_tc:
+        passes = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3}[prec]
+        tc_flops = 8 * Kvw * passes              # executed tensor flops per (q, state)
+        bf16 = float(peaks.get("bf16_tflops", 1800.0))
+        peak = bf16 * (TF32_PER_BF16 if prec == scff.TF32X3 else 1.0)
+        achieved = tc_flops * units / (kern_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "work": f"{flops_per_unit} algorithmic flop per (q*state)", "peak_source": peak_src}
+                "work": f"{tc_flops} tensor flop per (q*state) = 8 flop x {Kvw} (pair,v,w) rows x {passes} split "
+                        f"products; direct-form algorithmic work is {direct_flops} flop per (q*state)",
+                "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio 0.5"
+                                if prec == scff.TF32X3 else "of measured: MEASURED_PEAKS.json bf16_tflops"),
+                "algorithmic_tflops": direct_flops * units / (kern_ms / 1e3) / 1e12}
     else:
-        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        if prec == scff.FP64:
-            peak = 1.25
+        fp64_path = prec == scff.FP64
+        peak = 1.25 if fp64_path else N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = direct_flops * units / (kern_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "direct_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "work": f"{flops_per_unit} algorithmic flop per (q*state)",
-                "peak_source": "FP32: 148 SM x 128 lanes x 2 flop x 2032 MHz" if prec != scff.FP64
-                else "FP64 nominal 1.25 TFLOP/s"}
+                "frac": achieved / peak, "traffic": None, "work": f"{direct_flops} algorithmic flop per (q*state)",
+                "peak_source": "FP64 nominal 1.25 TFLOP/s" if fp64_path else
+                "FP32: 148 SM x 128 lanes x 2 flop x 2032 MHz"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -313,6 +445,13 @@ def main():
         e2e = {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
+    serving = None
+    if serving_jobs:
+        serving = serving_run(scff, ctx, serving_jobs, prec if prec != scff.FP64 else scff.TF32X3)
+    batch = None
+    if batch_jobs:
+        batch = batch_run(scff, ctx, batch_jobs, prec if prec != scff.FP64 else scff.TF32X3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(job, args.cpu_sample)
@@ -320,13 +459,16 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"tf32x3": "tf32x3->f32", "bf16x3": "bf16x3->f32", "bf16x2": "bf16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
+                "vs_baseline": None,
+                "dtype": {"tf32x3": "tf32x3->f32", "bf16x3": "bf16x3->f32", "bf16x2": "bf16x2->f32", "fp32": "f32",
+                          "fp64": "f64"}[args.precision],
                 "data": "synthetic (seeded molecules, basis and transition matrices)",
                 "config": {"workload": desc, "precision": args.precision, "n_pairs": n_pair,
-                           "monomial_rows": K, "l2": "flushed between timed steps (256 MB write)",
+                           "monomial_rows": K, "vw_rows": Kvw, "autotune": choice,
+                           "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"dp{world} (one job per rank)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "fp64_gpu_path": fp64, "clocks": clocks,
+                "fp64_gpu_path": fp64, "serving": serving, "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)
     ctx.close()

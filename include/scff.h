@@ -263,6 +263,18 @@ scff_status scff_sync(scff_ctx *ctx, void *stream);
  * accumulations at the cost of more epilogue traffic. */
 scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
 
+/* Autotuner.  When enabled, the first scff_form_factor call for a job shape
+ * (log-bucketed pair rows, states and grid points) in a tensor-core precision
+ * on a product grid times the candidate configurations -- the tensor-core
+ * path with TMEM drains of 8 and 16 k-chunks, and the FP32 direct path with
+ * state blocks of 8 and 16 -- on that job, and later calls of the same shape
+ * use the fastest.  Every candidate meets the requested precision's bar.
+ * scff_autotune_choice: out[0] = 1 tensor cores / 0 direct, out[1] = drain,
+ * out[2] = state block, out[3] = best time in microseconds. */
+scff_status scff_set_autotune(scff_ctx *ctx, int enable);
+scff_status scff_autotune_choice(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
+                                 scff_qgrid_h grid, int precision, int32_t *out);
+
 /* Stage timing.  With timing enabled every scff_form_factor call records
  * CUDA events on its stream; scff_last_timing then waits for the last call
  * and writes ms_out[0] = q-evaluation kernel time, ms_out[1] = pair-prep and

@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -477,46 +479,33 @@ extern "C" void scff_release_qgrid(scff_ctx *c, scff_qgrid_h h) {
 
 // ------------------------------------------------------------------ form factor
 
-extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_h t, scff_qgrid_h g, int precision,
-                                        double scale, void *f_out, void *f2_out, int out_on_device, void *stream) {
-    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: NULL context");
-    if (!b || std::find(c->bases.begin(), c->bases.end(), b) == c->bases.end())
-        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown basis handle");
-    if (!t || std::find(c->transs.begin(), c->transs.end(), t) == c->transs.end())
-        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown transitions handle");
-    if (!g || std::find(c->grids.begin(), c->grids.end(), g) == c->grids.end())
-        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown q-grid handle");
-    if (t->basis != b) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: transitions belong to another basis");
-    if (precision < SCFF_FP64 || precision > SCFF_BF16X2)
-        return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: precision %d", precision);
-    if (!f_out) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: f_out is NULL");
-    if (!isfinite(scale)) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: scale is not finite");
-    cudaSetDevice(c->device);
-    cudaStream_t st = (cudaStream_t)stream;
+// Footprint of one configuration (coefficients, geometry, tables, workspace).
+static size_t ff_footprint(const PairSetDev &ps, const scff_qgrid_s *g, int S, int precision, const FFChoice &ch) {
+    const bool fp64 = precision == SCFF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    const int S_pad = (S + ch.SB - 1) / ch.SB * ch.SB;
+    size_t foot = (size_t)S_pad * ps.n_rows * rsz + (size_t)ps.n_pair * 4 * sizeof(double) + 64;
+    if (ch.use_tc) {
+        const int kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+        foot += tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz, kind);
+    } else if (g->product) {
+        foot += (size_t)ps.n_pair * (g->nx + g->ny + g->nz) * 2 * rsz;
+    }
+    return foot;
+}
+
+// Pair-prep and q-evaluation of one configuration into device outputs.
+static scff_status ff_run(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_qgrid_s *g, int precision, double scale,
+                          void *fdev, void *f2dev, const FFChoice &ch, cudaStream_t st) {
     const PairSetDev &ps = b->dev;
     const int S = t->S;
     const int64_t nq = g->n;
     const bool fp64 = precision == SCFF_FP64;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
-    const bool use_tc = (precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2) &&
-                        g->product;
-    // split kind of the tensor-core kernel: 0 BF16 hi/lo, 1 BF16 hi/mid/lo, 2 TF32 hi/lo
-    const int tc_kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
-    const int SB = fp64 ? 4 : 8;
+    const int SB = ch.SB;
     const int S_pad = (S + SB - 1) / SB * SB;
-
-    // footprint check (admission): coefficients + tables + outputs
     const size_t coef_bytes = (size_t)S_pad * ps.n_rows * rsz;
     const size_t geom_bytes = (size_t)ps.n_pair * 4 * sizeof(double) + 64;
-    const size_t out_bytes = (size_t)S * nq * rsz * 3;
-    size_t tab_bytes = 0;
-    if (g->product) tab_bytes = (size_t)ps.n_pair * (g->nx + g->ny + g->nz) * 2 * rsz;
-    size_t tc_bytes = use_tc ? tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz, tc_kind) : 0;
-    const size_t foot = coef_bytes + geom_bytes + tab_bytes + tc_bytes + (out_on_device ? 0 : out_bytes);
-    if (foot > c->budget)
-        return fail(SCFF_ERR_ADMISSION, "scff_form_factor: footprint %zu bytes exceeds the budget %llu", foot,
-                    (unsigned long long)c->budget);
-
     TRY(grow(c, c->coef, coef_bytes + 256));
     TRY(grow(c, c->geom, geom_bytes));
     CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
@@ -525,19 +514,11 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     ++c->launches;
     CUDA_TRY(launch_pairprep(ps, t->d_T, S, SB, S_pad, fp64 ? (double *)c->coef.p : nullptr,
                              fp64 ? nullptr : (float *)c->coef.p, &c->launches, st));
-
-    void *fdev = f_out, *f2dev = f2_out;
-    if (!out_on_device) {
-        TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
-        fdev = c->fstage.p;
-        if (f2_out) {
-            TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
-            f2dev = c->f2stage.p;
-        }
-    }
-
-    if (use_tc) {
+    if (ch.use_tc) {
+        const int kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+        const size_t tc_bytes = tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz, kind);
         TcArgs ta;
+        memset(&ta, 0, sizeof(ta));
         ta.ps = &ps;
         ta.coef32 = (const float *)c->coef.p;
         ta.SB = SB;
@@ -557,8 +538,8 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
         ta.ws = c->tc_ws.p;
         ta.ws_bytes = c->tc_ws.cap;
         ta.ev_mark = c->timing ? c->ev[1] : nullptr;
-        ta.kind = tc_kind;
-        ta.drain_every = c->drain_every >= 0 ? c->drain_every : 8;
+        ta.kind = kind;
+        ta.drain_every = ch.drain;
         CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
     } else {
         DirectArgs a;
@@ -601,7 +582,124 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
         CUDA_TRY(cudaEventRecord(c->ev[2], st));
         c->timed_valid = 1;
     }
+    return SCFF_OK;
+}
 
+// Shape key of the autotuner: log2 buckets of pair monomial rows, states and
+// grid points, and the requested precision.
+static uint64_t tune_key(const PairSetDev &ps, int S, int64_t nq, int precision) {
+    auto lg = [](double x) { return (uint64_t)std::max(0.0, std::floor(std::log2(std::max(1.0, x)) * 2.0)); };
+    return (lg((double)ps.n_rows) << 32) | (lg((double)S) << 24) | (lg((double)nq) << 8) | (uint64_t)precision;
+}
+
+// Times every candidate configuration once on this job (outputs go to the
+// device staging buffers) and keeps the fastest.  All candidates meet the
+// accuracy of the requested precision: TMEM drains of 8 or 16 k-chunks for
+// the split tensor-core modes, and the FP32 direct path (1e-6) for the
+// 1e-5-grade modes.
+static scff_status autotune(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_qgrid_s *g, int precision,
+                            cudaStream_t st, FFChoice *best) {
+    const size_t rsz = sizeof(float);
+    const int S = t->S;
+    const int64_t nq = g->n;
+    const std::vector<FFChoice> cand = {{1, 8, 8}, {1, 16, 8}, {0, 0, 8}, {0, 0, 16}};
+    TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
+    TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = cand[0];
+    const int saved_timing = c->timing;
+    c->timing = 0;
+    for (const FFChoice &ch : cand) {
+        if (ff_footprint(b->dev, g, S, precision, ch) > c->budget) continue;
+        scff_status s = ff_run(c, b, t, g, precision, 1.0, c->fstage.p, c->f2stage.p, ch, st);  // warm-up
+        if (s != SCFF_OK) continue;
+        cudaEventRecord(e0, st);
+        s = ff_run(c, b, t, g, precision, 1.0, c->fstage.p, c->f2stage.p, ch, st);
+        cudaEventRecord(e1, st);
+        if (s != SCFF_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = ch;
+        }
+    }
+    c->timing = saved_timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune_ms[tune_key(b->dev, S, nq, precision)] = best_ms;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_set_autotune(scff_ctx *c, int enable) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_autotune: NULL context");
+    c->autotune = enable ? 1 : 0;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_autotune_choice(scff_ctx *c, scff_basis_h b, scff_trans_h t, scff_qgrid_h g,
+                                            int precision, int32_t *out) {
+    if (!c || !b || !t || !g || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_autotune_choice: NULL argument");
+    auto it = c->tune.find(tune_key(b->dev, t->S, g->n, precision));
+    if (it == c->tune.end()) return fail(SCFF_ERR_NOT_FOUND, "scff_autotune_choice: shape not tuned yet");
+    out[0] = it->second.use_tc;
+    out[1] = it->second.drain;
+    out[2] = it->second.SB;
+    out[3] = (int32_t)(1000.0f * c->tune_ms[it->first]);  // microseconds of the best candidate
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_h t, scff_qgrid_h g, int precision,
+                                        double scale, void *f_out, void *f2_out, int out_on_device, void *stream) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: NULL context");
+    if (!b || std::find(c->bases.begin(), c->bases.end(), b) == c->bases.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown basis handle");
+    if (!t || std::find(c->transs.begin(), c->transs.end(), t) == c->transs.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown transitions handle");
+    if (!g || std::find(c->grids.begin(), c->grids.end(), g) == c->grids.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown q-grid handle");
+    if (t->basis != b) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: transitions belong to another basis");
+    if (precision < SCFF_FP64 || precision > SCFF_BF16X2)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: precision %d", precision);
+    if (!f_out) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: f_out is NULL");
+    if (!isfinite(scale)) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: scale is not finite");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = t->S;
+    const int64_t nq = g->n;
+    const bool fp64 = precision == SCFF_FP64;
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
+    FFChoice ch = {tc_prec && g->product ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, fp64 ? 4 : 8};
+    if (c->autotune && tc_prec && g->product && nq > 0) {
+        const uint64_t key = tune_key(b->dev, S, nq, precision);
+        auto it = c->tune.find(key);
+        if (it == c->tune.end()) {
+            FFChoice best;
+            TRY(autotune(c, b, t, g, precision, st, &best));
+            it = c->tune.emplace(key, best).first;
+        }
+        ch = it->second;
+    }
+    // footprint check (admission)
+    const size_t out_bytes = (size_t)S * nq * rsz * 3;
+    const size_t foot = ff_footprint(b->dev, g, S, precision, ch) + (out_on_device ? 0 : out_bytes);
+    if (foot > c->budget)
+        return fail(SCFF_ERR_ADMISSION, "scff_form_factor: footprint %zu bytes exceeds the budget %llu", foot,
+                    (unsigned long long)c->budget);
+    void *fdev = f_out, *f2dev = f2_out;
+    if (!out_on_device) {
+        TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
+        fdev = c->fstage.p;
+        if (f2_out) {
+            TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
+            f2dev = c->f2stage.p;
+        }
+    }
+    TRY(ff_run(c, b, t, g, precision, scale, fdev, f2dev, ch, st));
     if (!out_on_device) {
         if (nq > 0) {
             CUDA_TRY(cudaMemcpyAsync(f_out, fdev, (size_t)S * nq * 2 * rsz, cudaMemcpyDeviceToHost, st));

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <vector>
 
 #include "../../include/scff.h"
@@ -17,6 +18,13 @@ struct DevBuf {
 
 struct scff_plan_s;
 struct scff_server_s;
+
+// Evaluation configuration chosen by the autotuner (scff_host.cpp).
+struct FFChoice {
+    int use_tc;
+    int drain;  // k-chunks per TMEM accumulation (tensor cores)
+    int SB;     // states per block (direct path)
+};
 
 struct scff_ctx {
     int device = 0;
@@ -36,6 +44,10 @@ struct scff_ctx {
     std::vector<struct scff_trans_s *> transs;
     std::vector<struct scff_qgrid_s *> grids;
     std::vector<struct scff_plan_s *> plans;
+    // autotuner: chosen configuration and its time per job-shape key
+    int autotune = 0;
+    std::map<uint64_t, struct FFChoice> tune;
+    std::map<uint64_t, float> tune_ms;
 };
 
 struct scff_basis_s {

@@ -30,7 +30,7 @@ _SYMBOLS = [
     "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_form_factor_static",
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
-    "scff_server_destroy",
+    "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice",
 ]
 
 
@@ -113,6 +113,10 @@ def load(build_if_missing: bool = True):
         getattr(lib, n).restype = I32
     lib.scff_server_destroy.argtypes = [P]
     lib.scff_server_destroy.restype = None
+    lib.scff_set_autotune.argtypes = [P, ctypes.c_int]
+    lib.scff_set_autotune.restype = I32
+    lib.scff_autotune_choice.argtypes = [P, P, P, P, ctypes.c_int, P]
+    lib.scff_autotune_choice.restype = I32
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_last_timing.argtypes = [P, P]
@@ -395,6 +399,18 @@ class Context:
     def set_tc_drain(self, drain_every: int):
         """k-chunks per tensor-core TMEM accumulation (0 = whole K, -1 = default)."""
         _check(self.lib.scff_set_tc_drain(self.h, int(drain_every)))
+
+    def set_autotune(self, enable: bool = True):
+        _check(self.lib.scff_set_autotune(self.h, 1 if enable else 0))
+
+    def autotune_choice(self, basis: Basis, trans: Transitions, grid: QGrid, precision=TF32X3) -> dict:
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        out = np.zeros(4, dtype=np.int32)
+        _check(self.lib.scff_autotune_choice(self.h, basis.handle, trans.handle, grid.handle, int(precision),
+                                             _p(out)))
+        return {"tensor_cores": bool(out[0]), "drain": int(out[1]), "state_block": int(out[2]),
+                "best_us": int(out[3])}
 
     def set_timing(self, enable: bool = True):
         _check(self.lib.scff_set_timing(self.h, 1 if enable else 0))
