@@ -8,7 +8,8 @@ every state, with the |f|^2 epilogue.  Metric: (q-point x state)/s.
 
 Default workload: the 10-heavy-atom molecule (10 heavy + 10 H, double-zeta +
 d basis, 170 Cartesian functions), 12 states, 128^3 grid on [-20, 20] Bohr^-1,
-in the 1e-5-grade TF32 hi/lo tensor-core mode with the autotuner on.  Beside
+in the 1e-5-grade split-BF16 tensor-core mode (BF16 hi/mid/lo pieces, six piece products, FP32
+accumulation) with the autotuner on.  Beside
 it the line reports the plain FP64 GPU path on the same job, the end-to-end
 rate through the C ABI with host buffers, the FP64 oracle on the host cores,
 and (unless --no-serving) a serving run: a Poisson stream of jobs drawn from
@@ -51,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="scff", choices=["scff", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x2", "fp32", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
@@ -447,10 +448,10 @@ def main():
 
     serving = None
     if serving_jobs:
-        serving = serving_run(scff, ctx, serving_jobs, prec if prec != scff.FP64 else scff.TF32X3)
+        serving = serving_run(scff, ctx, serving_jobs, prec if prec != scff.FP64 else scff.BF16X3)
     batch = None
     if batch_jobs:
-        batch = batch_run(scff, ctx, batch_jobs, prec if prec != scff.FP64 else scff.TF32X3)
+        batch = batch_run(scff, ctx, batch_jobs, prec if prec != scff.FP64 else scff.BF16X3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -45,7 +45,6 @@ constexpr int BN = 128;                              // columns (iy, iz) per til
 constexpr int ROW_BYTES = 64;                        // one K-chunk row (64B swizzle)
 constexpr int A_ARR = BM * ROW_BYTES;                // bytes of one A array
 constexpr int W_ARR = BN * ROW_BYTES;                // bytes of one W array
-constexpr int K_STAGE = 32 * 16;                     // k-index records of one chunk (<= 32 x int4)
 constexpr int GEN_WARPS = 8;                         // W generators and accumulator drains
 constexpr int THREADS = 128 + GEN_WARPS * 32;        // warpgroup 0: TMA warp, MMA warp, 2 idle
 constexpr int TMEM_COLS = 512;                       // two sets of (Re, Im) x 128 columns
@@ -77,7 +76,7 @@ template <int KIND> struct Kind {
     static constexpr int PER_VEC = 16 / ELEM;                        // elements per 16-byte vector
     static constexpr int A_STAGE = 2 * NP * A_ARR;                   // re pieces, then im pieces
     static constexpr int W_STAGE = 2 * NP * W_ARR;
-    static constexpr int STAGE = A_STAGE + W_STAGE + K_STAGE;
+    static constexpr int STAGE = A_STAGE + W_STAGE;
     static constexpr int STAGES = NP == 3 ? 2 : 3;
     static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256;
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
@@ -212,7 +211,7 @@ struct Layout {
     int M, M_pad, n_mt;
     int64_t N;
     int n_nt;
-    size_t off_X, off_Y, off_Z, off_k, off_A, total;
+    size_t off_X, off_Y, off_Z, off_k, off_ko, off_A, total;
 };
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -238,6 +237,8 @@ static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     o = align_up(o + sizeof(float2) * (size_t)(L.n_axrows + 1) * nz, 1024);
     L.off_k = o;
     o = align_up(o + sizeof(int4) * (size_t)L.K_pad, 1024);
+    L.off_ko = o;
+    o = align_up(o + sizeof(int2) * (size_t)L.K_pad, 1024);
     L.off_A = o;
     o = align_up(o + (size_t)L.n_mt * L.nkc * a_stage, 1024);
     L.total = o;
@@ -284,8 +285,10 @@ __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict_
     table[idx] = out;
 }
 
-// k -> (pair, v, w, first axis row of the pair); padding k -> (-1, 0, 0, zero row).
-__global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, int4 *__restrict__ kinfo) {
+// k -> (pair, v, w, first axis row of the pair); padding k -> (-1, 0, 0, zero row);
+// kofs[k] = element offsets of k's rows in the Y and Z tables.
+__global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, int ny, int nz, int4 *__restrict__ kinfo,
+                              int2 *__restrict__ kofs) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K_pad) return;
     int4 r = make_int4(-1, 0, 0, (int)n_axrows);
@@ -309,6 +312,7 @@ __global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, in
         r = make_int4(pr, v, w, axbase);
     }
     kinfo[k] = r;
+    kofs[k] = make_int2((r.w + r.y) * ny, (r.w + r.z) * nz);  // Y and Z row offsets of this k
 }
 
 // A[(s,ix), k] = sum_u D^s_{pair,(u,v,w)} X_{pair,u}(q_x[ix]), split into pieces
@@ -378,15 +382,20 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
     tc_fence_after();
     const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + set * (2 * BN) + colh;
 #pragma unroll
-    for (int cc = 0; cc < CQ; cc += 16) {
-        float re[16], im[16];
-        tmem_ld16(ta + cc, re);
-        tmem_ld16(ta + BN + cc, im);
+    for (int cc = 0; cc < CQ; cc += 32) {
+        // two 16-column loads of Re and of Im in flight per wait
+        float r0[16], r1[16], i0[16], i1[16];
+        tmem_ld16(ta + cc, r0);
+        tmem_ld16(ta + cc + 16, r1);
+        tmem_ld16(ta + BN + cc, i0);
+        tmem_ld16(ta + BN + cc + 16, i1);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            acc_re[cc + j] += re[j];
-            acc_im[cc + j] += im[j];
+            acc_re[cc + j] += r0[j];
+            acc_re[cc + 16 + j] += r1[j];
+            acc_im[cc + j] += i0[j];
+            acc_im[cc + 16 + j] += i1[j];
         }
     }
     tc_fence_before();
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
-    uint64_t *fullA = bars + 0;                  // [STAGES] A tile + k-index records landed (TMA)
+    uint64_t *fullA = bars + 0;                  // [STAGES] A tile landed (TMA)
     uint64_t *fullW = bars + STAGES;             // [STAGES] W tile written by the generators
     uint64_t *empty = bars + 2 * STAGES;         // [STAGES] MMAs of the stage completed
     uint64_t *accFull = bars + 3 * STAGES;       // [2] accumulator set holds a finished group
@@ -461,9 +470,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     uint8_t *st = smem + s * STAGE;
-                    mbar_arrive_expect_tx(&fullA[s], A_STAGE + BK * 16);
+                    mbar_arrive_expect_tx(&fullA[s], A_STAGE);
                     bulk_g2s(st, Abase + (size_t)it * A_STAGE, A_STAGE, &fullA[s]);
-                    bulk_g2s(st + A_STAGE + W_STAGE, J.kinfo + (size_t)it * BK, BK * 16, &fullA[s]);
                 }
             }
         } else if (warp == 1 && lane == 0) {
@@ -550,25 +558,27 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
             const int gc0 = gc;
             int drained = 0;
+            const int2 *kofs = J.kofs + khalf * KH;
             for (int it = 0; it < nkc && ok; ++it, ++gc) {
                 const int s = gc % STAGES;
-                bool w = mbar_wait(&fullA[s], (gc / STAGES) & 1);  // k-index records of this chunk
-                if (w && gc >= STAGES) w = mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
+                // Row offsets of this thread's k: independent of the A copy, so the
+                // gathers below overlap with the TMA instead of following it.
+                int2 ko[KH];
+#pragma unroll
+                for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
+                const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
                 if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                     ok = false;
                     break;
                 }
-                uint8_t *st = smem + s * STAGE;
-                const int4 *kin = reinterpret_cast<const int4 *>(st + A_STAGE + W_STAGE) + khalf * KH;
-                uint8_t *wst = st + A_STAGE;
+                uint8_t *wst = smem + s * STAGE + A_STAGE;
 #pragma unroll
                 for (int sb = 0; sb < KH; sb += KSUB) {
                     float2 y[KSUB], z[KSUB];
 #pragma unroll
                     for (int e = 0; e < KSUB; ++e) {
-                        const int4 ki = kin[sb + e];
-                        y[e] = Yc[(size_t)(ki.w + ki.y) * ny];
-                        z[e] = Zc[(size_t)(ki.w + ki.z) * nz];
+                        y[e] = __ldg(Yc + ko[sb + e].x);
+                        z[e] = __ldg(Zc + ko[sb + e].y);
                     }
 #pragma unroll
                     for (int jv = 0; jv < KSUB / V; ++jv) {
@@ -669,6 +679,7 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->Y = reinterpret_cast<float2 *>(w + L.off_Y);
     jd->Z = reinterpret_cast<float2 *>(w + L.off_Z);
     jd->kinfo = reinterpret_cast<int4 *>(w + L.off_k);
+    jd->kofs = reinterpret_cast<int2 *>(w + L.off_ko);
     jd->ny = a.ny;
     jd->nz = a.nz;
     jd->nx = a.nx;
@@ -705,7 +716,8 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
         axis_power_table_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.pair_geom, qa[ax], na[ax], ax,
                                                                                L.n_axrows, tab[ax]);
     }
-    kindex_kernel<<<(unsigned)((L.K_pad + 255) / 256), 256, 0, st>>>(ps, L.K_pad, L.n_axrows, kinfo);
+    int2 *kofs = reinterpret_cast<int2 *>(w + L.off_ko);
+    kindex_kernel<<<(unsigned)((L.K_pad + 255) / 256), 256, 0, st>>>(ps, L.K_pad, L.n_axrows, a.ny, a.nz, kinfo, kofs);
     {
         const int64_t tot = (int64_t)L.M_pad * (L.K_pad / KD::PER_VEC);
         abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.coef32, a.SB, a.nx, X, kinfo,

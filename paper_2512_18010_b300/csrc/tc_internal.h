@@ -35,6 +35,7 @@ struct TcJobDev {
     const uint8_t *A;      // swizzled split A tiles [n_mt][nkc][stage bytes]
     const float2 *Y, *Z;   // per-axis power tables
     const int4 *kinfo;     // [nkc * BK] k -> (pair, v, w, axis row)
+    const int2 *kofs;      // [nkc * BK] k -> element offsets in Y and Z
     int ny, nz, nx, nkc;
     int M, n_mt, n_nt, pad0;
     int64_t N, nq;
