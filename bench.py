@@ -292,6 +292,22 @@ def batch_run(scff, ctx, jobs, precision, steps=2):
             "graph": "one captured CUDA graph per plan, replayed"}
 
 
+def aggregate(ms_local: float, units_local: int, dist=None, device=None):
+    """Whole-job rate over ranks: every rank's step time, the max taken across
+    ranks (the slowest rank bounds the job), divided into all ranks' units."""
+    ms = float(ms_local)
+    units = int(units_local)
+    if dist is not None and dist.is_initialized():
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units = int(u.item())
+    return ms, units / (ms / 1e3)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -362,13 +378,8 @@ def main():
     clocks = sampler.stop()
     ctx.sync(stream)
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    ms = float(np.mean(step_ms))
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     units = S * nq
-    value = world * units / (ms / 1e3)
+    ms, value = aggregate(float(np.mean(step_ms)), units, dist, dev)
 
     # plain FP64 GPU path on the same job
     fp64 = None
