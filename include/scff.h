@@ -267,7 +267,7 @@ scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
  * (log-bucketed pair rows, states and grid points) in a tensor-core precision
  * on a product grid times the candidate configurations -- the tensor-core
  * path with TMEM drains of 8 and 16 k-chunks, and the FP32 direct path with
- * state blocks of 8 and 16 -- on that job, and later calls of the same shape
+ * state blocks of 8, 12 and 16 -- on that job, and later calls of the same shape
  * use the fastest.  Every candidate meets the requested precision's bar.
  * scff_autotune_choice: out[0] = 1 tensor cores / 0 direct, out[1] = drain,
  * out[2] = state block, out[3] = best time in microseconds. */

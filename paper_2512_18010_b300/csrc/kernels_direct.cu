@@ -498,6 +498,8 @@ cudaError_t launch_direct(const DirectArgs &a, int fp64, int list_mode, int64_t 
     } else {
         if (a.SB == 8)
             e = launch_direct_t<float, 8>(a, list_mode != 0, st);
+        else if (a.SB == 12)
+            e = launch_direct_t<float, 12>(a, list_mode != 0, st);
         else if (a.SB == 16)
             e = launch_direct_t<float, 16>(a, list_mode != 0, st);
         else

@@ -602,7 +602,7 @@ static scff_status autotune(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_
     const size_t rsz = sizeof(float);
     const int S = t->S;
     const int64_t nq = g->n;
-    const std::vector<FFChoice> cand = {{1, 8, 8}, {1, 16, 8}, {0, 0, 8}, {0, 0, 16}};
+    const std::vector<FFChoice> cand = {{1, 8, 8}, {1, 16, 8}, {0, 0, 8}, {0, 0, 12}, {0, 0, 16}};
     TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
     TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
     cudaEvent_t e0, e1;
@@ -673,7 +673,8 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const bool fp64 = precision == SCFF_FP64;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
     const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
-    FFChoice ch = {tc_prec && g->product ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, fp64 ? 4 : 8};
+    const bool tc_path = tc_prec && g->product;
+    FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_state_block(S, fp64)};
     if (c->autotune && tc_prec && g->product && nq > 0) {
         const uint64_t key = tune_key(b->dev, S, nq, precision);
         auto it = c->tune.find(key);
@@ -738,7 +739,7 @@ struct PlanJob {
     int tc;            // tensor-core job
     int group;         // group index (tensor-core jobs)
     size_t region;     // offset of the job's tables and A image in the group area
-    int S, S_pad;
+    int S, S_pad, SB;
 };
 
 struct scff_plan_s {
@@ -798,7 +799,8 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         pj.group = -1;
         pj.region = 0;
         pj.S = j.trans->S;
-        pj.S_pad = (pj.S + P->SB - 1) / P->SB * P->SB;
+        pj.SB = pj.tc ? 8 : direct_state_block(pj.S, fp64);
+        pj.S_pad = (pj.S + pj.SB - 1) / pj.SB * pj.SB;
         const PairSetDev &ps = j.basis->dev;
         geom_max = std::max(geom_max, (size_t)ps.n_pair * 4 * sizeof(double));
         coef_max = std::max(coef_max, (size_t)pj.S_pad * ps.n_rows * (pj.tc ? sizeof(float) : rsz));
@@ -929,12 +931,12 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             const PairSetDev &ps = pj.job.basis->dev;
             CUDA_TRY(launch_pair_geom(ps, geom, st));
             ++*launches;
-            CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, P->SB, pj.S_pad, nullptr, (float *)coef, launches, st));
+            CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, pj.SB, pj.S_pad, nullptr, (float *)coef, launches, st));
             TcArgs ta;
             memset(&ta, 0, sizeof(ta));
             ta.ps = &ps;
             ta.coef32 = (const float *)coef;
-            ta.SB = P->SB;
+            ta.SB = pj.SB;
             ta.pair_geom = geom;
             ta.qx = pj.job.grid->d_qx;
             ta.qy = pj.job.grid->d_qy;
@@ -960,7 +962,7 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
         const scff_qgrid_s *gq = pj.job.grid;
         CUDA_TRY(launch_pair_geom(ps, geom, st));
         ++*launches;
-        CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, P->SB, pj.S_pad, fp64 ? (double *)coef : nullptr,
+        CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, pj.SB, pj.S_pad, fp64 ? (double *)coef : nullptr,
                                  fp64 ? nullptr : (float *)coef, launches, st));
         DirectArgs a;
         memset(&a, 0, sizeof(a));
@@ -968,7 +970,7 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
         a.coef = coef;
         a.nq = gq->n;
         a.S = pj.S;
-        a.SB = P->SB;
+        a.SB = pj.SB;
         a.scale = pj.job.scale;
         a.f = pj.job.f_out;
         a.f2 = pj.job.f2_out;

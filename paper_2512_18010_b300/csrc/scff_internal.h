@@ -97,6 +97,14 @@ struct EvalBuffers {
     int *err_flag = nullptr;     // device status word
 };
 
+// State block of the direct kernels: 4 in FP64; in FP32 the smallest of
+// 8/12/16 that covers S (12 for multiples of 12 above 16, else 16).  Shared by
+// every entry point so a job's arithmetic is the same alone and in a batch.
+inline int direct_state_block(int S, bool fp64) {
+    if (fp64) return 4;
+    return S <= 8 ? 8 : (S <= 12 ? 12 : (S <= 16 ? 16 : (S % 12 == 0 ? 12 : 16)));
+}
+
 // ---------------------------------------------------------------- kernels
 // All launchers return the launch status and never synchronise.
 

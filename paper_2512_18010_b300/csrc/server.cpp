@@ -175,7 +175,7 @@ void size_job(scff_server_s *sv, SJob *j) {
         b += up1k((size_t)ps.n_pair * (nx + ny + nz) * 2 * rsz);
     if (!j->req.out_on_device) b += up1k((size_t)j->S * j->nq * 3 * rsz);
     j->footprint = b;
-    const int SB = fp64 ? 4 : 8;
+    const int SB = tc_precision(sv->precision) ? 8 : direct_state_block(j->S, fp64);
     j->S_pad = (j->S + SB - 1) / SB * SB;
     j->scratch_need = up1k((size_t)ps.n_pair * 4 * sizeof(double)) + up1k((size_t)j->S_pad * ps.n_rows * rsz);
 }
@@ -202,7 +202,6 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
     const bool fp64 = sv->precision == SCFF_FP64;
     const bool tc = tc_precision(sv->precision);
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
-    const int SB = fp64 ? 4 : 8;
     int *d_err = reinterpret_cast<int *>(arena + B->scratch_off);
     double *geom = reinterpret_cast<double *>(arena + B->scratch_off + 1024);
     size_t geom_max = 0;
@@ -233,6 +232,7 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             fdev = work + work_bytes;
             f2dev = j->req.f2_out ? static_cast<uint8_t *>(fdev) + (size_t)j->S * j->nq * 2 * rsz : nullptr;
         }
+        const int SB = tc ? 8 : direct_state_block(j->S, fp64);
         if (launch_pair_geom(ps, geom, st) != cudaSuccess) return SCFF_ERR_CUDA;
         int64_t launches = 1;
         if (launch_pairprep(ps, j->req.trans->d_T, j->S, SB, j->S_pad, fp64 ? (double *)coef : nullptr,

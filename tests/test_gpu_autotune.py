@@ -24,7 +24,7 @@ def test_autotune_choice_and_parity(prec):
                 ctx.autotune_choice(b, t, g, prec)
             f1, _ = ctx.form_factor(b, t, g, precision=prec)
             ch = ctx.autotune_choice(b, t, g, prec)
-            assert ch["best_us"] > 0 and ch["state_block"] in (8, 16)
+            assert ch["best_us"] > 0 and ch["state_block"] in (8, 12, 16)
             n0 = ctx.kernel_launches()
             f2, _ = ctx.form_factor(b, t, g, precision=prec)
             assert ctx.kernel_launches() - n0 <= 12        # no re-tuning on the second call
