@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=0, help="also time a batched plan of this many batched-workload jobs")
+    ap.add_argument("--screen-eps", type=float, default=1e-8,
+                    help="also time the job with error-bounded pair screening at this eps (0 = skip)")
     return ap.parse_args()
 
 
@@ -430,6 +432,28 @@ def main():
                 "peak_source": "FP64 nominal 1.25 TFLOP/s" if fp64_path else
                 "FP32: 148 SM x 128 lanes x 2 flop x 2032 MHz"}
 
+    # the same job with error-bounded pair screening (results within eps * max|f| of the exact ones)
+    screened = None
+    if args.screen_eps > 0 and prec != scff.FP64:
+        ctx.set_screening(args.screen_eps)
+        for _ in range(2):
+            step()
+        sms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sms.append(e0.elapsed_time(e1))
+        info = ctx.screening_info(t, g)
+        ctx.set_screening(0.0)
+        sm = float(np.mean(sms))
+        screened = {"eps": args.screen_eps, "value": units / (sm / 1e3), "unit": UNIT, "ms_per_step": sm,
+                    "kept_pairs": info["kept_pairs"], "pairs": info["pairs"], "kept_rows": info["kept_rows"],
+                    "rows": info["rows"], "error_bound": "<= eps x max_q|f_s(q)| per state (rigorous)"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -480,7 +504,7 @@ def main():
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"dp{world} (one job per rank)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "fp64_gpu_path": fp64, "serving": serving, "batch": batch, "clocks": clocks,
+                "fp64_gpu_path": fp64, "screened": screened, "serving": serving, "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)
     ctx.close()

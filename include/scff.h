@@ -263,6 +263,22 @@ scff_status scff_sync(scff_ctx *ctx, void *stream);
  * accumulations at the cost of more epilogue traffic. */
 scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
 
+/*
+ * Error-bounded pair screening (the exact-tolerance form of the paper's
+ * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
+ * first scff_form_factor call for a (transitions, grid extent) bounds every
+ * pair's contribution over |q| <= the grid's largest |q|, evaluates f_s
+ * exactly at up to 64 grid points (F_s = their largest |f_s|), and removes
+ * the pairs of smallest bound while, for every state, the summed bounds of
+ * the removed pairs stay <= eps * F_s.  The result then differs from the
+ * exact one by at most eps * max_q |f_s(q)| for every state and q.  The
+ * compacted pair list is cached with the transitions.  eps = 0 (default)
+ * evaluates every pair.  scff_screening_info: out[0..3] = kept pairs, all
+ * pairs, kept and all contraction rows of the cached set.
+ */
+scff_status scff_set_screening(scff_ctx *ctx, double eps);
+scff_status scff_screening_info(scff_ctx *ctx, scff_trans_h trans, scff_qgrid_h grid, int64_t *out);
+
 /* Autotuner.  When enabled, the first scff_form_factor call for a job shape
  * (log-bucketed pair rows, states and grid points) in a tensor-core precision
  * on a product grid times the candidate configurations -- the tensor-core

@@ -150,6 +150,18 @@ static void free_trans(scff_trans_s *t) {
     cudaFree(t->d_T);
     delete t;
 }
+
+static void drop_screened(scff_ctx *c, scff_trans_s *t) {
+    for (size_t i = 0; i < c->screened.size();) {
+        if (!t || c->screened[i]->trans == t) {
+            cudaFree(c->screened[i]->dev.pair_rec);
+            delete c->screened[i];
+            c->screened.erase(c->screened.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
 static void free_grid(scff_qgrid_s *g) {
     cudaFree(g->d_qx);
     cudaFree(g->d_qy);
@@ -164,6 +176,7 @@ extern "C" void scff_destroy(scff_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    drop_screened(c, nullptr);
     for (auto *t : c->transs) free_trans(t);
     for (auto *b : c->bases) free_basis(b);
     for (auto *g : c->grids) free_grid(g);
@@ -400,6 +413,13 @@ extern "C" scff_status scff_qgrid_product(scff_ctx *c, const double *qx, int nx,
     g->hx.assign(qx, qx + nx);
     g->hy.assign(qy, qy + ny);
     g->hz.assign(qz, qz + nz);
+    {
+        double m[3] = {0, 0, 0};
+        for (int i = 0; i < nx; ++i) m[0] = std::max(m[0], fabs(qx[i]));
+        for (int i = 0; i < ny; ++i) m[1] = std::max(m[1], fabs(qy[i]));
+        for (int i = 0; i < nz; ++i) m[2] = std::max(m[2], fabs(qz[i]));
+        g->qmax = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    }
     scff_status st;
     if ((st = upload(&g->d_qx, g->hx)) || (st = upload(&g->d_qy, g->hy)) || (st = upload(&g->d_qz, g->hz))) {
         free_grid(g);
@@ -423,8 +443,11 @@ extern "C" scff_status scff_qgrid_list(scff_ctx *c, const double *q, int64_t n, 
     g->nx = g->ny = g->nz = 0;
     g->n = n;
     g->d_qx = g->d_qy = g->d_qz = g->d_q = nullptr;
+    for (int64_t i = 0; i < n; ++i)
+        g->qmax = std::max(g->qmax, sqrt(q[3 * i] * q[3 * i] + q[3 * i + 1] * q[3 * i + 1] + q[3 * i + 2] * q[3 * i + 2]));
     if (n > 0) {
         std::vector<double> v(q, q + 3 * n);
+        g->hq = v;
         scff_status st = upload(&g->d_q, v);
         if (st) {
             free_grid(g);
@@ -456,6 +479,7 @@ extern "C" void scff_release_basis(scff_ctx *c, scff_basis_h h) {
     // transitions built on this basis go with it
     for (size_t i = 0; i < c->transs.size();) {
         if (c->transs[i]->basis == h) {
+            drop_screened(c, c->transs[i]);
             free_trans(c->transs[i]);
             c->transs.erase(c->transs.begin() + i);
         } else {
@@ -468,6 +492,7 @@ extern "C" void scff_release_transitions(scff_ctx *c, scff_trans_h h) {
     if (!c || !h) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    if (std::find(c->transs.begin(), c->transs.end(), h) != c->transs.end()) drop_screened(c, h);
     release_from(c->transs, h, free_trans);
 }
 extern "C" void scff_release_qgrid(scff_ctx *c, scff_qgrid_h h) {
@@ -495,9 +520,8 @@ static size_t ff_footprint(const PairSetDev &ps, const scff_qgrid_s *g, int S, i
 }
 
 // Pair-prep and q-evaluation of one configuration into device outputs.
-static scff_status ff_run(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_qgrid_s *g, int precision, double scale,
-                          void *fdev, void *f2dev, const FFChoice &ch, cudaStream_t st) {
-    const PairSetDev &ps = b->dev;
+static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, scff_qgrid_s *g, int precision,
+                          double scale, void *fdev, void *f2dev, const FFChoice &ch, cudaStream_t st) {
     const int S = t->S;
     const int64_t nq = g->n;
     const bool fp64 = precision == SCFF_FP64;
@@ -597,7 +621,7 @@ static uint64_t tune_key(const PairSetDev &ps, int S, int64_t nq, int precision)
 // accuracy of the requested precision: TMEM drains of 8 or 16 k-chunks for
 // the split tensor-core modes, and the FP32 direct path (1e-6) for the
 // 1e-5-grade modes.
-static scff_status autotune(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_qgrid_s *g, int precision,
+static scff_status autotune(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, scff_qgrid_s *g, int precision,
                             cudaStream_t st, FFChoice *best) {
     const size_t rsz = sizeof(float);
     const int S = t->S;
@@ -613,11 +637,11 @@ static scff_status autotune(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_
     const int saved_timing = c->timing;
     c->timing = 0;
     for (const FFChoice &ch : cand) {
-        if (ff_footprint(b->dev, g, S, precision, ch) > c->budget) continue;
-        scff_status s = ff_run(c, b, t, g, precision, 1.0, c->fstage.p, c->f2stage.p, ch, st);  // warm-up
+        if (ff_footprint(ps, g, S, precision, ch) > c->budget) continue;
+        scff_status s = ff_run(c, ps, t, g, precision, 1.0, c->fstage.p, c->f2stage.p, ch, st);  // warm-up
         if (s != SCFF_OK) continue;
         cudaEventRecord(e0, st);
-        s = ff_run(c, b, t, g, precision, 1.0, c->fstage.p, c->f2stage.p, ch, st);
+        s = ff_run(c, ps, t, g, precision, 1.0, c->fstage.p, c->f2stage.p, ch, st);
         cudaEventRecord(e1, st);
         if (s != SCFF_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
         float ms = 0.f;
@@ -630,7 +654,197 @@ static scff_status autotune(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_
     c->timing = saved_timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->tune_ms[tune_key(b->dev, S, nq, precision)] = best_ms;
+    c->tune_ms[tune_key(ps, S, nq, precision)] = best_ms;
+    return SCFF_OK;
+}
+
+// ---- error-bounded pair screening
+
+static ScreenedSet *find_screened(scff_ctx *c, scff_trans_s *t, scff_qgrid_s *g) {
+    for (ScreenedSet *e : c->screened)
+        if (e->trans == t && e->eps == c->screen_eps && fabs(e->qmax - g->qmax) <= 1e-12 * (1.0 + g->qmax)) return e;
+    return nullptr;
+}
+
+// Up to 64 q points of the grid itself: the 8 nearest the origin and a
+// seeded sample, so max over them of |f_s| never exceeds its grid maximum.
+static std::vector<double> probe_points(const scff_qgrid_s *g) {
+    std::vector<double> q;
+    if (g->product) {
+        auto nearest2 = [](const std::vector<double> &ax) {
+            std::vector<int> idx(ax.size());
+            for (size_t i = 0; i < ax.size(); ++i) idx[i] = (int)i;
+            std::sort(idx.begin(), idx.end(), [&](int a, int b) { return fabs(ax[a]) < fabs(ax[b]); });
+            idx.resize(std::min<size_t>(2, idx.size()));
+            return idx;
+        };
+        for (int ix : nearest2(g->hx))
+            for (int iy : nearest2(g->hy))
+                for (int iz : nearest2(g->hz)) q.insert(q.end(), {g->hx[ix], g->hy[iy], g->hz[iz]});
+        uint64_t x = 0x9E3779B97F4A7C15ull;
+        while (q.size() < 3 * 64 && q.size() < (size_t)(3 * g->n)) {
+            x ^= x << 13;
+            x ^= x >> 7;
+            x ^= x << 17;
+            q.insert(q.end(), {g->hx[x % g->nx], g->hy[(x >> 20) % g->ny], g->hz[(x >> 40) % g->nz]});
+        }
+    } else {
+        const int64_t n = std::min<int64_t>(g->n, 64);
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t j = g->n <= 64 ? i : (i * (g->n / 64));
+            q.insert(q.end(), {g->hq[3 * j], g->hq[3 * j + 1], g->hq[3 * j + 2]});
+        }
+    }
+    return q;
+}
+
+// Drops every pair whose bounded contribution, summed over the dropped pairs,
+// stays below eps * F_s for every state s, where F_s is the largest |f_s| at
+// the probe points (a lower bound of max |f_s| on the grid): the screened
+// result then differs from the exact one by at most eps * max_q |f_s(q)|.
+static scff_status get_screened(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, scff_qgrid_s *g, cudaStream_t st,
+                                ScreenedSet **out) {
+    if (ScreenedSet *e = find_screened(c, t, g)) {
+        *out = e;
+        return SCFF_OK;
+    }
+    const PairSetDev &ps = b->dev;
+    const int S = t->S;
+    const int SB = direct_state_block(S, false);
+    const int S_pad = (S + SB - 1) / SB * SB;
+    TRY(grow(c, c->coef, (size_t)S_pad * ps.n_rows * sizeof(float) + 256));
+    TRY(grow(c, c->geom, (size_t)ps.n_pair * 4 * sizeof(double) + 64));
+    CUDA_TRY(launch_pair_geom(ps, (double *)c->geom.p, st));
+    CUDA_TRY(launch_pairprep(ps, t->d_T, S, SB, S_pad, nullptr, (float *)c->coef.p, &c->launches, st));
+    std::vector<double> qp = probe_points(g);
+    const int np = (int)(qp.size() / 3);
+    float *d_bound = nullptr, *d_fp = nullptr;
+    double *d_q = nullptr;
+    const size_t nb = (size_t)ps.n_pair * S;
+    if (cudaMalloc(&d_bound, sizeof(float) * std::max<size_t>(nb, 1)) != cudaSuccess ||
+        cudaMalloc(&d_fp, sizeof(float) * 2 * (size_t)S * std::max(np, 1)) != cudaSuccess ||
+        cudaMalloc(&d_q, sizeof(double) * std::max<size_t>(qp.size(), 3)) != cudaSuccess) {
+        cudaFree(d_bound);
+        cudaFree(d_fp);
+        cudaFree(d_q);
+        return fail(SCFF_ERR_OOM, "scff_form_factor: screening buffers");
+    }
+    std::vector<float> hb(nb), hf(2 * (size_t)S * np);
+    scff_status rc = SCFF_OK;
+    do {
+        if (launch_pair_bounds(ps, (const float *)c->coef.p, SB, S, g->qmax, d_bound, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_q, qp.data(), sizeof(double) * qp.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = fail(SCFF_ERR_CUDA, "scff_form_factor: screening launch failed");
+            break;
+        }
+        DirectArgs a;
+        memset(&a, 0, sizeof(a));
+        a.ps = &ps;
+        a.coef = c->coef.p;
+        a.qlist = d_q;
+        a.pair_geom = (const double *)c->geom.p;
+        a.nq = np;
+        a.S = S;
+        a.SB = SB;
+        a.scale = 1.0;
+        a.f = d_fp;
+        a.err_flag = c->d_err;
+        if (launch_direct(a, 0, 1, &c->launches, st) != cudaSuccess ||
+            cudaMemcpyAsync(hb.data(), d_bound, sizeof(float) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hf.data(), d_fp, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = fail(SCFF_ERR_CUDA, "scff_form_factor: screening probe failed");
+            break;
+        }
+    } while (0);
+    cudaFree(d_bound);
+    cudaFree(d_fp);
+    cudaFree(d_q);
+    if (rc != SCFF_OK) return rc;
+    std::vector<double> F(S, 0.0);
+    for (int s = 0; s < S; ++s)
+        for (int i = 0; i < np; ++i) {
+            const double re = hf[2 * ((size_t)s * np + i)], im = hf[2 * ((size_t)s * np + i) + 1];
+            F[s] = std::max(F[s], sqrt(re * re + im * im) * (1.0 - 1e-4));  // margin for the FP32 probe
+        }
+    // greedy: smallest relative bound first, stop at the first pair that does not fit
+    std::vector<double> score(ps.n_pair);
+    for (int p = 0; p < ps.n_pair; ++p) {
+        double m = 0.0;
+        for (int s = 0; s < S; ++s) {
+            const double bb = hb[(size_t)p * S + s];
+            m = std::max(m, F[s] > 0 ? bb / F[s] : (bb > 0 ? 1e300 : 0.0));
+        }
+        score[p] = m;
+    }
+    std::vector<int> order(ps.n_pair);
+    for (int p = 0; p < ps.n_pair; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return score[x] < score[y]; });
+    std::vector<char> keep(ps.n_pair, 1);
+    std::vector<double> cum(S, 0.0);
+    for (int p : order) {
+        bool fits = true;
+        for (int s = 0; s < S && fits; ++s) fits = cum[s] + hb[(size_t)p * S + s] <= c->screen_eps * F[s];
+        if (!fits) break;
+        for (int s = 0; s < S; ++s) cum[s] += hb[(size_t)p * S + s];
+        keep[p] = 0;
+    }
+    // compacted pair list, still ordered by class
+    std::vector<int2> all(ps.n_pair), kept;
+    CUDA_TRY(cudaMemcpy(all.data(), ps.pair_rec, sizeof(int2) * ps.n_pair, cudaMemcpyDeviceToHost));
+    ScreenedSet *e = new ScreenedSet();
+    e->trans = t;
+    e->eps = c->screen_eps;
+    e->qmax = g->qmax;
+    e->dev = ps;
+    e->total = ps.n_pair;
+    e->dev.pair_off[0] = 0;
+    e->dev.row_off[0] = e->dev.krow_off[0] = e->dev.axrow_off[0] = 0;
+    for (int L = 0; L < kNumClasses; ++L) {
+        int cnt = 0;
+        for (int p = ps.pair_off[L]; p < ps.pair_off[L + 1]; ++p)
+            if (keep[p]) {
+                kept.push_back(all[p]);
+                ++cnt;
+            }
+        e->dev.pair_off[L + 1] = e->dev.pair_off[L] + cnt;
+        e->dev.row_off[L + 1] = e->dev.row_off[L] + (int64_t)cnt * mono_count(L);
+        e->dev.krow_off[L + 1] = e->dev.krow_off[L] + (int64_t)cnt * vw_count(L);
+        e->dev.axrow_off[L + 1] = e->dev.axrow_off[L] + (int64_t)cnt * (L + 1);
+    }
+    e->dev.n_pair = (int)kept.size();
+    e->dev.n_rows = e->dev.row_off[kNumClasses];
+    e->dev.n_krows = e->dev.krow_off[kNumClasses];
+    e->dev.n_axrows = e->dev.axrow_off[kNumClasses];
+    e->kept = (int)kept.size();
+    e->dev.pair_rec = nullptr;
+    if (!kept.empty()) {
+        scff_status us = upload(&e->dev.pair_rec, kept);
+        if (us != SCFF_OK) {
+            delete e;
+            return us;
+        }
+    }
+    c->screened.push_back(e);
+    *out = e;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_set_screening(scff_ctx *c, double eps) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_screening: NULL context");
+    if (!(eps >= 0.0 && eps < 1.0)) return fail(SCFF_ERR_INVALID_ARG, "scff_set_screening: eps %g", eps);
+    c->screen_eps = eps;
+    return SCFF_OK;
+}
+
+extern "C" scff_status scff_screening_info(scff_ctx *c, scff_trans_h t, scff_qgrid_h g, int64_t *out) {
+    if (!c || !t || !g || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_screening_info: NULL argument");
+    ScreenedSet *e = find_screened(c, t, g);
+    if (!e) return fail(SCFF_ERR_NOT_FOUND, "scff_screening_info: no screened pair set for this job");
+    out[0] = e->kept;
+    out[1] = e->total;
+    out[2] = e->dev.n_krows;
+    out[3] = t->basis->dev.n_krows;
     return SCFF_OK;
 }
 
@@ -643,7 +857,8 @@ extern "C" scff_status scff_set_autotune(scff_ctx *c, int enable) {
 extern "C" scff_status scff_autotune_choice(scff_ctx *c, scff_basis_h b, scff_trans_h t, scff_qgrid_h g,
                                             int precision, int32_t *out) {
     if (!c || !b || !t || !g || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_autotune_choice: NULL argument");
-    auto it = c->tune.find(tune_key(b->dev, t->S, g->n, precision));
+    const ScreenedSet *se = c->screen_eps > 0 ? find_screened(c, t, g) : nullptr;
+    auto it = c->tune.find(tune_key(se ? se->dev : b->dev, t->S, g->n, precision));
     if (it == c->tune.end()) return fail(SCFF_ERR_NOT_FOUND, "scff_autotune_choice: shape not tuned yet");
     out[0] = it->second.use_tc;
     out[1] = it->second.drain;
@@ -675,19 +890,25 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
     const bool tc_path = tc_prec && g->product;
     FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_state_block(S, fp64)};
+    const PairSetDev *ps = &b->dev;
+    if (c->screen_eps > 0 && nq > 0) {
+        ScreenedSet *se = nullptr;
+        TRY(get_screened(c, b, t, g, st, &se));
+        ps = &se->dev;
+    }
     if (c->autotune && tc_prec && g->product && nq > 0) {
-        const uint64_t key = tune_key(b->dev, S, nq, precision);
+        const uint64_t key = tune_key(*ps, S, nq, precision);
         auto it = c->tune.find(key);
         if (it == c->tune.end()) {
             FFChoice best;
-            TRY(autotune(c, b, t, g, precision, st, &best));
+            TRY(autotune(c, *ps, t, g, precision, st, &best));
             it = c->tune.emplace(key, best).first;
         }
         ch = it->second;
     }
     // footprint check (admission)
     const size_t out_bytes = (size_t)S * nq * rsz * 3;
-    const size_t foot = ff_footprint(b->dev, g, S, precision, ch) + (out_on_device ? 0 : out_bytes);
+    const size_t foot = ff_footprint(*ps, g, S, precision, ch) + (out_on_device ? 0 : out_bytes);
     if (foot > c->budget)
         return fail(SCFF_ERR_ADMISSION, "scff_form_factor: footprint %zu bytes exceeds the budget %llu", foot,
                     (unsigned long long)c->budget);
@@ -700,7 +921,14 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
             f2dev = c->f2stage.p;
         }
     }
-    TRY(ff_run(c, b, t, g, precision, scale, fdev, f2dev, ch, st));
+    if (ps->n_pair == 0) {  // every pair screened away: the result is zero to within eps
+        if (nq > 0) {
+            CUDA_TRY(cudaMemsetAsync(fdev, 0, (size_t)S * nq * 2 * rsz, st));
+            if (f2dev) CUDA_TRY(cudaMemsetAsync(f2dev, 0, (size_t)S * nq * rsz, st));
+        }
+    } else {
+        TRY(ff_run(c, *ps, t, g, precision, scale, fdev, f2dev, ch, st));
+    }
     if (!out_on_device) {
         if (nq > 0) {
             CUDA_TRY(cudaMemcpyAsync(f_out, fdev, (size_t)S * nq * 2 * rsz, cudaMemcpyDeviceToHost, st));

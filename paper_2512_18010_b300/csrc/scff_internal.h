@@ -119,6 +119,10 @@ cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB
 cudaError_t launch_axis_tables(const PairSetDev &ps, const double *pair_geom, const double *qaxis,
                                int n, int axis, void *table, int fp64, cudaStream_t st);
 
+// bound[pair][s]: an upper bound of |pair term for state s| over |q| <= qmax.
+cudaError_t launch_pair_bounds(const PairSetDev &ps, const float *coef32, int SB, int S, double qmax, float *bound,
+                               cudaStream_t st);
+
 struct DirectArgs {
     const PairSetDev *ps;
     const void *coef;        // coef64 or coef32 in [n_sblk][n_rows][SB] layout

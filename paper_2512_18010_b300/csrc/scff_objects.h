@@ -44,6 +44,9 @@ struct scff_ctx {
     std::vector<struct scff_trans_s *> transs;
     std::vector<struct scff_qgrid_s *> grids;
     std::vector<struct scff_plan_s *> plans;
+    // error-bounded pair screening (0 = off) and its cached compacted pair sets
+    double screen_eps = 0.0;
+    std::vector<struct ScreenedSet *> screened;
     // autotuner: chosen configuration and its time per job-shape key
     int autotune = 0;
     std::map<uint64_t, struct FFChoice> tune;
@@ -68,8 +71,20 @@ struct scff_qgrid_s {
     int product;
     int nx, ny, nz;
     int64_t n;
+    double qmax = 0.0;           // largest |q| of the grid
+    std::vector<double> hq;      // host copy of an explicit list
     double *d_qx, *d_qy, *d_qz;  // product grid axes
     double *d_q;                 // list [n][3]
     std::vector<double> hx, hy, hz;
 };
 
+
+// A pair list with the pairs whose bounded contribution is negligible
+// removed (scff_set_screening); records are borrowed from the basis.
+struct ScreenedSet {
+    struct scff_trans_s *trans;
+    double eps;
+    double qmax;
+    scff::PairSetDev dev;  // own pair_rec, everything else shared with the basis
+    int kept, total;
+};

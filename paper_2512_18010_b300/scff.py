@@ -30,7 +30,8 @@ _SYMBOLS = [
     "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_form_factor_static",
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
-    "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice",
+    "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
+    "scff_screening_info",
 ]
 
 
@@ -113,6 +114,10 @@ def load(build_if_missing: bool = True):
         getattr(lib, n).restype = I32
     lib.scff_server_destroy.argtypes = [P]
     lib.scff_server_destroy.restype = None
+    lib.scff_set_screening.argtypes = [P, D]
+    lib.scff_set_screening.restype = I32
+    lib.scff_screening_info.argtypes = [P, P, P, P]
+    lib.scff_screening_info.restype = I32
     lib.scff_set_autotune.argtypes = [P, ctypes.c_int]
     lib.scff_set_autotune.restype = I32
     lib.scff_autotune_choice.argtypes = [P, P, P, P, ctypes.c_int, P]
@@ -399,6 +404,15 @@ class Context:
     def set_tc_drain(self, drain_every: int):
         """k-chunks per tensor-core TMEM accumulation (0 = whole K, -1 = default)."""
         _check(self.lib.scff_set_tc_drain(self.h, int(drain_every)))
+
+    def set_screening(self, eps: float):
+        """Error-bounded pair screening: results within eps * max|f| of the exact ones (0 = off)."""
+        _check(self.lib.scff_set_screening(self.h, float(eps)))
+
+    def screening_info(self, trans: Transitions, grid: QGrid) -> dict:
+        out = np.zeros(4, dtype=np.int64)
+        _check(self.lib.scff_screening_info(self.h, trans.handle, grid.handle, _p(out)))
+        return {"kept_pairs": int(out[0]), "pairs": int(out[1]), "kept_rows": int(out[2]), "rows": int(out[3])}
 
     def set_autotune(self, enable: bool = True):
         _check(self.lib.scff_set_autotune(self.h, 1 if enable else 0))
