@@ -264,6 +264,21 @@ scff_status scff_sync(scff_ctx *ctx, void *stream);
 scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
 
 /*
+ * Separable integrals (Sec. "Cartesian Grid Method": the one-axis V-tensors
+ * alone give integrals of f_S against a product of one-axis functions):
+ *   out[s] = scale * sum_{ix,iy,iz} wx[ix] wy[iy] wz[iz] f_s(qx[ix], qy[iy], qz[iz])
+ * as (Re, Im) pairs, out[n_states][2] on the host, in FP64, without forming
+ * the three-dimensional grid: the cost is linear in nx + ny + nz (the weights
+ * carry the quadrature rule and the one-axis functions).  Host arrays in,
+ * synchronous.
+ */
+scff_status scff_separable_integral(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
+                                    const double *qx, const double *wx, int nx,
+                                    const double *qy, const double *wy, int ny,
+                                    const double *qz, const double *wz, int nz, double scale,
+                                    double *out);
+
+/*
  * Error-bounded pair screening (the exact-tolerance form of the paper's
  * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
  * first scff_form_factor call for a (transitions, grid extent) bounds every

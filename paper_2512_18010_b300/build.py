@@ -13,7 +13,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libscff.so")
-SOURCES = ["scff_host.cpp", "kernels_direct.cu", "kernels_tc.cu", "static_entry.cu", "server.cpp"]
+SOURCES = ["scff_host.cpp", "kernels_direct.cu", "kernels_tc.cu", "kernels_separable.cu", "static_entry.cu",
+           "server.cpp"]
 HEADERS = ["scff_internal.h", "tc_internal.h", "device_common.cuh", "scff_objects.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -941,6 +941,68 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     return SCFF_OK;
 }
 
+// Separable integral of every state's form factor against wx(qx) wy(qy) wz(qz).
+extern "C" scff_status scff_separable_integral(scff_ctx *c, scff_basis_h b, scff_trans_h t, const double *qx,
+                                               const double *wx, int nx, const double *qy, const double *wy, int ny,
+                                               const double *qz, const double *wz, int nz, double scale,
+                                               double *out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_separable_integral: NULL argument");
+    if (!b || std::find(c->bases.begin(), c->bases.end(), b) == c->bases.end())
+        return fail(SCFF_ERR_NOT_FOUND, "scff_separable_integral: unknown basis handle");
+    if (!t || std::find(c->transs.begin(), c->transs.end(), t) == c->transs.end() || t->basis != b)
+        return fail(SCFF_ERR_NOT_FOUND, "scff_separable_integral: unknown or mismatched transitions handle");
+    if (nx < 1 || ny < 1 || nz < 1 || !qx || !wx || !qy || !wy || !qz || !wz || !isfinite(scale))
+        return fail(SCFF_ERR_INVALID_ARG, "scff_separable_integral: empty axis or NULL array");
+    cudaSetDevice(c->device);
+    const PairSetDev &ps = b->dev;
+    const int S = t->S, SB = 4, S_pad = (S + 3) / 4 * 4;
+    const int n[3] = {nx, ny, nz};
+    const double *hq[3] = {qx, qy, qz}, *hw[3] = {wx, wy, wz};
+    size_t bytes = (size_t)ps.n_pair * 32 + 256;
+    const size_t coef_off = bytes;
+    bytes += (size_t)S_pad * ps.n_rows * 8 + 256;
+    const size_t ax_off = bytes;
+    bytes += sizeof(double) * 2 * (size_t)(nx + ny + nz) + 256;
+    const size_t sums_off = bytes;
+    bytes += sizeof(double2) * 3 * (size_t)(ps.n_axrows + 1) + 256;
+    const size_t part_off = bytes;
+    bytes += sizeof(double2) * (size_t)S * (ps.n_pair + 1) + 256;
+    const size_t out_off = bytes;
+    bytes += sizeof(double) * 2 * S + 256;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) return fail(SCFF_ERR_OOM, "scff_separable_integral: %zu bytes", bytes);
+    uint8_t *B = static_cast<uint8_t *>(buf);
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    double *geom = reinterpret_cast<double *>(B);
+    double *coef = reinterpret_cast<double *>(B + al(coef_off));
+    double *dq[3], *dw[3];
+    size_t o = al(ax_off);
+    for (int a = 0; a < 3; ++a) {
+        dq[a] = reinterpret_cast<double *>(B + o);
+        o += sizeof(double) * n[a];
+        dw[a] = reinterpret_cast<double *>(B + o);
+        o += sizeof(double) * n[a];
+    }
+    double2 *sums = reinterpret_cast<double2 *>(B + al(sums_off));
+    double2 *part = reinterpret_cast<double2 *>(B + al(part_off));
+    double *dout = reinterpret_cast<double *>(B + al(out_off));
+    scff_status rc = SCFF_OK;
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        e = cudaMemcpy(dq[a], hq[a], sizeof(double) * n[a], cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dw[a], hw[a], sizeof(double) * n[a], cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = launch_pair_geom(ps, geom, 0);
+    if (e == cudaSuccess) e = launch_pairprep(ps, t->d_T, S, SB, S_pad, coef, nullptr, &c->launches, 0);
+    const double *cq[3] = {dq[0], dq[1], dq[2]}, *cw[3] = {dw[0], dw[1], dw[2]};
+    if (e == cudaSuccess)
+        e = launch_separable(ps, geom, coef, SB, S, cq, cw, n, sums, part, scale, dout, &c->launches, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = fail(SCFF_ERR_CUDA, "scff_separable_integral: %s", cudaGetErrorString(e));
+    cudaFree(buf);
+    return rc;
+}
+
 // Reads the device status word after all work on `stream` has finished.
 extern "C" scff_status scff_sync(scff_ctx *c, void *stream) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_sync: NULL context");

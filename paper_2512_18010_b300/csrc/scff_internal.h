@@ -123,6 +123,12 @@ cudaError_t launch_axis_tables(const PairSetDev &ps, const double *pair_geom, co
 cudaError_t launch_pair_bounds(const PairSetDev &ps, const float *coef32, int SB, int S, double qmax, float *bound,
                                cudaStream_t st);
 
+// Separable integrals I_s = sum wx wy wz f_s over a product grid (FP64).
+// sums: 3 * n_axrows double2; part: S * n_pair double2; out: [S][2].
+cudaError_t launch_separable(const PairSetDev &ps, const double *geom, const double *coef64, int SB, int S,
+                             const double *const q[3], const double *const w[3], const int n[3], double2 *sums,
+                             double2 *part, double scale, double *out, int64_t *launches, cudaStream_t st);
+
 struct DirectArgs {
     const PairSetDev *ps;
     const void *coef;        // coef64 or coef32 in [n_sblk][n_rows][SB] layout

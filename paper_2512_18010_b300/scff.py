@@ -31,7 +31,7 @@ _SYMBOLS = [
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
-    "scff_screening_info",
+    "scff_screening_info", "scff_separable_integral",
 ]
 
 
@@ -114,6 +114,9 @@ def load(build_if_missing: bool = True):
         getattr(lib, n).restype = I32
     lib.scff_server_destroy.argtypes = [P]
     lib.scff_server_destroy.restype = None
+    lib.scff_separable_integral.argtypes = [P, P, P, P, P, ctypes.c_int, P, P, ctypes.c_int, P, P, ctypes.c_int,
+                                            D, P]
+    lib.scff_separable_integral.restype = I32
     lib.scff_set_screening.argtypes = [P, D]
     lib.scff_set_screening.restype = I32
     lib.scff_screening_info.argtypes = [P, P, P, P]
@@ -404,6 +407,18 @@ class Context:
     def set_tc_drain(self, drain_every: int):
         """k-chunks per tensor-core TMEM accumulation (0 = whole K, -1 = default)."""
         _check(self.lib.scff_set_tc_drain(self.h, int(drain_every)))
+
+    def separable_integral(self, basis: Basis, trans: Transitions, qx, wx, qy, wy, qz, wz,
+                           scale: float = 1.0) -> np.ndarray:
+        """I_s = scale * sum wx(qx) wy(qy) wz(qz) f_s(q) over the product grid, as complex [S]."""
+        arrs = [_np(a, np.float64) for a in (qx, wx, qy, wy, qz, wz)]
+        if len(arrs[0]) != len(arrs[1]) or len(arrs[2]) != len(arrs[3]) or len(arrs[4]) != len(arrs[5]):
+            raise ValueError("each axis needs as many weights as points")
+        out = np.zeros((trans.n_states, 2), dtype=np.float64)
+        _check(self.lib.scff_separable_integral(self.h, basis.handle, trans.handle, _p(arrs[0]), _p(arrs[1]),
+                                                len(arrs[0]), _p(arrs[2]), _p(arrs[3]), len(arrs[2]), _p(arrs[4]),
+                                                _p(arrs[5]), len(arrs[4]), float(scale), _p(out)))
+        return out[:, 0] + 1j * out[:, 1]
 
     def set_screening(self, eps: float):
         """Error-bounded pair screening: results within eps * max|f| of the exact ones (0 = off)."""
