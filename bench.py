@@ -83,7 +83,7 @@ def workload(name: str, rank: int = 0):
 
 def pair_stats(mol):
     """Pair records, monomial rows K and (v,w) rows of a basis."""
-    lmax = {0: 0, 1: 1, 2: 2, -1: 1}
+    lmax = {0: 0, 1: 1, 2: 2, 3: 3, -1: 1}
     recs = []
     for l, n in zip(mol.shell_l, mol.shell_nprim):
         recs += [lmax[int(l)]] * int(n)

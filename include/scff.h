@@ -49,7 +49,7 @@ typedef int32_t scff_status;
 enum {
     SCFF_OK = 0,
     SCFF_ERR_INVALID_ARG = 1,  /* a size, pointer, code or layout is invalid */
-    SCFF_ERR_UNSUPPORTED_L = 2,/* shell angular momentum above Cartesian d */
+    SCFF_ERR_UNSUPPORTED_L = 2,/* shell angular momentum above Cartesian f */
     SCFF_ERR_OOM = 3,          /* device or host allocation failed */
     SCFF_ERR_ADMISSION = 4,    /* job footprint exceeds the context's HBM budget */
     SCFF_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the name) */
@@ -96,17 +96,19 @@ const char *scff_last_error(void);
  * expansion into Cartesian terms).
  *   xyz[n_atoms][3]       atom centres, Bohr.
  *   shell_atom[n_shells]  atom index of each shell.
- *   shell_l[n_shells]     0 = s, 1 = p, 2 = Cartesian d, -1 = sp (s and p
- *                         sharing exponents).  Other values give
- *                         SCFF_ERR_UNSUPPORTED_L (l >= 3) or INVALID_ARG.
+ *   shell_l[n_shells]     0 = s, 1 = p, 2 = Cartesian d, 3 = Cartesian f,
+ *                         -1 = sp (s and p sharing exponents).  Other
+ *                         values give SCFF_ERR_UNSUPPORTED_L (l >= 4) or
+ *                         INVALID_ARG.
  *   shell_nprim[n_shells] primitives per shell (1..64).
  *   exponents[]           alpha of exp(-alpha r^2), all shells concatenated
  *                         (sum of shell_nprim entries), each > 0.
  *   coefficients[]        contraction coefficients, concatenated; an sp
  *                         shell stores nprim s coefficients then nprim p
  *                         coefficients.
- * Functions are numbered shell by shell; Cartesian components are ordered
- * x,y,z and xx,xy,xz,yy,yz,zz; an sp shell gives s,px,py,pz.  Each primitive
+ * Functions are numbered shell by shell; Cartesian components are ordered by
+ * descending x power, then descending y power: x,y,z; xx,xy,xz,yy,yz,zz;
+ * xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz; an sp shell gives s,px,py,pz.  Each primitive
  * Cartesian term is normalised to unit norm; with SCFF_RENORM_CONTRACTED the
  * contracted function is then rescaled to unit norm as well.
  * On success *out is a new handle and *nbf_out the function count.

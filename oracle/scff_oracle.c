@@ -33,8 +33,10 @@
  * exponent form (Eqs. sigmaTidbits, positionTidbits with sigma^2 = 1/(2 alpha)).
  * Accumulation over function pairs runs in long double.
  *
- * Basis conventions: shell codes 0 = s, 1 = p, 2 = Cartesian d, -1 = sp; the
- * Cartesian components are ordered x,y,z and xx,xy,xz,yy,yz,zz; an sp shell
+ * Basis conventions: shell codes 0 = s, 1 = p, 2 = Cartesian d, 3 = Cartesian
+ * f, -1 = sp; the Cartesian components of a shell of angular momentum l are
+ * ordered by descending x power, then descending y power (x,y,z;
+ * xx,xy,xz,yy,yz,zz; xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz); an sp shell
  * gives s,px,py,pz and stores its s coefficients before its p coefficients.
  */
 #include <complex.h>
@@ -63,6 +65,7 @@ static int nfn_of(int l) {
     case 0: return 1;
     case 1: return 3;
     case 2: return 6;
+    case 3: return 10;
     case -1: return 4;
     default: return -1;
     }
@@ -73,9 +76,12 @@ static void powers_of(int l, int i, int pw[3]) {
     static const int P1[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     static const int P2[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1},
                                  {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+    static const int P3[10][3] = {{3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1},
+                                  {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
     pw[0] = pw[1] = pw[2] = 0;
     if (l == 1) memcpy(pw, P1[i], sizeof(int) * 3);
     else if (l == 2) memcpy(pw, P2[i], sizeof(int) * 3);
+    else if (l == 3) memcpy(pw, P3[i], sizeof(int) * 3);
     else if (l == -1 && i > 0) memcpy(pw, P1[i - 1], sizeof(int) * 3);
 }
 
@@ -161,21 +167,21 @@ static void free_functions(ofn_t *fns, int nbf) {
 }
 
 /* Coefficients e_t of (y + u)^a (y + v)^b = sum_t e_t y^t (binomial theorem). */
-static int binomial_product(int a, double u, int b, double v, double e[5]) {
-    double ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+static int binomial_product(int a, double u, int b, double v, double e[7]) {
+    double ea[4] = {0, 0, 0, 0}, eb[4] = {0, 0, 0, 0};
     /* (y+u)^a = sum_i C(a,i) u^{a-i} y^i */
-    static const double C[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 2, 1}};
+    static const double C[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
     for (int i = 0; i <= a; ++i) ea[i] = C[a][i] * pow(u, a - i);
     for (int j = 0; j <= b; ++j) eb[j] = C[b][j] * pow(v, b - j);
-    for (int t = 0; t < 5; ++t) e[t] = 0.0;
+    for (int t = 0; t < 7; ++t) e[t] = 0.0;
     for (int i = 0; i <= a; ++i)
         for (int j = 0; j <= b; ++j) e[i + j] += ea[i] * eb[j];
     return a + b;
 }
 
 /* sum_t e_t J_t(q) with J from the integration-by-parts recurrence. */
-static double complex axis_factor(const double e[5], int tmax, double p, double q) {
-    double complex J[5];
+static double complex axis_factor(const double e[7], int tmax, double p, double q) {
+    double complex J[7];
     J[0] = sqrt(M_PI / p) * exp(-q * q / (4.0 * p));
     if (tmax >= 1) J[1] = (I * q / (2.0 * p)) * J[0];
     for (int t = 1; t < tmax; ++t) J[t + 1] = (I * q * J[t] + (double)t * J[t - 1]) / (2.0 * p);
@@ -201,7 +207,7 @@ static double complex pair_integral(const ofn_t *m, const ofn_t *n, const double
             double phase = 0.0;
             for (int i = 0; i < 3; ++i) {
                 P[i] = (al * A[i] + be * B[i]) / p;
-                double e[5];
+                double e[7];
                 const int tmax = binomial_product(m->pw[i], P[i] - A[i], n->pw[i], P[i] - B[i], e);
                 prod *= axis_factor(e, tmax, p, q[i]);
                 phase += q[i] * P[i];

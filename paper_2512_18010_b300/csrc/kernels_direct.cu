@@ -25,37 +25,49 @@ namespace scff {
 
 // ------------------------------------------------------------------ helpers
 
-// Cartesian exponent of function j of a record type along axis ax.
+// Cartesian exponent of function j of a record type along axis ax
+// (s; p: x,y,z; d: xx,xy,xz,yy,yz,zz; sp: s,x,y,z; f: xxx,xxy,...,zzz).
 __host__ __device__ constexpr int fn_pow(int type, int j, int ax) {
-    // s: (000); p: x,y,z; d: xx,xy,xz,yy,yz,zz; sp: s,x,y,z
-    return type == REC_S   ? 0
-           : type == REC_P ? (j == ax ? 1 : 0)
-           : type == REC_SP
-               ? (j == 0 ? 0 : (j - 1 == ax ? 1 : 0))
-               : /* d */ (ax == 0 ? (j == 0 ? 2 : (j == 1 || j == 2) ? 1 : 0)
-                          : ax == 1 ? (j == 3 ? 2 : (j == 1 || j == 4) ? 1 : 0)
-                                    : (j == 5 ? 2 : (j == 2 || j == 4) ? 1 : 0));
+    return type == REC_SP ? (j == 0 ? 0 : cart_pow(1, j - 1, ax)) : cart_pow(rec_lmax(type), j, ax);
 }
 
-// (u+2m)! / (m! u! 2^m) for u + 2m <= 4.
+// (u+2m)! / (m! u! 2^m), the Hermite-to-monomial factor of Eq. Ccoefficients.
 __device__ __forceinline__ double herm_mono_factor(int u, int m) {
-    if (m == 0) return 1.0;
-    if (m == 1) return u == 0 ? 1.0 : u == 1 ? 3.0 : 6.0;  // 2!/2, 3!/2, 4!/(2!*2)
-    return 3.0;                                            // u = 0, m = 2: 4!/(2!*4)
+    double num = 1.0;
+    for (int k = 2; k <= u + 2 * m; ++k) num *= k;
+    double den = 1.0;
+    for (int k = 2; k <= m; ++k) den *= k;
+    for (int k = 2; k <= u; ++k) den *= k;
+    for (int k = 0; k < m; ++k) den *= 2.0;
+    return num / den;
 }
 
 // C^u for exponents (a, a2) along one axis, PA = P - A, PB = P - B, s2 = 1/(2p).
 __device__ double c_coef(int a, int a2, int u, double PA, double PB, double s2) {
     const int deg = a + a2;
     if (u > deg) return 0.0;
-    // binomial coefficients of (y+PA)^a and (y+PB)^a2 (a, a2 <= 2)
-    double ea[3], eb[3];
-    ea[0] = (a == 0) ? 1.0 : (a == 1) ? PA : PA * PA;
-    ea[1] = (a == 0) ? 0.0 : (a == 1) ? 1.0 : 2.0 * PA;
-    ea[2] = (a == 2) ? 1.0 : 0.0;
-    eb[0] = (a2 == 0) ? 1.0 : (a2 == 1) ? PB : PB * PB;
-    eb[1] = (a2 == 0) ? 0.0 : (a2 == 1) ? 1.0 : 2.0 * PB;
-    eb[2] = (a2 == 2) ? 1.0 : 0.0;
+    // binomial coefficients of (y+PA)^a and (y+PB)^a2 (a, a2 <= 3)
+    double ea[4], eb[4];
+    for (int i = 0; i <= 3; ++i) {
+        ea[i] = 0.0;
+        eb[i] = 0.0;
+    }
+    {
+        double bc = 1.0;  // C(a, i) PA^(a-i)
+        for (int i = 0; i <= a; ++i) {
+            double pw = 1.0;
+            for (int k = 0; k < a - i; ++k) pw *= PA;
+            ea[i] = bc * pw;
+            bc = bc * (a - i) / (i + 1);
+        }
+        bc = 1.0;
+        for (int i = 0; i <= a2; ++i) {
+            double pw = 1.0;
+            for (int k = 0; k < a2 - i; ++k) pw *= PB;
+            eb[i] = bc * pw;
+            bc = bc * (a2 - i) / (i + 1);
+        }
+    }
     double c = 0.0;
     double s2pow = 1.0;
     for (int i = 0; i < u; ++i) s2pow *= s2;  // sigma^{2u}
@@ -125,10 +137,10 @@ __global__ void __launch_bounds__(128) pairprep_kernel(PairSetDev ps, const doub
         const int t1 = ps.rec_type[rr.x], t2 = ps.rec_type[rr.y];
         const int l1 = rec_lmax(t1), l2 = rec_lmax(t2);
         // C tables for this monomial: C[ax][a][a2]
-        double C[3][3][3];
+        double C[3][4][4];
         for (int ax = 0; ax < 3; ++ax)
-            for (int a = 0; a <= 2; ++a)
-                for (int a2 = 0; a2 <= 2; ++a2)
+            for (int a = 0; a <= 3; ++a)
+                for (int a2 = 0; a2 <= 3; ++a2)
                     C[ax][a][a2] = (a <= l1 && a2 <= l2) ? c_coef(a, a2, e[ax], PA[ax], PB[ax], s2) : 0.0;
         const int n1 = rec_nfn(t1), n2 = rec_nfn(t2);
         const int f1 = ps.rec_fn0[rr.x], f2 = ps.rec_fn0[rr.y];
@@ -137,7 +149,7 @@ __global__ void __launch_bounds__(128) pairprep_kernel(PairSetDev ps, const doub
         const bool same = (rr.x == rr.y);
         double acc = 0.0;
         for (int i = 0; i < n1; ++i) {
-            const double wi = ps.rec_w[6 * rr.x + i];
+            const double wi = ps.rec_w[kRecW * rr.x + i];
             const int ai = fn_pow(t1, i, 0), bi = fn_pow(t1, i, 1), ci = fn_pow(t1, i, 2);
             for (int j = 0; j < n2; ++j) {
                 const int aj = fn_pow(t2, j, 0), bj = fn_pow(t2, j, 1), cj = fn_pow(t2, j, 2);
@@ -145,7 +157,7 @@ __global__ void __launch_bounds__(128) pairprep_kernel(PairSetDev ps, const doub
                 if (D == 0.0) continue;
                 double tw = Ts[(size_t)(f1 + i) * nbf + (f2 + j)];
                 if (!same) tw += Ts[(size_t)(f2 + j) * nbf + (f1 + i)];
-                acc += tw * wi * ps.rec_w[6 * rr.y + j] * D;
+                acc += tw * wi * ps.rec_w[kRecW * rr.y + j] * D;
             }
         }
         const int n = e[0] + e[1] + e[2];
@@ -220,7 +232,16 @@ struct DirectParams {
     double scale;
     void *f, *f2;
     int *err;
+    int part;  // kPartContinue: start from the raw sums in f; kPartFinal: write scaled f and |f|^2
 };
+
+// Pair classes of degree >= kHighClass (pairs with an f shell) run in a second
+// launch of their own, so that the registers their long unrolled monomial
+// sums need do not lower the occupancy of the common s/p/d classes.  The
+// first launch leaves unscaled sums in f and the second continues from them.
+constexpr int kHighClass = 5;
+constexpr int kPartContinue = 1;
+constexpr int kPartFinal = 2;
 
 // Gaussian x phase factor of one pair at this thread's q point.
 template <typename R, bool LIST>
@@ -296,7 +317,7 @@ template <typename R, int SB> struct Acc {
 
 template <typename R, int SB, int L, bool LIST>
 __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf, int pr0,
-                                              int np, const R (&px)[5], const R (&py)[5], const R (&pz)[5],
+                                              int np, const R (&px)[kMaxPairL + 1], const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1],
                                               int ix, int iy, int iz, double qx, double qy, double qz,
                                               double q2, Acc<R, SB> &acc) {
     constexpr int mL = mono_count(L);
@@ -334,8 +355,8 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
 // false (uniformly across the block) when a wait timed out.
 template <typename R, int SB, int L, bool LIST>
 __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, uint64_t *bars,
-                                          uint32_t &phase, int sblk, const R (&px)[5], const R (&py)[5],
-                                          const R (&pz)[5], int ix, int iy, int iz, double qx, double qy,
+                                          uint32_t &phase, int sblk, const R (&px)[kMaxPairL + 1],
+                                          const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1], int ix, int iy, int iz, double qx, double qy,
                                           double qz, double q2, Acc<R, SB> &acc) {
     constexpr int mL = mono_count(L);
     constexpr int pair_bytes = mL * SB * (int)sizeof(R);
@@ -377,7 +398,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
     return ok;
 }
 
-template <typename R, int SB, bool LIST>
+template <typename R, int SB, bool LIST, bool HIGH>
 __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) {
     __shared__ __align__(128) unsigned char smem[2 * kChunkBytes];
     __shared__ __align__(8) uint64_t bars[2];
@@ -410,41 +431,58 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
         qz = p.qaz[iz];
     }
     const double q2 = qx * qx + qy * qy + qz * qz;
-    R px[5], py[5], pz[5];
+    R px[kMaxPairL + 1], py[kMaxPairL + 1], pz[kMaxPairL + 1];
     px[0] = py[0] = pz[0] = R(1);
 #pragma unroll
-    for (int k = 1; k < 5; ++k) {
+    for (int k = 1; k <= kMaxPairL; ++k) {
         px[k] = px[k - 1] * (R)qx;
         py[k] = py[k - 1] * (R)qy;
         pz[k] = pz[k - 1] * (R)qz;
     }
+    using V = typename Cplx<R>::T;
+    V *f = static_cast<V *>(p.f);
     Acc<R, SB> acc;
     acc.zero();
+    if ((p.part & kPartContinue) && valid) {
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+            const int s = sblk * SB + j;
+            if (s < p.S) {
+                const V v = f[(size_t)s * p.nq + q];
+                if constexpr (sizeof(R) == 4) {
+                    acc.hr[j] = v.x;
+                    acc.hi[j] = v.y;
+                } else {
+                    acc.pr[j] = v.x;
+                    acc.pi[j] = v.y;
+                }
+            }
+        }
+    }
 
     uint32_t phase = 0;
-    bool ok = run_class<R, SB, 0, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy,
-                                        qz, q2, acc);
-    if (ok)
-        ok = run_class<R, SB, 1, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, acc);
-    if (ok)
-        ok = run_class<R, SB, 2, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, acc);
-    if (ok)
-        ok = run_class<R, SB, 3, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, acc);
-    if (ok)
-        ok = run_class<R, SB, 4, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                       q2, acc);
+    bool ok = true;
+    auto run = [&](auto LC) {
+        constexpr int L = decltype(LC)::value;
+        if (ok)
+            ok = run_class<R, SB, L, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy,
+                                           qz, q2, acc);
+    };
+    if constexpr (HIGH) {
+        static_for<kMaxPairL + 1 - kHighClass>([&](auto I) {
+            run(std::integral_constant<int, kHighClass + decltype(I)::value>{});
+        });
+    } else {
+        static_for<kHighClass>([&](auto I) { run(I); });
+    }
     if (!ok) {
         if (threadIdx.x == 0) flag_error(p.err, kDevErrTimeout);
         return;
     }
     if (!valid) return;
-    using V = typename Cplx<R>::T;
-    V *f = static_cast<V *>(p.f);
     R *f2 = static_cast<R *>(p.f2);
-    const R sc = (R)p.scale;
+    const bool final_part = (p.part & kPartFinal) != 0;
+    const R sc = final_part ? (R)p.scale : R(1);
 #pragma unroll
     for (int j = 0; j < SB; ++j) {
         const int s = sblk * SB + j;
@@ -453,13 +491,13 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
             v.x = sc * acc.re(j);
             v.y = sc * acc.im(j);
             f[(size_t)s * p.nq + q] = v;
-            if (f2) f2[(size_t)s * p.nq + q] = v.x * v.x + v.y * v.y;
+            if (f2 && final_part) f2[(size_t)s * p.nq + q] = v.x * v.x + v.y * v.y;
         }
     }
 }
 
 template <typename R, int SB>
-static cudaError_t launch_direct_t(const DirectArgs &a, bool list, cudaStream_t st) {
+static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *launches, cudaStream_t st) {
     DirectParams p;
     p.ps = *a.ps;
     p.coef = a.coef;
@@ -482,10 +520,24 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, cudaStream_t 
     p.err = a.err_flag;
     const int nsb = (a.S + SB - 1) / SB;
     dim3 grid((unsigned)((a.nq + kDirectThreads - 1) / kDirectThreads), (unsigned)nsb);
-    if (list)
-        direct_kernel<R, SB, true><<<grid, kDirectThreads, 0, st>>>(p);
-    else
-        direct_kernel<R, SB, false><<<grid, kDirectThreads, 0, st>>>(p);
+    const bool has_low = a.ps->pair_off[kHighClass] > 0;
+    const bool has_high = a.ps->pair_off[kMaxPairL + 1] > a.ps->pair_off[kHighClass];
+    if (has_low || !has_high) {
+        p.part = has_high ? 0 : kPartFinal;
+        if (list)
+            direct_kernel<R, SB, true, false><<<grid, kDirectThreads, 0, st>>>(p);
+        else
+            direct_kernel<R, SB, false, false><<<grid, kDirectThreads, 0, st>>>(p);
+        if (launches) ++*launches;
+    }
+    if (has_high) {
+        p.part = kPartFinal | (has_low ? kPartContinue : 0);
+        if (list)
+            direct_kernel<R, SB, true, true><<<grid, kDirectThreads, 0, st>>>(p);
+        else
+            direct_kernel<R, SB, false, true><<<grid, kDirectThreads, 0, st>>>(p);
+        if (launches) ++*launches;
+    }
     return cudaGetLastError();
 }
 
@@ -494,18 +546,17 @@ cudaError_t launch_direct(const DirectArgs &a, int fp64, int list_mode, int64_t 
     cudaError_t e;
     if (fp64) {
         if (a.SB != 4) return cudaErrorInvalidValue;
-        e = launch_direct_t<double, 4>(a, list_mode != 0, st);
+        e = launch_direct_t<double, 4>(a, list_mode != 0, launches, st);
     } else {
         if (a.SB == 8)
-            e = launch_direct_t<float, 8>(a, list_mode != 0, st);
+            e = launch_direct_t<float, 8>(a, list_mode != 0, launches, st);
         else if (a.SB == 12)
-            e = launch_direct_t<float, 12>(a, list_mode != 0, st);
+            e = launch_direct_t<float, 12>(a, list_mode != 0, launches, st);
         else if (a.SB == 16)
-            e = launch_direct_t<float, 16>(a, list_mode != 0, st);
+            e = launch_direct_t<float, 16>(a, list_mode != 0, launches, st);
         else
             return cudaErrorInvalidValue;
     }
-    if (launches) ++*launches;
     return e;
 }
 

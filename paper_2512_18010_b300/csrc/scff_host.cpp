@@ -202,7 +202,7 @@ struct HostRec {
     double alpha;
     int type;
     int fn0;
-    double w[6];
+    double w[kRecW];
 };
 
 // (2n-1)!! with (-1)!! = 1
@@ -214,12 +214,8 @@ double dfact_odd(int n) {
 
 // Cartesian exponents of the functions of each record type.
 void type_powers(int type, int j, int pw[3]) {
-    static const int P[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    static const int D[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
-    pw[0] = pw[1] = pw[2] = 0;
-    if (type == REC_P) memcpy(pw, P[j], sizeof(P[j]));
-    else if (type == REC_D) memcpy(pw, D[j], sizeof(D[j]));
-    else if (type == REC_SP && j > 0) memcpy(pw, P[j - 1], sizeof(P[j - 1]));
+    for (int ax = 0; ax < 3; ++ax)
+        pw[ax] = type == REC_SP ? (j == 0 ? 0 : cart_pow(1, j - 1, ax)) : cart_pow(rec_lmax(type), j, ax);
 }
 
 // Unit-norm factor of x^a y^b z^c exp(-alpha r^2):
@@ -266,11 +262,11 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
     const bool renorm = (flags & SCFF_RENORM_CONTRACTED) != 0;
     for (int s = 0; s < n_shells; ++s) {
         const int l = shell_l[s], np = shell_nprim[s], at = shell_atom[s];
-        if (l > 2) return fail(SCFF_ERR_UNSUPPORTED_L, "scff_basis: shell %d has l=%d (Cartesian d is the maximum)", s, l);
+        if (l > 3) return fail(SCFF_ERR_UNSUPPORTED_L, "scff_basis: shell %d has l=%d (Cartesian f is the maximum)", s, l);
         if (l < -1) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d has invalid code %d", s, l);
         if (np < 1 || np > 64) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d has %d primitives", s, np);
         if (at < 0 || at >= n_atoms) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: shell %d on atom %d", s, at);
-        const int type = (l == 0) ? REC_S : (l == 1) ? REC_P : (l == 2) ? REC_D : REC_SP;
+        const int type = (l == 0) ? REC_S : (l == 1) ? REC_P : (l == 2) ? REC_D : (l == 3) ? REC_F : REC_SP;
         const int nf = rec_nfn(type);
         for (int k = 0; k < np; ++k)
             if (!(exps[eoff + k] > 0.0) || !isfinite(exps[eoff + k]))
@@ -302,7 +298,7 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
             r.alpha = exps[eoff + k];
             r.type = type;
             r.fn0 = nbf;
-            for (int j = 0; j < 6; ++j) r.w[j] = j < nf ? w[(size_t)j * np + k] : 0.0;
+            for (int j = 0; j < kRecW; ++j) r.w[j] = j < nf ? w[(size_t)j * np + k] : 0.0;
             recs.push_back(r);
         }
         nbf += nf;
@@ -340,14 +336,14 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
     d.n_rows = d.row_off[kNumClasses];
     d.n_krows = d.krow_off[kNumClasses];
     d.n_axrows = axrows;
-    std::vector<double> rx(3 * (size_t)nrec), ra(nrec), rw(6 * (size_t)nrec);
+    std::vector<double> rx(3 * (size_t)nrec), ra(nrec), rw(kRecW * (size_t)nrec);
     std::vector<int32_t> rt(nrec), rf(nrec);
     for (int i = 0; i < nrec; ++i) {
         for (int k = 0; k < 3; ++k) rx[3 * i + k] = xyz[3 * recs[i].atom + k];
         ra[i] = recs[i].alpha;
         rt[i] = recs[i].type;
         rf[i] = recs[i].fn0;
-        for (int j = 0; j < 6; ++j) rw[6 * i + j] = recs[i].w[j];
+        for (int j = 0; j < kRecW; ++j) rw[kRecW * i + j] = recs[i].w[j];
     }
     scff_status st = SCFF_OK;
     cudaSetDevice(c->device);

@@ -9,8 +9,10 @@
 
 namespace scff {
 
-// Highest total polynomial degree of a pair of primitive shells (d with d).
-constexpr int kMaxPairL = 4;
+// Highest total polynomial degree of a pair of primitive shells (f with f).
+constexpr int kMaxPairL = 6;
+// Cartesian functions of the widest primitive-shell record (f: 10).
+constexpr int kRecW = 10;
 constexpr int kNumClasses = kMaxPairL + 1;
 
 // Number of monomials q_x^u q_y^v q_z^w with u+v+w <= L.
@@ -62,9 +64,23 @@ __host__ __device__ constexpr int mono_index(int u, int v, int w) {
 }
 
 // Record types of a primitive shell.
-enum RecType : int32_t { REC_S = 0, REC_P = 1, REC_D = 2, REC_SP = 3 };
-__host__ __device__ constexpr int rec_nfn(int t) { return t == REC_S ? 1 : t == REC_P ? 3 : t == REC_D ? 6 : 4; }
-__host__ __device__ constexpr int rec_lmax(int t) { return t == REC_S ? 0 : t == REC_D ? 2 : 1; }
+enum RecType : int32_t { REC_S = 0, REC_P = 1, REC_D = 2, REC_SP = 3, REC_F = 4 };
+__host__ __device__ constexpr int rec_nfn(int t) {
+    return t == REC_S ? 1 : t == REC_P ? 3 : t == REC_D ? 6 : t == REC_F ? 10 : 4;
+}
+__host__ __device__ constexpr int rec_lmax(int t) { return t == REC_S ? 0 : t == REC_D ? 2 : t == REC_F ? 3 : 1; }
+
+// Cartesian exponents of component j of a shell of angular momentum l (the
+// order x^l, x^(l-1) y, x^(l-1) z, ...: x power descending, then y).
+__host__ __device__ constexpr int cart_pow(int l, int j, int ax) {
+    int i = 0;
+    for (int a = l; a >= 0; --a)
+        for (int b = l - a; b >= 0; --b) {
+            if (i == j) return ax == 0 ? a : ax == 1 ? b : l - a - b;
+            ++i;
+        }
+    return 0;
+}
 
 // Device view of one basis: primitive-shell records and the pair list sorted
 // by pair class L = lmax(r1) + lmax(r2).
@@ -84,7 +100,7 @@ struct PairSetDev {
     double *rec_alpha = nullptr; // [n_rec]
     int32_t *rec_type = nullptr; // [n_rec]
     int32_t *rec_fn0 = nullptr;  // [n_rec] first function index
-    double *rec_w = nullptr;     // [n_rec][6] normalised weights
+    double *rec_w = nullptr;     // [n_rec][kRecW] normalised weights
     int2 *pair_rec = nullptr;    // [n_pair] (r1, r2), r1 <= r2
 };
 

@@ -52,7 +52,7 @@ constexpr size_t kOffAlpha = kOffXyz + align256(sizeof(double) * 3 * kMaxRecords
 constexpr size_t kOffType = kOffAlpha + align256(sizeof(double) * kMaxRecords);
 constexpr size_t kOffFn0 = kOffType + align256(sizeof(int32_t) * kMaxRecords);
 constexpr size_t kOffW = kOffFn0 + align256(sizeof(int32_t) * kMaxRecords);
-constexpr size_t kOffPairs = kOffW + align256(sizeof(double) * 6 * kMaxRecords);
+constexpr size_t kOffPairs = kOffW + align256(sizeof(double) * kRecW * kMaxRecords);
 constexpr size_t kOffGeom = kOffPairs + align256(sizeof(int2) * kMaxPairs);
 constexpr size_t kOffCoef = kOffGeom + align256(sizeof(double) * 4 * kMaxPairs);
 static_assert(kOffCoef < kScratchBytes, "scratch layout");
@@ -64,7 +64,7 @@ struct HostStage {
     double alpha[kMaxRecords];
     int32_t type[kMaxRecords];
     int32_t fn0[kMaxRecords];
-    double w[6 * kMaxRecords];
+    double w[kRecW * kMaxRecords];
     int2 pairs[kMaxPairs];
     int err;
 };
@@ -106,15 +106,8 @@ double dfact_odd(int n) {
 }
 
 void powers(int type, int j, int pw[3]) {
-    pw[0] = pw[1] = pw[2] = 0;
-    if (type == REC_P) {
-        pw[j] = 1;
-    } else if (type == REC_SP) {
-        if (j > 0) pw[j - 1] = 1;
-    } else if (type == REC_D) {
-        static const int D[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
-        for (int i = 0; i < 3; ++i) pw[i] = D[j][i];
-    }
+    for (int ax = 0; ax < 3; ++ax)
+        pw[ax] = type == REC_SP ? (j == 0 ? 0 : cart_pow(1, j - 1, ax)) : cart_pow(rec_lmax(type), j, ax);
 }
 
 // Unit-norm factor of x^a y^b z^c exp(-alpha r^2).
@@ -157,14 +150,14 @@ extern "C" scff_status scff_form_factor_static(int n_atoms, const double *xyz, i
     size_t eo = 0, co = 0;
     for (int s = 0; s < n_shells; ++s) {
         const int l = shell_l[s], np = shell_nprim[s], at = shell_atom[s];
-        if (l > 2) return err(SCFF_ERR_UNSUPPORTED_L, "scff_form_factor_static: shell %d has l=%d", s, l);
+        if (l > 3) return err(SCFF_ERR_UNSUPPORTED_L, "scff_form_factor_static: shell %d has l=%d", s, l);
         if (l < -1 || np < 1 || np > 64 || at < 0 || at >= n_atoms)
             return err(SCFF_ERR_INVALID_ARG, "scff_form_factor_static: shell %d is invalid", s);
         if (nrec + np > kMaxRecords)
             return err(SCFF_ERR_INVALID_ARG,
                        "scff_form_factor_static: more than %d primitive-shell records (the static scratch limit)",
                        kMaxRecords);
-        const int type = (l == 0) ? REC_S : (l == 1) ? REC_P : (l == 2) ? REC_D : REC_SP;
+        const int type = (l == 0) ? REC_S : (l == 1) ? REC_P : (l == 2) ? REC_D : (l == 3) ? REC_F : REC_SP;
         const int nf = rec_nfn(type);
         for (int k = 0; k < np; ++k)
             if (!(exponents[eo + k] > 0.0) || !isfinite(exponents[eo + k]))
@@ -177,7 +170,7 @@ extern "C" scff_status scff_form_factor_static(int n_atoms, const double *xyz, i
             h.type[r] = type;
             h.fn0[r] = nbf;
         }
-        for (int j = 0; j < 6; ++j) {
+        for (int j = 0; j < kRecW; ++j) {
             int pw[3];
             if (j < nf) powers(type, j, pw);
             const double *c = coefficients + co + ((type == REC_SP && j > 0) ? np : 0);
@@ -185,16 +178,16 @@ extern "C" scff_status scff_form_factor_static(int n_atoms, const double *xyz, i
             for (int k = 0; k < np; ++k) {
                 const double wk = j < nf ? c[k] * prim_norm(exponents[eo + k], pw) : 0.0;
                 if (!isfinite(wk)) return err(SCFF_ERR_INVALID_ARG, "scff_form_factor_static: shell %d coefficient", s);
-                g_host.w[6 * (nrec + k) + j] = wk;
+                g_host.w[kRecW * (nrec + k) + j] = wk;
             }
             if (j < nf && renorm) {
                 for (int k = 0; k < np; ++k)
                     for (int kk = 0; kk < np; ++kk)
-                        ov += g_host.w[6 * (nrec + k) + j] * g_host.w[6 * (nrec + kk) + j] *
+                        ov += g_host.w[kRecW * (nrec + k) + j] * g_host.w[kRecW * (nrec + kk) + j] *
                               self_overlap(exponents[eo + k] + exponents[eo + kk], pw);
                 if (!(ov > 0.0)) return err(SCFF_ERR_INVALID_ARG, "scff_form_factor_static: shell %d has zero norm", s);
                 const double r = 1.0 / sqrt(ov);
-                for (int k = 0; k < np; ++k) g_host.w[6 * (nrec + k) + j] *= r;
+                for (int k = 0; k < np; ++k) g_host.w[kRecW * (nrec + k) + j] *= r;
             }
         }
         nrec += np;
@@ -257,7 +250,7 @@ extern "C" scff_status scff_form_factor_static(int n_atoms, const double *xyz, i
     STATIC_CUDA(cudaMemcpyAsync(ps.rec_alpha, g_host.alpha, sizeof(double) * nrec, cudaMemcpyHostToDevice, st));
     STATIC_CUDA(cudaMemcpyAsync(ps.rec_type, g_host.type, sizeof(int32_t) * nrec, cudaMemcpyHostToDevice, st));
     STATIC_CUDA(cudaMemcpyAsync(ps.rec_fn0, g_host.fn0, sizeof(int32_t) * nrec, cudaMemcpyHostToDevice, st));
-    STATIC_CUDA(cudaMemcpyAsync(ps.rec_w, g_host.w, sizeof(double) * 6 * nrec, cudaMemcpyHostToDevice, st));
+    STATIC_CUDA(cudaMemcpyAsync(ps.rec_w, g_host.w, sizeof(double) * kRecW * nrec, cudaMemcpyHostToDevice, st));
     STATIC_CUDA(cudaMemcpyAsync(ps.pair_rec, g_host.pairs, sizeof(int2) * ps.n_pair, cudaMemcpyHostToDevice, st));
 
     // ---- the same kernels as scff_form_factor (FP64, explicit q list)

@@ -34,7 +34,7 @@ from typing import List, Optional
 import numpy as np
 
 # Cartesian function count per shell code (bookkeeping only).
-NFN = {0: 1, 1: 3, 2: 6, -1: 4}
+NFN = {0: 1, 1: 3, 2: 6, 3: 10, -1: 4}
 
 
 @dataclasses.dataclass
@@ -283,6 +283,39 @@ def molecule_dz_d(seed: int, n_heavy: int, n_h: Optional[int] = None) -> Molecul
     for a in range(n_heavy, n_heavy + n_h):
         _double_zeta_h(sh, a, rng)
     return sh.molecule(f"dz-d-{n_heavy}h-{seed}", xyz, heavy=n_heavy)
+
+
+def molecule_pol_f(seed: int, n_heavy: int, n_h: Optional[int] = None) -> Molecule:
+    """Random connected molecule with double-zeta + d + f on heavy atoms and p on H.
+
+    Heavy atoms carry core s, two sp shells, one Cartesian d (2 primitives) and
+    one Cartesian f (1 primitive): 25 functions; each H carries two s shells
+    and a p polarisation shell: 5 functions.
+    """
+    rng = np.random.default_rng(seed)
+    if n_h is None:
+        n_h = n_heavy
+    heavy, hyd = grow_geometry(rng, n_heavy, n_h)
+    xyz = np.vstack([heavy, hyd]) if len(hyd) else heavy
+    sh = _ShellList()
+    for a in range(n_heavy):
+        sh.add(a, 0, log_uniform(rng, 0.2, 3000.0, 6), rng)
+        sh.add(a, -1, log_uniform(rng, 0.3, 30.0, 3), rng)
+        sh.add(a, -1, log_uniform(rng, 0.08, 0.3, 1), rng)
+        sh.add(a, 2, log_uniform(rng, 0.4, 2.5, 2), rng)
+        sh.add(a, 3, log_uniform(rng, 0.5, 1.5, 1), rng)
+    for a in range(n_heavy, n_heavy + n_h):
+        _double_zeta_h(sh, a, rng)
+        sh.add(a, 1, log_uniform(rng, 0.5, 1.2, 1), rng)
+    return sh.molecule(f"pol-f-{n_heavy}h-{seed}", xyz, heavy=n_heavy)
+
+
+def config_f(seed: int = 3500, n_heavy: int = 4, n_states: int = 6, n: int = 48) -> Job:
+    """f-shell workload: 4 heavy + 4 H with d and f polarisation (120 functions), 48^3 on [-15,15]."""
+    mol = molecule_pol_f(seed, n_heavy)
+    T = transition_matrices(seed, n_states, mol.nbf)
+    ax = axis(n, 15.0)
+    return Job(mol, T, ax, ax.copy(), ax.copy(), seed)
 
 
 def config3(seed: int = 3000, n: int = 128) -> Job:

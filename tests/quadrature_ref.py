@@ -17,6 +17,8 @@ _COMP = {
     0: [(0, 0, 0)],
     1: [(1, 0, 0), (0, 1, 0), (0, 0, 1)],
     2: [(2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)],
+    3: [(3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2),
+        (0, 3, 0), (0, 2, 1), (0, 1, 2), (0, 0, 3)],
     -1: [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)],
 }
 

@@ -135,7 +135,7 @@ def test_scale_and_device_outputs(ctx):
 def test_invalid_inputs_are_rejected(ctx):
     job = W.config1()
     m = job.mol
-    bad = W.Molecule(**{**m.__dict__, "shell_l": np.where(m.shell_l == 2, 3, m.shell_l).astype(np.int32)})
+    bad = W.Molecule(**{**m.__dict__, "shell_l": np.where(m.shell_l == 2, 4, m.shell_l).astype(np.int32)})
     with pytest.raises(scff.ScffError) as e:
         ctx.basis(bad)
     assert e.value.code == 2  # UNSUPPORTED_L
@@ -148,3 +148,43 @@ def test_invalid_inputs_are_rejected(ctx):
         ctx.transitions(b, np.zeros((1, 3, 3)))
     with pytest.raises(scff.ScffError):
         ctx.qgrid_product([], [0.0], [0.0])
+
+
+# ---------------------------------------------------------------- Cartesian f shells
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32] + TC)
+def test_f_shells_grid_sampled(ctx, prec):
+    # d and f polarisation on heavy atoms, p on H: pair classes up to degree 6.
+    job = W.config_f()
+    f, f2 = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 1500, 3501)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+    assert np.allclose(f2, np.abs(f) ** 2, rtol=1e-5 if prec else 1e-12, atol=1e-30)
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32])
+def test_f_shells_list_path(ctx, prec):
+    job = W.config_f(n_heavy=2, n_states=5)
+    rng = np.random.default_rng(35)
+    q = np.vstack([np.zeros((1, 3)), rng.uniform(-10, 10, size=(257, 3))])
+    f, _ = scff.evaluate_job(ctx, job, precision=prec, q_list=q)
+    ref = oracle.form_factor(job.mol, job.T, q)
+    assert rel_err(f, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+def test_f_only_basis(ctx, prec):
+    # Every pair has degree 6: only the f-pair classes run.
+    rng = np.random.default_rng(36)
+    xyz = rng.uniform(-1.2, 1.2, size=(2, 3))
+    mol = W.Molecule(name="f-only", xyz=xyz, shell_atom=np.array([0, 1], np.int32),
+                     shell_l=np.array([3, 3], np.int32), shell_nprim=np.array([2, 1], np.int32),
+                     exponents=np.array([1.3, 0.45, 0.8]), coefficients=rng.standard_normal(3), heavy=2)
+    T = W.transition_matrices(36, 3, mol.nbf)
+    ax = W.axis(24, 9.0)
+    job = W.Job(mol, T, ax, W.axis(19, 7.0), W.axis(33, 10.0), 36)
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 800, 37)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]

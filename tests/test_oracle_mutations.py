@@ -35,6 +35,8 @@ MUTATIONS = {
     "d_component_order": ("{1, 1, 0}, {1, 0, 1},\n                                 {0, 2, 0}",
                           "{1, 0, 1}, {1, 1, 0},\n                                 {0, 2, 0}"),
     "binomial_power": ("ea[i] = C[a][i] * pow(u, a - i);", "ea[i] = C[a][i] * pow(u, i);"),
+    "f_component_order": ("{{3, 0, 0}, {2, 1, 0}, {2, 0, 1}", "{{3, 0, 0}, {2, 0, 1}, {2, 1, 0}"),
+    "cubic_binomial": ("{1, 2, 1, 0}, {1, 3, 3, 1}}", "{1, 2, 1, 0}, {1, 2, 2, 1}}"),
 }
 
 
@@ -98,6 +100,10 @@ def pins_pass(lib):
                  [(0, -1, [3.1, 0.7], rng.standard_normal(4)), (1, 0, [0.4], [1.0])])
     Tsp = rng.standard_normal((1, msp.nbf, msp.nbf))
     ok.append(rel(ff(lib, msp, Tsp, qq), Q.form_factor(msp, Tsp, qq)) < 1e-10)
+    # f shells: one f primitive on each of two centres, every component pair
+    mf = mol_of(rng.uniform(-1.5, 1.5, size=(2, 3)), [(0, 3, [1.1], [1.0]), (1, 3, [0.6], [1.0])])
+    Tf = rng.standard_normal((1, 20, 20))
+    ok.append(rel(ff(lib, mf, Tf, qq), Q.form_factor(mf, Tf, qq)) < 1e-10)
     return all(ok)
 
 

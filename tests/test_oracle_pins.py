@@ -51,7 +51,8 @@ def test_pz_normalisation_matches_paper(alpha):
     assert oracle.prim_norm(alpha, 0, 0, 1) == pytest.approx(expected, rel=1e-14)
 
 
-@pytest.mark.parametrize("pw", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (1, 1, 0), (0, 1, 1)])
+@pytest.mark.parametrize("pw", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (1, 1, 0), (0, 1, 1),
+                                (3, 0, 0), (2, 0, 1), (1, 1, 1)])
 def test_primitive_normalisation_textbook(pw):
     for alpha in (0.1, 1.7, 250.0):
         assert oracle.prim_norm(alpha, *pw) == pytest.approx(prim_norm_textbook(alpha, *pw), rel=1e-13)
@@ -136,6 +137,40 @@ def test_p_and_d_from_centre_derivatives():
     assert rel_err(f, exp) < 1e-12
 
 
+def test_f_from_centre_derivatives():
+    # Three A_x-derivatives of g = exp(-a (x-A_x)^2) give
+    # (x-A_x)^3 g = g^(3)/(8a^3) + 3 g^(1)/(4a^2); with d(log I)/dA = c1 and
+    # d^2(log I)/dA_x^2 = c2 = -2ab/p the s-s integral gives I^(3) = (c1^3 + 3 c1 c2) I.
+    A, B = np.array([0.4, 0.2, -0.6]), np.array([-0.5, 0.9, 0.7])
+    a, b = 0.7, 1.3
+    q = np.random.default_rng(12).uniform(-6, 6, size=(30, 3))
+    I, p = _gpt(a, A, b, B, q)
+    c1 = -2 * a * b * (A - B)[None, :] / p + 1j * q * a / p
+    c2 = -2 * a * b / p
+    Ns = prim_norm_textbook(b, 0, 0, 0)
+    mol = mol_of(np.vstack([A, B]), [(0, 3, [a], [1.0]), (1, 0, [b], [1.0])])
+
+    def f_of(i):
+        T = np.zeros((1, 11, 11))
+        T[0, i, 10] = 1.0
+        return oracle.form_factor(mol, T, q)[0]
+
+    cx, cy, cz = c1[:, 0], c1[:, 1], c1[:, 2]
+    # xxx (index 0)
+    exp = (prim_norm_textbook(a, 3, 0, 0) * Ns * I *
+           ((cx ** 3 + 3 * cx * c2) / (8 * a ** 3) + 3 * cx / (4 * a * a)))
+    assert rel_err(f_of(0), exp) < 1e-12
+    # xxy (index 1): (x-A_x)^2 from two derivatives, (y-A_y) from one
+    exp = prim_norm_textbook(a, 2, 1, 0) * Ns * I * (cx ** 2 + c2 + 2 * a) * cy / (8 * a ** 3)
+    assert rel_err(f_of(1), exp) < 1e-12
+    # xyz (index 4)
+    exp = prim_norm_textbook(a, 1, 1, 1) * Ns * I * cx * cy * cz / (8 * a ** 3)
+    assert rel_err(f_of(4), exp) < 1e-12
+    # yzz (index 8)
+    exp = prim_norm_textbook(a, 0, 1, 2) * Ns * I * cy * (cz ** 2 + c2 + 2 * a) / (8 * a ** 3)
+    assert rel_err(f_of(8), exp) < 1e-12
+
+
 # ---------------------------------------------------------------- brute force
 
 def test_config1_against_quadrature():
@@ -155,6 +190,22 @@ def test_sp_shells_against_quadrature():
     nbf = mol.nbf
     T = rng.standard_normal((2, nbf, nbf))
     q = rng.uniform(-7, 7, size=(6, 3))
+    assert rel_err(oracle.form_factor(mol, T, q), Q.form_factor(mol, T, q)) < 1e-11
+
+
+def test_f_shells_against_quadrature():
+    # f on two centres (pair degree up to 6) plus d, sp and p partners, contracted.
+    rng = np.random.default_rng(13)
+    xyz = rng.uniform(-1.5, 1.5, size=(3, 3))
+    mol = mol_of(xyz, [(0, 3, [1.4, 0.5], rng.standard_normal(2)),
+                       (1, 3, [0.9], [1.0]),
+                       (1, 2, [0.6, 2.2], rng.standard_normal(2)),
+                       (2, -1, [2.5, 0.4], rng.standard_normal(4)),
+                       (2, 1, [0.8], [1.0])])
+    nbf = mol.nbf
+    assert nbf == 10 + 10 + 6 + 4 + 3
+    T = rng.standard_normal((2, nbf, nbf))
+    q = np.vstack([np.zeros(3), rng.uniform(-7, 7, size=(6, 3))])
     assert rel_err(oracle.form_factor(mol, T, q), Q.form_factor(mol, T, q)) < 1e-11
 
 
@@ -260,6 +311,53 @@ def test_rotation_covariance():
     assert rel_err(g, f) < 1e-11
 
 
+def _monomials(l):
+    """Cartesian exponents of degree l, descending x power then descending y power."""
+    return [(a, b, l - a - b) for a in range(l, -1, -1) for b in range(l - a, -1, -1)]
+
+
+def _rotation_map_lsq(mol, R):
+    """Same map as _rotation_map, found numerically for any shell.
+
+    m_i(R^T x) = sum_j M[j, i] m_j(x) is solved by least squares on random
+    points (exact: both sides are homogeneous of the same degree); the
+    primitive normalisation ratio N_i / N_j = prod Gamma(a_j + 1/2)^(1/2) /
+    prod Gamma(a_i + 1/2)^(1/2) does not depend on the exponent.
+    """
+    from math import gamma
+    x = np.random.default_rng(99).standard_normal((64, 3))
+    blocks = []
+    for l in mol.shell_l:
+        l = int(l)
+        comps = [(0, 0, 0)] + _monomials(1) if l == -1 else _monomials(l)
+        V = np.array([[np.prod(xx ** np.array(c)) for c in comps] for xx in x])
+        Y = np.array([[np.prod((R.T @ xx) ** np.array(c)) for c in comps] for xx in x])
+        M = np.linalg.lstsq(V, Y, rcond=None)[0]
+        N = np.array([np.prod([gamma(e + 0.5) for e in c]) ** -0.5 for c in comps])
+        blocks.append(M * N[None, :] / N[:, None])
+    n = sum(b.shape[0] for b in blocks)
+    G = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        m = b.shape[0]
+        G[o:o + m, o:o + m] = b
+        o += m
+    return G
+
+
+def test_rotation_covariance_f_shells():
+    job = W.config_f(n_heavy=2, n_states=2, n=8)
+    R = W.random_rotation(np.random.default_rng(17))
+    assert np.allclose(_rotation_map_lsq(W.config1().mol, R), _rotation_map(W.config1().mol, R), atol=1e-12)
+    mol2 = W.Molecule(**{**job.mol.__dict__, "xyz": job.mol.xyz @ R.T})
+    G = _rotation_map_lsq(job.mol, R)
+    T2 = np.einsum("ji,sik,lk->sjl", G, job.T, G)
+    q = np.random.default_rng(18).uniform(-8, 8, size=(30, 3))
+    f = oracle.form_factor(job.mol, job.T, q)
+    g = oracle.form_factor(mol2, T2, q @ R.T)
+    assert rel_err(g, f) < 1e-11
+
+
 def test_antisymmetric_T_gives_zero():
     job = W.config1()
     A = job.T - np.transpose(job.T, (0, 2, 1))
@@ -274,7 +372,8 @@ def test_inversion_parity():
     rng = np.random.default_rng(10)
     A = rng.uniform(-1.5, 1.5, size=(2, 3))
     xyz = np.vstack([A, -A])
-    base = [(0, 0, [2.0, 0.5]), (0, -1, [1.1, 0.3]), (0, 2, [0.8]), (1, 0, [0.9, 0.2])]
+    base = [(0, 0, [2.0, 0.5]), (0, -1, [1.1, 0.3]), (0, 2, [0.8]), (1, 0, [0.9, 0.2]),
+            (1, 3, [0.7])]
     shells = []
     coefs = [rng.standard_normal(len(e) * (2 if l == -1 else 1)) for (_, l, e) in base]
     for partner in (0, 2):
@@ -285,7 +384,7 @@ def test_inversion_parity():
     half = n // 2
     sign = []
     for (_, l, _) in base:
-        sign += {0: [1], -1: [1, -1, -1, -1], 2: [1] * 6, 1: [-1] * 3}[l]
+        sign += {0: [1], -1: [1, -1, -1, -1], 2: [1] * 6, 1: [-1] * 3, 3: [-1] * 10}[l]
     P = np.zeros((n, n))
     for i in range(half):
         P[half + i, i] = sign[i]
