@@ -45,6 +45,32 @@ SM_MAX_MHZ = 2032.0
 TF32_PER_BF16 = 0.5   # dense TF32 / dense BF16 tensor rate (nominal 1.1 vs 2.25 PFLOP/s)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one q-evaluation
+# launch, from one ncu capture of the default workload (see profiles/); valid
+# only while the kernel sources hash to the value recorded with it.
+TC_SOURCES = ["kernels_tc.cu", "tc_internal.h", "device_common.cuh", "scff_internal.h"]
+MEASURED_TRAFFIC = {
+    ("cfg3", "bf16x3"): {"bytes": 1566491136 + 301608448, "src": "50d902831263e9a9",
+                         "profile": "profiles/tc_bf16x3_cfg3_launches.md"},
+}
+
+
+def tc_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2512_18010_b300", "csrc", name), "rb") as f:
+            h.update(hashlib.sha256(f.read()).hexdigest().encode())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, precision: str):
+    rec = MEASURED_TRAFFIC.get((workload, precision))
+    if rec is None or rec["src"] != tc_source_hash():
+        return None
+    return rec
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,8 +442,10 @@ def main():
         bf16 = float(peaks.get("bf16_tflops", 1800.0))
         peak = bf16 * (TF32_PER_BF16 if prec == scff.TF32X3 else 1.0)
         achieved = tc_flops * units / (kern_ms / 1e3) / 1e12
+        trec = measured_traffic(args.workload, args.precision)
         roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "work": f"{tc_flops} tensor flop per (q*state) = 8 flop x {Kvw} (pair,v,w) rows x {passes} split "
                         f"products; direct-form algorithmic work is {direct_flops} flop per (q*state)",
                 "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio 0.5"

@@ -76,6 +76,8 @@ typedef enum {
 
 /* scff_basis flags */
 #define SCFF_RENORM_CONTRACTED 1u /* rescale each contracted function to <phi|phi> = 1 */
+#define SCFF_PURE_D 2u /* d shells are the 5 spherical-harmonic (pure) functions */
+#define SCFF_PURE_F 4u /* f shells are the 7 spherical-harmonic (pure) functions */
 
 typedef struct scff_ctx scff_ctx;
 typedef struct scff_basis_s *scff_basis_h;
@@ -111,7 +113,19 @@ const char *scff_last_error(void);
  * xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz; an sp shell gives s,px,py,pz.  Each primitive
  * Cartesian term is normalised to unit norm; with SCFF_RENORM_CONTRACTED the
  * contracted function is then rescaled to unit norm as well.
- * On success *out is a new handle and *nbf_out the function count.
+ *
+ * Pure shells (Appendix A, Eq. defprimitive with several Cartesian terms k_i):
+ * with SCFF_PURE_D (SCFF_PURE_F) every d (f) shell gives the 2l+1 real solid
+ * harmonics, ordered m = -l..l, as these polynomials times the Gaussian:
+ *   d: xy, yz, 2z^2-x^2-y^2, xz, x^2-y^2
+ *   f: 3x^2y-y^3, xyz, 4yz^2-x^2y-y^3, 2z^3-3x^2z-3y^2z, 4xz^2-x^3-xy^2,
+ *      x^2z-y^2z, x^3-3xy^2
+ * and each primitive (the whole polynomial) is normalised to unit norm.
+ * T is then given in this basis; the library expands it to the Cartesian
+ * components internally (the form factor is bilinear in the functions), so
+ * the cost per q point is that of the Cartesian shell.
+ * On success *out is a new handle and *nbf_out the function count (pure
+ * shells counted with 2l+1 functions).
  */
 scff_status scff_basis(scff_ctx *ctx, int n_atoms, const double *xyz, int n_shells,
                        const int32_t *shell_atom, const int32_t *shell_l,
@@ -337,7 +351,8 @@ int64_t scff_kernel_launches(scff_ctx *ctx);
  * loaded the library until the process exits; host staging uses static
  * storage.  On success the call allocates nothing: no cudaMalloc, cudaFree
  * or other allocating routine (a rejected call stores its message for
- * scff_last_error()).
+ * scff_last_error()).  Only Cartesian shells: flags may hold
+ * SCFF_RENORM_CONTRACTED alone; pure-shell flags return SCFF_ERR_INVALID_ARG.
  *
  * Limits: at most 256 primitive-shell records (one per primitive of every
  * shell) and n_states x coefficient rows within the scratch (about 3.9 M FP64

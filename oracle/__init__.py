@@ -52,7 +52,7 @@ def _load():
         lib.scff_oracle_functions.restype = ctypes.c_int
         lib.scff_oracle_prim_norm.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.scff_oracle_prim_norm.restype = ctypes.c_double
-        lib.scff_oracle_nbf.argtypes = [ctypes.c_int, P]
+        lib.scff_oracle_nbf.argtypes = [ctypes.c_int, P, ctypes.c_int]
         lib.scff_oracle_nbf.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -64,6 +64,14 @@ def _c(a, dtype):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# flag bits of the C entry points (same meaning as the library's basis flags)
+RENORM, PURE_D, PURE_F = 1, 2, 4
+
+
+def _flags(mol, renorm: bool) -> int:
+    return (RENORM if renorm else 0) | (int(getattr(mol, "pure", 0)) & (PURE_D | PURE_F))
 
 
 def form_factor(mol, T: np.ndarray, q: np.ndarray, scale: float = 1.0,
@@ -80,7 +88,7 @@ def form_factor(mol, T: np.ndarray, q: np.ndarray, scale: float = 1.0,
     S = T.shape[0]
     out = np.zeros((S, q.shape[0], 2), dtype=np.float64)
     rc = lib.scff_oracle_form_factor(mol.n_atoms, _ptr(xyz), mol.n_shells, _ptr(sa), _ptr(sl),
-                                     _ptr(sn), _ptr(ex), _ptr(co), int(renorm), S, _ptr(T),
+                                     _ptr(sn), _ptr(ex), _ptr(co), _flags(mol, renorm), S, _ptr(T),
                                      q.shape[0], _ptr(q), float(scale), _ptr(out), int(threads))
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
@@ -88,14 +96,16 @@ def form_factor(mol, T: np.ndarray, q: np.ndarray, scale: float = 1.0,
 
 
 def functions(mol, renorm: bool = True):
-    """Function table: (atom[nbf], powers[nbf,3], list of (alpha[k], weight[k]))."""
+    """Function table of a Cartesian basis: (atom[nbf], powers[nbf,3], list of (alpha[k], weight[k]))."""
+    if _flags(mol, False):
+        raise ValueError("functions() describes Cartesian shells only")
     lib = _load()
     sa, sl, sn = _c(mol.shell_atom, np.int32), _c(mol.shell_l, np.int32), _c(mol.shell_nprim, np.int32)
     ex, co = _c(mol.exponents, np.float64), _c(mol.coefficients, np.float64)
-    nbf = lib.scff_oracle_nbf(mol.n_shells, _ptr(sl))
+    nbf = lib.scff_oracle_nbf(mol.n_shells, _ptr(sl), 0)
     if nbf <= 0:
         raise ValueError("bad shell codes")
-    maxp = int(np.sum(np.asarray(mol.shell_nprim)) * 6 + 6)
+    maxp = int(np.sum(10 * np.asarray(mol.shell_nprim, dtype=np.int64))) + 1
     atom = np.zeros(nbf, np.int32)
     pw = np.zeros((nbf, 3), np.int32)
     npr = np.zeros(nbf, np.int32)

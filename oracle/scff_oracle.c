@@ -38,6 +38,16 @@
  * ordered by descending x power, then descending y power (x,y,z;
  * xx,xy,xz,yy,yz,zz; xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz); an sp shell
  * gives s,px,py,pz and stores its s coefficients before its p coefficients.
+ *
+ * Pure (spherical-harmonic) d and f shells (flag bits ORACLE_PURE_D and
+ * ORACLE_PURE_F) follow Appendix A, Eq. defprimitive: each primitive is a sum
+ * of Cartesian terms k_i x^a y^b z^c with one normalisation constant N for the
+ * whole sum, N^-2 = sum_ij k_i k_j prod_axes Int x^(a_i+a_j) exp(-x^2/sigma^2) dx
+ * (the printed double sum; terms with an odd exponent sum vanish).  The 2l+1
+ * functions are the real solid harmonics, ordered m = -l..l:
+ *   d: xy, yz, 2z^2-x^2-y^2, xz, x^2-y^2
+ *   f: 3x^2y-y^3, xyz, 4yz^2-x^2y-y^3, 2z^3-3x^2z-3y^2z, 4xz^2-x^3-xy^2,
+ *      x^2z-y^2z, x^3-3xy^2
  */
 #include <complex.h>
 #include <math.h>
@@ -52,15 +62,52 @@
 #define ORACLE_EINVAL -1
 #define ORACLE_ENOMEM -2
 
+#define ORACLE_RENORM 1
+#define ORACLE_PURE_D 2
+#define ORACLE_PURE_F 4
+
+#define MAX_TERMS 3
+
 typedef struct {
     int atom;
-    int pw[3];
+    int nterm;              /* Cartesian terms of the angular factor */
+    int pw[MAX_TERMS][3];   /* their exponents */
+    double k[MAX_TERMS];    /* their coefficients k_i */
     int nprim;
-    const double *alpha; /* nprim exponents */
-    double *w;           /* nprim normalised weights c_k N_k R */
+    const double *alpha;    /* nprim exponents */
+    double *w;              /* nprim normalised weights c_k N_k R */
 } ofn_t;
 
-static int nfn_of(int l) {
+typedef struct {
+    int nterm;
+    int pw[MAX_TERMS][3];
+    double k[MAX_TERMS];
+} pure_t;
+
+/* Real solid harmonics, m = -l..l (unnormalised polynomials). */
+static const pure_t PURE_D[5] = {
+    {1, {{1, 1, 0}}, {1.0}},
+    {1, {{0, 1, 1}}, {1.0}},
+    {3, {{0, 0, 2}, {2, 0, 0}, {0, 2, 0}}, {2.0, -1.0, -1.0}},
+    {1, {{1, 0, 1}}, {1.0}},
+    {2, {{2, 0, 0}, {0, 2, 0}}, {1.0, -1.0}},
+};
+static const pure_t PURE_F[7] = {
+    {2, {{2, 1, 0}, {0, 3, 0}}, {3.0, -1.0}},
+    {1, {{1, 1, 1}}, {1.0}},
+    {3, {{0, 1, 2}, {2, 1, 0}, {0, 3, 0}}, {4.0, -1.0, -1.0}},
+    {3, {{0, 0, 3}, {2, 0, 1}, {0, 2, 1}}, {2.0, -3.0, -3.0}},
+    {3, {{1, 0, 2}, {3, 0, 0}, {1, 2, 0}}, {4.0, -1.0, -1.0}},
+    {2, {{2, 0, 1}, {0, 2, 1}}, {1.0, -1.0}},
+    {2, {{3, 0, 0}, {1, 2, 0}}, {1.0, -3.0}},
+};
+
+static int is_pure(int l, int flags) {
+    return (l == 2 && (flags & ORACLE_PURE_D)) || (l == 3 && (flags & ORACLE_PURE_F));
+}
+
+static int nfn_of(int l, int flags) {
+    if (is_pure(l, flags)) return 2 * l + 1;
     switch (l) {
     case 0: return 1;
     case 1: return 3;
@@ -96,15 +143,43 @@ double scff_oracle_prim_norm(double alpha, int a, int b, int c) {
     return 1.0 / sqrt(prod);
 }
 
+/* Appendix A normalisation of a primitive whose angular factor is the sum of
+ * Cartesian terms k_i x^a_i y^b_i z^c_i:
+ * N = [ sum_ij k_i k_j prod_axes sigma^{1+n} Gamma((n+1)/2) ]^{-1/2} with n the
+ * axis exponent sum of terms i and j; odd n contributes zero. */
+static double multi_term_norm(double alpha, int nterm, const int pw[][3], const double *k) {
+    const double sigma = 1.0 / sqrt(2.0 * alpha);
+    double sum = 0.0;
+    for (int i = 0; i < nterm; ++i)
+        for (int j = 0; j < nterm; ++j) {
+            double prod = k[i] * k[j];
+            for (int ax = 0; ax < 3; ++ax) {
+                const int n = pw[i][ax] + pw[j][ax];
+                if (n & 1) {
+                    prod = 0.0;
+                    break;
+                }
+                prod *= pow(sigma, 1.0 + n) * tgamma(0.5 * (n + 1));
+            }
+            sum += prod;
+        }
+    return 1.0 / sqrt(sum);
+}
+
 /* Int x^{2a} exp(-p x^2) dx = Gamma(a + 1/2) / p^{a + 1/2}. */
 static double even_moment(int a, double p) {
     return tgamma(a + 0.5) / pow(p, a + 0.5);
 }
 
-int scff_oracle_nbf(int n_shells, const int32_t *shell_l) {
+/* Int x^n exp(-p x^2) dx for any n >= 0 (zero for odd n). */
+static double moment(int n, double p) {
+    return (n & 1) ? 0.0 : even_moment(n / 2, p);
+}
+
+int scff_oracle_nbf(int n_shells, const int32_t *shell_l, int flags) {
     int nbf = 0;
     for (int s = 0; s < n_shells; ++s) {
-        int n = nfn_of(shell_l[s]);
+        int n = nfn_of(shell_l[s], flags);
         if (n < 0) return ORACLE_EINVAL;
         nbf += n;
     }
@@ -114,9 +189,10 @@ int scff_oracle_nbf(int n_shells, const int32_t *shell_l) {
 /* Builds the function table; caller frees fns[i].w and fns. */
 static int build_functions(int n_atoms, int n_shells, const int32_t *shell_atom,
                            const int32_t *shell_l, const int32_t *shell_nprim,
-                           const double *exps, const double *coefs, int renorm,
+                           const double *exps, const double *coefs, int flags,
                            ofn_t **out, int *nbf_out) {
-    int nbf = scff_oracle_nbf(n_shells, shell_l);
+    const int renorm = flags & ORACLE_RENORM;
+    int nbf = scff_oracle_nbf(n_shells, shell_l, flags);
     if (nbf <= 0) return ORACLE_EINVAL;
     ofn_t *fns = (ofn_t *)calloc((size_t)nbf, sizeof(ofn_t));
     if (!fns) return ORACLE_ENOMEM;
@@ -129,25 +205,42 @@ static int build_functions(int n_atoms, int n_shells, const int32_t *shell_atom,
             free(fns);
             return ORACLE_EINVAL;
         }
-        const int nf = nfn_of(l);
+        const int nf = nfn_of(l, flags);
+        const int pure = is_pure(l, flags);
         for (int i = 0; i < nf; ++i, ++f) {
             ofn_t *fn = &fns[f];
             fn->atom = shell_atom[s];
-            powers_of(l, i, fn->pw);
+            if (pure) {
+                const pure_t *h = (l == 2) ? &PURE_D[i] : &PURE_F[i];
+                fn->nterm = h->nterm;
+                memcpy(fn->pw, h->pw, sizeof(fn->pw));
+                memcpy(fn->k, h->k, sizeof(fn->k));
+            } else {
+                fn->nterm = 1;
+                powers_of(l, i, fn->pw[0]);
+                fn->k[0] = 1.0;
+            }
             fn->nprim = np;
             fn->alpha = exps + eoff;
             fn->w = (double *)malloc(sizeof(double) * (size_t)np);
             const double *c = coefs + coff + ((l == -1 && i > 0) ? (size_t)np : 0);
             for (int k = 0; k < np; ++k)
-                fn->w[k] = c[k] * scff_oracle_prim_norm(fn->alpha[k], fn->pw[0], fn->pw[1], fn->pw[2]);
+                fn->w[k] = c[k] * (pure ? multi_term_norm(fn->alpha[k], fn->nterm, fn->pw, fn->k)
+                                        : scff_oracle_prim_norm(fn->alpha[k], fn->pw[0][0], fn->pw[0][1],
+                                                                fn->pw[0][2]));
             if (renorm) {
-                /* <phi|phi> = sum_kk' w_k w_k' prod_axes Int x^{2a} e^{-(a_k+a_k') x^2} */
+                /* <phi|phi> = sum_kk' w_k w_k' sum_ij k_i k_j prod_axes Int x^(a_i+a_j) e^{-(a_k+a_k') x^2} */
                 double nrm = 0.0;
                 for (int k = 0; k < np; ++k)
                     for (int kk = 0; kk < np; ++kk) {
                         const double p = fn->alpha[k] + fn->alpha[kk];
-                        nrm += fn->w[k] * fn->w[kk] * even_moment(fn->pw[0], p) *
-                               even_moment(fn->pw[1], p) * even_moment(fn->pw[2], p);
+                        double ang = 0.0;
+                        for (int ti = 0; ti < fn->nterm; ++ti)
+                            for (int tj = 0; tj < fn->nterm; ++tj)
+                                ang += fn->k[ti] * fn->k[tj] * moment(fn->pw[ti][0] + fn->pw[tj][0], p) *
+                                       moment(fn->pw[ti][1] + fn->pw[tj][1], p) *
+                                       moment(fn->pw[ti][2] + fn->pw[tj][2], p);
+                        nrm += fn->w[k] * fn->w[kk] * ang;
                     }
                 const double r = 1.0 / sqrt(nrm);
                 for (int k = 0; k < np; ++k) fn->w[k] *= r;
@@ -203,16 +296,23 @@ static double complex pair_integral(const ofn_t *m, const ofn_t *n, const double
             const double p = al + be;
             const double K = exp(-al * be * AB2 / p);
             double P[3];
-            double complex prod = 1.0;
             double phase = 0.0;
             for (int i = 0; i < 3; ++i) {
                 P[i] = (al * A[i] + be * B[i]) / p;
-                double e[7];
-                const int tmax = binomial_product(m->pw[i], P[i] - A[i], n->pw[i], P[i] - B[i], e);
-                prod *= axis_factor(e, tmax, p, q[i]);
                 phase += q[i] * P[i];
             }
-            total += m->w[k] * n->w[kk] * K * prod * cexp(I * phase);
+            double complex ang = 0.0;
+            for (int ti = 0; ti < m->nterm; ++ti)
+                for (int tj = 0; tj < n->nterm; ++tj) {
+                    double complex prod = m->k[ti] * n->k[tj];
+                    for (int i = 0; i < 3; ++i) {
+                        double e[7];
+                        const int tmax = binomial_product(m->pw[ti][i], P[i] - A[i], n->pw[tj][i], P[i] - B[i], e);
+                        prod *= axis_factor(e, tmax, p, q[i]);
+                    }
+                    ang += prod;
+                }
+            total += m->w[k] * n->w[kk] * K * ang * cexp(I * phase);
         }
     }
     return total;
@@ -220,12 +320,13 @@ static double complex pair_integral(const ofn_t *m, const ofn_t *n, const double
 
 /*
  * f_out[s][iq][0..1] = Re, Im of f_s(q_iq).  T is [n_states][nbf][nbf]
- * row-major; q is [n_q][3].  Returns 0 or a negative error code.
+ * row-major; q is [n_q][3]; flags = ORACLE_RENORM | ORACLE_PURE_D | ORACLE_PURE_F.
+ * Returns 0 or a negative error code.
  */
 int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
                             const int32_t *shell_atom, const int32_t *shell_l,
                             const int32_t *shell_nprim, const double *exps,
-                            const double *coefs, int renorm, int n_states,
+                            const double *coefs, int flags, int n_states,
                             const double *T, int64_t n_q, const double *q,
                             double scale, double *f_out, int n_threads) {
     if (n_atoms <= 0 || n_shells <= 0 || n_states <= 0 || n_q < 0 || !xyz || !T || !f_out)
@@ -233,7 +334,7 @@ int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
     ofn_t *fns = NULL;
     int nbf = 0;
     int rc = build_functions(n_atoms, n_shells, shell_atom, shell_l, shell_nprim, exps,
-                             coefs, renorm, &fns, &nbf);
+                             coefs, flags, &fns, &nbf);
     if (rc) return rc;
     const size_t nn = (size_t)nbf * nbf;
 #ifdef _OPENMP
@@ -279,24 +380,26 @@ int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
 }
 
 /*
- * Function table for tests: per function its atom, Cartesian exponents and
+ * Function table for tests (Cartesian shells only: flags may hold
+ * ORACLE_RENORM alone): per function its atom, Cartesian exponents and
  * normalised primitive weights (w_out holds sum_k nprim entries in function
  * order; nprim_out[f] gives the count).  Returns nbf or a negative code.
  */
 int scff_oracle_functions(int n_atoms, int n_shells, const int32_t *shell_atom,
                           const int32_t *shell_l, const int32_t *shell_nprim,
-                          const double *exps, const double *coefs, int renorm,
+                          const double *exps, const double *coefs, int flags,
                           int32_t *atom_out, int32_t *pw_out, int32_t *nprim_out,
                           double *alpha_out, double *w_out) {
+    if (flags & ~ORACLE_RENORM) return ORACLE_EINVAL;
     ofn_t *fns = NULL;
     int nbf = 0;
     int rc = build_functions(n_atoms, n_shells, shell_atom, shell_l, shell_nprim, exps,
-                             coefs, renorm, &fns, &nbf);
+                             coefs, flags, &fns, &nbf);
     if (rc) return rc;
     size_t o = 0;
     for (int f = 0; f < nbf; ++f) {
         atom_out[f] = fns[f].atom;
-        for (int i = 0; i < 3; ++i) pw_out[3 * f + i] = fns[f].pw[i];
+        for (int i = 0; i < 3; ++i) pw_out[3 * f + i] = fns[f].pw[0][i];
         nprim_out[f] = fns[f].nprim;
         for (int k = 0; k < fns[f].nprim; ++k, ++o) {
             alpha_out[o] = fns[f].alpha[k];

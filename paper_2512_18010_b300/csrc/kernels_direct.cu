@@ -210,6 +210,40 @@ cudaError_t launch_axis_tables(const PairSetDev &ps, const double *pair_geom, co
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ pure shells -> Cartesian T
+
+__global__ void pure_to_cart_kernel(int S, int ncart, int nuser, const int32_t *__restrict__ idx,
+                                    const double *__restrict__ c, const double *__restrict__ Tu,
+                                    double *__restrict__ Tc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nn = (int64_t)ncart * ncart;
+    if (t >= (int64_t)S * nn) return;
+    const int s = (int)(t / nn);
+    const int a = (int)((t % nn) / ncart), b = (int)(t % ncart);
+    const double *T = Tu + (size_t)s * nuser * nuser;
+    double v = 0.0;
+    for (int e = 0; e < kMaxPureTerms; ++e) {
+        const int i = idx[a * kMaxPureTerms + e];
+        if (i < 0) break;
+        double row = 0.0;
+        for (int f = 0; f < kMaxPureTerms; ++f) {
+            const int j = idx[b * kMaxPureTerms + f];
+            if (j < 0) break;
+            row = fma(c[b * kMaxPureTerms + f], T[(size_t)i * nuser + j], row);
+        }
+        v = fma(c[a * kMaxPureTerms + e], row, v);
+    }
+    Tc[t] = v;
+}
+
+cudaError_t launch_pure_to_cart(int S, int ncart, int nuser, const int32_t *idx, const double *c,
+                                const double *Tu, double *Tc, cudaStream_t st) {
+    const int64_t tot = (int64_t)S * ncart * ncart;
+    if (tot == 0) return cudaSuccess;
+    pure_to_cart_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(S, ncart, nuser, idx, c, Tu, Tc);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ K2 direct q-evaluation
 
 template <typename R> struct Cplx;

@@ -144,6 +144,8 @@ static void free_basis(scff_basis_s *b) {
     cudaFree(d.rec_fn0);
     cudaFree(d.rec_w);
     cudaFree(d.pair_rec);
+    cudaFree(b->cmap_idx);
+    cudaFree(b->cmap_c);
     delete b;
 }
 static void free_trans(scff_trans_s *t) {
@@ -235,6 +237,71 @@ double same_centre_overlap(double p, const int pw[3]) {
     return v;
 }
 
+// <x^a y^b z^c e^{-p r^2/2} | x^a' y^b' z^c' e^{-p r^2/2}> on one centre:
+// per axis Int x^n e^{-p x^2} dx = (n-1)!! / (2p)^{n/2} sqrt(pi/p) for even n, 0 for odd n.
+double mono_overlap(double p, const int pa[3], const int pb[3]) {
+    double v = pow(M_PI / p, 1.5);
+    for (int i = 0; i < 3; ++i) {
+        const int n = pa[i] + pb[i];
+        if (n & 1) return 0.0;
+        v *= dfact_odd(n / 2) / pow(2.0 * p, n / 2);
+    }
+    return v;
+}
+
+// Real solid harmonics of the pure d and f shells, m = -l..l, as Cartesian
+// polynomials: up to three terms (k, exponents) each.
+struct PureTerm {
+    double k;
+    int pw[3];
+};
+struct PureFn {
+    int n;
+    PureTerm t[kMaxPureTerms];
+};
+const PureFn kPureD[5] = {
+    {1, {{1, {1, 1, 0}}}},
+    {1, {{1, {0, 1, 1}}}},
+    {3, {{2, {0, 0, 2}}, {-1, {2, 0, 0}}, {-1, {0, 2, 0}}}},
+    {1, {{1, {1, 0, 1}}}},
+    {2, {{1, {2, 0, 0}}, {-1, {0, 2, 0}}}},
+};
+const PureFn kPureF[7] = {
+    {2, {{3, {2, 1, 0}}, {-1, {0, 3, 0}}}},
+    {1, {{1, {1, 1, 1}}}},
+    {3, {{4, {0, 1, 2}}, {-1, {2, 1, 0}}, {-1, {0, 3, 0}}}},
+    {3, {{2, {0, 0, 3}}, {-3, {2, 0, 1}}, {-3, {0, 2, 1}}}},
+    {3, {{4, {1, 0, 2}}, {-1, {3, 0, 0}}, {-1, {1, 2, 0}}}},
+    {2, {{1, {2, 0, 1}}, {-1, {0, 2, 1}}}},
+    {2, {{1, {3, 0, 0}}, {-3, {1, 2, 0}}}},
+};
+
+// Coefficients of pure function m of shell l on the unit-norm Cartesian
+// components: phi_m = sum_i k_i (N_m / n_i) chi_i, where N_m normalises the
+// whole polynomial primitive (Appendix A) and n_i the single term.  Both
+// scale as alpha^{(2l+3)/4}, so the ratio is exponent-independent and equal
+// contraction renormalisation factors cancel; it is evaluated at alpha = 1/2.
+void pure_coefficients(int l, int m, int cart_out[kMaxPureTerms], double coef_out[kMaxPureTerms], int *n_out) {
+    const PureFn &h = (l == 2) ? kPureD[m] : kPureF[m];
+    const double alpha = 0.5, p = 2.0 * alpha;
+    double norm2 = 0.0;
+    for (int i = 0; i < h.n; ++i)
+        for (int j = 0; j < h.n; ++j) norm2 += h.t[i].k * h.t[j].k * mono_overlap(p, h.t[i].pw, h.t[j].pw);
+    const double Nm = 1.0 / sqrt(norm2);
+    const int ncart = (l + 1) * (l + 2) / 2;
+    for (int i = 0; i < h.n; ++i) {
+        int ci = -1;
+        for (int j = 0; j < ncart; ++j) {
+            int pw[3];
+            for (int ax = 0; ax < 3; ++ax) pw[ax] = cart_pow(l, j, ax);
+            if (pw[0] == h.t[i].pw[0] && pw[1] == h.t[i].pw[1] && pw[2] == h.t[i].pw[2]) ci = j;
+        }
+        cart_out[i] = ci;
+        coef_out[i] = h.t[i].k * Nm / prim_norm(alpha, h.t[i].pw);
+    }
+    *n_out = h.n;
+}
+
 template <typename T>
 scff_status upload(T **dst, const std::vector<T> &src) {
     *dst = nullptr;
@@ -256,9 +323,14 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
         return fail(SCFF_ERR_INVALID_ARG, "scff_basis: empty basis or NULL array");
     for (int i = 0; i < 3 * n_atoms; ++i)
         if (!isfinite(xyz[i])) return fail(SCFF_ERR_INVALID_ARG, "scff_basis: non-finite coordinate %d", i);
+    if (flags & ~(SCFF_RENORM_CONTRACTED | SCFF_PURE_D | SCFF_PURE_F))
+        return fail(SCFF_ERR_INVALID_ARG, "scff_basis: unknown flag bits 0x%x", flags);
     std::vector<HostRec> recs;
     size_t eoff = 0, coff = 0;
-    int nbf = 0;
+    int nbf = 0, nuser = 0;
+    bool any_pure = false;
+    std::vector<int32_t> cm_idx;  // [ncart][kMaxPureTerms]
+    std::vector<double> cm_c;
     const bool renorm = (flags & SCFF_RENORM_CONTRACTED) != 0;
     for (int s = 0; s < n_shells; ++s) {
         const int l = shell_l[s], np = shell_nprim[s], at = shell_atom[s];
@@ -301,6 +373,34 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
             for (int j = 0; j < kRecW; ++j) r.w[j] = j < nf ? w[(size_t)j * np + k] : 0.0;
             recs.push_back(r);
         }
+        // caller functions -> Cartesian components
+        const bool pure = (l == 2 && (flags & SCFF_PURE_D)) || (l == 3 && (flags & SCFF_PURE_F));
+        cm_idx.resize((size_t)(nbf + nf) * kMaxPureTerms, -1);
+        cm_c.resize((size_t)(nbf + nf) * kMaxPureTerms, 0.0);
+        if (pure) {
+            any_pure = true;
+            std::vector<int> used(nf, 0);
+            for (int m = 0; m < 2 * l + 1; ++m) {
+                int cart[kMaxPureTerms], n = 0;
+                double co[kMaxPureTerms];
+                pure_coefficients(l, m, cart, co, &n);
+                for (int i = 0; i < n; ++i) {
+                    const int a = nbf + cart[i];
+                    if (cart[i] < 0 || used[cart[i]] >= kMaxPureTerms)
+                        return fail(SCFF_ERR_INVALID_ARG, "scff_basis: internal pure-shell table error");
+                    cm_idx[(size_t)a * kMaxPureTerms + used[cart[i]]] = nuser + m;
+                    cm_c[(size_t)a * kMaxPureTerms + used[cart[i]]] = co[i];
+                    ++used[cart[i]];
+                }
+            }
+            nuser += 2 * l + 1;
+        } else {
+            for (int j = 0; j < nf; ++j) {
+                cm_idx[(size_t)(nbf + j) * kMaxPureTerms] = nuser + j;
+                cm_c[(size_t)(nbf + j) * kMaxPureTerms] = 1.0;
+            }
+            nuser += nf;
+        }
         nbf += nf;
         eoff += np;
         coff += ncoef;
@@ -315,7 +415,7 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
         }
     scff_basis_s *B = new scff_basis_s();
     B->ctx = c;
-    B->nbf = nbf;
+    B->nbf = nuser;
     PairSetDev &d = B->dev;
     d.n_rec = nrec;
     d.nbf = nbf;
@@ -348,13 +448,14 @@ extern "C" scff_status scff_basis(scff_ctx *c, int n_atoms, const double *xyz, i
     scff_status st = SCFF_OK;
     cudaSetDevice(c->device);
     if ((st = upload(&d.rec_xyz, rx)) || (st = upload(&d.rec_alpha, ra)) || (st = upload(&d.rec_type, rt)) ||
-        (st = upload(&d.rec_fn0, rf)) || (st = upload(&d.rec_w, rw)) || (st = upload(&d.pair_rec, pairs))) {
+        (st = upload(&d.rec_fn0, rf)) || (st = upload(&d.rec_w, rw)) || (st = upload(&d.pair_rec, pairs)) ||
+        (any_pure && ((st = upload(&B->cmap_idx, cm_idx)) || (st = upload(&B->cmap_c, cm_c))))) {
         free_basis(B);
         return st;
     }
     c->bases.push_back(B);
     *out = B;
-    if (nbf_out) *nbf_out = nbf;
+    if (nbf_out) *nbf_out = nuser;
     return SCFF_OK;
 }
 
@@ -366,17 +467,43 @@ extern "C" scff_status scff_transitions(scff_ctx *c, scff_basis_h b, int n_state
         return fail(SCFF_ERR_NOT_FOUND, "scff_transitions: unknown basis handle");
     if (n_states <= 0 || !T) return fail(SCFF_ERR_INVALID_ARG, "scff_transitions: n_states=%d, T=%p", n_states, (const void *)T);
     const size_t bytes = sizeof(double) * (size_t)n_states * b->nbf * b->nbf;
+    const int ncart = b->dev.nbf;
+    const size_t cbytes = sizeof(double) * (size_t)n_states * ncart * ncart;
     cudaSetDevice(c->device);
     scff_trans_s *t = new scff_trans_s();
     t->ctx = c;
     t->basis = b;
     t->S = n_states;
     t->d_T = nullptr;
-    if (cudaMalloc(&t->d_T, bytes) != cudaSuccess) {
+    if (cudaMalloc(&t->d_T, cbytes) != cudaSuccess) {
         delete t;
-        return fail(SCFF_ERR_OOM, "scff_transitions: cannot allocate %zu bytes", bytes);
+        return fail(SCFF_ERR_OOM, "scff_transitions: cannot allocate %zu bytes", cbytes);
     }
-    cudaError_t e = cudaMemcpy(t->d_T, T, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    cudaError_t e = cudaSuccess;
+    if (!b->cmap_idx) {
+        e = cudaMemcpy(t->d_T, T, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+        // a device-to-device copy may return early: the caller may free T after this call
+        if (e == cudaSuccess && on_dev) e = cudaStreamSynchronize(0);
+    } else {
+        // pure shells: expand T to the Cartesian components on the device
+        const double *Tu = T;
+        double *stage = nullptr;
+        if (!on_dev) {
+            if (cudaMalloc(&stage, bytes) != cudaSuccess) {
+                free_trans(t);
+                return fail(SCFF_ERR_OOM, "scff_transitions: cannot allocate %zu staging bytes", bytes);
+            }
+            e = cudaMemcpy(stage, T, bytes, cudaMemcpyHostToDevice);
+            Tu = stage;
+        }
+        if (e == cudaSuccess)
+            e = launch_pure_to_cart(n_states, ncart, b->nbf, b->cmap_idx, b->cmap_c, Tu, t->d_T, 0);
+        if (e == cudaSuccess) {
+            ++c->launches;
+            e = cudaStreamSynchronize(0);
+        }
+        if (stage) cudaFree(stage);
+    }
     if (e != cudaSuccess) {
         free_trans(t);
         return fail(SCFF_ERR_CUDA, "scff_transitions: copy failed: %s", cudaGetErrorString(e));

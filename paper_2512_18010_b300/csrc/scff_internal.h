@@ -145,6 +145,12 @@ cudaError_t launch_separable(const PairSetDev &ps, const double *geom, const dou
                              const double *const q[3], const double *const w[3], const int n[3], double2 *sums,
                              double2 *part, double scale, double *out, int64_t *launches, cudaStream_t st);
 
+// Expansion of caller-basis transition matrices to the Cartesian components:
+// Tc[s][a][b] = sum_e sum_f c[a][e] c[b][f] Tu[s][idx[a][e]][idx[b][f]].
+constexpr int kMaxPureTerms = 3;
+cudaError_t launch_pure_to_cart(int S, int ncart, int nuser, const int32_t *idx, const double *c,
+                                const double *Tu, double *Tc, cudaStream_t st);
+
 struct DirectArgs {
     const PairSetDev *ps;
     const void *coef;        // coef64 or coef32 in [n_sblk][n_rows][SB] layout

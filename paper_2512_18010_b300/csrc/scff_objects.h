@@ -55,8 +55,13 @@ struct scff_ctx {
 
 struct scff_basis_s {
     scff_ctx *ctx;
-    int nbf;
-    scff::PairSetDev dev;
+    int nbf;  // functions the caller numbers (pure shells count 2l+1)
+    scff::PairSetDev dev;  // Cartesian records; dev.nbf counts Cartesian components
+    // Pure shells: Cartesian component a = sum over e < kMaxPureTerms of
+    // cmap_c[a][e] x caller function cmap_idx[a][e] (-1 ends the list); null
+    // when every shell is Cartesian.
+    int32_t *cmap_idx = nullptr;
+    double *cmap_c = nullptr;
 };
 
 struct scff_trans_s {

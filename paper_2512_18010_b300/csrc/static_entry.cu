@@ -145,6 +145,9 @@ extern "C" scff_status scff_form_factor_static(int n_atoms, const double *xyz, i
     if (rc != SCFF_OK) return rc;
 
     // ---- basis ingest into static host storage: records, then pairs by class
+    if (flags & ~SCFF_RENORM_CONTRACTED)
+        return err(SCFF_ERR_INVALID_ARG,
+                   "scff_form_factor_static: only SCFF_RENORM_CONTRACTED is accepted (pure shells need scff_basis)");
     const bool renorm = (flags & SCFF_RENORM_CONTRACTED) != 0;
     int nrec = 0, nbf = 0;
     size_t eo = 0, co = 0;

@@ -19,6 +19,12 @@ from . import build as _build
 FP64, FP32, BF16X3, TF32X3, BF16X2 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3, "bf16x2": BF16X2}
 RENORM_CONTRACTED = 1
+PURE_D = 2   # d shells are the 5 real solid harmonics
+PURE_F = 4   # f shells are the 7 real solid harmonics
+
+
+def _basis_flags(mol, renorm: bool) -> int:
+    return (RENORM_CONTRACTED if renorm else 0) | (int(getattr(mol, "pure", 0)) & (PURE_D | PURE_F))
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_L", 3: "OOM", 4: "ADMISSION", 5: "CUDA",
           6: "TIMEOUT", 7: "CANCELLED", 8: "NOT_FOUND"}
@@ -293,7 +299,7 @@ class Context:
         h = ctypes.c_void_p()
         nbf = ctypes.c_int32()
         _check(self.lib.scff_basis(self.h, int(xyz.shape[0]), _p(xyz), int(sl.shape[0]), _p(sa), _p(sl), _p(sn),
-                                   _p(ex), _p(co), RENORM_CONTRACTED if renorm else 0, ctypes.byref(h),
+                                   _p(ex), _p(co), _basis_flags(mol, renorm), ctypes.byref(h),
                                    ctypes.byref(nbf)))
         return Basis(self, h, nbf.value)
 
@@ -305,6 +311,8 @@ class Context:
             if T.dim() == 2:
                 T = T.unsqueeze(0)
             S = int(T.shape[0])
+            if tuple(T.shape[1:]) != (basis.nbf, basis.nbf):
+                raise ValueError(f"T has shape {tuple(T.shape)}, basis has {basis.nbf} functions")
             _check(self.lib.scff_transitions(self.h, basis.handle, S, ctypes.c_void_p(T.data_ptr()), 1,
                                              ctypes.byref(h)))
         else:
@@ -482,7 +490,7 @@ def form_factor_static(mol, T_dev, q_dev, f_dev, f2_dev=None, scale: float = 1.0
         stream = torch.cuda.current_stream(f_dev.device)
     sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     rc = lib.scff_form_factor_static(int(xyz.shape[0]), _p(xyz), int(sl.shape[0]), _p(sa), _p(sl), _p(sn), _p(ex),
-                                     _p(co), RENORM_CONTRACTED if renorm else 0, S,
+                                     _p(co), _basis_flags(mol, renorm), S,
                                      ctypes.c_void_p(T_dev.data_ptr()), n, ctypes.c_void_p(q_dev.data_ptr()),
                                      float(scale), ctypes.c_void_p(f_dev.data_ptr()),
                                      ctypes.c_void_p(f2_dev.data_ptr()) if f2_dev is not None else None, sp)

@@ -35,6 +35,9 @@ import numpy as np
 
 # Cartesian function count per shell code (bookkeeping only).
 NFN = {0: 1, 1: 3, 2: 6, 3: 10, -1: 4}
+# Basis flag bits for pure (spherical-harmonic) d and f shells: 2l+1 functions.
+PURE_D, PURE_F = 2, 4
+_PURE_BIT = {2: PURE_D, 3: PURE_F}
 
 
 @dataclasses.dataclass
@@ -47,6 +50,7 @@ class Molecule:
     exponents: np.ndarray      # [sum nprim] float64
     coefficients: np.ndarray   # [sum nprim * (2 if sp else 1)] float64
     heavy: int = 0
+    pure: int = 0              # PURE_D | PURE_F: those shells are spherical-harmonic
 
     @property
     def n_atoms(self) -> int:
@@ -58,7 +62,11 @@ class Molecule:
 
     @property
     def nbf(self) -> int:
-        return int(sum(NFN[int(l)] for l in self.shell_l))
+        n = 0
+        for l in self.shell_l:
+            l = int(l)
+            n += 2 * l + 1 if (self.pure & _PURE_BIT.get(l, 0)) else NFN[l]
+        return n
 
     def translated(self, a) -> "Molecule":
         m = dataclasses.replace(self)
@@ -162,7 +170,7 @@ class _ShellList:
         ncoef = 2 * n if l == -1 else n
         self.coefs.append(rng.standard_normal(ncoef))
 
-    def molecule(self, name, xyz, heavy) -> Molecule:
+    def molecule(self, name, xyz, heavy, pure: int = 0) -> Molecule:
         return Molecule(
             name=name,
             xyz=np.ascontiguousarray(xyz, dtype=np.float64),
@@ -172,6 +180,7 @@ class _ShellList:
             exponents=np.concatenate(self.exps),
             coefficients=np.concatenate(self.coefs),
             heavy=heavy,
+            pure=pure,
         )
 
 
@@ -285,7 +294,7 @@ def molecule_dz_d(seed: int, n_heavy: int, n_h: Optional[int] = None) -> Molecul
     return sh.molecule(f"dz-d-{n_heavy}h-{seed}", xyz, heavy=n_heavy)
 
 
-def molecule_pol_f(seed: int, n_heavy: int, n_h: Optional[int] = None) -> Molecule:
+def molecule_pol_f(seed: int, n_heavy: int, n_h: Optional[int] = None, pure: int = 0) -> Molecule:
     """Random connected molecule with double-zeta + d + f on heavy atoms and p on H.
 
     Heavy atoms carry core s, two sp shells, one Cartesian d (2 primitives) and
@@ -307,12 +316,16 @@ def molecule_pol_f(seed: int, n_heavy: int, n_h: Optional[int] = None) -> Molecu
     for a in range(n_heavy, n_heavy + n_h):
         _double_zeta_h(sh, a, rng)
         sh.add(a, 1, log_uniform(rng, 0.5, 1.2, 1), rng)
-    return sh.molecule(f"pol-f-{n_heavy}h-{seed}", xyz, heavy=n_heavy)
+    return sh.molecule(f"pol-f-{n_heavy}h-{seed}" + ("-pure" if pure else ""), xyz, heavy=n_heavy, pure=pure)
 
 
-def config_f(seed: int = 3500, n_heavy: int = 4, n_states: int = 6, n: int = 48) -> Job:
-    """f-shell workload: 4 heavy + 4 H with d and f polarisation (120 functions), 48^3 on [-15,15]."""
-    mol = molecule_pol_f(seed, n_heavy)
+def config_f(seed: int = 3500, n_heavy: int = 4, n_states: int = 6, n: int = 48, pure: int = 0) -> Job:
+    """f-shell workload: 4 heavy + 4 H with d and f polarisation, 48^3 on [-15,15].
+
+    120 Cartesian functions; with pure = PURE_D | PURE_F the d and f shells
+    are spherical-harmonic (5 and 7 functions) and the basis has 104.
+    """
+    mol = molecule_pol_f(seed, n_heavy, pure=pure)
     T = transition_matrices(seed, n_states, mol.nbf)
     ax = axis(n, 15.0)
     return Job(mol, T, ax, ax.copy(), ax.copy(), seed)

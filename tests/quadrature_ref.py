@@ -22,6 +22,25 @@ _COMP = {
     -1: [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)],
 }
 
+# Pure (spherical-harmonic) shells: the real solid harmonics r^l Z_lm as
+# Cartesian polynomials [(k, (a, b, c)), ...], m = -l..l.  Their harmonicity
+# and their match with sympy's real spherical harmonics are tested separately.
+PURE = {
+    2: [[(1, (1, 1, 0))],
+        [(1, (0, 1, 1))],
+        [(2, (0, 0, 2)), (-1, (2, 0, 0)), (-1, (0, 2, 0))],
+        [(1, (1, 0, 1))],
+        [(1, (2, 0, 0)), (-1, (0, 2, 0))]],
+    3: [[(3, (2, 1, 0)), (-1, (0, 3, 0))],
+        [(1, (1, 1, 1))],
+        [(4, (0, 1, 2)), (-1, (2, 1, 0)), (-1, (0, 3, 0))],
+        [(2, (0, 0, 3)), (-3, (2, 0, 1)), (-3, (0, 2, 1))],
+        [(4, (1, 0, 2)), (-1, (3, 0, 0)), (-1, (1, 2, 0))],
+        [(1, (2, 0, 1)), (-1, (0, 2, 1))],
+        [(1, (3, 0, 0)), (-3, (1, 2, 0))]],
+}
+PURE_FLAG = {2: 2, 3: 4}
+
 
 def _trap_axis(a, A, alpha, b, B, beta, q):
     """Int (x-A)^a (x-B)^b exp(-alpha (x-A)^2 - beta (x-B)^2 + i q x) dx by trapezoid."""
@@ -37,23 +56,28 @@ def _trap_axis(a, A, alpha, b, B, beta, q):
 
 
 class QuadBasis:
-    """Contracted Cartesian Gaussians normalised by quadrature."""
+    """Contracted Gaussians (Cartesian or pure) normalised by quadrature."""
 
     def __init__(self, mol, renorm=True):
-        self.fn = []   # (center[3], powers(3), alphas[k], weights[k])
+        self.fn = []   # (center[3], terms [(k, powers)], alphas[k], weights[k])
+        pure_bits = int(getattr(mol, "pure", 0))
         eo = co = 0
         for s in range(mol.n_shells):
             l = int(mol.shell_l[s])
             np_ = int(mol.shell_nprim[s])
             A = np.asarray(mol.xyz[int(mol.shell_atom[s])], dtype=np.float64)
             al = np.asarray(mol.exponents[eo:eo + np_], dtype=np.float64)
-            for i, pw in enumerate(_COMP[l]):
+            if l in PURE and pure_bits & PURE_FLAG[l]:
+                funcs = PURE[l]
+            else:
+                funcs = [[(1, pw)] for pw in _COMP[l]]
+            for i, terms in enumerate(funcs):
                 off = co + (np_ if (l == -1 and i > 0) else 0)
                 c = np.asarray(mol.coefficients[off:off + np_], dtype=np.float64)
                 # primitive normalisation by quadrature: Int chi^2 = 1
-                nrm = np.array([self._self_overlap(pw, a_) for a_ in al])
+                nrm = np.array([self._self_overlap(terms, a_) for a_ in al])
                 w = c / np.sqrt(nrm)
-                self.fn.append([A, pw, al, w])
+                self.fn.append([A, terms, al, w])
             eo += np_
             co += np_ * (2 if l == -1 else 1)
         if renorm:
@@ -62,22 +86,28 @@ class QuadBasis:
                 f[3] = f[3] / np.sqrt(s)
 
     @staticmethod
-    def _self_overlap(pw, alpha):
-        v = 1.0
-        for i in range(3):
-            v *= _trap_axis(pw[i], 0.0, alpha, pw[i], 0.0, alpha, 0.0).real
-        return v
+    def _self_overlap(terms, alpha):
+        tot = 0.0
+        for ka, pa in terms:
+            for kb, pb in terms:
+                v = ka * kb
+                for i in range(3):
+                    v *= _trap_axis(pa[i], 0.0, alpha, pb[i], 0.0, alpha, 0.0).real
+                tot += v
+        return tot
 
     def _pair(self, f, g, q):
-        A, pa, aa, wa = f
-        B, pb, ab, wb = g
+        A, ta, aa, wa = f
+        B, tb, ab, wb = g
         tot = 0j
         for k in range(len(aa)):
             for kk in range(len(ab)):
-                v = 1.0 + 0j
-                for i in range(3):
-                    v *= _trap_axis(pa[i], A[i], aa[k], pb[i], B[i], ab[kk], q[i])
-                tot += wa[k] * wb[kk] * v
+                for ka, pa in ta:
+                    for kb, pb in tb:
+                        v = ka * kb + 0j
+                        for i in range(3):
+                            v *= _trap_axis(pa[i], A[i], aa[k], pb[i], B[i], ab[kk], q[i])
+                        tot += wa[k] * wb[kk] * v
         return tot
 
     @property
@@ -100,8 +130,10 @@ class QuadBasis:
         D = np.zeros((3, n, n))
         for i in range(n):
             for j in range(n):
-                A, pa, aa, wa = self.fn[i]
-                B, pb, ab, wb = self.fn[j]
+                A, ta, aa, wa = self.fn[i]
+                B, tb, ab, wb = self.fn[j]
+                assert len(ta) == 1 and len(tb) == 1, "dipole_matrices: Cartesian functions only"
+                pa, pb = ta[0][1], tb[0][1]
                 for k in range(3):
                     tot = 0.0
                     for u in range(len(aa)):

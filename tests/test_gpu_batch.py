@@ -25,7 +25,10 @@ def mixed_jobs():
     j3 = W.Job(j1.mol, W.transition_matrices(55, 5, j1.mol.nbf), W.axis(9, 7.0), W.axis(33, 8.0), W.axis(70, 9.0))
     m4 = W.molecule_dz_d(4077, 6)
     j4 = W.Job(m4, W.transition_matrices(4077, 4, m4.nbf), W.axis(30, 20.0), W.axis(30, 20.0), W.axis(30, 20.0))
-    return [j1, j2, j3, j4]
+    # pure d and f shells (pair classes up to degree 6, T expanded to Cartesian components)
+    m5 = W.molecule_pol_f(4099, 2, pure=W.PURE_D | W.PURE_F)
+    j5 = W.Job(m5, W.transition_matrices(4099, 3, m5.nbf), W.axis(20, 12.0), W.axis(26, 12.0), W.axis(17, 12.0))
+    return [j1, j2, j3, j4, j5]
 
 
 def make_batch(ctx, jobs, prec):

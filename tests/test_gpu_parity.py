@@ -188,3 +188,42 @@ def test_f_only_basis(ctx, prec):
     idx = W.subset_indices(job.nq, 800, 37)
     ref = oracle.grid_form_factor(job, idx)
     assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
+# ---------------------------------------------------------------- pure (spherical-harmonic) d and f shells
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3, scff.TF32X3])
+def test_pure_shells_grid_sampled(ctx, prec):
+    job = W.config_f(pure=W.PURE_D | W.PURE_F)
+    assert job.mol.nbf == 104
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 1500, 3502)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
+def test_pure_transitions_from_device_match_host(ctx):
+    import torch
+    job = W.config_f(n_heavy=2, n_states=4, n=20, pure=W.PURE_D)
+    b = ctx.basis(job.mol)
+    assert b.nbf == job.mol.nbf
+    g = ctx.qgrid_product(job.qx, job.qy, job.qz)
+    fh, _ = ctx.form_factor(b, ctx.transitions(b, job.T), g, precision=scff.FP64)
+    td = torch.tensor(job.T, dtype=torch.float64, device="cuda")
+    fd, _ = ctx.form_factor(b, ctx.transitions(b, td), g, precision=scff.FP64)
+    assert np.array_equal(fh, fd)
+    ref = oracle.grid_form_factor(job, W.subset_indices(job.nq, 400, 7))
+    assert rel_err(fh[:, W.subset_indices(job.nq, 400, 7)], ref) < TOL[scff.FP64]
+    with pytest.raises(ValueError):
+        ctx.transitions(b, torch.zeros((1, 105, 105), dtype=torch.float64, device="cuda"))
+
+
+def test_static_entry_rejects_pure_shells(ctx):
+    import torch
+    job = W.config_f(n_heavy=1, n_states=2, n=4, pure=W.PURE_F)
+    T = torch.tensor(job.T, dtype=torch.float64, device="cuda")
+    q = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    f = torch.zeros((2, 3, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(scff.ScffError) as e:
+        scff.form_factor_static(job.mol, T, q, f)
+    assert e.value.code == 1

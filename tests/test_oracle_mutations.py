@@ -17,12 +17,12 @@ from tests.test_oracle_pins import _gpt, mol_of, prim_norm_textbook
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "scff_oracle.c")
 
 MUTATIONS = {
-    "phase_sign": ("total += m->w[k] * n->w[kk] * K * prod * cexp(I * phase);",
-                   "total += m->w[k] * n->w[kk] * K * prod * cexp(-I * phase);"),
+    "phase_sign": ("total += m->w[k] * n->w[kk] * K * ang * cexp(I * phase);",
+                   "total += m->w[k] * n->w[kk] * K * ang * cexp(-I * phase);"),
     "dropped_recurrence_term": ("J[t + 1] = (I * q * J[t] + (double)t * J[t - 1]) / (2.0 * p);",
                                 "J[t + 1] = (I * q * J[t]) / (2.0 * p);"),
-    "swapped_centres": ("binomial_product(m->pw[i], P[i] - A[i], n->pw[i], P[i] - B[i], e);",
-                        "binomial_product(m->pw[i], P[i] - B[i], n->pw[i], P[i] - A[i], e);"),
+    "swapped_centres": ("binomial_product(m->pw[ti][i], P[i] - A[i], n->pw[tj][i], P[i] - B[i], e);",
+                        "binomial_product(m->pw[ti][i], P[i] - B[i], n->pw[tj][i], P[i] - A[i], e);"),
     "gamma_argument": ("prod *= pow(sigma, 1.0 + 2.0 * e[i]) * tgamma(e[i] + 0.5);",
                        "prod *= pow(sigma, 1.0 + 2.0 * e[i]) * tgamma(e[i] + 1.5);"),
     "gaussian_width": ("J[0] = sqrt(M_PI / p) * exp(-q * q / (4.0 * p));",
@@ -37,6 +37,10 @@ MUTATIONS = {
     "binomial_power": ("ea[i] = C[a][i] * pow(u, a - i);", "ea[i] = C[a][i] * pow(u, i);"),
     "f_component_order": ("{{3, 0, 0}, {2, 1, 0}, {2, 0, 1}", "{{3, 0, 0}, {2, 0, 1}, {2, 1, 0}"),
     "cubic_binomial": ("{1, 2, 1, 0}, {1, 3, 3, 1}}", "{1, 2, 1, 0}, {1, 2, 2, 1}}"),
+    "pure_dz2_coefficient": ("{2.0, -1.0, -1.0}},\n    {1, {{1, 0, 1}}", "{1.0, -1.0, -1.0}},\n    {1, {{1, 0, 1}}"),
+    "pure_norm_cross_terms": ("        for (int j = 0; j < nterm; ++j) {\n            double prod = k[i] * k[j];",
+                              "        for (int j = i; j <= i; ++j) {\n            double prod = k[i] * k[j];"),
+    "pure_f_coefficient": ("{4.0, -1.0, -1.0}},\n    {3, {{0, 0, 3},", "{3.0, -1.0, -1.0}},\n    {3, {{0, 0, 3},"),
 }
 
 
@@ -55,7 +59,7 @@ def compile_variant(src_text, path):
     return lib
 
 
-def ff(lib, mol, T, q):
+def ff(lib, mol, T, q, flags=1):
     c = lambda a, d: np.ascontiguousarray(a, dtype=d)  # noqa: E731
     xyz, sa, sl, sn = c(mol.xyz, np.float64), c(mol.shell_atom, np.int32), c(mol.shell_l, np.int32), \
         c(mol.shell_nprim, np.int32)
@@ -64,7 +68,7 @@ def ff(lib, mol, T, q):
     q = c(q, np.float64).reshape(-1, 3)
     out = np.zeros((T.shape[0], q.shape[0], 2))
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-    rc = lib.scff_oracle_form_factor(mol.n_atoms, p(xyz), mol.n_shells, p(sa), p(sl), p(sn), p(ex), p(co), 1,
+    rc = lib.scff_oracle_form_factor(mol.n_atoms, p(xyz), mol.n_shells, p(sa), p(sl), p(sn), p(ex), p(co), flags,
                                      T.shape[0], p(T), q.shape[0], p(q), 1.0, p(out), 2)
     assert rc == 0
     return out[..., 0] + 1j * out[..., 1]
@@ -104,6 +108,12 @@ def pins_pass(lib):
     mf = mol_of(rng.uniform(-1.5, 1.5, size=(2, 3)), [(0, 3, [1.1], [1.0]), (1, 3, [0.6], [1.0])])
     Tf = rng.standard_normal((1, 20, 20))
     ok.append(rel(ff(lib, mf, Tf, qq), Q.form_factor(mf, Tf, qq)) < 1e-10)
+    # pure d and f shells, without contraction rescaling (which would hide a
+    # wrong primitive normalisation)
+    mp = mol_of(rng.uniform(-1.5, 1.5, size=(2, 3)), [(0, 2, [1.1], [1.0]), (1, 3, [0.6], [1.0])])
+    mp = W.Molecule(**{**mp.__dict__, "pure": W.PURE_D | W.PURE_F})
+    Tp = rng.standard_normal((1, 12, 12))
+    ok.append(rel(ff(lib, mp, Tp, qq, flags=6), Q.form_factor(mp, Tp, qq, renorm=False)) < 1e-10)
     return all(ok)
 
 

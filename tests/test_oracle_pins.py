@@ -209,6 +209,96 @@ def test_f_shells_against_quadrature():
     assert rel_err(oracle.form_factor(mol, T, q), Q.form_factor(mol, T, q)) < 1e-11
 
 
+# ---------------------------------------------------------------- pure (spherical-harmonic) shells
+
+def _pure_mol(xyz, shells, pure=W.PURE_D | W.PURE_F):
+    m = mol_of(xyz, shells)
+    return W.Molecule(**{**m.__dict__, "pure": pure})
+
+
+def _real_sph_harm(l, m, theta, phi):
+    """Real spherical harmonics from scipy's complex Y_l^m (any fixed sign convention)."""
+    from scipy.special import sph_harm_y
+    y = sph_harm_y(l, abs(m), theta, phi)
+    if m > 0:
+        return np.sqrt(2) * y.real
+    if m < 0:
+        return np.sqrt(2) * y.imag
+    return y.real
+
+
+@pytest.mark.parametrize("l", [2, 3])
+def test_pure_polynomials_are_the_real_solid_harmonics(l):
+    # Each polynomial of the quadrature reference's table is r^l Z_lm up to a
+    # constant factor: their ratio is the same at random points of the sphere.
+    rng = np.random.default_rng(40 + l)
+    v = rng.standard_normal((25, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    theta, phi = np.arccos(v[:, 2]), np.arctan2(v[:, 1], v[:, 0])
+    for i, terms in enumerate(Q.PURE[l]):
+        m = i - l
+        poly = sum(k * v[:, 0] ** a * v[:, 1] ** b * v[:, 2] ** c for k, (a, b, c) in terms)
+        ratio = poly / _real_sph_harm(l, m, theta, phi)
+        assert np.ptp(ratio) < 1e-10 * np.max(np.abs(ratio)), (l, m)
+
+
+def test_pure_shells_against_quadrature():
+    rng = np.random.default_rng(41)
+    xyz = rng.uniform(-1.4, 1.4, size=(3, 3))
+    mol = _pure_mol(xyz, [(0, 2, [1.3, 0.4], rng.standard_normal(2)),
+                          (0, 3, [0.9], [1.0]),
+                          (1, 3, [1.6, 0.5], rng.standard_normal(2)),
+                          (1, -1, [2.0, 0.6], rng.standard_normal(4)),
+                          (2, 2, [0.7], [1.0]),
+                          (2, 0, [0.5], [1.0])])
+    assert mol.nbf == 5 + 7 + 7 + 4 + 5 + 1
+    T = rng.standard_normal((2, mol.nbf, mol.nbf))
+    q = np.vstack([np.zeros(3), rng.uniform(-6, 6, size=(5, 3))])
+    for renorm in (True, False):
+        f = oracle.form_factor(mol, T, q, renorm=renorm)
+        g = Q.form_factor(mol, T, q, renorm=renorm)
+        assert rel_err(f, g) < 1e-11
+
+
+def test_pure_functions_orthonormal_on_one_centre():
+    # One primitive per shell, no contraction rescaling: the Appendix A
+    # normalisation (with its cross terms) must give unit norm by itself; the
+    # harmonics are orthogonal to each other and to lower degrees on the same
+    # centre (d to s, f to p).
+    A = np.array([[0.3, -0.2, 0.5]])
+    mol = _pure_mol(A, [(0, 0, [0.8], [1.0]), (0, 1, [1.1], [1.0]), (0, 2, [0.6], [1.0]), (0, 3, [0.9], [1.0])])
+    n = mol.nbf
+    assert n == 16
+    E = np.zeros((n * n, n, n))
+    for i in range(n):
+        for j in range(n):
+            E[i * n + j, i, j] = 1.0
+    S = oracle.form_factor(mol, E, np.zeros((1, 3)), renorm=False)[:, 0].real.reshape(n, n)
+    d, f = slice(4, 9), slice(9, 16)
+    assert np.allclose(S[d, d], np.eye(5), atol=1e-13)
+    assert np.allclose(S[f, f], np.eye(7), atol=1e-13)
+    assert np.max(np.abs(S[0, d])) < 1e-13
+    assert np.max(np.abs(S[1:4, f])) < 1e-13
+
+
+@pytest.mark.parametrize("l", [2, 3])
+def test_pure_shell_density_is_isotropic(l):
+    # sum_m phi_m^2 over a full pure shell is spherically symmetric (addition
+    # theorem), so with T = identity on the shell f(q) depends on |q| only.
+    # A Cartesian shell fails this (its components are not equally normalised).
+    mol = _pure_mol(np.zeros((1, 3)), [(0, l, [1.2, 0.35], [0.6, 0.5])])
+    T = np.eye(mol.nbf)[None]
+    rng = np.random.default_rng(42 + l)
+    u = rng.standard_normal((12, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    for qn in (0.7, 2.5, 5.0):
+        f = oracle.form_factor(mol, T, qn * u)[0]
+        assert np.max(np.abs(f - f[0])) < 1e-12 * abs(f[0])
+    cart = mol_of(np.zeros((1, 3)), [(0, l, [1.2, 0.35], [0.6, 0.5])])
+    fc = oracle.form_factor(cart, np.eye(cart.nbf)[None], 2.5 * u)[0]
+    assert np.max(np.abs(fc - fc[0])) > 1e-3 * abs(fc[0])
+
+
 def test_real_space_3d_sum_tiny():
     # Phi(r) = sum T phi phi tabulated on a 3-D grid and Fourier-summed directly.
     xyz = np.array([[0.0, 0.0, -0.7], [0.2, 0.1, 0.8]])
@@ -220,11 +310,11 @@ def test_real_space_3d_sum_tiny():
     x = np.arange(-9.0, 9.0 + h / 2, h)
     X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
     phis = []
-    for (A, pw, al, w) in qb.fn:
+    for (A, terms, al, w) in qb.fn:
         dx, dy, dz = X - A[0], Y - A[1], Z - A[2]
         r2 = dx * dx + dy * dy + dz * dz
         v = sum(wk * np.exp(-ak * r2) for ak, wk in zip(al, w))
-        phis.append(dx ** pw[0] * dy ** pw[1] * dz ** pw[2] * v)
+        phis.append(sum(k * dx ** pw[0] * dy ** pw[1] * dz ** pw[2] for k, pw in terms) * v)
     Phi = sum(T[0, m, n] * phis[m] * phis[n] for m in range(5) for n in range(5))
     qs = np.array([[0.0, 0.0, 0.0], [0.5, -0.3, 1.1], [2.0, 1.0, -1.5], [-3.0, 0.4, 0.2]])
     f = oracle.form_factor(mol, T, qs)[0]
