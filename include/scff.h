@@ -295,6 +295,45 @@ scff_status scff_separable_integral(scff_ctx *ctx, scff_basis_h basis, scff_tran
                                     double *out);
 
 /*
+ * Spherical method (Sec. "Analytic Method", Eqs. SphericalMethod, RTensor,
+ * WTensor, YYY; Appendix B; Sec. "Spherical Grid Method"):
+ *   f_s(q) = sum_{l <= lmax} sum_{m=-l..l} Y_l^m(q^) R^s_lm(|q|)
+ * with complex spherical harmonics carrying the Condon-Shortley phase and
+ * the coordinates of scff_basis as the expansion origin (centre the molecule
+ * for the fastest convergence in l).  Each R^s_lm(q) is the exact
+ * spherical-harmonic coefficient of f_s at radius q (no truncation inside
+ * it); only the sum over l is truncated at lmax.
+ *   grid->q[n_q]          radial |q| values (host, >= 0).
+ *   grid->theta[n_theta], grid->phi[n_phi]: the angular product grid of f
+ *                         (host; n_theta = n_phi = 0 for R and iso only).
+ *   grid->lmax            0..40.
+ * Outputs (any may be NULL; element type double for SCFF_FP64, float for the
+ * tensor-core precisions SCFF_BF16X3, SCFF_TF32X3, SCFF_BF16X2; other
+ * precisions give SCFF_ERR_INVALID_ARG):
+ *   R_out   [S][n_q][(lmax+1)^2][2]  R^s_lm(q), lm = l*l + l + m, times scale.
+ *   f_out   [S][n_q][n_theta][n_phi][2]  the truncated expansion on the grid.
+ *   f2_out  [S][n_q][n_theta][n_phi]     |f|^2.
+ *   iso_out [S][n_q]  (1/4pi) sum_{l <= lmax, m} |R_lm|^2, the isotropic
+ *                     average of |f|^2 over directions (exact as lmax grows).
+ * out_on_device selects device or host pointers; the call returns after
+ * `stream` has finished.  The dense pair contraction runs on the tensor cores
+ * for the split precisions and in FP64 on the CUDA cores for SCFF_FP64.
+ */
+typedef struct {
+    int lmax;
+    int n_q;
+    const double *q;
+    int n_theta;
+    const double *theta;
+    int n_phi;
+    const double *phi;
+} scff_sph_grid;
+
+scff_status scff_spherical(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans, const scff_sph_grid *grid,
+                           int precision, double scale, void *R_out, void *f_out, void *f2_out, void *iso_out,
+                           int out_on_device, void *stream);
+
+/*
  * Error-bounded pair screening (the exact-tolerance form of the paper's
  * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
  * first scff_form_factor call for a (transitions, grid extent) bounds every

@@ -368,6 +368,43 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
     }
 }
 
+// Split-and-swizzle image of a dense complex FP64 matrix src[M][lda] (K valid
+// columns; columns K..K_pad and rows M..M_pad are zero), in the same tile
+// layout as abuild_kernel.  One thread writes one 16-byte vector of each array.
+template <int KIND>
+__global__ void dense_image_kernel(const double2 *__restrict__ src, int64_t lda, int M, int64_t K, int M_pad,
+                                   int64_t K_pad, int nkc, uint8_t *__restrict__ Abuf) {
+    using KD = Kind<KIND>;
+    constexpr int V = KD::PER_VEC, BK = KD::BK, NP = KD::NP;
+    const int64_t kvn = K_pad / V;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M_pad * kvn) return;
+    const int m = (int)(idx / kvn);
+    const int64_t kv = idx % kvn;
+    float re[V], im[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int64_t k = kv * V + e;
+        double2 v = make_double2(0.0, 0.0);
+        if (m < M && k < K) v = src[(size_t)m * lda + k];
+        re[e] = (float)v.x;
+        im[e] = (float)v.y;
+    }
+    uint4 pr_[NP], pi_[NP];
+    split_vec<KIND>(re, pr_);
+    split_vec<KIND>(im, pi_);
+    const int mt = m / BM, r = m % BM;
+    const int64_t kc = (kv * V) / BK;
+    const int c0 = (int)((kv * V) % BK);
+    uint8_t *base = Abuf + ((size_t)mt * nkc + kc) * KD::A_STAGE;
+    const uint32_t off = sw64_offset<KIND>(r, c0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        *reinterpret_cast<uint4 *>(base + q * A_ARR + off) = pr_[q];
+        *reinterpret_cast<uint4 *>(base + (NP + q) * A_ARR + off) = pi_[q];
+    }
+}
+
 // ------------------------------------------------------------------ persistent main kernel
 
 // Adds the finished accumulator group with global index gg (TMEM set gg & 1)
@@ -546,10 +583,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int nkc = item.w;
             const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
             const int ngroups = (nkc + G - 1) / G;
-            const int ny = J.ny, nz = J.nz;
+            const int nz = J.nz;
             const int64_t n = (int64_t)item.z * BN + wrow;
             const bool nvalid = n < J.N;
-            const int iy = nvalid ? (int)(n / nz) : 0, iz = nvalid ? (int)(n % nz) : 0;
+            int iy = 0, iz = 0;
+            if (nvalid) {
+                iz = (int)(n % nz);
+                iy = (int)(n / nz);
+                if (J.ylm) {
+                    int l = (int)sqrtf((float)iz);
+                    while (l * l > iz) --l;
+                    while ((l + 1) * (l + 1) <= iz) ++l;
+                    iy = iy * J.ystride + l;
+                }
+            }
             const float vmask = nvalid ? 1.f : 0.f;
             const float2 *Yc = J.Y + iy;
             const float2 *Zc = J.Z + iz;
@@ -823,6 +870,93 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
     e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
+    return tc_launch_persistent(a.kind, d_job, d_items, (int)items.size(), a.drain_every, a.err, tc_num_sms(),
+                                launches, st);
+}
+
+// ------------------------------------------------------------------ generic two-table contraction
+
+template <int KIND> static int bk_of() { return tc::Kind<KIND>::BK; }
+
+int64_t tc_generic_kpad(int kind, int64_t K) {
+    const int BK = kind == tc::KIND_TF32X2 ? bk_of<tc::KIND_TF32X2>() : bk_of<tc::KIND_BF16X3>();
+    int64_t kp = (K + BK - 1) / BK * BK;
+    return kp > 0 ? kp : BK;
+}
+
+static size_t a_stage_of(int kind) {
+    switch (kind) {
+    case tc::KIND_BF16X2: return tc::Kind<tc::KIND_BF16X2>::A_STAGE;
+    case tc::KIND_BF16X3: return tc::Kind<tc::KIND_BF16X3>::A_STAGE;
+    default: return tc::Kind<tc::KIND_TF32X2>::A_STAGE;
+    }
+}
+
+size_t tc_generic_bytes(int kind, int M, int64_t K) {
+    const int64_t K_pad = tc_generic_kpad(kind, K);
+    const int BK = kind == tc::KIND_TF32X2 ? bk_of<tc::KIND_TF32X2>() : bk_of<tc::KIND_BF16X3>();
+    const int n_mt = (M + tc::BM - 1) / tc::BM;
+    const size_t img = (size_t)n_mt * (size_t)(K_pad / BK) * a_stage_of(kind);
+    return (img + 1023) / 1024 * 1024 + 1024;
+}
+
+template <int KIND>
+static void dense_image_t(const TcGenericArgs &a, int M_pad, int64_t K_pad, int nkc, uint8_t *img, cudaStream_t st) {
+    using KD = tc::Kind<KIND>;
+    const int64_t tot = (int64_t)M_pad * (K_pad / KD::PER_VEC);
+    tc::dense_image_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a.A, a.lda, a.M, a.K, M_pad, K_pad,
+                                                                                 nkc, img);
+}
+
+cudaError_t tc_run_generic(const TcGenericArgs &a, int64_t *launches, cudaStream_t st) {
+    using namespace tc;
+    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+    const int64_t K_pad = tc_generic_kpad(a.kind, a.K);
+    const int BK = a.kind == KIND_TF32X2 ? bk_of<KIND_TF32X2>() : bk_of<KIND_BF16X3>();
+    const int nkc = (int)(K_pad / BK);
+    const int n_mt = (a.M + BM - 1) / BM, M_pad = n_mt * BM;
+    const int n_nt = (int)((a.N + BN - 1) / BN);
+    const size_t img_bytes = (size_t)n_mt * nkc * a_stage_of(a.kind);
+    const size_t img_al = (img_bytes + 1023) / 1024 * 1024;
+    std::vector<int4> items;
+    TcJobDev jd;
+    memset(&jd, 0, sizeof(jd));
+    uint8_t *img = static_cast<uint8_t *>(a.ws);
+    jd.A = img;
+    jd.Y = a.Y;
+    jd.Z = a.Z;
+    jd.kofs = a.kofs;
+    jd.nz = a.nz;
+    jd.ny = 0;
+    jd.nx = a.nx;
+    jd.nkc = nkc;
+    jd.M = a.M;
+    jd.n_mt = n_mt;
+    jd.n_nt = n_nt;
+    jd.ylm = a.ylm;
+    jd.ystride = a.ystride;
+    jd.N = a.N;
+    jd.nq = (int64_t)a.nx * a.N;
+    jd.scale = a.scale;
+    jd.f = a.C;
+    jd.f2 = a.C2;
+    tc_build_items(&jd, 1, items);
+    const size_t need = img_al + 256 + sizeof(int4) * items.size();
+    if (need > a.ws_bytes) return cudaErrorInvalidValue;
+    switch (a.kind) {
+    case KIND_BF16X2: dense_image_t<KIND_BF16X2>(a, M_pad, K_pad, nkc, img, st); break;
+    case KIND_BF16X3: dense_image_t<KIND_BF16X3>(a, M_pad, K_pad, nkc, img, st); break;
+    default: dense_image_t<KIND_TF32X2>(a, M_pad, K_pad, nkc, img, st); break;
+    }
+    if (launches) ++*launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TcJobDev *d_job = reinterpret_cast<TcJobDev *>(img + img_al);
+    int4 *d_items = reinterpret_cast<int4 *>(img + img_al + 256);
+    e = cudaMemcpyAsync(d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
     return tc_launch_persistent(a.kind, d_job, d_items, (int)items.size(), a.drain_every, a.err, tc_num_sms(),
                                 launches, st);
 }

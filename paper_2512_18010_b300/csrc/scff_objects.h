@@ -51,7 +51,12 @@ struct scff_ctx {
     int autotune = 0;
     std::map<uint64_t, struct FFChoice> tune;
     std::map<uint64_t, float> tune_ms;
+    // spherical method: coefficient tables (spherical.cpp) and workspace
+    struct SphCache *sph = nullptr;
+    DevBuf sph_ws;
 };
+
+void scff_sph_cache_free(struct SphCache *c);
 
 struct scff_basis_s {
     scff_ctx *ctx;

@@ -37,9 +37,16 @@ struct TcJobDev {
     const int4 *kinfo;     // [nkc * BK] k -> (pair, v, w, axis row)
     const int2 *kofs;      // [nkc * BK] k -> element offsets in Y and Z
     int ny, nz, nx, nkc;
-    int M, n_mt, n_nt, pad0;
+    int M, n_mt, n_nt;
+    // Column n of the output splits into (n / nz, n % nz).  ylm = 0: the Y
+    // table is read at column n / nz and the Z table at n % nz (product
+    // grids).  ylm = 1: Z is read at LM = n % nz and Y at
+    // (n / nz) * ystride + L with L = floor(sqrt(LM)) (radial x (L, M)
+    // columns of the spherical method).
+    int ylm;
     int64_t N, nq;
-    float scale, pad1;
+    float scale;
+    int ystride;
     float2 *f;             // [S][nq] complex output
     float *f2;             // [S][nq] or null
 };
@@ -58,5 +65,32 @@ void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items);
 cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
                                  int *err, int grid_ctas, int64_t *launches, cudaStream_t st);
 int tc_num_sms();
+
+// Generic two-table contraction on the tensor cores (the spherical method):
+//   C[(s, ix), n] = scale * sum_k A[(s, ix), k] * Y[kofs[k].x + iy(n)] * Z[kofs[k].y + iz(n)]
+// with A given as a dense complex FP64 matrix (row-major, leading dimension
+// lda, K valid columns) that is split and swizzled into the tile image here,
+// and (iy, iz) from the column rule of TcJobDev (ylm, ystride).  Rows are
+// m = s * nx + ix, M = S * nx; C is [S][nx][N] complex FP32, C2 = |C|^2 or null.
+struct TcGenericArgs {
+    int kind;
+    const double2 *A;
+    int64_t lda, K;
+    int M, nx;
+    const float2 *Y, *Z;
+    const int2 *kofs;      // [K_pad] (padding k must point at zero rows)
+    int nz, ylm, ystride;
+    int64_t N;
+    float scale;
+    float2 *C;
+    float *C2;
+    int drain_every;
+    int *err;
+    void *ws;              // workspace of tc_generic_bytes()
+    size_t ws_bytes;
+};
+int64_t tc_generic_kpad(int kind, int64_t K);
+size_t tc_generic_bytes(int kind, int M, int64_t K);
+cudaError_t tc_run_generic(const TcGenericArgs &a, int64_t *launches, cudaStream_t st);
 
 }  // namespace scff

@@ -37,7 +37,7 @@ _SYMBOLS = [
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
-    "scff_screening_info", "scff_separable_integral",
+    "scff_screening_info", "scff_separable_integral", "scff_spherical",
 ]
 
 
@@ -51,6 +51,12 @@ class _Request(ctypes.Structure):
                 ("qx", ctypes.c_void_p), ("nx", ctypes.c_int), ("qy", ctypes.c_void_p), ("ny", ctypes.c_int),
                 ("qz", ctypes.c_void_p), ("nz", ctypes.c_int), ("scale", ctypes.c_double),
                 ("f_out", ctypes.c_void_p), ("f2_out", ctypes.c_void_p), ("out_on_device", ctypes.c_int)]
+
+
+class _SphGrid(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("n_q", ctypes.c_int), ("q", ctypes.c_void_p),
+                ("n_theta", ctypes.c_int), ("theta", ctypes.c_void_p), ("n_phi", ctypes.c_int),
+                ("phi", ctypes.c_void_p)]
 
 
 class _Job(ctypes.Structure):
@@ -95,6 +101,7 @@ def load(build_if_missing: bool = True):
     lib.scff_qgrid_size.argtypes = [P, P]
     lib.scff_qgrid_size.restype = I64
     lib.scff_form_factor.argtypes = [P, P, P, P, ctypes.c_int, D, P, P, ctypes.c_int, P]
+    lib.scff_spherical.argtypes = [P, P, P, ctypes.POINTER(_SphGrid), ctypes.c_int, D, P, P, P, P, ctypes.c_int, P]
     lib.scff_sync.argtypes = [P, P]
     lib.scff_form_factor_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, U32, ctypes.c_int, P,
                                             I64, P, D, P, P, P]
@@ -427,6 +434,42 @@ class Context:
                                                 len(arrs[0]), _p(arrs[2]), _p(arrs[3]), len(arrs[2]), _p(arrs[4]),
                                                 _p(arrs[5]), len(arrs[4]), float(scale), _p(out)))
         return out[:, 0] + 1j * out[:, 1]
+
+    def spherical(self, basis: Basis, trans: Transitions, q, lmax: int, theta=None, phi=None,
+                  precision=FP64, scale: float = 1.0, want=("R", "f", "f2", "iso")) -> dict:
+        """Spherical method: R_lm(q), and on an angular grid f and |f|^2, and the isotropic average.
+
+        Returns host arrays: "R" complex [S, n_q, (lmax+1)^2], "f" complex
+        [S, n_q, n_theta, n_phi], "f2" [S, n_q, n_theta, n_phi], "iso" [S, n_q]
+        (those in `want`; f and f2 only with an angular grid).
+        """
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        q = _np(q, np.float64)
+        th = _np(theta if theta is not None else np.zeros(0), np.float64)
+        ph = _np(phi if phi is not None else np.zeros(0), np.float64)
+        S, nq, nt, npf = trans.n_states, len(q), len(th), len(ph)
+        NR = (lmax + 1) ** 2
+        rdt = np.float64 if precision == FP64 else np.float32
+        angular = nt > 0 and npf > 0
+        R = np.zeros((S, nq, NR, 2), rdt) if "R" in want else None
+        f = np.zeros((S, nq, nt, npf, 2), rdt) if ("f" in want and angular) else None
+        f2 = np.zeros((S, nq, nt, npf), rdt) if ("f2" in want and angular) else None
+        iso = np.zeros((S, nq), rdt) if "iso" in want else None
+        g = _SphGrid(int(lmax), nq, _p(q), nt, _p(th) if nt else None, npf, _p(ph) if npf else None)
+        ptr = lambda a: None if a is None else _p(a)  # noqa: E731
+        _check(self.lib.scff_spherical(self.h, basis.handle, trans.handle, ctypes.byref(g), int(precision),
+                                       float(scale), ptr(R), ptr(f), ptr(f2), ptr(iso), 0, None))
+        out = {}
+        if R is not None:
+            out["R"] = R[..., 0] + 1j * R[..., 1]
+        if f is not None:
+            out["f"] = f[..., 0] + 1j * f[..., 1]
+        if f2 is not None:
+            out["f2"] = f2
+        if iso is not None:
+            out["iso"] = iso
+        return out
 
     def set_screening(self, eps: float):
         """Error-bounded pair screening: results within eps * max|f| of the exact ones (0 = off)."""
