@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--only-spherical", action="store_true",
+                    help="run only the spherical-method measurement and print it (for profiling)")
+    ap.add_argument("--no-spherical", action="store_true",
+                    help="skip the spherical-method measurement (l_max 24 on a 100^3 (q, theta, phi) grid)")
     ap.add_argument("--serving-jobs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=0, help="also time a batched plan of this many batched-workload jobs")
     ap.add_argument("--screen-eps", type=float, default=1e-8,
@@ -105,6 +109,57 @@ def workload(name: str, rank: int = 0):
         "cfg3": "cfg3: 10 heavy + 10 H, 170 functions (double-zeta + d), 12 states, 128^3 on [-20,20]",
     }[name]
     return job, desc
+
+
+SPH_LMAX, SPH_NQ, SPH_NT, SPH_NP, SPH_QMAX = 24, 100, 100, 100, 4.0
+
+
+def spherical_run(ctx, b, t, S, prec, steps, stream, flush):
+    """Spherical method: R_lm for l <= 24 at 100 radii in [0, 4] Bohr^-1 and f, |f|^2 on a
+    100 x 100 (theta, phi) grid, all on the device; FP64 path at 10 radii beside it."""
+    import torch
+    from paper_2512_18010_b300 import scff
+    q = np.linspace(0.0, SPH_QMAX, SPH_NQ)
+    th = np.pi * (np.arange(SPH_NT) + 0.5) / SPH_NT
+    ph = 2 * np.pi * np.arange(SPH_NP) / SPH_NP
+
+    def call(precision, qq):
+        return ctx.spherical(b, t, qq, SPH_LMAX, th, ph, precision=precision, want=("R", "f", "f2", "iso"),
+                             out="cuda", stream=stream)
+
+    for _ in range(2):
+        call(prec, q)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = call(prec, q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    units = S * SPH_NQ * SPH_NT * SPH_NP
+    tms = float(np.mean(ms))
+    # FP64 path (CUDA cores) on the first 10 radii, and the split path's error there
+    q10 = q[:: SPH_NQ // 10][:10]
+    call(scff.FP64, q10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    o64 = call(scff.FP64, q10)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    o32 = call(prec, q10)
+    r64 = o64["R"].cpu().numpy()
+    r32 = o32["R"].double().cpu().numpy()
+    err = float(np.max(np.max(np.abs(r32 - r64).reshape(S, -1), axis=1) / np.max(np.abs(r64).reshape(S, -1), axis=1)))
+    del out, o64, o32
+    return {"workload": f"10-heavy-atom job, {S} states, l_max {SPH_LMAX}, {SPH_NQ} radii on [0, {SPH_QMAX}] x "
+                        f"{SPH_NT} theta x {SPH_NP} phi; R, f, |f|^2 and isotropic average on the device",
+            "value": units / (tms / 1e3), "unit": UNIT, "ms_per_call": tms,
+            "fp64_path": {"value": S * len(q10) * SPH_NT * SPH_NP / (ms64 / 1e3), "unit": UNIT, "ms_per_call": ms64,
+                          "radii": len(q10)},
+            "max_rel_err_R_vs_fp64": err}
 
 
 def pair_stats(mol):
@@ -375,6 +430,11 @@ def main():
     def step():
         ctx.form_factor(b, t, g, precision=prec, f_out=f, f2_out=f2, stream=stream)
 
+    if args.only_spherical:
+        if rank == 0:
+            print(json.dumps({"spherical": spherical_run(ctx, b, t, S, prec, args.steps, stream, flush)}), flush=True)
+        return 0
+
     ctx.set_timing(True)
     for _ in range(args.warmup):
         step()
@@ -482,6 +542,11 @@ def main():
                     "kept_pairs": info["kept_pairs"], "pairs": info["pairs"], "kept_rows": info["kept_rows"],
                     "rows": info["rows"], "error_bound": "<= eps x max_q|f_s(q)| per state (rigorous)"}
 
+    # the spherical method on the same molecule and states (a side measurement)
+    spherical = None
+    if not args.no_spherical and prec != scff.FP64 and args.workload == "cfg3":
+        spherical = spherical_run(ctx, b, t, S, prec, args.steps, stream, flush)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -531,7 +596,7 @@ def main():
                            "monomial_rows": K, "vw_rows": Kvw, "autotune": choice,
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"dp{world} (one job per rank)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "spherical": spherical, "gpu_launches": int(launches),
                 "fp64_gpu_path": fp64, "screened": screened, "serving": serving, "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)

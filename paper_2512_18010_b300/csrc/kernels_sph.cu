@@ -15,7 +15,10 @@
 //   Z^s[(lambda mu), (q, L M)] = sum_{(p, n)} W^{s,n}_{p,lambda mu} rho_{p,n,L}(q) y_{p,LM},
 //   W^{s,n}_{p,lambda mu} = sum_{u+v+w=n} D^s_uvw Theta^{uvw}_{lambda mu}   (the W tensor),
 //   rho_{p,n,L}(q) = exp(-q^2/4p) q^n j_L(q|P|),   y_{p,LM} = 4 pi i^L conj(Y_L^M(P^)),
-// followed by a small Gaunt contraction
+// Theta vanishes unless lambda and n have the same parity, so the contraction
+// splits into an even job (n and lambda even) and an odd job, each over its
+// own k = (pair, n) and rows (s, lambda mu): half the work of the full one.
+// This is followed by a small Gaunt contraction
 //   R^s_lm(q) = sum_{lambda mu, L} G(lambda mu, L (m-mu) -> l m) Z^s[(lambda mu), (q, L (m-mu))]
 // and, for a tabulated angular grid, a second dense contraction
 //   f_s(q, theta, phi) = sum_{lm} R^s_lm(q) p_l^m(cos theta) e^{i m phi}.
@@ -74,72 +77,104 @@ __global__ void sph_radial_kernel(PairSetDev ps, const double *__restrict__ geom
     }
 }
 
-// y[p][LM] = 4 pi i^L conj(Y_L^M(P^)) for L <= Lmax (P at the origin: P^ = z^).
+// y[p][LM] = 4 pi i^L conj(Y_L^M(P^)) for L <= Lmax (P at the origin: P^ = z^);
+// one thread per (pair, |M|) writes the +M and -M entries of every L.
 template <typename V>
 __global__ void sph_ypair_kernel(PairSetDev ps, const double *__restrict__ geom, int Lmax, V *__restrict__ table) {
-    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pr >= ps.n_pair) return;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)ps.n_pair * (Lmax + 1)) return;
+    const int pr = (int)(idx / (Lmax + 1)), M = (int)(idx % (Lmax + 1));
     const double Px = geom[4 * pr], Py = geom[4 * pr + 1], Pz = geom[4 * pr + 2];
     const double r = sqrt(Px * Px + Py * Py + Pz * Pz);
     const double x = r > 0.0 ? Pz / r : 1.0;
     const double phi = r > 0.0 ? atan2(Py, Px) : 0.0;
-    double p[(kMaxBigL + 1) * (kMaxBigL + 2) / 2];
-    sph::plm_all(Lmax, x, p);
+    double col[kMaxBigL + 1];
+    sph::plm_column(Lmax, M, x, col);
+    double sn, cs;
+    sincos(M * phi, &sn, &cs);
     const int NLM = (Lmax + 1) * (Lmax + 1);
     V *row = table + (size_t)pr * NLM;
     const double four_pi = 12.566370614359172;
-    for (int L = 0; L <= Lmax; ++L) {
+    const double sgn = (M & 1) ? -1.0 : 1.0;  // p_L^{-M} = (-1)^M p_L^M
+    for (int L = M; L <= Lmax; ++L) {
         // i^L
         const double ir = (L & 1) ? 0.0 : ((L & 2) ? -1.0 : 1.0);
         const double ii = (L & 1) ? ((L & 2) ? -1.0 : 1.0) : 0.0;
-        for (int M = -L; M <= L; ++M) {
-            double sn, cs;
-            sincos(-M * phi, &sn, &cs);  // conj(e^{i M phi})
-            const double a = four_pi * sph::plm_signed(p, L, M);
-            const double yr = a * cs, yi = a * sn;
-            V v;
+        const double a = four_pi * col[L - M];
+        // conj(Y_L^M) = p e^{-i M phi}
+        double yr = a * cs, yi = -a * sn;
+        V v;
+        v.x = ir * yr - ii * yi;
+        v.y = ir * yi + ii * yr;
+        row[sph::lm_index(L, M)] = v;
+        if (M > 0) {
+            // conj(Y_L^{-M}) = (-1)^M p e^{+i M phi}
+            yr = sgn * a * cs;
+            yi = sgn * a * sn;
             v.x = ir * yr - ii * yi;
             v.y = ir * yi + ii * yr;
-            row[sph::lm_index(L, M)] = v;
+            row[sph::lm_index(L, -M)] = v;
         }
     }
 }
 
-// kofs of the Z contraction: k = (pair, n) reads rho row k and y row pair;
-// padding k reads the zero rows.
-__global__ void sph_kofs_kernel(PairSetDev ps, int64_t K_pad, int nq, int NL, int NLM, int2 *__restrict__ kofs) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K_pad) return;
-    if (k < ps.n_axrows) {
-        const int Lc = axrow_class(ps, k);
-        const int pr = ps.pair_off[Lc] + (int)((k - ps.axrow_off[Lc]) / (Lc + 1));
-        kofs[k] = make_int2((int)(k * nq * NL), pr * NLM);
-    } else {
-        kofs[k] = make_int2((int)(ps.n_axrows * nq * NL), ps.n_pair * NLM);
-    }
+// Compact k of one parity job -> (class, pair, n, axis row).
+__device__ __forceinline__ bool sph_k_decode(const PairSetDev &ps, const SphParity &kp, int64_t k, int *Lc_out,
+                                             int *pr_out, int *n_out, int64_t *axrow_out) {
+    if (k >= kp.off[kNumClasses]) return false;
+    int Lc = 0;
+    while (Lc < kMaxPairL && k >= kp.off[Lc + 1]) ++Lc;
+    const int cnt = sph_parity_count(Lc, kp.par);
+    const int64_t local = k - kp.off[Lc];
+    const int pl = (int)(local / cnt);
+    const int n = kp.par + 2 * (int)(local % cnt);
+    *Lc_out = Lc;
+    *pr_out = ps.pair_off[Lc] + pl;
+    *n_out = n;
+    *axrow_out = ps.axrow_off[Lc] + (int64_t)pl * (Lc + 1) + n;
+    return true;
 }
 
-// W tensor as a dense complex matrix A[(s, lambda mu)][k = (pair, n)]:
+// kofs of one parity job: k = (pair, n) reads rho at axis row (pair, n) and y
+// at row pair; padding k reads the zero rows.
+__global__ void sph_kofs_kernel(PairSetDev ps, SphParity kp, int64_t K_pad, int nq, int NL, int NLM,
+                                int2 *__restrict__ kofs) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K_pad) return;
+    int Lc, pr, n;
+    int64_t ax;
+    if (sph_k_decode(ps, kp, k, &Lc, &pr, &n, &ax))
+        kofs[k] = make_int2((int)(ax * nq * NL), pr * NLM);
+    else
+        kofs[k] = make_int2((int)(ps.n_axrows * nq * NL), ps.n_pair * NLM);
+}
+
+// W tensor of one parity job as a dense complex matrix
+// A[(s, sub)][k = (pair, n)], sub the index of (lambda, mu) among the
+// harmonics of that parity:
 // W = i^(n mod 2) sum_{u+v+w=n} c^s_uvw Theta^{uvw}_{lambda mu} (the folded
 // pair-prep coefficients c carry the sign of i^n; the odd-n factor i is
 // restored here).  theta is [monomial][49] over lambda <= 6.
-__global__ void sph_wdense_kernel(PairSetDev ps, const double *__restrict__ coef64, int SB, int S, int NLAM,
-                                  const double2 *__restrict__ theta, int64_t K_pad, double2 *__restrict__ A) {
+__global__ void sph_wdense_kernel(PairSetDev ps, const double *__restrict__ coef64, int SB, int S, SphParity kp,
+                                  int n_sub, const double2 *__restrict__ theta, int64_t K_pad,
+                                  double2 *__restrict__ A) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)S * NLAM * K_pad) return;
+    if (idx >= (int64_t)S * n_sub * K_pad) return;
     const int m = (int)(idx / K_pad);
     const int64_t k = idx % K_pad;
-    const int s = m / NLAM, lm = m % NLAM;
-    int lam = (int)sqrtf((float)lm);
-    while (lam * lam > lm) --lam;
-    while ((lam + 1) * (lam + 1) <= lm) ++lam;
+    const int s = m / n_sub, sub = m % n_sub;
+    int lam = kp.par, base = 0;
+    while (sub >= base + 2 * lam + 1) {
+        base += 2 * lam + 1;
+        lam += 2;
+    }
+    const int lm = sph::lm_index(lam, sub - base - lam);
     double2 acc = make_double2(0.0, 0.0);
-    if (k < ps.n_axrows) {
-        const int Lc = axrow_class(ps, k);
-        const int64_t local = k - ps.axrow_off[Lc];
-        const int pr_local = (int)(local / (Lc + 1));
-        const int n = (int)(local % (Lc + 1));
-        if (lam <= n && ((n - lam) & 1) == 0) {
+    int Lc, pr, n;
+    int64_t ax;
+    if (sph_k_decode(ps, kp, k, &Lc, &pr, &n, &ax)) {
+        const int pr_local = pr - ps.pair_off[Lc];
+        if (lam <= n) {
             const int64_t rowbase = ps.row_off[Lc] + (int64_t)pr_local * mono_count(Lc);
             const double *cs = coef64 + ((size_t)(s / SB) * ps.n_rows) * SB + (s % SB);
             for (int u = n; u >= 0; --u)
@@ -156,11 +191,14 @@ __global__ void sph_wdense_kernel(PairSetDev ps, const double *__restrict__ coef
     A[idx] = acc;
 }
 
-// R^s_lm(q) = scale * sum_entries G Z^s[(lambda mu), (q, L M)].
+// R^s_lm(q) = scale * sum_entries G Z^s[(lambda mu), (q, L M)], with Z held
+// as the even and odd jobs' outputs [S][n_sub][nq x NLM]; an entry's x field
+// is sub | (parity << 16).
 template <typename VZ>
-__global__ void sph_gaunt_kernel(const VZ *__restrict__ Z, int S, int nq, int NLAM, int NLM, int NR,
-                                 const int *__restrict__ goff, const int2 *__restrict__ gidx,
-                                 const double *__restrict__ gval, double scale, double2 *__restrict__ R) {
+__global__ void sph_gaunt_kernel(const VZ *__restrict__ Ze, const VZ *__restrict__ Zo, int ne, int no, int S,
+                                 int nq, int NLM, int NR, const int *__restrict__ goff,
+                                 const int2 *__restrict__ gidx, const double *__restrict__ gval, double scale,
+                                 double2 *__restrict__ R) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)S * nq * NR) return;
     const int o = (int)(idx % NR);
@@ -170,7 +208,11 @@ __global__ void sph_gaunt_kernel(const VZ *__restrict__ Z, int S, int nq, int NL
     double re = 0.0, im = 0.0;
     for (int e = goff[o]; e < goff[o + 1]; ++e) {
         const int2 ix = gidx[e];
-        const VZ z = Z[((size_t)s * NLAM + ix.x) * N + (size_t)iq * NLM + ix.y];
+        const int sub = ix.x & 0xFFFF;
+        const bool odd = (ix.x >> 16) != 0;
+        const VZ *Z = odd ? Zo : Ze;
+        const int nsub = odd ? no : ne;
+        const VZ z = Z[((size_t)s * nsub + sub) * N + (size_t)iq * NLM + ix.y];
         const double g = gval[e];
         re = fma(g, (double)z.x, re);
         im = fma(g, (double)z.y, im);
@@ -196,20 +238,26 @@ __global__ void sph_r_to_f32_kernel(const double2 *__restrict__ R, int64_t n, fl
     if (idx < n) out[idx] = make_float2((float)R[idx].x, (float)R[idx].y);
 }
 
-// Angular tables: T1[(l m)][itheta] = p_l^m(cos theta), T2[(m + lmax)][iphi] = e^{i m phi}.
+// Angular tables: T1[(l m)][itheta] = p_l^m(cos theta), T2[(m + lmax)][iphi] = e^{i m phi};
+// one thread per (theta, |m|) fills the +m and -m rows.
 template <typename V>
 __global__ void sph_theta_table_kernel(const double *__restrict__ theta, int nt, int lmax, V *__restrict__ T1) {
-    const int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= nt) return;
-    double p[(sph::kMaxLmax + 1) * (sph::kMaxLmax + 2) / 2];
-    sph::plm_all(lmax, cos(theta[it]), p);
-    for (int l = 0; l <= lmax; ++l)
-        for (int m = -l; m <= l; ++m) {
-            V v;
-            v.x = sph::plm_signed(p, l, m);
-            v.y = 0;
-            T1[(size_t)sph::lm_index(l, m) * nt + it] = v;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nt * (lmax + 1)) return;
+    const int it = idx / (lmax + 1), m = idx % (lmax + 1);
+    double col[sph::kMaxLmax + 1];
+    sph::plm_column(lmax, m, cos(theta[it]), col);
+    const double sgn = (m & 1) ? -1.0 : 1.0;
+    for (int l = m; l <= lmax; ++l) {
+        V v;
+        v.x = col[l - m];
+        v.y = 0;
+        T1[(size_t)sph::lm_index(l, m) * nt + it] = v;
+        if (m > 0) {
+            v.x = sgn * col[l - m];
+            T1[(size_t)sph::lm_index(l, -m) * nt + it] = v;
         }
+    }
 }
 
 template <typename V>
@@ -345,38 +393,40 @@ cudaError_t launch_sph_radial(const PairSetDev &ps, const double *geom, const do
 
 cudaError_t launch_sph_ypair(const PairSetDev &ps, const double *geom, int Lmax, int fp64, void *table,
                              cudaStream_t st) {
-    if (ps.n_pair == 0) return cudaSuccess;
-    if (fp64)
-        sph_ypair_kernel<double2><<<blocks_of(ps.n_pair, 64), 64, 0, st>>>(ps, geom, Lmax, (double2 *)table);
-    else
-        sph_ypair_kernel<float2><<<blocks_of(ps.n_pair, 64), 64, 0, st>>>(ps, geom, Lmax, (float2 *)table);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sph_kofs(const PairSetDev &ps, int64_t K_pad, int nq, int NL, int NLM, int2 *kofs,
-                            cudaStream_t st) {
-    sph_kofs_kernel<<<blocks_of(K_pad, 256), 256, 0, st>>>(ps, K_pad, nq, NL, NLM, kofs);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sph_wdense(const PairSetDev &ps, const double *coef64, int SB, int S, int NLAM,
-                              const double2 *theta, int64_t K_pad, double2 *A, cudaStream_t st) {
-    const int64_t tot = (int64_t)S * NLAM * K_pad;
+    const int64_t tot = (int64_t)ps.n_pair * (Lmax + 1);
     if (tot == 0) return cudaSuccess;
-    sph_wdense_kernel<<<blocks_of(tot, 256), 256, 0, st>>>(ps, coef64, SB, S, NLAM, theta, K_pad, A);
+    if (fp64)
+        sph_ypair_kernel<double2><<<blocks_of(tot, 128), 128, 0, st>>>(ps, geom, Lmax, (double2 *)table);
+    else
+        sph_ypair_kernel<float2><<<blocks_of(tot, 128), 128, 0, st>>>(ps, geom, Lmax, (float2 *)table);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sph_gaunt(const void *Z, int fp64, int S, int nq, int NLAM, int NLM, int NR, const int *goff,
-                             const int2 *gidx, const double *gval, double scale, double2 *R, cudaStream_t st) {
+cudaError_t launch_sph_kofs(const PairSetDev &ps, const SphParity &kp, int64_t K_pad, int nq, int NL, int NLM,
+                            int2 *kofs, cudaStream_t st) {
+    sph_kofs_kernel<<<blocks_of(K_pad, 256), 256, 0, st>>>(ps, kp, K_pad, nq, NL, NLM, kofs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sph_wdense(const PairSetDev &ps, const double *coef64, int SB, int S, const SphParity &kp,
+                              int n_sub, const double2 *theta, int64_t K_pad, double2 *A, cudaStream_t st) {
+    const int64_t tot = (int64_t)S * n_sub * K_pad;
+    if (tot == 0) return cudaSuccess;
+    sph_wdense_kernel<<<blocks_of(tot, 256), 256, 0, st>>>(ps, coef64, SB, S, kp, n_sub, theta, K_pad, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sph_gaunt(const void *Ze, const void *Zo, int ne, int no, int fp64, int S, int nq, int NLM,
+                             int NR, const int *goff, const int2 *gidx, const double *gval, double scale, double2 *R,
+                             cudaStream_t st) {
     const int64_t tot = (int64_t)S * nq * NR;
     if (tot == 0) return cudaSuccess;
     if (fp64)
-        sph_gaunt_kernel<double2><<<blocks_of(tot, 256), 256, 0, st>>>((const double2 *)Z, S, nq, NLAM, NLM, NR,
-                                                                       goff, gidx, gval, scale, R);
+        sph_gaunt_kernel<double2><<<blocks_of(tot, 256), 256, 0, st>>>(
+            (const double2 *)Ze, (const double2 *)Zo, ne, no, S, nq, NLM, NR, goff, gidx, gval, scale, R);
     else
-        sph_gaunt_kernel<float2><<<blocks_of(tot, 256), 256, 0, st>>>((const float2 *)Z, S, nq, NLAM, NLM, NR, goff,
-                                                                      gidx, gval, scale, R);
+        sph_gaunt_kernel<float2><<<blocks_of(tot, 256), 256, 0, st>>>(
+            (const float2 *)Ze, (const float2 *)Zo, ne, no, S, nq, NLM, NR, goff, gidx, gval, scale, R);
     return cudaGetLastError();
 }
 
@@ -398,11 +448,13 @@ cudaError_t launch_sph_r_to_f32(const double2 *R, int64_t n, float2 *out, cudaSt
 cudaError_t launch_sph_angular_tables(const double *theta, int nt, const double *phi, int np, int lmax, int fp64,
                                       void *T1, void *T2, cudaStream_t st) {
     if (fp64) {
-        sph_theta_table_kernel<double2><<<blocks_of(nt, 64), 64, 0, st>>>(theta, nt, lmax, (double2 *)T1);
+        sph_theta_table_kernel<double2><<<blocks_of((int64_t)nt * (lmax + 1), 128), 128, 0, st>>>(theta, nt, lmax,
+                                                                                                  (double2 *)T1);
         sph_phi_table_kernel<double2><<<blocks_of((int64_t)(2 * lmax + 1) * np, 256), 256, 0, st>>>(
             phi, np, lmax, (double2 *)T2);
     } else {
-        sph_theta_table_kernel<float2><<<blocks_of(nt, 64), 64, 0, st>>>(theta, nt, lmax, (float2 *)T1);
+        sph_theta_table_kernel<float2><<<blocks_of((int64_t)nt * (lmax + 1), 128), 128, 0, st>>>(theta, nt, lmax,
+                                                                                                 (float2 *)T1);
         sph_phi_table_kernel<float2><<<blocks_of((int64_t)(2 * lmax + 1) * np, 256), 256, 0, st>>>(
             phi, np, lmax, (float2 *)T2);
     }

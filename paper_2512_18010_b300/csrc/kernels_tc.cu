@@ -908,57 +908,74 @@ static void dense_image_t(const TcGenericArgs &a, int M_pad, int64_t K_pad, int 
                                                                                  nkc, img);
 }
 
-cudaError_t tc_run_generic(const TcGenericArgs &a, int64_t *launches, cudaStream_t st) {
+cudaError_t tc_run_generic_multi(const TcGenericArgs *jobs, int n_jobs, int64_t *launches, cudaStream_t st) {
     using namespace tc;
-    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
-    const int64_t K_pad = tc_generic_kpad(a.kind, a.K);
-    const int BK = a.kind == KIND_TF32X2 ? bk_of<KIND_TF32X2>() : bk_of<KIND_BF16X3>();
-    const int nkc = (int)(K_pad / BK);
-    const int n_mt = (a.M + BM - 1) / BM, M_pad = n_mt * BM;
-    const int n_nt = (int)((a.N + BN - 1) / BN);
-    const size_t img_bytes = (size_t)n_mt * nkc * a_stage_of(a.kind);
-    const size_t img_al = (img_bytes + 1023) / 1024 * 1024;
-    std::vector<int4> items;
-    TcJobDev jd;
-    memset(&jd, 0, sizeof(jd));
-    uint8_t *img = static_cast<uint8_t *>(a.ws);
-    jd.A = img;
-    jd.Y = a.Y;
-    jd.Z = a.Z;
-    jd.kofs = a.kofs;
-    jd.nz = a.nz;
-    jd.ny = 0;
-    jd.nx = a.nx;
-    jd.nkc = nkc;
-    jd.M = a.M;
-    jd.n_mt = n_mt;
-    jd.n_nt = n_nt;
-    jd.ylm = a.ylm;
-    jd.ystride = a.ystride;
-    jd.N = a.N;
-    jd.nq = (int64_t)a.nx * a.N;
-    jd.scale = a.scale;
-    jd.f = a.C;
-    jd.f2 = a.C2;
-    tc_build_items(&jd, 1, items);
-    const size_t need = img_al + 256 + sizeof(int4) * items.size();
-    if (need > a.ws_bytes) return cudaErrorInvalidValue;
-    switch (a.kind) {
-    case KIND_BF16X2: dense_image_t<KIND_BF16X2>(a, M_pad, K_pad, nkc, img, st); break;
-    case KIND_BF16X3: dense_image_t<KIND_BF16X3>(a, M_pad, K_pad, nkc, img, st); break;
-    default: dense_image_t<KIND_TF32X2>(a, M_pad, K_pad, nkc, img, st); break;
+    if (n_jobs <= 0) return cudaSuccess;
+    const TcGenericArgs &a0 = jobs[0];
+    const int BK = a0.kind == KIND_TF32X2 ? bk_of<KIND_TF32X2>() : bk_of<KIND_BF16X3>();
+    std::vector<TcJobDev> descs;
+    std::vector<size_t> img_off;
+    size_t off = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const TcGenericArgs &a = jobs[j];
+        if (a.kind != a0.kind || a.ws != a0.ws) return cudaErrorInvalidValue;
+        if (a.M <= 0 || a.N <= 0) continue;
+        const int64_t K_pad = tc_generic_kpad(a.kind, a.K);
+        const int nkc = (int)(K_pad / BK);
+        const int n_mt = (a.M + BM - 1) / BM;
+        const int n_nt = (int)((a.N + BN - 1) / BN);
+        TcJobDev jd;
+        memset(&jd, 0, sizeof(jd));
+        jd.A = static_cast<uint8_t *>(a0.ws) + off;
+        jd.Y = a.Y;
+        jd.Z = a.Z;
+        jd.kofs = a.kofs;
+        jd.nz = a.nz;
+        jd.nx = a.nx;
+        jd.nkc = nkc;
+        jd.M = a.M;
+        jd.n_mt = n_mt;
+        jd.n_nt = n_nt;
+        jd.ylm = a.ylm;
+        jd.ystride = a.ystride;
+        jd.N = a.N;
+        jd.nq = (int64_t)a.nx * a.N;
+        jd.scale = a.scale;
+        jd.f = a.C;
+        jd.f2 = a.C2;
+        img_off.push_back(off);
+        descs.push_back(jd);
+        off += ((size_t)n_mt * nkc * a_stage_of(a.kind) + 1023) / 1024 * 1024;
+        // split-and-swizzle image of this job's A
+        const int M_pad = n_mt * BM;
+        uint8_t *img = static_cast<uint8_t *>(a0.ws) + img_off.back();
+        switch (a.kind) {
+        case KIND_BF16X2: dense_image_t<KIND_BF16X2>(a, M_pad, K_pad, nkc, img, st); break;
+        case KIND_BF16X3: dense_image_t<KIND_BF16X3>(a, M_pad, K_pad, nkc, img, st); break;
+        default: dense_image_t<KIND_TF32X2>(a, M_pad, K_pad, nkc, img, st); break;
+        }
+        if (launches) ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    if (launches) ++*launches;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    TcJobDev *d_job = reinterpret_cast<TcJobDev *>(img + img_al);
-    int4 *d_items = reinterpret_cast<int4 *>(img + img_al + 256);
-    e = cudaMemcpyAsync(d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, st);
+    if (descs.empty()) return cudaSuccess;
+    std::vector<int4> items;
+    tc_build_items(descs.data(), (int)descs.size(), items);
+    uint8_t *tail = static_cast<uint8_t *>(a0.ws) + off;
+    const size_t dbytes = (sizeof(TcJobDev) * descs.size() + 255) / 256 * 256;
+    if (off + dbytes + sizeof(int4) * items.size() > a0.ws_bytes) return cudaErrorInvalidValue;
+    TcJobDev *d_jobs = reinterpret_cast<TcJobDev *>(tail);
+    int4 *d_items = reinterpret_cast<int4 *>(tail + dbytes);
+    cudaError_t e = cudaMemcpyAsync(d_jobs, descs.data(), sizeof(TcJobDev) * descs.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    return tc_launch_persistent(a.kind, d_job, d_items, (int)items.size(), a.drain_every, a.err, tc_num_sms(),
+    return tc_launch_persistent(a0.kind, d_jobs, d_items, (int)items.size(), a0.drain_every, a0.err, tc_num_sms(),
                                 launches, st);
+}
+
+cudaError_t tc_run_generic(const TcGenericArgs &a, int64_t *launches, cudaStream_t st) {
+    return tc_run_generic_multi(&a, 1, launches, st);
 }
 
 }  // namespace scff

@@ -55,6 +55,25 @@ __host__ __device__ inline void plm_all(int lmax, double x, double *p) {
     }
 }
 
+// One column m >= 0 of the same functions: col[l - m] = p_l^m(x) for l = m..lmax.
+__host__ __device__ inline void plm_column(int lmax, int m, double x, double *col) {
+    const double s = sqrt(fmax(0.0, 1.0 - x * x));
+    double pmm = 0.28209479177387814;
+    for (int k = 1; k <= m; ++k) pmm = -sqrt((2.0 * k + 1.0) / (2.0 * k)) * s * pmm;
+    col[0] = pmm;
+    if (m + 1 > lmax) return;
+    double pl2 = pmm, pl1 = sqrt(2.0 * m + 3.0) * x * pmm;
+    col[1] = pl1;
+    for (int l = m + 2; l <= lmax; ++l) {
+        const double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+        const double b = sqrt(((double)(l - 1) * (l - 1) - (double)m * m) / (4.0 * (l - 1) * (l - 1) - 1.0));
+        const double pl = a * (x * pl1 - b * pl2);
+        col[l - m] = pl;
+        pl2 = pl1;
+        pl1 = pl;
+    }
+}
+
 // p_l^m for any sign of m: Y_l^{-m} = (-1)^m conj(Y_l^m), so with
 // Y_l^m = p_l^m e^{i m phi} for every m, p_l^{-m} = (-1)^m p_l^m.
 __host__ __device__ inline double plm_signed(const double *p, int l, int m) {
@@ -85,6 +104,7 @@ __host__ __device__ inline void sph_bessel_all(int nl, double x, double *j) {
         return;
     }
     const int start = (nl > (int)x ? nl : (int)x) + 24 + (int)(2.0 * sqrt(x + 1.0));
+    const double invx = 1.0 / x;
     double fp1 = 0.0, f = 1e-30, sum = 0.0, f0 = 0.0, f1 = 0.0;
     // downward sweep; f holds the unnormalised j_L, rescaled to avoid overflow
     for (int L = start; L >= 0; --L) {
@@ -92,7 +112,7 @@ __host__ __device__ inline void sph_bessel_all(int nl, double x, double *j) {
         if (L == 1) f1 = f;
         if (L == 0) f0 = f;
         sum += (2.0 * L + 1.0) * f * f;
-        const double fm1 = (2.0 * L + 1.0) / x * f - fp1;
+        const double fm1 = (2.0 * L + 1.0) * invx * f - fp1;
         fp1 = f;
         f = fm1;
         if (fabs(f) > 1e140) {

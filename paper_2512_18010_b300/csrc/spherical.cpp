@@ -133,7 +133,8 @@ namespace {
 // lambda <= lam, |l - lambda| <= L <= l + lambda with lambda + L + l even.  The
 // integrand is a polynomial of degree lambda + L + l <= 92, so 64
 // Gauss-Legendre nodes integrate it exactly.  Entries are grouped by output
-// (l, m) in CSR form.
+// (l, m) in CSR form; an entry holds (index of (lambda, mu) among the
+// harmonics of lambda's parity | parity << 16, index of (L, M)).
 scff_status build_gaunt(SphCache *cache, int lmax, int lam) {
     const int Lmax = lmax + lam;
     std::vector<double> gx, gw;
@@ -160,7 +161,7 @@ scff_status build_gaunt(SphCache *cache, int lmax, int lam) {
                         }
                         g *= 2.0 * M_PI;
                         if (fabs(g) < 1e-15) continue;
-                        idx.push_back(make_int2(sph::lm_index(la, mu), sph::lm_index(L, M)));
+                        idx.push_back(make_int2(sph_parity_sub(la, mu) | ((la & 1) << 16), sph::lm_index(L, M)));
                         val.push_back(g);
                     }
                 }
@@ -246,11 +247,23 @@ extern "C" scff_status scff_spherical(scff_ctx *c, scff_basis_h b, scff_trans_h 
     int lam = 0;
     for (int L = 0; L < kNumClasses; ++L)
         if (ps.pair_off[L + 1] > ps.pair_off[L]) lam = L;
-    const int Lmax = lmax + lam, NL = Lmax + 1, NLM = NL * NL, NLAM = (lam + 1) * (lam + 1);
+    const int Lmax = lmax + lam, NL = Lmax + 1, NLM = NL * NL;
     const int NR = (lmax + 1) * (lmax + 1);
     const int64_t K = ps.n_axrows;
     const int kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
-    const int64_t K_pad = tc ? tc_generic_kpad(kind, K) : K;
+    // the even and odd parity jobs: rows (s, lambda mu of that parity), k = (pair, n of that parity)
+    SphParity kp[2];
+    int nsub[2];
+    int64_t Kj[2], Kj_pad[2];
+    for (int par = 0; par < 2; ++par) {
+        kp[par].par = par;
+        kp[par].off[0] = 0;
+        for (int L = 0; L < kNumClasses; ++L)
+            kp[par].off[L + 1] = kp[par].off[L] + (int64_t)(ps.pair_off[L + 1] - ps.pair_off[L]) * sph_parity_count(L, par);
+        Kj[par] = kp[par].off[kNumClasses];
+        Kj_pad[par] = tc ? tc_generic_kpad(kind, Kj[par]) : std::max<int64_t>(Kj[par], 1);
+        nsub[par] = sph_parity_rows(lam, par);
+    }
     if ((K + 1) * nq * (int64_t)NL >= INT32_MAX || (int64_t)(ps.n_pair + 1) * NLM >= INT32_MAX)
         return sfail(SCFF_ERR_INVALID_ARG, "scff_spherical: tables exceed 2^31 entries (split the radial grid)");
     SphCache *cache = nullptr;
@@ -261,7 +274,7 @@ extern "C" scff_status scff_spherical(scff_ctx *c, scff_basis_h b, scff_trans_h 
     // ---- workspace plan
     const size_t el = fp64 ? sizeof(double2) : sizeof(float2);
     const int SB = 4, S_pad = (S + SB - 1) / SB * SB;
-    const int M = S * NLAM, M2 = S * nq;
+    const int M2 = S * nq;
     const int64_t NZ = (int64_t)nq * NLM;
     const int64_t K2 = NR, K2_pad = tc ? tc_generic_kpad(kind, K2) : K2;
     size_t o = 0;
@@ -270,15 +283,23 @@ extern "C" scff_status scff_spherical(scff_ctx *c, scff_basis_h b, scff_trans_h 
     const size_t o_q = o;      o = up256(o + sizeof(double) * (size_t)(nq + nt + np));
     const size_t o_rho = o;    o = up256(o + el * (size_t)(K + 1) * nq * NL);
     const size_t o_y = o;      o = up256(o + el * (size_t)(ps.n_pair + 1) * NLM);
-    const size_t o_kofs = o;   o = up256(o + sizeof(int2) * (size_t)K_pad);
-    const size_t o_A = o;      o = up256(o + sizeof(double2) * (size_t)M * K_pad);
-    const size_t o_Z = o;      o = up256(o + el * (size_t)M * NZ);
+    size_t o_kofs[2], o_A[2], o_Z[2];
+    for (int par = 0; par < 2; ++par) {
+        o_kofs[par] = o;
+        o = up256(o + sizeof(int2) * (size_t)Kj_pad[par]);
+        o_A[par] = o;
+        o = up256(o + sizeof(double2) * (size_t)S * nsub[par] * Kj_pad[par]);
+        o_Z[par] = o;
+        o = up256(o + el * (size_t)S * nsub[par] * NZ);
+    }
     const size_t o_R = o;      o = up256(o + sizeof(double2) * (size_t)M2 * NR);
     const size_t o_T1 = o;     o = up256(o + el * (size_t)(NR + 1) * std::max(nt, 1));
     const size_t o_T2 = o;     o = up256(o + el * (size_t)(2 * lmax + 2) * std::max(np, 1));
     const size_t o_k2 = o;     o = up256(o + sizeof(int2) * (size_t)K2_pad);
-    const size_t tcw = tc ? std::max(tc_generic_bytes(kind, M, K), tc_generic_bytes(kind, M2, K2)) +
-                                sizeof(int4) * (size_t)((M + 127) / 128 + (M2 + 127) / 128) *
+    const size_t tcw = tc ? std::max(tc_generic_bytes(kind, S * nsub[0], Kj[0]) + tc_generic_bytes(kind, S * nsub[1], Kj[1]),
+                                     tc_generic_bytes(kind, M2, K2)) +
+                                sizeof(int4) * (size_t)((S * nsub[0] + 127) / 128 + (S * nsub[1] + 127) / 128 +
+                                                        (M2 + 127) / 128) *
                                     (size_t)((std::max<int64_t>(NZ, (int64_t)nt * np) + 127) / 128) + 4096
                           : 0;
     const size_t o_tc = o;     o = up256(o + tcw);
@@ -307,9 +328,7 @@ extern "C" scff_status scff_spherical(scff_ctx *c, scff_basis_h b, scff_trans_h 
     double *geom = reinterpret_cast<double *>(w + o_geom);
     double *dq = reinterpret_cast<double *>(w + o_q), *dth = dq + nq, *dph = dth + nt;
     void *rho = w + o_rho, *ytab = w + o_y, *T1 = w + o_T1, *T2 = w + o_T2;
-    int2 *kofs = reinterpret_cast<int2 *>(w + o_kofs), *kofs2 = reinterpret_cast<int2 *>(w + o_k2);
-    double2 *A = reinterpret_cast<double2 *>(w + o_A);
-    void *Z = w + o_Z;
+    int2 *kofs2 = reinterpret_cast<int2 *>(w + o_k2);
     double2 *R64 = reinterpret_cast<double2 *>(w + o_R);
     uint8_t *outs = w + o_out;
     void *dR = out_on_device ? R_out : (R_out ? (void *)outs : nullptr);
@@ -333,56 +352,69 @@ extern "C" scff_status scff_spherical(scff_ctx *c, scff_basis_h b, scff_trans_h 
     SCUDA(cudaMemsetAsync(static_cast<uint8_t *>(ytab) + el * (size_t)ps.n_pair * NLM, 0, el * (size_t)NLM, st));
     SCUDA(launch_sph_radial(ps, geom, dq, nq, NL, fp64 ? 1 : 0, rho, st));
     SCUDA(launch_sph_ypair(ps, geom, Lmax, fp64 ? 1 : 0, ytab, st));
-    SCUDA(launch_sph_kofs(ps, K_pad, nq, NL, NLM, kofs, st));
-    SCUDA(launch_sph_wdense(ps, coef, SB, S, NLAM, cache->theta, K_pad, A, st));
-    c->launches += 4;
-    // ---- Z = W (rho y): the dense contraction over (pair, n)
+    c->launches += 2;
+    for (int par = 0; par < 2; ++par) {
+        if (nsub[par] == 0) continue;
+        SCUDA(launch_sph_kofs(ps, kp[par], Kj_pad[par], nq, NL, NLM, reinterpret_cast<int2 *>(w + o_kofs[par]), st));
+        SCUDA(launch_sph_wdense(ps, coef, SB, S, kp[par], nsub[par], cache->theta, Kj_pad[par],
+                                reinterpret_cast<double2 *>(w + o_A[par]), st));
+        c->launches += 2;
+    }
+    // ---- Z = W (rho y): the dense contraction over (pair, n), one job per parity
     if (fp64) {
-        Gemm64Args g;
-        memset(&g, 0, sizeof(g));
-        g.A = A;
-        g.lda = K_pad;
-        g.K = K;
-        g.M = M;
-        g.nx = NLAM;
-        g.Y = static_cast<const double2 *>(rho);
-        g.Z = static_cast<const double2 *>(ytab);
-        g.kofs = kofs;
-        g.nz = NLM;
-        g.ylm = 1;
-        g.ystride = NL;
-        g.N = NZ;
-        g.scale = 1.0;
-        g.C = static_cast<double2 *>(Z);
-        SCUDA(launch_gen_gemm64(g, st));
-        ++c->launches;
+        for (int par = 0; par < 2; ++par) {
+            if (nsub[par] == 0) continue;
+            Gemm64Args g;
+            memset(&g, 0, sizeof(g));
+            g.A = reinterpret_cast<const double2 *>(w + o_A[par]);
+            g.lda = Kj_pad[par];
+            g.K = Kj[par];
+            g.M = S * nsub[par];
+            g.nx = nsub[par];
+            g.Y = static_cast<const double2 *>(rho);
+            g.Z = static_cast<const double2 *>(ytab);
+            g.kofs = reinterpret_cast<const int2 *>(w + o_kofs[par]);
+            g.nz = NLM;
+            g.ylm = 1;
+            g.ystride = NL;
+            g.N = NZ;
+            g.scale = 1.0;
+            g.C = reinterpret_cast<double2 *>(w + o_Z[par]);
+            SCUDA(launch_gen_gemm64(g, st));
+            ++c->launches;
+        }
     } else {
-        TcGenericArgs g;
-        memset(&g, 0, sizeof(g));
-        g.kind = kind;
-        g.A = A;
-        g.lda = K_pad;
-        g.K = K;
-        g.M = M;
-        g.nx = NLAM;
-        g.Y = static_cast<const float2 *>(rho);
-        g.Z = static_cast<const float2 *>(ytab);
-        g.kofs = kofs;
-        g.nz = NLM;
-        g.ylm = 1;
-        g.ystride = NL;
-        g.N = NZ;
-        g.scale = 1.0f;
-        g.C = static_cast<float2 *>(Z);
-        g.drain_every = c->drain_every >= 0 ? c->drain_every : 8;
-        g.err = c->d_err;
-        g.ws = w + o_tc;
-        g.ws_bytes = tcw;
-        SCUDA(tc_run_generic(g, &c->launches, st));
+        TcGenericArgs g[2];
+        int nj = 0;
+        for (int par = 0; par < 2; ++par) {
+            if (nsub[par] == 0) continue;
+            TcGenericArgs &a = g[nj++];
+            memset(&a, 0, sizeof(a));
+            a.kind = kind;
+            a.A = reinterpret_cast<const double2 *>(w + o_A[par]);
+            a.lda = Kj_pad[par];
+            a.K = Kj[par];
+            a.M = S * nsub[par];
+            a.nx = nsub[par];
+            a.Y = static_cast<const float2 *>(rho);
+            a.Z = static_cast<const float2 *>(ytab);
+            a.kofs = reinterpret_cast<const int2 *>(w + o_kofs[par]);
+            a.nz = NLM;
+            a.ylm = 1;
+            a.ystride = NL;
+            a.N = NZ;
+            a.scale = 1.0f;
+            a.C = reinterpret_cast<float2 *>(w + o_Z[par]);
+            a.drain_every = c->drain_every >= 0 ? c->drain_every : 8;
+            a.err = c->d_err;
+            a.ws = w + o_tc;
+            a.ws_bytes = tcw;
+        }
+        SCUDA(tc_run_generic_multi(g, nj, &c->launches, st));
     }
     // ---- R = Gaunt-coupled Z (scaled), then the outputs that follow from it
-    SCUDA(launch_sph_gaunt(Z, fp64 ? 1 : 0, S, nq, NLAM, NLM, NR, cache->goff, cache->gidx, cache->gval, scale, R64,
-                           st));
+    SCUDA(launch_sph_gaunt(w + o_Z[0], w + o_Z[1], nsub[0], nsub[1], fp64 ? 1 : 0, S, nq, NLM, NR, cache->goff,
+                           cache->gidx, cache->gval, scale, R64, st));
     ++c->launches;
     if (dR) {
         if (fp64)

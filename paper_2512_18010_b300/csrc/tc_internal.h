@@ -92,5 +92,9 @@ struct TcGenericArgs {
 int64_t tc_generic_kpad(int kind, int64_t K);
 size_t tc_generic_bytes(int kind, int M, int64_t K);
 cudaError_t tc_run_generic(const TcGenericArgs &a, int64_t *launches, cudaStream_t st);
+// Several such contractions (same kind, same workspace) in one persistent
+// launch; the workspace holds their images back to back, then the
+// descriptors and the work list (tc_generic_bytes summed, plus the list).
+cudaError_t tc_run_generic_multi(const TcGenericArgs *jobs, int n_jobs, int64_t *launches, cudaStream_t st);
 
 }  // namespace scff

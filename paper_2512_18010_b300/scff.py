@@ -436,12 +436,15 @@ class Context:
         return out[:, 0] + 1j * out[:, 1]
 
     def spherical(self, basis: Basis, trans: Transitions, q, lmax: int, theta=None, phi=None,
-                  precision=FP64, scale: float = 1.0, want=("R", "f", "f2", "iso")) -> dict:
+                  precision=FP64, scale: float = 1.0, want=("R", "f", "f2", "iso"), out: str = "host",
+                  stream=None) -> dict:
         """Spherical method: R_lm(q), and on an angular grid f and |f|^2, and the isotropic average.
 
-        Returns host arrays: "R" complex [S, n_q, (lmax+1)^2], "f" complex
-        [S, n_q, n_theta, n_phi], "f2" [S, n_q, n_theta, n_phi], "iso" [S, n_q]
-        (those in `want`; f and f2 only with an angular grid).
+        Returns "R" complex [S, n_q, (lmax+1)^2], "f" complex [S, n_q, n_theta,
+        n_phi], "f2" [S, n_q, n_theta, n_phi], "iso" [S, n_q] (those in
+        `want`; f and f2 only with an angular grid): numpy arrays, or with
+        out="cuda" the raw torch tensors written on the device (complex
+        values as a trailing axis of 2).
         """
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
@@ -450,16 +453,27 @@ class Context:
         ph = _np(phi if phi is not None else np.zeros(0), np.float64)
         S, nq, nt, npf = trans.n_states, len(q), len(th), len(ph)
         NR = (lmax + 1) ** 2
-        rdt = np.float64 if precision == FP64 else np.float32
         angular = nt > 0 and npf > 0
-        R = np.zeros((S, nq, NR, 2), rdt) if "R" in want else None
-        f = np.zeros((S, nq, nt, npf, 2), rdt) if ("f" in want and angular) else None
-        f2 = np.zeros((S, nq, nt, npf), rdt) if ("f2" in want and angular) else None
-        iso = np.zeros((S, nq), rdt) if "iso" in want else None
+        shapes = {"R": (S, nq, NR, 2), "f": (S, nq, nt, npf, 2), "f2": (S, nq, nt, npf), "iso": (S, nq)}
+        keys = [k for k in ("R", "f", "f2", "iso") if k in want and (angular or k in ("R", "iso"))]
         g = _SphGrid(int(lmax), nq, _p(q), nt, _p(th) if nt else None, npf, _p(ph) if npf else None)
-        ptr = lambda a: None if a is None else _p(a)  # noqa: E731
+        if out == "cuda":
+            import torch
+            tdt = torch.float64 if precision == FP64 else torch.float32
+            bufs = {k: torch.empty(shapes[k], dtype=tdt, device="cuda") for k in keys}
+            ptr = lambda k: ctypes.c_void_p(bufs[k].data_ptr()) if k in bufs else None  # noqa: E731
+            if stream is None:
+                stream = torch.cuda.current_stream()
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+            _check(self.lib.scff_spherical(self.h, basis.handle, trans.handle, ctypes.byref(g), int(precision),
+                                           float(scale), ptr("R"), ptr("f"), ptr("f2"), ptr("iso"), 1, sp))
+            return bufs
+        rdt = np.float64 if precision == FP64 else np.float32
+        arrs = {k: np.zeros(shapes[k], rdt) for k in keys}
+        ptr = lambda k: _p(arrs[k]) if k in arrs else None  # noqa: E731
         _check(self.lib.scff_spherical(self.h, basis.handle, trans.handle, ctypes.byref(g), int(precision),
-                                       float(scale), ptr(R), ptr(f), ptr(f2), ptr(iso), 0, None))
+                                       float(scale), ptr("R"), ptr("f"), ptr("f2"), ptr("iso"), 0, None))
+        R, f, f2, iso = (arrs.get(k) for k in ("R", "f", "f2", "iso"))
         out = {}
         if R is not None:
             out["R"] = R[..., 0] + 1j * R[..., 1]
