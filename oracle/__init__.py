@@ -53,6 +53,10 @@ def _load():
         lib.scff_oracle_prim_norm.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.scff_oracle_prim_norm.restype = ctypes.c_double
         lib.scff_oracle_nbf.argtypes = [ctypes.c_int, P, ctypes.c_int]
+        lib.scff_oracle_density.argtypes = [
+            ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+            ctypes.c_int, P, ctypes.c_int64, P, ctypes.c_double, P, ctypes.c_int]
+        lib.scff_oracle_density.restype = ctypes.c_int
         lib.scff_oracle_nbf.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -93,6 +97,26 @@ def form_factor(mol, T: np.ndarray, q: np.ndarray, scale: float = 1.0,
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
     return out[..., 0] + 1j * out[..., 1]
+
+
+def density(mol, T: np.ndarray, r: np.ndarray, scale: float = 1.0, renorm: bool = True,
+            threads: int = 0) -> np.ndarray:
+    """Phi[s, ir] = scale * sum T^s[mu][nu] phi_mu(r) phi_nu(r) at points r[n, 3]."""
+    lib = _load()
+    xyz = _c(mol.xyz, np.float64)
+    sa, sl, sn = _c(mol.shell_atom, np.int32), _c(mol.shell_l, np.int32), _c(mol.shell_nprim, np.int32)
+    ex, co = _c(mol.exponents, np.float64), _c(mol.coefficients, np.float64)
+    T = _c(T, np.float64)
+    if T.ndim == 2:
+        T = T[None]
+    r = _c(r, np.float64).reshape(-1, 3)
+    out = np.zeros((T.shape[0], r.shape[0]), dtype=np.float64)
+    rc = lib.scff_oracle_density(mol.n_atoms, _ptr(xyz), mol.n_shells, _ptr(sa), _ptr(sl), _ptr(sn),
+                                 _ptr(ex), _ptr(co), _flags(mol, renorm), T.shape[0], _ptr(T), r.shape[0],
+                                 _ptr(r), float(scale), _ptr(out), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the input (code {rc})")
+    return out
 
 
 def functions(mol, renorm: bool = True):

@@ -411,3 +411,61 @@ int scff_oracle_functions(int n_atoms, int n_shells, const int32_t *shell_atom,
 }
 
 int scff_oracle_version(void) { return 1; }
+
+/*
+ * Transition densities Phi_s(r) = scale * sum_{mu,nu} T^s[mu][nu] phi_mu(r) phi_nu(r)
+ * at n_r points r[n_r][3] (the real-space integrand of Eq. fSreal, which the
+ * FFT method tabulates).  out[s][ir].  Same basis conventions and flags as
+ * scff_oracle_form_factor.  Returns 0 or a negative error code.
+ */
+int scff_oracle_density(int n_atoms, const double *xyz, int n_shells, const int32_t *shell_atom,
+                        const int32_t *shell_l, const int32_t *shell_nprim, const double *exps,
+                        const double *coefs, int flags, int n_states, const double *T, int64_t n_r,
+                        const double *r, double scale, double *out, int n_threads) {
+    if (n_atoms <= 0 || n_shells <= 0 || n_states <= 0 || n_r < 0 || !xyz || !T || !out) return ORACLE_EINVAL;
+    ofn_t *fns = NULL;
+    int nbf = 0;
+    int rc = build_functions(n_atoms, n_shells, shell_atom, shell_l, shell_nprim, exps, coefs, flags, &fns, &nbf);
+    if (rc) return rc;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    int fail = 0;
+#pragma omp parallel
+    {
+        double *phi = (double *)malloc(sizeof(double) * (size_t)nbf);
+        if (!phi) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t ir = 0; ir < n_r; ++ir) {
+            if (!phi) continue;
+            const double *rv = r + 3 * ir;
+            for (int mu = 0; mu < nbf; ++mu) {
+                const ofn_t *fn = &fns[mu];
+                const double *A = xyz + 3 * fn->atom;
+                const double d[3] = {rv[0] - A[0], rv[1] - A[1], rv[2] - A[2]};
+                const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double ang = 0.0;
+                for (int t = 0; t < fn->nterm; ++t)
+                    ang += fn->k[t] * pow(d[0], fn->pw[t][0]) * pow(d[1], fn->pw[t][1]) * pow(d[2], fn->pw[t][2]);
+                double rad = 0.0;
+                for (int k = 0; k < fn->nprim; ++k) rad += fn->w[k] * exp(-fn->alpha[k] * r2);
+                phi[mu] = ang * rad;
+            }
+            for (int s = 0; s < n_states; ++s) {
+                long double acc = 0.0L;
+                const double *Ts = T + (size_t)s * nbf * nbf;
+                for (int mu = 0; mu < nbf; ++mu)
+                    for (int nu = 0; nu < nbf; ++nu) acc += (long double)Ts[(size_t)mu * nbf + nu] * phi[mu] * phi[nu];
+                out[(size_t)s * n_r + ir] = (double)(scale * acc);
+            }
+        }
+        free(phi);
+    }
+    free_functions(fns, nbf);
+    return fail ? ORACLE_ENOMEM : ORACLE_OK;
+}
