@@ -334,6 +334,41 @@ scff_status scff_spherical(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans
                            int out_on_device, void *stream);
 
 /*
+ * FFT method (Sec. "The (Fast) Fourier Transform", Eqs. Falbega, continuFFT,
+ * fftABC, qabc; Sec. "Fast Fourier Transform Method"): the transition density
+ * Phi_s(r) = sum T^s_{mu nu} phi_mu(r) phi_nu(r) is tabulated on a box of
+ * n[i] points per axis (powers of two, 4..1024), side L_i = 2 pi / dq[i],
+ * centred at centre[i] (x_a = centre - L/2 + a L/n), and
+ *   f_s(q) = scale * V_pix * sum_a Phi_s(x_a) e^{+i q.x_a},
+ *   q = dq * (alpha - n/2), alpha = 0..n-1 per axis (ascending),
+ * V_pix = prod_i L_i / n_i: the discrete Fourier sum that approximates Eq.
+ * fSreal up to aliasing (spacing L/n too coarse for the densest Gaussians)
+ * and tiling (box too small); the analytic methods have neither error.
+ *   threshold  > 0: a primitive is dropped at points where its Gaussian
+ *              factor exp(-alpha |r - A|^2) is below threshold (the paper's
+ *              tabulation thresholding); 0 tabulates exactly.
+ * Outputs (element type double for SCFF_FP64, float for SCFF_FP32; other
+ * precisions give SCFF_ERR_INVALID_ARG):
+ *   f_out  [S][n0][n1][n2][2], f2_out [S][n0][n1][n2] (either may be NULL);
+ *   parseval_out [S][2] host doubles or NULL: (sum |Phi|^2 V_pix,
+ *   sum |f|^2 dq0 dq1 dq2 / (2 pi)^3), equal for an exact discrete transform
+ *   (Sec. "Verification", Parseval's theorem).
+ * The basis may have at most ~1500 Cartesian functions (FP32; ~750 in FP64)
+ * so that one tile's function values fit in shared memory.  The call
+ * returns after `stream` has finished.
+ */
+typedef struct {
+    int n[3];
+    double dq[3];
+    double centre[3];
+    double threshold;
+} scff_fft_grid;
+
+scff_status scff_fft_form_factor(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans, const scff_fft_grid *grid,
+                                 int precision, double scale, void *f_out, void *f2_out, double *parseval_out,
+                                 int out_on_device, void *stream);
+
+/*
  * Error-bounded pair screening (the exact-tolerance form of the paper's
  * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
  * first scff_form_factor call for a (transitions, grid extent) bounds every

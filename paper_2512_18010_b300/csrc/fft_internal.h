@@ -1,0 +1,53 @@
+// Internal interface of the FFT method (kernels_fft.cu, fft_method.cpp).
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "scff_internal.h"
+
+namespace scff {
+
+// Density tabulation: Phi_s(x_a) for the n[0] x n[1] x n[2] box points into
+// out[(s / 2) * npts + p][s % 2] (two states per complex field).
+struct FftDensityArgs {
+    PairSetDev ps;             // records of the basis (Cartesian components)
+    int nbf, nbf_pad;          // Cartesian functions; padded to a multiple of 32
+    int S;
+    const void *T;             // [S][nbf][nbf] Cartesian transition matrices, float or double
+    void *out;                 // packed complex fields, float or double pairs
+    double xmin[3], dx[3];
+    int nx, ny, nz;
+    int64_t npts;
+    double cut;                // drop a primitive where alpha |r - A|^2 > cut (0 = never)
+    double scale, vpix;
+    double *parseval;          // [S][2] (real-space sums accumulated here) or null
+};
+
+struct FftAxisArgs {
+    void *data;                // complex fields (float2 or double2), in place
+    int n, logn, W;            // line length, log2, lines per CTA
+    int64_t es;                // element stride along the line
+    int64_t inner;             // lines adjacent in memory (stride 1) per block when es > 1
+    int64_t block_stride;      // distance between consecutive such blocks
+};
+
+struct FftUnpackArgs {
+    const void *data;          // transformed fields
+    int S;
+    int n[3];
+    double dq[3], xmin[3];
+    double vpix;
+    double dq3_over_2pi3;
+    void *f, *f2;              // [S][n0][n1][n2] complex and |f|^2 (float or double), either may be null
+    double *parseval;          // [S][2] (momentum-space sums accumulated here) or null
+};
+
+size_t fft_density_smem(int fp64, int nbf_pad, int tp);
+cudaError_t launch_fft_density(const FftDensityArgs &a, int fp64, int tp, cudaStream_t st);
+cudaError_t launch_fft_axis(const FftAxisArgs &a, int fp64, int64_t n_groups, cudaStream_t st);
+cudaError_t launch_fft_unpack(const FftUnpackArgs &a, int fp64, cudaStream_t st);
+cudaError_t launch_cast_f64_to_f32(const double *in, int64_t n, float *out, cudaStream_t st);
+
+}  // namespace scff

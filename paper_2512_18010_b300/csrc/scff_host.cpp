@@ -184,7 +184,7 @@ extern "C" void scff_destroy(scff_ctx *c) {
     for (auto *g : c->grids) free_grid(g);
     for (auto *p : c->plans) free_plan_any(p);
     scff_sph_cache_free(c->sph);
-    DevBuf *bufs[] = {&c->coef, &c->geom, &c->gx, &c->gy, &c->gz, &c->fstage, &c->f2stage, &c->tc_ws, &c->sph_ws};
+    DevBuf *bufs[] = {&c->coef, &c->geom, &c->gx, &c->gy, &c->gz, &c->fstage, &c->f2stage, &c->tc_ws, &c->sph_ws, &c->fft_ws};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->d_err);

@@ -54,6 +54,8 @@ struct scff_ctx {
     // spherical method: coefficient tables (spherical.cpp) and workspace
     struct SphCache *sph = nullptr;
     DevBuf sph_ws;
+    // FFT method workspace (fft_method.cpp)
+    DevBuf fft_ws;
 };
 
 void scff_sph_cache_free(struct SphCache *c);

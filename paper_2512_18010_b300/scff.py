@@ -37,7 +37,7 @@ _SYMBOLS = [
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
-    "scff_screening_info", "scff_separable_integral", "scff_spherical",
+    "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor",
 ]
 
 
@@ -57,6 +57,11 @@ class _SphGrid(ctypes.Structure):
     _fields_ = [("lmax", ctypes.c_int), ("n_q", ctypes.c_int), ("q", ctypes.c_void_p),
                 ("n_theta", ctypes.c_int), ("theta", ctypes.c_void_p), ("n_phi", ctypes.c_int),
                 ("phi", ctypes.c_void_p)]
+
+
+class _FftGrid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("dq", ctypes.c_double * 3), ("centre", ctypes.c_double * 3),
+                ("threshold", ctypes.c_double)]
 
 
 class _Job(ctypes.Structure):
@@ -101,6 +106,7 @@ def load(build_if_missing: bool = True):
     lib.scff_qgrid_size.argtypes = [P, P]
     lib.scff_qgrid_size.restype = I64
     lib.scff_form_factor.argtypes = [P, P, P, P, ctypes.c_int, D, P, P, ctypes.c_int, P]
+    lib.scff_fft_form_factor.argtypes = [P, P, P, ctypes.POINTER(_FftGrid), ctypes.c_int, D, P, P, P, ctypes.c_int, P]
     lib.scff_spherical.argtypes = [P, P, P, ctypes.POINTER(_SphGrid), ctypes.c_int, D, P, P, P, P, ctypes.c_int, P]
     lib.scff_sync.argtypes = [P, P]
     lib.scff_form_factor_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, U32, ctypes.c_int, P,
@@ -484,6 +490,56 @@ class Context:
         if iso is not None:
             out["iso"] = iso
         return out
+
+    def fft_form_factor(self, basis: Basis, trans: Transitions, n, dq, centre=(0.0, 0.0, 0.0),
+                        threshold: float = 0.0, precision=FP32, scale: float = 1.0, want=("f", "f2"),
+                        out: str = "host", stream=None) -> dict:
+        """FFT method on a box of n[i] points, side 2 pi / dq[i], centred at `centre`.
+
+        Returns "f" complex [S, n0, n1, n2] at q = dq (index - n/2), "f2", and
+        "parseval" [S, 2] = (sum |Phi|^2 V_pix, sum |f|^2 dq^3 / (2 pi)^3); with
+        out="cuda", f and f2 are torch tensors on the device (complex as a
+        trailing axis of 2).
+        """
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        if np.isscalar(n):
+            n = (n, n, n)
+        if np.isscalar(dq):
+            dq = (dq, dq, dq)
+        g = _FftGrid((ctypes.c_int * 3)(*[int(v) for v in n]), (ctypes.c_double * 3)(*[float(v) for v in dq]),
+                     (ctypes.c_double * 3)(*[float(v) for v in centre]), float(threshold))
+        S = trans.n_states
+        shp = (S, int(n[0]), int(n[1]), int(n[2]))
+        par = np.zeros((S, 2), np.float64)
+        if out == "cuda":
+            import torch
+            tdt = torch.float64 if precision == FP64 else torch.float32
+            bufs = {}
+            if "f" in want:
+                bufs["f"] = torch.empty(shp + (2,), dtype=tdt, device="cuda")
+            if "f2" in want:
+                bufs["f2"] = torch.empty(shp, dtype=tdt, device="cuda")
+            if stream is None:
+                stream = torch.cuda.current_stream()
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+            ptr = lambda k: ctypes.c_void_p(bufs[k].data_ptr()) if k in bufs else None  # noqa: E731
+            _check(self.lib.scff_fft_form_factor(self.h, basis.handle, trans.handle, ctypes.byref(g), int(precision),
+                                                 float(scale), ptr("f"), ptr("f2"), _p(par), 1, sp))
+            bufs["parseval"] = par
+            return bufs
+        rdt = np.float64 if precision == FP64 else np.float32
+        f = np.zeros(shp + (2,), rdt) if "f" in want else None
+        f2 = np.zeros(shp, rdt) if "f2" in want else None
+        _check(self.lib.scff_fft_form_factor(self.h, basis.handle, trans.handle, ctypes.byref(g), int(precision),
+                                             float(scale), None if f is None else _p(f),
+                                             None if f2 is None else _p(f2), _p(par), 0, None))
+        res = {"parseval": par}
+        if f is not None:
+            res["f"] = f[..., 0] + 1j * f[..., 1]
+        if f2 is not None:
+            res["f2"] = f2
+        return res
 
     def set_screening(self, eps: float):
         """Error-bounded pair screening: results within eps * max|f| of the exact ones (0 = off)."""
