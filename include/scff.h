@@ -354,7 +354,8 @@ scff_status scff_spherical(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans
  *   sum |f|^2 dq0 dq1 dq2 / (2 pi)^3), equal for an exact discrete transform
  *   (Sec. "Verification", Parseval's theorem).
  * The basis may have at most ~1500 Cartesian functions (FP32; ~750 in FP64)
- * so that one tile's function values fit in shared memory.  The call
+ * so that one tile's function values fit in shared memory (bases above ~370
+ * functions in FP32, ~180 in FP64, run with 32-point tiles).  The call
  * returns after `stream` has finished.
  */
 typedef struct {

@@ -23,6 +23,10 @@ struct FftDensityArgs {
     double cut;                // drop a primitive where alpha |r - A|^2 > cut (0 = never)
     double scale, vpix;
     double *parseval;          // [S][2] (real-space sums accumulated here) or null
+    const void *tsym;          // [ceil(S / sbf)][kpad][sbf] symmetrised T per pair (fft_tsym)
+    const int2 *pairs;         // [kpad] (mu, nu) per pair, (-1, -1) for padding
+    int64_t kpad;              // pairs padded to whole chunks
+    int *err;                  // set on a timed-out wait
 };
 
 struct FftAxisArgs {
@@ -44,8 +48,13 @@ struct FftUnpackArgs {
     double *parseval;          // [S][2] (momentum-space sums accumulated here) or null
 };
 
-size_t fft_density_smem(int fp64, int nbf_pad, int tp);
-cudaError_t launch_fft_density(const FftDensityArgs &a, int fp64, int tp, cudaStream_t st);
+// Shared memory of the density kernel for sweeps of sbf states and tp points per tile.
+size_t fft_density_smem(int fp64, int nbf_pad, int sbf, int tp);
+cudaError_t launch_fft_density(const FftDensityArgs &a, int fp64, int sbf, int tp, cudaStream_t st);
+// Pairs (mu <= nu) of nbf functions padded to whole staging chunks.
+int64_t fft_pair_kpad(int nbf);
+cudaError_t launch_fft_tsym(const void *T, int fp64, int nbf, int S, int sbf, void *tsym, int2 *pairs,
+                            cudaStream_t st);
 cudaError_t launch_fft_axis(const FftAxisArgs &a, int fp64, int64_t n_groups, cudaStream_t st);
 cudaError_t launch_fft_unpack(const FftUnpackArgs &a, int fp64, cudaStream_t st);
 cudaError_t launch_cast_f64_to_f32(const double *in, int64_t n, float *out, cudaStream_t st);

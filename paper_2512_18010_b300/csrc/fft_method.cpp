@@ -73,13 +73,17 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     const int64_t npts = (int64_t)nx * ny * nz;
     const int nfield = (S + 1) / 2;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
-    // tile of points per CTA: the largest whose functions fit in shared memory
+    // states per register sweep (FP32 12, 8 or 4; FP64 8 or 4: as many as there are states)
+    // and points per tile (the largest whose function values fit in shared memory)
+    const int sbf = fp64 ? (S > 4 ? 8 : 4) : (S > 8 ? 12 : S > 4 ? 8 : 4);
     int tp = 0;
-    for (int cand : {128, 64, 32})
-        if (fft_density_smem(fp64 ? 1 : 0, nbf_pad, cand) <= 200 * 1024) {
+    for (int cand : {128, 64, 32}) {
+        if (fp64 ? cand == 128 : cand == 64) continue;
+        if (fft_density_smem(fp64 ? 1 : 0, nbf_pad, sbf, cand) <= 220 * 1024) {
             tp = cand;
             break;
         }
+    }
     if (!tp)
         return ffail(SCFF_ERR_INVALID_ARG, "scff_fft_form_factor: %d functions exceed the tile's shared memory", nbf);
     // ---- workspace: packed fields, T in the arithmetic type, host staging, Parseval sums
@@ -90,6 +94,12 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     o = up256(o + (fp64 ? 0 : sizeof(float) * (size_t)S * nbf * nbf));
     const size_t o_par = o;
     o = up256(o + sizeof(double) * 2 * (size_t)S);
+    const int64_t kpad = fft_pair_kpad(nbf);
+    const int nsweep = (S + sbf - 1) / sbf;
+    const size_t o_tsym = o;
+    o = up256(o + rsz * (size_t)nsweep * kpad * sbf);
+    const size_t o_pairs = o;
+    o = up256(o + sizeof(int2) * (size_t)kpad);
     const size_t bytes_f = 2 * rsz * (size_t)S * npts, bytes_f2 = rsz * (size_t)S * npts;
     const size_t o_out = o;
     if (!out_on_device) o = up256(o + up256(bytes_f) + up256(bytes_f2));
@@ -125,6 +135,9 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
         xmin[i] = grid->centre[i] - 0.5 * L[i];
     }
     const double vpix = dx[0] * dx[1] * dx[2];
+    FCUDA(launch_fft_tsym(Tdev, fp64 ? 1 : 0, nbf, S, sbf, w + o_tsym, reinterpret_cast<int2 *>(w + o_pairs), st));
+    ++c->launches;
+    FCUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     // ---- 1. density tabulation and contraction
     FftDensityArgs da;
     memset(&da, 0, sizeof(da));
@@ -146,7 +159,11 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     da.scale = scale;
     da.vpix = vpix;
     da.parseval = par;
-    FCUDA(launch_fft_density(da, fp64 ? 1 : 0, tp, st));
+    da.tsym = w + o_tsym;
+    da.pairs = reinterpret_cast<const int2 *>(w + o_pairs);
+    da.kpad = kpad;
+    da.err = c->d_err;
+    FCUDA(launch_fft_density(da, fp64 ? 1 : 0, sbf, tp, st));
     ++c->launches;
     // ---- 2. three in-place passes, z, y, x
     const int64_t cap_elems = fp64 ? 4096 : 8192;  // complex elements of one CTA's line buffer
@@ -196,6 +213,9 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     }
     if (parseval_out)
         FCUDA(cudaMemcpyAsync(parseval_out, par, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, st));
+    FCUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     FCUDA(cudaStreamSynchronize(st));
+    if (*c->h_err)
+        return ffail(SCFF_ERR_TIMEOUT, "scff_fft_form_factor: a device-side wait timed out (code %d)", *c->h_err);
     return SCFF_OK;
 }

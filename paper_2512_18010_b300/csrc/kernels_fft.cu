@@ -37,21 +37,74 @@ __device__ __forceinline__ void rec_powers(int type, int j, int pw[3]) {
 }
 
 constexpr int kFftThreads = 256;
-constexpr int kMuBlock = 32;  // functions per contraction pass (8 warps x 4)
+constexpr int kPairChunk = 256;  // (mu <= nu) pairs per staged chunk
 
-// smem: phi[nbf_pad][TP] and the staged transposed T block Tt[nbf_pad][kMuBlock],
-// then the per-warp partial densities [8][TP].
-template <typename R, int TP>
+// Tsym[sweep][k][q] for the pairs k = (mu <= nu) of the basis in row order
+// (mu ascending, nu = mu..nbf-1): T_mu,mu on the diagonal and T_mu,nu + T_nu,mu
+// above it, for states s = sweep * SBF + q (zero beyond S and beyond the last
+// pair); pairs[k] = (mu, nu), (-1, -1) for the padding.
+template <typename R>
+__global__ void fft_tsym_kernel(const R *__restrict__ T, int nbf, int S, int sbf, int64_t kpad, int nsweep,
+                                R *__restrict__ tsym, int2 *__restrict__ pairs) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nsweep * kpad * sbf) return;
+    const int q = (int)(idx % sbf);
+    const int64_t k = (idx / sbf) % kpad;
+    const int sweep = (int)(idx / ((int64_t)sbf * kpad));
+    const int64_t kf = (int64_t)nbf * (nbf + 1) / 2;
+    R v = R(0);
+    int2 pr = make_int2(-1, -1);
+    if (k < kf) {
+        // invert k = mu nbf - mu (mu - 1) / 2 + (nu - mu)
+        const double bq = 2.0 * nbf + 1.0;
+        int mu = (int)floor((bq - sqrt(bq * bq - 8.0 * (double)k)) * 0.5);
+        while (mu > 0 && (int64_t)mu * nbf - (int64_t)mu * (mu - 1) / 2 > k) --mu;
+        while ((int64_t)(mu + 1) * nbf - (int64_t)(mu + 1) * mu / 2 <= k) ++mu;
+        const int nu = mu + (int)(k - ((int64_t)mu * nbf - (int64_t)mu * (mu - 1) / 2));
+        pr = make_int2(mu, nu);
+        const int s = sweep * sbf + q;
+        if (s < S) {
+            const R *Ts = T + (size_t)s * nbf * nbf;
+            v = Ts[(size_t)mu * nbf + nu];
+            if (mu != nu) v += Ts[(size_t)nu * nbf + mu];
+        }
+    }
+    tsym[idx] = v;
+    if (sweep == 0 && q == 0) pairs[k] = pr;
+}
+
+// Phi_s(r) = sum_{mu <= nu} Tsym^s_{mu nu} phi_mu(r) phi_nu(r).  The pair
+// products are state-independent, so each is formed once per point and used
+// for the SBF states of a sweep held in registers.
+//
+// CTA: TP points (TP / 32 contiguous per lane) x 8 warps.  The pairs stream
+// through shared memory in chunks (1-D bulk async copies of the contiguous
+// Tsym and pair rows, double-buffered on mbarriers with bounded waits); warp w
+// takes pairs w, w + 8, ... of a chunk, so its lanes read the same Tsym row
+// (broadcast) at different points.  A pair with a function that is
+// identically zero on the tile (its Gaussians underflow, or the threshold
+// dropped every primitive) is skipped by the whole warp: an exact pruning.
+// smem: phi[nbf_pad][TP], active[nbf_pad] (bytes), 2 stages of
+// (Tsym[kPairChunk][SBF], pairs[kPairChunk]), one state's partial densities [8][TP].
+template <typename R, int SBF, int TP>
 __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *phi = reinterpret_cast<R *>(smem_raw);
-    R *Tt = phi + (size_t)a.nbf_pad * TP;
-    R *part = Tt + (size_t)a.nbf_pad * kMuBlock;
-    __shared__ int any_nonzero;
-    constexpr int PT = TP / 32;  // points per lane: lane + 32 i, i < PT
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int PT = TP / 32;
+    constexpr uint32_t T_BYTES = kPairChunk * SBF * sizeof(R), P_BYTES = kPairChunk * sizeof(int2);
+    constexpr uint32_t STAGE = T_BYTES + P_BYTES;
+    static_assert(T_BYTES % 16 == 0 && STAGE % 16 == 0, "bulk copies move multiples of 16 bytes");
+    unsigned char *stage0 = smem_raw;  // [2][STAGE]
+    R *part = reinterpret_cast<R *>(smem_raw + 2 * STAGE);
+    R *phi = part + (size_t)8 * TP;
+    unsigned char *active = reinterpret_cast<unsigned char *>(phi + (size_t)a.nbf_pad * TP);
+    __shared__ __align__(8) uint64_t bars[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * TP;
-    if (tid == 0) any_nonzero = 0;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbarrier_init();
+    }
     for (int e = tid; e < a.nbf_pad * TP; e += kFftThreads) phi[e] = R(0);
     __syncthreads();
     // ---- 1. basis function values at the tile's points
@@ -60,13 +113,13 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
         if (p < a.npts) {
             const int c = (int)(p % a.nz), b = (int)((p / a.nz) % a.ny), aa = (int)(p / ((int64_t)a.ny * a.nz));
             const double rx = a.xmin[0] + aa * a.dx[0], ry = a.xmin[1] + b * a.dx[1], rz = a.xmin[2] + c * a.dx[2];
-            bool nz = false;
             for (int rec = 0; rec < a.ps.n_rec; ++rec) {
                 const double dxr = rx - a.ps.rec_xyz[3 * rec], dyr = ry - a.ps.rec_xyz[3 * rec + 1],
                              dzr = rz - a.ps.rec_xyz[3 * rec + 2];
                 const double ex = a.ps.rec_alpha[rec] * (dxr * dxr + dyr * dyr + dzr * dzr);
                 if (a.cut > 0.0 && ex > a.cut) continue;
                 const R g = fexp((R)(-ex));
+                if (g == R(0)) continue;
                 const int type = a.ps.rec_type[rec], fn0 = a.ps.rec_fn0[rec];
                 const int nf = rec_nfn(type);
                 const R d[3] = {(R)dxr, (R)dyr, (R)dzr};
@@ -76,80 +129,116 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
                     R v = (R)a.ps.rec_w[kRecW * rec + j] * g;
                     for (int ax = 0; ax < 3; ++ax)
                         for (int k = 0; k < pw[ax]; ++k) v *= d[ax];
+                    // row-major points within a lane's group: point tid lives at lane*PT+i
                     phi[(size_t)(fn0 + j) * TP + tid] += v;
                 }
-                nz = true;
             }
-            if (nz) any_nonzero = 1;
         }
     }
     __syncthreads();
-    const bool skip = any_nonzero == 0;
-    // ---- 2. Phi_s = sum_mu phi_mu (sum_nu T_mu,nu phi_nu), state by state
-    for (int s = 0; s < a.S; ++s) {
-        R dens[PT];
+    for (int mu = tid; mu < a.nbf_pad; mu += kFftThreads) {
+        bool nzf = false;
+        if (mu < a.nbf)
+            for (int i = 0; i < TP && !nzf; ++i) nzf = phi[(size_t)mu * TP + i] != R(0);
+        active[mu] = nzf ? 1 : 0;
+    }
+    __syncthreads();
+    // ---- 2. state sweeps; chunk g (global count over the sweeps) sits in stage g & 1
+    const int nchunks = (int)(a.kpad / kPairChunk);
+    const int nsweep = (a.S + SBF - 1) / SBF;
+    int g = 0;
+    bool ok = true;
+    auto issue = [&](int sweep, int c, int gg) {
+        unsigned char *st = stage0 + (gg & 1) * STAGE;
+        mbar_arrive_expect_tx(&bars[gg & 1], STAGE);
+        bulk_g2s(st, static_cast<const R *>(a.tsym) + ((size_t)sweep * a.kpad + (size_t)c * kPairChunk) * SBF,
+                 T_BYTES, &bars[gg & 1]);
+        bulk_g2s(st + T_BYTES, a.pairs + (size_t)c * kPairChunk, P_BYTES, &bars[gg & 1]);
+    };
+    for (int sweep = 0; sweep < nsweep && ok; ++sweep) {
+        R tot[SBF][PT];
 #pragma unroll
-        for (int i = 0; i < PT; ++i) dens[i] = R(0);
-        if (!skip) {
-            const R *Ts = static_cast<const R *>(a.T) + (size_t)s * a.nbf * a.nbf;
-            for (int mu0 = 0; mu0 < a.nbf; mu0 += kMuBlock) {
-                // Tt[nu][j] = T[mu0 + j][nu]
-                for (int e = tid; e < kMuBlock * a.nbf_pad; e += kFftThreads) {
-                    const int j = e / a.nbf_pad, nu = e % a.nbf_pad;
-                    const int mu = mu0 + j;
-                    Tt[(size_t)nu * kMuBlock + j] = (mu < a.nbf && nu < a.nbf) ? Ts[(size_t)mu * a.nbf + nu] : R(0);
+        for (int q = 0; q < SBF; ++q)
+#pragma unroll
+            for (int i = 0; i < PT; ++i) tot[q][i] = R(0);
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            issue(sweep, 0, g);
+            if (nchunks > 1) issue(sweep, 1, g + 1);
+        }
+        for (int c = 0; c < nchunks; ++c, ++g) {
+            const bool got = mbar_wait(&bars[g & 1], (g >> 1) & 1);
+            if (__syncthreads_or(!got)) {
+                ok = false;
+                break;
+            }
+            const unsigned char *st = stage0 + (g & 1) * STAGE;
+            const R *Tc = reinterpret_cast<const R *>(st);
+            const int2 *pc = reinterpret_cast<const int2 *>(st + T_BYTES);
+            R acc[SBF][PT];
+#pragma unroll
+            for (int q = 0; q < SBF; ++q)
+#pragma unroll
+                for (int i = 0; i < PT; ++i) acc[q][i] = R(0);
+            for (int kk = warp; kk < kPairChunk; kk += kFftThreads / 32) {
+                const int2 pr = pc[kk];
+                if (pr.x < 0 || !active[pr.x] || !active[pr.y]) continue;
+                const R *pa = phi + (size_t)pr.x * TP + lane * PT;
+                const R *pb = phi + (size_t)pr.y * TP + lane * PT;
+                R prod[PT];
+#pragma unroll
+                for (int i = 0; i < PT; ++i) prod[i] = pa[i] * pb[i];
+                const R *tr = Tc + (size_t)kk * SBF;
+#pragma unroll
+                for (int q = 0; q < SBF; ++q) {
+                    const R t = tr[q];
+#pragma unroll
+                    for (int i = 0; i < PT; ++i) acc[q][i] = fma(t, prod[i], acc[q][i]);
                 }
-                __syncthreads();
-                R acc[4][PT];
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < SBF; ++q)
 #pragma unroll
-                    for (int i = 0; i < PT; ++i) acc[j][i] = R(0);
-                const int jw = warp * 4;
-                for (int nu = 0; nu < a.nbf; ++nu) {
-                    R t[4], v[PT];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) t[j] = Tt[(size_t)nu * kMuBlock + jw + j];
-#pragma unroll
-                    for (int i = 0; i < PT; ++i) v[i] = phi[(size_t)nu * TP + lane + 32 * i];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-#pragma unroll
-                        for (int i = 0; i < PT; ++i) acc[j][i] = fma(t[j], v[i], acc[j][i]);
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int mu = mu0 + jw + j;
-                    if (mu < a.nbf) {
-#pragma unroll
-                        for (int i = 0; i < PT; ++i)
-                            dens[i] = fma(phi[(size_t)mu * TP + lane + 32 * i], acc[j][i], dens[i]);
-                    }
-                }
-                __syncthreads();
+                for (int i = 0; i < PT; ++i) tot[q][i] += acc[q][i];
+            __syncthreads();
+            if (tid == 0 && c + 2 < nchunks) {
+                fence_proxy_async_smem();
+                issue(sweep, c + 2, g + 2);
             }
         }
-        // reduce the eight warps' partial sums
+        if (!ok) break;
+        // reduce the eight warps' partial sums state by state and write the fields
+        // (point index lane * PT + i)
 #pragma unroll
-        for (int i = 0; i < PT; ++i) part[warp * TP + lane + 32 * i] = dens[i];
-        __syncthreads();
-        if (tid < TP) {
-            R v = R(0);
-            for (int w = 0; w < kFftThreads / 32; ++w) v += part[w * TP + tid];
-            v *= (R)a.scale;
-            const int64_t p = p0 + tid;
-            double sq = 0.0;
-            if (p < a.npts) {
-                R *field = static_cast<R *>(a.out) + ((size_t)(s >> 1) * a.npts + p) * 2;
-                field[s & 1] = v;
-                if ((s & 1) == 0 && s + 1 == a.S) field[1] = R(0);
-                sq = (double)v * (double)v;
+        for (int q = 0; q < SBF; ++q) {
+#pragma unroll
+            for (int i = 0; i < PT; ++i) part[(size_t)warp * TP + lane * PT + i] = tot[q][i];
+            __syncthreads();
+            const int s = sweep * SBF + q;
+            if (tid < TP) {
+                R v = R(0);
+                for (int w = 0; w < kFftThreads / 32; ++w) v += part[(size_t)w * TP + tid];
+                v *= (R)a.scale;
+                const int64_t p = p0 + tid;
+                double sq = 0.0;
+                if (s < a.S && p < a.npts) {
+                    R *field = static_cast<R *>(a.out) + ((size_t)(s >> 1) * a.npts + p) * 2;
+                    field[s & 1] = v;
+                    if ((s & 1) == 0 && s + 1 == a.S) field[1] = R(0);
+                    sq = (double)v * (double)v;
+                }
+                // Parseval over the tile's points (TP is a multiple of 32)
+                for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+                if (lane == 0 && s < a.S && a.parseval) atomicAdd(&a.parseval[2 * s], sq * a.vpix);
             }
-            // Parseval: sum over the tile's points, one atomic per warp
-            for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
-            if (lane == 0 && a.parseval) atomicAdd(&a.parseval[2 * s], sq * a.vpix);
+            __syncthreads();
         }
-        __syncthreads();
+    }
+    if (!ok && tid == 0) {
+        flag_error(a.err, kDevErrTimeout);
+        // let the copies still in flight land before the CTA's shared memory goes away
+        mbar_wait(&bars[g & 1], (g >> 1) & 1);
+        mbar_wait(&bars[(g + 1) & 1], ((g + 1) >> 1) & 1);
     }
 }
 
@@ -283,32 +372,62 @@ cudaError_t launch_cast_f64_to_f32(const double *in, int64_t n, float *out, cuda
     return cudaGetLastError();
 }
 
-template <typename R, int TP>
+template <typename R, int SBF, int TP>
 static cudaError_t density_t(const FftDensityArgs &a, cudaStream_t st) {
-    const size_t smem = sizeof(R) * ((size_t)a.nbf_pad * TP + (size_t)a.nbf_pad * kMuBlock + 8 * TP);
-    cudaError_t e = cudaFuncSetAttribute(fft_density_kernel<R, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = fft_density_smem(sizeof(R) == 8, a.nbf_pad, SBF, TP);
+    cudaError_t e = cudaFuncSetAttribute(fft_density_kernel<R, SBF, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.npts + TP - 1) / TP;
-    fft_density_kernel<R, TP><<<(unsigned)tiles, kFftThreads, smem, st>>>(a);
+    fft_density_kernel<R, SBF, TP><<<(unsigned)tiles, kFftThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-size_t fft_density_smem(int fp64, int nbf_pad, int tp) {
+size_t fft_density_smem(int fp64, int nbf_pad, int sbf, int tp) {
     const size_t rs = fp64 ? sizeof(double) : sizeof(float);
-    return rs * ((size_t)nbf_pad * tp + (size_t)nbf_pad * kMuBlock + 8 * (size_t)tp);
+    const size_t stage = (size_t)kPairChunk * sbf * rs + (size_t)kPairChunk * sizeof(int2);
+    return 2 * stage + rs * ((size_t)8 * tp + (size_t)nbf_pad * tp) + (size_t)nbf_pad + 128;
 }
 
-cudaError_t launch_fft_density(const FftDensityArgs &a, int fp64, int tp, cudaStream_t st) {
+int64_t fft_pair_kpad(int nbf) {
+    const int64_t kf = (int64_t)nbf * (nbf + 1) / 2;
+    return (kf + kPairChunk - 1) / kPairChunk * kPairChunk;
+}
+
+cudaError_t launch_fft_tsym(const void *T, int fp64, int nbf, int S, int sbf, void *tsym, int2 *pairs,
+                            cudaStream_t st) {
+    const int64_t kpad = fft_pair_kpad(nbf);
+    const int nsweep = (S + sbf - 1) / sbf;
+    const int64_t tot = (int64_t)nsweep * kpad * sbf;
+    const unsigned blocks = (unsigned)((tot + 255) / 256);
+    if (fp64)
+        fft_tsym_kernel<double><<<blocks, 256, 0, st>>>((const double *)T, nbf, S, sbf, kpad, nsweep, (double *)tsym,
+                                                        pairs);
+    else
+        fft_tsym_kernel<float><<<blocks, 256, 0, st>>>((const float *)T, nbf, S, sbf, kpad, nsweep, (float *)tsym,
+                                                       pairs);
+    return cudaGetLastError();
+}
+
+// Instantiated shapes: FP32 (12|8|4 states) x (128|32 points); FP64 (8|4) x (64|32).
+cudaError_t launch_fft_density(const FftDensityArgs &a, int fp64, int sbf, int tp, cudaStream_t st) {
     if (a.npts == 0) return cudaSuccess;
     if (fp64) {
-        if (tp == 128) return density_t<double, 128>(a, st);
-        if (tp == 64) return density_t<double, 64>(a, st);
-        return density_t<double, 32>(a, st);
+        if (tp == 64) return sbf == 8 ? density_t<double, 8, 64>(a, st) : density_t<double, 4, 64>(a, st);
+        if (tp == 32) return sbf == 8 ? density_t<double, 8, 32>(a, st) : density_t<double, 4, 32>(a, st);
+        return cudaErrorInvalidValue;
     }
-    if (tp == 128) return density_t<float, 128>(a, st);
-    if (tp == 64) return density_t<float, 64>(a, st);
-    return density_t<float, 32>(a, st);
+    if (tp == 128) {
+        if (sbf == 12) return density_t<float, 12, 128>(a, st);
+        if (sbf == 8) return density_t<float, 8, 128>(a, st);
+        return density_t<float, 4, 128>(a, st);
+    }
+    if (tp == 32) {
+        if (sbf == 12) return density_t<float, 12, 32>(a, st);
+        if (sbf == 8) return density_t<float, 8, 32>(a, st);
+        return density_t<float, 4, 32>(a, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fft_axis(const FftAxisArgs &a, int fp64, int64_t n_groups, cudaStream_t st) {
