@@ -85,8 +85,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--only-fft", action="store_true",
+                    help="run only the FFT-method measurement and print it (for profiling)")
     ap.add_argument("--only-spherical", action="store_true",
                     help="run only the spherical-method measurement and print it (for profiling)")
+    ap.add_argument("--no-fft", action="store_true",
+                    help="skip the FFT-method measurement (128^3 box, FP32)")
     ap.add_argument("--no-spherical", action="store_true",
                     help="skip the spherical-method measurement (l_max 24 on a 100^3 (q, theta, phi) grid)")
     ap.add_argument("--serving-jobs", type=int, default=40)
@@ -160,6 +164,67 @@ def spherical_run(ctx, b, t, S, prec, steps, stream, flush):
             "fp64_path": {"value": S * len(q10) * SPH_NT * SPH_NP / (ms64 / 1e3), "unit": UNIT, "ms_per_call": ms64,
                           "radii": len(q10)},
             "max_rel_err_R_vs_fp64": err}
+
+
+FFT_N, FFT_QMAX = 128, 20.0
+
+
+def fft_run(ctx, b, t, S, steps, stream, flush, job):
+    """FFT method: density on a 128^3 box (side 2 pi / dq, dq = 40/128 so that q spans
+    [-20, 20) like the product grid) in FP32, all on the device; FP64 on a 64^3 box beside
+    it, and the discretisation error against the analytic FP64 path at sampled q."""
+    import torch
+    from paper_2512_18010_b300 import scff
+    dq = 2 * FFT_QMAX / FFT_N
+
+    def call(precision, n, d):
+        return ctx.fft_form_factor(b, t, n, d, precision=precision, want=("f", "f2"), out="cuda", stream=stream)
+
+    for _ in range(2):
+        call(scff.FP32, FFT_N, dq)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = call(scff.FP32, FFT_N, dq)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    tms = float(np.mean(ms))
+    f32 = out["f"]
+    par = out["parseval"]
+    # discretisation error: FP32 FFT method vs the analytic FP64 path at 512 sampled q of the grid
+    rng = np.random.default_rng(8)
+    idx = rng.integers(0, FFT_N, size=(512, 3))
+    q = dq * (idx - FFT_N // 2)
+    g = ctx.qgrid_list(q)
+    fa, _ = ctx.form_factor(b, t, g, precision=scff.FP64)
+    ctx.release(g)
+    fs = f32[:, idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    fs = fs[..., 0] + 1j * fs[..., 1]
+    disc = float(np.max(np.max(np.abs(fs - fa), axis=1) / np.max(np.abs(fa), axis=1)))
+    # FP64 path on a 64^3 box and FP32 arithmetic error on the same box
+    n64, dq64 = 64, 2 * FFT_QMAX / 64
+    call(scff.FP64, n64, dq64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    o64 = call(scff.FP64, n64, dq64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    o32 = call(scff.FP32, n64, dq64)
+    a64 = o64["f"].cpu().numpy()
+    a32 = o32["f"].double().cpu().numpy()
+    arith = float(np.max(np.max(np.abs(a32 - a64).reshape(S, -1), axis=1) / np.max(np.abs(a64).reshape(S, -1), axis=1)))
+    del out, o64, o32, f32
+    return {"workload": f"10-heavy-atom job, {S} states, {FFT_N}^3 box, side 2pi/dq with dq = {dq:.4f} "
+                        f"(q in [-{FFT_QMAX:g}, {FFT_QMAX:g})); density, transform and |f|^2 on the device",
+            "value": S * FFT_N ** 3 / (tms / 1e3), "unit": UNIT, "ms_per_call": tms, "precision": "fp32",
+            "parseval_rel_diff": float(np.max(np.abs(par[:, 0] - par[:, 1]) / par[:, 0])),
+            "fp32_vs_fp64_same_box_64": arith,
+            "discretisation_err_vs_analytic": disc,
+            "fp64_path": {"value": S * n64 ** 3 / (ms64 / 1e3), "unit": UNIT, "ms_per_call": ms64, "box": "64^3"}}
 
 
 def pair_stats(mol):
@@ -434,6 +499,10 @@ def main():
         if rank == 0:
             print(json.dumps({"spherical": spherical_run(ctx, b, t, S, prec, args.steps, stream, flush)}), flush=True)
         return 0
+    if args.only_fft:
+        if rank == 0:
+            print(json.dumps({"fft_method": fft_run(ctx, b, t, S, args.steps, stream, flush, job)}), flush=True)
+        return 0
 
     ctx.set_timing(True)
     for _ in range(args.warmup):
@@ -547,6 +616,10 @@ def main():
     if not args.no_spherical and prec != scff.FP64 and args.workload == "cfg3":
         spherical = spherical_run(ctx, b, t, S, prec, args.steps, stream, flush)
 
+    fftm = None
+    if not args.no_fft and prec != scff.FP64 and args.workload == "cfg3":
+        fftm = fft_run(ctx, b, t, S, args.steps, stream, flush, job)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -596,7 +669,7 @@ def main():
                            "monomial_rows": K, "vw_rows": Kvw, "autotune": choice,
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"dp{world} (one job per rank)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "spherical": spherical, "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "gpu_launches": int(launches),
                 "fp64_gpu_path": fp64, "screened": screened, "serving": serving, "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)
