@@ -105,74 +105,80 @@ cudaError_t launch_pair_geom(const PairSetDev &ps, double *pair_geom, cudaStream
 
 // ------------------------------------------------------------------ K1 pair-prep
 
-__global__ void __launch_bounds__(128) pairprep_kernel(PairSetDev ps, const double *__restrict__ T,
-                                                       int S, int SB, double *__restrict__ coef64,
-                                                       float *__restrict__ coef32) {
+// One thread per (pair, monomial) row: the geometry, the prefactor K and the
+// C tables are computed once (C in shared memory, indexed by the functions'
+// exponents) and reused for every state.
+constexpr int kPrepThreads = 128;
+
+__global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, const double *__restrict__ T,
+                                                                int S, int S_pad, int SB,
+                                                                double *__restrict__ coef64,
+                                                                float *__restrict__ coef32) {
+    __shared__ double Csm[3 * 4 * 4][kPrepThreads];  // C[ax][a][a2] of this thread's row
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
     if (row >= ps.n_rows) return;
+    const int tid = threadIdx.x;
     int L = 0;
     while (L < kMaxPairL && row >= ps.row_off[L + 1]) ++L;
     const int mL = mono_count(L);
     const int64_t local = row - ps.row_off[L];
     const int pr = ps.pair_off[L] + (int)(local / mL);
     const int m = (int)(local % mL);
-    double val = 0.0;
-    if (s < S) {
-        const int2 rr = ps.pair_rec[pr];
-        const double al = ps.rec_alpha[rr.x], be = ps.rec_alpha[rr.y];
-        const double p = al + be;
-        const double s2 = 0.5 / p;
-        double A[3], B[3], PA[3], PB[3], ab2 = 0.0;
-        for (int ax = 0; ax < 3; ++ax) {
-            A[ax] = ps.rec_xyz[3 * rr.x + ax];
-            B[ax] = ps.rec_xyz[3 * rr.y + ax];
-            const double P = (al * A[ax] + be * B[ax]) / p;
-            PA[ax] = P - A[ax];
-            PB[ax] = P - B[ax];
-            ab2 += (A[ax] - B[ax]) * (A[ax] - B[ax]);
-        }
-        const double K = pow(M_PI / p, 1.5) * exp(-al * be * ab2 / p);
-        const int e[3] = {mono_u(m), mono_v(m), mono_w(m)};
-        const int t1 = ps.rec_type[rr.x], t2 = ps.rec_type[rr.y];
-        const int l1 = rec_lmax(t1), l2 = rec_lmax(t2);
-        // C tables for this monomial: C[ax][a][a2]
-        double C[3][4][4];
-        for (int ax = 0; ax < 3; ++ax)
-            for (int a = 0; a <= 3; ++a)
-                for (int a2 = 0; a2 <= 3; ++a2)
-                    C[ax][a][a2] = (a <= l1 && a2 <= l2) ? c_coef(a, a2, e[ax], PA[ax], PB[ax], s2) : 0.0;
-        const int n1 = rec_nfn(t1), n2 = rec_nfn(t2);
-        const int f1 = ps.rec_fn0[rr.x], f2 = ps.rec_fn0[rr.y];
-        const int nbf = ps.nbf;
-        const double *Ts = T + (size_t)s * nbf * nbf;
-        const bool same = (rr.x == rr.y);
+    const int2 rr = ps.pair_rec[pr];
+    const double al = ps.rec_alpha[rr.x], be = ps.rec_alpha[rr.y];
+    const double p = al + be;
+    const double s2 = 0.5 / p;
+    double PA[3], PB[3], ab2 = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double A = ps.rec_xyz[3 * rr.x + ax], B = ps.rec_xyz[3 * rr.y + ax];
+        const double P = (al * A + be * B) / p;
+        PA[ax] = P - A;
+        PB[ax] = P - B;
+        ab2 += (A - B) * (A - B);
+    }
+    const double K = pow(M_PI / p, 1.5) * exp(-al * be * ab2 / p);
+    const int e[3] = {mono_u(m), mono_v(m), mono_w(m)};
+    const int t1 = ps.rec_type[rr.x], t2 = ps.rec_type[rr.y];
+    const int l1 = rec_lmax(t1), l2 = rec_lmax(t2);
+    for (int ax = 0; ax < 3; ++ax)
+        for (int a = 0; a <= l1; ++a)
+            for (int a2 = 0; a2 <= l2; ++a2) Csm[(ax * 4 + a) * 4 + a2][tid] = c_coef(a, a2, e[ax], PA[ax], PB[ax], s2);
+    const int n1 = rec_nfn(t1), n2 = rec_nfn(t2);
+    const int f1 = ps.rec_fn0[rr.x], f2 = ps.rec_fn0[rr.y];
+    const int nbf = ps.nbf;
+    const bool same = (rr.x == rr.y);
+    const int n = e[0] + e[1] + e[2];
+    const double sgn = K * ((n & 2) ? -1.0 : 1.0);  // i^n = +1, +i, -1, -i
+    for (int s = 0; s < S_pad; ++s) {
         double acc = 0.0;
-        for (int i = 0; i < n1; ++i) {
-            const double wi = ps.rec_w[kRecW * rr.x + i];
-            const int ai = fn_pow(t1, i, 0), bi = fn_pow(t1, i, 1), ci = fn_pow(t1, i, 2);
-            for (int j = 0; j < n2; ++j) {
-                const int aj = fn_pow(t2, j, 0), bj = fn_pow(t2, j, 1), cj = fn_pow(t2, j, 2);
-                const double D = C[0][ai][aj] * C[1][bi][bj] * C[2][ci][cj];
-                if (D == 0.0) continue;
-                double tw = Ts[(size_t)(f1 + i) * nbf + (f2 + j)];
-                if (!same) tw += Ts[(size_t)(f2 + j) * nbf + (f1 + i)];
-                acc += tw * wi * ps.rec_w[kRecW * rr.y + j] * D;
+        if (s < S) {
+            const double *Ts = T + (size_t)s * nbf * nbf;
+            for (int i = 0; i < n1; ++i) {
+                const double wi = ps.rec_w[kRecW * rr.x + i];
+                const int ai = fn_pow(t1, i, 0), bi = fn_pow(t1, i, 1), ci = fn_pow(t1, i, 2);
+                for (int j = 0; j < n2; ++j) {
+                    const int aj = fn_pow(t2, j, 0), bj = fn_pow(t2, j, 1), cj = fn_pow(t2, j, 2);
+                    const double D = Csm[(0 * 4 + ai) * 4 + aj][tid] * Csm[(1 * 4 + bi) * 4 + bj][tid] *
+                                     Csm[(2 * 4 + ci) * 4 + cj][tid];
+                    if (D == 0.0) continue;
+                    double tw = Ts[(size_t)(f1 + i) * nbf + (f2 + j)];
+                    if (!same) tw += Ts[(size_t)(f2 + j) * nbf + (f1 + i)];
+                    acc += tw * wi * ps.rec_w[kRecW * rr.y + j] * D;
+                }
             }
         }
-        const int n = e[0] + e[1] + e[2];
-        val = K * acc * ((n & 2) ? -1.0 : 1.0);  // i^n = +1, +i, -1, -i
+        const double val = sgn * acc;
+        const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
+        if (coef64) coef64[idx] = val;
+        if (coef32) coef32[idx] = (float)val;
     }
-    const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
-    if (coef64) coef64[idx] = val;
-    if (coef32) coef32[idx] = (float)val;
 }
 
 cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB, int S_pad,
                             double *coef64, float *coef32, int64_t *launches, cudaStream_t st) {
     if (ps.n_rows == 0) return cudaSuccess;
-    dim3 grid((unsigned)((ps.n_rows + 127) / 128), (unsigned)S_pad);
-    pairprep_kernel<<<grid, 128, 0, st>>>(ps, T, S, SB, coef64, coef32);
+    const unsigned grid = (unsigned)((ps.n_rows + kPrepThreads - 1) / kPrepThreads);
+    pairprep_kernel<<<grid, kPrepThreads, 0, st>>>(ps, T, S, S_pad, SB, coef64, coef32);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

@@ -252,37 +252,35 @@ static Layout make_layout_k(const PairSetDev &ps, int S, int nx, int ny, int nz)
 
 // ------------------------------------------------------------------ prep kernels
 
-// X_{pair,u}(q_i) = (i q_i)^u exp(-q_i^2/(4p)) e^{i q_i P_axis}, FP64 then FP32.
+// X_{pair,u}(q_i) = (i q_i)^u exp(-q_i^2/(4p)) e^{i q_i P_axis}, FP64 then FP32:
+// one thread per (pair, q_i) evaluates the Gaussian and the phase once and
+// writes the rows u = 0..L of its pair; the extra row n_axrows is zero.
 __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict__ geom,
                                         const double *__restrict__ qaxis, int n, int axis, int64_t n_axrows,
                                         float2 *__restrict__ table) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (n_axrows + 1) * n) return;
-    const int64_t row = idx / n;
+    if (idx >= ((int64_t)ps.n_pair + 1) * n) return;
+    const int pr = (int)(idx / n);
     const int i = (int)(idx % n);
-    float2 out = make_float2(0.f, 0.f);
-    if (row < n_axrows) {
-        int L = 0;
-        while (L < kMaxPairL && row >= ps.axrow_off[L + 1]) ++L;
-        const int64_t local = row - ps.axrow_off[L];
-        const int pr = ps.pair_off[L] + (int)(local / (L + 1));
-        const int u = (int)(local % (L + 1));
-        const double q = qaxis[i];
-        const double P = geom[4 * pr + axis], inv4p = geom[4 * pr + 3];
-        double sn, cs;
-        sincos(q * P, &sn, &cs);
-        double amp = exp(-q * q * inv4p);
-        for (int t = 0; t < u; ++t) amp *= q;
-        double re, im;
-        switch (u & 3) {  // times i^u
-        case 0: re = cs; im = sn; break;
-        case 1: re = -sn; im = cs; break;
-        case 2: re = -cs; im = -sn; break;
-        default: re = sn; im = -cs; break;
-        }
-        out = make_float2((float)(amp * re), (float)(amp * im));
+    if (pr == ps.n_pair) {
+        table[n_axrows * n + i] = make_float2(0.f, 0.f);
+        return;
     }
-    table[idx] = out;
+    int L = 0;
+    while (L < kMaxPairL && pr >= ps.pair_off[L + 1]) ++L;
+    const int64_t row0 = ps.axrow_off[L] + (int64_t)(pr - ps.pair_off[L]) * (L + 1);
+    const double q = qaxis[i];
+    const double P = geom[4 * pr + axis], inv4p = geom[4 * pr + 3];
+    double sn, cs;
+    sincos(q * P, &sn, &cs);
+    double re = cs * exp(-q * q * inv4p), im = sn * exp(-q * q * inv4p);
+    for (int u = 0; u <= L; ++u) {
+        table[(row0 + u) * n + i] = make_float2((float)re, (float)im);
+        // times i q
+        const double nr = -q * im, ni = q * re;
+        re = nr;
+        im = ni;
+    }
 }
 
 // k -> (pair, v, w, first axis row of the pair); padding k -> (-1, 0, 0, zero row);
@@ -759,7 +757,7 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
     float2 *tab[3] = {X, Y, Z};
     const int na[3] = {a.nx, a.ny, a.nz};
     for (int ax = 0; ax < 3; ++ax) {
-        const int64_t tot = (L.n_axrows + 1) * na[ax];
+        const int64_t tot = ((int64_t)ps.n_pair + 1) * na[ax];
         axis_power_table_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.pair_geom, qa[ax], na[ax], ax,
                                                                                L.n_axrows, tab[ax]);
     }

@@ -52,15 +52,11 @@ __host__ __device__ constexpr int mono_w(int m) {
             }
     return -1;
 }
+// Position of (u, v, w) in that order: the monomials of lower degree n = u+v+w
+// come first, then those of degree n with a larger u, then larger v.
 __host__ __device__ constexpr int mono_index(int u, int v, int w) {
-    int i = 0;
-    for (int n = 0; n <= kMaxPairL; ++n)
-        for (int uu = n; uu >= 0; --uu)
-            for (int vv = n - uu; vv >= 0; --vv) {
-                if (uu == u && vv == v && n - uu - vv == w) return i;
-                ++i;
-            }
-    return -1;
+    const int n = u + v + w;
+    return n * (n + 1) * (n + 2) / 6 + (n - u) * (n - u + 1) / 2 + (n - u - v);
 }
 
 // Record types of a primitive shell.
