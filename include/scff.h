@@ -370,6 +370,16 @@ scff_status scff_fft_form_factor(scff_ctx *ctx, scff_basis_h basis, scff_trans_h
                                  int out_on_device, void *stream);
 
 /*
+ * Test hook of the failure-detection path (no counterpart in the paper):
+ * launches one thread that waits on an mbarrier nothing arrives at, gives up
+ * after `tries` (1..2^24) attempts exactly as every bounded wait of the
+ * library does, and reports it through the context's error word.  Returns
+ * SCFF_ERR_TIMEOUT when the wait ran out (the expected outcome); the context
+ * remains usable afterwards.  Synchronous.
+ */
+scff_status scff_wait_selftest(scff_ctx *ctx, int64_t tries);
+
+/*
  * Error-bounded pair screening (the exact-tolerance form of the paper's
  * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
  * first scff_form_factor call for a (transitions, grid extent) bounds every

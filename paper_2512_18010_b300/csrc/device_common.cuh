@@ -62,12 +62,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; false after kWaitLimit tries.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
+// Bounded wait for the phase of the given parity; false after `limit` tries.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+
+// Bounded wait for the phase of the given parity; false after kWaitLimit tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) { return mbar_wait_n(bar, parity, kWaitLimit); }
 
 // 1-D bulk async copy global -> shared (TMA engine), completion on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.

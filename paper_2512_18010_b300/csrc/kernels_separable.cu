@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include "scff_internal.h"
+#include "device_common.cuh"
 
 namespace scff {
 
@@ -113,6 +114,27 @@ cudaError_t launch_separable(const PairSetDev &ps, const double *geom, const dou
                                                                              sums + 2 * rows, S, part);
     separable_reduce_kernel<<<S, 256, 0, st>>>(part, ps.n_pair, scale, out);
     if (launches) *launches += 5;
+    return cudaGetLastError();
+}
+
+}  // namespace scff
+
+namespace scff {
+
+// Exercises the bounded-wait error path: one thread waits on an mbarrier that
+// no one arrives at, gives up after `tries` attempts, records the timeout in
+// the context's error word and returns normally (the context stays usable).
+__global__ void wait_selftest_kernel(long long tries, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbarrier_init();
+        if (!mbar_wait_n(&bar, 0, tries)) flag_error(err, kDevErrTimeout);
+    }
+}
+
+cudaError_t launch_wait_selftest(long long tries, int *err, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(tries, err);
     return cudaGetLastError();
 }
 

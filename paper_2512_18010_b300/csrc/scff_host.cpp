@@ -1128,6 +1128,20 @@ extern "C" scff_status scff_separable_integral(scff_ctx *c, scff_basis_h b, scff
 }
 
 // Reads the device status word after all work on `stream` has finished.
+extern "C" scff_status scff_wait_selftest(scff_ctx *c, int64_t tries) {
+    if (!c || tries < 1 || tries > (int64_t)1 << 24)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_wait_selftest: tries must be 1..2^24");
+    cudaSetDevice(c->device);
+    CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+    CUDA_TRY(launch_wait_selftest((long long)tries, c->d_err, 0));
+    ++c->launches;
+    int h = 0;
+    CUDA_TRY(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+    if (h) return fail(SCFF_ERR_TIMEOUT, "scff_wait_selftest: the device-side wait gave up as intended (code %d)", h);
+    return SCFF_OK;
+}
+
 extern "C" scff_status scff_sync(scff_ctx *c, void *stream) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_sync: NULL context");
     cudaSetDevice(c->device);

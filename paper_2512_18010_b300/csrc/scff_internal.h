@@ -147,6 +147,10 @@ constexpr int kMaxPureTerms = 3;
 cudaError_t launch_pure_to_cart(int S, int ncart, int nuser, const int32_t *idx, const double *c,
                                 const double *Tu, double *Tc, cudaStream_t st);
 
+// One-thread kernel whose mbarrier wait runs out after `tries` attempts and
+// sets the error word (the bounded-wait error path, for tests).
+cudaError_t launch_wait_selftest(long long tries, int *err, cudaStream_t st);
+
 struct DirectArgs {
     const PairSetDev *ps;
     const void *coef;        // coef64 or coef32 in [n_sblk][n_rows][SB] layout

@@ -37,7 +37,7 @@ _SYMBOLS = [
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
-    "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor",
+    "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor", "scff_wait_selftest",
 ]
 
 
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
     lib.scff_qgrid_size.restype = I64
     lib.scff_form_factor.argtypes = [P, P, P, P, ctypes.c_int, D, P, P, ctypes.c_int, P]
     lib.scff_fft_form_factor.argtypes = [P, P, P, ctypes.POINTER(_FftGrid), ctypes.c_int, D, P, P, P, ctypes.c_int, P]
+    lib.scff_wait_selftest.argtypes = [P, I64]
     lib.scff_spherical.argtypes = [P, P, P, ctypes.POINTER(_SphGrid), ctypes.c_int, D, P, P, P, P, ctypes.c_int, P]
     lib.scff_sync.argtypes = [P, P]
     lib.scff_form_factor_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, U32, ctypes.c_int, P,
@@ -540,6 +541,10 @@ class Context:
         if f2 is not None:
             res["f2"] = f2
         return res
+
+    def wait_selftest(self, tries: int = 4096):
+        """Runs the bounded-wait failure path once; raises ScffError(TIMEOUT) as intended."""
+        _check(self.lib.scff_wait_selftest(self.h, int(tries)))
 
     def set_screening(self, eps: float):
         """Error-bounded pair screening: results within eps * max|f| of the exact ones (0 = off)."""

@@ -227,3 +227,15 @@ def test_static_entry_rejects_pure_shells(ctx):
     with pytest.raises(scff.ScffError) as e:
         scff.form_factor_static(job.mol, T, q, f)
     assert e.value.code == 1
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(ctx):
+    # A device-side wait on an mbarrier nothing arrives at gives up after its
+    # limit and raises the context's TIMEOUT status instead of hanging; the
+    # context keeps working afterwards.
+    with pytest.raises(scff.ScffError) as e:
+        ctx.wait_selftest(4096)
+    assert e.value.code == 6
+    job = W.config1()
+    f, _ = scff.evaluate_job(ctx, job, precision=scff.FP64)
+    assert rel_err(f, oracle.grid_form_factor(job)) < TOL[scff.FP64]
