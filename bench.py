@@ -537,6 +537,10 @@ def main():
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
     units = S * nq
     ms, value = aggregate(float(np.mean(step_ms)), units, dist, dev)
+    # Hermitian half: on antisymmetric axes the library evaluates half of the grid and writes
+    # the rest as f(-q) = conj(f(q)); the kernels' executed work counts the evaluated points only
+    half = all(np.array_equal(np.asarray(a)[::-1], -np.asarray(a)) for a in (job.qx, job.qy, job.qz)) and nq > 1
+    nx_rows = (len(job.qx) + 1) // 2 if half else len(job.qx)
 
     # plain FP64 GPU path on the same job
     fp64 = None
@@ -570,7 +574,8 @@ def main():
         tc_flops = 8 * Kvw * passes              # executed tensor flops per (q, state)
         bf16 = float(peaks.get("bf16_tflops", 1800.0))
         peak = bf16 * (TF32_PER_BF16 if prec == scff.TF32X3 else 1.0)
-        achieved = tc_flops * units / (kern_ms / 1e3) / 1e12
+        units_eval = S * nx_rows * len(job.qy) * len(job.qz)
+        achieved = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
         trec = measured_traffic(args.workload, args.precision)
         roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
@@ -579,15 +584,37 @@ def main():
                         f"products; direct-form algorithmic work is {direct_flops} flop per (q*state)",
                 "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio 0.5"
                                 if prec == scff.TF32X3 else "of measured: MEASURED_PEAKS.json bf16_tflops"),
-                "algorithmic_tflops": direct_flops * units / (kern_ms / 1e3) / 1e12}
+                "algorithmic_tflops": direct_flops * units_eval / (kern_ms / 1e3) / 1e12,
+                "evaluated_units_per_launch": units_eval}
     else:
         fp64_path = prec == scff.FP64
         peak = 1.25 if fp64_path else N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        achieved = direct_flops * units / (kern_ms / 1e3) / 1e12
+        units_eval = S * ((nq + 1) // 2 if half else nq)
+        achieved = direct_flops * units_eval / (kern_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "direct_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "work": f"{direct_flops} algorithmic flop per (q*state)",
                 "peak_source": "FP64 nominal 1.25 TFLOP/s" if fp64_path else
                 "FP32: 148 SM x 128 lanes x 2 flop x 2032 MHz"}
+
+    # the same job with every grid point evaluated (Hermitian half off)
+    no_symmetry = None
+    if half:
+        ctx.set_hermitian(False)
+        for _ in range(2):
+            step()
+        nms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nms.append(e0.elapsed_time(e1))
+        ctx.set_hermitian(True)
+        nm = float(np.mean(nms))
+        no_symmetry = {"value": units / (nm / 1e3), "unit": UNIT, "ms_per_step": nm,
+                       "what": "every grid point evaluated (no f(-q) = conj f(q) mirror)"}
 
     # the same job with error-bounded pair screening (results within eps * max|f| of the exact ones)
     screened = None
@@ -668,8 +695,9 @@ def main():
                 "config": {"workload": desc, "precision": args.precision, "n_pairs": n_pair,
                            "monomial_rows": K, "vw_rows": Kvw, "autotune": choice,
                            "l2": "flushed between timed steps (256 MB write)",
+                           "hermitian_half": bool(half),
                            "parallelism": f"dp{world} (one job per rank)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "no_symmetry": no_symmetry, "gpu_launches": int(launches),
                 "fp64_gpu_path": fp64, "screened": screened, "serving": serving, "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)

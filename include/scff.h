@@ -370,6 +370,20 @@ scff_status scff_fft_form_factor(scff_ctx *ctx, scff_basis_h basis, scff_trans_h
                                  int out_on_device, void *stream);
 
 /*
+ * Hermitian half (default on).  For real T (the only kind this library
+ * takes) the form factor obeys f(-q) = conj(f(q)) exactly (Eq. fSreal with a
+ * real integrand).  On a product grid whose three axes are antisymmetric
+ * (q[n-1-i] == -q[i] bitwise, e.g. the inclusive symmetric axes of the
+ * paper's grids) scff_form_factor, plans and the server then evaluate only
+ * the points of the first half of the flattened grid (the rows ix < nx/2 on
+ * the tensor cores, plus the middle row when nx is odd) and write every other
+ * point as the conjugate of its mirror; the output is the full grid.  enable
+ * = 0 evaluates every point.  Applies to jobs created or submitted after the
+ * call.
+ */
+scff_status scff_set_hermitian(scff_ctx *ctx, int enable);
+
+/*
  * Test hook of the failure-detection path (no counterpart in the paper):
  * launches one thread that waits on an mbarrier nothing arrives at, gives up
  * after `tries` (1..2^24) attempts exactly as every bounded wait of the

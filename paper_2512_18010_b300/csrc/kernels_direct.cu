@@ -267,7 +267,8 @@ struct DirectParams {
     int nx, ny, nz;
     const double *qlist;
     const double *pair_geom;
-    int64_t nq;
+    int64_t nq;      // points computed
+    int64_t nq_out;  // points of the output grid (state stride); > nq: mirror into the rest
     int S;
     double scale;
     void *f, *f2;
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
         for (int j = 0; j < SB; ++j) {
             const int s = sblk * SB + j;
             if (s < p.S) {
-                const V v = f[(size_t)s * p.nq + q];
+                const V v = f[(size_t)s * p.nq_out + q];
                 if constexpr (sizeof(R) == 4) {
                     acc.hr[j] = v.x;
                     acc.hi[j] = v.y;
@@ -530,8 +531,17 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
             V v;
             v.x = sc * acc.re(j);
             v.y = sc * acc.im(j);
-            f[(size_t)s * p.nq + q] = v;
-            if (f2 && final_part) f2[(size_t)s * p.nq + q] = v.x * v.x + v.y * v.y;
+            f[(size_t)s * p.nq_out + q] = v;
+            if (f2 && final_part) f2[(size_t)s * p.nq_out + q] = v.x * v.x + v.y * v.y;
+            // f(-q) = conj(f(q)): the mirrored point of an antisymmetric grid
+            const int64_t qm = p.nq_out - 1 - q;
+            if (p.nq_out > p.nq && qm != q && final_part) {
+                V w;
+                w.x = v.x;
+                w.y = -v.y;
+                f[(size_t)s * p.nq_out + qm] = w;
+                if (f2) f2[(size_t)s * p.nq_out + qm] = v.x * v.x + v.y * v.y;
+            }
         }
     }
 }
@@ -553,6 +563,7 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *laun
     p.qlist = a.qlist;
     p.pair_geom = a.pair_geom;
     p.nq = a.nq;
+    p.nq_out = a.nq_out > 0 ? a.nq_out : a.nq;
     p.S = a.S;
     p.scale = a.scale;
     p.f = a.f;

@@ -317,7 +317,7 @@ __global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, in
 // and written as the swizzled shared-memory image of each tile.  One thread
 // writes one 16-byte vector (PER_VEC consecutive k) of each array.
 template <int KIND>
-__global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int nx,
+__global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int nxr, int nx,
                               const float2 *__restrict__ X, const int4 *__restrict__ kinfo, int64_t K_pad, int nkc,
                               int M, int M_pad, uint8_t *__restrict__ Abuf) {
     using KD = Kind<KIND>;
@@ -329,7 +329,7 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
     const int64_t kv = idx % kvn;
     float re[V], im[V];
     const bool mvalid = m < M;
-    const int s = mvalid ? m / nx : 0, ix = mvalid ? m % nx : 0;
+    const int s = mvalid ? m / nxr : 0, ix = mvalid ? m % nxr : 0;  // rows (s, ix < nxr); X has nx columns
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const int4 ki = kinfo[kv * V + e];
@@ -673,13 +673,22 @@ __global__ void __launch_bounds__(THREADS, 1)
                 float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
                 float *f2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ix * J.N : nullptr;
                 const float sc = J.scale;
+                const int ixm = J.nxf - 1 - ix;  // mirror row (f(-q) = conj f(q))
+                const bool mir = J.mirror && ixm != ix;
+                float2 *mrow = J.f + (size_t)sidx * J.nq + (size_t)ixm * J.N;
+                float *m2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ixm * J.N : nullptr;
 #pragma unroll
                 for (int j = 0; j < CQ; ++j) {
                     const int64_t nn = n0 + j;
                     if (nn < J.N) {
                         const float2 v = make_float2(sc * acc_re[j], sc * acc_im[j]);
+                        const float a2 = v.x * v.x + v.y * v.y;
                         frow[nn] = v;
-                        if (f2row) f2row[nn] = v.x * v.x + v.y * v.y;
+                        if (f2row) f2row[nn] = a2;
+                        if (mir) {
+                            mrow[J.N - 1 - nn] = make_float2(v.x, -v.y);
+                            if (m2row) m2row[J.N - 1 - nn] = a2;
+                        }
                     }
                 }
             }
@@ -715,10 +724,23 @@ size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, i
 }
 
 // Descriptor of one job whose tables and A image live in `ws`.
+// Layout of one job with the rows actually computed: all (s, ix), or with
+// `half` the rows ix < ceil(nx/2) (the sizes stay those of the full job).
+template <int KIND>
+static tc::Layout job_layout(const TcArgs &a) {
+    using namespace tc;
+    Layout L = make_layout_k<KIND>(*a.ps, a.S, a.nx, a.ny, a.nz);
+    const int nxr = a.half ? (a.nx + 1) / 2 : a.nx;
+    L.M = a.S * nxr;
+    L.M_pad = (L.M + BM - 1) / BM * BM;
+    L.n_mt = L.M_pad / BM;
+    return L;
+}
+
 template <int KIND>
 static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     using namespace tc;
-    const Layout L = make_layout_k<KIND>(*a.ps, a.S, a.nx, a.ny, a.nz);
+    const Layout L = job_layout<KIND>(a);
     uint8_t *w = static_cast<uint8_t *>(ws);
     jd->A = w + L.off_A;
     jd->Y = reinterpret_cast<float2 *>(w + L.off_Y);
@@ -727,16 +749,18 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->kofs = reinterpret_cast<int2 *>(w + L.off_ko);
     jd->ny = a.ny;
     jd->nz = a.nz;
-    jd->nx = a.nx;
+    jd->nx = a.half ? (a.nx + 1) / 2 : a.nx;  // rows per state
     jd->nkc = L.nkc;
     jd->M = L.M;
     jd->n_mt = L.n_mt;
     jd->n_nt = L.n_nt;
     jd->N = L.N;
-    jd->nq = (int64_t)a.nx * L.N;
+    jd->nq = (int64_t)a.nx * L.N;  // the full grid: state stride
     jd->scale = (float)a.scale;
     jd->f = reinterpret_cast<float2 *>(a.f);
     jd->f2 = a.f2;
+    jd->mirror = a.half;
+    jd->nxf = a.nx;
 }
 
 // Tables, k-index and the A image of one job in `ws` (tc_job_bytes bytes).
@@ -745,7 +769,7 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
     using namespace tc;
     using KD = Kind<KIND>;
     const PairSetDev &ps = *a.ps;
-    const Layout L = make_layout_k<KIND>(ps, a.S, a.nx, a.ny, a.nz);
+    const Layout L = job_layout<KIND>(a);
     if (L.n_mt > (1 << 24)) return cudaErrorInvalidConfiguration;
     uint8_t *w = static_cast<uint8_t *>(ws);
     float2 *X = reinterpret_cast<float2 *>(w + L.off_X);
@@ -765,8 +789,8 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
     kindex_kernel<<<(unsigned)((L.K_pad + 255) / 256), 256, 0, st>>>(ps, L.K_pad, L.n_axrows, a.ny, a.nz, kinfo, kofs);
     {
         const int64_t tot = (int64_t)L.M_pad * (L.K_pad / KD::PER_VEC);
-        abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.coef32, a.SB, a.nx, X, kinfo,
-                                                                           L.K_pad, L.nkc, L.M, L.M_pad, Abuf);
+        abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+            ps, a.coef32, a.SB, a.half ? (a.nx + 1) / 2 : a.nx, a.nx, X, kinfo, L.K_pad, L.nkc, L.M, L.M_pad, Abuf);
     }
     if (launches) *launches += 5;
     if (jd) job_desc_t<KIND>(a, ws, jd);

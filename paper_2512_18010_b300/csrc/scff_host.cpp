@@ -514,6 +514,26 @@ extern "C" scff_status scff_transitions(scff_ctx *c, scff_basis_h b, int n_state
     return SCFF_OK;
 }
 
+int scff_axes_antisym(const double *qx, int nx, const double *qy, int ny, const double *qz, int nz) {
+    const double *ax[3] = {qx, qy, qz};
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < n[a]; ++i)
+            if (!(ax[a][n[a] - 1 - i] == -ax[a][i])) return 0;
+    return 1;
+}
+
+// Whether a job on grid g computes half its points (Hermitian symmetry).
+static int grid_half(const scff_ctx *c, const scff_qgrid_s *g) {
+    return (c->hermitian && g->product && g->antisym && g->n > 1) ? 1 : 0;
+}
+
+extern "C" scff_status scff_set_hermitian(scff_ctx *c, int enable) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_hermitian: NULL context");
+    c->hermitian = enable ? 1 : 0;
+    return SCFF_OK;
+}
+
 extern "C" scff_status scff_qgrid_product(scff_ctx *c, const double *qx, int nx, const double *qy, int ny,
                                           const double *qz, int nz, scff_qgrid_h *out) {
     if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_product: NULL context or output");
@@ -537,6 +557,7 @@ extern "C" scff_status scff_qgrid_product(scff_ctx *c, const double *qx, int nx,
     g->hx.assign(qx, qx + nx);
     g->hy.assign(qy, qy + ny);
     g->hz.assign(qz, qz + nz);
+    g->antisym = scff_axes_antisym(qx, nx, qy, ny, qz, nz);
     {
         double m[3] = {0, 0, 0};
         for (int i = 0; i < nx; ++i) m[0] = std::max(m[0], fabs(qx[i]));
@@ -688,13 +709,15 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         ta.ev_mark = c->timing ? c->ev[1] : nullptr;
         ta.kind = kind;
         ta.drain_every = ch.drain;
+        ta.half = grid_half(c, g);
         CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
     } else {
         DirectArgs a;
         memset(&a, 0, sizeof(a));
         a.ps = &ps;
         a.coef = c->coef.p;
-        a.nq = nq;
+        a.nq = grid_half(c, g) ? (nq + 1) / 2 : nq;
+        a.nq_out = nq;
         a.S = S;
         a.SB = SB;
         a.scale = scale;
@@ -1168,6 +1191,7 @@ struct PlanJob {
     int group;         // group index (tensor-core jobs)
     size_t region;     // offset of the job's tables and A image in the group area
     int S, S_pad, SB;
+    int half;          // Hermitian half of an antisymmetric product grid
 };
 
 struct scff_plan_s {
@@ -1224,6 +1248,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         PlanJob pj;
         pj.job = j;
         pj.tc = tc_prec && j.grid->product;
+        pj.half = grid_half(c, j.grid);
         pj.group = -1;
         pj.region = 0;
         pj.S = j.trans->S;
@@ -1320,6 +1345,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
             ta.f = (float *)pj.job.f_out;
             ta.f2 = (float *)pj.job.f2_out;
             ta.kind = P->tc_kind;
+            ta.half = pj.half;
             TcJobDev jd;
             memset(&jd, 0, sizeof(jd));
             tc_job_desc(ta, base + P->off_group + pj.region, &jd);
@@ -1377,6 +1403,7 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             ta.f = (float *)pj.job.f_out;
             ta.f2 = (float *)pj.job.f2_out;
             ta.kind = P->tc_kind;
+            ta.half = pj.half;
             CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));
         }
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
@@ -1396,7 +1423,8 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
         memset(&a, 0, sizeof(a));
         a.ps = &ps;
         a.coef = coef;
-        a.nq = gq->n;
+        a.nq = pj.half ? (gq->n + 1) / 2 : gq->n;
+        a.nq_out = gq->n;
         a.S = pj.S;
         a.SB = pj.SB;
         a.scale = pj.job.scale;

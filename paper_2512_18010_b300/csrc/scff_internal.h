@@ -159,12 +159,16 @@ struct DirectArgs {
     int nx, ny, nz;
     const double *qlist;     // [n][3] (list mode)
     const double *pair_geom; // list mode
-    int64_t nq;
+    int64_t nq;              // points computed (the first nq of the flattened grid)
     int S, SB;
     double scale;
-    void *f;                 // [S][nq][2]
-    void *f2;                // [S][nq] or null
+    void *f;                 // [S][nq_out][2]
+    void *f2;                // [S][nq_out] or null
     int *err_flag;
+    // Hermitian half (product grids with antisymmetric axes): nq_out points in
+    // all, point p also writes conj at nq_out - 1 - p (unless that is p);
+    // nq_out = 0 means nq_out = nq without a mirror.
+    int64_t nq_out;
 };
 cudaError_t launch_direct(const DirectArgs &a, int fp64, int list_mode, int64_t *launches,
                           cudaStream_t st);

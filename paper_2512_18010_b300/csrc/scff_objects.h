@@ -56,7 +56,13 @@ struct scff_ctx {
     DevBuf sph_ws;
     // FFT method workspace (fft_method.cpp)
     DevBuf fft_ws;
+    // Hermitian half (scff_set_hermitian): on antisymmetric product grids
+    // compute half the points and fill the rest with f(-q) = conj(f(q))
+    int hermitian = 1;
 };
+
+// 1 when every axis of the host array pairs point i with -(point n-1-i) exactly.
+int scff_axes_antisym(const double *qx, int nx, const double *qy, int ny, const double *qz, int nz);
 
 void scff_sph_cache_free(struct SphCache *c);
 
@@ -88,6 +94,7 @@ struct scff_qgrid_s {
     double *d_qx, *d_qy, *d_qz;  // product grid axes
     double *d_q;                 // list [n][3]
     std::vector<double> hx, hy, hz;
+    int antisym = 0;             // product grid with q[n-1-i] == -q[i] on every axis
 };
 
 

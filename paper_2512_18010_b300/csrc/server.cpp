@@ -115,6 +115,7 @@ struct SJob {
     std::vector<double> ax[3];
     int S = 0, S_pad = 0;
     int64_t nq = 0;
+    int half = 0;            // Hermitian half of an antisymmetric grid (fixed at submit)
     size_t footprint = 0;    // bytes of the job's arena block
     size_t off = 0;          // arena offset
     size_t scratch_need = 0; // pair geometry + coefficients of this job
@@ -256,6 +257,7 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             ta.f = (float *)fdev;
             ta.f2 = (float *)f2dev;
             ta.kind = tc_kind_of(sv->precision);
+            ta.half = j->half;
             TcJobDev jd;
             memset(&jd, 0, sizeof(jd));
             if (tc_prep_job(ta, work, &jd, &launches, st) != cudaSuccess) return SCFF_ERR_CUDA;
@@ -265,7 +267,8 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             memset(&a, 0, sizeof(a));
             a.ps = &ps;
             a.coef = coef;
-            a.nq = j->nq;
+            a.nq = j->half ? (j->nq + 1) / 2 : j->nq;
+            a.nq_out = j->nq;
             a.S = j->S;
             a.SB = SB;
             a.scale = j->req.scale;
@@ -502,6 +505,8 @@ extern "C" scff_status scff_submit(scff_server_h sv, const scff_request *r, int6
     j->ax[0].assign(r->qx, r->qx + r->nx);
     j->ax[1].assign(r->qy, r->qy + r->ny);
     j->ax[2].assign(r->qz, r->qz + r->nz);
+    j->half = (sv->ctx->hermitian && scff_axes_antisym(r->qx, r->nx, r->qy, r->ny, r->qz, r->nz) &&
+               (int64_t)r->nx * r->ny * r->nz > 1) ? 1 : 0;
     j->S = r->trans->S;
     j->nq = (int64_t)r->nx * r->ny * r->nz;
     j->t_submit = now_ms();

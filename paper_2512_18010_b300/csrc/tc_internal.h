@@ -28,6 +28,9 @@ struct TcArgs {
     cudaEvent_t ev_mark;       // if set, recorded just before the main kernel
     int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
+    // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
+    // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
+    int half;
 };
 
 // Device descriptor of one prepared job (read by the persistent kernel).
@@ -47,6 +50,9 @@ struct TcJobDev {
     int64_t N, nq;
     float scale;
     int ystride;
+    // mirror = 1: row ix (of nxf) also writes conj at row nxf-1-ix, column N-1-n
+    // (unless that is the row itself): f(-q) = conj(f(q)) on antisymmetric axes
+    int mirror, nxf;
     float2 *f;             // [S][nq] complex output
     float *f2;             // [S][nq] or null
 };

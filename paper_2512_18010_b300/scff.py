@@ -37,7 +37,7 @@ _SYMBOLS = [
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
-    "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor", "scff_wait_selftest",
+    "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor", "scff_wait_selftest", "scff_set_hermitian",
 ]
 
 
@@ -541,6 +541,10 @@ class Context:
         if f2 is not None:
             res["f2"] = f2
         return res
+
+    def set_hermitian(self, enable: bool = True):
+        """Evaluate half of an antisymmetric product grid and mirror f(-q) = conj(f(q)) (default on)."""
+        _check(self.lib.scff_set_hermitian(self.h, 1 if enable else 0))
 
     def wait_selftest(self, tries: int = 4096):
         """Runs the bounded-wait failure path once; raises ScffError(TIMEOUT) as intended."""

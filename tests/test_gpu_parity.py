@@ -239,3 +239,31 @@ def test_bounded_wait_reports_timeout_and_context_survives(ctx):
     job = W.config1()
     f, _ = scff.evaluate_job(ctx, job, precision=scff.FP64)
     assert rel_err(f, oracle.grid_form_factor(job)) < TOL[scff.FP64]
+
+
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+def test_hermitian_half_is_exact_mirror(prec):
+    # On an antisymmetric grid the half-evaluated result (default) mirrors
+    # f(-q) = conj(f(q)) exactly and agrees with the full evaluation within the
+    # tolerance; a grid that is not antisymmetric is evaluated in full.
+    c = scff.Context(0)
+    try:
+        base = W.config1()
+        T = W.transition_matrices(91, 5, base.mol.nbf)
+        job = W.Job(base.mol, T, W.axis(9, 7.0), W.axis(12, 8.0), W.axis(33, 9.0), 91)
+        f_half, f2_half = scff.evaluate_job(c, job, precision=prec)
+        n = (9, 12, 33)
+        g = f_half.reshape(5, *n)
+        assert np.array_equal(g, np.conj(g[:, ::-1, ::-1, ::-1]))
+        assert np.array_equal(f2_half.reshape(5, *n), f2_half.reshape(5, *n)[:, ::-1, ::-1, ::-1])
+        c.set_hermitian(False)
+        f_full, _ = scff.evaluate_job(c, job, precision=prec)
+        ref = oracle.grid_form_factor(job)
+        assert rel_err(f_half, ref) < TOL[prec]
+        assert rel_err(f_full, ref) < TOL[prec]
+        c.set_hermitian(True)
+        shifted = W.Job(base.mol, T, W.axis(9, 7.0) + 0.1, W.axis(12, 8.0), W.axis(33, 9.0), 91)
+        f_s, _ = scff.evaluate_job(c, shifted, precision=prec)
+        assert rel_err(f_s, oracle.grid_form_factor(shifted)) < TOL[prec]
+    finally:
+        c.close()
