@@ -211,8 +211,21 @@ struct Layout {
     int M, M_pad, n_mt;
     int64_t N;
     int n_nt;
-    size_t off_X, off_Y, off_Z, off_k, off_ko, off_A, total;
+    int part_tiles;    // partial-sum tiles reserved for the tail split
+    size_t off_X, off_Y, off_Z, off_k, off_ko, off_A, off_part, off_cnt, total;
 };
+
+// Tail split of a job with `items` equal tiles of nkc chunks on P SMs: the
+// last R = items mod P tiles run as s parts (k split evenly), so that the
+// final wave keeps the SMs busy.  s = 0: no split.
+static void tail_split(int items, int nkc, int P, int *R, int *s) {
+    *R = items % P;
+    *s = 0;
+    if (*R == 0 || nkc >= 32768) return;
+    int parts = std::min(16, std::min(P / *R, nkc / 8));
+    if (parts >= 2) *s = parts;
+    else *R = 0;
+}
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -241,6 +254,12 @@ static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     o = align_up(o + sizeof(int2) * (size_t)L.K_pad, 1024);
     L.off_A = o;
     o = align_up(o + (size_t)L.n_mt * L.nkc * a_stage, 1024);
+    // a split never needs more than P partial tiles (R * s <= P)
+    L.part_tiles = std::min<int64_t>(tc_num_sms(), (int64_t)L.n_mt * L.n_nt * 16);
+    L.off_part = o;
+    o = align_up(o + sizeof(float2) * (size_t)L.part_tiles * BM * BN, 1024);
+    L.off_cnt = o;
+    o = align_up(o + sizeof(int) * 8 * (size_t)L.part_tiles, 1024);
     L.total = o;
     return L;
 }
@@ -496,9 +515,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             int gc = 0;  // global chunk counter
             for (int idx = blockIdx.x; idx < n_items && !*abort_flag; idx += gridDim.x) {
                 const int4 item = items[idx];
-                const TcJobDev &J = jobs[item.x];
-                const uint8_t *Abase = J.A + (size_t)item.y * J.nkc * A_STAGE;
-                for (int it = 0; it < J.nkc; ++it, ++gc) {
+                const TcJobDev &J = jobs[item_job(item.x)];
+                const uint8_t *Abase = J.A + ((size_t)item_mt(item.y) * J.nkc + item_k0(item.y)) * A_STAGE;
+                for (int it = 0; it < item.w; ++it, ++gc) {
                     const int s = gc % STAGES;
                     if (gc >= STAGES && !mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1)) {
                         *abort_flag = 1;
@@ -577,8 +596,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
             const int4 item = items[idx];
-            const TcJobDev &J = jobs[item.x];
+            const TcJobDev &J = jobs[item_job(item.x)];
             const int nkc = item.w;
+            const int mt = item_mt(item.y), k0 = item_k0(item.y);
             const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
             const int ngroups = (nkc + G - 1) / G;
             const int nz = J.nz;
@@ -603,7 +623,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
             const int gc0 = gc;
             int drained = 0;
-            const int2 *kofs = J.kofs + khalf * KH;
+            const int2 *kofs = J.kofs + (size_t)k0 * BK + khalf * KH;
             for (int it = 0; it < nkc && ok; ++it, ++gc) {
                 const int s = gc % STAGES;
                 // Row offsets of this thread's k: independent of the A copy, so the
@@ -666,8 +686,44 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             gbase += ngroups;
             gc = gc0 + nkc;
-            const int m = item.y * BM + lg * 32 + lane;
-            if (ok && m < J.M) {
+            const int m = mt * BM + lg * 32 + lane;
+            const int slot = item_slot(item.x);
+            bool write = ok && m < J.M;
+            if (ok && slot >= 0) {
+                // part of a split tile: raw partial sums of this warp's region
+                const int row = lg * 32 + lane;
+                float2 *pp = J.part + ((size_t)slot * BM + row) * BN + colh;
+#pragma unroll
+                for (int j = 0; j < CQ; ++j) pp[j] = make_float2(acc_re[j], acc_im[j]);
+                __threadfence();
+                __syncwarp();
+                const int tile = slot / J.nsplit, region = warp - 4;
+                int last = 0;
+                if (lane == 0) {
+                    int *c = J.cnt + tile * 8 + region;
+                    last = atomicAdd(c, 1) == J.nsplit - 1;
+                    if (last) *c = 0;  // ready for the next launch
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                write = write && last;
+                if (last) {
+                    // every part of this region has landed: sum them in part order
+                    __threadfence();
+                    const int first = tile * J.nsplit;
+#pragma unroll
+                    for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
+                    for (int pt = 0; pt < J.nsplit; ++pt) {
+                        const float2 *src = J.part + ((size_t)(first + pt) * BM + row) * BN + colh;
+#pragma unroll
+                        for (int j = 0; j < CQ; ++j) {
+                            const float2 v = __ldcg(src + j);
+                            acc_re[j] += v.x;
+                            acc_im[j] += v.y;
+                        }
+                    }
+                }
+            }
+            if (write) {
                 const int sidx = m / J.nx, ix = m % J.nx;
                 const int64_t n0 = (int64_t)item.z * BN + colh;
                 float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
@@ -720,7 +776,8 @@ size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     const tc::Layout L = kind == tc::KIND_BF16X2   ? tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz)
                          : kind == tc::KIND_BF16X3 ? tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz)
                                                    : tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz);
-    return L.total + 1024 + sizeof(TcJobDev) + sizeof(int4) * (size_t)L.n_mt * L.n_nt;
+    // work items: the tiles plus at most P extra parts of the tail split
+    return L.total + 1024 + sizeof(TcJobDev) + sizeof(int4) * ((size_t)L.n_mt * L.n_nt + tc_num_sms());
 }
 
 // Descriptor of one job whose tables and A image live in `ws`.
@@ -761,6 +818,12 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->f2 = a.f2;
     jd->mirror = a.half;
     jd->nxf = a.nx;
+    int R = 0, sp = 0;
+    tail_split(L.n_mt * L.n_nt, L.nkc, tc_num_sms(), &R, &sp);
+    jd->part = reinterpret_cast<float2 *>(w + L.off_part);
+    jd->cnt = reinterpret_cast<int *>(w + L.off_cnt);
+    jd->nsplit = sp;
+    jd->split_tiles = sp ? R : 0;
 }
 
 // Tables, k-index and the A image of one job in `ws` (tc_job_bytes bytes).
@@ -793,6 +856,8 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
             ps, a.coef32, a.SB, a.half ? (a.nx + 1) / 2 : a.nx, a.nx, X, kinfo, L.K_pad, L.nkc, L.M, L.M_pad, Abuf);
     }
     if (launches) *launches += 5;
+    cudaError_t e = cudaMemsetAsync(w + L.off_cnt, 0, sizeof(int) * 8 * (size_t)L.part_tiles, st);
+    if (e != cudaSuccess) return e;
     if (jd) job_desc_t<KIND>(a, ws, jd);
     return cudaGetLastError();
 }
@@ -818,9 +883,24 @@ cudaError_t tc_prep_job(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launch
 // items to CTAs balances well.
 void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) {
     items.clear();
-    for (int j = 0; j < n_jobs; ++j)
-        for (int mt = 0; mt < jobs[j].n_mt; ++mt)
-            for (int nt = 0; nt < jobs[j].n_nt; ++nt) items.push_back(make_int4(j, mt, nt, jobs[j].nkc));
+    for (int j = 0; j < n_jobs; ++j) {
+        const TcJobDev &J = jobs[j];
+        const int n_items = J.n_mt * J.n_nt;
+        const int first_split = J.nsplit ? n_items - J.split_tiles : n_items;
+        for (int i = 0; i < n_items; ++i) {
+            const int mt = i / J.n_nt, nt = i % J.n_nt;
+            if (i < first_split) {
+                items.push_back(make_int4(j, mt, nt, J.nkc));
+                continue;
+            }
+            for (int p = 0; p < J.nsplit; ++p) {
+                const int k0 = (int)((int64_t)p * J.nkc / J.nsplit), k1 = (int)((int64_t)(p + 1) * J.nkc / J.nsplit);
+                const int slot = (i - first_split) * J.nsplit + p;
+                items.push_back(make_int4(j | ((slot + 1) << 16), mt | (k0 << 16), nt, k1 - k0));
+            }
+        }
+    }
+    // longest first; the stable order keeps each job's tiles row-major and its parts last
     std::stable_sort(items.begin(), items.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
 }
 

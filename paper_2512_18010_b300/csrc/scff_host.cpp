@@ -1320,7 +1320,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
             const PlanJob &pj = P->jobs[i];
             const int64_t M = (int64_t)pj.S * pj.job.grid->nx;
             const int64_t N = (int64_t)pj.job.grid->ny * pj.job.grid->nz;
-            nitems_est[g] += (size_t)((M + 127) / 128) * (size_t)((N + 127) / 128);
+            nitems_est[g] += (size_t)((M + 127) / 128) * (size_t)((N + 127) / 128) + tc_num_sms();
         }
         items_bytes += up1k(sizeof(int4) * nitems_est[g]);
     }

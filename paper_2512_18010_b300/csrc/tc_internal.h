@@ -55,7 +55,23 @@ struct TcJobDev {
     int mirror, nxf;
     float2 *f;             // [S][nq] complex output
     float *f2;             // [S][nq] or null
+    // Tail split: the last split_tiles tiles of the job run as nsplit parts over
+    // disjoint k ranges; parts write raw partial sums to part[slot][BM][BN] and
+    // the last of the eight warp regions of a tile to arrive (counter cnt[tile][8])
+    // sums the parts in order and writes the tile.  nsplit = 0: no split.
+    float2 *part;
+    int *cnt;
+    int nsplit, split_tiles;
 };
+
+// Work item of the persistent kernel (int4):
+//   x = job | (slot + 1) << 16   (slot: part of a split tile, 0 in the high half: whole tile)
+//   y = m-tile | k0 << 16        (k0: first k-chunk of the item)
+//   z = n-tile, w = number of k-chunks.
+__host__ __device__ inline int item_job(int x) { return x & 0xFFFF; }
+__host__ __device__ inline int item_slot(int x) { return (x >> 16) - 1; }
+__host__ __device__ inline int item_mt(int y) { return y & 0xFFFF; }
+__host__ __device__ inline int item_k0(int y) { return y >> 16; }
 
 // Workspace of one job prepared by tc_prep_job.
 size_t tc_job_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind);
