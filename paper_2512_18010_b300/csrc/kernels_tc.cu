@@ -1,5 +1,5 @@
-// Tensor-core (tcgen05) split-BF16 evaluation of the form factor on product
-// grids.
+// Tensor-core (tcgen05) split-precision evaluation of the form factor on
+// product grids.
 //
 // The Cartesian method factorises per axis (Eq. CartesianMethod with the
 // V-tensors of Eq. CartesianVector): each pair term is
@@ -12,20 +12,27 @@
 // turns the whole product-grid evaluation into one dense complex contraction
 //   f[(s, ix), (iy, iz)] = sum_k A[(s,ix), k] W[k, (iy,iz)],
 // which runs on the 5th-generation tensor cores:
-//   * A (complex, FP32) is split into BF16 hi + lo parts and stored as the
-//     128B-row-free SW64 K-major shared-memory image of each 128 x 32 tile,
-//     so one 1-D bulk TMA copy per stage lands it in shared memory;
+//   * A (complex, FP32) is split into pieces (BF16 hi/mid/lo, BF16 hi/lo or
+//     TF32 hi/lo) and stored as the SW64-swizzled K-major shared-memory image
+//     of each 128 x 32-byte tile, so one 1-D bulk TMA copy lands a stage;
 //   * W is generated on the fly by eight warps from FP64-accurate per-axis
-//     tables (FP32 storage) and split into BF16 hi + lo in shared memory;
-//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM):
-//     Re += Ar Wr - Ai Wi and Im += Ar Wi + Ai Wr, each product as
-//     hi*hi + hi*lo + lo*hi (three passes), the minus sign through the
-//     instruction's negate-A bit;
-//   * the accumulators (Re and Im, 128 x 256 FP32 each: all 512 TMEM columns)
-//     are drained with tcgen05.ld into the FP32 output, optionally every
-//     `drain_every` k-chunks to bound the length of each TMEM accumulation.
-// FP64 is used only for the per-axis phase/Gaussian tables (range reduction
-// of q.P) and upstream in the pair-prep.
+//     tables (FP32 storage) and split the same way in shared memory;
+//   * one thread issues tcgen05.mma (kind::f16 or kind::tf32, M = N = 128):
+//     Re += Ar Wr - Ai Wi and Im += Ar Wi + Ai Wr, each product as the piece
+//     products that matter for the split (six for hi/mid/lo, three for
+//     hi/lo), the minus sign through the instruction's negate-A bit;
+//   * two TMEM accumulator sets (Re and Im, 128 x 128 FP32 each: all 512
+//     columns) alternate, and the generators drain a finished set into FP32
+//     registers every `drain_every` k-chunks (bounding each TMEM sum);
+//   * one persistent CTA per SM walks a cost-sorted list of (job, m-tile,
+//     n-tile) items; the last (tiles mod SMs) tiles of a job run as parts over
+//     disjoint k ranges whose partial sums the last part to finish adds up in
+//     part order (the tail split);
+//   * on antisymmetric grids only half the rows are evaluated and the
+//     epilogue also writes f(-q) = conj(f(q)) at the mirrored point.
+// The same kernel runs the spherical method's contractions (tc_run_generic),
+// with W generated from its radial and harmonic tables.  FP64 is used only for
+// the tables (range reduction of q.P) and upstream in the pair-prep.
 #include <cuda_bf16.h>
 #include <math.h>
 
