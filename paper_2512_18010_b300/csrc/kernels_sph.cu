@@ -36,6 +36,20 @@ namespace scff {
 
 using sph::kMaxBigL;
 
+// Recurrence coefficients of the associated Legendre functions for l <= kMaxBigL
+// (sph::plm_coefficients), filled once per device by sph_plm_init_kernel.
+constexpr int kPlmTri = (kMaxBigL + 1) * (kMaxBigL + 2) / 2;
+__device__ double g_plm_ab[2 * kPlmTri];
+
+__global__ void sph_plm_init_kernel() {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kPlmTri) return;
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= t) ++l;
+    const int m = t - l * (l + 1) / 2;
+    sph::plm_coefficients(l, m, g_plm_ab + 2 * t);
+}
+
 __device__ __forceinline__ int pair_class(const PairSetDev &ps, int pr) {
     int L = 0;
     while (L < kMaxPairL && pr >= ps.pair_off[L + 1]) ++L;
@@ -89,7 +103,7 @@ __global__ void sph_ypair_kernel(PairSetDev ps, const double *__restrict__ geom,
     const double x = r > 0.0 ? Pz / r : 1.0;
     const double phi = r > 0.0 ? atan2(Py, Px) : 0.0;
     double col[kMaxBigL + 1];
-    sph::plm_column(Lmax, M, x, col);
+    sph::plm_column_tab(Lmax, M, x, g_plm_ab, col);
     double sn, cs;
     sincos(M * phi, &sn, &cs);
     const int NLM = (Lmax + 1) * (Lmax + 1);
@@ -246,7 +260,7 @@ __global__ void sph_theta_table_kernel(const double *__restrict__ theta, int nt,
     if (idx >= nt * (lmax + 1)) return;
     const int it = idx / (lmax + 1), m = idx % (lmax + 1);
     double col[sph::kMaxLmax + 1];
-    sph::plm_column(lmax, m, cos(theta[it]), col);
+    sph::plm_column_tab(lmax, m, cos(theta[it]), g_plm_ab, col);
     const double sgn = (m & 1) ? -1.0 : 1.0;
     for (int l = m; l <= lmax; ++l) {
         V v;
@@ -379,6 +393,11 @@ __global__ void __launch_bounds__(256) gen_gemm64_kernel(Gemm64Args a) {
 // ------------------------------------------------------------------ launchers
 
 static unsigned blocks_of(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_sph_plm_init(cudaStream_t st) {
+    sph_plm_init_kernel<<<blocks_of(kPlmTri, 256), 256, 0, st>>>();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sph_radial(const PairSetDev &ps, const double *geom, const double *q, int nq, int NL, int fp64,
                               void *table, cudaStream_t st) {

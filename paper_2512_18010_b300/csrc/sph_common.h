@@ -74,6 +74,41 @@ __host__ __device__ inline void plm_column(int lmax, int m, double x, double *co
     }
 }
 
+// Coefficients of the recurrences above, one pair per (l, m) at tri(l, m):
+//   l == m:     ab[0] = -sqrt((2m + 1) / (2m))   (m >= 1; the p_mm step)
+//   l == m + 1: ab[0] = sqrt(2m + 3)
+//   l >= m + 2: ab[0] = a_lm, ab[1] = b_lm
+__host__ __device__ inline void plm_coefficients(int l, int m, double *ab) {
+    ab[0] = ab[1] = 0.0;
+    if (l == m) {
+        if (m >= 1) ab[0] = -sqrt((2.0 * m + 1.0) / (2.0 * m));
+    } else if (l == m + 1) {
+        ab[0] = sqrt(2.0 * m + 3.0);
+    } else {
+        ab[0] = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+        ab[1] = sqrt(((double)(l - 1) * (l - 1) - (double)m * m) / (4.0 * (l - 1) * (l - 1) - 1.0));
+    }
+}
+
+// plm_column with the coefficients read from a table filled by
+// plm_coefficients (2 doubles per tri(l, m)) instead of recomputed.
+__host__ __device__ inline void plm_column_tab(int lmax, int m, double x, const double *ab, double *col) {
+    const double s = sqrt(fmax(0.0, 1.0 - x * x));
+    double pmm = 0.28209479177387814;
+    for (int k = 1; k <= m; ++k) pmm = ab[2 * tri_index(k, k)] * s * pmm;
+    col[0] = pmm;
+    if (m + 1 > lmax) return;
+    double pl2 = pmm, pl1 = ab[2 * tri_index(m + 1, m)] * x * pmm;
+    col[1] = pl1;
+    for (int l = m + 2; l <= lmax; ++l) {
+        const double *c = ab + 2 * tri_index(l, m);
+        const double pl = c[0] * (x * pl1 - c[1] * pl2);
+        col[l - m] = pl;
+        pl2 = pl1;
+        pl1 = pl;
+    }
+}
+
 // p_l^m for any sign of m: Y_l^{-m} = (-1)^m conj(Y_l^m), so with
 // Y_l^m = p_l^m e^{i m phi} for every m, p_l^{-m} = (-1)^m p_l^m.
 __host__ __device__ inline double plm_signed(const double *p, int l, int m) {

@@ -53,6 +53,8 @@ __host__ __device__ inline int sph_parity_rows(int lam, int par) {
 
 // Table and contraction kernels of the spherical method; `fp64` selects
 // double2 (else float2) tables.
+// Fills the device table of Legendre recurrence coefficients (once per device).
+cudaError_t launch_sph_plm_init(cudaStream_t st);
 cudaError_t launch_sph_radial(const PairSetDev &ps, const double *geom, const double *q, int nq, int NL, int fp64,
                               void *table, cudaStream_t st);
 cudaError_t launch_sph_ypair(const PairSetDev &ps, const double *geom, int Lmax, int fp64, void *table,

@@ -109,6 +109,7 @@ std::vector<double> theta_table() {
 
 // Molecule-independent tables of the spherical method, cached per context.
 struct SphCache {
+    bool plm_ready = false;    // device table of Legendre recurrence coefficients filled
     double2 *theta = nullptr;  // [84][49]
     int lmax = -1, lam = -1;   // Gaunt table key
     int *goff = nullptr;       // [NR + 1]
@@ -192,6 +193,11 @@ scff_status build_gaunt(SphCache *cache, int lmax, int lam) {
 scff_status get_cache(scff_ctx *c, int lmax, int lam, SphCache **out) {
     if (!c->sph) c->sph = new SphCache();
     SphCache *k = c->sph;
+    if (!k->plm_ready) {
+        if (launch_sph_plm_init(0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess)
+            return sfail(SCFF_ERR_CUDA, "scff_spherical: cannot fill the Legendre coefficient table");
+        k->plm_ready = true;
+    }
     if (!k->theta) {
         const std::vector<double> t = theta_table();
         if (cudaMalloc(&k->theta, sizeof(double) * t.size()) != cudaSuccess)
