@@ -81,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed building libscff.so")
     link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *[_obj(s) for s in SOURCES],
-            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+            "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-Xlinker", "--no-undefined"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -42,6 +42,7 @@
 
 #include <algorithm>
 #include <string.h>
+#include <thread>
 #include <vector>
 
 namespace scff {
@@ -225,13 +226,22 @@ struct Layout {
 // Tail split of a job with `items` equal tiles of nkc chunks on P SMs: the
 // last R = items mod P tiles run as s parts (k split evenly), so that the
 // final wave keeps the SMs busy.  s = 0: no split.
+// s (2..16, parts of at least 8 chunks, at most 2P parts in all) minimises
+// the tail's length ceil(R s / P) / s in tile times; no s below 1 tile time
+// leaves the tail unsplit.
 static void tail_split(int items, int nkc, int P, int *R, int *s) {
     *R = items % P;
     *s = 0;
     if (*R == 0 || nkc >= 32768) return;
-    int parts = std::min(16, std::min(P / *R, nkc / 8));
-    if (parts >= 2) *s = parts;
-    else *R = 0;
+    double best = 1.0;
+    for (int c = 2; c <= 16 && c <= nkc / 8 && (int64_t)*R * c <= 2 * (int64_t)P; ++c) {
+        const double t = (double)((*R * c + P - 1) / P) / c;
+        if (t < best - 1e-9) {
+            best = t;
+            *s = c;
+        }
+    }
+    if (!*s) *R = 0;
 }
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -261,8 +271,8 @@ static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     o = align_up(o + sizeof(int2) * (size_t)L.K_pad, 1024);
     L.off_A = o;
     o = align_up(o + (size_t)L.n_mt * L.nkc * a_stage, 1024);
-    // a split never needs more than P partial tiles (R * s <= P)
-    L.part_tiles = std::min<int64_t>(tc_num_sms(), (int64_t)L.n_mt * L.n_nt * 16);
+    // a split never needs more than 2P partial tiles (R * s <= 2P)
+    L.part_tiles = std::min<int64_t>(2 * (int64_t)tc_num_sms(), (int64_t)L.n_mt * L.n_nt * 16);
     L.off_part = o;
     o = align_up(o + sizeof(float2) * (size_t)L.part_tiles * BM * BN, 1024);
     L.off_cnt = o;
@@ -475,7 +485,7 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
 template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_persistent_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items,
-                         int drain_every, int *err) {
+                         int drain_every, int *err, int *progress) {
     using KD = Kind<KIND>;
     constexpr bool TF32 = KD::TF32;
     constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = KD::STAGES;
@@ -599,7 +609,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // warps of a lane group take column halves.
         const int lg = warp & 3;
         const int colh = ((warp - 4) >> 2) * CQ;
-        int gc = 0, gbase = 0;
+        int gc = 0, gbase = 0, done_items = 0;
         bool ok = true;
         for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
             const int4 item = items[idx];
@@ -755,6 +765,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
             }
+            if (progress && ok) {
+                // publish how many items this warp has finished: its writes
+                // above reach memory (system scope) before the count does
+                __threadfence_system();
+                __syncwarp();
+                ++done_items;
+                if (lane == 0)
+                    *reinterpret_cast<volatile int *>(progress + blockIdx.x * GEN_WARPS + (warp - 4)) = done_items;
+            }
         }
         if (!ok) *abort_flag = 1;
     }
@@ -783,8 +802,10 @@ size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     const tc::Layout L = kind == tc::KIND_BF16X2   ? tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz)
                          : kind == tc::KIND_BF16X3 ? tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz)
                                                    : tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz);
-    // work items: the tiles plus at most P extra parts of the tail split
-    return L.total + 1024 + sizeof(TcJobDev) + sizeof(int4) * ((size_t)L.n_mt * L.n_nt + tc_num_sms());
+    // descriptors (one per band) and work items: the tiles plus at most 2P
+    // parts of the tail split per band
+    return L.total + 1024 + 256 + (sizeof(TcJobDev) * kMaxBands + 255) / 256 * 256 +
+           sizeof(int4) * (size_t)tc_max_items((int64_t)L.n_mt * L.n_nt + (int64_t)(kMaxBands - 1) * 2 * tc_num_sms());
 }
 
 // Descriptor of one job whose tables and A image live in `ws`.
@@ -885,35 +906,117 @@ cudaError_t tc_prep_job(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launch
     }
 }
 
+// Items of the tiles (mt, nt) of descriptor j, in the given order; the last
+// J.split_tiles of them run as J.nsplit parts.
+static void append_items(const TcJobDev &J, int j, const std::vector<int2> &tiles, std::vector<int4> &items) {
+    const int n = (int)tiles.size();
+    const int first_split = J.nsplit ? n - J.split_tiles : n;
+    for (int i = 0; i < n; ++i) {
+        const int mt = tiles[i].x, nt = tiles[i].y;
+        if (i < first_split) {
+            items.push_back(make_int4(j, mt, nt, J.nkc));
+            continue;
+        }
+        for (int p = 0; p < J.nsplit; ++p) {
+            const int k0 = (int)((int64_t)p * J.nkc / J.nsplit), k1 = (int)((int64_t)(p + 1) * J.nkc / J.nsplit);
+            const int slot = (i - first_split) * J.nsplit + p;
+            items.push_back(make_int4(j | ((slot + 1) << 16), mt | (k0 << 16), nt, k1 - k0));
+        }
+    }
+}
+
 // Work list of a group of prepared jobs: every (job, m-tile, n-tile), most
 // expensive first (longest k loop), so the static round-robin assignment of
 // items to CTAs balances well.
 void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) {
     items.clear();
+    std::vector<int2> tiles;
     for (int j = 0; j < n_jobs; ++j) {
         const TcJobDev &J = jobs[j];
-        const int n_items = J.n_mt * J.n_nt;
-        const int first_split = J.nsplit ? n_items - J.split_tiles : n_items;
-        for (int i = 0; i < n_items; ++i) {
-            const int mt = i / J.n_nt, nt = i % J.n_nt;
-            if (i < first_split) {
-                items.push_back(make_int4(j, mt, nt, J.nkc));
-                continue;
-            }
-            for (int p = 0; p < J.nsplit; ++p) {
-                const int k0 = (int)((int64_t)p * J.nkc / J.nsplit), k1 = (int)((int64_t)(p + 1) * J.nkc / J.nsplit);
-                const int slot = (i - first_split) * J.nsplit + p;
-                items.push_back(make_int4(j | ((slot + 1) << 16), mt | (k0 << 16), nt, k1 - k0));
-            }
-        }
+        tiles.clear();
+        for (int i = 0; i < J.n_mt * J.n_nt; ++i) tiles.push_back(make_int2(i / J.n_nt, i % J.n_nt));
+        append_items(J, j, tiles, items);
     }
     // longest first; the stable order keeps each job's tiles row-major and its parts last
     std::stable_sort(items.begin(), items.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
 }
 
+// Runs of n-tiles [runs[i][0], runs[i][1]) of the band [d0, d1).  With the
+// mirror, tile nt and its mirror n_nt-1-nt (which receives nt's mirrored
+// columns when N is a multiple of BN) belong to the same band: bands are
+// ranges of d = min(nt, n_nt-1-nt).  Without it d = nt.  Returns the number
+// of runs (0..2).
+static int band_runs(int n_nt, bool mirror, int d0, int d1, int runs[2][2]) {
+    if (!mirror) {
+        runs[0][0] = d0;
+        runs[0][1] = d1;
+        return d1 > d0 ? 1 : 0;
+    }
+    int n = 0;
+    if (d1 > d0) {
+        runs[n][0] = d0;
+        runs[n][1] = d1;
+        ++n;
+    }
+    const int lo = std::max(n_nt - d1, d1), hi = n_nt - d0;
+    if (hi > lo) {
+        runs[n][0] = lo;
+        runs[n][1] = hi;
+        ++n;
+    }
+    return n;
+}
+
+// Output columns of the d values below e: 2e column tiles with the mirror
+// (one for the middle tile of an odd n_nt), else e.
+static int64_t band_cols(int n_nt, bool mirror, int e) { return mirror ? std::min(2 * (int64_t)e, (int64_t)n_nt) : e; }
+
+// Band boundaries 0 = b[0] < ... < b[G] = D in d units for the band-major
+// tile order of one launch on `grid` CTAs; returns G (1: no banding).  A
+// requested count gives equal bands.  Automatic (jobs of at least 1.25
+// waves): CTA c runs items c, c + grid, ..., so the items below k * grid are
+// all written when wave k ends; the bands end at the last d boundary below
+// each wave end (the last kMaxBands - 1 of them), so each band's copy starts
+// one wave after its first tiles and only the last wave's columns (less the
+// tail split's time) wait for the launch to end.  first_split, nsplit: the
+// tail split of the job's tile count (items of tile t >= first_split are its
+// nsplit parts).
+static int band_bounds(const TcJobDev &jd, int requested, int grid, int64_t first_split, int nsplit,
+                       int b[kMaxBands + 1]) {
+    using namespace tc;
+    const int n_mt = jd.n_mt, n_nt = jd.n_nt;
+    const bool mirror = jd.mirror != 0;
+    if (requested == 1 || n_mt <= 0 || n_nt <= 0) return 1;
+    if (mirror && jd.N % BN) return 1;  // mirrored columns would straddle tiles
+    const int D = mirror ? (n_nt + 1) / 2 : n_nt;
+    int G = 0;
+    b[0] = 0;
+    if (requested > 0) {
+        G = std::min(std::min(requested, kMaxBands), D);
+        for (int g = 1; g <= G; ++g) b[g] = (int)((int64_t)g * D / G);
+        return G >= 2 ? G : 1;
+    }
+    const int64_t tiles = (int64_t)n_mt * n_nt;
+    if (tiles * 4 < 5 * (int64_t)grid) return 1;
+    auto item_end = [&](int e) {
+        const int64_t t = n_mt * band_cols(n_nt, mirror, e);
+        return t <= first_split ? t : first_split + (t - first_split) * nsplit;
+    };
+    std::vector<int> ends;  // d boundaries at wave ends, increasing
+    for (int64_t k = 1; item_end(D) > k * grid; ++k) {
+        int e = ends.empty() ? 0 : ends.back();
+        while (e < D && item_end(e + 1) <= k * grid) ++e;
+        if (e > (ends.empty() ? 0 : ends.back())) ends.push_back(e);
+    }
+    const int keep = std::min((int)ends.size(), kMaxBands - 1);
+    for (int i = (int)ends.size() - keep; i < (int)ends.size(); ++i) b[++G] = ends[i];
+    b[++G] = D;
+    return G >= 2 ? G : 1;
+}
+
 template <int KIND>
 static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
-                                int grid_ctas, int64_t *launches, cudaStream_t st) {
+                                int grid_ctas, int64_t *launches, cudaStream_t st, int *progress) {
     using namespace tc;
     using KD = Kind<KIND>;
     static bool attr_set = false;
@@ -933,19 +1036,25 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
     }
     if (n_items <= 0) return cudaSuccess;
     const int grid = std::max(1, std::min(grid_ctas, n_items));
-    tc_persistent_kernel<KIND><<<grid, THREADS, KD::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err);
+    tc_persistent_kernel<KIND><<<grid, THREADS, KD::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err,
+                                                                     progress);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
-                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st) {
+                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st, int *progress) {
     switch (kind) {
-    case tc::KIND_BF16X2: return persistent_t<tc::KIND_BF16X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st);
-    case tc::KIND_BF16X3: return persistent_t<tc::KIND_BF16X3>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st);
-    default: return persistent_t<tc::KIND_TF32X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st);
+    case tc::KIND_BF16X2:
+        return persistent_t<tc::KIND_BF16X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress);
+    case tc::KIND_BF16X3:
+        return persistent_t<tc::KIND_BF16X3>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress);
+    default:
+        return persistent_t<tc::KIND_TF32X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress);
     }
 }
+
+int64_t tc_max_items(int64_t tiles) { return tiles + 2 * (int64_t)tc_num_sms(); }
 
 int tc_num_sms() {
     static int n = 0;
@@ -959,16 +1068,44 @@ int tc_num_sms() {
 }
 
 // Single job: prepare it in the workspace, then one persistent launch over
-// its tiles.  The job descriptor and work list go to the end of the workspace.
+// its tiles.  The descriptor and work list go to the end of the workspace.
+// With host outputs and bands, the tiles are ordered band by band, the launch
+// reports its progress, and each band's columns are copied to the host while
+// later bands compute (see TcArgs).
 cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st) {
+    using tc::BN;
     const size_t jb = tc_job_bytes(*a.ps, a.S, a.nx, a.ny, a.nz, a.kind);
     if (jb + 1024 + sizeof(TcJobDev) > a.ws_bytes) return cudaErrorInvalidValue;
     TcJobDev jd;
     memset(&jd, 0, sizeof(jd));
     cudaError_t e = tc_prep_job(a, a.ws, &jd, launches, st);
     if (e != cudaSuccess) return e;
+    const bool can_band = a.f_host && a.copy_st && a.progress_dev && a.progress_host && a.ev_done && a.ev_copied;
+    // the job's tail split (job_desc_t) covers its last split_tiles tiles in any order
+    const int64_t n_tiles = (int64_t)jd.n_mt * jd.n_nt;
+    const int64_t first_split = jd.nsplit ? n_tiles - jd.split_tiles : n_tiles;
+    const int64_t n_items_all = first_split + (n_tiles - first_split) * (jd.nsplit ? jd.nsplit : 1);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tc_num_sms(), n_items_all));
+    int bounds[kMaxBands + 1];
+    const int G = can_band ? band_bounds(jd, a.n_bands, grid, first_split, jd.nsplit, bounds) : 1;
     std::vector<int4> items;
-    tc_build_items(&jd, 1, items);
+    int runs[kMaxBands][2][2], nruns[kMaxBands];
+    int64_t band_end[kMaxBands];
+    if (G == 1) {
+        tc_build_items(&jd, 1, items);
+    } else {
+        // tiles band by band; band g ends after the items of its tiles
+        std::vector<int2> tiles;
+        for (int g = 0; g < G; ++g) {
+            nruns[g] = band_runs(jd.n_nt, jd.mirror != 0, bounds[g], bounds[g + 1], runs[g]);
+            for (int mt = 0; mt < jd.n_mt; ++mt)
+                for (int r = 0; r < nruns[g]; ++r)
+                    for (int nt = runs[g][r][0]; nt < runs[g][r][1]; ++nt) tiles.push_back(make_int2(mt, nt));
+            const int64_t t = (int64_t)tiles.size();
+            band_end[g] = t <= first_split ? t : first_split + (t - first_split) * jd.nsplit;
+        }
+        append_items(jd, 0, tiles, items);
+    }
     uint8_t *tail = static_cast<uint8_t *>(a.ws) + (jb + 255) / 256 * 256;
     TcJobDev *d_job = reinterpret_cast<TcJobDev *>(tail);
     int4 *d_items = reinterpret_cast<int4 *>(tail + 256);
@@ -978,9 +1115,51 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
+    const int n_items = (int)items.size();
+    if (n_items != n_items_all) return cudaErrorInvalidValue;
+    if (G > 1)  // no launch of this context is running: the slots are free
+        for (int i = 0; i < grid * tc::GEN_WARPS; ++i) a.progress_host[i] = 0;
     if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
-    return tc_launch_persistent(a.kind, d_job, d_items, (int)items.size(), a.drain_every, a.err, tc_num_sms(),
-                                launches, st);
+    e = tc_launch_persistent(a.kind, d_job, d_items, n_items, a.drain_every, a.err, grid, launches, st,
+                             G > 1 ? a.progress_dev : nullptr);
+    if (a.bands_used) *a.bands_used = G;
+    if (e != cudaSuccess || G == 1) return e;
+    if ((e = cudaEventRecord(a.ev_done, st)) != cudaSuccess) return e;
+    // CTA b runs items b, b + grid, ...: items [0, E) are written once each of
+    // its generator warps has finished ceil((E - b) / grid) items (a split
+    // tile's last part writes the tile before it counts itself)
+    auto written = [&](int64_t E) {
+        for (int b = 0; b < grid && b < E; ++b) {
+            const int need = (int)((E - b + grid - 1) / grid);
+            for (int w = 0; w < tc::GEN_WARPS; ++w)
+                if (a.progress_host[b * tc::GEN_WARPS + w] < need) return false;
+        }
+        return true;
+    };
+    const size_t rows = (size_t)a.S * a.nx;  // output rows (s, ix) of N columns
+    bool launch_over = false;
+    for (int g = 0; g < G; ++g) {
+        // the launch ends in any case (every device wait is bounded), and
+        // then every band is final
+        while (!launch_over && !written(band_end[g])) {
+            const cudaError_t q = cudaEventQuery(a.ev_done);
+            if (q == cudaSuccess) launch_over = true;
+            else if (q != cudaErrorNotReady) return q;
+            else std::this_thread::yield();
+        }
+        for (int r = 0; r < nruns[g]; ++r) {
+            const int64_t c0 = (int64_t)runs[g][r][0] * BN, c1 = std::min<int64_t>(jd.N, (int64_t)runs[g][r][1] * BN);
+            if (c1 <= c0) continue;
+            e = cudaMemcpy2DAsync(a.f_host + 2 * c0, 8 * jd.N, a.f + 2 * c0, 8 * jd.N, 8 * (c1 - c0), rows,
+                                  cudaMemcpyDeviceToHost, a.copy_st);
+            if (e == cudaSuccess && a.f2_host && a.f2)
+                e = cudaMemcpy2DAsync(a.f2_host + c0, 4 * jd.N, a.f2 + c0, 4 * jd.N, 4 * (c1 - c0), rows,
+                                      cudaMemcpyDeviceToHost, a.copy_st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if ((e = cudaEventRecord(a.ev_copied, a.copy_st)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(st, a.ev_copied, 0);
 }
 
 // ------------------------------------------------------------------ generic two-table contraction

@@ -191,6 +191,10 @@ extern "C" void scff_destroy(scff_ctx *c) {
     cudaFreeHost(c->h_err);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->band_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_st) cudaStreamDestroy(c->copy_st);
+    if (c->progress_h) cudaFreeHost(c->progress_h);
     delete c;
 }
 
@@ -534,6 +538,14 @@ extern "C" scff_status scff_set_hermitian(scff_ctx *c, int enable) {
     return SCFF_OK;
 }
 
+extern "C" scff_status scff_set_download_bands(scff_ctx *c, int n_bands) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_download_bands: NULL context");
+    if (n_bands < 0 || n_bands > kMaxBands)
+        return fail(SCFF_ERR_INVALID_ARG, "scff_set_download_bands: %d bands (0..%d)", n_bands, kMaxBands);
+    c->bands = n_bands;
+    return SCFF_OK;
+}
+
 extern "C" scff_status scff_qgrid_product(scff_ctx *c, const double *qx, int nx, const double *qy, int ny,
                                           const double *qz, int nz, scff_qgrid_h *out) {
     if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_qgrid_product: NULL context or output");
@@ -664,9 +676,18 @@ static size_t ff_footprint(const PairSetDev &ps, const scff_qgrid_s *g, int S, i
     return foot;
 }
 
-// Pair-prep and q-evaluation of one configuration into device outputs.
+// Host destination of a call with host outputs: the tensor-core path may copy
+// the result there itself, band by band, overlapped with its launches (done).
+struct HostOut {
+    void *f, *f2;
+    bool done;
+};
+
+// Pair-prep and q-evaluation of one configuration into device outputs (and,
+// with ho, possibly already downloaded to ho's host buffers).
 static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, scff_qgrid_s *g, int precision,
-                          double scale, void *fdev, void *f2dev, const FFChoice &ch, cudaStream_t st) {
+                          double scale, void *fdev, void *f2dev, const FFChoice &ch, cudaStream_t st,
+                          HostOut *ho = nullptr) {
     const int S = t->S;
     const int64_t nq = g->n;
     const bool fp64 = precision == SCFF_FP64;
@@ -710,7 +731,29 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         ta.kind = kind;
         ta.drain_every = ch.drain;
         ta.half = grid_half(c, g);
+        int used = 1;
+        if (ho && c->bands != 1) {
+            if (!c->copy_st) CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+            for (auto &e : c->band_ev)
+                if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            if (!c->progress_h) {
+                const size_t pb = sizeof(int) * 8 * (size_t)tc_num_sms();
+                CUDA_TRY(cudaHostAlloc((void **)&c->progress_h, pb, cudaHostAllocMapped));
+                memset(c->progress_h, 0, pb);
+                CUDA_TRY(cudaHostGetDevicePointer((void **)&c->progress_d, c->progress_h, 0));
+            }
+            ta.n_bands = c->bands;
+            ta.f_host = (float *)ho->f;
+            ta.f2_host = (float *)ho->f2;
+            ta.copy_st = c->copy_st;
+            ta.progress_dev = c->progress_d;
+            ta.progress_host = c->progress_h;
+            ta.ev_done = c->band_ev[0];
+            ta.ev_copied = c->band_ev[1];
+            ta.bands_used = &used;
+        }
         CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
+        if (ho) ho->done = used > 1;
     } else {
         DirectArgs a;
         memset(&a, 0, sizeof(a));
@@ -1073,11 +1116,11 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
             CUDA_TRY(cudaMemsetAsync(fdev, 0, (size_t)S * nq * 2 * rsz, st));
             if (f2dev) CUDA_TRY(cudaMemsetAsync(f2dev, 0, (size_t)S * nq * rsz, st));
         }
-    } else {
-        TRY(ff_run(c, *ps, t, g, precision, scale, fdev, f2dev, ch, st));
     }
+    HostOut ho = {f_out, f2_out, false};
+    if (ps->n_pair != 0) TRY(ff_run(c, *ps, t, g, precision, scale, fdev, f2dev, ch, st, out_on_device ? nullptr : &ho));
     if (!out_on_device) {
-        if (nq > 0) {
+        if (nq > 0 && !ho.done) {
             CUDA_TRY(cudaMemcpyAsync(f_out, fdev, (size_t)S * nq * 2 * rsz, cudaMemcpyDeviceToHost, st));
             if (f2_out) CUDA_TRY(cudaMemcpyAsync(f2_out, f2dev, (size_t)S * nq * rsz, cudaMemcpyDeviceToHost, st));
         }
@@ -1320,7 +1363,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
             const PlanJob &pj = P->jobs[i];
             const int64_t M = (int64_t)pj.S * pj.job.grid->nx;
             const int64_t N = (int64_t)pj.job.grid->ny * pj.job.grid->nz;
-            nitems_est[g] += (size_t)((M + 127) / 128) * (size_t)((N + 127) / 128) + tc_num_sms();
+            nitems_est[g] += (size_t)tc_max_items(((M + 127) / 128) * ((N + 127) / 128));
         }
         items_bytes += up1k(sizeof(int4) * nitems_est[g]);
     }

@@ -59,6 +59,13 @@ struct scff_ctx {
     // Hermitian half (scff_set_hermitian): on antisymmetric product grids
     // compute half the points and fill the rest with f(-q) = conj(f(q))
     int hermitian = 1;
+    // overlapped download of host outputs (scff_set_download_bands): band
+    // count (0 = automatic); copy stream, events (end of launch, end of
+    // copies) and host-mapped progress slots, created on first use
+    int bands = 0;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t band_ev[2] = {};
+    int *progress_h = nullptr, *progress_d = nullptr;
 };
 
 // 1 when every axis of the host array pairs point i with -(point n-1-i) exactly.

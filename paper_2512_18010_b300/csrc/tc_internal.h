@@ -11,6 +11,8 @@
 
 namespace scff {
 
+constexpr int kMaxBands = 8;  // most launches of one job's overlapped download
+
 struct TcArgs {
     const PairSetDev *ps;
     const float *coef32;       // [n_sblk][n_rows][SB] signed coefficients (FP32)
@@ -31,6 +33,21 @@ struct TcArgs {
     // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
     // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
     int half;
+    // Host outputs with overlapped download (optional, f_host non-null): the
+    // tiles are ordered band by band (bands of output columns) in one launch
+    // that reports its progress to host-mapped slots; the host issues the
+    // copy of each band's columns to f_host / f2_host on copy_st as soon as
+    // every tile of the band is written, while the launch goes on.  st waits
+    // for the last copy.  n_bands: 0 = chosen from the tile count, 1 = off,
+    // 2..kMaxBands = that many equal bands where the grid allows.
+    // *bands_used gets the band count (1: nothing was copied).
+    int n_bands;
+    float *f_host, *f2_host;
+    cudaStream_t copy_st;
+    int *progress_dev;                  // >= 8 x SMs ints, host-mapped (device address)
+    volatile int *progress_host;        // the same slots (host address)
+    cudaEvent_t ev_done, ev_copied;     // end of the launch, end of the copies
+    int *bands_used;
 };
 
 // Device descriptor of one prepared job (read by the persistent kernel).
@@ -84,8 +101,14 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
 cudaError_t tc_prep_job(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launches, cudaStream_t st);
 void tc_job_desc(const TcArgs &a, void *ws, TcJobDev *jd);
 void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items);
+// Most work items one job of `tiles` tiles contributes (its tail split adds
+// at most 2P parts).
+int64_t tc_max_items(int64_t tiles);
+// progress (optional, e.g. host-mapped): progress[cta * 8 + w] = items that
+// generator warp w of CTA cta has finished (its outputs written and fenced
+// at system scope before the count); CTA b runs items b, b + grid, ...
 cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
-                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st);
+                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st, int *progress = nullptr);
 int tc_num_sms();
 
 // Generic two-table contraction on the tensor cores (the spherical method):

@@ -38,6 +38,7 @@ _SYMBOLS = [
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
     "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor", "scff_wait_selftest", "scff_set_hermitian",
+    "scff_set_download_bands",
 ]
 
 
@@ -147,6 +148,8 @@ def load(build_if_missing: bool = True):
     lib.scff_autotune_choice.restype = I32
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
+    lib.scff_set_download_bands.argtypes = [P, ctypes.c_int]
+    lib.scff_set_download_bands.restype = I32
     lib.scff_last_timing.argtypes = [P, P]
     lib.scff_kernel_launches.argtypes = [P]
     lib.scff_kernel_launches.restype = I64
@@ -545,6 +548,11 @@ class Context:
     def set_hermitian(self, enable: bool = True):
         """Evaluate half of an antisymmetric product grid and mirror f(-q) = conj(f(q)) (default on)."""
         _check(self.lib.scff_set_hermitian(self.h, 1 if enable else 0))
+
+    def set_download_bands(self, n_bands: int = 0):
+        """Host-output calls on the tensor cores: launches over column bands whose
+        downloads overlap the next band's compute (0 = automatic, 1 = off, 2..8)."""
+        _check(self.lib.scff_set_download_bands(self.h, int(n_bands)))
 
     def wait_selftest(self, tries: int = 4096):
         """Runs the bounded-wait failure path once; raises ScffError(TIMEOUT) as intended."""
