@@ -109,6 +109,7 @@ cudaError_t launch_pair_geom(const PairSetDev &ps, double *pair_geom, cudaStream
 // C tables are computed once (C in shared memory, indexed by the functions'
 // exponents) and reused for every state.
 constexpr int kPrepThreads = 128;
+constexpr int kPrepStates = 8;  // states per register block
 
 __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, const double *__restrict__ T,
                                                                 int S, int S_pad, int SB,
@@ -149,10 +150,16 @@ __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, c
     const bool same = (rr.x == rr.y);
     const int n = e[0] + e[1] + e[2];
     const double sgn = K * ((n & 2) ? -1.0 : 1.0);  // i^n = +1, +i, -1, -i
-    for (int s = 0; s < S_pad; ++s) {
-        double acc = 0.0;
-        if (s < S) {
-            const double *Ts = T + (size_t)s * nbf * nbf;
+    // states in register blocks of kPrepStates: the function-pair factor
+    // w_i w_j D (state-independent) is formed once per block, and each state
+    // adds T^s_ij (+ T^s_ji) times it
+    const size_t nn = (size_t)nbf * nbf;
+    for (int s0 = 0; s0 < S_pad; s0 += kPrepStates) {
+        const int ns = min(kPrepStates, S - s0);
+        double acc[kPrepStates];
+#pragma unroll
+        for (int u = 0; u < kPrepStates; ++u) acc[u] = 0.0;
+        if (ns > 0) {
             for (int i = 0; i < n1; ++i) {
                 const double wi = ps.rec_w[kRecW * rr.x + i];
                 const int ai = fn_pow(t1, i, 0), bi = fn_pow(t1, i, 1), ci = fn_pow(t1, i, 2);
@@ -161,16 +168,29 @@ __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, c
                     const double D = Csm[(0 * 4 + ai) * 4 + aj][tid] * Csm[(1 * 4 + bi) * 4 + bj][tid] *
                                      Csm[(2 * 4 + ci) * 4 + cj][tid];
                     if (D == 0.0) continue;
-                    double tw = Ts[(size_t)(f1 + i) * nbf + (f2 + j)];
-                    if (!same) tw += Ts[(size_t)(f2 + j) * nbf + (f1 + i)];
-                    acc += tw * wi * ps.rec_w[kRecW * rr.y + j] * D;
+                    const double w = wi * ps.rec_w[kRecW * rr.y + j] * D;
+                    const double *Tij = T + (size_t)s0 * nn + (size_t)(f1 + i) * nbf + (f2 + j);
+                    const double *Tji = T + (size_t)s0 * nn + (size_t)(f2 + j) * nbf + (f1 + i);
+#pragma unroll
+                    for (int u = 0; u < kPrepStates; ++u) {
+                        if (u < ns) {
+                            double tw = Tij[u * nn];
+                            if (!same) tw += Tji[u * nn];
+                            acc[u] = fma(tw, w, acc[u]);
+                        }
+                    }
                 }
             }
         }
-        const double val = sgn * acc;
-        const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
-        if (coef64) coef64[idx] = val;
-        if (coef32) coef32[idx] = (float)val;
+#pragma unroll
+        for (int u = 0; u < kPrepStates; ++u) {
+            const int s = s0 + u;
+            if (s >= S_pad) break;
+            const double val = sgn * acc[u];
+            const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
+            if (coef64) coef64[idx] = val;
+            if (coef32) coef32[idx] = (float)val;
+        }
     }
 }
 

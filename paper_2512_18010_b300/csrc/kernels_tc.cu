@@ -288,9 +288,13 @@ static Layout make_layout_k(const PairSetDev &ps, int S, int nx, int ny, int nz)
 
 // ------------------------------------------------------------------ prep kernels
 
-// X_{pair,u}(q_i) = (i q_i)^u exp(-q_i^2/(4p)) e^{i q_i P_axis}, FP64 then FP32:
+// X_{pair,u}(q_i) = (i q_i)^u exp(-q_i^2/(4p)) e^{i q_i P_axis}, stored in FP32:
 // one thread per (pair, q_i) evaluates the Gaussian and the phase once and
-// writes the rows u = 0..L of its pair; the extra row n_axrows is zero.
+// writes the rows u = 0..L of its pair; the extra row n_axrows is zero.  The
+// phase q P is reduced to [-pi, pi] in FP64 (Cody-Waite with 2 pi split in
+// two doubles), so the FP32 sine and cosine of the remainder and the FP32
+// exponential are as accurate as the FP32 table entries; the powers of i q
+// are applied in FP64.
 __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict__ geom,
                                         const double *__restrict__ qaxis, int n, int axis, int64_t n_axrows,
                                         float2 *__restrict__ table) {
@@ -307,9 +311,14 @@ __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict_
     const int64_t row0 = ps.axrow_off[L] + (int64_t)(pr - ps.pair_off[L]) * (L + 1);
     const double q = qaxis[i];
     const double P = geom[4 * pr + axis], inv4p = geom[4 * pr + 3];
-    double sn, cs;
-    sincos(q * P, &sn, &cs);
-    double re = cs * exp(-q * q * inv4p), im = sn * exp(-q * q * inv4p);
+    constexpr double kTwoPiHi = 6.283185307179586, kTwoPiLo = 2.4492935982947064e-16;
+    const double th = q * P;
+    const double nk = rint(th * (1.0 / kTwoPiHi));
+    const float r = (float)fma(-nk, kTwoPiLo, fma(-nk, kTwoPiHi, th));
+    float sf, cf;
+    sincosf(r, &sf, &cf);
+    const double g = (double)expf((float)(-q * q * inv4p));
+    double re = (double)cf * g, im = (double)sf * g;
     for (int u = 0; u <= L; ++u) {
         table[(row0 + u) * n + i] = make_float2((float)re, (float)im);
         // times i q
@@ -349,6 +358,21 @@ __global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, in
     kofs[k] = make_int2((r.w + r.y) * ny, (r.w + r.z) * nz);  // Y and Z row offsets of this k
 }
 
+// Thread index -> (row m, 16-byte vector kv) of a tile image: consecutive
+// threads take the vectors of one chunk row, then the next row of the same
+// chunk, so a warp writes 512 contiguous bytes of each array of the image.
+template <int KIND>
+__device__ __forceinline__ void image_coords(int64_t idx, int nkc, int &m, int64_t &kv) {
+    using KD = Kind<KIND>;
+    constexpr int VPC = KD::BK / KD::PER_VEC;  // vectors per chunk row
+    const int v = (int)(idx % VPC);
+    const int r = (int)((idx / VPC) % BM);
+    const int64_t tile = idx / (VPC * BM);  // mt * nkc + kc
+    const int64_t kc = tile % nkc;
+    m = (int)(tile / nkc) * BM + r;
+    kv = kc * VPC + v;
+}
+
 // A[(s,ix), k] = sum_u D^s_{pair,(u,v,w)} X_{pair,u}(q_x[ix]), split into pieces
 // and written as the swizzled shared-memory image of each tile.  One thread
 // writes one 16-byte vector (PER_VEC consecutive k) of each array.
@@ -361,8 +385,9 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
     const int64_t kvn = K_pad / V;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)M_pad * kvn) return;
-    const int m = (int)(idx / kvn);
-    const int64_t kv = idx % kvn;
+    int m;
+    int64_t kv;
+    image_coords<KIND>(idx, nkc, m, kv);
     float re[V], im[V];
     const bool mvalid = m < M;
     const int s = mvalid ? m / nxr : 0, ix = mvalid ? m % nxr : 0;  // rows (s, ix < nxr); X has nx columns
@@ -413,8 +438,9 @@ __global__ void dense_image_kernel(const double2 *__restrict__ src, int64_t lda,
     const int64_t kvn = K_pad / V;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)M_pad * kvn) return;
-    const int m = (int)(idx / kvn);
-    const int64_t kv = idx % kvn;
+    int m;
+    int64_t kv;
+    image_coords<KIND>(idx, nkc, m, kv);
     float re[V], im[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) {
