@@ -385,20 +385,22 @@ scff_status scff_set_hermitian(scff_ctx *ctx, int enable);
 
 /*
  * Overlapped download of host outputs (scff_form_factor with out_on_device =
- * 0 on the tensor-core path).  The output tiles then run as several launches,
- * each over a band of output columns; when a band's launch ends its columns
- * are complete in every row and a pitched device-to-host copy of them runs on
- * a copy stream of the context while the next band computes, so only the
- * last band's copy adds to the call.  n_bands: 0 = automatic (default: jobs
- * of at least 1.25 waves of 128 x 128 tiles get up to 8 bands that shrink
- * geometrically towards the last, so each copy hides behind the next band's
- * launch), 1 = off (one launch, then one copy), 2..8 = that many equal bands
- * where the grid allows.  Banding is skipped
- * when the Hermitian half is on and ny*nz is not a multiple of 128 (mirrored
- * columns would cross tiles).  Each band has its own tail split, so results
- * can differ from a device-output call in the last bits of the FP32 sums of
- * split tiles; both are within the split-precision bounds.  Returns
- * SCFF_ERR_INVALID_ARG for n_bands outside 0..8.
+ * 0 on the tensor-core path).  The output tiles then run band by band in one
+ * launch, a band being a set of output columns (with the Hermitian half, a
+ * column tile and its mirror together); the launch reports its progress to
+ * host-mapped memory, and as soon as every tile of a band is written the host
+ * issues a pitched device-to-host copy of the band's columns on a copy stream
+ * of the context, so the copies run while later bands compute.  n_bands: 0 =
+ * automatic (default: jobs of at least 1.25 waves of 128 x 128 tiles get
+ * bands that end at the waves of the launch, up to 8), 1 = off (one copy
+ * after the launch), 2..8 = that many equal bands where the grid allows.
+ * Banding is skipped when the Hermitian half is on and ny*nz is not a
+ * multiple of 128 (mirrored columns would cross tiles).  The band order hands
+ * the tail split (the last tiles run as k-range parts) to other tiles than a
+ * device-output call does, so results can differ from a device-output call
+ * in the last bits of the FP32 sums of those tiles; both are within the
+ * split-precision bounds.  Returns SCFF_ERR_INVALID_ARG for n_bands outside
+ * 0..8.
  */
 scff_status scff_set_download_bands(scff_ctx *ctx, int n_bands);
 

@@ -1,14 +1,14 @@
 """Overlapped download of host outputs on the tensor-core path
 (scff_set_download_bands).
 
-A host-output call runs the output tiles as launches over bands of output
-columns and copies each finished band while the next one computes.  Checks:
-the host result matches a device-output call of the same job (always one
-launch) within the split-precision bound (each band has its own tail split,
-so split tiles sum their parts in another grouping), one band reproduces the
-device result bitwise, the banded result matches the oracle on sampled
-points, and every band layout (mirrored pairs of column runs, contiguous runs,
-a ragged last tile, f2 omitted) lands every column.
+A host-output call runs the output tiles band by band (bands of output
+columns) in one launch that reports its progress, and copies each finished
+band while later bands compute.  Checks: the host result matches a
+device-output call of the same job within the split-precision bound (the band
+order hands the tail split to other tiles), one band reproduces the device
+result bitwise, the banded result matches the oracle on sampled points, and
+every band layout (mirrored pairs of column runs, contiguous runs, a ragged
+last tile, f2 omitted) lands every column.
 """
 import numpy as np
 import pytest
