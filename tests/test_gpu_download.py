@@ -115,3 +115,15 @@ def test_invalid_band_count(ctx):
         with pytest.raises(scff.ScffError) as e:
             ctx.set_download_bands(n)
         assert e.value.code == 1
+
+
+def test_bands_with_autotune_and_screening(ctx):
+    # the autotuner's choice and the screened pair set both feed the banded path
+    job = grid_job(4111, 6, 64, 32, 64)
+    ctx.set_download_bands(3)
+    ctx.set_autotune(True)
+    ctx.set_screening(1e-9)
+    fh, f2h, fd, f2d = both(ctx, job)
+    assert rel_err(fh, fd) < TOL
+    idx = W.subset_indices(job.nq, 400, 4112)
+    assert rel_err(fh[:, idx], oracle.grid_form_factor(job, idx)) < TOL
