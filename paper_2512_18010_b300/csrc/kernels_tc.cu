@@ -1143,8 +1143,12 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
     if (e != cudaSuccess) return e;
     const int n_items = (int)items.size();
     if (n_items != n_items_all) return cudaErrorInvalidValue;
-    if (G > 1)  // no launch of this context is running: the slots are free
+    if (G > 1) {
+        // the previous banded launch (if any) has ended, even if its call
+        // returned early, before its slots are reused
+        if ((e = cudaEventSynchronize(a.ev_done)) != cudaSuccess) return e;
         for (int i = 0; i < grid * tc::GEN_WARPS; ++i) a.progress_host[i] = 0;
+    }
     if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
     e = tc_launch_persistent(a.kind, d_job, d_items, n_items, a.drain_every, a.err, grid, launches, st,
                              G > 1 ? a.progress_dev : nullptr);
