@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-alu-peaks", action="store_true", help="skip the FP32/FP64 FMA-chain peak measurement")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--only-fft", action="store_true",
                     help="run only the FFT-method measurement and print it (for profiling)")
@@ -299,15 +300,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(job, n_points: int, seed: int = 99):
+CPU_SEED = 99
+# parity bars of the error metric (per state: max |f - f_oracle| / max |f_oracle| over the points)
+TOLERANCE = {"fp64": 1e-10, "fp32": 1e-6, "bf16x3": 1e-5, "tf32x3": 1e-5, "bf16x2": 5e-5}
+
+
+def cpu_baseline(job, n_points: int, f_gpu=None, precision=None, seed: int = CPU_SEED):
+    """Times the FP64 oracle on a seeded sample of the job's grid.  With f_gpu (the GPU result at the
+    same sample, [S, n] complex) also returns the parity of that result against the oracle and the
+    cancellation factor kappa = max sum|terms| / max |f| (oracle, first 256 sample points)."""
     import oracle
     idx = W.subset_indices(job.nq, n_points, seed)
     t0 = time.perf_counter()
-    oracle.grid_form_factor(job, idx)
+    ref = oracle.grid_form_factor(job, idx)
     dt = time.perf_counter() - t0
-    return {"value": len(idx) * job.n_states / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{len(idx)} seeded q points of the same job, all {job.n_states} states, "
-                      f"FP64 C oracle with OpenMP ({dt:.1f} s)"}
+    cpu = {"value": len(idx) * job.n_states / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{len(idx)} seeded q points of the same job, all {job.n_states} states, "
+                     f"FP64 C oracle with OpenMP ({dt:.1f} s)"}
+    parity = None
+    if f_gpu is not None:
+        den = np.max(np.abs(ref), axis=1)
+        err = np.max(np.max(np.abs(f_gpu - ref), axis=1) / den)
+        nk = min(256, len(idx))
+        _, term = oracle.grid_form_factor(job, idx[:nk], terms=True)
+        kappa = np.max(np.max(term, axis=1) / np.max(np.abs(ref[:, :nk]), axis=1))
+        parity = {"max_rel_err_vs_oracle": float(err), "tolerance": TOLERANCE.get(precision),
+                  "pass": bool(err < TOLERANCE.get(precision, np.inf)), "points": int(len(idx)),
+                  "states": int(job.n_states), "kappa": float(kappa), "kappa_points": int(nk),
+                  "what": "the last timed step's f at seeded grid points against the FP64 oracle"}
+    return cpu, parity
 
 
 def run_reference(args):
@@ -540,6 +561,12 @@ def main():
     launches = ctx.kernel_launches() - l0
     clocks = sampler.stop()
     ctx.sync(stream)
+    # the timed result at the oracle's sample points (compared in the CPU-baseline leg)
+    f_chk = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sel = torch.from_numpy(W.subset_indices(nq, args.cpu_sample, CPU_SEED)).to(dev)
+        fc = f.index_select(1, sel).double().cpu().numpy()
+        f_chk = fc[..., 0] + 1j * fc[..., 1]
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
     units = S * nq
     ms, value = aggregate(float(np.mean(step_ms)), units, dist, dev)
@@ -564,6 +591,14 @@ def main():
         fp64 = {"value": units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms, "steps": args.fp64_steps,
                 "speedup_of_value": value / (units / (fms / 1e3))}
         del f64
+
+    # measured FMA-chain peaks (FP32, FP64) of this GPU, beside the derived ALU peaks
+    alu = None
+    if not args.no_alu_peaks:
+        p32, _ = ctx.alu_peak(False, 65536)
+        p64, _ = ctx.alu_peak(True, 4096)
+        alu = {"fp32_tflops": p32, "fp64_tflops": p64,
+               "how": "dependent FMA chains, 8 per thread, 64 warps per SM, best of 3 launches after a warm-up"}
 
     # roofline of the dominant kernel (the q-evaluation)
     n_pair, K, Kvw = pair_stats(job.mol)
@@ -601,6 +636,10 @@ def main():
                 "frac": achieved / peak, "traffic": None, "work": f"{direct_flops} algorithmic flop per (q*state)",
                 "peak_source": "FP64 nominal 1.25 TFLOP/s" if fp64_path else
                 "FP32: 148 SM x 128 lanes x 2 flop x 2032 MHz"}
+        if alu:
+            m = alu["fp64_tflops" if fp64_path else "fp32_tflops"]
+            roof["measured_fma_peak"] = m
+            roof["frac_of_measured_fma"] = achieved / m
 
     # the same job with every grid point evaluated (Hermitian half off)
     no_symmetry = None
@@ -687,9 +726,9 @@ def main():
     if batch_jobs:
         batch = batch_run(scff, ctx, batch_jobs, prec if prec != scff.FP64 else scff.BF16X3)
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(job, args.cpu_sample)
+        cpu, parity = cpu_baseline(job, args.cpu_sample, f_chk, args.precision)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -703,7 +742,7 @@ def main():
                            "l2": "flushed between timed steps (256 MB write)",
                            "hermitian_half": bool(half),
                            "parallelism": f"dp{world} (one job per rank)"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "no_symmetry": no_symmetry, "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "alu_peaks": alu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "no_symmetry": no_symmetry, "gpu_launches": int(launches),
                 "fp64_gpu_path": fp64, "screened": screened, "serving": serving, "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)

@@ -415,6 +415,16 @@ scff_status scff_set_download_bands(scff_ctx *ctx, int n_bands);
 scff_status scff_wait_selftest(scff_ctx *ctx, int64_t tries);
 
 /*
+ * ALU peak microbenchmark (measurement utility; no counterpart in the paper):
+ * dependent fused multiply-add chains (8 per thread, 64 resident warps per SM)
+ * on the context's device, FP64 when fp64 != 0 else FP32, `iters` rounds per
+ * chain (1..2^24).  One warm-up launch, then the best of three timed launches:
+ * *tflops = 2 x FMAs / time, *ms = that launch's time.  Synchronous; the
+ * rooflines of the direct (CUDA-core) kernels are quoted against it.
+ */
+scff_status scff_alu_peak(scff_ctx *ctx, int fp64, int iters, double *tflops, double *ms);
+
+/*
  * Error-bounded pair screening (the exact-tolerance form of the paper's
  * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
  * first scff_form_factor call for a (transitions, grid extent) bounds every

@@ -47,6 +47,10 @@ def _load():
             ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
             ctypes.c_int, P, ctypes.c_int64, P, ctypes.c_double, P, ctypes.c_int]
         lib.scff_oracle_form_factor.restype = ctypes.c_int
+        lib.scff_oracle_form_factor_terms.argtypes = [
+            ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+            ctypes.c_int, P, ctypes.c_int64, P, ctypes.c_double, P, P, ctypes.c_int]
+        lib.scff_oracle_form_factor_terms.restype = ctypes.c_int
         lib.scff_oracle_functions.argtypes = [
             ctypes.c_int, ctypes.c_int, P, P, P, P, P, ctypes.c_int, P, P, P, P, P]
         lib.scff_oracle_functions.restype = ctypes.c_int
@@ -79,8 +83,14 @@ def _flags(mol, renorm: bool) -> int:
 
 
 def form_factor(mol, T: np.ndarray, q: np.ndarray, scale: float = 1.0,
-                renorm: bool = True, threads: int = 0) -> np.ndarray:
-    """f[s, iq] (complex128) for explicit q vectors q[n, 3]."""
+                renorm: bool = True, threads: int = 0, terms: bool = False):
+    """f[s, iq] (complex128) for explicit q vectors q[n, 3].
+
+    With terms=True also returns term[s, iq] = |scale| sum_{mu,nu} |T^s_{mu nu}
+    integral_{mu nu}(q)|, the sum of the magnitudes of the terms whose sum is
+    f (so term >= |f|); max term / max |f| measures how far cancellation
+    amplifies the rounding of the terms.
+    """
     lib = _load()
     xyz = _c(mol.xyz, np.float64)
     sa, sl, sn = _c(mol.shell_atom, np.int32), _c(mol.shell_l, np.int32), _c(mol.shell_nprim, np.int32)
@@ -91,12 +101,20 @@ def form_factor(mol, T: np.ndarray, q: np.ndarray, scale: float = 1.0,
     q = _c(q, np.float64).reshape(-1, 3)
     S = T.shape[0]
     out = np.zeros((S, q.shape[0], 2), dtype=np.float64)
-    rc = lib.scff_oracle_form_factor(mol.n_atoms, _ptr(xyz), mol.n_shells, _ptr(sa), _ptr(sl),
-                                     _ptr(sn), _ptr(ex), _ptr(co), _flags(mol, renorm), S, _ptr(T),
-                                     q.shape[0], _ptr(q), float(scale), _ptr(out), int(threads))
+    if terms:
+        term = np.zeros((S, q.shape[0]), dtype=np.float64)
+        rc = lib.scff_oracle_form_factor_terms(mol.n_atoms, _ptr(xyz), mol.n_shells, _ptr(sa), _ptr(sl),
+                                               _ptr(sn), _ptr(ex), _ptr(co), _flags(mol, renorm), S, _ptr(T),
+                                               q.shape[0], _ptr(q), float(scale), _ptr(out), _ptr(term),
+                                               int(threads))
+    else:
+        rc = lib.scff_oracle_form_factor(mol.n_atoms, _ptr(xyz), mol.n_shells, _ptr(sa), _ptr(sl),
+                                         _ptr(sn), _ptr(ex), _ptr(co), _flags(mol, renorm), S, _ptr(T),
+                                         q.shape[0], _ptr(q), float(scale), _ptr(out), int(threads))
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
-    return out[..., 0] + 1j * out[..., 1]
+    f = out[..., 0] + 1j * out[..., 1]
+    return (f, term) if terms else f
 
 
 def density(mol, T: np.ndarray, r: np.ndarray, scale: float = 1.0, renorm: bool = True,
@@ -151,9 +169,9 @@ def prim_norm(alpha: float, a: int, b: int, c: int) -> float:
 
 
 def grid_form_factor(job, flat_idx: Optional[np.ndarray] = None, scale: float = 1.0,
-                     threads: int = 0) -> np.ndarray:
+                     threads: int = 0, terms: bool = False):
     """Oracle on a product grid job, on all points or on the given flat indices."""
     if flat_idx is None:
         flat_idx = np.arange(job.nq)
     q = job.q_points(flat_idx)
-    return form_factor(job.mol, job.T, q, scale=scale, threads=threads)
+    return form_factor(job.mol, job.T, q, scale=scale, threads=threads, terms=terms)

@@ -321,14 +321,17 @@ static double complex pair_integral(const ofn_t *m, const ofn_t *n, const double
 /*
  * f_out[s][iq][0..1] = Re, Im of f_s(q_iq).  T is [n_states][nbf][nbf]
  * row-major; q is [n_q][3]; flags = ORACLE_RENORM | ORACLE_PURE_D | ORACLE_PURE_F.
- * Returns 0 or a negative error code.
+ * With term_out non-NULL, term_out[s][iq] = |scale| sum_{mu,nu} |T^s_{mu nu}
+ * integral_{mu nu}(q)|, the sum of the magnitudes of the function-pair terms
+ * whose sum is f_s(q) (the scale against which the rounding of the terms
+ * acts).  Returns 0 or a negative error code.
  */
-int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
+static int form_factor_impl(int n_atoms, const double *xyz, int n_shells,
                             const int32_t *shell_atom, const int32_t *shell_l,
                             const int32_t *shell_nprim, const double *exps,
                             const double *coefs, int flags, int n_states,
                             const double *T, int64_t n_q, const double *q,
-                            double scale, double *f_out, int n_threads) {
+                            double scale, double *f_out, double *term_out, int n_threads) {
     if (n_atoms <= 0 || n_shells <= 0 || n_states <= 0 || n_q < 0 || !xyz || !T || !f_out)
         return ORACLE_EINVAL;
     ofn_t *fns = NULL;
@@ -345,7 +348,7 @@ int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
     int fail = 0;
 #pragma omp parallel
     {
-        long double *acc = (long double *)malloc(sizeof(long double) * 2 * (size_t)n_states);
+        long double *acc = (long double *)malloc(sizeof(long double) * 3 * (size_t)n_states);
         if (!acc) {
 #pragma omp atomic write
             fail = 1;
@@ -353,7 +356,7 @@ int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
 #pragma omp for schedule(dynamic, 1)
         for (int64_t iq = 0; iq < n_q; ++iq) {
             if (!acc) continue;
-            for (int s = 0; s < 2 * n_states; ++s) acc[s] = 0.0L;
+            for (int s = 0; s < 3 * n_states; ++s) acc[s] = 0.0L;
             const double *qv = q + 3 * iq;
             for (int mu = 0; mu < nbf; ++mu) {
                 const double *A = xyz + 3 * fns[mu].atom;
@@ -361,22 +364,47 @@ int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
                     const double *B = xyz + 3 * fns[nu].atom;
                     const double complex v = pair_integral(&fns[mu], &fns[nu], A, B, qv);
                     const double vr = creal(v), vi = cimag(v);
+                    const double va = term_out ? cabs(v) : 0.0;
                     for (int s = 0; s < n_states; ++s) {
                         const long double t = T[(size_t)s * nn + (size_t)mu * nbf + nu];
                         acc[2 * s] += t * vr;
                         acc[2 * s + 1] += t * vi;
+                        if (term_out) acc[2 * n_states + s] += fabsl(t) * va;
                     }
                 }
             }
             for (int s = 0; s < n_states; ++s) {
                 f_out[((size_t)s * n_q + iq) * 2] = (double)(scale * acc[2 * s]);
                 f_out[((size_t)s * n_q + iq) * 2 + 1] = (double)(scale * acc[2 * s + 1]);
+                if (term_out) term_out[(size_t)s * n_q + iq] = (double)(fabs(scale) * acc[2 * n_states + s]);
             }
         }
         free(acc);
     }
     free_functions(fns, nbf);
     return fail ? ORACLE_ENOMEM : ORACLE_OK;
+}
+
+int scff_oracle_form_factor(int n_atoms, const double *xyz, int n_shells,
+                            const int32_t *shell_atom, const int32_t *shell_l,
+                            const int32_t *shell_nprim, const double *exps,
+                            const double *coefs, int flags, int n_states,
+                            const double *T, int64_t n_q, const double *q,
+                            double scale, double *f_out, int n_threads) {
+    return form_factor_impl(n_atoms, xyz, n_shells, shell_atom, shell_l, shell_nprim, exps, coefs,
+                            flags, n_states, T, n_q, q, scale, f_out, NULL, n_threads);
+}
+
+/* f_out as scff_oracle_form_factor, plus term_out[s][iq] (see form_factor_impl). */
+int scff_oracle_form_factor_terms(int n_atoms, const double *xyz, int n_shells,
+                                  const int32_t *shell_atom, const int32_t *shell_l,
+                                  const int32_t *shell_nprim, const double *exps,
+                                  const double *coefs, int flags, int n_states,
+                                  const double *T, int64_t n_q, const double *q,
+                                  double scale, double *f_out, double *term_out, int n_threads) {
+    if (!term_out) return ORACLE_EINVAL;
+    return form_factor_impl(n_atoms, xyz, n_shells, shell_atom, shell_l, shell_nprim, exps, coefs,
+                            flags, n_states, T, n_q, q, scale, f_out, term_out, n_threads);
 }
 
 /*

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libscff.so")
-SOURCES = ["scff_host.cpp", "kernels_direct.cu", "kernels_tc.cu", "kernels_separable.cu", "static_entry.cu",
+SOURCES = ["scff_host.cpp", "kernels_direct.cu", "kernels_tc.cu", "kernels_separable.cu", "kernels_peaks.cu", "static_entry.cu",
            "server.cpp", "kernels_sph.cu", "spherical.cpp", "kernels_fft.cu", "fft_method.cpp"]
 HEADERS = ["scff_internal.h", "tc_internal.h", "device_common.cuh", "scff_objects.h", "sph_common.h",
            "sph_internal.h", "fft_internal.h"]

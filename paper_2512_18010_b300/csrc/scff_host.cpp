@@ -1194,6 +1194,15 @@ extern "C" scff_status scff_separable_integral(scff_ctx *c, scff_basis_h b, scff
 }
 
 // Reads the device status word after all work on `stream` has finished.
+extern "C" scff_status scff_alu_peak(scff_ctx *c, int fp64, int iters, double *tflops, double *ms) {
+    if (!c || !tflops || !ms) return fail(SCFF_ERR_INVALID_ARG, "scff_alu_peak: NULL argument");
+    if (iters < 1 || iters > (1 << 24)) return fail(SCFF_ERR_INVALID_ARG, "scff_alu_peak: iters must be 1..2^24");
+    cudaSetDevice(c->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(measure_alu_peak(fp64 ? 1 : 0, iters, tflops, ms));
+    return SCFF_OK;
+}
+
 extern "C" scff_status scff_wait_selftest(scff_ctx *c, int64_t tries) {
     if (!c || tries < 1 || tries > (int64_t)1 << 24)
         return fail(SCFF_ERR_INVALID_ARG, "scff_wait_selftest: tries must be 1..2^24");

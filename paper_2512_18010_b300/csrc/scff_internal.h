@@ -150,6 +150,9 @@ cudaError_t launch_pure_to_cart(int S, int ncart, int nuser, const int32_t *idx,
 // One-thread kernel whose mbarrier wait runs out after `tries` attempts and
 // sets the error word (the bounded-wait error path, for tests).
 cudaError_t launch_wait_selftest(long long tries, int *err, cudaStream_t st);
+// FMA-chain rate of the current device (FP32 or FP64), best of three timed
+// launches after a warm-up launch; synchronous on the legacy stream.
+cudaError_t measure_alu_peak(int fp64, int iters, double *tflops, double *ms);
 
 struct DirectArgs {
     const PairSetDev *ps;

@@ -38,7 +38,7 @@ _SYMBOLS = [
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
     "scff_screening_info", "scff_separable_integral", "scff_spherical", "scff_fft_form_factor", "scff_wait_selftest", "scff_set_hermitian",
-    "scff_set_download_bands",
+    "scff_set_download_bands", "scff_alu_peak",
 ]
 
 
@@ -149,6 +149,8 @@ def load(build_if_missing: bool = True):
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_set_download_bands.argtypes = [P, ctypes.c_int]
+    lib.scff_alu_peak.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.scff_alu_peak.restype = I32
     lib.scff_set_download_bands.restype = I32
     lib.scff_last_timing.argtypes = [P, P]
     lib.scff_kernel_launches.argtypes = [P]
@@ -553,6 +555,13 @@ class Context:
         """Host-output calls on the tensor cores: launches over column bands whose
         downloads overlap the next band's compute (0 = automatic, 1 = off, 2..8)."""
         _check(self.lib.scff_set_download_bands(self.h, int(n_bands)))
+
+    def alu_peak(self, fp64: bool = False, iters: int = 65536):
+        """Measured FMA-chain rate of this device: (TFLOP/s, ms of the timed launch)."""
+        t = np.zeros(1, dtype=np.float64)
+        m = np.zeros(1, dtype=np.float64)
+        _check(self.lib.scff_alu_peak(self.h, 1 if fp64 else 0, int(iters), _p(t), _p(m)))
+        return float(t[0]), float(m[0])
 
     def wait_selftest(self, tries: int = 4096):
         """Runs the bounded-wait failure path once; raises ScffError(TIMEOUT) as intended."""

@@ -106,6 +106,27 @@ def test_s_s_two_centre_closed_form():
     assert rel_err(f, exp) < 1e-13
 
 
+def test_term_magnitudes_two_s_closed_form():
+    # Sum of |T_mn integral_mn(q)| over the four function pairs of two s functions,
+    # each integral from the Gaussian-product closed form; the sum bounds |f|.
+    A, B = np.array([0.1, -0.3, 0.2]), np.array([-0.8, 0.6, 1.1])
+    a, b = 0.9, 2.3
+    mol = mol_of(np.vstack([A, B]), [(0, 0, [a], [1.0]), (1, 0, [b], [1.0])])
+    T = np.array([[[0.7, -1.3], [0.4, -0.25]]])
+    q = np.random.default_rng(5).uniform(-5, 5, size=(30, 3))
+    f, term = oracle.form_factor(mol, T, q, scale=-2.0, terms=True)
+    na, nb = prim_norm_textbook(a, 0, 0, 0), prim_norm_textbook(b, 0, 0, 0)
+    Iaa, _ = _gpt(a, A, a, A, q)
+    Iab, _ = _gpt(a, A, b, B, q)
+    Ibb, _ = _gpt(b, B, b, B, q)
+    exp = 2.0 * (abs(T[0, 0, 0]) * na * na * np.abs(Iaa) + (abs(T[0, 0, 1]) + abs(T[0, 1, 0])) * na * nb * np.abs(Iab)
+                 + abs(T[0, 1, 1]) * nb * nb * np.abs(Ibb))
+    assert np.max(np.abs(term[0] - exp) / exp) < 1e-13
+    assert np.all(term[0] >= np.abs(f[0]) * (1 - 1e-14))
+    f_plain = oracle.form_factor(mol, T, q, scale=-2.0)
+    assert np.array_equal(f, f_plain)
+
+
 def test_p_and_d_from_centre_derivatives():
     # d/dA_x exp(-a|r-A|^2) = 2a (x-A_x) exp(...): the p_x-s integral is the
     # A_x-derivative of the s-s closed form over 2a; d shells take two derivatives.
