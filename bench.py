@@ -300,6 +300,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 CPU_SEED = 99
 # parity bars of the error metric (per state: max |f - f_oracle| / max |f_oracle| over the points)
 TOLERANCE = {"fp64": 1e-10, "fp32": 1e-6, "bf16x3": 1e-5, "tf32x3": 1e-5, "bf16x2": 5e-5}
@@ -315,6 +326,7 @@ def cpu_baseline(job, n_points: int, f_gpu=None, precision=None, seed: int = CPU
     ref = oracle.grid_form_factor(job, idx)
     dt = time.perf_counter() - t0
     cpu = {"value": len(idx) * job.n_states / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_model": cpu_model(),
            "sample": f"{len(idx)} seeded q points of the same job, all {job.n_states} states, "
                      f"FP64 C oracle with OpenMP ({dt:.1f} s)"}
     parity = None
@@ -353,7 +365,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "sample_per_step": f"{n_pts} seeded q points x {job.n_states} states"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{n_pts} q points per step"},
+                             "cpu_model": cpu_model(), "sample": f"{n_pts} q points per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
