@@ -1167,6 +1167,12 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
         return true;
     };
     const size_t rows = (size_t)a.S * a.nx;  // output rows (s, ix) of N columns
+    // on an error after some copies were queued, wait for them before returning:
+    // they write into the caller's buffers
+    auto fail_after_copies = [&](cudaError_t err) {
+        cudaStreamSynchronize(a.copy_st);
+        return err;
+    };
     bool launch_over = false;
     for (int g = 0; g < G; ++g) {
         // the launch ends in any case (every device wait is bounded), and
@@ -1174,7 +1180,7 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
         while (!launch_over && !written(band_end[g])) {
             const cudaError_t q = cudaEventQuery(a.ev_done);
             if (q == cudaSuccess) launch_over = true;
-            else if (q != cudaErrorNotReady) return q;
+            else if (q != cudaErrorNotReady) return fail_after_copies(q);
             else std::this_thread::yield();
         }
         for (int r = 0; r < nruns[g]; ++r) {
@@ -1185,11 +1191,12 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
             if (e == cudaSuccess && a.f2_host && a.f2)
                 e = cudaMemcpy2DAsync(a.f2_host + c0, 4 * jd.N, a.f2 + c0, 4 * jd.N, 4 * (c1 - c0), rows,
                                       cudaMemcpyDeviceToHost, a.copy_st);
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) return fail_after_copies(e);
         }
     }
-    if ((e = cudaEventRecord(a.ev_copied, a.copy_st)) != cudaSuccess) return e;
-    return cudaStreamWaitEvent(st, a.ev_copied, 0);
+    if ((e = cudaEventRecord(a.ev_copied, a.copy_st)) != cudaSuccess) return fail_after_copies(e);
+    e = cudaStreamWaitEvent(st, a.ev_copied, 0);
+    return e == cudaSuccess ? e : fail_after_copies(e);
 }
 
 // ------------------------------------------------------------------ generic two-table contraction

@@ -267,3 +267,17 @@ def test_hermitian_half_is_exact_mirror(prec):
         assert rel_err(f_s, oracle.grid_form_factor(shifted)) < TOL[prec]
     finally:
         c.close()
+
+
+def test_alu_peak_microbenchmark(ctx):
+    # FMA-chain rates of this GPU: positive, FP32 well above FP64, and not above
+    # the lanes x 2 flop x clock ceiling (148 SMs x 128 lanes x 2 x 2.1 GHz).
+    p32, ms32 = ctx.alu_peak(False, 16384)
+    p64, ms64 = ctx.alu_peak(True, 1024)
+    assert 5.0 < p32 < 148 * 128 * 2 * 2.1e9 / 1e12
+    assert 0.05 < p64 < p32
+    assert ms32 > 0 and ms64 > 0
+    for bad in (0, -5, 1 << 25):
+        with pytest.raises(scff.ScffError) as e:
+            ctx.alu_peak(False, bad)
+        assert e.value.code == 1
