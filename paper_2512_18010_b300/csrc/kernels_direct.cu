@@ -278,6 +278,7 @@ template <> struct Cplx<float> { using T = float2; };
 
 constexpr int kDirectThreads = 128;
 constexpr int kChunkBytes = 8192;
+constexpr int kMaxChunkPairs = kChunkBytes / 32;  // most pairs of a staged chunk (FP64, SB = 4, L = 0)
 
 struct DirectParams {
     PairSetDev ps;
@@ -294,6 +295,10 @@ struct DirectParams {
     void *f, *f2;
     int *err;
     int part;  // kPartContinue: start from the raw sums in f; kPartFinal: write scaled f and |f|^2
+    // product grid with nz a multiple of the block size: every block's points
+    // share (ix, iy), so the x and y table factors of a pair are the same for
+    // the whole block and are formed once per block into shared memory
+    int xy_uniform;
 };
 
 // Pair classes of degree >= kHighClass (pairs with an f shell) run in a second
@@ -377,13 +382,23 @@ template <typename R, int SB> struct Acc {
 };
 
 template <typename R, int SB, int L, bool LIST>
-__device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf, int pr0,
+__device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf,
+                                              const typename Cplx<R>::T *__restrict__ gxy, int pr0,
                                               int np, const R (&px)[kMaxPairL + 1], const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1],
                                               int ix, int iy, int iz, double qx, double qy, double qz,
                                               double q2, Acc<R, SB> &acc) {
     constexpr int mL = mono_count(L);
+    using V = typename Cplx<R>::T;
     for (int i = 0; i < np; ++i) {
-        const auto g = pair_factor<R, LIST>(p, pr0 + i, ix, iy, iz, qx, qy, qz, q2);
+        V g;
+        if (!LIST && p.xy_uniform) {
+            const V a = gxy[i];
+            const V c = static_cast<const V *>(p.gz)[(int64_t)(pr0 + i) * p.nz + iz];
+            g.x = a.x * c.x - a.y * c.y;
+            g.y = a.x * c.y + a.y * c.x;
+        } else {
+            g = pair_factor<R, LIST>(p, pr0 + i, ix, iy, iz, qx, qy, qz, q2);
+        }
         R E[SB], O[SB];
 #pragma unroll
         for (int j = 0; j < SB; ++j) E[j] = O[j] = R(0);
@@ -415,7 +430,8 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
 // Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
 // false (uniformly across the block) when a wait timed out.
 template <typename R, int SB, int L, bool LIST>
-__device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, uint64_t *bars,
+__device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, typename Cplx<R>::T *gxy,
+                                          int bx, int by, uint64_t *bars,
                                           uint32_t &phase, int sblk, const R (&px)[kMaxPairL + 1],
                                           const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1], int ix, int iy, int iz, double qx, double qy,
                                           double qz, double q2, Acc<R, SB> &acc) {
@@ -424,6 +440,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
     static_assert(pair_bytes <= kChunkBytes, "one pair's coefficients must fit a staging buffer");
     static_assert(pair_bytes % 16 == 0, "bulk copies move multiples of 16 bytes");
     constexpr int npc = kChunkBytes / pair_bytes;
+    static_assert(npc <= kMaxChunkPairs, "pair factors of a chunk must fit their shared array");
     const int pbeg = p.ps.pair_off[L], pend = p.ps.pair_off[L + 1];
     const int npairs = pend - pbeg;
     if (npairs <= 0) return true;
@@ -451,8 +468,22 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
             break;
         }
         const int n = min(npc, npairs - c * npc);
-        consume_chunk<R, SB, L, LIST>(p, bufs[b], pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz, q2,
-                                      acc);
+        if (!LIST && p.xy_uniform) {
+            // the block's x and y factors of this chunk's pairs, once per block
+            using V = typename Cplx<R>::T;
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                const int pr = pbeg + c * npc + t;
+                const V a = static_cast<const V *>(p.gx)[(int64_t)pr * p.nx + bx];
+                const V bb = static_cast<const V *>(p.gy)[(int64_t)pr * p.ny + by];
+                V v;
+                v.x = a.x * bb.x - a.y * bb.y;
+                v.y = a.x * bb.y + a.y * bb.x;
+                gxy[t] = v;
+            }
+            __syncthreads();
+        }
+        consume_chunk<R, SB, L, LIST>(p, bufs[b], gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz,
+                                      q2, acc);
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
     }
@@ -462,6 +493,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
 template <typename R, int SB, bool LIST, bool HIGH>
 __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) {
     __shared__ __align__(128) unsigned char smem[2 * kChunkBytes];
+    __shared__ __align__(16) typename Cplx<R>::T gxy[kMaxChunkPairs];
     __shared__ __align__(8) uint64_t bars[2];
     R *buf0 = reinterpret_cast<R *>(smem);
     R *buf1 = reinterpret_cast<R *>(smem + kChunkBytes);
@@ -492,6 +524,13 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
         qz = p.qaz[iz];
     }
     const double q2 = qx * qx + qy * qy + qz * qz;
+    // (ix, iy) of the block's first point: the block's own when xy_uniform
+    int bx = 0, by = 0;
+    if constexpr (!LIST) {
+        const int64_t q0 = (int64_t)blockIdx.x * kDirectThreads;
+        bx = (int)(q0 / ((int64_t)p.ny * p.nz));
+        by = (int)((q0 / p.nz) % p.ny);
+    }
     R px[kMaxPairL + 1], py[kMaxPairL + 1], pz[kMaxPairL + 1];
     px[0] = py[0] = pz[0] = R(1);
 #pragma unroll
@@ -526,8 +565,8 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
     auto run = [&](auto LC) {
         constexpr int L = decltype(LC)::value;
         if (ok)
-            ok = run_class<R, SB, L, LIST>(p, buf0, buf1, bars, phase, sblk, px, py, pz, ix, iy, iz, qx, qy,
-                                           qz, q2, acc);
+            ok = run_class<R, SB, L, LIST>(p, buf0, buf1, gxy, bx, by, bars, phase, sblk, px, py, pz, ix, iy, iz,
+                                           qx, qy, qz, q2, acc);
     };
     if constexpr (HIGH) {
         static_for<kMaxPairL + 1 - kHighClass>([&](auto I) {
@@ -589,6 +628,7 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *laun
     p.f = a.f;
     p.f2 = a.f2;
     p.err = a.err_flag;
+    p.xy_uniform = (!list && a.nz > 0 && a.nz % kDirectThreads == 0) ? 1 : 0;
     const int nsb = (a.S + SB - 1) / SB;
     dim3 grid((unsigned)((a.nq + kDirectThreads - 1) / kDirectThreads), (unsigned)nsb);
     const bool has_low = a.ps->pair_off[kHighClass] > 0;
