@@ -86,7 +86,14 @@ template <int KIND> struct Kind {
     static constexpr int W_STAGE = 2 * NP * W_ARR;
     static constexpr int STAGE = A_STAGE + W_STAGE;
     static constexpr int STAGES = NP == 3 ? 2 : 3;
-    static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256;
+    // stages, then the barriers (256 B), then each generator warp's two
+    // k-offset buffers (KO_BYTES).  Staging the k-offsets through shared
+    // memory pays where the generators set the pace (BF16 hi/lo: -8%); where
+    // the tensor pipe does (hi/mid/lo, TF32) it costs about 1%, so those read
+    // them straight from global memory.
+    static constexpr bool STAGE_KO = KIND == KIND_BF16X2;
+    static constexpr int KO_BYTES = STAGE_KO ? GEN_WARPS * 2 * (BK / 2) * 8 : 0;
+    static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256 + KO_BYTES;
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
 
@@ -104,6 +111,15 @@ __host__ __device__ __forceinline__ uint32_t sw64_offset(int row, int c) {
 }
 
 // ------------------------------------------------------------------ PTX wrappers
+
+// 8-byte asynchronous global -> shared copy (LDGSTS) and its group bookkeeping.
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
     // start address >> 4, LBO unused (0), SBO = 512 B (8 rows x 64 B),
@@ -635,6 +651,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         // warps of a lane group take column halves.
         const int lg = warp & 3;
         const int colh = ((warp - 4) >> 2) * CQ;
+        // (STAGE_KO) this warp's two k-offset buffers (KH records each): the next
+        // chunk's records are copied asynchronously while this chunk is generated
+        int2 *kobuf = reinterpret_cast<int2 *>(smem + STAGES * STAGE + 256) + (warp - 4) * 2 * KH;
         int gc = 0, gbase = 0, done_items = 0;
         bool ok = true;
         for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
@@ -667,13 +686,28 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int gc0 = gc;
             int drained = 0;
             const int2 *kofs = J.kofs + (size_t)k0 * BK + khalf * KH;
+            // Row offsets of this warp's k (independent of the A copy, so the
+            // gathers below overlap with the TMA instead of following it),
+            // staged one chunk ahead by asynchronous copies into shared memory.
+            if constexpr (KD::STAGE_KO) {
+                if (lane < KH) cp_async8(kobuf + lane, kofs + lane);
+                cp_async_commit();
+            }
             for (int it = 0; it < nkc && ok; ++it, ++gc) {
                 const int s = gc % STAGES;
-                // Row offsets of this thread's k: independent of the A copy, so the
-                // gathers below overlap with the TMA instead of following it.
                 int2 ko[KH];
+                if constexpr (KD::STAGE_KO) {
+                    if (it + 1 < nkc && lane < KH)
+                        cp_async8(kobuf + ((it + 1) & 1) * KH + lane, kofs + (size_t)(it + 1) * BK + lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();  // this chunk's records have landed
+                    __syncwarp();
 #pragma unroll
-                for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
+                    for (int e = 0; e < KH; ++e) ko[e] = kobuf[(it & 1) * KH + e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
+                }
                 const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
                 if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                     ok = false;
@@ -721,6 +755,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     ++drained;
                 }
+            }
+            if constexpr (KD::STAGE_KO) {
+                cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
+                __syncwarp();
             }
             while (ok && drained < ngroups) {
                 if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im))
