@@ -48,9 +48,9 @@ TF32_PER_BF16 = 0.5   # dense TF32 / dense BF16 tensor rate (nominal 1.1 vs 2.25
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one q-evaluation
 # launch, from one ncu capture of the default workload (see profiles/); valid
 # only while the kernel sources hash to the value recorded with it.
-TC_SOURCES = ["kernels_tc.cu", "tc_internal.h", "device_common.cuh", "scff_internal.h"]
+TC_SOURCES = ["kernels_tc.cu", "tc_internal.h", "tc_schedule.h", "device_common.cuh", "scff_internal.h"]
 MEASURED_TRAFFIC = {
-    ("cfg3", "bf16x3"): {"bytes": 874469632 + 377433600, "src": "f594415d4d63e9dc",
+    ("cfg3", "bf16x3"): {"bytes": 874469632 + 377433600, "src": "ead2a8a74474851c",
                          "profile": "profiles/tc_bf16x3_cfg3_launches.md"},
 }
 

@@ -21,7 +21,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libscff.so")
 SOURCES = ["scff_host.cpp", "kernels_direct.cu", "kernels_tc.cu", "kernels_separable.cu", "kernels_peaks.cu", "static_entry.cu",
            "server.cpp", "kernels_sph.cu", "spherical.cpp", "kernels_fft.cu", "fft_method.cpp"]
-HEADERS = ["scff_internal.h", "tc_internal.h", "device_common.cuh", "scff_objects.h", "sph_common.h",
+HEADERS = ["scff_internal.h", "tc_internal.h", "tc_schedule.h", "device_common.cuh", "scff_objects.h", "sph_common.h",
            "sph_internal.h", "fft_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -39,6 +39,7 @@
 #include "device_common.cuh"
 #include "scff_internal.h"
 #include "tc_internal.h"
+#include "tc_schedule.h"
 
 #include <algorithm>
 #include <string.h>
@@ -239,26 +240,7 @@ struct Layout {
     size_t off_X, off_Y, off_Z, off_k, off_ko, off_A, off_part, off_cnt, total;
 };
 
-// Tail split of a job with `items` equal tiles of nkc chunks on P SMs: the
-// last R = items mod P tiles run as s parts (k split evenly), so that the
-// final wave keeps the SMs busy.  s = 0: no split.
-// s (2..16, parts of at least 8 chunks, at most 2P parts in all) minimises
-// the tail's length ceil(R s / P) / s in tile times; no s below 1 tile time
-// leaves the tail unsplit.
-static void tail_split(int items, int nkc, int P, int *R, int *s) {
-    *R = items % P;
-    *s = 0;
-    if (*R == 0 || nkc >= 32768) return;
-    double best = 1.0;
-    for (int c = 2; c <= 16 && c <= nkc / 8 && (int64_t)*R * c <= 2 * (int64_t)P; ++c) {
-        const double t = (double)((*R * c + P - 1) / P) / c;
-        if (t < best - 1e-9) {
-            best = t;
-            *s = c;
-        }
-    }
-    if (!*s) *R = 0;
-}
+using sched::tail_split;
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -1005,77 +987,13 @@ void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) 
     std::stable_sort(items.begin(), items.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
 }
 
-// Runs of n-tiles [runs[i][0], runs[i][1]) of the band [d0, d1).  With the
-// mirror, tile nt and its mirror n_nt-1-nt (which receives nt's mirrored
-// columns when N is a multiple of BN) belong to the same band: bands are
-// ranges of d = min(nt, n_nt-1-nt).  Without it d = nt.  Returns the number
-// of runs (0..2).
-static int band_runs(int n_nt, bool mirror, int d0, int d1, int runs[2][2]) {
-    if (!mirror) {
-        runs[0][0] = d0;
-        runs[0][1] = d1;
-        return d1 > d0 ? 1 : 0;
-    }
-    int n = 0;
-    if (d1 > d0) {
-        runs[n][0] = d0;
-        runs[n][1] = d1;
-        ++n;
-    }
-    const int lo = std::max(n_nt - d1, d1), hi = n_nt - d0;
-    if (hi > lo) {
-        runs[n][0] = lo;
-        runs[n][1] = hi;
-        ++n;
-    }
-    return n;
-}
+using sched::band_runs;
 
-// Output columns of the d values below e: 2e column tiles with the mirror
-// (one for the middle tile of an odd n_nt), else e.
-static int64_t band_cols(int n_nt, bool mirror, int e) { return mirror ? std::min(2 * (int64_t)e, (int64_t)n_nt) : e; }
-
-// Band boundaries 0 = b[0] < ... < b[G] = D in d units for the band-major
-// tile order of one launch on `grid` CTAs; returns G (1: no banding).  A
-// requested count gives equal bands.  Automatic (jobs of at least 1.25
-// waves): CTA c runs items c, c + grid, ..., so the items below k * grid are
-// all written when wave k ends; the bands end at the last d boundary below
-// each wave end (the last kMaxBands - 1 of them), so each band's copy starts
-// one wave after its first tiles and only the last wave's columns (less the
-// tail split's time) wait for the launch to end.  first_split, nsplit: the
-// tail split of the job's tile count (items of tile t >= first_split are its
-// nsplit parts).
+// Band boundaries of one job's overlapped download (sched::band_bounds).
 static int band_bounds(const TcJobDev &jd, int requested, int grid, int64_t first_split, int nsplit,
                        int b[kMaxBands + 1]) {
-    using namespace tc;
-    const int n_mt = jd.n_mt, n_nt = jd.n_nt;
-    const bool mirror = jd.mirror != 0;
-    if (requested == 1 || n_mt <= 0 || n_nt <= 0) return 1;
-    if (mirror && jd.N % BN) return 1;  // mirrored columns would straddle tiles
-    const int D = mirror ? (n_nt + 1) / 2 : n_nt;
-    int G = 0;
-    b[0] = 0;
-    if (requested > 0) {
-        G = std::min(std::min(requested, kMaxBands), D);
-        for (int g = 1; g <= G; ++g) b[g] = (int)((int64_t)g * D / G);
-        return G >= 2 ? G : 1;
-    }
-    const int64_t tiles = (int64_t)n_mt * n_nt;
-    if (tiles * 4 < 5 * (int64_t)grid) return 1;
-    auto item_end = [&](int e) {
-        const int64_t t = n_mt * band_cols(n_nt, mirror, e);
-        return t <= first_split ? t : first_split + (t - first_split) * nsplit;
-    };
-    std::vector<int> ends;  // d boundaries at wave ends, increasing
-    for (int64_t k = 1; item_end(D) > k * grid; ++k) {
-        int e = ends.empty() ? 0 : ends.back();
-        while (e < D && item_end(e + 1) <= k * grid) ++e;
-        if (e > (ends.empty() ? 0 : ends.back())) ends.push_back(e);
-    }
-    const int keep = std::min((int)ends.size(), kMaxBands - 1);
-    for (int i = (int)ends.size() - keep; i < (int)ends.size(); ++i) b[++G] = ends[i];
-    b[++G] = D;
-    return G >= 2 ? G : 1;
+    return sched::band_bounds(jd.n_mt, jd.n_nt, jd.mirror != 0, jd.N, tc::BN, requested, grid, first_split, nsplit,
+                              kMaxBands, b);
 }
 
 template <int KIND>
