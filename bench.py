@@ -714,7 +714,7 @@ def main():
         fview = hf.numpy()
         f2view = hf2.numpy()
         tlist = []
-        for k in range(max(2, args.steps) + 1):
+        for k in range(max(10, args.steps) + 1):
             t0 = time.perf_counter()
             bb = ctx.basis(job.mol)
             tt = ctx.transitions(bb, hT.numpy())
