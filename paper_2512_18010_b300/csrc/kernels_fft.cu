@@ -36,7 +36,8 @@ __device__ __forceinline__ void rec_powers(int type, int j, int pw[3]) {
         pw[ax] = type == REC_SP ? (j == 0 ? 0 : cart_pow(1, j - 1, ax)) : cart_pow(rec_lmax(type), j, ax);
 }
 
-constexpr int kFftThreads = 256;
+constexpr int kFftThreads = 512;
+constexpr int kFftWarps = kFftThreads / 32;
 constexpr int kPairChunk = 256;  // (mu <= nu) pairs per staged chunk
 
 // Tsym[sweep][k][q] for the pairs k = (mu <= nu) of the basis in row order
@@ -77,15 +78,16 @@ __global__ void fft_tsym_kernel(const R *__restrict__ T, int nbf, int S, int sbf
 // products are state-independent, so each is formed once per point and used
 // for the SBF states of a sweep held in registers.
 //
-// CTA: TP points (TP / 32 contiguous per lane) x 8 warps.  The pairs stream
+// CTA: TP points (TP / 32 contiguous per lane) x 16 warps (the function values
+// of the tile hold one CTA per SM, so its own warps hide the latencies).  The pairs stream
 // through shared memory in chunks (1-D bulk async copies of the contiguous
 // Tsym and pair rows, double-buffered on mbarriers with bounded waits); warp w
-// takes pairs w, w + 8, ... of a chunk, so its lanes read the same Tsym row
+// takes pairs w, w + 16, ... of a chunk, so its lanes read the same Tsym row
 // (broadcast) at different points.  A pair with a function that is
 // identically zero on the tile (its Gaussians underflow, or the threshold
 // dropped every primitive) is skipped by the whole warp: an exact pruning.
 // smem: phi[nbf_pad][TP], active[nbf_pad] (bytes), 2 stages of
-// (Tsym[kPairChunk][SBF], pairs[kPairChunk]), one state's partial densities [8][TP].
+// (Tsym[kPairChunk][SBF], pairs[kPairChunk]), one state's partial densities [warps][TP].
 template <typename R, int SBF, int TP>
 __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
     static_assert(T_BYTES % 16 == 0 && STAGE % 16 == 0, "bulk copies move multiples of 16 bytes");
     unsigned char *stage0 = smem_raw;  // [2][STAGE]
     R *part = reinterpret_cast<R *>(smem_raw + 2 * STAGE);
-    R *phi = part + (size_t)8 * TP;
+    R *phi = part + (size_t)kFftWarps * TP;
     unsigned char *active = reinterpret_cast<unsigned char *>(phi + (size_t)a.nbf_pad * TP);
     __shared__ __align__(8) uint64_t bars[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -107,13 +109,21 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
     }
     for (int e = tid; e < a.nbf_pad * TP; e += kFftThreads) phi[e] = R(0);
     __syncthreads();
-    // ---- 1. basis function values at the tile's points
-    if (tid < TP) {
-        const int64_t p = p0 + tid;
+    // ---- 1. basis function values at the tile's points: kFftThreads / TP
+    // groups of TP threads, group g taking the records whose first function
+    // index is g modulo the group count, so all primitives of a function are
+    // added by one thread in record order (the values do not depend on the
+    // grouping)
+    static_assert(kFftThreads % TP == 0, "whole groups of TP threads");
+    constexpr int kTabGroups = kFftThreads / TP;
+    {
+        const int pt = tid % TP, grp = tid / TP;
+        const int64_t p = p0 + pt;
         if (p < a.npts) {
             const int c = (int)(p % a.nz), b = (int)((p / a.nz) % a.ny), aa = (int)(p / ((int64_t)a.ny * a.nz));
             const double rx = a.xmin[0] + aa * a.dx[0], ry = a.xmin[1] + b * a.dx[1], rz = a.xmin[2] + c * a.dx[2];
             for (int rec = 0; rec < a.ps.n_rec; ++rec) {
+                if (a.ps.rec_fn0[rec] % kTabGroups != grp) continue;
                 const double dxr = rx - a.ps.rec_xyz[3 * rec], dyr = ry - a.ps.rec_xyz[3 * rec + 1],
                              dzr = rz - a.ps.rec_xyz[3 * rec + 2];
                 const double ex = a.ps.rec_alpha[rec] * (dxr * dxr + dyr * dyr + dzr * dzr);
@@ -129,8 +139,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
                     R v = (R)a.ps.rec_w[kRecW * rec + j] * g;
                     for (int ax = 0; ax < 3; ++ax)
                         for (int k = 0; k < pw[ax]; ++k) v *= d[ax];
-                    // row-major points within a lane's group: point tid lives at lane*PT+i
-                    phi[(size_t)(fn0 + j) * TP + tid] += v;
+                    // row-major points within a lane's group: point pt lives at lane*PT+i
+                    phi[(size_t)(fn0 + j) * TP + pt] += v;
                 }
             }
         }
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
             for (int q = 0; q < SBF; ++q)
 #pragma unroll
                 for (int i = 0; i < PT; ++i) acc[q][i] = R(0);
-            for (int kk = warp; kk < kPairChunk; kk += kFftThreads / 32) {
+            for (int kk = warp; kk < kPairChunk; kk += kFftWarps) {
                 const int2 pr = pc[kk];
                 if (pr.x < 0 || !active[pr.x] || !active[pr.y]) continue;
                 const R *pa = phi + (size_t)pr.x * TP + lane * PT;
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
             }
         }
         if (!ok) break;
-        // reduce the eight warps' partial sums state by state and write the fields
+        // reduce the warps' partial sums state by state and write the fields
         // (point index lane * PT + i)
 #pragma unroll
         for (int q = 0; q < SBF; ++q) {
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
             const int s = sweep * SBF + q;
             if (tid < TP) {
                 R v = R(0);
-                for (int w = 0; w < kFftThreads / 32; ++w) v += part[(size_t)w * TP + tid];
+                for (int w = 0; w < kFftWarps; ++w) v += part[(size_t)w * TP + tid];
                 v *= (R)a.scale;
                 const int64_t p = p0 + tid;
                 double sq = 0.0;
@@ -386,7 +396,7 @@ static cudaError_t density_t(const FftDensityArgs &a, cudaStream_t st) {
 size_t fft_density_smem(int fp64, int nbf_pad, int sbf, int tp) {
     const size_t rs = fp64 ? sizeof(double) : sizeof(float);
     const size_t stage = (size_t)kPairChunk * sbf * rs + (size_t)kPairChunk * sizeof(int2);
-    return 2 * stage + rs * ((size_t)8 * tp + (size_t)nbf_pad * tp) + (size_t)nbf_pad + 128;
+    return 2 * stage + rs * ((size_t)kFftWarps * tp + (size_t)nbf_pad * tp) + (size_t)nbf_pad + 128;
 }
 
 int64_t fft_pair_kpad(int nbf) {
