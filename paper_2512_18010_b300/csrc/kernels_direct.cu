@@ -415,12 +415,21 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
                     E[j] = fma(c[m * SB + j], mono, E[j]);
             }
         });
+        if constexpr (L == 0) {
+            // s-s pairs have no odd monomial: f += g E
 #pragma unroll
-        for (int j = 0; j < SB; ++j) {
-            acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
-            acc.pr[j] = fma(-g.y, O[j], acc.pr[j]);
-            acc.pi[j] = fma(g.x, O[j], acc.pi[j]);
-            acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
+            for (int j = 0; j < SB; ++j) {
+                acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
+                acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < SB; ++j) {
+                acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
+                acc.pr[j] = fma(-g.y, O[j], acc.pr[j]);
+                acc.pi[j] = fma(g.x, O[j], acc.pi[j]);
+                acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
+            }
         }
         if ((i % kFlushPairs) == kFlushPairs - 1) acc.flush();
     }
@@ -656,8 +665,14 @@ cudaError_t launch_direct(const DirectArgs &a, int fp64, int list_mode, int64_t 
     if (a.nq == 0) return cudaSuccess;
     cudaError_t e;
     if (fp64) {
-        if (a.SB != 4) return cudaErrorInvalidValue;
-        e = launch_direct_t<double, 4>(a, list_mode != 0, launches, st);
+        if (a.SB == 4)
+            e = launch_direct_t<double, 4>(a, list_mode != 0, launches, st);
+        else if (a.SB == 8)
+            e = launch_direct_t<double, 8>(a, list_mode != 0, launches, st);
+        else if (a.SB == 12)
+            e = launch_direct_t<double, 12>(a, list_mode != 0, launches, st);
+        else
+            return cudaErrorInvalidValue;
     } else {
         if (a.SB == 8)
             e = launch_direct_t<float, 8>(a, list_mode != 0, launches, st);
