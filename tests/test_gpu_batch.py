@@ -46,11 +46,11 @@ def make_batch(ctx, jobs, prec):
     return specs, handles
 
 
-@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X3, scff.FP32])
+@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X3, scff.FP32, scff.FP64])
 @pytest.mark.parametrize("split", [False, True])
 def test_batch_equals_alone(ctx, prec, split):
     import torch
-    if split and prec == scff.FP32:
+    if split and prec in (scff.FP32, scff.FP64):
         pytest.skip("direct-path jobs are not grouped")
     jobs = mixed_jobs()
     specs, handles = make_batch(ctx, jobs, prec)
@@ -62,7 +62,7 @@ def test_batch_equals_alone(ctx, prec, split):
         plan.release()
         plan = ctx.plan(specs, precision=prec, workspace_bytes=int(0.85 * total))
         info = plan.info()
-    if prec != scff.FP32:
+    if prec not in (scff.FP32, scff.FP64):
         assert info["tc_jobs"] == len(jobs)
         assert (info["groups"] > 1) == split
     stream = torch.cuda.Stream()
@@ -89,7 +89,7 @@ def test_batch_equals_alone(ctx, prec, split):
         fc = f.cpu().numpy()
         fc = fc[..., 0] + 1j * fc[..., 1]
         err = np.max(np.abs(fc[:, idx] - ref)) / np.max(np.abs(ref))
-        assert err < 1e-5
+        assert err < (1e-10 if prec == scff.FP64 else 1e-5)
     plan.release()
 
 
