@@ -99,6 +99,9 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
     R *part = reinterpret_cast<R *>(smem_raw + 2 * STAGE);
     R *phi = part + (size_t)kFftWarps * TP;
     unsigned char *active = reinterpret_cast<unsigned char *>(phi + (size_t)a.nbf_pad * TP);
+    // the active pairs of the current chunk, compacted: (mu, nu, index in chunk)
+    int4 *alist = reinterpret_cast<int4 *>(((uintptr_t)(active + a.nbf_pad) + 15) & ~uintptr_t(15));
+    int *wcnt = reinterpret_cast<int *>(alist + kPairChunk);  // [kPairChunk / 32] counts per warp
     __shared__ __align__(8) uint64_t bars[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * TP;
@@ -185,16 +188,39 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
             const unsigned char *st = stage0 + (g & 1) * STAGE;
             const R *Tc = reinterpret_cast<const R *>(st);
             const int2 *pc = reinterpret_cast<const int2 *>(st + T_BYTES);
+            // compact the chunk's active pairs (both functions nonzero on the
+            // tile), in chunk order, so the product loop has neither branches
+            // nor dependent index loads
+            static_assert(kPairChunk <= kFftThreads && kPairChunk % 32 == 0, "one thread per pair of a chunk");
+            bool act = false;
+            int2 prc = make_int2(-1, -1);
+            if (tid < kPairChunk) {
+                prc = pc[tid];
+                act = prc.x >= 0 && active[prc.x] && active[prc.y];
+            }
+            const unsigned am = __ballot_sync(0xffffffffu, act);
+            if (tid < kPairChunk && lane == 0) wcnt[warp] = __popc(am);
+            __syncthreads();
+            int n_act = 0, off = 0;
+#pragma unroll
+            for (int w = 0; w < kPairChunk / 32; ++w) {
+                const int cw = wcnt[w];
+                if (w < warp) off += cw;
+                n_act += cw;
+            }
+            if (act) alist[off + __popc(am & ((1u << lane) - 1u))] = make_int4(prc.x, prc.y, tid, 0);
+            __syncthreads();
             R acc[SBF][PT];
 #pragma unroll
             for (int q = 0; q < SBF; ++q)
 #pragma unroll
                 for (int i = 0; i < PT; ++i) acc[q][i] = R(0);
-            for (int kk = warp; kk < kPairChunk; kk += kFftWarps) {
-                const int2 pr = pc[kk];
-                if (pr.x < 0 || !active[pr.x] || !active[pr.y]) continue;
-                const R *pa = phi + (size_t)pr.x * TP + lane * PT;
-                const R *pb = phi + (size_t)pr.y * TP + lane * PT;
+#pragma unroll 2
+            for (int t = warp; t < n_act; t += kFftWarps) {
+                const int4 e = alist[t];
+                const int kk = e.z;
+                const R *pa = phi + (size_t)e.x * TP + lane * PT;
+                const R *pb = phi + (size_t)e.y * TP + lane * PT;
                 R prod[PT];
 #pragma unroll
                 for (int i = 0; i < PT; ++i) prod[i] = pa[i] * pb[i];
@@ -396,7 +422,8 @@ static cudaError_t density_t(const FftDensityArgs &a, cudaStream_t st) {
 size_t fft_density_smem(int fp64, int nbf_pad, int sbf, int tp) {
     const size_t rs = fp64 ? sizeof(double) : sizeof(float);
     const size_t stage = (size_t)kPairChunk * sbf * rs + (size_t)kPairChunk * sizeof(int2);
-    return 2 * stage + rs * ((size_t)kFftWarps * tp + (size_t)nbf_pad * tp) + (size_t)nbf_pad + 128;
+    return 2 * stage + rs * ((size_t)kFftWarps * tp + (size_t)nbf_pad * tp) + (size_t)nbf_pad + 16 +
+           sizeof(int4) * kPairChunk + sizeof(int) * (kPairChunk / 32) + 128;
 }
 
 int64_t fft_pair_kpad(int nbf) {
