@@ -1080,7 +1080,11 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
     const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
     const bool tc_path = tc_prec && g->product;
-    FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_state_block(S, fp64)};
+    int dev_sms = 148;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int direct_sb = fp64 ? direct_state_block_fp64(S, grid_half(c, g) ? (nq + 1) / 2 : nq, dev_sms)
+                               : direct_state_block(S, false);
+    FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_sb};
     const PairSetDev *ps = &b->dev;
     if (c->screen_eps > 0 && nq > 0) {
         ScreenedSet *se = nullptr;

@@ -128,6 +128,22 @@ inline int direct_state_block(int S, bool fp64) {
     return S <= 8 ? 8 : (S <= 12 ? 12 : (S <= 16 ? 16 : (S % 12 == 0 ? 12 : 16)));
 }
 
+// FP64 state block for a job of nq evaluated points: blocks of 12 states
+// share the pair factors and monomials best, but a small job needs more,
+// smaller blocks to fill the GPU (128 points per block); the largest of
+// 12, 8, 4 (fewest padded states first) that still gives two blocks per SM,
+// else 4.  The results do not depend on the block size.
+inline int direct_state_block_fp64(int S, int64_t nq, int sms) {
+    const int64_t qb = (nq + 127) / 128;
+    const int pref = direct_state_block(S, true);
+    for (int sb : {12, 8, 4}) {
+        if (sb > pref) continue;
+        if ((S + sb - 1) / sb * sb > (S + pref - 1) / pref * pref && sb != 4) continue;
+        if (qb * ((S + sb - 1) / sb) >= 2 * (int64_t)sms) return sb;
+    }
+    return 4;
+}
+
 // ---------------------------------------------------------------- kernels
 // All launchers return the launch status and never synchronise.
 
