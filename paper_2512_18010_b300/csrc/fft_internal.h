@@ -46,6 +46,7 @@ struct FftUnpackArgs {
     double dq3_over_2pi3;
     void *f, *f2;              // [S][n0][n1][n2] complex and |f|^2 (float or double), either may be null
     double *parseval;          // [S][2] (momentum-space sums accumulated here) or null
+    double2 *phase;            // workspace: [n0 + n1 + n2] per-axis factors e^{i dq al x_min}
 };
 
 // Shared memory of the density kernel for sweeps of sbf states and tp points per tile.

@@ -101,6 +101,8 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     const size_t o_pairs = o;
     o = up256(o + sizeof(int2) * (size_t)kpad);
     const size_t bytes_f = 2 * rsz * (size_t)S * npts, bytes_f2 = rsz * (size_t)S * npts;
+    const size_t o_phase = o;
+    o = up256(o + sizeof(double2) * (size_t)(nx + ny + nz));
     const size_t o_out = o;
     if (!out_on_device) o = up256(o + up256(bytes_f) + up256(bytes_f2));
     const size_t total = o + 1024;
@@ -205,8 +207,9 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     ua.f = df;
     ua.f2 = df2;
     ua.parseval = par;
+    ua.phase = reinterpret_cast<double2 *>(w + o_phase);
     FCUDA(launch_fft_unpack(ua, fp64 ? 1 : 0, st));
-    ++c->launches;
+    c->launches += 2;
     if (!out_on_device) {
         if (f_out) FCUDA(cudaMemcpyAsync(f_out, df, bytes_f, cudaMemcpyDeviceToHost, st));
         if (f2_out) FCUDA(cudaMemcpyAsync(f2_out, df2, bytes_f2, cudaMemcpyDeviceToHost, st));

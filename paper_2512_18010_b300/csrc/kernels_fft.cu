@@ -377,9 +377,10 @@ __global__ void fft_unpack_kernel(FftUnpackArgs a) {
             fr = 0.5 * ((double)G.y + (double)Gm.y);
             fi = -0.5 * ((double)G.x - (double)Gm.x);
         }
-        const double ph = a.dq[0] * al[0] * a.xmin[0] + a.dq[1] * al[1] * a.xmin[1] + a.dq[2] * al[2] * a.xmin[2];
-        double sn, cs;
-        sincos(ph, &sn, &cs);
+        // e^{i q.x_min} as the product of the three per-axis factors
+        const double2 px = a.phase[ix], py = a.phase[a.n[0] + iy], pz = a.phase[a.n[0] + a.n[1] + iz];
+        const double xyr = px.x * py.x - px.y * py.y, xyi = px.x * py.y + px.y * py.x;
+        const double cs = xyr * pz.x - xyi * pz.y, sn = xyr * pz.y + xyi * pz.x;
         const double vr = a.vpix * (fr * cs - fi * sn), vi = a.vpix * (fr * sn + fi * cs);
         V out;
         out.x = (R)vr;
@@ -388,11 +389,35 @@ __global__ void fft_unpack_kernel(FftUnpackArgs a) {
         if (a.f2) reinterpret_cast<R *>(a.f2)[idx] = out.x * out.x + out.y * out.y;
         sq = vr * vr + vi * vi;
     }
-    // Parseval, momentum side: one atomic per warp.  npts is a multiple of 32,
-    // so a warp never spans two states; every thread of the block reaches the
-    // shuffle (no early return).
+    // Parseval, momentum side: warp sums, then one atomic per block when the
+    // block lies within one state (npts a multiple of the block size), else
+    // one per warp (npts is a multiple of 32, so a warp never spans two
+    // states).  Every thread of the block reaches the shuffles (no early return).
+    __shared__ double wsum[8];
     for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
-    if ((threadIdx.x & 31) == 0 && idx < total && a.parseval) atomicAdd(&a.parseval[2 * s + 1], sq * a.dq3_over_2pi3);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (npts % blockDim.x == 0) {
+        if (lane == 0) wsum[wid] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0 && idx < total && a.parseval) {
+            double b = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += wsum[w];
+            atomicAdd(&a.parseval[2 * s + 1], b * a.dq3_over_2pi3);
+        }
+    } else if (lane == 0 && idx < total && a.parseval) {
+        atomicAdd(&a.parseval[2 * s + 1], sq * a.dq3_over_2pi3);
+    }
+}
+
+// Per-axis factors e^{i dq_k al x_min,k} of the box-corner phase, al = i - n_k/2.
+__global__ void fft_phase_table_kernel(FftUnpackArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n[0] + a.n[1] + a.n[2]) return;
+    const int ax = i < a.n[0] ? 0 : (i < a.n[0] + a.n[1] ? 1 : 2);
+    const int j = i - (ax > 0 ? a.n[0] : 0) - (ax > 1 ? a.n[1] : 0);
+    double sn, cs;
+    sincos(a.dq[ax] * (j - a.n[ax] / 2) * a.xmin[ax], &sn, &cs);
+    a.phase[i] = make_double2(cs, sn);
 }
 
 __global__ void cast_f64_to_f32_kernel(const double *__restrict__ in, int64_t n, float *__restrict__ out) {
@@ -486,6 +511,8 @@ cudaError_t launch_fft_axis(const FftAxisArgs &a, int fp64, int64_t n_groups, cu
 cudaError_t launch_fft_unpack(const FftUnpackArgs &a, int fp64, cudaStream_t st) {
     const int64_t tot = (int64_t)a.S * a.n[0] * a.n[1] * a.n[2];
     if (tot == 0) return cudaSuccess;
+    const int nax = a.n[0] + a.n[1] + a.n[2];
+    fft_phase_table_kernel<<<(nax + 127) / 128, 128, 0, st>>>(a);
     const unsigned blocks = (unsigned)((tot + 255) / 256);
     if (fp64)
         fft_unpack_kernel<double><<<blocks, 256, 0, st>>>(a);
