@@ -27,6 +27,11 @@ struct FftDensityArgs {
     const int2 *pairs;         // [kpad] (mu, nu) per pair, (-1, -1) for padding
     int64_t kpad;              // pairs padded to whole chunks
     int *err;                  // set on a timed-out wait
+    // FP32 tabulation only (fft_record_prep): per record, the centre's grid
+    // coordinate split into an integer and a fraction, and the exponent, as
+    // (ia_x, ia_y, ia_z, alpha) and (fa_x, fa_y, fa_z, 0); weights [n_rec][kRecW]
+    const float4 *recg;
+    const float *recw;
 };
 
 struct FftAxisArgs {
@@ -52,6 +57,8 @@ struct FftUnpackArgs {
 // Shared memory of the density kernel for sweeps of sbf states and tp points per tile.
 size_t fft_density_smem(int fp64, int nbf_pad, int sbf, int tp);
 cudaError_t launch_fft_density(const FftDensityArgs &a, int fp64, int sbf, int tp, cudaStream_t st);
+// Per-record FP32 tabulation data (FftDensityArgs::recg, recw) of the box in a.
+cudaError_t launch_fft_record_prep(const FftDensityArgs &a, float4 *recg, float *recw, cudaStream_t st);
 // Pairs (mu <= nu) of nbf functions padded to whole staging chunks.
 int64_t fft_pair_kpad(int nbf);
 cudaError_t launch_fft_tsym(const void *T, int fp64, int nbf, int S, int sbf, void *tsym, int2 *pairs,

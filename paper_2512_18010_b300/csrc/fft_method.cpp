@@ -103,6 +103,10 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     const size_t bytes_f = 2 * rsz * (size_t)S * npts, bytes_f2 = rsz * (size_t)S * npts;
     const size_t o_phase = o;
     o = up256(o + sizeof(double2) * (size_t)(nx + ny + nz));
+    const size_t o_recg = o;
+    o = up256(o + (fp64 ? 0 : 2 * sizeof(float4) * (size_t)ps.n_rec));
+    const size_t o_recw = o;
+    o = up256(o + (fp64 ? 0 : sizeof(float) * kRecW * (size_t)ps.n_rec));
     const size_t o_out = o;
     if (!out_on_device) o = up256(o + up256(bytes_f) + up256(bytes_f2));
     const size_t total = o + 1024;
@@ -165,6 +169,12 @@ extern "C" scff_status scff_fft_form_factor(scff_ctx *c, scff_basis_h b, scff_tr
     da.pairs = reinterpret_cast<const int2 *>(w + o_pairs);
     da.kpad = kpad;
     da.err = c->d_err;
+    if (!fp64) {
+        da.recg = reinterpret_cast<const float4 *>(w + o_recg);
+        da.recw = reinterpret_cast<const float *>(w + o_recw);
+        FCUDA(launch_fft_record_prep(da, reinterpret_cast<float4 *>(w + o_recg), reinterpret_cast<float *>(w + o_recw), st));
+        ++c->launches;
+    }
     FCUDA(launch_fft_density(da, fp64 ? 1 : 0, sbf, tp, st));
     ++c->launches;
     // ---- 2. three in-place passes, z, y, x

@@ -119,7 +119,40 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
     // grouping)
     static_assert(kFftThreads % TP == 0, "whole groups of TP threads");
     constexpr int kTabGroups = kFftThreads / TP;
-    {
+    if constexpr (sizeof(R) == 4) {
+        // FP32: the displacement from a record's centre is ((i - ia) - fa) dx
+        // per axis, an exact integer difference less a fraction, so it keeps
+        // its relative accuracy however close the point is to the centre
+        const int pt = tid % TP, grp = tid / TP;
+        const int64_t p = p0 + pt;
+        if (p < a.npts) {
+            const float ci = (float)(p % a.nz), bi = (float)((p / a.nz) % a.ny),
+                        ai = (float)(p / ((int64_t)a.ny * a.nz));
+            const float dxf = (float)a.dx[0], dyf = (float)a.dx[1], dzf = (float)a.dx[2];
+            const float cutf = (float)a.cut;
+            for (int rec = 0; rec < a.ps.n_rec; ++rec) {
+                const int fn0 = a.ps.rec_fn0[rec];
+                if (fn0 % kTabGroups != grp) continue;
+                const float4 gi = a.recg[2 * rec], gf = a.recg[2 * rec + 1];
+                const float d[3] = {((ai - gi.x) - gf.x) * dxf, ((bi - gi.y) - gf.y) * dyf,
+                                    ((ci - gi.z) - gf.z) * dzf};
+                const float ex = gi.w * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (cutf > 0.f && ex > cutf) continue;
+                const float g = expf(-ex);
+                if (g == 0.f) continue;
+                const int type = a.ps.rec_type[rec];
+                const int nf = rec_nfn(type);
+                for (int j = 0; j < nf; ++j) {
+                    int pw[3];
+                    rec_powers(type, j, pw);
+                    float v = a.recw[kRecW * rec + j] * g;
+                    for (int ax = 0; ax < 3; ++ax)
+                        for (int k = 0; k < pw[ax]; ++k) v *= d[ax];
+                    phi[(size_t)(fn0 + j) * TP + pt] += (R)v;
+                }
+            }
+        }
+    } else {
         const int pt = tid % TP, grp = tid / TP;
         const int64_t p = p0 + pt;
         if (p < a.npts) {
@@ -285,7 +318,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_density_kernel(FftDensityArgs
 template <typename R>
 __global__ void __launch_bounds__(256) fft_axis_kernel(FftAxisArgs a) {
     using V = typename C2<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     V *buf = reinterpret_cast<V *>(smem_raw);
     V *tw = buf + (size_t)a.W * a.n;
     V *data = reinterpret_cast<V *>(a.data);
@@ -430,6 +463,27 @@ __global__ void cast_f64_to_f32_kernel(const double *__restrict__ in, int64_t n,
 cudaError_t launch_cast_f64_to_f32(const double *in, int64_t n, float *out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     cast_f64_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+__global__ void fft_record_prep_kernel(FftDensityArgs a, float4 *__restrict__ recg, float *__restrict__ recw) {
+    const int rec = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rec >= a.ps.n_rec) return;
+    float ia[3], fa[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        const double gc = (a.ps.rec_xyz[3 * rec + ax] - a.xmin[ax]) / a.dx[ax];
+        const double fl = floor(gc);
+        ia[ax] = (float)fl;
+        fa[ax] = (float)(gc - fl);
+    }
+    recg[2 * rec] = make_float4(ia[0], ia[1], ia[2], (float)a.ps.rec_alpha[rec]);
+    recg[2 * rec + 1] = make_float4(fa[0], fa[1], fa[2], 0.f);
+    for (int j = 0; j < kRecW; ++j) recw[kRecW * rec + j] = (float)a.ps.rec_w[kRecW * rec + j];
+}
+
+cudaError_t launch_fft_record_prep(const FftDensityArgs &a, float4 *recg, float *recw, cudaStream_t st) {
+    if (a.ps.n_rec == 0) return cudaSuccess;
+    fft_record_prep_kernel<<<(a.ps.n_rec + 127) / 128, 128, 0, st>>>(a, recg, recw);
     return cudaGetLastError();
 }
 
