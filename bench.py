@@ -399,6 +399,28 @@ def make_jobs(fn, n):
                 os.environ[k] = v
 
 
+def tc_useful(jobs, precision, seconds, scff):
+    """Tensor work of a set of jobs on the split-precision path per second: 8 flop per complex
+    multiply-add x (pair,v,w) rows x split products, over the rows (s, ix) of the evaluated
+    half of each antisymmetric grid, against the measured sustained BF16 rate."""
+    pieces = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3}.get(precision)
+    if pieces is None or seconds <= 0:
+        return None
+    flops = 0
+    for j in jobs:
+        kvw = pair_stats(j.mol)[2]
+        flops += 8 * pieces * kvw * j.n_states * ((len(j.qx) + 1) // 2) * len(j.qy) * len(j.qz)
+    tf = flops / seconds / 1e12
+    out = {"tensor_tflops_useful": tf, "flop": float(flops)}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        sus = float(peaks["bf16_tflops_sustained"]) * (TF32_PER_BF16 if precision == scff.TF32X3 else 1.0)
+        out["frac_of_measured_sustained"] = tf / sus
+    except Exception:
+        pass
+    return out
+
+
 def serving_run(scff, ctx, jobs, precision, rate_factor=0.7):
     """Saturation throughput, then a Poisson stream at rate_factor x capacity: p50/p99 latency."""
     import torch
@@ -439,7 +461,8 @@ def serving_run(scff, ctx, jobs, precision, rate_factor=0.7):
     return {
         "jobs": len(jobs), "large_jobs": int(sum(1 for j in jobs if j.mol.heavy >= 40)),
         "saturation": {"value": units / wall_sat, "unit": UNIT, "wall_s": wall_sat, "batches": st_sat["batches"],
-                       "max_inflight": st_sat["max_inflight"]},
+                       "max_inflight": st_sat["max_inflight"],
+                       "tensor": tc_useful(jobs, precision, wall_sat, scff)},
         "poisson": {"rate_jobs_per_s": rate, "rate_factor_of_capacity": rate_factor, "value": units / wall,
                     "unit": UNIT, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
@@ -475,6 +498,7 @@ def batch_run(scff, ctx, jobs, precision, steps=2):
         ctx.release(s[2])
         ctx.release(s[0])
     return {"jobs": len(jobs), "value": units / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms,
+            "tensor": tc_useful(jobs, precision, ms / 1e3, scff),
             "launches_per_run": info["launches_per_run"], "groups": info["groups"], "tiles": info["tiles"],
             "graph": "one captured CUDA graph per plan, replayed"}
 
