@@ -381,7 +381,13 @@ template <typename R, int SB> struct Acc {
     __device__ __forceinline__ R im(int j) const { return sizeof(R) == 4 ? hi[j] + li[j] : pi[j]; }
 };
 
-template <typename R, int SB, int L, bool LIST>
+// VEC: the per-state coefficients of a monomial are read four per 16-byte
+// shared-memory load (a pair's rows are SB floats, so each starts 16-byte
+// aligned).  It pays where the block's points share (ix, iy) (10-heavy-atom
+// job, 128^3: 105 -> 90 ms) and costs where three table entries per pair
+// come from global memory (benzene-scale job, 64^3: 5.2 -> 5.5 ms), so the
+// launcher picks it for the first case only.
+template <typename R, int SB, int L, bool LIST, bool VEC>
 __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf,
                                               const typename Cplx<R>::T *__restrict__ gxy, int pr0,
                                               int np, const R (&px)[kMaxPairL + 1], const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1],
@@ -407,12 +413,29 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
             constexpr int m = decltype(M)::value;
             constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
             const R mono = px[u] * py[v] * pz[w];
+            if constexpr (VEC) {
+                static_assert(sizeof(R) == 4 && SB % 4 == 0, "four FP32 coefficients per load");
+                const float4 *c4 = reinterpret_cast<const float4 *>(c + m * SB);
 #pragma unroll
-            for (int j = 0; j < SB; ++j) {
-                if constexpr (((u + v + w) & 1) != 0)
-                    O[j] = fma(c[m * SB + j], mono, O[j]);
-                else
-                    E[j] = fma(c[m * SB + j], mono, E[j]);
+                for (int jj = 0; jj < SB / 4; ++jj) {
+                    const float4 cv = c4[jj];
+                    const R cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if constexpr (((u + v + w) & 1) != 0)
+                            O[4 * jj + t] = fma(cc[t], mono, O[4 * jj + t]);
+                        else
+                            E[4 * jj + t] = fma(cc[t], mono, E[4 * jj + t]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < SB; ++j) {
+                    if constexpr (((u + v + w) & 1) != 0)
+                        O[j] = fma(c[m * SB + j], mono, O[j]);
+                    else
+                        E[j] = fma(c[m * SB + j], mono, E[j]);
+                }
             }
         });
         if constexpr (L == 0) {
@@ -438,7 +461,7 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
 
 // Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
 // false (uniformly across the block) when a wait timed out.
-template <typename R, int SB, int L, bool LIST>
+template <typename R, int SB, int L, bool LIST, bool VEC>
 __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, typename Cplx<R>::T *gxy,
                                           int bx, int by, uint64_t *bars,
                                           uint32_t &phase, int sblk, const R (&px)[kMaxPairL + 1],
@@ -491,7 +514,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
             }
             __syncthreads();
         }
-        consume_chunk<R, SB, L, LIST>(p, bufs[b], gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz,
+        consume_chunk<R, SB, L, LIST, VEC>(p, bufs[b], gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz,
                                       q2, acc);
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
@@ -499,7 +522,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
     return ok;
 }
 
-template <typename R, int SB, bool LIST, bool HIGH>
+template <typename R, int SB, bool LIST, bool HIGH, bool VEC = false>
 __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) {
     __shared__ __align__(128) unsigned char smem[2 * kChunkBytes];
     __shared__ __align__(16) typename Cplx<R>::T gxy[kMaxChunkPairs];
@@ -574,7 +597,7 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
     auto run = [&](auto LC) {
         constexpr int L = decltype(LC)::value;
         if (ok)
-            ok = run_class<R, SB, L, LIST>(p, buf0, buf1, gxy, bx, by, bars, phase, sblk, px, py, pz, ix, iy, iz,
+            ok = run_class<R, SB, L, LIST, VEC>(p, buf0, buf1, gxy, bx, by, bars, phase, sblk, px, py, pz, ix, iy, iz,
                                            qx, qy, qz, q2, acc);
     };
     if constexpr (HIGH) {
@@ -644,8 +667,13 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *laun
     const bool has_high = a.ps->pair_off[kMaxPairL + 1] > a.ps->pair_off[kHighClass];
     if (has_low || !has_high) {
         p.part = has_high ? 0 : kPartFinal;
+        // the vector loads for 12-state FP32 blocks on block-shared rows only
+        // (the other state blocks, and the f classes, spill with them)
+        constexpr bool kVec = sizeof(R) == 4 && SB == 12;
         if (list)
             direct_kernel<R, SB, true, false><<<grid, kDirectThreads, 0, st>>>(p);
+        else if (kVec && p.xy_uniform)
+            direct_kernel<R, SB, false, false, kVec><<<grid, kDirectThreads, 0, st>>>(p);
         else
             direct_kernel<R, SB, false, false><<<grid, kDirectThreads, 0, st>>>(p);
         if (launches) ++*launches;

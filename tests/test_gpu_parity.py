@@ -93,6 +93,20 @@ def test_ragged_grid_and_odd_state_count(ctx, prec):
     assert rel_err(f[:, idx], ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32])
+def test_block_shared_rows_with_padded_states(ctx, prec):
+    # z axis a multiple of the 128-point block (every block's points share (ix, iy), the FP32
+    # path's shared-row variant), 10 states padded to a block of 12, odd x axis (Hermitian half
+    # ends inside a block)
+    base = W.config1()
+    T = W.transition_matrices(78, 10, base.mol.nbf)
+    job = W.Job(base.mol, T, W.axis(5, 6.0), W.axis(3, 9.0), W.axis(256, 11.0))
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 600, 6)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
 def test_degenerate_inputs(ctx):
     job = W.config1()
     b = ctx.basis(job.mol)
