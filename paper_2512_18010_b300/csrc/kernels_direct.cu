@@ -387,7 +387,10 @@ template <typename R, int SB> struct Acc {
 // job, 128^3: 105 -> 90 ms) and costs where three table entries per pair
 // come from global memory (benzene-scale job, 64^3: 5.2 -> 5.5 ms), so the
 // launcher picks it for the first case only.
-template <typename R, int SB, int L, bool LIST, bool VEC>
+// NOUNI: compiled for grids whose blocks do not share (ix, iy), without the
+// shared-row branches at all (the runtime test alone, although uniform across
+// the block, took the 64^3 FP32 job from 3.8 to 5.1 ms).
+template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI>
 __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf,
                                               const typename Cplx<R>::T *__restrict__ gxy, int pr0,
                                               int np, const R (&px)[kMaxPairL + 1], const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1],
@@ -397,7 +400,7 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
     using V = typename Cplx<R>::T;
     for (int i = 0; i < np; ++i) {
         V g;
-        if (!LIST && p.xy_uniform) {
+        if (!LIST && !NOUNI && p.xy_uniform) {
             const V a = gxy[i];
             const V c = static_cast<const V *>(p.gz)[(int64_t)(pr0 + i) * p.nz + iz];
             g.x = a.x * c.x - a.y * c.y;
@@ -461,7 +464,7 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
 
 // Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
 // false (uniformly across the block) when a wait timed out.
-template <typename R, int SB, int L, bool LIST, bool VEC>
+template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI>
 __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, typename Cplx<R>::T *gxy,
                                           int bx, int by, uint64_t *bars,
                                           uint32_t &phase, int sblk, const R (&px)[kMaxPairL + 1],
@@ -500,7 +503,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
             break;
         }
         const int n = min(npc, npairs - c * npc);
-        if (!LIST && p.xy_uniform) {
+        if (!LIST && !NOUNI && p.xy_uniform) {
             // the block's x and y factors of this chunk's pairs, once per block
             using V = typename Cplx<R>::T;
             for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -514,7 +517,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
             }
             __syncthreads();
         }
-        consume_chunk<R, SB, L, LIST, VEC>(p, bufs[b], gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz,
+        consume_chunk<R, SB, L, LIST, VEC, NOUNI>(p, bufs[b], gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz,
                                       q2, acc);
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
@@ -522,7 +525,7 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
     return ok;
 }
 
-template <typename R, int SB, bool LIST, bool HIGH, bool VEC = false>
+template <typename R, int SB, bool LIST, bool HIGH, bool VEC = false, bool NOUNI = false>
 __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) {
     __shared__ __align__(128) unsigned char smem[2 * kChunkBytes];
     __shared__ __align__(16) typename Cplx<R>::T gxy[kMaxChunkPairs];
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
     auto run = [&](auto LC) {
         constexpr int L = decltype(LC)::value;
         if (ok)
-            ok = run_class<R, SB, L, LIST, VEC>(p, buf0, buf1, gxy, bx, by, bars, phase, sblk, px, py, pz, ix, iy, iz,
+            ok = run_class<R, SB, L, LIST, VEC, NOUNI>(p, buf0, buf1, gxy, bx, by, bars, phase, sblk, px, py, pz, ix, iy, iz,
                                            qx, qy, qz, q2, acc);
     };
     if constexpr (HIGH) {
@@ -674,6 +677,8 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *laun
             direct_kernel<R, SB, true, false><<<grid, kDirectThreads, 0, st>>>(p);
         else if (kVec && p.xy_uniform)
             direct_kernel<R, SB, false, false, kVec><<<grid, kDirectThreads, 0, st>>>(p);
+        else if (!p.xy_uniform)
+            direct_kernel<R, SB, false, false, false, true><<<grid, kDirectThreads, 0, st>>>(p);
         else
             direct_kernel<R, SB, false, false><<<grid, kDirectThreads, 0, st>>>(p);
         if (launches) ++*launches;
@@ -682,6 +687,8 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *laun
         p.part = kPartFinal | (has_low ? kPartContinue : 0);
         if (list)
             direct_kernel<R, SB, true, true><<<grid, kDirectThreads, 0, st>>>(p);
+        else if (!p.xy_uniform)
+            direct_kernel<R, SB, false, true, false, true><<<grid, kDirectThreads, 0, st>>>(p);
         else
             direct_kernel<R, SB, false, true><<<grid, kDirectThreads, 0, st>>>(p);
         if (launches) ++*launches;
