@@ -70,7 +70,6 @@ struct HostStage {
 };
 static HostStage g_host;
 static std::mutex g_mu;
-static void *g_addr[kMaxDevices];  // device address of g_scratch per device
 
 scff_status err(scff_status code, const char *fmt, ...) {
     char buf[384];
@@ -81,21 +80,20 @@ scff_status err(scff_status code, const char *fmt, ...) {
     return set_last_error(code, buf);
 }
 
-// Device address of g_scratch on the current device, resolved on the first
-// call made on that device.
+// Device address of g_scratch in the current device's current context.  It
+// is looked up on every call (the lookup allocates nothing), so an address
+// never outlives the context it belongs to: after cudaDeviceReset the next
+// call resolves the array of the new context instead of using a stale one.
 scff_status scratch_address(unsigned char **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return err(SCFF_ERR_CUDA, "scff_form_factor_static: cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return err(SCFF_ERR_INVALID_ARG, "scff_form_factor_static: device %d", dev);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return err(SCFF_ERR_CUDA, "scff_form_factor_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_addr[dev] = p;
-    }
-    *out = static_cast<unsigned char *>(g_addr[dev]);
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+        return err(SCFF_ERR_CUDA, "scff_form_factor_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    *out = static_cast<unsigned char *>(p);
     return SCFF_OK;
 }
 

@@ -67,6 +67,19 @@ def test_static_entry_matches_regular_entry_twice():
         ctx.close()
 
 
+def test_static_entry_matches_oracle():
+    """The allocation-free call checked against the FP64 oracle directly (not only against the
+    regular entry point): config 1 on explicit q points, including q = 0."""
+    import oracle
+    job = W.config1()
+    rng = np.random.default_rng(22)
+    q = np.vstack([np.zeros((1, 3)), rng.uniform(-10, 10, size=(255, 3))])
+    f, f2 = static_call(job, q)
+    ref = oracle.form_factor(job.mol, job.T, q)
+    assert rel_err(f, ref) < FP64_TOL
+    assert rel_err(f2, np.abs(ref) ** 2) < FP64_TOL
+
+
 def test_static_entry_rejects_oversize_basis():
     import torch
     big = W.molecule_dz_d(4242, 30)                # 30 heavy + 30 H: 450 records > 256
