@@ -68,10 +68,19 @@ typedef enum {
                         (six piece products per complex part), FP32 accumulation */
     SCFF_TF32X3 = 3, /* tensor cores, TF32 split into hi + lo pieces (three
                         piece products per complex part), FP32 accumulation */
-    SCFF_BF16X2 = 4  /* tensor cores, BF16 hi + lo (three piece products): the
-                        fastest mode, about 2e-5 relative error on the bundled
-                        workloads.  The tensor-core modes need a product grid;
-                        on an explicit q list they run the FP32 direct path. */
+    SCFF_BF16X2 = 4, /* tensor cores, BF16 hi + lo (three piece products),
+                        about 2e-5 relative error on the bundled workloads */
+    SCFF_FP16X2 = 5  /* tensor cores, FP16 hi + lo (three piece products,
+                        about 22 significant bits per operand), FP32
+                        accumulation: half the tensor work of SCFF_BF16X3 at
+                        the same 1e-5 bar.  FP16's narrow exponent range is
+                        handled by exact power-of-two scaling of the per-axis
+                        table rows, the A columns and the whole job (removed
+                        in the epilogue).  Product-grid form factors (single
+                        calls, plans, the server); the spherical method does
+                        not take it.  The tensor-core modes need a product
+                        grid; on an explicit q list they run the FP32 direct
+                        path (scff_last_path reports which path ran). */
 } scff_precision;
 
 /* scff_basis flags */
@@ -494,8 +503,10 @@ int64_t scff_kernel_launches(scff_ctx *ctx);
  * coefficients, states padded to a multiple of 4); larger inputs return
  * SCFF_ERR_INVALID_ARG with the limit in the message.
  *
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call looks up the scratch array's device address in the current
+ * context (cudaGetSymbolAddress, which allocates nothing), so the address
+ * stays valid across cudaDeviceReset; the first call on a device loads the
+ * library's module there, so make it before any stream capture.
  * Every call reuses the same scratch array, which keeps the previous call's
  * contents: the call rewrites everything it reads and clears its status word
  * itself.  Calls are serialised on the host, but calls whose GPU work could

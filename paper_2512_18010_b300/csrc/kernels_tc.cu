@@ -12,8 +12,8 @@
 // turns the whole product-grid evaluation into one dense complex contraction
 //   f[(s, ix), (iy, iz)] = sum_k A[(s,ix), k] W[k, (iy,iz)],
 // which runs on the 5th-generation tensor cores:
-//   * A (complex, FP32) is split into pieces (BF16 hi/mid/lo, BF16 hi/lo or
-//     TF32 hi/lo) and stored as the SW64-swizzled K-major shared-memory image
+//   * A (complex, FP32) is split into pieces (BF16 hi/mid/lo, BF16 hi/lo,
+//     FP16 hi/lo or TF32 hi/lo) and stored as the SW64-swizzled K-major shared-memory image
 //     of each 128 x 32-byte tile, so one 1-D bulk TMA copy lands a stage;
 //   * W is generated on the fly by eight warps from FP64-accurate per-axis
 //     tables (FP32 storage) and split the same way in shared memory;
@@ -34,14 +34,17 @@
 // with W generated from its radial and harmonic tables.  FP64 is used only for
 // the tables (range reduction of q.P) and upstream in the pair-prep.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "device_common.cuh"
+#include "../../include/scff.h"
 #include "scff_internal.h"
 #include "tc_internal.h"
 #include "tc_schedule.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <string.h>
 #include <thread>
 #include <vector>
@@ -68,16 +71,27 @@ static_assert(128 * LOW_REGS + GEN_WARPS * 32 * HIGH_REGS == THREADS * LAUNCH_RE
 static_assert(2 * BN == GEN_WARPS * 32, "two generator threads per W row");
 
 // Split kinds.  Every value x of A and W is stored as NP pieces whose sum is x
-// to about 8*NP (BF16) or 22 (TF32) bits; the products kept are those whose
+// to about 8*NP (BF16), 22 (FP16, TF32) bits; the products kept are those whose
 // piece orders add up to at most NP-1, which bounds the dropped terms by the
 // precision of the split.
 //   KIND_BF16X2: BF16 hi + lo,        products hh, hl, lh          (~2^-16)
 //   KIND_BF16X3: BF16 hi + mid + lo,  products hh, hm, mh, hl, lh, mm (~2^-24)
 //   KIND_TF32X2: TF32 hi + lo,        products hh, hl, lh          (~2^-21)
-enum { KIND_BF16X2 = 0, KIND_BF16X3 = 1, KIND_TF32X2 = 2 };
+//   KIND_FP16X2: FP16 hi + lo,        products hh, hl, lh          (~2^-22)
+// FP16 has 11 significant bits but only five exponent bits, so that kind
+// works on scaled operands: every (pair, axis, power) row of the Y and Z
+// tables is multiplied by a power of two that brings its largest possible
+// magnitude on the grid to 2^6 (so |W| <= 2^12), each A column by the inverse
+// of its W row's factor, and all of A by one further power of two per job
+// chosen from a bound on the largest term; the epilogue removes that factor.
+// Power-of-two factors are exact, so only the pieces' rounding remains.
+enum { KIND_BF16X2 = 0, KIND_BF16X3 = 1, KIND_TF32X2 = 2, KIND_FP16X2 = 3 };
 
 template <int KIND> struct Kind {
     static constexpr bool TF32 = KIND == KIND_TF32X2;
+    static constexpr bool FP16 = KIND == KIND_FP16X2;
+    // operand format of the instruction descriptor: 0 FP16, 1 BF16 (kind::f16), 2 TF32 (kind::tf32)
+    static constexpr uint32_t FMT = TF32 ? 2u : FP16 ? 0u : 1u;
     static constexpr int NP = KIND == KIND_BF16X3 ? 3 : 2;          // pieces per value
     static constexpr int NPROD = NP == 3 ? 6 : 3;                    // piece products per complex part
     static constexpr int ELEM = TF32 ? 4 : 2;
@@ -92,7 +106,7 @@ template <int KIND> struct Kind {
     // memory pays where the generators set the pace (BF16 hi/lo: -8%); where
     // the tensor pipe does (hi/mid/lo, TF32) it costs about 1%, so those read
     // them straight from global memory.
-    static constexpr bool STAGE_KO = KIND == KIND_BF16X2;
+    static constexpr bool STAGE_KO = KIND == KIND_BF16X2 || KIND == KIND_FP16X2;
     static constexpr int KO_BYTES = STAGE_KO ? GEN_WARPS * 2 * (BK / 2) * 8 : 0;
     static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256 + KO_BYTES;
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
@@ -109,6 +123,45 @@ __host__ __device__ __forceinline__ uint32_t sw64_offset(int row, int c) {
     constexpr int E = Kind<KIND>::ELEM, V = Kind<KIND>::PER_VEC;
     const int rr = row & 7;
     return (uint32_t)((row >> 3) * 512 + rr * 64 + ((((c / V) ^ ((rr >> 1) & 3))) << 4) + (c % V) * E);
+}
+
+// ------------------------------------------------------------------ FP16 operand scaling
+
+// Exponent e with 2^e >= max_{|q| <= Q} |q|^u exp(-q^2/(4p)) (inv4p = 1/(4p)):
+// the largest magnitude row u of a pair's axis table can take on an axis
+// whose points satisfy |q| <= Q.  For u >= 1 the maximum sits at q^2 = 2pu,
+// or at |q| = Q when the grid ends before it.  FP32 arithmetic with a margin
+// of 1e-3 in the exponent, rounded up, clamped to [-60, 60].
+__host__ __device__ __forceinline__ int axis_row_exp(int u, double inv4p, double Q) {
+    if (u == 0) return 0;
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float fu = (float)u, i4 = (float)inv4p, q = (float)Q;
+    const float peak2 = fu / (2.f * i4);
+    const float l2 = peak2 <= q * q ? 0.5f * fu * (log2f(peak2) - kLog2e) : fu * log2f(q) - q * q * i4 * kLog2e;
+    return (int)fminf(60.f, fmaxf(-60.f, ceilf(l2 + 1e-3f)));
+}
+
+// Target magnitude exponents of the FP16 kind: table rows are scaled to at
+// most 2^kRowExp, so |W| <= 2^(2 kRowExp); A is scaled so its largest
+// possible entry is at most 2^kAExp.
+constexpr int kRowExp = 6;
+constexpr int kAExp = 14;
+
+// x * 2^n for |n| <= 252, exact unless the result over- or underflows.
+__device__ __forceinline__ float pow2_scale(float x, int n) {
+    const int a = n / 2, b = n - a;
+    return x * __int_as_float((127 + a) << 23) * __int_as_float((127 + b) << 23);
+}
+
+// Job exponent G of the FP16 kind from the bound t of its largest term
+// (FP64 bits, 0 for an all-zero job): A carries 2^G so that the largest term
+// maps to about 2^(kAExp + 2 kRowExp).  ceil(log2 t) is read from the bits.
+__device__ __forceinline__ int fp16_job_exp(const unsigned long long *tmax) {
+    const unsigned long long b = *tmax;
+    if (b == 0) return 0;
+    const int ex = (int)((b >> 52) & 0x7FF) - 1023;
+    const int cl = ex + ((b & 0xFFFFFFFFFFFFFull) != 0 ? 1 : 0);
+    return max(-100, min(100, kAExp + 2 * kRowExp - cl));
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -128,12 +181,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
-// Instruction descriptor: D FP32, A/B BF16 (kind::f16) or TF32 (kind::tf32),
-// both K-major, M = 128, N = 128; bit 13 negates A.
-template <bool TF32>
+// Instruction descriptor: D FP32, A and B of one format (FMT: 0 FP16 or
+// 1 BF16 under kind::f16, 2 TF32 under kind::tf32), both K-major, M = 128,
+// N = 128; bit 13 negates A.
+template <uint32_t FMT>
 constexpr uint32_t idesc_mma(bool neg_a) {
-    return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | ((neg_a ? 1u : 0u) << 13) |
-           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (FMT << 7) | (FMT << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
 }
 
 template <bool TF32>
@@ -207,6 +261,20 @@ __device__ __forceinline__ void split_vec(const float *x, uint4 (&pc)[Kind<KIND>
         }
         pc[0] = make_uint4(h[0], h[1], h[2], h[3]);
         pc[1] = make_uint4(l[0], l[1], l[2], l[3]);
+    } else if constexpr (Kind<KIND>::FP16) {
+        // hi = x rounded to FP16, lo = the remainder rounded to FP16 (the
+        // operands are scaled into FP16's normal range beforehand)
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 hh = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+            const float2 hf = __half22float2(hh);
+            const __half2 ll = __floats2half2_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+            h[i] = *reinterpret_cast<const uint32_t *>(&hh);
+            l[i] = *reinterpret_cast<const uint32_t *>(&ll);
+        }
+        pc[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        pc[1] = make_uint4(l[0], l[1], l[2], l[3]);
     } else {
         float r[8];
 #pragma unroll
@@ -237,7 +305,7 @@ struct Layout {
     int64_t N;
     int n_nt;
     int part_tiles;    // partial-sum tiles reserved for the tail split
-    size_t off_X, off_Y, off_Z, off_k, off_ko, off_A, off_part, off_cnt, total;
+    size_t off_X, off_Y, off_Z, off_k, off_ko, off_kexp, off_tmax, off_A, off_part, off_cnt, total;
 };
 
 using sched::tail_split;
@@ -267,6 +335,10 @@ static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     o = align_up(o + sizeof(int4) * (size_t)L.K_pad, 1024);
     L.off_ko = o;
     o = align_up(o + sizeof(int2) * (size_t)L.K_pad, 1024);
+    L.off_kexp = o;  // FP16 kind: per-k exponent of the W row factor
+    o = align_up(o + sizeof(int) * (size_t)L.K_pad, 1024);
+    L.off_tmax = o;  // FP16 kind: bound of the job's largest term (FP64 bits)
+    o = align_up(o + 256, 1024);
     L.off_A = o;
     o = align_up(o + (size_t)L.n_mt * L.nkc * a_stage, 1024);
     // a split never needs more than 2P partial tiles (R * s <= 2P)
@@ -293,9 +365,11 @@ static Layout make_layout_k(const PairSetDev &ps, int S, int nx, int ny, int nz)
 // two doubles), so the FP32 sine and cosine of the remainder and the FP32
 // exponential are as accurate as the FP32 table entries; the powers of i q
 // are applied in FP64.
+// With Q >= 0 (FP16 kind) every row u is multiplied by 2^(kRowExp - e_u),
+// e_u = axis_row_exp(u, 1/(4p), Q) with Q >= max |q_i| of the axis.
 __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict__ geom,
                                         const double *__restrict__ qaxis, int n, int axis, int64_t n_axrows,
-                                        float2 *__restrict__ table) {
+                                        float2 *__restrict__ table, double Q) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ((int64_t)ps.n_pair + 1) * n) return;
     const int pr = (int)(idx / n);
@@ -318,7 +392,8 @@ __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict_
     const double g = (double)expf((float)(-q * q * inv4p));
     double re = (double)cf * g, im = (double)sf * g;
     for (int u = 0; u <= L; ++u) {
-        table[(row0 + u) * n + i] = make_float2((float)re, (float)im);
+        const double f = Q >= 0.0 ? ldexp(1.0, kRowExp - axis_row_exp(u, inv4p, Q)) : 1.0;
+        table[(row0 + u) * n + i] = make_float2((float)(re * f), (float)(im * f));
         // times i q
         const double nr = -q * im, ni = q * re;
         re = nr;
@@ -356,6 +431,43 @@ __global__ void kindex_kernel(PairSetDev ps, int64_t K_pad, int64_t n_axrows, in
     kofs[k] = make_int2((r.w + r.y) * ny, (r.w + r.z) * nz);  // Y and Z row offsets of this k
 }
 
+// FP16 kind: per k = (pair, v, w), kexp[k] = e_v(Y) + e_w(Z), the exponent
+// of the factor 2^(2 kRowExp - kexp) that the scaled tables put on W row k,
+// and a bound of the term of k over the grid,
+//   t_k = max_s sum_u |D^s_{pair,uvw}| 2^(e_u(X)) * 2^kexp >= |A[(s,ix),k] W[k,n]|,
+// whose maximum over k (FP64 bits; positive doubles order as integers) sets
+// the job exponent (fp16_job_exp).
+__global__ void fp16_bound_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int S,
+                                  const double *__restrict__ geom, const int4 *__restrict__ kinfo, int64_t K_pad,
+                                  double Qx, double Qy, double Qz, int *__restrict__ kexp,
+                                  unsigned long long *__restrict__ tmax) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K_pad) return;
+    const int4 ki = kinfo[k];
+    if (ki.x < 0) {
+        kexp[k] = 0;
+        return;
+    }
+    int L = 0;
+    while (L < kMaxPairL && ki.x >= ps.pair_off[L + 1]) ++L;
+    const double inv4p = geom[4 * ki.x + 3];
+    const int e = axis_row_exp(ki.y, inv4p, Qy) + axis_row_exp(ki.z, inv4p, Qz);
+    kexp[k] = e;
+    const int nu = L - ki.y - ki.z + 1;
+    float xb[kMaxPairL + 1];
+    for (int u = 0; u < nu; ++u) xb[u] = ldexpf(1.f, axis_row_exp(u, inv4p, Qx));
+    const int64_t rowbase = ps.row_off[L] + (int64_t)(ki.x - ps.pair_off[L]) * mono_count(L);
+    float best = 0.f;
+    for (int s = 0; s < S; ++s) {
+        const float *cs = coef32 + ((size_t)(s / SB) * ps.n_rows) * SB + (s % SB);
+        float sum = 0.f;
+        for (int u = 0; u < nu; ++u) sum += fabsf(cs[(size_t)(rowbase + mono_index(u, ki.y, ki.z)) * SB]) * xb[u];
+        best = fmaxf(best, sum);
+    }
+    const double t = ldexp((double)best, e);
+    if (t > 0.0) atomicMax(tmax, (unsigned long long)__double_as_longlong(t));
+}
+
 // Thread index -> (row m, 16-byte vector kv) of a tile image: consecutive
 // threads take the vectors of one chunk row, then the next row of the same
 // chunk, so a warp writes 512 contiguous bytes of each array of the image.
@@ -374,10 +486,13 @@ __device__ __forceinline__ void image_coords(int64_t idx, int nkc, int &m, int64
 // A[(s,ix), k] = sum_u D^s_{pair,(u,v,w)} X_{pair,u}(q_x[ix]), split into pieces
 // and written as the swizzled shared-memory image of each tile.  One thread
 // writes one 16-byte vector (PER_VEC consecutive k) of each array.
+// FP16 kind: column k is multiplied by 2^(kexp[k] - 2 kRowExp + G), G the
+// job exponent (the scaled W row k carries 2^(2 kRowExp - kexp[k])).
 template <int KIND>
 __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int nxr, int nx,
                               const float2 *__restrict__ X, const int4 *__restrict__ kinfo, int64_t K_pad, int nkc,
-                              int M, int M_pad, uint8_t *__restrict__ Abuf) {
+                              int M, int M_pad, uint8_t *__restrict__ Abuf, const int *__restrict__ kexp,
+                              const unsigned long long *__restrict__ tmax) {
     using KD = Kind<KIND>;
     constexpr int V = KD::PER_VEC, BK = KD::BK, NP = KD::NP;
     const int64_t kvn = K_pad / V;
@@ -386,6 +501,8 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
     int m;
     int64_t kv;
     image_coords<KIND>(idx, nkc, m, kv);
+    int G = 0;
+    if constexpr (KD::FP16) G = fp16_job_exp(tmax) - 2 * kRowExp;
     float re[V], im[V];
     const bool mvalid = m < M;
     const int s = mvalid ? m / nxr : 0, ix = mvalid ? m % nxr : 0;  // rows (s, ix < nxr); X has nx columns
@@ -405,6 +522,11 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
                 const float2 x = X[(size_t)(ki.w + u) * nx + ix];
                 ar = fmaf(c, x.x, ar);
                 ai = fmaf(c, x.y, ai);
+            }
+            if constexpr (KD::FP16) {
+                const int sh = kexp[kv * V + e] + G;
+                ar = pow2_scale(ar, sh);
+                ai = pow2_scale(ai, sh);
             }
         }
         re[e] = ar;
@@ -571,7 +693,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
         } else if (warp == 1 && lane == 0) {
             // ---------------- MMA issuer: global group gg accumulates into TMEM set gg & 1
-            constexpr uint32_t ID = idesc_mma<TF32>(false), IDN = idesc_mma<TF32>(true);
+            constexpr uint32_t ID = idesc_mma<KD::FMT>(false), IDN = idesc_mma<KD::FMT>(true);
             int gc = 0, gbase = 0;
             for (int idx = blockIdx.x; idx < n_items && !*abort_flag; idx += gridDim.x) {
                 const int nkc = items[idx].w;
@@ -787,6 +909,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (write) {
+                if constexpr (KD::FP16) {
+                    // remove the job factor 2^G of the FP16 kind's scaled A
+                    const int G = fp16_job_exp(J.tmax);
+#pragma unroll
+                    for (int j = 0; j < CQ; ++j) {
+                        acc_re[j] = pow2_scale(acc_re[j], -G);
+                        acc_im[j] = pow2_scale(acc_im[j], -G);
+                    }
+                }
                 const int sidx = m / J.nx, ix = m % J.nx;
                 const int64_t n0 = (int64_t)item.z * BN + colh;
                 float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
@@ -836,18 +967,27 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // ------------------------------------------------------------------ host side
 
-size_t tc_job_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
+// Calls f(std::integral_constant<int, KIND>) for the run-time split kind.
+template <typename F>
+static auto with_kind(int kind, F &&f) {
     switch (kind) {
-    case tc::KIND_BF16X2: return tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz).total;
-    case tc::KIND_BF16X3: return tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz).total;
-    default: return tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz).total;
+    case tc::KIND_BF16X2: return f(std::integral_constant<int, tc::KIND_BF16X2>{});
+    case tc::KIND_BF16X3: return f(std::integral_constant<int, tc::KIND_BF16X3>{});
+    case tc::KIND_FP16X2: return f(std::integral_constant<int, tc::KIND_FP16X2>{});
+    default: return f(std::integral_constant<int, tc::KIND_TF32X2>{});
     }
 }
 
+static tc::Layout layout_of(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
+    return with_kind(kind, [&](auto K) { return tc::make_layout_k<decltype(K)::value>(ps, S, nx, ny, nz); });
+}
+
+size_t tc_job_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
+    return layout_of(ps, S, nx, ny, nz, kind).total;
+}
+
 size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
-    const tc::Layout L = kind == tc::KIND_BF16X2   ? tc::make_layout_k<tc::KIND_BF16X2>(ps, S, nx, ny, nz)
-                         : kind == tc::KIND_BF16X3 ? tc::make_layout_k<tc::KIND_BF16X3>(ps, S, nx, ny, nz)
-                                                   : tc::make_layout_k<tc::KIND_TF32X2>(ps, S, nx, ny, nz);
+    const tc::Layout L = layout_of(ps, S, nx, ny, nz, kind);
     // descriptors (one per band) and work items: the tiles plus at most 2P
     // parts of the tail split per band
     return L.total + 1024 + 256 + (sizeof(TcJobDev) * kMaxBands + 255) / 256 * 256 +
@@ -898,6 +1038,7 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->cnt = reinterpret_cast<int *>(w + L.off_cnt);
     jd->nsplit = sp;
     jd->split_tiles = sp ? R : 0;
+    jd->tmax = Kind<KIND>::FP16 ? reinterpret_cast<const unsigned long long *>(w + L.off_tmax) : nullptr;
 }
 
 // Tables, k-index and the A image of one job in `ws` (tc_job_bytes bytes).
@@ -919,15 +1060,27 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
     const int na[3] = {a.nx, a.ny, a.nz};
     for (int ax = 0; ax < 3; ++ax) {
         const int64_t tot = ((int64_t)ps.n_pair + 1) * na[ax];
+        // FP16 kind: the Y and Z rows are scaled (X only enters A in FP32)
+        const double Q = KD::FP16 && ax > 0 ? a.qabs[ax] : -1.0;
         axis_power_table_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, a.pair_geom, qa[ax], na[ax], ax,
-                                                                               L.n_axrows, tab[ax]);
+                                                                               L.n_axrows, tab[ax], Q);
     }
     int2 *kofs = reinterpret_cast<int2 *>(w + L.off_ko);
     kindex_kernel<<<(unsigned)((L.K_pad + 255) / 256), 256, 0, st>>>(ps, L.K_pad, L.n_axrows, a.ny, a.nz, kinfo, kofs);
+    int *kexp = reinterpret_cast<int *>(w + L.off_kexp);
+    unsigned long long *tmax = reinterpret_cast<unsigned long long *>(w + L.off_tmax);
+    if constexpr (KD::FP16) {
+        cudaError_t e = cudaMemsetAsync(tmax, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        fp16_bound_kernel<<<(unsigned)((L.K_pad + 255) / 256), 256, 0, st>>>(
+            ps, a.coef32, a.SB, a.S, a.pair_geom, kinfo, L.K_pad, a.qabs[0], a.qabs[1], a.qabs[2], kexp, tmax);
+        if (launches) *launches += 1;
+    }
     {
         const int64_t tot = (int64_t)L.M_pad * (L.K_pad / KD::PER_VEC);
         abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-            ps, a.coef32, a.SB, a.half ? (a.nx + 1) / 2 : a.nx, a.nx, X, kinfo, L.K_pad, L.nkc, L.M, L.M_pad, Abuf);
+            ps, a.coef32, a.SB, a.half ? (a.nx + 1) / 2 : a.nx, a.nx, X, kinfo, L.K_pad, L.nkc, L.M, L.M_pad, Abuf,
+            kexp, tmax);
     }
     if (launches) *launches += 5;
     cudaError_t e = cudaMemsetAsync(w + L.off_cnt, 0, sizeof(int) * 8 * (size_t)L.part_tiles, st);
@@ -937,19 +1090,11 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
 }
 
 void tc_job_desc(const TcArgs &a, void *ws, TcJobDev *jd) {
-    switch (a.kind) {
-    case tc::KIND_BF16X2: job_desc_t<tc::KIND_BF16X2>(a, ws, jd); break;
-    case tc::KIND_BF16X3: job_desc_t<tc::KIND_BF16X3>(a, ws, jd); break;
-    default: job_desc_t<tc::KIND_TF32X2>(a, ws, jd); break;
-    }
+    with_kind(a.kind, [&](auto K) { job_desc_t<decltype(K)::value>(a, ws, jd); });
 }
 
 cudaError_t tc_prep_job(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *launches, cudaStream_t st) {
-    switch (a.kind) {
-    case tc::KIND_BF16X2: return prep_job_t<tc::KIND_BF16X2>(a, ws, jd, launches, st);
-    case tc::KIND_BF16X3: return prep_job_t<tc::KIND_BF16X3>(a, ws, jd, launches, st);
-    default: return prep_job_t<tc::KIND_TF32X2>(a, ws, jd, launches, st);
-    }
+    return with_kind(a.kind, [&](auto K) { return prep_job_t<decltype(K)::value>(a, ws, jd, launches, st); });
 }
 
 // Items of the tiles (mt, nt) of descriptor j, in the given order; the last
@@ -1026,13 +1171,29 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
 
 cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
                                  int *err, int grid_ctas, int64_t *launches, cudaStream_t st, int *progress) {
-    switch (kind) {
-    case tc::KIND_BF16X2:
-        return persistent_t<tc::KIND_BF16X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress);
-    case tc::KIND_BF16X3:
-        return persistent_t<tc::KIND_BF16X3>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress);
-    default:
-        return persistent_t<tc::KIND_TF32X2>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress);
+    return with_kind(kind, [&](auto K) {
+        return persistent_t<decltype(K)::value>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
+                                                progress);
+    });
+}
+
+int tc_kind_of_precision(int precision) {
+    switch (precision) {
+    case SCFF_BF16X2: return tc::KIND_BF16X2;
+    case SCFF_BF16X3: return tc::KIND_BF16X3;
+    case SCFF_TF32X3: return tc::KIND_TF32X2;
+    case SCFF_FP16X2: return tc::KIND_FP16X2;
+    default: return -1;
+    }
+}
+
+void tc_axes_abs_max(const double *qx, int nx, const double *qy, int ny, const double *qz, int nz, double out[3]) {
+    const double *q[3] = {qx, qy, qz};
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        double m = 0.0;
+        for (int i = 0; i < n[a]; ++i) m = std::max(m, fabs(q[a][i]));
+        out[a] = m;
     }
 }
 

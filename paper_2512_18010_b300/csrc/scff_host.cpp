@@ -668,7 +668,7 @@ static size_t ff_footprint(const PairSetDev &ps, const scff_qgrid_s *g, int S, i
     const int S_pad = (S + ch.SB - 1) / ch.SB * ch.SB;
     size_t foot = (size_t)S_pad * ps.n_rows * rsz + (size_t)ps.n_pair * 4 * sizeof(double) + 64;
     if (ch.use_tc) {
-        const int kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+        const int kind = tc_kind_of_precision(precision);
         foot += tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz, kind);
     } else if (g->product) {
         foot += (size_t)ps.n_pair * (g->nx + g->ny + g->nz) * 2 * rsz;
@@ -705,7 +705,7 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
     CUDA_TRY(launch_pairprep(ps, t->d_T, S, SB, S_pad, fp64 ? (double *)c->coef.p : nullptr,
                              fp64 ? nullptr : (float *)c->coef.p, &c->launches, st));
     if (ch.use_tc) {
-        const int kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+        const int kind = tc_kind_of_precision(precision);
         const size_t tc_bytes = tc_workspace_bytes(ps, S, g->nx, g->ny, g->nz, kind);
         TcArgs ta;
         memset(&ta, 0, sizeof(ta));
@@ -729,6 +729,7 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         ta.ws_bytes = c->tc_ws.cap;
         ta.ev_mark = c->timing ? c->ev[1] : nullptr;
         ta.kind = kind;
+        tc_axes_abs_max(g->hx.data(), g->nx, g->hy.data(), g->ny, g->hz.data(), g->nz, ta.qabs);
         ta.drain_every = ch.drain;
         ta.half = grid_half(c, g);
         int used = 1;
@@ -1068,7 +1069,7 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     if (!g || std::find(c->grids.begin(), c->grids.end(), g) == c->grids.end())
         return fail(SCFF_ERR_NOT_FOUND, "scff_form_factor: unknown q-grid handle");
     if (t->basis != b) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: transitions belong to another basis");
-    if (precision < SCFF_FP64 || precision > SCFF_BF16X2)
+    if (precision < SCFF_FP64 || precision > SCFF_FP16X2)
         return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: precision %d", precision);
     if (!f_out) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: f_out is NULL");
     if (!isfinite(scale)) return fail(SCFF_ERR_INVALID_ARG, "scff_form_factor: scale is not finite");
@@ -1078,7 +1079,7 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const int64_t nq = g->n;
     const bool fp64 = precision == SCFF_FP64;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
-    const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
+    const bool tc_prec = tc_kind_of_precision(precision) >= 0;
     const bool tc_path = tc_prec && g->product;
     int dev_sms = 148;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -1277,16 +1278,16 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: NULL context or output");
     *out = nullptr;
     if (n_jobs <= 0 || !jobs) return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: no jobs");
-    if (precision < SCFF_FP64 || precision > SCFF_BF16X2)
+    if (precision < SCFF_FP64 || precision > SCFF_FP16X2)
         return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: precision %d", precision);
     cudaSetDevice(c->device);
-    const bool tc_prec = precision == SCFF_BF16X3 || precision == SCFF_TF32X3 || precision == SCFF_BF16X2;
+    const bool tc_prec = tc_kind_of_precision(precision) >= 0;
     const bool fp64 = precision == SCFF_FP64;
     const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
     scff_plan_s *P = new scff_plan_s();
     P->ctx = c;
     P->precision = precision;
-    P->tc_kind = precision == SCFF_BF16X2 ? 0 : precision == SCFF_BF16X3 ? 1 : 2;
+    P->tc_kind = tc_kind_of_precision(precision);
     P->SB = fp64 ? 4 : 8;
     uint64_t budget = workspace_bytes ? workspace_bytes : std::min<uint64_t>(c->budget, 64ull << 30);
     size_t geom_max = 256, coef_max = 256, tab_max = 256;
@@ -1461,6 +1462,8 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             ta.f2 = (float *)pj.job.f2_out;
             ta.kind = P->tc_kind;
             ta.half = pj.half;
+            tc_axes_abs_max(pj.job.grid->hx.data(), ta.nx, pj.job.grid->hy.data(), ta.ny, pj.job.grid->hz.data(), ta.nz,
+                            ta.qabs);
             CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));
         }
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;

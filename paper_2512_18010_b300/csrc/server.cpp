@@ -159,8 +159,8 @@ struct scff_server_s {
 
 namespace {
 
-bool tc_precision(int p) { return p == SCFF_BF16X3 || p == SCFF_TF32X3 || p == SCFF_BF16X2; }
-int tc_kind_of(int p) { return p == SCFF_BF16X2 ? 0 : p == SCFF_BF16X3 ? 1 : 2; }
+bool tc_precision(int p) { return tc_kind_of_precision(p) >= 0; }
+int tc_kind_of(int p) { return tc_kind_of_precision(p); }
 
 // Device bytes of one job: q axes, tables + A image (tensor cores) or axis
 // tables (direct path), and device outputs when the client's are on the host.
@@ -258,6 +258,8 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             ta.f2 = (float *)f2dev;
             ta.kind = tc_kind_of(sv->precision);
             ta.half = j->half;
+            tc_axes_abs_max(j->ax[0].data(), j->req.nx, j->ax[1].data(), j->req.ny, j->ax[2].data(), j->req.nz,
+                            ta.qabs);
             TcJobDev jd;
             memset(&jd, 0, sizeof(jd));
             if (tc_prep_job(ta, work, &jd, &launches, st) != cudaSuccess) return SCFF_ERR_CUDA;
@@ -454,7 +456,7 @@ extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options
     if (!c || !out) return serr(SCFF_ERR_INVALID_ARG, "scff_server_create: NULL context or output");
     *out = nullptr;
     scff_server_options o = opt ? *opt : scff_server_options{SCFF_TF32X3, 2, 64, 0};
-    if (o.precision < SCFF_FP64 || o.precision > SCFF_BF16X2 || o.slots < 1 || o.slots > 8 || o.max_batch_jobs < 1)
+    if (o.precision < SCFF_FP64 || o.precision > SCFF_FP16X2 || o.slots < 1 || o.slots > 8 || o.max_batch_jobs < 1)
         return serr(SCFF_ERR_INVALID_ARG, "scff_server_create: invalid options");
     cudaSetDevice(c->device);
     scff_server_s *sv = new scff_server_s();

@@ -28,7 +28,8 @@ struct TcArgs {
     void *ws;                  // workspace of tc_workspace_bytes()
     size_t ws_bytes;
     cudaEvent_t ev_mark;       // if set, recorded just before the main kernel
-    int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo
+    int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo, 3: FP16 hi/lo
+    double qabs[3];            // largest |q| of each axis (bounds of the FP16 kind's scaling)
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
     // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
     // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
@@ -79,7 +80,15 @@ struct TcJobDev {
     float2 *part;
     int *cnt;
     int nsplit, split_tiles;
+    // FP16 kind: FP64 bits of the bound of the job's largest term, from which
+    // the job exponent of the scaled A is derived (null for the other kinds)
+    const unsigned long long *tmax;
 };
+
+// Split kind of a tensor-core precision (scff_precision), -1 for the others.
+int tc_kind_of_precision(int precision);
+// Largest |q| of each axis of a product grid, for TcArgs::qabs.
+void tc_axes_abs_max(const double *qx, int nx, const double *qy, int ny, const double *qz, int nz, double out[3]);
 
 // Work item of the persistent kernel (int4):
 //   x = job | (slot + 1) << 16   (slot: part of a split tile, 0 in the high half: whole tile)

@@ -46,7 +46,7 @@ def make_batch(ctx, jobs, prec):
     return specs, handles
 
 
-@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X3, scff.FP32, scff.FP64])
+@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X3, scff.FP16X2, scff.FP32, scff.FP64])
 @pytest.mark.parametrize("split", [False, True])
 def test_batch_equals_alone(ctx, prec, split):
     import torch

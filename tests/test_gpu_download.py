@@ -101,7 +101,7 @@ def test_mirror_with_ragged_columns_runs_unbanded(ctx):
     assert np.array_equal(fh, fd) and np.array_equal(f2h, f2d)
 
 
-@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X2])
+@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X2, scff.FP16X2])
 def test_bands_without_f2_and_other_kinds(ctx, prec):
     job = grid_job(4109, 3, 64, 32, 32)
     ctx.set_download_bands(3)

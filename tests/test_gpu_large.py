@@ -14,7 +14,7 @@ from paper_2512_18010_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5, scff.TF32X3: 1e-5}
+TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5, scff.TF32X3: 1e-5, scff.FP16X2: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +36,7 @@ def large():
     return job, idx, oracle.grid_form_factor(job, idx)
 
 
-@pytest.mark.parametrize("prec", [scff.BF16X3, scff.TF32X3])
+@pytest.mark.parametrize("prec", [scff.BF16X3, scff.TF32X3, scff.FP16X2])
 def test_large_job_tensor_cores(ctx, large, prec):
     job, idx, ref = large
     assert job.mol.nbf == 680 and job.n_states == 32
@@ -54,11 +54,12 @@ def test_large_job_direct_list_path(ctx, large, prec):
     assert rel_err(f, ref) < TOL[prec]
 
 
-def test_largest_batched_molecules(ctx):
+@pytest.mark.parametrize("prec", [scff.BF16X3, scff.FP16X2])
+def test_largest_batched_molecules(ctx, prec):
     # the three largest molecules among the first 64 of the batched distribution
     jobs = sorted((W.config4_job(i) for i in range(64)), key=lambda j: -j.mol.nbf)[:3]
     for k, job in enumerate(jobs):
         idx = W.subset_indices(job.nq, 128, 5995 + k)
         ref = oracle.grid_form_factor(job, idx)
-        f, _ = scff.evaluate_job(ctx, job, precision=scff.BF16X3)
-        assert rel_err(f[:, idx], ref) < TOL[scff.BF16X3], (job.mol.nbf, job.n_states, len(job.qx))
+        f, _ = scff.evaluate_job(ctx, job, precision=prec)
+        assert rel_err(f[:, idx], ref) < TOL[prec], (job.mol.nbf, job.n_states, len(job.qx))

@@ -2,9 +2,9 @@
 
 Error metric (per state): max_q |f_gpu - f_oracle| / max_q |f_oracle| over
 the compared points.  Bars: FP64 1e-10, FP32 1e-6, the 1e-5-grade tensor-core
-splits (BF16 hi/mid/lo, TF32 hi/lo) 1e-5.  The fast BF16 hi/lo split keeps
-three products of two 8-bit pieces, so its per-product error is ~2^-16; it is
-held to its own documented 5e-5 bar.
+splits (BF16 hi/mid/lo, TF32 hi/lo, FP16 hi/lo) 1e-5.  The fast BF16 hi/lo
+split keeps three products of two 8-bit pieces, so its per-product error is
+~2^-16; it is held to its own documented 5e-5 bar.
 """
 import numpy as np
 import pytest
@@ -15,8 +15,9 @@ from paper_2512_18010_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5, scff.TF32X3: 1e-5, scff.BF16X2: 5e-5}
-TC = [scff.BF16X3, scff.TF32X3, scff.BF16X2]
+TOL = {scff.FP64: 1e-10, scff.FP32: 1e-6, scff.BF16X3: 1e-5, scff.TF32X3: 1e-5, scff.BF16X2: 5e-5,
+       scff.FP16X2: 1e-5}
+TC = [scff.BF16X3, scff.TF32X3, scff.BF16X2, scff.FP16X2]
 
 
 @pytest.fixture(scope="module")
@@ -177,6 +178,19 @@ def test_f_shells_grid_sampled(ctx, prec):
     assert np.allclose(f2, np.abs(f) ** 2, rtol=1e-5 if prec else 1e-12, atol=1e-30)
 
 
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.FP16X2])
+def test_f_shells_on_block_shared_rows(ctx, prec):
+    # f-pair classes (degree 5 and 6) on a z axis of 128 points: every 128-point block of the
+    # direct kernels shares (ix, iy), so the f classes run the block-shared-row variant and merge
+    # with the low classes' partial result; an odd x axis ends the Hermitian half inside a block.
+    base = W.config_f(n_heavy=2, n_states=5)
+    job = W.Job(base.mol, base.T, W.axis(7, 12.0), W.axis(5, 9.0), W.axis(128, 14.0), 3510)
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 900, 3511)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", [scff.FP64, scff.FP32])
 def test_f_shells_list_path(ctx, prec):
     job = W.config_f(n_heavy=2, n_states=5)
@@ -187,7 +201,7 @@ def test_f_shells_list_path(ctx, prec):
     assert rel_err(f, ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3, scff.FP16X2])
 def test_f_only_basis(ctx, prec):
     # Every pair has degree 6: only the f-pair classes run.
     rng = np.random.default_rng(36)
@@ -206,7 +220,7 @@ def test_f_only_basis(ctx, prec):
 
 # ---------------------------------------------------------------- pure (spherical-harmonic) d and f shells
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3, scff.TF32X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3, scff.TF32X3, scff.FP16X2])
 def test_pure_shells_grid_sampled(ctx, prec):
     job = W.config_f(pure=W.PURE_D | W.PURE_F)
     assert job.mol.nbf == 104
@@ -255,7 +269,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(ctx):
     assert rel_err(f, oracle.grid_form_factor(job)) < TOL[scff.FP64]
 
 
-@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.FP64, scff.FP32, scff.BF16X3, scff.FP16X2])
 def test_hermitian_half_is_exact_mirror(prec):
     # On an antisymmetric grid the half-evaluated result (default) mirrors
     # f(-q) = conj(f(q)) exactly and agrees with the full evaluation within the

@@ -49,7 +49,7 @@ def alone(ctx, job, prec):
     return out
 
 
-@pytest.mark.parametrize("prec", [scff.TF32X3, scff.FP32])
+@pytest.mark.parametrize("prec", [scff.TF32X3, scff.FP16X2, scff.FP32])
 def test_mixed_stream_equals_alone(ctx, prec):
     import torch
     jobs = small_jobs(14, seed=1)
