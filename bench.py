@@ -43,6 +43,7 @@ FP32_LANES_PER_SM = 128
 N_SM = 148
 SM_MAX_MHZ = 2032.0
 TF32_PER_BF16 = 0.5   # dense TF32 / dense BF16 tensor rate (nominal 1.1 vs 2.25 PFLOP/s)
+TC_PREC_NAMES = ("bf16x3", "tf32x3", "bf16x2", "fp16x2")
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one q-evaluation
@@ -82,7 +83,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="scff", choices=["scff", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16x2", "fp32", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
@@ -235,7 +236,7 @@ def fft_run(ctx, b, t, S, steps, stream, flush, job):
 
 
 def pair_stats(mol):
-    """Pair records, monomial rows K and (v,w) rows of a basis."""
+    """Pair records, monomial rows K, (v,w) rows and s-s pairs (degree 0) of a basis."""
     lmax = {0: 0, 1: 1, 2: 2, 3: 3, -1: 1}
     recs = []
     for l, n in zip(mol.shell_l, mol.shell_nprim):
@@ -245,7 +246,14 @@ def pair_stats(mol):
     Lp = (recs[:, None] + recs[None, :])[iu]
     K = int(np.sum((Lp + 1) * (Lp + 2) * (Lp + 3) // 6))
     Kvw = int(np.sum((Lp + 1) * (Lp + 2) // 2))
-    return len(Lp), K, Kvw
+    return len(Lp), K, Kvw, int(np.sum(Lp == 0))
+
+
+def algorithmic_flops(n_pair: int, K: int, n_ss: int) -> int:
+    """The work the method needs per (q-point x state), the one count every roofline here uses:
+    one multiply-add per pair monomial (2K) and one complex multiply-add of the pair's Gaussian x
+    phase factor with its polynomial (8 per pair), 4 for s-s pairs whose polynomial is real."""
+    return 2 * K + 8 * n_pair - 4 * n_ss
 
 
 class ClockSampler:
@@ -313,7 +321,7 @@ def cpu_model() -> str:
 
 CPU_SEED = 99
 # parity bars of the error metric (per state: max |f - f_oracle| / max |f_oracle| over the points)
-TOLERANCE = {"fp64": 1e-10, "fp32": 1e-6, "bf16x3": 1e-5, "tf32x3": 1e-5, "bf16x2": 5e-5}
+TOLERANCE = {"fp64": 1e-10, "fp32": 1e-6, "bf16x3": 1e-5, "tf32x3": 1e-5, "bf16x2": 5e-5, "fp16x2": 1e-5}
 
 
 def cpu_baseline(job, n_points: int, f_gpu=None, precision=None, seed: int = CPU_SEED):
@@ -403,7 +411,7 @@ def tc_useful(jobs, precision, seconds, scff):
     """Tensor work of a set of jobs on the split-precision path per second: 8 flop per complex
     multiply-add x (pair,v,w) rows x split products, over the rows (s, ix) of the evaluated
     half of each antisymmetric grid, against the measured sustained BF16 rate."""
-    pieces = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3}.get(precision)
+    pieces = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3, scff.FP16X2: 3}.get(precision)
     if pieces is None or seconds <= 0:
         return None
     flops = 0
@@ -542,6 +550,7 @@ def main():
     job, desc = workload(args.workload, rank)
     S, nq = job.n_states, job.nq
     prec = scff.PRECISIONS[args.precision]
+    TC_PRECS = tuple(scff.PRECISIONS[n] for n in TC_PREC_NAMES)
     ctx = scff.Context(local)
     if not args.no_autotune:
         ctx.set_autotune(True)
@@ -573,7 +582,7 @@ def main():
     torch.cuda.synchronize()
     ctx.sync(stream)
     choice = None
-    if prec in (scff.TF32X3, scff.BF16X3, scff.BF16X2) and not args.no_autotune:
+    if prec in TC_PRECS and not args.no_autotune:
         choice = ctx.autotune_choice(b, t, g, prec)
 
     sampler = ClockSampler(local)
@@ -637,41 +646,48 @@ def main():
                "how": "dependent FMA chains, 8 per thread, 64 warps per SM, best of 3 launches after a warm-up"}
 
     # roofline of the dominant kernel (the q-evaluation)
-    n_pair, K, Kvw = pair_stats(job.mol)
+    n_pair, K, Kvw, n_ss = pair_stats(job.mol)
     kern_ms = float(np.mean(qeval_ms))
-    direct_flops = 2 * K + 8 * n_pair           # per (q, state): polynomial + complex phase multiply-add
-    used_tc = prec in (scff.BF16X3, scff.TF32X3, scff.BF16X2) and (choice is None or choice["tensor_cores"])
+    alg_flops = algorithmic_flops(n_pair, K, n_ss)
+    used_tc = prec in TC_PRECS and (choice is None or choice["tensor_cores"])
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     if used_tc:
-        passes = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3}[prec]
+        passes = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3, scff.FP16X2: 3}[prec]
         tc_flops = 8 * Kvw * passes              # executed tensor flops per (q, state)
         measured_peak = "bf16_tflops" in peaks
         bf16 = float(peaks.get("bf16_tflops", 1800.0))  # fallback: one earlier B300 measurement
         peak = bf16 * (TF32_PER_BF16 if prec == scff.TF32X3 else 1.0)
         units_eval = S * nx_rows * len(job.qy) * len(job.qz)
-        achieved = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
+        achieved = alg_flops * units_eval / (kern_ms / 1e3) / 1e12
+        executed = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
         trec = measured_traffic(args.workload, args.precision)
         roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "work": f"{tc_flops} tensor flop per (q*state) = 8 flop x {Kvw} (pair,v,w) rows x {passes} split "
-                        f"products; direct-form algorithmic work is {direct_flops} flop per (q*state)",
+                "work": f"{alg_flops} algorithmic flop per (q*state) = 2K + 8 n_pairs - 4 n_ss with K = {K} "
+                        f"monomial rows, {n_pair} pairs, {n_ss} s-s pairs (the work the method needs), times "
+                        f"{units_eval} evaluated (q*state) units per launch",
+                "executed_tensor_tflops": executed, "executed_frac": executed / peak,
+                "executed_work": f"{tc_flops} tensor flop per (q*state) = 8 flop x {Kvw} (pair,v,w) rows x "
+                                 f"{passes} split products",
                 "peak_source": (("of measured: MEASURED_PEAKS.json bf16_tflops" if measured_peak
                                  else "of fallback: 1.8 PFLOP/s BF16 (MEASURED_PEAKS.json absent)")
-                                + (" x nominal TF32/BF16 ratio 0.5" if prec == scff.TF32X3 else "")),
-                "algorithmic_tflops": direct_flops * units_eval / (kern_ms / 1e3) / 1e12,
+                                + (" x nominal TF32/BF16 ratio 0.5" if prec == scff.TF32X3 else "")
+                                + (" (FP16 and BF16 have the same nominal dense rate)" if prec == scff.FP16X2
+                                   else "")),
                 "evaluated_units_per_launch": units_eval}
     else:
         fp64_path = prec == scff.FP64
         peak = 1.25 if fp64_path else N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         units_eval = S * ((nq + 1) // 2 if half else nq)
-        achieved = direct_flops * units_eval / (kern_ms / 1e3) / 1e12
+        achieved = alg_flops * units_eval / (kern_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "direct_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "work": f"{direct_flops} algorithmic flop per (q*state)",
+                "frac": achieved / peak, "traffic": None,
+                "work": f"{alg_flops} algorithmic flop per (q*state) = 2K + 8 n_pairs - 4 n_ss",
                 "peak_source": "FP64 nominal 1.25 TFLOP/s" if fp64_path else
                 "FP32: 148 SM x 128 lanes x 2 flop x 2032 MHz"}
         if alu:
@@ -772,8 +788,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": {"tf32x3": "tf32x3->f32", "bf16x3": "bf16x3->f32", "bf16x2": "bf16x2->f32", "fp32": "f32",
-                          "fp64": "f64"}[args.precision],
+                "dtype": {"tf32x3": "tf32x3->f32", "bf16x3": "bf16x3->f32", "bf16x2": "bf16x2->f32",
+                          "fp16x2": "fp16x2->f32", "fp32": "f32", "fp64": "f64"}[args.precision],
                 "data": "synthetic (seeded molecules, basis and transition matrices)",
                 "config": {"workload": desc, "precision": args.precision, "n_pairs": n_pair,
                            "monomial_rows": K, "vw_rows": Kvw, "autotune": choice,
