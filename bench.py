@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1],
+                    help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -554,6 +556,7 @@ def main():
     ctx = scff.Context(local)
     if not args.no_autotune:
         ctx.set_autotune(True)
+    ctx.set_tc_zstage(args.zstage)
     b = ctx.basis(job.mol)
     t = ctx.transitions(b, job.T)
     g = ctx.qgrid_product(job.qx, job.qy, job.qz)

@@ -291,6 +291,17 @@ scff_status scff_sync(scff_ctx *ctx, void *stream);
  * the default; longer runs are faster by about 1% only. */
 scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
 
+/* Tensor-core W generator variant (no counterpart in the paper).  On product
+ * grids whose z axis is a multiple of 128 points, every 128-column output
+ * tile lies in one y row, so one warp can stage each k-chunk's Z row slices
+ * (1-D bulk copies) and Y values in shared memory for the generators, instead
+ * of each generator thread gathering its table entries from global memory.
+ * mode: -1 automatic (the default: on where the grid allows it; with the
+ * autotuner on, tuned per job shape), 0 never, 1 wherever the grid allows it.
+ * Both variants form bitwise the same W, so results do not depend on the
+ * choice.  Applies to calls, plans and servers created after it. */
+scff_status scff_set_tc_zstage(scff_ctx *ctx, int mode);
+
 /*
  * Separable integrals (Sec. "Cartesian Grid Method": the one-axis V-tensors
  * alone give integrals of f_S against a product of one-axis functions):
@@ -460,8 +471,9 @@ scff_status scff_screening_info(scff_ctx *ctx, scff_trans_h trans, scff_qgrid_h 
  * use the fastest.  Every candidate meets the requested precision's bar (the
  * drain length is not tuned: the TMEM accumulation error grows linearly with
  * it, see scff_set_tc_drain).
- * scff_autotune_choice: out[0] = 1 tensor cores / 0 direct, out[1] = drain,
- * out[2] = state block, out[3] = best time in microseconds. */
+ * scff_autotune_choice writes five values: out[0] = 1 tensor cores / 0 direct,
+ * out[1] = drain, out[2] = state block, out[3] = best time in microseconds,
+ * out[4] = 1 if the Z-staging W generator variant was chosen. */
 scff_status scff_set_autotune(scff_ctx *ctx, int enable);
 scff_status scff_autotune_choice(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
                                  scff_qgrid_h grid, int precision, int32_t *out);

@@ -112,6 +112,27 @@ template <int KIND> struct Kind {
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
 
+// Launch configuration of the persistent kernel per split kind and W source.
+//   ZS = false: the generators gather their Y and Z table entries from global
+//     memory (any product grid, the spherical method's tables).
+//   ZS = true (two-piece kinds, grids with nz a multiple of 128): every tile
+//     lies in one y row, so a chunk needs one Y value per k (shared by all
+//     tile rows) and one 128-entry slice of a Z row per k; warp 2 stages both
+//     into shared memory one chunk ahead (the slices by 1-D bulk copies), and
+//     the generators read shared memory only.  Two stages then fit beside
+//     the two Z slots.
+template <int KIND, bool ZS> struct Cfg {
+    using KD = Kind<KIND>;
+    static constexpr int STAGES = ZS ? 2 : KD::STAGES;
+    static constexpr int ZSLOT = KD::BK * BN * 8;   // Z row slices of one chunk (float2)
+    static constexpr int YSLOT = KD::BK * 8;        // Y values of one chunk
+    static constexpr int ZBYTES = ZS ? STAGES * (ZSLOT + YSLOT) : 0;
+    static constexpr int KO_BYTES = ZS ? 0 : KD::KO_BYTES;
+    static constexpr int SMEM_BYTES = STAGES * KD::STAGE + 1024 + 256 + KO_BYTES + ZBYTES;
+    static_assert(!ZS || KD::NP == 2, "Z staging is built for the two-piece kinds");
+    static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+};
+
 // Piece orders of the kept products (A piece, W piece).
 __host__ __device__ constexpr int prod_a(int i) { return i == 0 ? 0 : i == 1 ? 0 : i == 2 ? 1 : i == 3 ? 0 : i == 4 ? 2 : 1; }
 __host__ __device__ constexpr int prod_w(int i) { return i == 0 ? 0 : i == 1 ? 1 : i == 2 ? 0 : i == 3 ? 2 : i == 4 ? 0 : 1; }
@@ -293,6 +314,13 @@ __device__ __forceinline__ void split_vec(const float *x, uint4 (&pc)[Kind<KIND>
             pc[q] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
+}
+
+// One element of W: the complex product y z with each rounding explicit, so
+// every generator variant forms bitwise the same value.
+__device__ __forceinline__ void w_elem(float2 a, float2 b, float &re, float &im) {
+    re = __fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y));
+    im = __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x));
 }
 
 // ------------------------------------------------------------------ layout
@@ -628,14 +656,16 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
 // are counted globally across items, so consecutive items pipeline without
 // re-initialisation.  Each tile's reduction order depends only on its own
 // job, never on the rest of the batch.
-template <int KIND>
+template <int KIND, bool ZS>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_persistent_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items,
                          int drain_every, int *err, int *progress) {
     using KD = Kind<KIND>;
+    using CF = Cfg<KIND, ZS>;
     constexpr bool TF32 = KD::TF32;
-    constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = KD::STAGES;
-    constexpr int A_STAGE = KD::A_STAGE, W_STAGE = KD::W_STAGE, STAGE = KD::STAGE;
+    constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = CF::STAGES;
+    constexpr int ZSLOT = CF::ZSLOT, YSLOT = CF::YSLOT;
+    constexpr int A_STAGE = KD::A_STAGE, STAGE = KD::STAGE;
     constexpr int KH = BK / 2;        // k per generator thread (two threads per W row)
     constexpr int KSUB = 8;           // loads in flight per sub-batch
     constexpr int CQ = BN / 2;        // accumulator columns (of Re and of Im) per drain thread
@@ -649,6 +679,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *accEmpty = bars + 3 * STAGES + 2;  // [2] accumulator set drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * STAGES + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3 * STAGES + 5);
+    uint64_t *zfull = bars + 16;                 // [STAGES] (ZS) Z slices landed and Y values stored
+    uint64_t *zempty = bars + 16 + STAGES;       // [STAGES] (ZS) generators done with the Z slot
+    uint8_t *zbase = smem + STAGES * STAGE + 256;  // (ZS) [STAGES][Z slices | Y values]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -661,6 +694,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int j = 0; j < 2; ++j) {
             mbar_init(&accFull[j], 1);
             mbar_init(&accEmpty[j], GEN_WARPS);
+        }
+        if constexpr (ZS) {
+            for (int s = 0; s < STAGES; ++s) {
+                mbar_init(&zfull[s], BK);
+                mbar_init(&zempty[s], GEN_WARPS);
+            }
         }
         *abort_flag = 0;
         fence_mbarrier_init();
@@ -691,6 +730,51 @@ __global__ void __launch_bounds__(THREADS, 1)
                     bulk_g2s(st, Abase + (size_t)it * A_STAGE, A_STAGE, &fullA[s]);
                 }
             }
+            // the copies of the last stages have landed before the CTA may exit
+            // (consumed phases report complete at once; bounded either way)
+            for (int c = max(0, gc - STAGES); c < gc; ++c) mbar_wait(&fullA[c % STAGES], (c / STAGES) & 1);
+        } else if (ZS && warp == 2) {
+            // ---------------- Z/Y stager (ZS): for chunk gc, lane j < BK copies
+            // the tile's 128-entry slice of k's Z row (1 KB, bulk copy) and
+            // stores k's Y value of the tile's y row
+            int gc = 0;
+            bool ok = true;
+            for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+                const int4 item = items[idx];
+                const TcJobDev &J = jobs[item_job(item.x)];
+                const int64_t n0 = (int64_t)item.z * BN;
+                const float2 *Yc = J.Y + (int)(n0 / J.nz);
+                const float2 *Zc = J.Z + (int)(n0 % J.nz);
+                const int2 *kofs = J.kofs + (size_t)item_k0(item.y) * BK;
+                for (int it = 0; it < item.w; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    // the chunk's k-offsets and Y values are read before the
+                    // slot frees, so their latency overlaps the wait
+                    int2 ko = make_int2(0, 0);
+                    float2 y = make_float2(0.f, 0.f);
+                    if (lane < BK) {
+                        ko = __ldg(kofs + (size_t)it * BK + lane);
+                        y = __ldg(Yc + ko.x);
+                    }
+                    const bool w = gc < STAGES || mbar_wait(&zempty[s], ((gc / STAGES) - 1) & 1);
+                    if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *zb = zbase + s * (ZSLOT + YSLOT);
+                    if (lane == 0) mbar_expect_tx(&zfull[s], ZSLOT);
+                    __syncwarp();
+                    if (lane < BK) {
+                        bulk_g2s(zb + lane * (BN * 8), Zc + ko.y, BN * 8, &zfull[s]);
+                        reinterpret_cast<float2 *>(zb + ZSLOT)[lane] = y;
+                        mbar_arrive(&zfull[s]);
+                    }
+                }
+            }
+            if (!ok) *abort_flag = 1;
+            if (lane == 0)
+                for (int c = max(0, gc - STAGES); c < gc; ++c) mbar_wait(&zfull[c % STAGES], (c / STAGES) & 1);
+            __syncwarp();
         } else if (warp == 1 && lane == 0) {
             // ---------------- MMA issuer: global group gg accumulates into TMEM set gg & 1
             constexpr uint32_t ID = idesc_mma<KD::FMT>(false), IDN = idesc_mma<KD::FMT>(true);
@@ -781,7 +865,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                     iy = iy * J.ystride + l;
                 }
             }
-            const float vmask = nvalid ? 1.f : 0.f;
             const float2 *Yc = J.Y + iy;
             const float2 *Zc = J.Z + iz;
             float acc_re[CQ], acc_im[CQ];
@@ -793,25 +876,101 @@ __global__ void __launch_bounds__(THREADS, 1)
             // Row offsets of this warp's k (independent of the A copy, so the
             // gathers below overlap with the TMA instead of following it),
             // staged one chunk ahead by asynchronous copies into shared memory.
-            if constexpr (KD::STAGE_KO) {
+            if constexpr (KD::STAGE_KO && !ZS) {
                 if (lane < KH) cp_async8(kobuf + lane, kofs + lane);
                 cp_async_commit();
             }
             for (int it = 0; it < nkc && ok; ++it, ++gc) {
                 const int s = gc % STAGES;
-                int2 ko[KH];
-                if constexpr (KD::STAGE_KO) {
-                    if (it + 1 < nkc && lane < KH)
-                        cp_async8(kobuf + ((it + 1) & 1) * KH + lane, kofs + (size_t)(it + 1) * BK + lane);
-                    cp_async_commit();
-                    cp_async_wait<1>();  // this chunk's records have landed
+                if constexpr (ZS) {
+                    // W from the staged Z slices and Y values of this chunk
+                    const bool w = mbar_wait(&zfull[s], (gc / STAGES) & 1) &&
+                                   (gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1));
+                    if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const uint8_t *zb = zbase + s * (ZSLOT + YSLOT);
+                    const float2 *zr = reinterpret_cast<const float2 *>(zb) + (size_t)(khalf * KH) * BN + wrow;
+                    const float2 *yv = reinterpret_cast<const float2 *>(zb + ZSLOT) + khalf * KH;
+                    uint8_t *wst = smem + s * STAGE + A_STAGE;
+#pragma unroll
+                    for (int sb = 0; sb < KH; sb += KSUB) {
+                        float2 y[KSUB], z[KSUB];
+#pragma unroll
+                        for (int e = 0; e < KSUB; ++e) {
+                            y[e] = yv[sb + e];
+                            z[e] = zr[(sb + e) * BN];
+                        }
+#pragma unroll
+                        for (int jv = 0; jv < KSUB / V; ++jv) {
+                            float re[V], im[V];
+#pragma unroll
+                            for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
+                            uint4 pr_[NP], pi_[NP];
+                            split_vec<KIND>(re, pr_);
+                            split_vec<KIND>(im, pi_);
+                            const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
+#pragma unroll
+                            for (int q = 0; q < NP; ++q) {
+                                *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
+                                *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
+                            }
+                        }
+                    }
+                    // W visible to the tensor core; the Z slot's reads done
+                    // before the stager's next bulk copy overwrites it
+                    fence_proxy_async_smem();
                     __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&fullW[s]);
+                        mbar_arrive(&zempty[s]);
+                    }
+                } else if constexpr (KD::STAGE_KO) {
+                // all KH table pairs of this chunk are requested at once (the
+                // k-offsets come from this warp's shared-memory buffer, staged
+                // one chunk ahead), before the wait for the stage
+                if (it + 1 < nkc && lane < KH)
+                    cp_async8(kobuf + ((it + 1) & 1) * KH + lane, kofs + (size_t)(it + 1) * BK + lane);
+                cp_async_commit();
+                cp_async_wait<1>();  // this chunk's records have landed
+                __syncwarp();
+                const int2 *kb = kobuf + (it & 1) * KH;
+                float2 y[KH], z[KH];
 #pragma unroll
-                    for (int e = 0; e < KH; ++e) ko[e] = kobuf[(it & 1) * KH + e];
-                } else {
-#pragma unroll
-                    for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
+                for (int e = 0; e < KH; ++e) {
+                    const int2 k2 = kb[e];
+                    y[e] = __ldg(Yc + k2.x);
+                    z[e] = __ldg(Zc + k2.y);
                 }
+                const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
+                if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *wst = smem + s * STAGE + A_STAGE;
+#pragma unroll
+                for (int jv = 0; jv < KH / V; ++jv) {
+                    float re[V], im[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
+                    uint4 pr_[NP], pi_[NP];
+                    split_vec<KIND>(re, pr_);
+                    split_vec<KIND>(im, pi_);
+                    const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + jv * V);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
+                        *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fullW[s]);
+                } else {
+                int2 ko[KH];
+#pragma unroll
+                for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
                 const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
                 if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                     ok = false;
@@ -830,11 +989,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int jv = 0; jv < KSUB / V; ++jv) {
                         float re[V], im[V];
 #pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            const float2 a = y[jv * V + e], b = z[jv * V + e];
-                            re[e] = vmask * (a.x * b.x - a.y * b.y);
-                            im[e] = vmask * (a.x * b.y + a.y * b.x);
-                        }
+                        for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
                         uint4 pr_[NP], pi_[NP];
                         split_vec<KIND>(re, pr_);
                         split_vec<KIND>(im, pi_);
@@ -849,6 +1004,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&fullW[s]);
+                }
                 // Local group gd is complete once the MMAs of its last chunk
                 // are; that is guaranteed STAGES chunks later, so drain it then
                 // without stalling the tensor pipe.
@@ -860,7 +1016,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     ++drained;
                 }
             }
-            if constexpr (KD::STAGE_KO) {
+            if constexpr (KD::STAGE_KO && !ZS) {
                 cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
                 __syncwarp();
             }
@@ -1141,11 +1297,11 @@ static int band_bounds(const TcJobDev &jd, int requested, int grid, int64_t firs
                               kMaxBands, b);
 }
 
-template <int KIND>
+template <int KIND, bool ZS>
 static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
                                 int grid_ctas, int64_t *launches, cudaStream_t st, int *progress) {
     using namespace tc;
-    using KD = Kind<KIND>;
+    using CF = Cfg<KIND, ZS>;
     static bool attr_set = false;
     cudaError_t e;
     if (!attr_set) {
@@ -1153,27 +1309,41 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
         // registers per thread at launch; anything else could leave the
         // increasing warpgroups waiting, so refuse to launch.
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, tc_persistent_kernel<KIND>);
+        e = cudaFuncGetAttributes(&fa, tc_persistent_kernel<KIND, ZS>);
         if (e != cudaSuccess) return e;
         if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
-        e = cudaFuncSetAttribute(tc_persistent_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 KD::SMEM_BYTES);
+        e = cudaFuncSetAttribute(tc_persistent_kernel<KIND, ZS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (n_items <= 0) return cudaSuccess;
     const int grid = std::max(1, std::min(grid_ctas, n_items));
-    tc_persistent_kernel<KIND><<<grid, THREADS, KD::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err,
-                                                                     progress);
+    tc_persistent_kernel<KIND, ZS><<<grid, THREADS, CF::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err,
+                                                                         progress);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
-                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st, int *progress) {
+bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs) {
+    if (kind == tc::KIND_BF16X3 || n_jobs <= 0) return false;
+    for (int j = 0; j < n_jobs; ++j)
+        if (jobs[j].ylm || jobs[j].nz % tc::BN != 0) return false;
+    return true;
+}
+
+cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
+                                 int drain_every, int *err, int grid_ctas, int64_t *launches, cudaStream_t st,
+                                 int *progress) {
     return with_kind(kind, [&](auto K) {
-        return persistent_t<decltype(K)::value>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
+        constexpr int KIND = decltype(K)::value;
+        if constexpr (KIND != tc::KIND_BF16X3) {
+            if (zstage)
+                return persistent_t<KIND, true>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
                                                 progress);
+        }
+        return persistent_t<KIND, false>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
+                                         progress);
     });
 }
 
@@ -1267,8 +1437,8 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
         for (int i = 0; i < grid * tc::GEN_WARPS; ++i) a.progress_host[i] = 0;
     }
     if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
-    e = tc_launch_persistent(a.kind, d_job, d_items, n_items, a.drain_every, a.err, grid, launches, st,
-                             G > 1 ? a.progress_dev : nullptr);
+    e = tc_launch_persistent(a.kind, a.zstage && tc_zstage_ok(a.kind, &jd, 1), d_job, d_items, n_items,
+                             a.drain_every, a.err, grid, launches, st, G > 1 ? a.progress_dev : nullptr);
     if (a.bands_used) *a.bands_used = G;
     if (e != cudaSuccess || G == 1) return e;
     if ((e = cudaEventRecord(a.ev_done, st)) != cudaSuccess) return e;
@@ -1412,8 +1582,8 @@ cudaError_t tc_run_generic_multi(const TcGenericArgs *jobs, int n_jobs, int64_t 
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    return tc_launch_persistent(a0.kind, d_jobs, d_items, (int)items.size(), a0.drain_every, a0.err, tc_num_sms(),
-                                launches, st);
+    return tc_launch_persistent(a0.kind, false, d_jobs, d_items, (int)items.size(), a0.drain_every, a0.err,
+                                tc_num_sms(), launches, st);
 }
 
 cudaError_t tc_run_generic(const TcGenericArgs &a, int64_t *launches, cudaStream_t st) {

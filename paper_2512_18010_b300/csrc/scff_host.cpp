@@ -115,6 +115,13 @@ extern "C" scff_status scff_set_tc_drain(scff_ctx *c, int drain_every) {
     return SCFF_OK;
 }
 
+extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: NULL context");
+    if (mode < -1 || mode > 1) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
+    c->tc_zstage = mode;
+    return SCFF_OK;
+}
+
 extern "C" scff_status scff_set_timing(scff_ctx *c, int enable) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_timing: NULL context");
     c->timing = enable ? 1 : 0;
@@ -731,6 +738,7 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         ta.kind = kind;
         tc_axes_abs_max(g->hx.data(), g->nx, g->hy.data(), g->ny, g->hz.data(), g->nz, ta.qabs);
         ta.drain_every = ch.drain;
+        ta.zstage = ch.zs;
         ta.half = grid_half(c, g);
         int used = 1;
         if (ho && c->bands != 1) {
@@ -818,7 +826,12 @@ static scff_status autotune(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, 
     const size_t rsz = sizeof(float);
     const int S = t->S;
     const int64_t nq = g->n;
-    const std::vector<FFChoice> cand = {{1, 8, 8}, {0, 0, 8}, {0, 0, 12}, {0, 0, 16}};
+    std::vector<FFChoice> cand;
+    // tensor cores with both W generator variants (bitwise the same results) unless the
+    // context fixes one, then the FP32 direct path's state blocks
+    for (int zs : {1, 0})
+        if (c->tc_zstage < 0 || c->tc_zstage == zs) cand.push_back({1, 8, 8, zs});
+    for (int sb : {8, 12, 16}) cand.push_back({0, 0, sb, 0});
     TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
     TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
     cudaEvent_t e0, e1;
@@ -1056,6 +1069,7 @@ extern "C" scff_status scff_autotune_choice(scff_ctx *c, scff_basis_h b, scff_tr
     out[1] = it->second.drain;
     out[2] = it->second.SB;
     out[3] = (int32_t)(1000.0f * c->tune_ms[it->first]);  // microseconds of the best candidate
+    out[4] = it->second.zs;
     return SCFF_OK;
 }
 
@@ -1085,7 +1099,8 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
     const int direct_sb = fp64 ? direct_state_block_fp64(S, grid_half(c, g) ? (nq + 1) / 2 : nq, dev_sms)
                                : direct_state_block(S, false);
-    FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_sb};
+    FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_sb,
+                   c->tc_zstage != 0 ? 1 : 0};
     const PairSetDev *ps = &b->dev;
     if (c->screen_eps > 0 && nq > 0) {
         ScreenedSet *se = nullptr;
@@ -1261,6 +1276,7 @@ struct scff_plan_s {
     std::vector<std::vector<int>> groups;
     std::vector<size_t> group_desc, group_items;  // offsets in dev
     std::vector<int> group_nitems;
+    std::vector<char> group_zs;                   // group runs the Z-staging kernel variant
     void *dev = nullptr;
     size_t dev_bytes = 0;
     size_t off_geom = 0, off_coef = 0, off_tab = 0, off_group = 0;
@@ -1369,6 +1385,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         desc_bytes += up1k(sizeof(TcJobDev) * P->groups[g].size());
         P->group_items.push_back(0);
         P->group_nitems.push_back(0);
+        P->group_zs.push_back(0);
     }
     // work lists need the descriptors (tile counts), which need addresses: allocate first
     size_t items_bytes = 0;
@@ -1412,6 +1429,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         tc_build_items(gdesc[g].data(), (int)gdesc[g].size(), gitems[g]);
         P->group_items[g] = ioff;
         P->group_nitems[g] = (int)gitems[g].size();
+        P->group_zs[g] = c->tc_zstage != 0 && tc_zstage_ok(P->tc_kind, gdesc[g].data(), (int)gdesc[g].size()) ? 1 : 0;
         ioff += up1k(sizeof(int4) * nitems_est[g]);
         cudaError_t e1 = cudaMemcpy(base + P->group_desc[g], gdesc[g].data(), sizeof(TcJobDev) * gdesc[g].size(),
                                     cudaMemcpyHostToDevice);
@@ -1424,7 +1442,8 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         }
     }
     // Kernel attributes are set outside any later stream capture.
-    if (!P->groups.empty()) tc_launch_persistent(P->tc_kind, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
+    for (size_t g = 0; g < P->groups.size(); ++g)
+        tc_launch_persistent(P->tc_kind, P->group_zs[g] != 0, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
     c->plans.push_back(P);
     *out = P;
     return SCFF_OK;
@@ -1467,7 +1486,8 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));
         }
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
-        CUDA_TRY(tc_launch_persistent(P->tc_kind, reinterpret_cast<const TcJobDev *>(base + P->group_desc[g]),
+        CUDA_TRY(tc_launch_persistent(P->tc_kind, P->group_zs[g] != 0,
+                                      reinterpret_cast<const TcJobDev *>(base + P->group_desc[g]),
                                       reinterpret_cast<const int4 *>(base + P->group_items[g]), P->group_nitems[g],
                                       drain, c->d_err, tc_num_sms(), launches, st));
     }

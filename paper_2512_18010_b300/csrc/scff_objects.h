@@ -24,6 +24,7 @@ struct FFChoice {
     int use_tc;
     int drain;  // k-chunks per TMEM accumulation (tensor cores)
     int SB;     // states per block (direct path)
+    int zs = 1; // tensor cores: the Z-staging generator variant where the grid allows it
 };
 
 struct scff_ctx {
@@ -38,6 +39,7 @@ struct scff_ctx {
     // q-evaluation, after the q-evaluation
     int timing = 0;
     int drain_every = -1;  // tensor-core TMEM accumulation length (-1 = default)
+    int tc_zstage = -1;    // Z-staging generator variant: -1 automatic, 0 off, 1 on where the grid allows
     int timed_valid = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<struct scff_basis_s *> bases;

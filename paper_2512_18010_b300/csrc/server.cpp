@@ -307,7 +307,10 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
         if (cudaMemcpyAsync(desc_dev, hs, need, cudaMemcpyHostToDevice, st) != cudaSuccess) return SCFF_ERR_CUDA;
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
         int64_t launches = 0;
-        if (tc_launch_persistent(tc_kind_of(sv->precision), reinterpret_cast<const TcJobDev *>(desc_dev),
+        if (tc_launch_persistent(tc_kind_of(sv->precision),
+                                 c->tc_zstage != 0 &&
+                                     tc_zstage_ok(tc_kind_of(sv->precision), descs.data(), (int)descs.size()),
+                                 reinterpret_cast<const TcJobDev *>(desc_dev),
                                  reinterpret_cast<const int4 *>(desc_dev + up1k(sizeof(TcJobDev) * descs.size())),
                                  (int)items.size(), drain, d_err, tc_num_sms(), &launches, st) != cudaSuccess)
             return SCFF_ERR_CUDA;
@@ -490,7 +493,8 @@ extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options
     }
     // tensor-core kernel attributes are set once, outside the server thread's launches
     if (tc_precision(sv->precision))
-        tc_launch_persistent(tc_kind_of(sv->precision), nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
+        for (bool zs : {false, true})
+            tc_launch_persistent(tc_kind_of(sv->precision), zs, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
     sv->th = std::thread(server_loop, sv);
     *out = sv;
     return SCFF_OK;

@@ -31,6 +31,7 @@ struct TcArgs {
     int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo, 3: FP16 hi/lo
     double qabs[3];            // largest |q| of each axis (bounds of the FP16 kind's scaling)
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
+    int zstage;                // 1: the Z-staging generator variant where the grid allows it
     // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
     // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
     int half;
@@ -116,8 +117,15 @@ int64_t tc_max_items(int64_t tiles);
 // progress (optional, e.g. host-mapped): progress[cta * 8 + w] = items that
 // generator warp w of CTA cta has finished (its outputs written and fenced
 // at system scope before the count); CTA b runs items b, b + grid, ...
-cudaError_t tc_launch_persistent(int kind, const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every,
-                                 int *err, int grid_ctas, int64_t *launches, cudaStream_t st, int *progress = nullptr);
+// zstage: launch the variant whose generators read Z and Y staged in shared
+// memory (tc_zstage_ok of the launch's jobs must hold).  Kernel attributes
+// are set on a call with n_items = 0, before any capture.
+cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
+                                 int drain_every, int *err, int grid_ctas, int64_t *launches, cudaStream_t st,
+                                 int *progress = nullptr);
+// Whether every job of a launch can use the Z-staging variant (two-piece
+// kinds, product grids whose nz is a multiple of 128).
+bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs);
 int tc_num_sms();
 
 // Generic two-table contraction on the tensor cores (the spherical method):

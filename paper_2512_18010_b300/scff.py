@@ -33,7 +33,7 @@ _SYMBOLS = [
     "scff_create", "scff_destroy", "scff_last_error", "scff_basis", "scff_transitions",
     "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
-    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_form_factor_static",
+    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_set_tc_zstage", "scff_form_factor_static",
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
@@ -148,6 +148,8 @@ def load(build_if_missing: bool = True):
     lib.scff_autotune_choice.restype = I32
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
+    lib.scff_set_tc_zstage.argtypes = [P, ctypes.c_int]
+    lib.scff_set_tc_zstage.restype = I32
     lib.scff_set_download_bands.argtypes = [P, ctypes.c_int]
     lib.scff_alu_peak.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.scff_alu_peak.restype = I32
@@ -435,6 +437,11 @@ class Context:
         """k-chunks per tensor-core TMEM accumulation (0 = whole K, -1 = default)."""
         _check(self.lib.scff_set_tc_drain(self.h, int(drain_every)))
 
+    def set_tc_zstage(self, mode: int):
+        """Tensor-core W generator variant: -1 automatic, 0 gather from global memory, 1 stage Z and Y
+        in shared memory where the grid allows it (bitwise the same results)."""
+        _check(self.lib.scff_set_tc_zstage(self.h, int(mode)))
+
     def separable_integral(self, basis: Basis, trans: Transitions, qx, wx, qy, wy, qz, wz,
                            scale: float = 1.0) -> np.ndarray:
         """I_s = scale * sum wx(qx) wy(qy) wz(qz) f_s(q) over the product grid, as complex [S]."""
@@ -582,11 +589,11 @@ class Context:
     def autotune_choice(self, basis: Basis, trans: Transitions, grid: QGrid, precision=TF32X3) -> dict:
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        out = np.zeros(4, dtype=np.int32)
+        out = np.zeros(5, dtype=np.int32)
         _check(self.lib.scff_autotune_choice(self.h, basis.handle, trans.handle, grid.handle, int(precision),
                                              _p(out)))
         return {"tensor_cores": bool(out[0]), "drain": int(out[1]), "state_block": int(out[2]),
-                "best_us": int(out[3])}
+                "best_us": int(out[3]), "zstage": int(out[4])}
 
     def set_timing(self, enable: bool = True):
         _check(self.lib.scff_set_timing(self.h, 1 if enable else 0))

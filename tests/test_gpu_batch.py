@@ -93,6 +93,35 @@ def test_batch_equals_alone(ctx, prec, split):
     plan.release()
 
 
+@pytest.mark.parametrize("prec", [scff.FP16X2, scff.TF32X3, scff.BF16X2])
+def test_zstaged_batch_equals_alone(ctx, prec):
+    # every job's z axis is a multiple of 128, so the group runs the variant whose generators
+    # read Z and Y staged in shared memory; odd and even x, ny not a multiple of anything
+    import torch
+    m1 = W.molecule_dz_d(4101, 3)
+    m2 = W.molecule_pol_f(4102, 2)
+    jobs = [W.Job(m1, W.transition_matrices(4101, 5, m1.nbf), W.axis(7, 12.0), W.axis(5, 9.0), W.axis(128, 14.0)),
+            W.Job(m2, W.transition_matrices(4102, 3, m2.nbf), W.axis(10, 8.0), W.axis(3, 11.0), W.axis(256, 16.0)),
+            W.Job(m1, W.transition_matrices(4103, 9, m1.nbf), W.axis(4, 20.0), W.axis(9, 20.0), W.axis(128, 20.0))]
+    specs, handles = make_batch(ctx, jobs, prec)
+    plan = ctx.plan(specs, precision=prec)
+    stream = torch.cuda.Stream()
+    plan.run_graph(stream)
+    stream.synchronize()
+    ctx.sync(stream)
+    tol = 5e-5 if prec == scff.BF16X2 else 1e-5
+    for (b, t, g), s, job in zip(handles, specs, jobs):
+        fa, f2a = ctx.form_factor(b, t, g, precision=prec, scale=s[5], f_out="cuda")
+        ctx.sync()
+        assert torch.equal(fa, s[3]) and torch.equal(f2a, s[4])
+        idx = W.subset_indices(job.nq, 400, 11)
+        ref = oracle.grid_form_factor(job, idx, scale=s[5])
+        fc = s[3].cpu().numpy()
+        fc = fc[..., 0] + 1j * fc[..., 1]
+        assert np.max(np.abs(fc[:, idx] - ref)) / np.max(np.abs(ref)) < tol
+    plan.release()
+
+
 def test_admission_rejects_oversize_job(ctx):
     import torch
     job = W.config3()
