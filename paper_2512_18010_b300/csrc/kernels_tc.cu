@@ -60,6 +60,8 @@ constexpr int W_ARR = BN * ROW_BYTES;                // bytes of one W array
 constexpr int GEN_WARPS = 8;                         // W generators and accumulator drains
 constexpr int THREADS = 128 + GEN_WARPS * 32;        // warpgroup 0: TMA warp, MMA warp, 2 idle
 constexpr int TMEM_COLS = 512;                       // two sets of (Re, Im) x 128 columns
+constexpr int BAR_BYTES = 512;                       // mbarriers, TMEM slot, abort flag, item ring
+constexpr int IRING = 4;                             // work items published ahead to the roles
 // Register split between warpgroups (setmaxnreg): the launch provides
 // THREADS x LAUNCH_REGS registers; warpgroup 0 keeps LOW_REGS per thread and
 // the two generator warpgroups take HIGH_REGS.  The shares add up to the
@@ -98,9 +100,16 @@ template <int KIND> struct Kind {
     static constexpr int BK = ROW_BYTES / ELEM;                      // k per chunk
     static constexpr int PER_VEC = 16 / ELEM;                        // elements per 16-byte vector
     static constexpr int A_STAGE = 2 * NP * A_ARR;                   // re pieces, then im pieces
-    static constexpr int W_STAGE = 2 * NP * W_ARR;
+    // FUSE (two-piece kinds): each W piece is stored as three adjacent
+    // 128-row arrays [-Wi | Wr | Wi], so one N = 256 MMA with B = rows
+    // [Wr; Wi] adds [Ar Wr | Ar Wi] and one with B = [-Wi; Wr] adds
+    // [-Ai Wi | Ai Wr] to the [Re | Im] accumulator: half the MMA
+    // instructions of four N = 128 products, and a quarter fewer operand
+    // bytes read from shared memory.  Otherwise the pieces are [Wr... | Wi...].
+    static constexpr bool FUSE = NP == 2;
+    static constexpr int W_STAGE = (FUSE ? 3 : 2) * NP * W_ARR;
     static constexpr int STAGE = A_STAGE + W_STAGE;
-    static constexpr int STAGES = NP == 3 ? 2 : 3;
+    static constexpr int STAGES = 2;
     // stages, then the barriers (256 B), then each generator warp's two
     // k-offset buffers (KO_BYTES).  Staging the k-offsets through shared
     // memory pays where the generators set the pace (BF16 hi/lo: -8%); where
@@ -108,7 +117,7 @@ template <int KIND> struct Kind {
     // them straight from global memory.
     static constexpr bool STAGE_KO = KIND == KIND_BF16X2 || KIND == KIND_FP16X2;
     static constexpr int KO_BYTES = STAGE_KO ? GEN_WARPS * 2 * (BK / 2) * 8 : 0;
-    static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + 256 + KO_BYTES;
+    static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + BAR_BYTES + KO_BYTES;
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
 
@@ -126,9 +135,12 @@ template <int KIND, bool ZS> struct Cfg {
     static constexpr int STAGES = ZS ? 2 : KD::STAGES;
     static constexpr int ZSLOT = KD::BK * BN * 8;   // Z row slices of one chunk (float2)
     static constexpr int YSLOT = KD::BK * 8;        // Y values of one chunk
-    static constexpr int ZBYTES = ZS ? STAGES * (ZSLOT + YSLOT) : 0;
+    // Z slots: three (the stager two chunks ahead) where shared memory allows
+    static constexpr int ZSLOTS =
+        STAGES * KD::STAGE + 1024 + BAR_BYTES + 3 * (ZSLOT + YSLOT) <= 232448 ? 3 : 2;
+    static constexpr int ZBYTES = ZS ? ZSLOTS * (ZSLOT + YSLOT) : 0;
     static constexpr int KO_BYTES = ZS ? 0 : KD::KO_BYTES;
-    static constexpr int SMEM_BYTES = STAGES * KD::STAGE + 1024 + 256 + KO_BYTES + ZBYTES;
+    static constexpr int SMEM_BYTES = STAGES * KD::STAGE + 1024 + BAR_BYTES + KO_BYTES + ZBYTES;
     static_assert(!ZS || KD::NP == 2, "Z staging is built for the two-piece kinds");
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
@@ -205,10 +217,34 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
 // Instruction descriptor: D FP32, A and B of one format (FMT: 0 FP16 or
 // 1 BF16 under kind::f16, 2 TF32 under kind::tf32), both K-major, M = 128,
 // N = 128; bit 13 negates A.
-template <uint32_t FMT>
+template <uint32_t FMT, int N = BN>
 constexpr uint32_t idesc_mma(bool neg_a) {
-    return (1u << 4) | (FMT << 7) | (FMT << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) |
+    return (1u << 4) | (FMT << 7) | (FMT << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(BM >> 4) << 24);
+}
+
+// Stores one 16-byte vector of W pieces (real pr, imaginary pi) at byte
+// offset off of every array of a W stage, in the kind's layout.
+template <int KIND>
+__device__ __forceinline__ void store_w(uint8_t *wst, uint32_t off, const uint4 (&pr)[Kind<KIND>::NP],
+                                        const uint4 (&pi)[Kind<KIND>::NP]) {
+    using KD = Kind<KIND>;
+    constexpr int NP = KD::NP;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        if constexpr (KD::FUSE) {
+            // sign bits of the pieces: 16-bit elements in pairs, TF32 one per word
+            constexpr uint32_t SGN = KD::TF32 ? 0x80000000u : 0x80008000u;
+            const uint4 ni = make_uint4(pi[q].x ^ SGN, pi[q].y ^ SGN, pi[q].z ^ SGN, pi[q].w ^ SGN);
+            uint8_t *pb = wst + q * 3 * W_ARR + off;
+            *reinterpret_cast<uint4 *>(pb) = ni;
+            *reinterpret_cast<uint4 *>(pb + W_ARR) = pr[q];
+            *reinterpret_cast<uint4 *>(pb + 2 * W_ARR) = pi[q];
+        } else {
+            *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr[q];
+            *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi[q];
+        }
+    }
 }
 
 template <bool TF32>
@@ -649,6 +685,30 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
     return true;
 }
 
+// Bounded wait that also gives up once the CTA's abort flag is set.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+// A consumer role's next work item from the item ring (ic = its count of
+// items taken so far): the index, -1 when the CTA has no more, -2 if the wait
+// ran out or the CTA gave up.  Called by a whole warp (lane 0 frees the slot
+// once every lane has read it) or by a single thread (lane 0).  The wait polls
+// the abort flag, so a producer that gave up never leaves a role waiting long.
+__device__ __forceinline__ int ring_take(uint64_t *ifull, uint64_t *iempty, volatile int *iring, int ic,
+                                         volatile int *abort_flag, int lane) {
+    const int r = ic % IRING;
+    const bool got = mbar_wait_abort(&ifull[r], (ic / IRING) & 1, abort_flag);
+    const int idx = got ? iring[r] : -2;
+    __syncwarp(__activemask());
+    if (got && lane == 0) mbar_arrive(&iempty[r]);
+    return idx;
+}
+
 // One CTA per SM walks its share of the work list: items blockIdx.x,
 // blockIdx.x + gridDim.x, ... of a list sorted by cost.  An item is one
 // 128 x 128 output tile of one job; its contraction runs over the job's k
@@ -659,12 +719,12 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
 template <int KIND, bool ZS>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_persistent_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items,
-                         int drain_every, int *err, int *progress) {
+                         int drain_every, int *err, int *progress, int *queue) {
     using KD = Kind<KIND>;
     using CF = Cfg<KIND, ZS>;
     constexpr bool TF32 = KD::TF32;
     constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = CF::STAGES;
-    constexpr int ZSLOT = CF::ZSLOT, YSLOT = CF::YSLOT;
+    constexpr int ZSLOT = CF::ZSLOT, YSLOT = CF::YSLOT, ZSLOTS = CF::ZSLOTS;
     constexpr int A_STAGE = KD::A_STAGE, STAGE = KD::STAGE;
     constexpr int KH = BK / 2;        // k per generator thread (two threads per W row)
     constexpr int KSUB = 8;           // loads in flight per sub-batch
@@ -679,9 +739,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *accEmpty = bars + 3 * STAGES + 2;  // [2] accumulator set drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * STAGES + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 3 * STAGES + 5);
-    uint64_t *zfull = bars + 16;                 // [STAGES] (ZS) Z slices landed and Y values stored
-    uint64_t *zempty = bars + 16 + STAGES;       // [STAGES] (ZS) generators done with the Z slot
-    uint8_t *zbase = smem + STAGES * STAGE + 256;  // (ZS) [STAGES][Z slices | Y values]
+    uint64_t *zfull = bars + 16;                 // [ZSLOTS] (ZS) Z slices landed and Y values stored
+    uint64_t *zempty = bars + 20;                // [ZSLOTS] (ZS) generators done with the Z slot
+    uint8_t *zbase = smem + STAGES * STAGE + BAR_BYTES;  // (ZS) [ZSLOTS][Z slices | Y values]
+    uint64_t *ifull = bars + 24;                 // [IRING] item index published
+    uint64_t *iempty = bars + 28;                // [IRING] every role has read it
+    volatile int *iring = reinterpret_cast<volatile int *>(bars + 32);  // [IRING] item indices (-1: done)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -696,10 +759,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&accEmpty[j], GEN_WARPS);
         }
         if constexpr (ZS) {
-            for (int s = 0; s < STAGES; ++s) {
+            for (int s = 0; s < ZSLOTS; ++s) {
                 mbar_init(&zfull[s], BK);
                 mbar_init(&zempty[s], GEN_WARPS);
             }
+        }
+        for (int r = 0; r < IRING; ++r) {
+            mbar_init(&ifull[r], 1);
+            mbar_init(&iempty[r], 1 + GEN_WARPS + (ZS ? 1 : 0));  // MMA thread, generators, stager
         }
         *abort_flag = 0;
         fence_mbarrier_init();
@@ -714,8 +781,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(LOW_REGS));
         if (warp == 0 && lane == 0) {
             // ---------------- TMA producer: A tile and the chunk's k-index records
+            // It also takes the CTA's work items -- the next index of the
+            // shared queue counter (queue != null: CTAs that finish early take
+            // more items) or item blockIdx.x + ic * gridDim.x -- and publishes
+            // each to the other roles through the item ring (-1: no more).
             int gc = 0;  // global chunk counter
-            for (int idx = blockIdx.x; idx < n_items && !*abort_flag; idx += gridDim.x) {
+            for (int ic = 0;; ++ic) {
+                const int r = ic % IRING;
+                if (ic >= IRING && !mbar_wait_abort(&iempty[r], ((ic / IRING) - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                int idx = queue ? atomicAdd(queue, 1) : blockIdx.x + ic * gridDim.x;
+                if (idx >= n_items || *abort_flag) idx = -1;
+                iring[r] = idx;
+                mbar_arrive(&ifull[r]);
+                if (idx < 0) break;
                 const int4 item = items[idx];
                 const TcJobDev &J = jobs[item_job(item.x)];
                 const uint8_t *Abase = J.A + ((size_t)item_mt(item.y) * J.nkc + item_k0(item.y)) * A_STAGE;
@@ -729,6 +810,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     mbar_arrive_expect_tx(&fullA[s], A_STAGE);
                     bulk_g2s(st, Abase + (size_t)it * A_STAGE, A_STAGE, &fullA[s]);
                 }
+                if (*abort_flag) break;
             }
             // the copies of the last stages have landed before the CTA may exit
             // (consumed phases report complete at once; bounded either way)
@@ -739,7 +821,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             // stores k's Y value of the tile's y row
             int gc = 0;
             bool ok = true;
-            for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+            for (int ic = 0; ok; ++ic) {
+                const int idx = ring_take(ifull, iempty, iring, ic, abort_flag, lane);
+                if (idx == -2) ok = false;
+                if (idx < 0) break;
                 const int4 item = items[idx];
                 const TcJobDev &J = jobs[item_job(item.x)];
                 const int64_t n0 = (int64_t)item.z * BN;
@@ -747,7 +832,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float2 *Zc = J.Z + (int)(n0 % J.nz);
                 const int2 *kofs = J.kofs + (size_t)item_k0(item.y) * BK;
                 for (int it = 0; it < item.w; ++it, ++gc) {
-                    const int s = gc % STAGES;
+                    const int s = gc % ZSLOTS;
                     // the chunk's k-offsets and Y values are read before the
                     // slot frees, so their latency overlaps the wait
                     int2 ko = make_int2(0, 0);
@@ -756,7 +841,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ko = __ldg(kofs + (size_t)it * BK + lane);
                         y = __ldg(Yc + ko.x);
                     }
-                    const bool w = gc < STAGES || mbar_wait(&zempty[s], ((gc / STAGES) - 1) & 1);
+                    const bool w = gc < ZSLOTS || mbar_wait(&zempty[s], ((gc / ZSLOTS) - 1) & 1);
                     if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                         ok = false;
                         break;
@@ -773,13 +858,17 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (!ok) *abort_flag = 1;
             if (lane == 0)
-                for (int c = max(0, gc - STAGES); c < gc; ++c) mbar_wait(&zfull[c % STAGES], (c / STAGES) & 1);
+                for (int c = max(0, gc - ZSLOTS); c < gc; ++c) mbar_wait(&zfull[c % ZSLOTS], (c / ZSLOTS) & 1);
             __syncwarp();
         } else if (warp == 1 && lane == 0) {
             // ---------------- MMA issuer: global group gg accumulates into TMEM set gg & 1
             constexpr uint32_t ID = idesc_mma<KD::FMT>(false), IDN = idesc_mma<KD::FMT>(true);
+            constexpr uint32_t ID2 = idesc_mma<KD::FMT, 2 * BN>(false);  // N = 256: [Re | Im] at once
             int gc = 0, gbase = 0;
-            for (int idx = blockIdx.x; idx < n_items && !*abort_flag; idx += gridDim.x) {
+            for (int ic = 0;; ++ic) {
+                const int idx = ring_take(ifull, iempty, iring, ic, abort_flag, 0);
+                if (idx == -2) *abort_flag = 1;
+                if (idx < 0) break;
                 const int nkc = items[idx].w;
                 const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
                 bool ok = true;
@@ -808,13 +897,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const int qa = prod_a(pq), qw = prod_w(pq);
                             const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
                             const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
-                            const uint64_t wr = smem_desc_sw64(w0 + qw * W_ARR + ko);
-                            const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
                             const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
-                            mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
-                            mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
-                            mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
-                            mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+                            if constexpr (KD::FUSE) {
+                                const uint32_t pb = w0 + qw * 3 * W_ARR + ko;
+                                mma_issue<TF32>(t_re, ar, smem_desc_sw64(pb + W_ARR), ID2, acc);  // += [Ar Wr | Ar Wi]
+                                mma_issue<TF32>(t_re, ai, smem_desc_sw64(pb), ID2, 1);            // += [-Ai Wi | Ai Wr]
+                            } else {
+                                const uint64_t wr = smem_desc_sw64(w0 + qw * W_ARR + ko);
+                                const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
+                                mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
+                                mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
+                                mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
+                                mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+                            }
                         }
                     }
                     mma_commit(&empty[s]);
@@ -841,10 +936,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int colh = ((warp - 4) >> 2) * CQ;
         // (STAGE_KO) this warp's two k-offset buffers (KH records each): the next
         // chunk's records are copied asynchronously while this chunk is generated
-        int2 *kobuf = reinterpret_cast<int2 *>(smem + STAGES * STAGE + 256) + (warp - 4) * 2 * KH;
+        int2 *kobuf = reinterpret_cast<int2 *>(smem + STAGES * STAGE + BAR_BYTES) + (warp - 4) * 2 * KH;
         int gc = 0, gbase = 0, done_items = 0;
         bool ok = true;
-        for (int idx = blockIdx.x; idx < n_items && ok; idx += gridDim.x) {
+        for (int ic = 0; ok; ++ic) {
+            const int idx = ring_take(ifull, iempty, iring, ic, abort_flag, lane);
+            if (idx == -2) ok = false;
+            if (idx < 0) break;
             const int4 item = items[idx];
             const TcJobDev &J = jobs[item_job(item.x)];
             const int nkc = item.w;
@@ -884,13 +982,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int s = gc % STAGES;
                 if constexpr (ZS) {
                     // W from the staged Z slices and Y values of this chunk
-                    const bool w = mbar_wait(&zfull[s], (gc / STAGES) & 1) &&
+                    const int zs = gc % ZSLOTS;
+                    const bool w = mbar_wait(&zfull[zs], (gc / ZSLOTS) & 1) &&
                                    (gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1));
                     if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                         ok = false;
                         break;
                     }
-                    const uint8_t *zb = zbase + s * (ZSLOT + YSLOT);
+                    const uint8_t *zb = zbase + zs * (ZSLOT + YSLOT);
                     const float2 *zr = reinterpret_cast<const float2 *>(zb) + (size_t)(khalf * KH) * BN + wrow;
                     const float2 *yv = reinterpret_cast<const float2 *>(zb + ZSLOT) + khalf * KH;
                     uint8_t *wst = smem + s * STAGE + A_STAGE;
@@ -911,11 +1010,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             split_vec<KIND>(re, pr_);
                             split_vec<KIND>(im, pi_);
                             const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
-#pragma unroll
-                            for (int q = 0; q < NP; ++q) {
-                                *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
-                                *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
-                            }
+                            store_w<KIND>(wst, off, pr_, pi_);
                         }
                     }
                     // W visible to the tensor core; the Z slot's reads done
@@ -924,7 +1019,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     __syncwarp();
                     if (lane == 0) {
                         mbar_arrive(&fullW[s]);
-                        mbar_arrive(&zempty[s]);
+                        mbar_arrive(&zempty[zs]);
                     }
                 } else if constexpr (KD::STAGE_KO) {
                 // all KH table pairs of this chunk are requested at once (the
@@ -958,11 +1053,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     split_vec<KIND>(re, pr_);
                     split_vec<KIND>(im, pi_);
                     const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + jv * V);
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
-                        *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
-                    }
+                    store_w<KIND>(wst, off, pr_, pi_);
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -994,11 +1085,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         split_vec<KIND>(re, pr_);
                         split_vec<KIND>(im, pi_);
                         const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
-#pragma unroll
-                        for (int q = 0; q < NP; ++q) {
-                            *reinterpret_cast<uint4 *>(wst + q * W_ARR + off) = pr_[q];
-                            *reinterpret_cast<uint4 *>(wst + (NP + q) * W_ARR + off) = pi_[q];
-                        }
+                        store_w<KIND>(wst, off, pr_, pi_);
                     }
                 }
                 fence_proxy_async_smem();
@@ -1299,7 +1386,7 @@ static int band_bounds(const TcJobDev &jd, int requested, int grid, int64_t firs
 
 template <int KIND, bool ZS>
 static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
-                                int grid_ctas, int64_t *launches, cudaStream_t st, int *progress) {
+                                int grid_ctas, int64_t *launches, cudaStream_t st, int *progress, int *queue) {
     using namespace tc;
     using CF = Cfg<KIND, ZS>;
     static bool attr_set = false;
@@ -1320,10 +1407,12 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
     if (n_items <= 0) return cudaSuccess;
     const int grid = std::max(1, std::min(grid_ctas, n_items));
     tc_persistent_kernel<KIND, ZS><<<grid, THREADS, CF::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err,
-                                                                         progress);
+                                                                         progress, queue);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
+
+bool tc_zstage_preferred(int kind) { return kind == tc::KIND_TF32X2; }
 
 bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs) {
     if (kind == tc::KIND_BF16X3 || n_jobs <= 0) return false;
@@ -1334,16 +1423,21 @@ bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs) {
 
 cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
                                  int drain_every, int *err, int grid_ctas, int64_t *launches, cudaStream_t st,
-                                 int *progress) {
+                                 int *progress, int *queue) {
+    if (queue && n_items > 0) {
+        // the queue counter starts at zero for every launch (a memset node in a captured graph)
+        const cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
     return with_kind(kind, [&](auto K) {
         constexpr int KIND = decltype(K)::value;
         if constexpr (KIND != tc::KIND_BF16X3) {
             if (zstage)
                 return persistent_t<KIND, true>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
-                                                progress);
+                                                progress, queue);
         }
         return persistent_t<KIND, false>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
-                                         progress);
+                                         progress, queue);
     });
 }
 

@@ -115,6 +115,14 @@ extern "C" scff_status scff_set_tc_drain(scff_ctx *c, int drain_every) {
     return SCFF_OK;
 }
 
+// Whether a call in this precision asks for the Z-staging generator variant
+// (where the grid allows it): the context's mode, or the kind's default.
+int zstage_mode(const scff_ctx *c, int precision) {
+    if (c->tc_zstage >= 0) return c->tc_zstage;
+    const int k = tc_kind_of_precision(precision);
+    return k >= 0 && tc_zstage_preferred(k) ? 1 : 0;
+}
+
 extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: NULL context");
     if (mode < -1 || mode > 1) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
@@ -1100,7 +1108,7 @@ extern "C" scff_status scff_form_factor(scff_ctx *c, scff_basis_h b, scff_trans_
     const int direct_sb = fp64 ? direct_state_block_fp64(S, grid_half(c, g) ? (nq + 1) / 2 : nq, dev_sms)
                                : direct_state_block(S, false);
     FFChoice ch = {tc_path ? 1 : 0, c->drain_every >= 0 ? c->drain_every : 8, tc_path ? 8 : direct_sb,
-                   c->tc_zstage != 0 ? 1 : 0};
+                   zstage_mode(c, precision)};
     const PairSetDev *ps = &b->dev;
     if (c->screen_eps > 0 && nq > 0) {
         ScreenedSet *se = nullptr;
@@ -1277,6 +1285,7 @@ struct scff_plan_s {
     std::vector<size_t> group_desc, group_items;  // offsets in dev
     std::vector<int> group_nitems;
     std::vector<char> group_zs;                   // group runs the Z-staging kernel variant
+    size_t off_queue = 0;                         // device int: the launches' work-queue counter
     void *dev = nullptr;
     size_t dev_bytes = 0;
     size_t off_geom = 0, off_coef = 0, off_tab = 0, off_group = 0;
@@ -1399,7 +1408,8 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         }
         items_bytes += up1k(sizeof(int4) * nitems_est[g]);
     }
-    P->dev_bytes = off_desc + desc_bytes + items_bytes;
+    P->off_queue = off_desc + desc_bytes + items_bytes;  // work-queue counter of the persistent launches
+    P->dev_bytes = P->off_queue + 1024;
     if (cudaMalloc(&P->dev, P->dev_bytes) != cudaSuccess) {
         delete P;
         return fail(SCFF_ERR_OOM, "scff_plan_create: cannot allocate %zu bytes", P->dev_bytes);
@@ -1429,7 +1439,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         tc_build_items(gdesc[g].data(), (int)gdesc[g].size(), gitems[g]);
         P->group_items[g] = ioff;
         P->group_nitems[g] = (int)gitems[g].size();
-        P->group_zs[g] = c->tc_zstage != 0 && tc_zstage_ok(P->tc_kind, gdesc[g].data(), (int)gdesc[g].size()) ? 1 : 0;
+        P->group_zs[g] = zstage_mode(c, precision) && tc_zstage_ok(P->tc_kind, gdesc[g].data(), (int)gdesc[g].size()) ? 1 : 0;
         ioff += up1k(sizeof(int4) * nitems_est[g]);
         cudaError_t e1 = cudaMemcpy(base + P->group_desc[g], gdesc[g].data(), sizeof(TcJobDev) * gdesc[g].size(),
                                     cudaMemcpyHostToDevice);
@@ -1489,7 +1499,8 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
         CUDA_TRY(tc_launch_persistent(P->tc_kind, P->group_zs[g] != 0,
                                       reinterpret_cast<const TcJobDev *>(base + P->group_desc[g]),
                                       reinterpret_cast<const int4 *>(base + P->group_items[g]), P->group_nitems[g],
-                                      drain, c->d_err, tc_num_sms(), launches, st));
+                                      drain, c->d_err, tc_num_sms(), launches, st, nullptr,
+                                      reinterpret_cast<int *>(base + P->off_queue)));
     }
     for (const PlanJob &pj : P->jobs) {
         if (pj.tc) continue;

@@ -116,3 +116,8 @@ struct ScreenedSet {
     scff::PairSetDev dev;  // own pair_rec, everything else shared with the basis
     int kept, total;
 };
+
+// Whether a call in this precision asks for the Z-staging W generator variant
+// of the tensor-core kernel (where the grid allows it): the context's mode,
+// or the split kind's default.
+int zstage_mode(const scff_ctx *c, int precision);

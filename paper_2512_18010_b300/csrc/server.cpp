@@ -308,11 +308,12 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
         int64_t launches = 0;
         if (tc_launch_persistent(tc_kind_of(sv->precision),
-                                 c->tc_zstage != 0 &&
+                                 zstage_mode(c, sv->precision) &&
                                      tc_zstage_ok(tc_kind_of(sv->precision), descs.data(), (int)descs.size()),
                                  reinterpret_cast<const TcJobDev *>(desc_dev),
                                  reinterpret_cast<const int4 *>(desc_dev + up1k(sizeof(TcJobDev) * descs.size())),
-                                 (int)items.size(), drain, d_err, tc_num_sms(), &launches, st) != cudaSuccess)
+                                 (int)items.size(), drain, d_err, tc_num_sms(), &launches, st, nullptr,
+                                 reinterpret_cast<int *>(arena + B->scratch_off + 256)) != cudaSuccess)
             return SCFF_ERR_CUDA;
         c->launches += launches;
     }

@@ -120,12 +120,19 @@ int64_t tc_max_items(int64_t tiles);
 // zstage: launch the variant whose generators read Z and Y staged in shared
 // memory (tc_zstage_ok of the launch's jobs must hold).  Kernel attributes
 // are set on a call with n_items = 0, before any capture.
+// queue (optional, device int): CTAs take their items from this shared counter
+// (reset to zero on `st` before the launch) instead of the static sequence
+// blockIdx.x, blockIdx.x + grid, ...; progress reporting needs the static one.
 cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
                                  int drain_every, int *err, int grid_ctas, int64_t *launches, cudaStream_t st,
-                                 int *progress = nullptr);
+                                 int *progress = nullptr, int *queue = nullptr);
 // Whether every job of a launch can use the Z-staging variant (two-piece
 // kinds, product grids whose nz is a multiple of 128).
 bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs);
+// Whether the automatic mode takes the Z-staging variant for a kind where it
+// can (measured: faster for TF32 hi/lo, slower for the 16-bit kinds, whose
+// wider stages leave room for only two Z slots).
+bool tc_zstage_preferred(int kind);
 int tc_num_sms();
 
 // Generic two-table contraction on the tensor cores (the spherical method):
