@@ -8,12 +8,14 @@ every state, with the |f|^2 epilogue.  Metric: (q-point x state)/s.
 
 Default workload: the 10-heavy-atom molecule (10 heavy + 10 H, double-zeta +
 d basis, 170 Cartesian functions), 12 states, 128^3 grid on [-20, 20] Bohr^-1,
-in the 1e-5-grade split-BF16 tensor-core mode (BF16 hi/mid/lo pieces, six piece products, FP32
-accumulation) with the autotuner on.  Beside
-it the line reports the plain FP64 GPU path on the same job, the end-to-end
-rate through the C ABI with host buffers, the FP64 oracle on the host cores,
-and (unless --no-serving) a serving run: a Poisson stream of jobs drawn from
-the batched-workload distribution plus 5% large jobs, with p50/p99 latency.
+in the 1e-5-grade FP16 hi/lo tensor-core split (three piece products, FP32
+accumulation) with the autotuner on.  Beside it the line reports the BF16
+hi/mid/lo split on the same job, the plain FP64 GPU path, the end-to-end rate
+through the C ABI with host buffers, the FP64 oracle on the host cores, the
+batched workload (256 molecules of 5-30 heavy atoms, 4-24 states, 48^3-96^3
+grids, one plan replayed from a captured graph) and a serving run (a stream of
+200 jobs of that distribution with 5% large jobs, on the split path and on
+the plain FP64 GPU path, with p50/p99 latency).
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank evaluates its own job (weak scaling, no data-path
@@ -83,7 +85,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="scff", choices=["scff", "reference"])
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
+    ap.add_argument("--precision", default="fp16x2", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1],
                     help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y")
@@ -97,14 +99,20 @@ def parse():
                     help="run only the FFT-method measurement and print it (for profiling)")
     ap.add_argument("--only-spherical", action="store_true",
                     help="run only the spherical-method measurement and print it (for profiling)")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the other split precision (BF16 hi/mid/lo beside FP16 hi/lo) on the same job")
     ap.add_argument("--no-full-compare", action="store_true",
                     help="skip the every-point (no Hermitian half) comparison run")
     ap.add_argument("--no-fft", action="store_true",
                     help="skip the FFT-method measurement (128^3 box, FP32)")
     ap.add_argument("--no-spherical", action="store_true",
                     help="skip the spherical-method measurement (l_max 24 on a 100^3 (q, theta, phi) grid)")
-    ap.add_argument("--serving-jobs", type=int, default=40)
-    ap.add_argument("--batch", type=int, default=0, help="also time a batched plan of this many batched-workload jobs")
+    ap.add_argument("--serving-jobs", type=int, default=200,
+                    help="jobs of the serving stream (5%% of them the large job shape)")
+    ap.add_argument("--serving-fp64-jobs", type=int, default=8,
+                    help="regular jobs of the stream the plain FP64 serving arm runs")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="time a batched plan of this many jobs of the batched workload (0 = skip)")
     ap.add_argument("--screen-eps", type=float, default=1e-8,
                     help="also time the job with error-bounded pair screening at this eps (0 = skip)")
     return ap.parse_args()
@@ -353,6 +361,16 @@ def cpu_baseline(job, n_points: int, f_gpu=None, precision=None, seed: int = CPU
     return cpu, parity
 
 
+def sample_parity(job, idx, f_gpu, precision):
+    """Error metric of GPU values f_gpu [S, len(idx)] at grid points idx against the FP64 oracle (part of
+    the CPU-baseline leg)."""
+    import oracle
+    ref = oracle.grid_form_factor(job, idx)
+    err = float(np.max(np.max(np.abs(f_gpu - ref), axis=1) / np.max(np.abs(ref), axis=1)))
+    return {"max_rel_err_vs_oracle": err, "tolerance": TOLERANCE.get(precision),
+            "pass": bool(err < TOLERANCE.get(precision, np.inf))}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -381,8 +399,8 @@ def run_reference(args):
     return 0
 
 
-def _serving_job(i):
-    return W.config5_job(i)
+def _serving_job(i, n):
+    return W.config5_stream_job(i, n)
 
 
 def _batch_job(i):
@@ -431,8 +449,17 @@ def tc_useful(jobs, precision, seconds, scff):
     return out
 
 
-def serving_run(scff, ctx, jobs, precision, rate_factor=0.7):
-    """Saturation throughput, then a Poisson stream at rate_factor x capacity: p50/p99 latency."""
+def serving_run(scff, ctx, jobs, precision, fp64_jobs=8):
+    """The serving stream on the split path and on the plain FP64 GPU path (both through the server).
+
+    Split arm (all jobs): saturation throughput (every job submitted at t = 0), latency on an idle
+    server (each job submitted after the previous one finished: the latency at arrival rates far
+    below capacity, e.g. 0.7 x the FP64 path's capacity), and Poisson arrivals at 0.5, 0.7 and 0.9 x
+    its own capacity.  FP64 arm: the first `fp64_jobs` regular jobs of the same stream at saturation
+    and under Poisson arrivals at 0.7 x its capacity (the split arm is timed on the same jobs), and the
+    large job shape's FP64 service time measured on one z slab of its grid (4 of 128 planes,
+    scaled by the evaluated points); the FP64 rate on the whole stream is estimated from these two
+    measured per-kind rates."""
     import torch
     handles, outs = [], []
     for job in jobs:
@@ -441,47 +468,136 @@ def serving_run(scff, ctx, jobs, precision, rate_factor=0.7):
         handles.append((b, t))
         outs.append((torch.empty((job.n_states, job.nq, 2), device="cuda"),
                      torch.empty((job.n_states, job.nq), device="cuda")))
-    units = sum(j.n_states * j.nq for j in jobs)
+    n = len(jobs)
+    units = [j.n_states * j.nq for j in jobs]
+    large = [i for i, j in enumerate(jobs) if j.mol.heavy >= 40]
+    regular = [i for i in range(n) if i not in large]
 
-    def one_pass(arrivals):
-        srv = scff.Server(ctx, precision=precision, slots=2, max_batch_jobs=16)
+    def one_pass(prec, idxs, arrivals, outs_, sequential=False):
+        srv = scff.Server(ctx, precision=prec, slots=2, max_batch_jobs=16, arena_bytes=48 << 30)
         ids = []
         t0 = time.perf_counter()
-        for job, (b, t), (f, f2), ta in zip(jobs, handles, outs, arrivals):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
+        for k, i in enumerate(idxs):
+            job = jobs[i]
+            if arrivals is not None:
+                dt = arrivals[k] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            (b, t), (f, f2) = handles[i], outs_[i]
             ids.append(srv.submit(b, t, job.qx, job.qy, job.qz, f, f2))
+            if sequential:
+                srv.wait(ids[-1], timeout_s=600)
         for i in ids:
-            srv.wait(i, timeout_s=600)
+            srv.wait(i, timeout_s=900)
         wall = time.perf_counter() - t0
         lat = np.array([srv.times(i)[2] - srv.times(i)[0] for i in ids])
         st = srv.stats()
         srv.close()
         return wall, lat, st
 
-    one_pass([0.0] * len(jobs))                       # warm pass
-    wall_sat, lat_sat, st_sat = one_pass([0.0] * len(jobs))
-    capacity_jobs = len(jobs) / wall_sat
-    rate = rate_factor * capacity_jobs
-    arr = W.poisson_arrivals(len(jobs), rate, seed=5555)
-    wall, lat, st = one_pass(list(arr))
+    def lat_stats(lat):
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "jobs": int(len(lat))}
+
+    all_idx = list(range(n))
+    u_all = sum(units)
+    one_pass(precision, all_idx, None, outs)                       # warm pass
+    wall_sat, lat_sat, st_sat = one_pass(precision, all_idx, None, outs)
+    cap = n / wall_sat
+    wall_seq, lat_seq, _ = one_pass(precision, all_idx, None, outs, sequential=True)
+    sweep = []
+    for rf in (0.5, 0.7, 0.9):
+        arr = W.poisson_arrivals(n, rf * cap, seed=5555)
+        wall, lat, st = one_pass(precision, all_idx, arr, outs)
+        sweep.append({"rate_factor_of_capacity": rf, "rate_jobs_per_s": rf * cap, "value": u_all / wall,
+                      "unit": UNIT, "wall_s": wall, "batches": st["batches"], "max_inflight": st["max_inflight"],
+                      **lat_stats(lat)})
+    # samples of the served results (checked against the oracle in the CPU-baseline leg)
+    samples = []
+    for i in ([large[0]] if large else []) + regular[:2]:
+        job = jobs[i]
+        idx = W.subset_indices(job.nq, 64 if i in large else 128, 7000 + i)
+        fc = outs[i][0][:, torch.from_numpy(idx).cuda()].double().cpu().numpy()
+        samples.append((i, idx, fc[..., 0] + 1j * fc[..., 1]))
+
+    # FP64 arm on the first regular jobs of the same stream, and the split arm on the same jobs
+    reg = regular[:fp64_jobs]
+    outs64 = {i: (torch.empty((jobs[i].n_states, jobs[i].nq, 2), dtype=torch.float64, device="cuda"),
+                  torch.empty((jobs[i].n_states, jobs[i].nq), dtype=torch.float64, device="cuda")) for i in reg}
+    u_reg = sum(units[i] for i in reg)
+    wall64, lat64_sat, _ = one_pass(scff.FP64, reg, None, outs64)
+    cap64 = len(reg) / wall64
+    arr64 = W.poisson_arrivals(len(reg), 0.7 * cap64, seed=6666)
+    wall64p, lat64, st64 = one_pass(scff.FP64, reg, arr64, outs64)
+    wall_r, _, _ = one_pass(precision, reg, None, outs)
+    wall_rp, lat_rp, _ = one_pass(precision, reg, arr64, outs)     # same arrivals as the FP64 arm
+    del outs64
+    # the large job shape in FP64: one z slab (4 of its planes) of the grid, every point evaluated
+    large64 = None
+    if large:
+        jl = jobs[large[0]]
+        b, t = handles[large[0]]
+        nzs = 4
+        gw = ctx.qgrid_product(jl.qx, jl.qy, jl.qz[:1])
+        fw = torch.empty((jl.n_states, gw.n, 2), dtype=torch.float64, device="cuda")
+        ctx.form_factor(b, t, gw, precision=scff.FP64, f_out=fw)     # warm-up on one plane
+        ctx.release(gw)
+        del fw
+        g = ctx.qgrid_product(jl.qx, jl.qy, jl.qz[:nzs])
+        f64 = torch.empty((jl.n_states, g.n, 2), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.form_factor(b, t, g, precision=scff.FP64, f_out=f64)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        ctx.release(g)
+        del f64
+        # the full grid evaluates its Hermitian half: (nq + 1) / 2 points
+        t_full = ts * ((jl.nq + 1) // 2) / (len(jl.qx) * len(jl.qy) * nzs)
+        large64 = {"slab_points": int(len(jl.qx) * len(jl.qy) * nzs), "slab_s": ts, "est_service_s": t_full,
+                   "value": jl.n_states * jl.nq / t_full, "unit": UNIT}
+    rate64_reg = u_reg / wall64
+    est64 = None
+    if large64:
+        t_est = sum(units[i] for i in regular) / rate64_reg + sum(units[i] for i in large) / large64["value"]
+        est64 = {"value": u_all / t_est, "unit": UNIT, "capacity_jobs_per_s": n / t_est,
+                 "what": "FP64 path on the whole stream, estimated from the measured rates on its regular "
+                         "jobs and on the large job shape"}
     for b, _ in handles:
         ctx.release(b)
     return {
-        "jobs": len(jobs), "large_jobs": int(sum(1 for j in jobs if j.mol.heavy >= 40)),
-        "saturation": {"value": units / wall_sat, "unit": UNIT, "wall_s": wall_sat, "batches": st_sat["batches"],
-                       "max_inflight": st_sat["max_inflight"],
-                       "tensor": tc_useful(jobs, precision, wall_sat, scff)},
-        "poisson": {"rate_jobs_per_s": rate, "rate_factor_of_capacity": rate_factor, "value": units / wall,
-                    "unit": UNIT, "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
-                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                    "batches": st["batches"], "max_inflight": st["max_inflight"]},
+        "jobs": n, "large_jobs": len(large), "precision": {v: k for k, v in scff.PRECISIONS.items()}[precision],
+        "split": {
+            "saturation": {"value": u_all / wall_sat, "unit": UNIT, "wall_s": wall_sat, "capacity_jobs_per_s": cap,
+                           "batches": st_sat["batches"], "max_inflight": st_sat["max_inflight"],
+                           "tensor": tc_useful(jobs, precision, wall_sat, scff)},
+            "idle_server": {"what": "each job submitted when the previous one finished: the latency at arrival "
+                                    "rates far below capacity (0.7 x the FP64 path's capacity is "
+                                    f"{100 * 0.7 * (est64['capacity_jobs_per_s'] if est64 else cap64) / cap:.2f}% "
+                                    "of this arm's)", "wall_s": wall_seq, **lat_stats(lat_seq)},
+            "poisson_sweep": sweep,
+        },
+        "fp64": {
+            "jobs": len(reg), "what": f"the first {len(reg)} regular jobs of the stream",
+            "saturation": {"value": rate64_reg, "unit": UNIT, "wall_s": wall64, "capacity_jobs_per_s": cap64},
+            "poisson": {"rate_factor_of_capacity": 0.7, "rate_jobs_per_s": 0.7 * cap64, "value": u_reg / wall64p,
+                        "unit": UNIT, "wall_s": wall64p, **lat_stats(lat64)},
+            "large_job": large64, "stream_estimate": est64,
+        },
+        "same_jobs": {
+            "what": f"the split arm on the FP64 arm's {len(reg)} jobs: saturation, and the FP64 arm's arrivals",
+            "split_value": u_reg / wall_r, "fp64_value": rate64_reg, "speedup": (u_reg / wall_r) / rate64_reg,
+            "split_poisson": lat_stats(lat_rp), "fp64_poisson": lat_stats(lat64),
+        },
+        "_samples": samples,
     }
 
 
-def batch_run(scff, ctx, jobs, precision, steps=2):
+def batch_run(scff, ctx, jobs, precision, steps=3):
+    """The batched workload as one plan (persistent launches over a device work queue, one captured
+    CUDA graph), replayed: ms per batch, rate, and the algorithmic and useful tensor work rates."""
     import torch
+    t0 = time.perf_counter()
     specs = []
     for job in jobs:
         b = ctx.basis(job.mol)
@@ -490,9 +606,12 @@ def batch_run(scff, ctx, jobs, precision, steps=2):
         specs.append((b, t, g, torch.empty((job.n_states, job.nq, 2), device="cuda"),
                       torch.empty((job.n_states, job.nq), device="cuda"), 1.0))
     plan = ctx.plan(specs, precision=precision)
+    t_setup = time.perf_counter() - t0
     stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
     plan.run_graph(stream)               # capture + first replay (warm-up)
     stream.synchronize()
+    t_first = time.perf_counter() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
@@ -502,15 +621,29 @@ def batch_run(scff, ctx, jobs, precision, steps=2):
     ctx.sync(stream)
     ms = e0.elapsed_time(e1) / steps
     units = sum(j.n_states * j.nq for j in jobs)
+    alg = 0.0
+    for j in jobs:
+        n_pair, K, _, n_ss = pair_stats(j.mol)
+        alg += algorithmic_flops(n_pair, K, n_ss) * j.n_states * ((len(j.qx) + 1) // 2) * len(j.qy) * len(j.qz)
+    alg_tf = alg / (ms / 1e3) / 1e12
+    out = {"jobs": len(jobs), "precision": {v: k for k, v in scff.PRECISIONS.items()}[precision],
+           "value": units / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "replays_timed": steps,
+           "algorithmic_tflops": alg_tf, "tensor": tc_useful(jobs, precision, ms / 1e3, scff),
+           "setup_s": t_setup, "capture_and_first_replay_s": t_first,
+           "graph": "one captured CUDA graph per plan, replayed", "schedule": "device work queue (atomic pull)"}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        out["algorithmic_frac_of_measured_sustained"] = alg_tf / float(peaks["bf16_tflops_sustained"])
+    except Exception:
+        pass
     info = plan.info()
+    out.update({"launches_per_run": info["launches_per_run"], "groups": info["groups"], "tiles": info["tiles"],
+                "device_bytes": info["device_bytes"]})
     plan.release()
-    for s in specs:
-        ctx.release(s[2])
-        ctx.release(s[0])
-    return {"jobs": len(jobs), "value": units / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms,
-            "tensor": tc_useful(jobs, precision, ms / 1e3, scff),
-            "launches_per_run": info["launches_per_run"], "groups": info["groups"], "tiles": info["tiles"],
-            "graph": "one captured CUDA graph per plan, replayed"}
+    for sp in specs:
+        ctx.release(sp[2])
+        ctx.release(sp[0])
+    return out
 
 
 def aggregate(ms_local: float, units_local: int, dist=None, device=None):
@@ -538,7 +671,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     serving_jobs = batch_jobs = None
     if rank == 0 and world == 1 and not args.no_serving and args.serving_jobs > 0:
-        serving_jobs = make_jobs(_serving_job, args.serving_jobs)
+        import functools
+        serving_jobs = make_jobs(functools.partial(_serving_job, n=args.serving_jobs), args.serving_jobs)
     if rank == 0 and world == 1 and args.batch > 0:
         batch_jobs = make_jobs(_batch_job, args.batch)
     import torch
@@ -572,7 +706,9 @@ def main():
 
     if args.only_spherical:
         if rank == 0:
-            print(json.dumps({"spherical": spherical_run(ctx, b, t, S, prec, args.steps, stream, flush)}), flush=True)
+            sph_prec = prec if prec in (scff.BF16X3, scff.TF32X3, scff.BF16X2) else scff.BF16X3
+            print(json.dumps({"spherical": spherical_run(ctx, b, t, S, sph_prec, args.steps, stream, flush)}),
+                  flush=True)
         return 0
     if args.only_fft:
         if rank == 0:
@@ -718,6 +854,34 @@ def main():
         no_symmetry = {"value": units / (nm / 1e3), "unit": UNIT, "ms_per_step": nm,
                        "what": "every grid point evaluated (no f(-q) = conj f(q) mirror)"}
 
+    # the same job in the other 1e-5-grade split (BF16 hi/mid/lo beside FP16 hi/lo, and the reverse)
+    side = None
+    side_name = {"fp16x2": "bf16x3", "bf16x3": "fp16x2"}.get(args.precision)
+    if side_name and not args.no_side:
+        sp = scff.PRECISIONS[side_name]
+        for _ in range(2):
+            ctx.form_factor(b, t, g, precision=sp, f_out=f, f2_out=f2, stream=stream)
+        sms, qms = [], []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.form_factor(b, t, g, precision=sp, f_out=f, f2_out=f2, stream=stream)
+            e1.record(stream)
+            qms.append(ctx.last_timing()[0])
+            torch.cuda.synchronize()
+            sms.append(e0.elapsed_time(e1))
+        sm = float(np.mean(sms))
+        kq = float(np.mean(qms))
+        passes_s = {scff.BF16X3: 6, scff.FP16X2: 3}[sp]
+        side = {"precision": side_name, "value": units / (sm / 1e3), "unit": UNIT, "ms_per_step": sm,
+                "qeval_ms": kq, "alg_frac": alg_flops * units_eval / (kq / 1e3) / 1e12 / roof["peak"],
+                "executed_frac": 8 * Kvw * passes_s * units_eval / (kq / 1e3) / 1e12 / roof["peak"]}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            sel = torch.from_numpy(W.subset_indices(nq, args.cpu_sample, CPU_SEED)).to(dev)
+            fc = f.index_select(1, sel).double().cpu().numpy()
+            side["_f"] = fc[..., 0] + 1j * fc[..., 1]
+
     # the same job with error-bounded pair screening (results within eps * max|f| of the exact ones)
     screened = None
     if args.screen_eps > 0 and prec != scff.FP64:
@@ -743,7 +907,10 @@ def main():
     # the spherical method on the same molecule and states (a side measurement)
     spherical = None
     if not args.no_spherical and prec != scff.FP64 and args.workload == "cfg3":
-        spherical = spherical_run(ctx, b, t, S, prec, args.steps, stream, flush)
+        # the spherical method takes the BF16 and TF32 splits (not FP16 hi/lo)
+        sph_prec = prec if prec in (scff.BF16X3, scff.TF32X3, scff.BF16X2) else scff.BF16X3
+        spherical = spherical_run(ctx, b, t, S, sph_prec, args.steps, stream, flush)
+        spherical["precision"] = {v: k for k, v in scff.PRECISIONS.items()}[sph_prec]
 
     fftm = None
     if not args.no_fft and prec != scff.FP64 and args.workload == "cfg3":
@@ -778,14 +945,28 @@ def main():
 
     serving = None
     if serving_jobs:
-        serving = serving_run(scff, ctx, serving_jobs, prec if prec != scff.FP64 else scff.BF16X3)
+        serving = serving_run(scff, ctx, serving_jobs, prec if prec in TC_PRECS else scff.FP16X2,
+                              fp64_jobs=args.serving_fp64_jobs)
+        serving_jobs_keep = serving_jobs
+        torch.cuda.empty_cache()
     batch = None
     if batch_jobs:
-        batch = batch_run(scff, ctx, batch_jobs, prec if prec != scff.FP64 else scff.BF16X3)
+        batch = batch_run(scff, ctx, batch_jobs, prec if prec in TC_PRECS else scff.FP16X2)
 
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, parity = cpu_baseline(job, args.cpu_sample, f_chk, args.precision)
+        if side is not None:
+            side["parity_vs_oracle"] = sample_parity(job, W.subset_indices(nq, args.cpu_sample, CPU_SEED),
+                                                     side.pop("_f"), side["precision"])
+        if serving is not None:
+            serving["served_parity_vs_oracle"] = [
+                {"job": int(i), "nbf": int(serving_jobs_keep[i].mol.nbf),
+                 "states": int(serving_jobs_keep[i].n_states), "points": int(len(idx)),
+                 **sample_parity(serving_jobs_keep[i], idx, fs, serving["precision"])}
+                for i, idx, fs in serving["_samples"]]
+    if serving is not None:
+        serving.pop("_samples", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -800,7 +981,8 @@ def main():
                            "hermitian_half": bool(half),
                            "parallelism": f"dp{world} (one job per rank)"},
                 "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "alu_peaks": alu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "no_symmetry": no_symmetry, "gpu_launches": int(launches),
-                "fp64_gpu_path": fp64, "screened": screened, "serving": serving, "batch": batch, "clocks": clocks,
+                "fp64_gpu_path": fp64, "side_precision": side, "screened": screened, "serving": serving,
+                "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)
     ctx.close()

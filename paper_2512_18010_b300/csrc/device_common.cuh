@@ -12,9 +12,19 @@ namespace scff {
 // Status codes written into the device error word (match scff.h).
 constexpr int kDevErrTimeout = 6;
 
-// Spin limit of every mbarrier wait: try_wait suspends for a hardware-chosen
-// interval per attempt, so this bounds a wait to well under a minute.
+// Limits of every mbarrier wait: at most kWaitLimit attempts and at most
+// kWaitNs nanoseconds of the global timer.  try_wait suspends the thread for
+// a hardware-chosen interval per attempt (measured: tens of microseconds), so
+// the attempt count alone would let a stuck wait last many minutes; the time
+// limit ends it after a few seconds, far above any legitimate wait here.
 constexpr long long kWaitLimit = 1ll << 24;
+constexpr unsigned long long kWaitNs = 4000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 template <typename F, int... I>
 __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
@@ -69,14 +79,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; false after `limit` tries.
+// Bounded wait for the phase of the given parity; false after `limit` tries
+// or kWaitNs nanoseconds, whichever comes first.
 __device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, uint32_t parity, long long limit) {
-    for (long long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1; i < limit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 15) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 
-// Bounded wait for the phase of the given parity; false after kWaitLimit tries.
+// Bounded wait for the phase of the given parity (kWaitLimit tries, kWaitNs).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) { return mbar_wait_n(bar, parity, kWaitLimit); }
 
 // 1-D bulk async copy global -> shared (TMA engine), completion on `bar`.

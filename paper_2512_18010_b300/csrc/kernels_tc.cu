@@ -687,9 +687,11 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
 
 // Bounded wait that also gives up once the CTA's abort flag is set.
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1; i < kWaitLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255) == 255 && *abort_flag) return false;
+        if ((i & 15) == 0 && (*abort_flag || global_ns() - t0 > kWaitNs)) return false;
     }
     return false;
 }

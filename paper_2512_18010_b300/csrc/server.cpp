@@ -371,7 +371,6 @@ void server_loop(scff_server_s *sv) {
             }
         if (slot >= 0 && !sv->pending.empty()) {
             Batch *B = new Batch();
-            size_t scratch = 1024 + sv->stage_bytes;
             size_t geom_max = 0, coef_max = 0;
             bool blocked = false;
             for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)B->jobs.size() < sv->max_batch;) {
@@ -380,22 +379,38 @@ void server_loop(scff_server_s *sv) {
                     it = sv->pending.erase(it);
                     continue;
                 }
-                if (j->footprint + j->scratch_need + scratch > sv->arena.size()) {
+                const PairSetDev &jps = j->req.basis->dev;
+                const size_t jgeom = up1k((size_t)jps.n_pair * 4 * sizeof(double));
+                // the job alone with the batch scratch it needs (the form of sbytes below)
+                if (j->footprint + up1k(1024 + jgeom + j->scratch_need + sv->stage_bytes) > sv->arena.size()) {
                     it = sv->pending.erase(it);
                     finish_job(sv, j, FAILED, SCFF_ERR_ADMISSION);
                     progress = true;
                     continue;
                 }
                 if (blocked) break;
-                size_t off;
-                if (sv->arena.alloc(j->footprint, &off)) {
+                // Admitted only if its block and the batch scratch grown to cover it
+                // both fit (a trial allocation of the scratch, given back at once), so
+                // the scratch allocation after the loop always succeeds: an empty arena
+                // always takes the first job, and batches cannot be put back forever.
+                const size_t g2 = std::max(geom_max, jgeom), c2 = std::max(coef_max, j->scratch_need);
+                size_t off, toff;
+                bool fit = sv->arena.alloc(j->footprint, &off);
+                if (fit) {
+                    if (sv->arena.alloc(up1k(1024 + g2 + c2 + sv->stage_bytes), &toff)) {
+                        sv->arena.release(toff, up1k(1024 + g2 + c2 + sv->stage_bytes));
+                    } else {
+                        sv->arena.release(off, j->footprint);
+                        fit = false;
+                    }
+                }
+                if (fit) {
                     j->off = off;
                     j->state = RUNNING;
                     j->t_admit = now_ms();
                     B->jobs.push_back(j);
-                    const PairSetDev &ps = j->req.basis->dev;
-                    geom_max = std::max(geom_max, up1k((size_t)ps.n_pair * 4 * sizeof(double)));
-                    coef_max = std::max(coef_max, j->scratch_need);
+                    geom_max = g2;
+                    coef_max = c2;
                     it = sv->pending.erase(it);
                 } else {
                     if (++j->skipped > 8) blocked = true;  // starving: stop admitting jobs behind it
@@ -405,7 +420,8 @@ void server_loop(scff_server_s *sv) {
             size_t soff = 0;
             const size_t sbytes = up1k(1024 + geom_max + coef_max + sv->stage_bytes);
             if (!B->jobs.empty() && !sv->arena.alloc(sbytes, &soff)) {
-                // put the jobs back (front, in order) and retry after a retirement
+                // (not reached: admission reserved room for the scratch) put the jobs
+                // back (front, in order) and retry after a retirement
                 for (auto r = B->jobs.rbegin(); r != B->jobs.rend(); ++r) {
                     sv->arena.release((*r)->off, (*r)->footprint);
                     (*r)->state = PENDING;

@@ -372,6 +372,21 @@ def config5_job(i: int) -> Job:
     return config4_job(1000 + i)
 
 
+def config5_large_positions(n: int, frac: float = 0.05, seed: int = 5050) -> np.ndarray:
+    """Indices of the large jobs in a serving stream of n jobs: exactly round(frac * n) of them,
+    at seeded positions."""
+    k = int(round(frac * n))
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False)) if k else np.zeros(0, int)
+
+
+def config5_stream_job(i: int, n: int) -> Job:
+    """Job i of a serving stream of n jobs: the config-4 size distribution, with exactly 5% of the
+    positions (seeded) taken by the large job shape (40 heavy + 40 H, 680 functions, 32 states, 128^3)."""
+    if i in set(config5_large_positions(n).tolist()):
+        return config5_large(5000 + 100000 + i)
+    return config4_job(1000 + i)
+
+
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 5555) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
