@@ -53,8 +53,8 @@ TC_PREC_NAMES = ("bf16x3", "tf32x3", "bf16x2", "fp16x2")
 # only while the kernel sources hash to the value recorded with it.
 TC_SOURCES = ["kernels_tc.cu", "tc_internal.h", "tc_schedule.h", "device_common.cuh", "scff_internal.h"]
 MEASURED_TRAFFIC = {
-    ("cfg3", "bf16x3"): {"bytes": 874469632 + 377433600, "src": "ad09446cb313390b",
-                         "profile": "profiles/tc_bf16x3_cfg3_launches.md"},
+    ("cfg3", "fp16x2", 0): {"bytes": 640825344 + 334578944, "src": "934acd17cfd39fe8",
+                            "profile": "profiles/tc_fp16x2_cfg3_full.md"},
 }
 
 
@@ -71,8 +71,10 @@ def tc_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload: str, precision: str):
-    rec = MEASURED_TRAFFIC.get((workload, precision))
+def measured_traffic(workload: str, precision: str, zstage: int):
+    """The recorded traffic of (workload, precision, W generator variant), or None once the kernel
+    sources have changed since the capture."""
+    rec = MEASURED_TRAFFIC.get((workload, precision, zstage))
     if rec is None or rec["src"] != tc_source_hash():
         return None
     return rec
@@ -238,7 +240,13 @@ def fft_run(ctx, b, t, S, steps, stream, flush, job):
     del out, o64, o32, f32
     return {"workload": f"10-heavy-atom job, {S} states, {FFT_N}^3 box, side 2pi/dq with dq = {dq:.4f} "
                         f"(q in [-{FFT_QMAX:g}, {FFT_QMAX:g})); density, transform and |f|^2 on the device",
-            "value": S * FFT_N ** 3 / (tms / 1e3), "unit": UNIT, "ms_per_call": tms, "precision": "fp32",
+            "throughput_at_stated_error": S * FFT_N ** 3 / (tms / 1e3), "unit": UNIT, "ms_per_call": tms,
+            "precision": "fp32", "comparable_to_analytic": False,
+            "why_not_comparable": "the discretisation error below is far from the analytic paths' 1e-5 bar: the "
+                                  "synthetic transition matrices weight the core s functions (exponents up to "
+                                  "3000), whose densities are ~0.01 Bohr wide and whose transforms barely decay "
+                                  "by |q| = 20, so no practical box resolves them and every q carries aliased "
+                                  "copies; the rate measures the FFT kernels only",
             "parseval_rel_diff": float(np.max(np.abs(par[:, 0] - par[:, 1]) / par[:, 0])),
             "fp32_vs_fp64_same_box_64": arith,
             "discretisation_err_vs_analytic": disc,
@@ -803,7 +811,9 @@ def main():
         units_eval = S * nx_rows * len(job.qy) * len(job.qz)
         achieved = alg_flops * units_eval / (kern_ms / 1e3) / 1e12
         executed = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
-        trec = measured_traffic(args.workload, args.precision)
+        zs_used = int(choice["zstage"]) if choice else (args.zstage if args.zstage >= 0 else
+                                                         (1 if args.precision == "tf32x3" else 0))
+        trec = measured_traffic(args.workload, args.precision, zs_used if len(job.qz) % 128 == 0 else 0)
         roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",

@@ -291,6 +291,15 @@ scff_status scff_sync(scff_ctx *ctx, void *stream);
  * the default; longer runs are faster by about 1% only. */
 scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
 
+/* Path that the last successful scff_form_factor call of this context ran
+ * (no counterpart in the paper): out[0] = 0 direct FP64, 1 direct FP32,
+ * 2 tensor cores; out[1] = the scff_precision of its arithmetic (SCFF_FP32
+ * when a tensor-core precision was asked for on an explicit q list, or when
+ * the autotuner chose the FP32 direct path); out[2] = 1 if the tensor-core
+ * kernel ran the Z-staging W generator variant.  All -1 before the first
+ * call. */
+scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
+
 /* Tensor-core W generator variant (no counterpart in the paper).  On product
  * grids whose z axis is a multiple of 128 points, every 128-column output
  * tile lies in one y row, so one warp can stage each k-chunk's Z row slices
@@ -451,8 +460,9 @@ scff_status scff_alu_peak(scff_ctx *ctx, int fp64, int iters, double *tflops, do
  * Error-bounded pair screening (the exact-tolerance form of the paper's
  * pair thresholding, Sec. "Cartesian Grid Method").  With eps > 0, the
  * first scff_form_factor call for a (transitions, grid extent) bounds every
- * pair's contribution over |q| <= the grid's largest |q|, evaluates f_s
- * exactly at up to 64 grid points (F_s = their largest |f_s|), and removes
+ * pair's contribution over |q| <= the grid's largest |q| (in FP64, from the
+ * FP64 coefficients), evaluates f_s with the FP64 path at up to 64 grid
+ * points (F_s = their largest |f_s|, lowered by a relative 1e-9), and removes
  * the pairs of smallest bound while, for every state, the summed bounds of
  * the removed pairs stay <= eps * F_s.  The result then differs from the
  * exact one by at most eps * max_q |f_s(q)| for every state and q.  The

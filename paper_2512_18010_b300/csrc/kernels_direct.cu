@@ -731,8 +731,10 @@ namespace scff {
 // |G| = exp(-|q|^2/4p) and |q_x^u q_y^v q_z^w| <= |q|^n (n = u+v+w), so
 // |term| <= sum_m |c_m| sup_{r <= qmax} r^n exp(-r^2/4p); the supremum sits at
 // r = sqrt(2pn) (or at qmax when that is closer).
-__global__ void pair_bound_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int S, double qmax,
-                                  float *__restrict__ bound) {
+// Everything in FP64 from the FP64 coefficients; the result is raised by a
+// relative 1e-12, far above the rounding of this short sum of positive terms.
+__global__ void pair_bound_kernel(PairSetDev ps, const double *__restrict__ coef64, int SB, int S, double qmax,
+                                  double *__restrict__ bound) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)ps.n_pair * S) return;
     const int pr = (int)(idx / S), s = (int)(idx % S);
@@ -751,17 +753,17 @@ __global__ void pair_bound_kernel(PairSetDev ps, const float *__restrict__ coef3
     }
     const int mL = mono_count(L);
     const int64_t row0 = ps.row_off[L] + (int64_t)(pr - ps.pair_off[L]) * mL;
-    const float *cs = coef32 + ((size_t)(s / SB) * ps.n_rows) * SB + (s % SB);
+    const double *cs = coef64 + ((size_t)(s / SB) * ps.n_rows) * SB + (s % SB);
     double b = 0.0;
-    for (int m = 0; m < mL; ++m) b += fabs((double)cs[(size_t)(row0 + m) * SB]) * sup[mono_u(m) + mono_v(m) + mono_w(m)];
-    bound[idx] = (float)(b * 1.0001 + 1e-38);  // rounding margin of the FP32 coefficients
+    for (int m = 0; m < mL; ++m) b += fabs(cs[(size_t)(row0 + m) * SB]) * sup[mono_u(m) + mono_v(m) + mono_w(m)];
+    bound[idx] = b * (1.0 + 1e-12);
 }
 
-cudaError_t launch_pair_bounds(const PairSetDev &ps, const float *coef32, int SB, int S, double qmax, float *bound,
+cudaError_t launch_pair_bounds(const PairSetDev &ps, const double *coef64, int SB, int S, double qmax, double *bound,
                                cudaStream_t st) {
     const int64_t tot = (int64_t)ps.n_pair * S;
     if (tot == 0) return cudaSuccess;
-    pair_bound_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, coef32, SB, S, qmax, bound);
+    pair_bound_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ps, coef64, SB, S, qmax, bound);
     return cudaGetLastError();
 }
 

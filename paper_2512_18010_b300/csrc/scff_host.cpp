@@ -123,6 +123,12 @@ int zstage_mode(const scff_ctx *c, int precision) {
     return k >= 0 && tc_zstage_preferred(k) ? 1 : 0;
 }
 
+extern "C" scff_status scff_last_path(scff_ctx *c, int32_t *out) {
+    if (!c || !out) return fail(SCFF_ERR_INVALID_ARG, "scff_last_path: NULL argument");
+    for (int i = 0; i < 3; ++i) out[i] = c->last_path[i];
+    return SCFF_OK;
+}
+
 extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: NULL context");
     if (mode < -1 || mode > 1) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
@@ -771,6 +777,9 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         }
         CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
         if (ho) ho->done = used > 1;
+        c->last_path[0] = 2;
+        c->last_path[1] = precision;
+        c->last_path[2] = ta.zstage && g->nz % 128 == 0 && kind != 1 ? 1 : 0;
     } else {
         DirectArgs a;
         memset(&a, 0, sizeof(a));
@@ -808,6 +817,9 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         }
         if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[1], st));
         CUDA_TRY(launch_direct(a, fp64 ? 1 : 0, g->product ? 0 : 1, &c->launches, st));
+        c->last_path[0] = fp64 ? 0 : 1;
+        c->last_path[1] = fp64 ? SCFF_FP64 : SCFF_FP32;
+        c->last_path[2] = 0;
     }
     if (c->timing) {
         CUDA_TRY(cudaEventRecord(c->ev[2], st));
@@ -923,29 +935,31 @@ static scff_status get_screened(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, s
     }
     const PairSetDev &ps = b->dev;
     const int S = t->S;
-    const int SB = direct_state_block(S, false);
+    // the bounds and the probe values come from the FP64 coefficients and the
+    // FP64 path, so that only FP64 rounding is left in the error argument
+    const int SB = direct_state_block(S, true);
     const int S_pad = (S + SB - 1) / SB * SB;
-    TRY(grow(c, c->coef, (size_t)S_pad * ps.n_rows * sizeof(float) + 256));
+    TRY(grow(c, c->coef, (size_t)S_pad * ps.n_rows * sizeof(double) + 256));
     TRY(grow(c, c->geom, (size_t)ps.n_pair * 4 * sizeof(double) + 64));
     CUDA_TRY(launch_pair_geom(ps, (double *)c->geom.p, st));
-    CUDA_TRY(launch_pairprep(ps, t->d_T, S, SB, S_pad, nullptr, (float *)c->coef.p, &c->launches, st));
+    CUDA_TRY(launch_pairprep(ps, t->d_T, S, SB, S_pad, (double *)c->coef.p, nullptr, &c->launches, st));
     std::vector<double> qp = probe_points(g);
     const int np = (int)(qp.size() / 3);
-    float *d_bound = nullptr, *d_fp = nullptr;
+    double *d_bound = nullptr, *d_fp = nullptr;
     double *d_q = nullptr;
     const size_t nb = (size_t)ps.n_pair * S;
-    if (cudaMalloc(&d_bound, sizeof(float) * std::max<size_t>(nb, 1)) != cudaSuccess ||
-        cudaMalloc(&d_fp, sizeof(float) * 2 * (size_t)S * std::max(np, 1)) != cudaSuccess ||
+    if (cudaMalloc(&d_bound, sizeof(double) * std::max<size_t>(nb, 1)) != cudaSuccess ||
+        cudaMalloc(&d_fp, sizeof(double) * 2 * (size_t)S * std::max(np, 1)) != cudaSuccess ||
         cudaMalloc(&d_q, sizeof(double) * std::max<size_t>(qp.size(), 3)) != cudaSuccess) {
         cudaFree(d_bound);
         cudaFree(d_fp);
         cudaFree(d_q);
         return fail(SCFF_ERR_OOM, "scff_form_factor: screening buffers");
     }
-    std::vector<float> hb(nb), hf(2 * (size_t)S * np);
+    std::vector<double> hb(nb), hf(2 * (size_t)S * np);
     scff_status rc = SCFF_OK;
     do {
-        if (launch_pair_bounds(ps, (const float *)c->coef.p, SB, S, g->qmax, d_bound, st) != cudaSuccess ||
+        if (launch_pair_bounds(ps, (const double *)c->coef.p, SB, S, g->qmax, d_bound, st) != cudaSuccess ||
             cudaMemcpyAsync(d_q, qp.data(), sizeof(double) * qp.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
             rc = fail(SCFF_ERR_CUDA, "scff_form_factor: screening launch failed");
             break;
@@ -962,9 +976,9 @@ static scff_status get_screened(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, s
         a.scale = 1.0;
         a.f = d_fp;
         a.err_flag = c->d_err;
-        if (launch_direct(a, 0, 1, &c->launches, st) != cudaSuccess ||
-            cudaMemcpyAsync(hb.data(), d_bound, sizeof(float) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(hf.data(), d_fp, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (launch_direct(a, 1, 1, &c->launches, st) != cudaSuccess ||
+            cudaMemcpyAsync(hb.data(), d_bound, sizeof(double) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hf.data(), d_fp, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             rc = fail(SCFF_ERR_CUDA, "scff_form_factor: screening probe failed");
             break;
@@ -978,7 +992,7 @@ static scff_status get_screened(scff_ctx *c, scff_basis_s *b, scff_trans_s *t, s
     for (int s = 0; s < S; ++s)
         for (int i = 0; i < np; ++i) {
             const double re = hf[2 * ((size_t)s * np + i)], im = hf[2 * ((size_t)s * np + i) + 1];
-            F[s] = std::max(F[s], sqrt(re * re + im * im) * (1.0 - 1e-4));  // margin for the FP32 probe
+            F[s] = std::max(F[s], sqrt(re * re + im * im) * (1.0 - 1e-9));  // margin for the FP64 probe
         }
     // greedy: smallest relative bound first, stop at the first pair that does not fit
     std::vector<double> score(ps.n_pair);

@@ -158,8 +158,9 @@ cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB
 cudaError_t launch_axis_tables(const PairSetDev &ps, const double *pair_geom, const double *qaxis,
                                int n, int axis, void *table, int fp64, cudaStream_t st);
 
-// bound[pair][s]: an upper bound of |pair term for state s| over |q| <= qmax.
-cudaError_t launch_pair_bounds(const PairSetDev &ps, const float *coef32, int SB, int S, double qmax, float *bound,
+// bound[pair][s]: an upper bound of |pair term for state s| over |q| <= qmax,
+// from the FP64 coefficients (state block SB), in FP64.
+cudaError_t launch_pair_bounds(const PairSetDev &ps, const double *coef64, int SB, int S, double qmax, double *bound,
                                cudaStream_t st);
 
 // Separable integrals I_s = sum wx wy wz f_s over a product grid (FP64).

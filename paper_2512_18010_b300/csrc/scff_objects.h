@@ -40,6 +40,7 @@ struct scff_ctx {
     int timing = 0;
     int drain_every = -1;  // tensor-core TMEM accumulation length (-1 = default)
     int tc_zstage = -1;    // Z-staging generator variant: -1 automatic, 0 off, 1 on where the grid allows
+    int last_path[3] = {-1, -1, -1};  // path of the last form-factor call (scff_last_path)
     int timed_valid = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<struct scff_basis_s *> bases;

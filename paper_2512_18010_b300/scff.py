@@ -33,7 +33,7 @@ _SYMBOLS = [
     "scff_create", "scff_destroy", "scff_last_error", "scff_basis", "scff_transitions",
     "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
-    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_set_tc_zstage", "scff_form_factor_static",
+    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_set_tc_zstage", "scff_last_path", "scff_form_factor_static",
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
@@ -150,6 +150,8 @@ def load(build_if_missing: bool = True):
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_zstage.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_zstage.restype = I32
+    lib.scff_last_path.argtypes = [P, P]
+    lib.scff_last_path.restype = I32
     lib.scff_set_download_bands.argtypes = [P, ctypes.c_int]
     lib.scff_alu_peak.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.scff_alu_peak.restype = I32
@@ -436,6 +438,15 @@ class Context:
     def set_tc_drain(self, drain_every: int):
         """k-chunks per tensor-core TMEM accumulation (0 = whole K, -1 = default)."""
         _check(self.lib.scff_set_tc_drain(self.h, int(drain_every)))
+
+    def last_path(self) -> dict:
+        """The path the last form-factor call ran: direct FP64/FP32 or tensor cores, the precision of its
+        arithmetic, and whether the Z-staging generator variant ran."""
+        out = np.zeros(3, dtype=np.int32)
+        _check(self.lib.scff_last_path(self.h, _p(out)))
+        names = {v: k for k, v in PRECISIONS.items()}
+        return {"path": {0: "direct_fp64", 1: "direct_fp32", 2: "tensor_cores"}.get(int(out[0])),
+                "precision": names.get(int(out[1])), "zstage": bool(out[2] == 1)}
 
     def set_tc_zstage(self, mode: int):
         """Tensor-core W generator variant: -1 automatic, 0 gather from global memory, 1 stage Z and Y

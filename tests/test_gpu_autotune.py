@@ -11,7 +11,7 @@ from paper_2512_18010_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X3])
+@pytest.mark.parametrize("prec", [scff.TF32X3, scff.BF16X3, scff.FP16X2])
 def test_autotune_choice_and_parity(prec):
     ctx = scff.Context(0)
     try:
@@ -32,5 +32,57 @@ def test_autotune_choice_and_parity(prec):
             idx = W.subset_indices(job.nq, 500, 8)
             ref = oracle.grid_form_factor(job, idx)
             assert np.max(np.abs(f1[:, idx] - ref)) / np.max(np.abs(ref)) < 1e-5
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec", [scff.FP16X2, scff.TF32X3, scff.BF16X2])
+def test_generator_variants_agree_bitwise(prec):
+    # On a grid whose z axis is a multiple of 128 both W generator variants can run (Z and Y staged
+    # in shared memory, or gathered from global memory); they form the same W, so the results are
+    # bitwise equal, and scff_last_path reports which one ran.
+    base = W.config_f(n_heavy=2, n_states=5)
+    job = W.Job(base.mol, base.T, W.axis(9, 12.0), W.axis(6, 9.0), W.axis(128, 14.0), 3520)
+    ctx = scff.Context(0)
+    try:
+        out = {}
+        for z in (0, 1):
+            ctx.set_tc_zstage(z)
+            f, f2 = scff.evaluate_job(ctx, job, precision=prec)
+            p = ctx.last_path()
+            assert p["path"] == "tensor_cores" and p["zstage"] == bool(z)
+            out[z] = (f, f2)
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        idx = W.subset_indices(job.nq, 600, 12)
+        ref = oracle.grid_form_factor(job, idx)
+        tol = 5e-5 if prec == scff.BF16X2 else 1e-5
+        assert np.max(np.abs(out[0][0][:, idx] - ref)) / np.max(np.abs(ref)) < tol
+        # with the autotuner on, both variants are candidates and the choice is reported
+        ctx.set_tc_zstage(-1)
+        ctx.set_autotune(True)
+        b = ctx.basis(job.mol)
+        t = ctx.transitions(b, job.T)
+        g = ctx.qgrid_product(job.qx, job.qy, job.qz)
+        fa, _ = ctx.form_factor(b, t, g, precision=prec)
+        ch = ctx.autotune_choice(b, t, g, prec)
+        assert ch["zstage"] in (0, 1)
+        if ch["tensor_cores"]:
+            assert np.array_equal(fa, out[0][0])
+    finally:
+        ctx.close()
+
+
+def test_last_path_reports_the_path_taken():
+    job = W.config1()
+    ctx = scff.Context(0)
+    try:
+        assert ctx.last_path()["path"] is None
+        scff.evaluate_job(ctx, job, precision=scff.FP16X2)
+        assert ctx.last_path() == {"path": "tensor_cores", "precision": "fp16x2", "zstage": False}
+        # a tensor-core precision on an explicit q list runs the FP32 direct path
+        scff.evaluate_job(ctx, job, precision=scff.BF16X3, q_list=np.array([[0.1, 0.2, 0.3], [1.0, 0.0, 0.0]]))
+        assert ctx.last_path() == {"path": "direct_fp32", "precision": "fp32", "zstage": False}
+        scff.evaluate_job(ctx, job, precision=scff.FP64)
+        assert ctx.last_path()["path"] == "direct_fp64"
     finally:
         ctx.close()
