@@ -119,6 +119,7 @@ struct SJob {
     size_t footprint = 0;    // bytes of the job's arena block
     size_t off = 0;          // arena offset
     size_t scratch_need = 0; // pair geometry + coefficients of this job
+    double cost = 0;         // work estimate: contraction rows x states x evaluated points
     int skipped = 0;
     int state = PENDING;
     scff_status status = SCFF_OK;
@@ -139,6 +140,7 @@ struct scff_server_s {
     int precision = SCFF_TF32X3;
     int slots = 2;
     int max_batch = 64;
+    double cost_ratio = 0.0;         // batch members' work within this factor of the first one's (<= 0: any)
     std::vector<cudaStream_t> streams;
     std::vector<Batch *> busy;       // per slot, null when free
     std::vector<void *> h_stage;     // pinned staging for descriptors and work lists, per slot
@@ -178,6 +180,8 @@ void size_job(scff_server_s *sv, SJob *j) {
     j->footprint = b;
     const int SB = tc_precision(sv->precision) ? 8 : direct_state_block(j->S, fp64);
     j->S_pad = (j->S + SB - 1) / SB * SB;
+    const double rows = tc_precision(sv->precision) ? (double)ps.n_krows : (double)ps.n_rows;
+    j->cost = rows * j->S * (double)(j->half ? (j->nq + 1) / 2 : j->nq);
     j->scratch_need = up1k((size_t)ps.n_pair * 4 * sizeof(double)) + up1k((size_t)j->S_pad * ps.n_rows * rsz);
 }
 
@@ -389,6 +393,15 @@ void server_loop(scff_server_s *sv) {
                     continue;
                 }
                 if (blocked) break;
+                // Jobs of very different cost go to different batches: every job of a
+                // batch completes when the batch's launch ends, so a small job batched
+                // with a large one would wait for it.  Skipping for this reason does not
+                // count as starving (the first pending job always opens the next batch).
+                if (!B->jobs.empty() && sv->cost_ratio > 0 &&
+                    (j->cost > sv->cost_ratio * B->jobs[0]->cost || B->jobs[0]->cost > sv->cost_ratio * j->cost)) {
+                    ++it;
+                    continue;
+                }
                 // Admitted only if its block and the batch scratch grown to cover it
                 // both fit (a trial allocation of the scratch, given back at once), so
                 // the scratch allocation after the loop always succeeds: an empty arena
@@ -475,7 +488,7 @@ void server_loop(scff_server_s *sv) {
 extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options *opt, scff_server_h *out) {
     if (!c || !out) return serr(SCFF_ERR_INVALID_ARG, "scff_server_create: NULL context or output");
     *out = nullptr;
-    scff_server_options o = opt ? *opt : scff_server_options{SCFF_TF32X3, 2, 64, 0};
+    scff_server_options o = opt ? *opt : scff_server_options{SCFF_TF32X3, 2, 64, 0, 0.0};
     if (o.precision < SCFF_FP64 || o.precision > SCFF_FP16X2 || o.slots < 1 || o.slots > 8 || o.max_batch_jobs < 1)
         return serr(SCFF_ERR_INVALID_ARG, "scff_server_create: invalid options");
     cudaSetDevice(c->device);
@@ -484,6 +497,7 @@ extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options
     sv->precision = o.precision;
     sv->slots = o.slots;
     sv->max_batch = o.max_batch_jobs;
+    sv->cost_ratio = o.batch_cost_ratio;
     size_t arena = o.arena_bytes ? o.arena_bytes : (size_t)(c->budget / 2);
     if (cudaMalloc(&sv->arena_ptr, arena) != cudaSuccess) {
         delete sv;

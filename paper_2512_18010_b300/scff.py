@@ -44,7 +44,7 @@ _SYMBOLS = [
 
 class _ServerOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("slots", ctypes.c_int), ("max_batch_jobs", ctypes.c_int),
-                ("arena_bytes", ctypes.c_uint64)]
+                ("arena_bytes", ctypes.c_uint64), ("batch_cost_ratio", ctypes.c_double)]
 
 
 class _Request(ctypes.Structure):
@@ -235,12 +235,13 @@ class Server:
     """Continuous-batching request loop (see scff_server_create)."""
 
     def __init__(self, ctx: "Context", precision=TF32X3, slots: int = 2, max_batch_jobs: int = 64,
-                 arena_bytes: int = 0):
+                 arena_bytes: int = 0, batch_cost_ratio: float = 0.0):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         self.ctx = ctx
         self.precision = precision
-        opt = _ServerOptions(int(precision), int(slots), int(max_batch_jobs), int(arena_bytes))
+        opt = _ServerOptions(int(precision), int(slots), int(max_batch_jobs), int(arena_bytes),
+                             float(batch_cost_ratio))
         h = ctypes.c_void_p()
         _check(ctx.lib.scff_server_create(ctx.h, ctypes.byref(opt), ctypes.byref(h)))
         self.h = h

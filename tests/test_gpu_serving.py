@@ -129,3 +129,40 @@ def test_server_parity_cancel_timeout_admission(ctx):
     assert st["failed"] == 1
     ctx.release(b)
     ctx.release(bb)
+
+
+@pytest.mark.parametrize("ratio", [16.0, 0.0])
+def test_batch_cost_ratio_separates_large_and_small_jobs(ctx, ratio):
+    # With a ratio of 16 a job ~100x more work than the first of a batch waits for the next
+    # batch; with no limit (0, the default) all of them may share one.  Results equal the jobs alone.
+    import torch
+    small = small_jobs(3, seed=4)
+    big = W.scaled_job(W.config3(), 40)
+    jobs = small + [big]
+    ref = [alone(ctx, j, scff.FP16X2) for j in jobs]
+    srv = scff.Server(ctx, precision=scff.FP16X2, slots=1, max_batch_jobs=8, batch_cost_ratio=ratio)
+    handles, outs, ids = [], [], []
+    for job in jobs:
+        b = ctx.basis(job.mol)
+        t = ctx.transitions(b, job.T)
+        handles.append((b, t))
+        f = torch.full((job.n_states, job.nq, 2), float("nan"), device="cuda")
+        f2 = torch.full((job.n_states, job.nq), float("nan"), device="cuda")
+        outs.append((f, f2))
+    # hold the slot with a first batch so that the rest queue up together
+    ids.append(srv.submit(*handles[0], jobs[0].qx, jobs[0].qy, jobs[0].qz, *outs[0]))
+    for k in range(1, len(jobs)):
+        ids.append(srv.submit(*handles[k], jobs[k].qx, jobs[k].qy, jobs[k].qz, *outs[k]))
+    for i in ids:
+        srv.wait(i, timeout_s=120)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(jobs)
+    if ratio <= 0:
+        assert st["batches"] <= 2
+    else:
+        assert st["batches"] >= 2
+    for (f, f2), (fr, f2r) in zip(outs, ref):
+        assert torch.equal(f, fr) and torch.equal(f2, f2r)
+    for b, _ in handles:
+        ctx.release(b)
