@@ -381,6 +381,13 @@ template <typename R, int SB> struct Acc {
     __device__ __forceinline__ R im(int j) const { return sizeof(R) == 4 ? hi[j] + li[j] : pi[j]; }
 };
 
+// Slots of the collapsed sums of a pair of degree L (the VEC variant): for
+// w < L both parities of u + v + w occur (slots 2w and 2w + 1), for w = L only
+// u = v = 0, of the parity of L (slot 2L): 2L + 1 slots.
+__host__ __device__ constexpr int collapse_slot(int L, int w, int odd) { return w < L ? 2 * w + odd : 2 * L; }
+__host__ __device__ constexpr int collapse_w(int L, int t) { return t < 2 * L ? t / 2 : L; }
+__host__ __device__ constexpr bool collapse_odd(int L, int t) { return t < 2 * L ? (t & 1) != 0 : (L & 1) != 0; }
+
 // VEC: the per-state coefficients of a monomial are read four per 16-byte
 // shared-memory load (a pair's rows are SB floats, so each starts 16-byte
 // aligned).  It pays where the block's points share (ix, iy) (10-heavy-atom
@@ -392,6 +399,7 @@ template <typename R, int SB> struct Acc {
 // the block, took the 64^3 FP32 job from 3.8 to 5.1 ms).
 template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI>
 __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf,
+                                              const R *__restrict__ bbuf,
                                               const typename Cplx<R>::T *__restrict__ gxy, int pr0,
                                               int np, const R (&px)[kMaxPairL + 1], const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1],
                                               int ix, int iy, int iz, double qx, double qy, double qz,
@@ -411,27 +419,37 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
         R E[SB], O[SB];
 #pragma unroll
         for (int j = 0; j < SB; ++j) E[j] = O[j] = R(0);
-        const R *c = cbuf + (size_t)i * mL * SB;
-        static_for<mL>([&](auto M) {
-            constexpr int m = decltype(M)::value;
-            constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
-            const R mono = px[u] * py[v] * pz[w];
-            if constexpr (VEC) {
-                static_assert(sizeof(R) == 4 && SB % 4 == 0, "four FP32 coefficients per load");
-                const float4 *c4 = reinterpret_cast<const float4 *>(c + m * SB);
+        if constexpr (VEC) {
+            // the block's x and y powers are already folded into the chunk's
+            // collapsed sums (see run_class): E and O are polynomials in q_z
+            // alone, 2L+1 terms per pair instead of (L+1)(L+2)(L+3)/6
+            static_assert(sizeof(R) == 4 && SB % 4 == 0, "four FP32 sums per load");
+            constexpr int NS = 2 * L + 1;
+            const R *bb = bbuf + (size_t)i * NS * SB;
+            static_for<NS>([&](auto T) {
+                constexpr int t = decltype(T)::value;
+                constexpr int w = collapse_w(L, t);
+                const R zw = pz[w];
+                const float4 *b4 = reinterpret_cast<const float4 *>(bb + t * SB);
 #pragma unroll
                 for (int jj = 0; jj < SB / 4; ++jj) {
-                    const float4 cv = c4[jj];
+                    const float4 cv = b4[jj];
                     const R cc[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if constexpr (((u + v + w) & 1) != 0)
-                            O[4 * jj + t] = fma(cc[t], mono, O[4 * jj + t]);
+                    for (int tt = 0; tt < 4; ++tt) {
+                        if constexpr (collapse_odd(L, t))
+                            O[4 * jj + tt] = fma(cc[tt], zw, O[4 * jj + tt]);
                         else
-                            E[4 * jj + t] = fma(cc[t], mono, E[4 * jj + t]);
+                            E[4 * jj + tt] = fma(cc[tt], zw, E[4 * jj + tt]);
                     }
                 }
-            } else {
+            });
+        } else {
+            const R *c = cbuf + (size_t)i * mL * SB;
+            static_for<mL>([&](auto M) {
+                constexpr int m = decltype(M)::value;
+                constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
+                const R mono = px[u] * py[v] * pz[w];
 #pragma unroll
                 for (int j = 0; j < SB; ++j) {
                     if constexpr (((u + v + w) & 1) != 0)
@@ -439,8 +457,8 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
                     else
                         E[j] = fma(c[m * SB + j], mono, E[j]);
                 }
-            }
-        });
+            });
+        }
         if constexpr (L == 0) {
             // s-s pairs have no odd monomial: f += g E
 #pragma unroll
@@ -465,7 +483,7 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
 // Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
 // false (uniformly across the block) when a wait timed out.
 template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI>
-__device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, typename Cplx<R>::T *gxy,
+__device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, R *bbuf, typename Cplx<R>::T *gxy,
                                           int bx, int by, uint64_t *bars,
                                           uint32_t &phase, int sblk, const R (&px)[kMaxPairL + 1],
                                           const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1], int ix, int iy, int iz, double qx, double qy,
@@ -515,19 +533,53 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
                 v.y = a.x * bb.y + a.y * bb.x;
                 gxy[t] = v;
             }
+            if constexpr (VEC) {
+                // Collapsed sums of the chunk (x and y fixed for the block):
+                //   B[pair][t][s] = sum_{u,v} D^s_{pair,(u,v,w)} q_x^u q_y^v over the
+                // (u, v) of slot t (collapse_slot: one slot per w and parity of
+                // u + v + w), so that E_s and O_s are sums of q_z^w B[t][s].
+                constexpr int NS = 2 * L + 1;
+                R bx_[kMaxPairL + 1], by_[kMaxPairL + 1];
+                bx_[0] = by_[0] = R(1);
+                const R qxb = (R)p.qax[bx], qyb = (R)p.qay[by];
+#pragma unroll
+                for (int k = 1; k <= kMaxPairL; ++k) {
+                    bx_[k] = bx_[k - 1] * qxb;
+                    by_[k] = by_[k - 1] * qyb;
+                }
+                const R *cb = bufs[b];
+                for (int e = threadIdx.x; e < n * NS * SB; e += blockDim.x) {
+                    const int js = e % SB, t = (e / SB) % NS, i = e / (SB * NS);
+                    const R *c = cb + (size_t)i * mL * SB + js;
+                    R sum = R(0);
+                    static_for<mL>([&](auto M) {
+                        constexpr int m = decltype(M)::value;
+                        constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
+                        constexpr int tm = collapse_slot(L, w, (u + v + w) & 1);
+                        if (t == tm) sum = fma(c[m * SB], bx_[u] * by_[v], sum);
+                    });
+                    bbuf[e] = sum;
+                }
+            }
             __syncthreads();
         }
-        consume_chunk<R, SB, L, LIST, VEC, NOUNI>(p, bufs[b], gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx, qy, qz,
-                                      q2, acc);
+        consume_chunk<R, SB, L, LIST, VEC, NOUNI>(p, bufs[b], bbuf, gxy, pbeg + c * npc, n, px, py, pz, ix, iy, iz, qx,
+                                                  qy, qz, q2, acc);
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
     }
     return ok;
 }
 
+// Blocks per SM the VEC variant (block-shared rows, collapsed sums) is
+// compiled for: its registers allow 5 with 8 states, 4 with 12, 3 with 16.
+template <int SB, bool VEC> constexpr int direct_min_blocks() { return !VEC ? 1 : SB <= 8 ? 5 : SB <= 12 ? 4 : 3; }
+
 template <typename R, int SB, bool LIST, bool HIGH, bool VEC = false, bool NOUNI = false>
-__global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) {
+__global__ void __launch_bounds__(kDirectThreads, (direct_min_blocks<SB, VEC>())) direct_kernel(DirectParams p) {
     __shared__ __align__(128) unsigned char smem[2 * kChunkBytes];
+    // (VEC) the chunk's collapsed sums: at most the size of its coefficients
+    __shared__ __align__(16) unsigned char bsm[VEC ? kChunkBytes : 16];
     __shared__ __align__(16) typename Cplx<R>::T gxy[kMaxChunkPairs];
     __shared__ __align__(8) uint64_t bars[2];
     R *buf0 = reinterpret_cast<R *>(smem);
@@ -600,7 +652,8 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(DirectParams p) 
     auto run = [&](auto LC) {
         constexpr int L = decltype(LC)::value;
         if (ok)
-            ok = run_class<R, SB, L, LIST, VEC, NOUNI>(p, buf0, buf1, gxy, bx, by, bars, phase, sblk, px, py, pz, ix, iy, iz,
+            ok = run_class<R, SB, L, LIST, VEC, NOUNI>(p, buf0, buf1, reinterpret_cast<R *>(bsm), gxy, bx, by, bars, phase,
+                                                       sblk, px, py, pz, ix, iy, iz,
                                            qx, qy, qz, q2, acc);
     };
     if constexpr (HIGH) {
@@ -670,9 +723,9 @@ static cudaError_t launch_direct_t(const DirectArgs &a, bool list, int64_t *laun
     const bool has_high = a.ps->pair_off[kMaxPairL + 1] > a.ps->pair_off[kHighClass];
     if (has_low || !has_high) {
         p.part = has_high ? 0 : kPartFinal;
-        // the vector loads for 12-state FP32 blocks on block-shared rows only
-        // (the other state blocks, and the f classes, spill with them)
-        constexpr bool kVec = sizeof(R) == 4 && SB == 12;
+        // the collapsed sums and vector loads for FP32 blocks on block-shared
+        // rows (not for the f classes, which need more registers)
+        constexpr bool kVec = sizeof(R) == 4 && SB % 4 == 0;
         if (list)
             direct_kernel<R, SB, true, false><<<grid, kDirectThreads, 0, st>>>(p);
         else if (kVec && p.xy_uniform)

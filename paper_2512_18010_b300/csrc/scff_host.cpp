@@ -849,8 +849,10 @@ static scff_status autotune(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, 
     std::vector<FFChoice> cand;
     // tensor cores with both W generator variants (bitwise the same results) unless the
     // context fixes one, then the FP32 direct path's state blocks
+    const int kind = tc_kind_of_precision(precision);
+    const bool zs_can = kind >= 0 && kind != 1 && g->nz % 128 == 0;  // not BF16 hi/mid/lo; nz multiple of 128
     for (int zs : {1, 0})
-        if (c->tc_zstage < 0 || c->tc_zstage == zs) cand.push_back({1, 8, 8, zs});
+        if ((c->tc_zstage < 0 || c->tc_zstage == zs) && (zs == 0 || zs_can)) cand.push_back({1, 8, 8, zs});
     for (int sb : {8, 12, 16}) cand.push_back({0, 0, sb, 0});
     TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
     TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));

@@ -108,6 +108,20 @@ def test_block_shared_rows_with_padded_states(ctx, prec):
     assert rel_err(f[:, idx], ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("S", [5, 16])
+def test_fp32_state_blocks_on_block_shared_rows(ctx, S):
+    # FP32 state blocks of 8 and 16 states on a grid whose z axis is a multiple of 128: the
+    # variant that collapses each pair's x and y powers once per block and evaluates polynomials
+    # in q_z alone; d shells (pair degree up to 4) and an odd x axis
+    base = W.config2()
+    T = W.transition_matrices(79, S, base.mol.nbf)
+    job = W.Job(base.mol, T, W.axis(7, 12.0), W.axis(4, 9.0), W.axis(128, 15.0), 79)
+    f, _ = scff.evaluate_job(ctx, job, precision=scff.FP32)
+    idx = W.subset_indices(job.nq, 700, 7)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[scff.FP32]
+
+
 def test_degenerate_inputs(ctx):
     job = W.config1()
     b = ctx.basis(job.mol)
