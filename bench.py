@@ -89,8 +89,10 @@ def parse():
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--precision", default="fp16x2", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1],
-                    help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y")
+    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y, 2 prefetch")
+    ap.add_argument("--drain", type=int, default=-1,
+                    help="tensor-core k-chunks per TMEM accumulation group (-1 = library default, 8)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -699,6 +701,7 @@ def main():
     if not args.no_autotune:
         ctx.set_autotune(True)
     ctx.set_tc_zstage(args.zstage)
+    ctx.set_tc_drain(args.drain)
     b = ctx.basis(job.mol)
     t = ctx.transitions(b, job.T)
     g = ctx.qgrid_product(job.qx, job.qy, job.qz)
@@ -751,6 +754,7 @@ def main():
     if dist:
         dist.barrier()
     launches = ctx.kernel_launches() - l0
+    path_used = ctx.last_path()
     clocks = sampler.stop()
     ctx.sync(stream)
     # the timed result at the oracle's sample points (compared in the CPU-baseline leg)
@@ -811,9 +815,8 @@ def main():
         units_eval = S * nx_rows * len(job.qy) * len(job.qz)
         achieved = alg_flops * units_eval / (kern_ms / 1e3) / 1e12
         executed = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
-        zs_used = int(choice["zstage"]) if choice else (args.zstage if args.zstage >= 0 else
-                                                         (1 if args.precision == "tf32x3" else 0))
-        trec = measured_traffic(args.workload, args.precision, zs_used if len(job.qz) % 128 == 0 else 0)
+        zs_used = {v: k for k, v in scff.GEN_VARIANTS.items()}.get(path_used["variant"], 0)
+        trec = measured_traffic(args.workload, args.precision, zs_used)
         roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",

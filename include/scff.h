@@ -303,20 +303,30 @@ scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
  * (no counterpart in the paper): out[0] = 0 direct FP64, 1 direct FP32,
  * 2 tensor cores; out[1] = the scff_precision of its arithmetic (SCFF_FP32
  * when a tensor-core precision was asked for on an explicit q list, or when
- * the autotuner chose the FP32 direct path); out[2] = 1 if the tensor-core
- * kernel ran the Z-staging W generator variant.  All -1 before the first
+ * the autotuner chose the FP32 direct path); out[2] = the W generator
+ * variant the tensor-core kernel ran (0 gather, 1 Z staging, 2 prefetch; see
+ * scff_set_tc_zstage), 0 off the tensor cores.  All -1 before the first
  * call. */
 scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
 
-/* Tensor-core W generator variant (no counterpart in the paper).  On product
- * grids whose z axis is a multiple of 128 points, every 128-column output
- * tile lies in one y row, so one warp can stage each k-chunk's Z row slices
- * (1-D bulk copies) and Y values in shared memory for the generators, instead
- * of each generator thread gathering its table entries from global memory.
- * mode: -1 automatic (the default: on where the grid allows it; with the
- * autotuner on, tuned per job shape), 0 never, 1 wherever the grid allows it.
- * Both variants form bitwise the same W, so results do not depend on the
- * choice.  Applies to calls, plans and servers created after it. */
+/* Tensor-core W generator variant (no counterpart in the paper).
+ *   0 gather: each generator thread gathers its Y and Z table entries from
+ *     global memory and keeps its share of the tile's running sums in
+ *     registers.
+ *   1 Z staging: on product grids whose z axis is a multiple of 128 points,
+ *     every 128-column output tile lies in one y row, so one warp stages each
+ *     k-chunk's Z row slices (1-D bulk copies) and Y values in shared memory
+ *     for the generators.
+ *   2 prefetch (FP16 hi/lo and BF16 hi/lo): the running sums live in tensor
+ *     memory, and each generator thread gathers the next k-chunk's table
+ *     entries while it forms the current chunk's W.
+ * mode: -1 automatic (the default: Z staging for TF32 hi/lo, gather for the
+ * 16-bit splits; with the autotuner on,
+ * tuned per job shape over the variants the grid and split allow), 0, 1 or 2
+ * to request one (a variant the grid or split does not allow runs as 0).  All
+ * variants form bitwise the same W and add the same partial sums in the same
+ * order, so results do not depend on the choice.  Applies to calls, plans and
+ * servers created after it. */
 scff_status scff_set_tc_zstage(scff_ctx *ctx, int mode);
 
 /*
@@ -491,7 +501,7 @@ scff_status scff_screening_info(scff_ctx *ctx, scff_trans_h trans, scff_qgrid_h 
  * it, see scff_set_tc_drain).
  * scff_autotune_choice writes five values: out[0] = 1 tensor cores / 0 direct,
  * out[1] = drain, out[2] = state block, out[3] = best time in microseconds,
- * out[4] = 1 if the Z-staging W generator variant was chosen. */
+ * out[4] = the W generator variant chosen (scff_set_tc_zstage's modes 0-2). */
 scff_status scff_set_autotune(scff_ctx *ctx, int enable);
 scff_status scff_autotune_choice(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
                                  scff_qgrid_h grid, int precision, int32_t *out);

@@ -66,9 +66,12 @@ constexpr int IRING = 4;                             // work items published ahe
 // THREADS x LAUNCH_REGS registers; warpgroup 0 keeps LOW_REGS per thread and
 // the two generator warpgroups take HIGH_REGS.  The shares add up to the
 // launch total exactly, and the host checks the compiled count before launch.
+// Warpgroup 0 runs two single-thread roles (and the Z stager), which fit in
+// 40; the generators' extra registers removed their spills (FP16 hi/lo on the
+// 10-heavy-atom job: 7.73 ms with 72/216, 7.36 ms with 40/232).
 constexpr int LAUNCH_REGS = 168;
-constexpr int LOW_REGS = 72;
-constexpr int HIGH_REGS = 216;
+constexpr int LOW_REGS = 40;
+constexpr int HIGH_REGS = 232;
 static_assert(128 * LOW_REGS + GEN_WARPS * 32 * HIGH_REGS == THREADS * LAUNCH_REGS, "register split");
 static_assert(2 * BN == GEN_WARPS * 32, "two generator threads per W row");
 
@@ -121,17 +124,30 @@ template <int KIND> struct Kind {
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
 
-// Launch configuration of the persistent kernel per split kind and W source.
-//   ZS = false: the generators gather their Y and Z table entries from global
-//     memory (any product grid, the spherical method's tables).
-//   ZS = true (two-piece kinds, grids with nz a multiple of 128): every tile
+// Launch configuration of the persistent kernel per split kind and W generator
+// variant VAR:
+//   VAR_GATHER: the generators gather their Y and Z table entries from global
+//     memory (any product grid, the spherical method's tables) and keep the
+//     tile's running sums in registers; two TMEM accumulator sets alternate.
+//   VAR_ZSTAGE (two-piece kinds, grids with nz a multiple of 128): every tile
 //     lies in one y row, so a chunk needs one Y value per k (shared by all
 //     tile rows) and one 128-entry slice of a Z row per k; warp 2 stages both
 //     into shared memory one chunk ahead (the slices by 1-D bulk copies), and
 //     the generators read shared memory only.  Two stages then fit beside
 //     the two Z slots.
-template <int KIND, bool ZS> struct Cfg {
+//   VAR_PREFETCH (kinds that stage their k-offsets): the running sums live in
+//     TMEM (one accumulator set for the MMAs, one for the sums, added to by
+//     the generators in FP32 at every drain), which frees the registers for
+//     a second set of table entries: each generator thread gathers the next
+//     chunk's entries before it forms the current chunk's W, so the gather
+//     latency overlaps the W work instead of preceding it.  The additions are
+//     the same, in the same order, as VAR_GATHER's, so both give bitwise the
+//     same tile.
+enum { VAR_GATHER = 0, VAR_ZSTAGE = 1, VAR_PREFETCH = 2 };
+template <int KIND, int VAR> struct Cfg {
     using KD = Kind<KIND>;
+    static constexpr bool ZS = VAR == VAR_ZSTAGE;
+    static constexpr bool PF = VAR == VAR_PREFETCH;
     static constexpr int STAGES = ZS ? 2 : KD::STAGES;
     static constexpr int ZSLOT = KD::BK * BN * 8;   // Z row slices of one chunk (float2)
     static constexpr int YSLOT = KD::BK * 8;        // Y values of one chunk
@@ -142,6 +158,7 @@ template <int KIND, bool ZS> struct Cfg {
     static constexpr int KO_BYTES = ZS ? 0 : KD::KO_BYTES;
     static constexpr int SMEM_BYTES = STAGES * KD::STAGE + 1024 + BAR_BYTES + KO_BYTES + ZBYTES;
     static_assert(!ZS || KD::NP == 2, "Z staging is built for the two-piece kinds");
+    static_assert(!PF || KD::STAGE_KO, "the prefetching generators read staged k-offsets");
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
 
@@ -299,6 +316,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 lanes x 16 consecutive 32-bit columns from registers into TMEM.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 "
+        "[%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Splits one 16-byte vector worth of values into NP pieces (pieces[0] = hi).
 //   BF16: 8 values per vector; each piece rounds the remaining residual to BF16.
@@ -685,6 +718,74 @@ __device__ __forceinline__ bool drain_group(int gg, uint64_t *accFull, uint64_t 
     return true;
 }
 
+// VAR_PREFETCH: adds the finished accumulator group with global index gg
+// (the single MMA set, TMEM columns [0, 2 BN): Re then Im) to the running
+// sums in columns [2 BN, 4 BN), FP32 adds in registers, 16 columns of Re and
+// of Im at a time.  first: the sums start at +0 (0 + x, exactly as the
+// register sums of VAR_GATHER start).  The MMA set is released once read.
+template <int CQ>
+__device__ __forceinline__ bool drain_to_master(int gg, bool first, uint64_t *accFull, uint64_t *accEmpty,
+                                                uint32_t tmem, int lg, int lane, int colh) {
+    const bool got = mbar_wait(accFull, gg & 1);
+    if (__any_sync(0xffffffffu, !got)) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + colh;
+#pragma unroll
+    for (int cc = 0; cc < CQ; cc += 16) {
+        float wr[16], wi[16], mr[16], mi[16];
+        tmem_ld16(ta + cc, wr);
+        tmem_ld16(ta + BN + cc, wi);
+        if (!first) {
+            tmem_ld16(ta + 2 * BN + cc, mr);
+            tmem_ld16(ta + 3 * BN + cc, mi);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            mr[j] = (first ? 0.f : mr[j]) + wr[j];
+            mi[j] = (first ? 0.f : mi[j]) + wi[j];
+        }
+        tmem_st16(ta + 2 * BN + cc, mr);
+        tmem_st16(ta + 3 * BN + cc, mi);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(accEmpty);
+    tmem_wait_st();  // the sums are complete before this thread next reads them
+    return true;
+}
+
+// VAR_PREFETCH, last group of a tile: running sums (if any) plus the group,
+// into this thread's registers; the MMA set is released once read.
+template <int CQ>
+__device__ __forceinline__ bool drain_final(int gg, bool only, uint64_t *accFull, uint64_t *accEmpty, uint32_t tmem,
+                                            int lg, int lane, int colh, float (&acc_re)[CQ], float (&acc_im)[CQ]) {
+    const bool got = mbar_wait(accFull, gg & 1);
+    if (__any_sync(0xffffffffu, !got)) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + colh;
+#pragma unroll
+    for (int cc = 0; cc < CQ; cc += 16) {
+        float wr[16], wi[16], mr[16], mi[16];
+        tmem_ld16(ta + cc, wr);
+        tmem_ld16(ta + BN + cc, wi);
+        if (!only) {
+            tmem_ld16(ta + 2 * BN + cc, mr);
+            tmem_ld16(ta + 3 * BN + cc, mi);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            acc_re[cc + j] = (only ? 0.f : mr[j]) + wr[j];
+            acc_im[cc + j] = (only ? 0.f : mi[j]) + wi[j];
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(accEmpty);
+    return true;
+}
+
 // Bounded wait that also gives up once the CTA's abort flag is set.
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -718,12 +819,13 @@ __device__ __forceinline__ int ring_take(uint64_t *ifull, uint64_t *iempty, vola
 // are counted globally across items, so consecutive items pipeline without
 // re-initialisation.  Each tile's reduction order depends only on its own
 // job, never on the rest of the batch.
-template <int KIND, bool ZS>
+template <int KIND, int VAR>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_persistent_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items,
                          int drain_every, int *err, int *progress, int *queue) {
     using KD = Kind<KIND>;
-    using CF = Cfg<KIND, ZS>;
+    using CF = Cfg<KIND, VAR>;
+    constexpr bool ZS = CF::ZS, PF = CF::PF;
     constexpr bool TF32 = KD::TF32;
     constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = CF::STAGES;
     constexpr int ZSLOT = CF::ZSLOT, YSLOT = CF::YSLOT, ZSLOTS = CF::ZSLOTS;
@@ -881,9 +983,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ok = false;
                         break;
                     }
-                    const int gg = gbase + it / G, set = gg & 1;
+                    // groups alternate between the two TMEM sets; VAR_PREFETCH has
+                    // one set (the other holds the running sums), freed by every drain
+                    const int gg = gbase + it / G, set = PF ? 0 : gg & 1;
                     const bool first = (it % G) == 0;
-                    if (first && gg >= 2 && !mbar_wait(&accEmpty[set], ((gg - 2) >> 1) & 1)) {
+                    if (first && (PF ? gg >= 1 && !mbar_wait(&accEmpty[0], (gg - 1) & 1)
+                                     : gg >= 2 && !mbar_wait(&accEmpty[set], ((gg - 2) >> 1) & 1))) {
                         ok = false;
                         break;
                     }
@@ -967,41 +1072,191 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             const float2 *Yc = J.Y + iy;
             const float2 *Zc = J.Z + iz;
-            float acc_re[CQ], acc_im[CQ];
+            float acc_re[CQ], acc_im[CQ];  // the tile's sums (VAR_PREFETCH: filled by the last drain)
 #pragma unroll
-            for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
+                for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
             const int gc0 = gc;
             int drained = 0;
             const int2 *kofs = J.kofs + (size_t)k0 * BK + khalf * KH;
-            // Row offsets of this warp's k (independent of the A copy, so the
-            // gathers below overlap with the TMA instead of following it),
-            // staged one chunk ahead by asynchronous copies into shared memory.
-            if constexpr (KD::STAGE_KO && !ZS) {
+            if constexpr (PF) {
+                // Chunk it+1's table entries are gathered into the other
+                // register set before chunk it's W is formed; the k-offsets run
+                // two chunks ahead through this warp's two shared-memory buffers
+                // (buffer b holds chunk c with c & 1 == b).
+                float2 yv[2][KH], zv[2][KH];  // set it & 1 holds chunk it's entries
                 if (lane < KH) cp_async8(kobuf + lane, kofs + lane);
                 cp_async_commit();
-            }
-            for (int it = 0; it < nkc && ok; ++it, ++gc) {
-                const int s = gc % STAGES;
-                if constexpr (ZS) {
-                    // W from the staged Z slices and Y values of this chunk
-                    const int zs = gc % ZSLOTS;
-                    const bool w = mbar_wait(&zfull[zs], (gc / ZSLOTS) & 1) &&
-                                   (gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1));
+                if (nkc > 1 && lane < KH) cp_async8(kobuf + KH + lane, kofs + BK + lane);
+                cp_async_commit();
+                cp_async_wait<1>();  // chunk 0's records have landed
+                __syncwarp();
+#pragma unroll
+                for (int e = 0; e < KH; ++e) {
+                    const int2 k2 = kobuf[e];
+                    yv[0][e] = __ldg(Yc + k2.x);
+                    zv[0][e] = __ldg(Zc + k2.y);
+                }
+                __syncwarp();  // every lane has read buffer 0 before chunk 2's records overwrite it
+                for (int it0 = 0; it0 < nkc && ok; it0 += 2) {
+                    // two chunks per pass, so each names its register sets at compile time
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const int it = it0 + p;
+                        if (it < nkc && ok) {
+                        const int gcc = gc0 + it, s = gcc % STAGES;
+                        if (it + 2 < nkc && lane < KH)
+                            cp_async8(kobuf + p * KH + lane, kofs + (size_t)(it + 2) * BK + lane);
+                        cp_async_commit();
+                        cp_async_wait<1>();  // chunk it+1's records have landed
+                        __syncwarp();
+                        if (it + 1 < nkc) {
+                            const int2 *kb = kobuf + (p ^ 1) * KH;
+#pragma unroll
+                            for (int e = 0; e < KH; ++e) {
+                                const int2 k2 = kb[e];
+                                yv[p ^ 1][e] = __ldg(Yc + k2.x);
+                                zv[p ^ 1][e] = __ldg(Zc + k2.y);
+                            }
+                        }
+                        const bool w = gcc < STAGES || mbar_wait(&empty[s], ((gcc / STAGES) - 1) & 1);
+                        ok = !__any_sync(0xffffffffu, !w) && !*abort_flag;
+                        uint8_t *wst = smem + s * STAGE + A_STAGE;
+                        if (ok) {
+#pragma unroll
+                        for (int jv = 0; jv < KH / V; ++jv) {
+                            float re[V], im[V];
+#pragma unroll
+                            for (int e = 0; e < V; ++e) w_elem(yv[p][jv * V + e], zv[p][jv * V + e], re[e], im[e]);
+                            uint4 pr_[NP], pi_[NP];
+                            split_vec<KIND>(re, pr_);
+                            split_vec<KIND>(im, pi_);
+                            const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + jv * V);
+                            store_w<KIND>(wst, off, pr_, pi_);
+                        }
+                        fence_proxy_async_smem();
+                        __syncwarp();  // also: every lane has read buffer p ^ 1 before it is refilled
+                        if (lane == 0) mbar_arrive(&fullW[s]);
+                        // the first chunk of group gd+1 is in place: add group gd to the
+                        // sums as soon as its MMAs complete (the MMAs of group gd+1 wait for it)
+                        if (it > 0 && it % G == 0) {
+                            const int gd = it / G - 1;
+                            ok = drain_to_master<CQ>(gbase + gd, gd == 0, &accFull[0], &accEmpty[0], tmem, lg, lane,
+                                                     colh);
+                        }
+                        }
+                        }
+                    }
+                }
+                cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
+                __syncwarp();
+                if (ok && !drain_final<CQ>(gbase + ngroups - 1, ngroups == 1, &accFull[0], &accEmpty[0], tmem, lg,
+                                           lane, colh, acc_re, acc_im))
+                    ok = false;
+            } else {
+                // Row offsets of this warp's k (independent of the A copy, so the
+                // gathers below overlap with the TMA instead of following it),
+                // staged one chunk ahead by asynchronous copies into shared memory.
+                if constexpr (KD::STAGE_KO && !ZS) {
+                    if (lane < KH) cp_async8(kobuf + lane, kofs + lane);
+                    cp_async_commit();
+                }
+                for (int it = 0; it < nkc && ok; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    if constexpr (ZS) {
+                        // W from the staged Z slices and Y values of this chunk
+                        const int zs = gc % ZSLOTS;
+                        const bool w = mbar_wait(&zfull[zs], (gc / ZSLOTS) & 1) &&
+                                       (gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1));
+                        if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        const uint8_t *zb = zbase + zs * (ZSLOT + YSLOT);
+                        const float2 *zr = reinterpret_cast<const float2 *>(zb) + (size_t)(khalf * KH) * BN + wrow;
+                        const float2 *yv = reinterpret_cast<const float2 *>(zb + ZSLOT) + khalf * KH;
+                        uint8_t *wst = smem + s * STAGE + A_STAGE;
+#pragma unroll
+                        for (int sb = 0; sb < KH; sb += KSUB) {
+                            float2 y[KSUB], z[KSUB];
+#pragma unroll
+                            for (int e = 0; e < KSUB; ++e) {
+                                y[e] = yv[sb + e];
+                                z[e] = zr[(sb + e) * BN];
+                            }
+#pragma unroll
+                            for (int jv = 0; jv < KSUB / V; ++jv) {
+                                float re[V], im[V];
+#pragma unroll
+                                for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
+                                uint4 pr_[NP], pi_[NP];
+                                split_vec<KIND>(re, pr_);
+                                split_vec<KIND>(im, pi_);
+                                const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
+                                store_w<KIND>(wst, off, pr_, pi_);
+                            }
+                        }
+                        // W visible to the tensor core; the Z slot's reads done
+                        // before the stager's next bulk copy overwrites it
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&fullW[s]);
+                            mbar_arrive(&zempty[zs]);
+                        }
+                    } else if constexpr (KD::STAGE_KO) {
+                    // all KH table pairs of this chunk are requested at once (the
+                    // k-offsets come from this warp's shared-memory buffer, staged
+                    // one chunk ahead), before the wait for the stage
+                    if (it + 1 < nkc && lane < KH)
+                        cp_async8(kobuf + ((it + 1) & 1) * KH + lane, kofs + (size_t)(it + 1) * BK + lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();  // this chunk's records have landed
+                    __syncwarp();
+                    const int2 *kb = kobuf + (it & 1) * KH;
+                    float2 y[KH], z[KH];
+#pragma unroll
+                    for (int e = 0; e < KH; ++e) {
+                        const int2 k2 = kb[e];
+                        y[e] = __ldg(Yc + k2.x);
+                        z[e] = __ldg(Zc + k2.y);
+                    }
+                    const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
                     if (__any_sync(0xffffffffu, !w) || *abort_flag) {
                         ok = false;
                         break;
                     }
-                    const uint8_t *zb = zbase + zs * (ZSLOT + YSLOT);
-                    const float2 *zr = reinterpret_cast<const float2 *>(zb) + (size_t)(khalf * KH) * BN + wrow;
-                    const float2 *yv = reinterpret_cast<const float2 *>(zb + ZSLOT) + khalf * KH;
+                    uint8_t *wst = smem + s * STAGE + A_STAGE;
+#pragma unroll
+                    for (int jv = 0; jv < KH / V; ++jv) {
+                        float re[V], im[V];
+#pragma unroll
+                        for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
+                        uint4 pr_[NP], pi_[NP];
+                        split_vec<KIND>(re, pr_);
+                        split_vec<KIND>(im, pi_);
+                        const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + jv * V);
+                        store_w<KIND>(wst, off, pr_, pi_);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&fullW[s]);
+                    } else {
+                    int2 ko[KH];
+#pragma unroll
+                    for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
+                    const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
+                    if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
                     uint8_t *wst = smem + s * STAGE + A_STAGE;
 #pragma unroll
                     for (int sb = 0; sb < KH; sb += KSUB) {
                         float2 y[KSUB], z[KSUB];
 #pragma unroll
                         for (int e = 0; e < KSUB; ++e) {
-                            y[e] = yv[sb + e];
-                            z[e] = zr[(sb + e) * BN];
+                            y[e] = __ldg(Yc + ko[sb + e].x);
+                            z[e] = __ldg(Zc + ko[sb + e].y);
                         }
 #pragma unroll
                         for (int jv = 0; jv < KSUB / V; ++jv) {
@@ -1015,104 +1270,30 @@ __global__ void __launch_bounds__(THREADS, 1)
                             store_w<KIND>(wst, off, pr_, pi_);
                         }
                     }
-                    // W visible to the tensor core; the Z slot's reads done
-                    // before the stager's next bulk copy overwrites it
                     fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0) {
-                        mbar_arrive(&fullW[s]);
-                        mbar_arrive(&zempty[zs]);
+                    if (lane == 0) mbar_arrive(&fullW[s]);
                     }
-                } else if constexpr (KD::STAGE_KO) {
-                // all KH table pairs of this chunk are requested at once (the
-                // k-offsets come from this warp's shared-memory buffer, staged
-                // one chunk ahead), before the wait for the stage
-                if (it + 1 < nkc && lane < KH)
-                    cp_async8(kobuf + ((it + 1) & 1) * KH + lane, kofs + (size_t)(it + 1) * BK + lane);
-                cp_async_commit();
-                cp_async_wait<1>();  // this chunk's records have landed
-                __syncwarp();
-                const int2 *kb = kobuf + (it & 1) * KH;
-                float2 y[KH], z[KH];
-#pragma unroll
-                for (int e = 0; e < KH; ++e) {
-                    const int2 k2 = kb[e];
-                    y[e] = __ldg(Yc + k2.x);
-                    z[e] = __ldg(Zc + k2.y);
-                }
-                const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
-                if (__any_sync(0xffffffffu, !w) || *abort_flag) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *wst = smem + s * STAGE + A_STAGE;
-#pragma unroll
-                for (int jv = 0; jv < KH / V; ++jv) {
-                    float re[V], im[V];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
-                    uint4 pr_[NP], pi_[NP];
-                    split_vec<KIND>(re, pr_);
-                    split_vec<KIND>(im, pi_);
-                    const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + jv * V);
-                    store_w<KIND>(wst, off, pr_, pi_);
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&fullW[s]);
-                } else {
-                int2 ko[KH];
-#pragma unroll
-                for (int e = 0; e < KH; ++e) ko[e] = __ldg(kofs + (size_t)it * BK + e);
-                const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
-                if (__any_sync(0xffffffffu, !w) || *abort_flag) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *wst = smem + s * STAGE + A_STAGE;
-#pragma unroll
-                for (int sb = 0; sb < KH; sb += KSUB) {
-                    float2 y[KSUB], z[KSUB];
-#pragma unroll
-                    for (int e = 0; e < KSUB; ++e) {
-                        y[e] = __ldg(Yc + ko[sb + e].x);
-                        z[e] = __ldg(Zc + ko[sb + e].y);
-                    }
-#pragma unroll
-                    for (int jv = 0; jv < KSUB / V; ++jv) {
-                        float re[V], im[V];
-#pragma unroll
-                        for (int e = 0; e < V; ++e) w_elem(y[jv * V + e], z[jv * V + e], re[e], im[e]);
-                        uint4 pr_[NP], pi_[NP];
-                        split_vec<KIND>(re, pr_);
-                        split_vec<KIND>(im, pi_);
-                        const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + sb + jv * V);
-                        store_w<KIND>(wst, off, pr_, pi_);
+                    // Local group gd is complete once the MMAs of its last chunk
+                    // are; that is guaranteed STAGES chunks later, so drain it then
+                    // without stalling the tensor pipe.
+                    while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
+                        if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) {
+                            ok = false;
+                            break;
+                        }
+                        ++drained;
                     }
                 }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&fullW[s]);
+                if constexpr (KD::STAGE_KO && !ZS) {
+                    cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
+                    __syncwarp();
                 }
-                // Local group gd is complete once the MMAs of its last chunk
-                // are; that is guaranteed STAGES chunks later, so drain it then
-                // without stalling the tensor pipe.
-                while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
-                    if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im)) {
+                while (ok && drained < ngroups) {
+                    if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im))
                         ok = false;
-                        break;
-                    }
                     ++drained;
                 }
-            }
-            if constexpr (KD::STAGE_KO && !ZS) {
-                cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
-                __syncwarp();
-            }
-            while (ok && drained < ngroups) {
-                if (!drain_group<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, colh, acc_re, acc_im))
-                    ok = false;
-                ++drained;
             }
             gbase += ngroups;
             gc = gc0 + nkc;
@@ -1386,11 +1567,11 @@ static int band_bounds(const TcJobDev &jd, int requested, int grid, int64_t firs
                               kMaxBands, b);
 }
 
-template <int KIND, bool ZS>
+template <int KIND, int VAR>
 static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
                                 int grid_ctas, int64_t *launches, cudaStream_t st, int *progress, int *queue) {
     using namespace tc;
-    using CF = Cfg<KIND, ZS>;
+    using CF = Cfg<KIND, VAR>;
     static bool attr_set = false;
     cudaError_t e;
     if (!attr_set) {
@@ -1398,23 +1579,25 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
         // registers per thread at launch; anything else could leave the
         // increasing warpgroups waiting, so refuse to launch.
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, tc_persistent_kernel<KIND, ZS>);
+        e = cudaFuncGetAttributes(&fa, tc_persistent_kernel<KIND, VAR>);
         if (e != cudaSuccess) return e;
         if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
-        e = cudaFuncSetAttribute(tc_persistent_kernel<KIND, ZS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_persistent_kernel<KIND, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (n_items <= 0) return cudaSuccess;
     const int grid = std::max(1, std::min(grid_ctas, n_items));
-    tc_persistent_kernel<KIND, ZS><<<grid, THREADS, CF::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err,
+    tc_persistent_kernel<KIND, VAR><<<grid, THREADS, CF::SMEM_BYTES, st>>>(d_jobs, d_items, n_items, drain_every, err,
                                                                          progress, queue);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
-bool tc_zstage_preferred(int kind) { return kind == tc::KIND_TF32X2; }
+int tc_variant_preferred(int kind) { return kind == tc::KIND_TF32X2 ? 1 : 0; }
+
+bool tc_prefetch_ok(int kind) { return kind == tc::KIND_FP16X2 || kind == tc::KIND_BF16X2; }
 
 bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs) {
     if (kind == tc::KIND_BF16X3 || n_jobs <= 0) return false;
@@ -1423,7 +1606,17 @@ bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs) {
     return true;
 }
 
-cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
+int tc_variant_resolve(int kind, int requested, bool zstage_grid) {
+    if (requested == tc::VAR_ZSTAGE) return kind != tc::KIND_BF16X3 && zstage_grid ? tc::VAR_ZSTAGE : tc::VAR_GATHER;
+    if (requested == tc::VAR_PREFETCH) return tc_prefetch_ok(kind) ? tc::VAR_PREFETCH : tc::VAR_GATHER;
+    return tc::VAR_GATHER;
+}
+
+int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs) {
+    return tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
+}
+
+cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
                                  int drain_every, int *err, int grid_ctas, int64_t *launches, cudaStream_t st,
                                  int *progress, int *queue) {
     if (queue && n_items > 0) {
@@ -1434,12 +1627,17 @@ cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, 
     return with_kind(kind, [&](auto K) {
         constexpr int KIND = decltype(K)::value;
         if constexpr (KIND != tc::KIND_BF16X3) {
-            if (zstage)
-                return persistent_t<KIND, true>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
-                                                progress, queue);
+            if (variant == tc::VAR_ZSTAGE)
+                return persistent_t<KIND, tc::VAR_ZSTAGE>(d_jobs, d_items, n_items, drain_every, err, grid_ctas,
+                                                          launches, st, progress, queue);
         }
-        return persistent_t<KIND, false>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
-                                         progress, queue);
+        if constexpr (tc::Kind<KIND>::STAGE_KO) {
+            if (variant == tc::VAR_PREFETCH)
+                return persistent_t<KIND, tc::VAR_PREFETCH>(d_jobs, d_items, n_items, drain_every, err, grid_ctas,
+                                                            launches, st, progress, queue);
+        }
+        return persistent_t<KIND, tc::VAR_GATHER>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches,
+                                                  st, progress, queue);
     });
 }
 
@@ -1533,7 +1731,7 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
         for (int i = 0; i < grid * tc::GEN_WARPS; ++i) a.progress_host[i] = 0;
     }
     if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
-    e = tc_launch_persistent(a.kind, a.zstage && tc_zstage_ok(a.kind, &jd, 1), d_job, d_items, n_items,
+    e = tc_launch_persistent(a.kind, tc_variant_for(a.kind, a.zstage, &jd, 1), d_job, d_items, n_items,
                              a.drain_every, a.err, grid, launches, st, G > 1 ? a.progress_dev : nullptr);
     if (a.bands_used) *a.bands_used = G;
     if (e != cudaSuccess || G == 1) return e;
@@ -1678,7 +1876,7 @@ cudaError_t tc_run_generic_multi(const TcGenericArgs *jobs, int n_jobs, int64_t 
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    return tc_launch_persistent(a0.kind, false, d_jobs, d_items, (int)items.size(), a0.drain_every, a0.err,
+    return tc_launch_persistent(a0.kind, tc::VAR_GATHER, d_jobs, d_items, (int)items.size(), a0.drain_every, a0.err,
                                 tc_num_sms(), launches, st);
 }
 

@@ -115,12 +115,12 @@ extern "C" scff_status scff_set_tc_drain(scff_ctx *c, int drain_every) {
     return SCFF_OK;
 }
 
-// Whether a call in this precision asks for the Z-staging generator variant
-// (where the grid allows it): the context's mode, or the kind's default.
+// The W generator variant a call in this precision asks for (tc_variant_resolve
+// decides what the grid and kind allow): the context's mode, or the kind's default.
 int zstage_mode(const scff_ctx *c, int precision) {
     if (c->tc_zstage >= 0) return c->tc_zstage;
     const int k = tc_kind_of_precision(precision);
-    return k >= 0 && tc_zstage_preferred(k) ? 1 : 0;
+    return k >= 0 ? tc_variant_preferred(k) : 0;
 }
 
 extern "C" scff_status scff_last_path(scff_ctx *c, int32_t *out) {
@@ -131,7 +131,7 @@ extern "C" scff_status scff_last_path(scff_ctx *c, int32_t *out) {
 
 extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: NULL context");
-    if (mode < -1 || mode > 1) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
+    if (mode < -1 || mode > 2) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
     c->tc_zstage = mode;
     return SCFF_OK;
 }
@@ -779,7 +779,7 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
         if (ho) ho->done = used > 1;
         c->last_path[0] = 2;
         c->last_path[1] = precision;
-        c->last_path[2] = ta.zstage && g->nz % 128 == 0 && kind != 1 ? 1 : 0;
+        c->last_path[2] = tc_variant_resolve(kind, ta.zstage, g->nz % 128 == 0);
     } else {
         DirectArgs a;
         memset(&a, 0, sizeof(a));
@@ -850,9 +850,9 @@ static scff_status autotune(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, 
     // tensor cores with both W generator variants (bitwise the same results) unless the
     // context fixes one, then the FP32 direct path's state blocks
     const int kind = tc_kind_of_precision(precision);
-    const bool zs_can = kind >= 0 && kind != 1 && g->nz % 128 == 0;  // not BF16 hi/mid/lo; nz multiple of 128
-    for (int zs : {1, 0})
-        if ((c->tc_zstage < 0 || c->tc_zstage == zs) && (zs == 0 || zs_can)) cand.push_back({1, 8, 8, zs});
+    for (int zs : {2, 1, 0})
+        if ((c->tc_zstage < 0 || c->tc_zstage == zs) && kind >= 0 && tc_variant_resolve(kind, zs, g->nz % 128 == 0) == zs)
+            cand.push_back({1, 8, 8, zs});
     for (int sb : {8, 12, 16}) cand.push_back({0, 0, sb, 0});
     TRY(grow(c, c->fstage, (size_t)S * nq * 2 * rsz + 256));
     TRY(grow(c, c->f2stage, (size_t)S * nq * rsz + 256));
@@ -1300,7 +1300,7 @@ struct scff_plan_s {
     std::vector<std::vector<int>> groups;
     std::vector<size_t> group_desc, group_items;  // offsets in dev
     std::vector<int> group_nitems;
-    std::vector<char> group_zs;                   // group runs the Z-staging kernel variant
+    std::vector<char> group_zs;                   // W generator variant of each group's launch
     size_t off_queue = 0;                         // device int: the launches' work-queue counter
     void *dev = nullptr;
     size_t dev_bytes = 0;
@@ -1455,7 +1455,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
         tc_build_items(gdesc[g].data(), (int)gdesc[g].size(), gitems[g]);
         P->group_items[g] = ioff;
         P->group_nitems[g] = (int)gitems[g].size();
-        P->group_zs[g] = zstage_mode(c, precision) && tc_zstage_ok(P->tc_kind, gdesc[g].data(), (int)gdesc[g].size()) ? 1 : 0;
+        P->group_zs[g] = (char)tc_variant_for(P->tc_kind, zstage_mode(c, precision), gdesc[g].data(), (int)gdesc[g].size());
         ioff += up1k(sizeof(int4) * nitems_est[g]);
         cudaError_t e1 = cudaMemcpy(base + P->group_desc[g], gdesc[g].data(), sizeof(TcJobDev) * gdesc[g].size(),
                                     cudaMemcpyHostToDevice);
@@ -1469,7 +1469,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     }
     // Kernel attributes are set outside any later stream capture.
     for (size_t g = 0; g < P->groups.size(); ++g)
-        tc_launch_persistent(P->tc_kind, P->group_zs[g] != 0, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
+        tc_launch_persistent(P->tc_kind, P->group_zs[g], nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
     c->plans.push_back(P);
     *out = P;
     return SCFF_OK;
@@ -1512,7 +1512,7 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));
         }
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
-        CUDA_TRY(tc_launch_persistent(P->tc_kind, P->group_zs[g] != 0,
+        CUDA_TRY(tc_launch_persistent(P->tc_kind, P->group_zs[g],
                                       reinterpret_cast<const TcJobDev *>(base + P->group_desc[g]),
                                       reinterpret_cast<const int4 *>(base + P->group_items[g]), P->group_nitems[g],
                                       drain, c->d_err, tc_num_sms(), launches, st, nullptr,

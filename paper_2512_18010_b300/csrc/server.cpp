@@ -312,8 +312,8 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
         int64_t launches = 0;
         if (tc_launch_persistent(tc_kind_of(sv->precision),
-                                 zstage_mode(c, sv->precision) &&
-                                     tc_zstage_ok(tc_kind_of(sv->precision), descs.data(), (int)descs.size()),
+                                 tc_variant_for(tc_kind_of(sv->precision), zstage_mode(c, sv->precision), descs.data(),
+                                                (int)descs.size()),
                                  reinterpret_cast<const TcJobDev *>(desc_dev),
                                  reinterpret_cast<const int4 *>(desc_dev + up1k(sizeof(TcJobDev) * descs.size())),
                                  (int)items.size(), drain, d_err, tc_num_sms(), &launches, st, nullptr,
@@ -524,8 +524,8 @@ extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options
     }
     // tensor-core kernel attributes are set once, outside the server thread's launches
     if (tc_precision(sv->precision))
-        for (bool zs : {false, true})
-            tc_launch_persistent(tc_kind_of(sv->precision), zs, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
+        for (int v : {0, 1, 2})
+            tc_launch_persistent(tc_kind_of(sv->precision), v, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
     sv->th = std::thread(server_loop, sv);
     *out = sv;
     return SCFF_OK;

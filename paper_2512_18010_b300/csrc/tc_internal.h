@@ -31,7 +31,7 @@ struct TcArgs {
     int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo, 3: FP16 hi/lo
     double qabs[3];            // largest |q| of each axis (bounds of the FP16 kind's scaling)
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
-    int zstage;                // 1: the Z-staging generator variant where the grid allows it
+    int zstage;                // W generator variant requested (tc_variant_resolve): 0 gather, 1 Z staging, 2 prefetch
     // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
     // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
     int half;
@@ -117,22 +117,31 @@ int64_t tc_max_items(int64_t tiles);
 // progress (optional, e.g. host-mapped): progress[cta * 8 + w] = items that
 // generator warp w of CTA cta has finished (its outputs written and fenced
 // at system scope before the count); CTA b runs items b, b + grid, ...
-// zstage: launch the variant whose generators read Z and Y staged in shared
-// memory (tc_zstage_ok of the launch's jobs must hold).  Kernel attributes
-// are set on a call with n_items = 0, before any capture.
+// variant: the W generator variant (0 gather, 1 Z staging, 2 prefetch; see
+// tc_variant_resolve), which the launch's jobs and kind must allow.  Kernel
+// attributes are set on a call with n_items = 0, before any capture.
 // queue (optional, device int): CTAs take their items from this shared counter
 // (reset to zero on `st` before the launch) instead of the static sequence
 // blockIdx.x, blockIdx.x + grid, ...; progress reporting needs the static one.
-cudaError_t tc_launch_persistent(int kind, bool zstage, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
+cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
                                  int drain_every, int *err, int grid_ctas, int64_t *launches, cudaStream_t st,
                                  int *progress = nullptr, int *queue = nullptr);
 // Whether every job of a launch can use the Z-staging variant (two-piece
 // kinds, product grids whose nz is a multiple of 128).
 bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs);
-// Whether the automatic mode takes the Z-staging variant for a kind where it
-// can (measured: faster for TF32 hi/lo, slower for the 16-bit kinds, whose
-// wider stages leave room for only two Z slots).
-bool tc_zstage_preferred(int kind);
+// Whether a kind has the prefetching variant (the kinds that stage their
+// k-offsets: FP16 hi/lo and BF16 hi/lo).
+bool tc_prefetch_ok(int kind);
+// The variant a launch runs for a requested one: 1 (Z staging) where the kind
+// and every job's grid allow it (zstage_grid: tc_zstage_ok), 2 (prefetch)
+// where the kind has it, else 0 (gather).  All three form bitwise the same W
+// and add the same partial sums in the same order, so the choice never
+// changes a result.
+int tc_variant_resolve(int kind, int requested, bool zstage_grid);
+int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs);
+// The automatic mode's variant for a kind (measured fastest on the
+// 10-heavy-atom job): Z staging for TF32 hi/lo, gather for the 16-bit kinds.
+int tc_variant_preferred(int kind);
 int tc_num_sms();
 
 // Generic two-table contraction on the tensor cores (the spherical method):

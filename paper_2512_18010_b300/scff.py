@@ -18,6 +18,8 @@ from . import build as _build
 
 FP64, FP32, BF16X3, TF32X3, BF16X2, FP16X2 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3, "bf16x2": BF16X2, "fp16x2": FP16X2}
+# tensor-core W generator variants (scff_set_tc_zstage modes, scff_last_path's third entry)
+GEN_VARIANTS = {0: "gather", 1: "zstage", 2: "prefetch"}
 RENORM_CONTRACTED = 1
 PURE_D = 2   # d shells are the 5 real solid harmonics
 PURE_F = 4   # f shells are the 7 real solid harmonics
@@ -442,16 +444,20 @@ class Context:
 
     def last_path(self) -> dict:
         """The path the last form-factor call ran: direct FP64/FP32 or tensor cores, the precision of its
-        arithmetic, and whether the Z-staging generator variant ran."""
+        arithmetic, and the tensor-core W generator variant that ran (gather, zstage or prefetch; None
+        off the tensor cores)."""
         out = np.zeros(3, dtype=np.int32)
         _check(self.lib.scff_last_path(self.h, _p(out)))
         names = {v: k for k, v in PRECISIONS.items()}
-        return {"path": {0: "direct_fp64", 1: "direct_fp32", 2: "tensor_cores"}.get(int(out[0])),
-                "precision": names.get(int(out[1])), "zstage": bool(out[2] == 1)}
+        path = {0: "direct_fp64", 1: "direct_fp32", 2: "tensor_cores"}.get(int(out[0]))
+        return {"path": path, "precision": names.get(int(out[1])),
+                "variant": GEN_VARIANTS.get(int(out[2])) if path == "tensor_cores" else None}
 
     def set_tc_zstage(self, mode: int):
         """Tensor-core W generator variant: -1 automatic, 0 gather from global memory, 1 stage Z and Y
-        in shared memory where the grid allows it (bitwise the same results)."""
+        in shared memory where the grid allows it, 2 prefetch the next chunk's table entries with the
+        running sums in TMEM where the split kind allows it (FP16 hi/lo, BF16 hi/lo); all three give
+        bitwise the same results."""
         _check(self.lib.scff_set_tc_zstage(self.h, int(mode)))
 
     def separable_integral(self, basis: Basis, trans: Transitions, qx, wx, qy, wy, qz, wz,
