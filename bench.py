@@ -89,8 +89,9 @@ def parse():
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--precision", default="fp16x2", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1, 2],
-                    help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y, 2 prefetch")
+    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y, 2 prefetch, "
+                         "3 CTA pairs")
     ap.add_argument("--drain", type=int, default=-1,
                     help="tensor-core k-chunks per TMEM accumulation group (-1 = library default, 8)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
@@ -990,6 +991,7 @@ def main():
                 "data": "synthetic (seeded molecules, basis and transition matrices)",
                 "config": {"workload": desc, "precision": args.precision, "n_pairs": n_pair,
                            "monomial_rows": K, "vw_rows": Kvw, "autotune": choice,
+                           "generator_variant": path_used["variant"],
                            "l2": "flushed between timed steps (256 MB write)",
                            "hermitian_half": bool(half),
                            "parallelism": f"dp{world} (one job per rank)"},

@@ -304,7 +304,7 @@ scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
  * 2 tensor cores; out[1] = the scff_precision of its arithmetic (SCFF_FP32
  * when a tensor-core precision was asked for on an explicit q list, or when
  * the autotuner chose the FP32 direct path); out[2] = the W generator
- * variant the tensor-core kernel ran (0 gather, 1 Z staging, 2 prefetch; see
+ * variant the tensor-core kernel ran (0 gather, 1 Z staging, 2 prefetch, 3 CTA pairs; see
  * scff_set_tc_zstage), 0 off the tensor cores.  All -1 before the first
  * call. */
 scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
@@ -320,10 +320,14 @@ scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
  *   2 prefetch (FP16 hi/lo and BF16 hi/lo): the running sums live in tensor
  *     memory, and each generator thread gathers the next k-chunk's table
  *     entries while it forms the current chunk's W.
- * mode: -1 automatic (the default: Z staging for TF32 hi/lo, gather for the
- * 16-bit splits; with the autotuner on,
- * tuned per job shape over the variants the grid and split allow), 0, 1 or 2
- * to request one (a variant the grid or split does not allow runs as 0).  All
+ *   3 CTA pairs (FP16 hi/lo and BF16 hi/lo, product grids): two CTAs on two
+ *     SMs (a cluster) share each 256-row MMA (cta_group::2); each CTA holds
+ *     the A rows of its half and generates W for half of the tile's columns,
+ *     so every SM forms half as much W per unit of tensor work.
+ * mode: -1 automatic (the default: Z staging for TF32 hi/lo, CTA pairs for
+ * FP16 hi/lo and BF16 hi/lo, gather for BF16 hi/mid/lo; with the autotuner on,
+ * tuned per job shape over the variants the grid and split allow), 0, 1, 2 or
+ * 3 to request one (a variant the grid or split does not allow runs as 0).  All
  * variants form bitwise the same W and add the same partial sums in the same
  * order, so results do not depend on the choice.  Applies to calls, plans and
  * servers created after it. */
@@ -501,7 +505,7 @@ scff_status scff_screening_info(scff_ctx *ctx, scff_trans_h trans, scff_qgrid_h 
  * it, see scff_set_tc_drain).
  * scff_autotune_choice writes five values: out[0] = 1 tensor cores / 0 direct,
  * out[1] = drain, out[2] = state block, out[3] = best time in microseconds,
- * out[4] = the W generator variant chosen (scff_set_tc_zstage's modes 0-2). */
+ * out[4] = the W generator variant chosen (scff_set_tc_zstage's modes 0-3). */
 scff_status scff_set_autotune(scff_ctx *ctx, int enable);
 scff_status scff_autotune_choice(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
                                  scff_qgrid_h grid, int precision, int32_t *out);

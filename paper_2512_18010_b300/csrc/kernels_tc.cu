@@ -143,7 +143,7 @@ template <int KIND> struct Kind {
 //     latency overlaps the W work instead of preceding it.  The additions are
 //     the same, in the same order, as VAR_GATHER's, so both give bitwise the
 //     same tile.
-enum { VAR_GATHER = 0, VAR_ZSTAGE = 1, VAR_PREFETCH = 2 };
+enum { VAR_GATHER = 0, VAR_ZSTAGE = 1, VAR_PREFETCH = 2, VAR_PAIR = 3 };
 template <int KIND, int VAR> struct Cfg {
     using KD = Kind<KIND>;
     static constexpr bool ZS = VAR == VAR_ZSTAGE;
@@ -160,6 +160,31 @@ template <int KIND, int VAR> struct Cfg {
     static_assert(!ZS || KD::NP == 2, "Z staging is built for the two-piece kinds");
     static_assert(!PF || KD::STAGE_KO, "the prefetching generators read staged k-offsets");
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+};
+
+// CTA-pair launch (VAR_PAIR): a cluster of two CTAs on two SMs computes a
+// 256-row x 128-column tile with M = 256 MMAs (cta_group::2).  Each CTA holds
+// the A rows of its own 128-row half, and the B operand (W) is split along N:
+// each CTA generates W for 64 of the tile's 128 columns only, as
+// [-Wi | Wr | Wi] arrays of 64 rows, so that CTA r supplies the pair's B rows
+// [Wr | Wi] (and [-Wi | Wr]) of its columns.  D in each CTA's TMEM is then
+// [Re | Im] of columns 0-63 followed by [Re | Im] of columns 64-127, for the
+// CTA's own rows.  Per SM the MMA work per chunk is that of the single-CTA
+// kernel, and the W generation half of it.
+template <int KIND> struct PairCfg {
+    using KD = Kind<KIND>;
+    static constexpr int BNH = BN / 2;                     // W rows (complex columns) per CTA
+    static constexpr int W_ARRH = BNH * ROW_BYTES;         // one 64-row W array
+    static constexpr int W_STAGE = 3 * KD::NP * W_ARRH;
+    static constexpr int STAGE = KD::A_STAGE + W_STAGE;
+    static constexpr int STAGES = 4;
+    static constexpr int KQ = KD::BK / 4;                  // k per generator thread (four per W row)
+    static constexpr int KO_BYTES = GEN_WARPS * 2 * KQ * 8;
+    static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + BAR_BYTES + KO_BYTES;
+    static_assert(KD::FUSE && KD::STAGE_KO && !KD::TF32, "pairs are built for the 16-bit two-piece kinds");
+    static_assert(KQ == KD::PER_VEC, "one 16-byte vector per generator thread and chunk");
+    static_assert(4 * BNH == GEN_WARPS * 32, "four generator threads per W row");
+    static_assert(STAGES <= 4 && SMEM_BYTES <= 232448, "shared memory budget");
 };
 
 // Piece orders of the kept products (A piece, W piece).
@@ -234,10 +259,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
 // Instruction descriptor: D FP32, A and B of one format (FMT: 0 FP16 or
 // 1 BF16 under kind::f16, 2 TF32 under kind::tf32), both K-major, M = 128,
 // N = 128; bit 13 negates A.
-template <uint32_t FMT, int N = BN>
+template <uint32_t FMT, int N = BN, int M = BM>
 constexpr uint32_t idesc_mma(bool neg_a) {
     return (1u << 4) | (FMT << 7) | (FMT << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
+           ((uint32_t)(M >> 4) << 24);
 }
 
 // Stores one 16-byte vector of W pieces (real pr, imaginary pi) at byte
@@ -333,6 +358,95 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// ---- CTA pairs (a cluster of two CTAs on two SMs sharing each MMA)
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared-memory address of the same location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(const void *p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+
+// Arrives on an mbarrier of another CTA of the cluster (release at cluster
+// scope: this thread's earlier writes, shared or global, are visible to a
+// thread that observes the phase with an acquiring wait).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_s32(uint32_t cluster_addr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (as mbar_wait) acquiring at cluster scope, for barriers that
+// other CTAs of the cluster arrive on; also gives up once abort_flag is set.
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1; i < kWaitLimit; ++i) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if ((i & 15) == 0 && (*abort_flag || global_ns() - t0 > kWaitNs)) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMEM allocation shared by the pair: one warp of each CTA takes part.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// One MMA over the pair (issued by the even CTA): A rows 0-127 from CTA 0's
+// shared memory and 128-255 from CTA 1's at the same address, B's N rows
+// 0-127 from CTA 0 and 128-255 from CTA 1; each CTA's TMEM receives its own
+// 128 rows of D at tmem_d.
+__device__ __forceinline__ void mma_issue_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Arrives once on the mbarrier at this address in both CTAs of the pair when
+// the issuing thread's earlier MMAs have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
 // Splits one 16-byte vector worth of values into NP pieces (pieces[0] = hi).
 //   BF16: 8 values per vector; each piece rounds the remaining residual to BF16.
 //   TF32: 4 values per vector; hi = x with the 13 low mantissa bits cleared
@@ -417,7 +531,8 @@ static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     if (L.K_pad == 0) L.K_pad = BK;
     L.nkc = (int)(L.K_pad / BK);
     L.M = S * nx;
-    L.M_pad = (L.M + BM - 1) / BM * BM;
+    // sized for an even number of m-tiles, so a job can also be laid out for the CTA-pair launch
+    L.M_pad = (L.M + 2 * BM - 1) / (2 * BM) * (2 * BM);
     L.n_mt = L.M_pad / BM;
     L.N = (int64_t)ny * nz;
     L.n_nt = (int)((L.N + BN - 1) / BN);
@@ -784,6 +899,90 @@ __device__ __forceinline__ bool drain_final(int gg, bool only, uint64_t *accFull
     __syncwarp();
     if (lane == 0) mbar_arrive(accEmpty);
     return true;
+}
+
+// Writes one finished tile (this thread's row of the warp's region): a
+// part of a split tile stores its raw partial sums, and the last part of a
+// region to arrive sums all parts in part order; a whole tile (or the last
+// part) is scaled and written, with the mirrored row on antisymmetric grids.
+// pm, pr: parts and counters are indexed (tile * nsplit + part) * pm + pr and
+// tile * pm + pr (pm = 2, pr = CTA rank: the two halves of a CTA pair's tile).
+template <int KIND, int CQ>
+__device__ __forceinline__ void tile_epilogue(const TcJobDev &J, const int4 &item, int mt, int pm, int pr, bool ok,
+                                              int lg, int lane, int colh, int region, float (&acc_re)[CQ],
+                                              float (&acc_im)[CQ]) {
+    using KD = Kind<KIND>;
+    const int m = mt * BM + lg * 32 + lane;
+    const int slot = item_slot(item.x);
+    bool write = ok && m < J.M;
+    if (ok && slot >= 0) {
+        // part of a split tile: raw partial sums of this warp's region
+        const int row = lg * 32 + lane;
+        const int tile = slot / J.nsplit;
+        float2 *pp = J.part + ((size_t)((tile * J.nsplit + slot % J.nsplit) * pm + pr) * BM + row) * BN + colh;
+#pragma unroll
+        for (int j = 0; j < CQ; ++j) pp[j] = make_float2(acc_re[j], acc_im[j]);
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            int *c = J.cnt + (tile * pm + pr) * 8 + region;
+            last = atomicAdd(c, 1) == J.nsplit - 1;
+            if (last) *c = 0;  // ready for the next launch
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        write = write && last;
+        if (last) {
+            // every part of this region has landed: sum them in part order
+            __threadfence();
+            const int first = tile * J.nsplit;
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
+            for (int pt = 0; pt < J.nsplit; ++pt) {
+                const float2 *src = J.part + ((size_t)((first + pt) * pm + pr) * BM + row) * BN + colh;
+#pragma unroll
+                for (int j = 0; j < CQ; ++j) {
+                    const float2 v = __ldcg(src + j);
+                    acc_re[j] += v.x;
+                    acc_im[j] += v.y;
+                }
+            }
+        }
+    }
+    if (write) {
+        if constexpr (KD::FP16) {
+            // remove the job factor 2^G of the FP16 kind's scaled A
+            const int G = fp16_job_exp(J.tmax);
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) {
+                acc_re[j] = pow2_scale(acc_re[j], -G);
+                acc_im[j] = pow2_scale(acc_im[j], -G);
+            }
+        }
+        const int sidx = m / J.nx, ix = m % J.nx;
+        const int64_t n0 = (int64_t)item.z * BN + colh;
+        float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
+        float *f2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ix * J.N : nullptr;
+        const float sc = J.scale;
+        const int ixm = J.nxf - 1 - ix;  // mirror row (f(-q) = conj f(q))
+        const bool mir = J.mirror && ixm != ix;
+        float2 *mrow = J.f + (size_t)sidx * J.nq + (size_t)ixm * J.N;
+        float *m2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ixm * J.N : nullptr;
+#pragma unroll
+        for (int j = 0; j < CQ; ++j) {
+            const int64_t nn = n0 + j;
+            if (nn < J.N) {
+                const float2 v = make_float2(sc * acc_re[j], sc * acc_im[j]);
+                const float a2 = v.x * v.x + v.y * v.y;
+                frow[nn] = v;
+                if (f2row) f2row[nn] = a2;
+                if (mir) {
+                    mrow[J.N - 1 - nn] = make_float2(v.x, -v.y);
+                    if (m2row) m2row[J.N - 1 - nn] = a2;
+                }
+            }
+        }
+    }
 }
 
 // Bounded wait that also gives up once the CTA's abort flag is set.
@@ -1297,77 +1496,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             gbase += ngroups;
             gc = gc0 + nkc;
-            const int m = mt * BM + lg * 32 + lane;
-            const int slot = item_slot(item.x);
-            bool write = ok && m < J.M;
-            if (ok && slot >= 0) {
-                // part of a split tile: raw partial sums of this warp's region
-                const int row = lg * 32 + lane;
-                float2 *pp = J.part + ((size_t)slot * BM + row) * BN + colh;
-#pragma unroll
-                for (int j = 0; j < CQ; ++j) pp[j] = make_float2(acc_re[j], acc_im[j]);
-                __threadfence();
-                __syncwarp();
-                const int tile = slot / J.nsplit, region = warp - 4;
-                int last = 0;
-                if (lane == 0) {
-                    int *c = J.cnt + tile * 8 + region;
-                    last = atomicAdd(c, 1) == J.nsplit - 1;
-                    if (last) *c = 0;  // ready for the next launch
-                }
-                last = __shfl_sync(0xffffffffu, last, 0);
-                write = write && last;
-                if (last) {
-                    // every part of this region has landed: sum them in part order
-                    __threadfence();
-                    const int first = tile * J.nsplit;
-#pragma unroll
-                    for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
-                    for (int pt = 0; pt < J.nsplit; ++pt) {
-                        const float2 *src = J.part + ((size_t)(first + pt) * BM + row) * BN + colh;
-#pragma unroll
-                        for (int j = 0; j < CQ; ++j) {
-                            const float2 v = __ldcg(src + j);
-                            acc_re[j] += v.x;
-                            acc_im[j] += v.y;
-                        }
-                    }
-                }
-            }
-            if (write) {
-                if constexpr (KD::FP16) {
-                    // remove the job factor 2^G of the FP16 kind's scaled A
-                    const int G = fp16_job_exp(J.tmax);
-#pragma unroll
-                    for (int j = 0; j < CQ; ++j) {
-                        acc_re[j] = pow2_scale(acc_re[j], -G);
-                        acc_im[j] = pow2_scale(acc_im[j], -G);
-                    }
-                }
-                const int sidx = m / J.nx, ix = m % J.nx;
-                const int64_t n0 = (int64_t)item.z * BN + colh;
-                float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
-                float *f2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ix * J.N : nullptr;
-                const float sc = J.scale;
-                const int ixm = J.nxf - 1 - ix;  // mirror row (f(-q) = conj f(q))
-                const bool mir = J.mirror && ixm != ix;
-                float2 *mrow = J.f + (size_t)sidx * J.nq + (size_t)ixm * J.N;
-                float *m2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ixm * J.N : nullptr;
-#pragma unroll
-                for (int j = 0; j < CQ; ++j) {
-                    const int64_t nn = n0 + j;
-                    if (nn < J.N) {
-                        const float2 v = make_float2(sc * acc_re[j], sc * acc_im[j]);
-                        const float a2 = v.x * v.x + v.y * v.y;
-                        frow[nn] = v;
-                        if (f2row) f2row[nn] = a2;
-                        if (mir) {
-                            mrow[J.N - 1 - nn] = make_float2(v.x, -v.y);
-                            if (m2row) m2row[J.N - 1 - nn] = a2;
-                        }
-                    }
-                }
-            }
+            tile_epilogue<KIND, CQ>(J, item, mt, 1, 0, ok, lg, lane, colh, warp - 4, acc_re, acc_im);
             if (progress && ok) {
                 // publish how many items this warp has finished: its writes
                 // above reach memory (system scope) before the count does
@@ -1386,6 +1515,367 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------ CTA-pair kernel
+
+// A pair role's next work item (ring_take for clusters): the ring slot is
+// written and published by the even CTA; every consumer of either CTA frees
+// it on the even CTA's iempty barrier.
+__device__ __forceinline__ int ring_take_pair(uint64_t *ifull, uint64_t *iempty, volatile int *iring, int ic,
+                                              volatile int *abort_flag, int lane) {
+    const int r = ic % IRING;
+    const bool got = mbar_wait_cl(&ifull[r], (ic / IRING) & 1, abort_flag);
+    const int idx = got ? iring[r] : -2;
+    __syncwarp(__activemask());
+    if (got && lane == 0) mbar_arrive_cluster(mapa_shared(&iempty[r], 0));
+    return idx;
+}
+
+// Adds finished accumulator group gg (TMEM set gg & 1) into this thread's
+// register sums: row = TMEM lane, CQ columns of Re at column re0 of the set
+// and of Im at re0 + im_off; frees the set on the even CTA's accEmpty.
+template <int CQ>
+__device__ __forceinline__ bool drain_group_pair(int gg, uint64_t *accFull, uint64_t *accEmpty, uint32_t tmem,
+                                                 int lg, int lane, int re0, int im_off, float (&acc_re)[CQ],
+                                                 float (&acc_im)[CQ], volatile int *abort_flag) {
+    const int set = gg & 1;
+    const bool got = mbar_wait_abort(&accFull[set], (gg >> 1) & 1, abort_flag);
+    if (__any_sync(0xffffffffu, !got)) return false;
+    tc_fence_after();
+    const uint32_t ta = tmem + ((uint32_t)(lg * 32) << 16) + set * (2 * BN) + re0;
+#pragma unroll
+    for (int cc = 0; cc < CQ; cc += 32) {
+        float r0[16], r1[16], i0[16], i1[16];
+        tmem_ld16(ta + cc, r0);
+        tmem_ld16(ta + cc + 16, r1);
+        tmem_ld16(ta + im_off + cc, i0);
+        tmem_ld16(ta + im_off + cc + 16, i1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            acc_re[cc + j] += r0[j];
+            acc_re[cc + 16 + j] += r1[j];
+            acc_im[cc + j] += i0[j];
+            acc_im[cc + 16 + j] += i1[j];
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive_cluster(mapa_shared(&accEmpty[set], 0));
+    return true;
+}
+
+// Persistent kernel over CTA pairs (PairCfg).  Items are (job, m-tile pair,
+// n-tile) as for the single-CTA kernel, with the m field holding the pair
+// index mp: CTA r of the cluster computes rows of m-tile 2 mp + r.  Roles:
+//   even CTA: warp 0 lane 0 takes the items (queue counter or the static
+//     sequence cluster, cluster + clusters, ...), publishes each to both
+//     CTAs' item rings and bulk-copies its own A stages; warp 1 lane 0 issues
+//     the pair's MMAs once both CTAs' A and W stages have landed and commits
+//     to the stage and accumulator barriers of both CTAs;
+//   odd CTA: warp 0 lane 0 bulk-copies its A stages; warp 1 lane 0 relays
+//     each landed stage to the even CTA's fullA barrier;
+//   both: eight generator warps write the CTA's half of W (arriving on the
+//     even CTA's fullW) and drain the CTA's TMEM rows into registers (freeing
+//     a set on the even CTA's accEmpty), then write the CTA's half tile.
+// The per-tile arithmetic (W elements, MMA order, drain groups, sums) is the
+// single-CTA kernel's, so the two launches give bitwise the same results.
+template <int KIND>
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_pair_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items, int drain_every,
+                   int *err, int *progress, int *queue) {
+    using KD = Kind<KIND>;
+    using PC = PairCfg<KIND>;
+    constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = PC::STAGES, KQ = PC::KQ;
+    constexpr int A_STAGE = KD::A_STAGE, STAGE = PC::STAGE, W_ARRH = PC::W_ARRH, BNH = PC::BNH;
+    constexpr int CQ = BN / 2;  // accumulator columns (of Re and of Im) per drain thread
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+    uint64_t *fullA = bars + 0;     // [STAGES] A stage landed (even CTA: both CTAs' stages)
+    uint64_t *fullW = bars + 4;     // [STAGES] (even CTA) W stage written by both CTAs' generators
+    uint64_t *empty = bars + 8;     // [STAGES] MMAs of the stage completed (both CTAs)
+    uint64_t *accFull = bars + 12;  // [2] accumulator set holds a finished group (both CTAs)
+    uint64_t *accEmpty = bars + 14; // [2] (even CTA) accumulator set drained in both CTAs
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 17);
+    uint64_t *ifull = bars + 20;    // [IRING] item published
+    uint64_t *iempty = bars + 24;   // [IRING] (even CTA) every role of both CTAs has read it
+    volatile int *iring = reinterpret_cast<volatile int *>(bars + 28);
+    int2 *kobuf_all = reinterpret_cast<int2 *>(smem + STAGES * STAGE + BAR_BYTES);
+
+    const uint32_t rank = cluster_rank();
+    const bool lead = rank == 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t cid, ncl;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(ncl));
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&fullA[s], 1);
+            // even CTA: its generator warps and the odd CTA's relay (A and W of the odd CTA landed)
+            mbar_init(&fullW[s], GEN_WARPS + (lead ? 1 : 0));
+            mbar_init(&empty[s], 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(&accFull[j], 1);
+            mbar_init(&accEmpty[j], 2 * GEN_WARPS);
+        }
+        for (int r = 0; r < IRING; ++r) {
+            mbar_init(&ifull[r], 1);
+            // consumers: even CTA MMA thread + generators, odd CTA copier + relay + generators
+            mbar_init(&iempty[r], (1 + GEN_WARPS) + (2 + GEN_WARPS));
+        }
+        *abort_flag = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 0) tmem_alloc_pair(tmem_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // barriers of both CTAs initialised and TMEM allocated before any remote access
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(LOW_REGS));
+        if (warp == 0 && lane == 0) {
+            // ---------------- items (even CTA) and this CTA's A stages
+            int gc = 0;
+            for (int ic = 0;; ++ic) {
+                int idx;
+                if (lead) {
+                    const int r = ic % IRING;
+                    if (ic >= IRING && !mbar_wait_cl(&iempty[r], ((ic / IRING) - 1) & 1, abort_flag)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    idx = queue ? atomicAdd(queue, 1) : (int)(cid + (uint32_t)ic * ncl);
+                    if (idx >= n_items || *abort_flag) idx = -1;
+                    iring[r] = idx;
+                    st_cluster_s32(mapa_shared((const void *)&iring[r], 1), idx);
+                    mbar_arrive(&ifull[r]);
+                    mbar_arrive_cluster(mapa_shared(&ifull[r], 1));
+                } else {
+                    idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, 0);
+                    if (idx == -2) *abort_flag = 1;
+                }
+                if (idx < 0) break;
+                const int4 item = items[idx];
+                const TcJobDev &J = jobs[item_job(item.x)];
+                const int mt = 2 * item_mt(item.y) + (int)rank;
+                const uint8_t *Abase = J.A + ((size_t)mt * J.nkc + item_k0(item.y)) * A_STAGE;
+                for (int it = 0; it < item.w; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    if (gc >= STAGES && !mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&fullA[s], A_STAGE);
+                    bulk_g2s(smem + s * STAGE, Abase + (size_t)it * A_STAGE, A_STAGE, &fullA[s]);
+                }
+                if (*abort_flag) break;
+            }
+            // the copies of the last stages have landed before the CTA may exit
+            for (int c = max(0, gc - STAGES); c < gc; ++c)
+                mbar_wait_n(&fullA[c % STAGES], (c / STAGES) & 1, kWaitLimit);
+        } else if (warp == 1 && lane == 0 && !lead) {
+            // ---------------- odd CTA: once a stage's A has landed and its W is
+            // written, one release arrival on the even CTA's fullW covers both
+            int gc = 0;
+            bool ok = true;
+            for (int ic = 0; ok; ++ic) {
+                const int idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, 0);
+                if (idx == -2) ok = false;
+                if (idx < 0) break;
+                const int nkc = items[idx].w;
+                for (int it = 0; it < nkc; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    const uint32_t par = (gc / STAGES) & 1;
+                    if (*abort_flag || !mbar_wait_abort(&fullA[s], par, abort_flag) ||
+                        !mbar_wait_abort(&fullW[s], par, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_shared(&fullW[s], 0));
+                }
+            }
+            if (!ok) *abort_flag = 1;
+        } else if (warp == 1 && lane == 0) {
+            // ---------------- even CTA: MMA issuer for the pair
+            constexpr uint32_t ID2 = idesc_mma<KD::FMT, 2 * BN, 2 * BM>(false);  // M = 256, N = 256
+            int gc = 0, gbase = 0;
+            for (int ic = 0;; ++ic) {
+                const int idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, 0);
+                if (idx == -2) *abort_flag = 1;
+                if (idx < 0) break;
+                const int nkc = items[idx].w;
+                const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
+                bool ok = true;
+                for (int it = 0; it < nkc; ++it, ++gc) {
+                    const int s = gc % STAGES;
+                    const uint32_t par = (gc / STAGES) & 1;
+                    if (*abort_flag || !mbar_wait_abort(&fullA[s], par, abort_flag) ||
+                        !mbar_wait_cl(&fullW[s], par, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const int gg = gbase + it / G, set = gg & 1;
+                    const bool first = (it % G) == 0;
+                    if (first && gg >= 2 && !mbar_wait_cl(&accEmpty[set], ((gg - 2) >> 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t t_d = tmem + set * (2 * BN);
+                    const uint32_t a0 = smem_u32(smem + s * STAGE);
+                    const uint32_t w0 = a0 + A_STAGE;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t ko = kk * 32;  // 32 bytes = one MMA K step
+#pragma unroll
+                        for (int pq = 0; pq < KD::NPROD; ++pq) {
+                            const int qa = prod_a(pq), qw = prod_w(pq);
+                            const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
+                            const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
+                            const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
+                            const uint32_t pb = w0 + qw * 3 * W_ARRH + ko;
+                            mma_issue_pair(t_d, ar, smem_desc_sw64(pb + W_ARRH), ID2, acc);  // += [Ar Wr | Ar Wi] per half
+                            mma_issue_pair(t_d, ai, smem_desc_sw64(pb), ID2, 1);             // += [-Ai Wi | Ai Wr]
+                        }
+                    }
+                    mma_commit_pair(&empty[s]);
+                    if ((it % G) == G - 1 || it == nkc - 1) mma_commit_pair(&accFull[set]);
+                }
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                gbase += (nkc + G - 1) / G;
+            }
+        }
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(HIGH_REGS));
+        // ---------------- W generators (four threads per W row of this CTA's
+        // half), accumulator drains and the half tile's epilogue
+        const int gt = threadIdx.x - 128;   // 0..255
+        const int wrow = gt & (BNH - 1);    // W row: column n0 + rank * BNH + wrow
+        const int kq = gt / BNH;            // quarter of the chunk's k (one per warp)
+        const int lg = warp & 3;            // TMEM lane group of the drains
+        const int hsel = (warp - 4) >> 2;   // column half of the drains
+        int2 *kobuf = kobuf_all + (warp - 4) * 2 * KQ;
+        int gc = 0, gbase = 0, done_items = 0;
+        bool ok = true;
+        for (int ic = 0; ok; ++ic) {
+            const int idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, lane);
+            if (idx == -2) ok = false;
+            if (idx < 0) break;
+            const int4 item = items[idx];
+            const TcJobDev &J = jobs[item_job(item.x)];
+            const int nkc = item.w;
+            const int mp = item_mt(item.y), k0 = item_k0(item.y);
+            const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
+            const int ngroups = (nkc + G - 1) / G;
+            const int64_t n = (int64_t)item.z * BN + rank * BNH + wrow;
+            int iy = 0, iz = 0;
+            if (n < J.N) {
+                iz = (int)(n % J.nz);
+                iy = (int)(n / J.nz);
+            }
+            const float2 *Yc = J.Y + iy;
+            const float2 *Zc = J.Z + iz;
+            float acc_re[CQ], acc_im[CQ];
+#pragma unroll
+            for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
+            const int gc0 = gc;
+            int drained = 0;
+            const int2 *kofs = J.kofs + (size_t)k0 * BK + kq * KQ;
+            if (lane < KQ) cp_async8(kobuf + lane, kofs + lane);
+            cp_async_commit();
+            for (int it = 0; it < nkc && ok; ++it, ++gc) {
+                const int s = gc % STAGES;
+                if (it + 1 < nkc && lane < KQ)
+                    cp_async8(kobuf + ((it + 1) & 1) * KQ + lane, kofs + (size_t)(it + 1) * BK + lane);
+                cp_async_commit();
+                cp_async_wait<1>();  // this chunk's records have landed
+                __syncwarp();
+                const int2 *kb = kobuf + (it & 1) * KQ;
+                float2 y[KQ], z[KQ];
+#pragma unroll
+                for (int e = 0; e < KQ; ++e) {
+                    const int2 k2 = kb[e];
+                    y[e] = __ldg(Yc + k2.x);
+                    z[e] = __ldg(Zc + k2.y);
+                }
+                const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
+                if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *wst = smem + s * STAGE + A_STAGE;
+                {
+                    float re[V], im[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) w_elem(y[e], z[e], re[e], im[e]);
+                    uint4 pr_[NP], pi_[NP];
+                    split_vec<KIND>(re, pr_);
+                    split_vec<KIND>(im, pi_);
+                    const uint32_t off = sw64_offset<KIND>(wrow, kq * KQ);
+                    constexpr uint32_t SGN = 0x80008000u;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        uint8_t *pb = wst + q * 3 * W_ARRH + off;
+                        *reinterpret_cast<uint4 *>(pb) =
+                            make_uint4(pi_[q].x ^ SGN, pi_[q].y ^ SGN, pi_[q].z ^ SGN, pi_[q].w ^ SGN);
+                        *reinterpret_cast<uint4 *>(pb + W_ARRH) = pr_[q];
+                        *reinterpret_cast<uint4 *>(pb + 2 * W_ARRH) = pi_[q];
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&fullW[s]);  // the odd CTA's relay forwards it
+                while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
+                    if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, hsel * 2 * BNH,
+                                              BNH, acc_re, acc_im, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ++drained;
+                }
+            }
+            cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
+            __syncwarp();
+            while (ok && drained < ngroups) {
+                if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, hsel * 2 * BNH, BNH,
+                                          acc_re, acc_im, abort_flag))
+                    ok = false;
+                ++drained;
+            }
+            gbase += ngroups;
+            gc = gc0 + nkc;
+            tile_epilogue<KIND, CQ>(J, item, 2 * mp + (int)rank, 2, (int)rank, ok, lg, lane, hsel * CQ, warp - 4,
+                                    acc_re, acc_im);
+            if (progress && ok) {
+                // items this warp has finished (static schedule: cluster c runs c, c + clusters, ...),
+                // its writes above visible at system scope before the count
+                __threadfence_system();
+                __syncwarp();
+                ++done_items;
+                if (lane == 0)
+                    *reinterpret_cast<volatile int *>(progress + blockIdx.x * GEN_WARPS + (warp - 4)) = done_items;
+            }
+        }
+        if (!ok) *abort_flag = 1;
+    }
+    if (threadIdx.x == 0 && *abort_flag) flag_error(err, kDevErrTimeout);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // no CTA leaves while the other may still reach its shared memory or TMEM
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, TMEM_COLS);
     }
 }
 
@@ -1428,8 +1918,9 @@ static tc::Layout job_layout(const TcArgs &a) {
     using namespace tc;
     Layout L = make_layout_k<KIND>(*a.ps, a.S, a.nx, a.ny, a.nz);
     const int nxr = a.half ? (a.nx + 1) / 2 : a.nx;
+    const int mq = a.pair ? 2 * BM : BM;  // pairs: an even number of m-tiles (the last may be all padding)
     L.M = a.S * nxr;
-    L.M_pad = (L.M + BM - 1) / BM * BM;
+    L.M_pad = (L.M + mq - 1) / mq * mq;
     L.n_mt = L.M_pad / BM;
     return L;
 }
@@ -1459,7 +1950,9 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->mirror = a.half;
     jd->nxf = a.nx;
     int R = 0, sp = 0;
-    tail_split(L.n_mt * L.n_nt, L.nkc, tc_num_sms(), &R, &sp);
+    if (a.pair) tail_split((L.n_mt / 2) * L.n_nt, L.nkc, tc_num_pairs(), &R, &sp);
+    else tail_split(L.n_mt * L.n_nt, L.nkc, tc_num_sms(), &R, &sp);
+    jd->pair = a.pair ? 1 : 0;
     jd->part = reinterpret_cast<float2 *>(w + L.off_part);
     jd->cnt = reinterpret_cast<int *>(w + L.off_cnt);
     jd->nsplit = sp;
@@ -1551,7 +2044,8 @@ void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) 
     for (int j = 0; j < n_jobs; ++j) {
         const TcJobDev &J = jobs[j];
         tiles.clear();
-        for (int i = 0; i < J.n_mt * J.n_nt; ++i) tiles.push_back(make_int2(i / J.n_nt, i % J.n_nt));
+        const int n_rows = J.pair ? J.n_mt / 2 : J.n_mt;  // m-tiles, or m-tile pairs
+        for (int i = 0; i < n_rows * J.n_nt; ++i) tiles.push_back(make_int2(i / J.n_nt, i % J.n_nt));
         append_items(J, j, tiles, items);
     }
     // longest first; the stable order keeps each job's tiles row-major and its parts last
@@ -1560,12 +2054,6 @@ void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) 
 
 using sched::band_runs;
 
-// Band boundaries of one job's overlapped download (sched::band_bounds).
-static int band_bounds(const TcJobDev &jd, int requested, int grid, int64_t first_split, int nsplit,
-                       int b[kMaxBands + 1]) {
-    return sched::band_bounds(jd.n_mt, jd.n_nt, jd.mirror != 0, jd.N, tc::BN, requested, grid, first_split, nsplit,
-                              kMaxBands, b);
-}
 
 template <int KIND, int VAR>
 static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
@@ -1595,7 +2083,75 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
     return cudaGetLastError();
 }
 
-int tc_variant_preferred(int kind) { return kind == tc::KIND_TF32X2 ? 1 : 0; }
+// CTA-pair launch: grid = 2 x pairs, clusters of two CTAs.
+template <int KIND>
+static cudaError_t pair_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
+                          int grid_ctas, int64_t *launches, cudaStream_t st, int *progress, int *queue) {
+    using namespace tc;
+    using PC = PairCfg<KIND>;
+    static bool attr_set = false;
+    cudaError_t e;
+    if (!attr_set) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, tc_pair_kernel<KIND>);
+        if (e != cudaSuccess) return e;
+        if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
+        e = cudaFuncSetAttribute(tc_pair_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (n_items <= 0) return cudaSuccess;
+    const int pairs = std::max(1, std::min(std::min(grid_ctas / 2, tc_num_pairs()), n_items));
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(2 * pairs, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = PC::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, tc_pair_kernel<KIND>, d_jobs, d_items, n_items, drain_every, err, progress, queue);
+    if (launches) ++*launches;
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+int tc_num_pairs() {
+    static int n = 0;
+    if (!n) {
+        // the pair kernels of both kinds have the same footprint (one CTA per SM)
+        using PC = tc::PairCfg<tc::KIND_FP16X2>;
+        cudaFuncSetAttribute(tc::tc_pair_kernel<tc::KIND_FP16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PC::SMEM_BYTES);
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(2 * 1024, 1, 1);
+        cfg.blockDim = dim3(tc::THREADS, 1, 1);
+        cfg.dynamicSmemBytes = PC::SMEM_BYTES;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, tc::tc_pair_kernel<tc::KIND_FP16X2>, &cfg) != cudaSuccess || c <= 0) {
+            cudaGetLastError();
+            c = tc_num_sms() / 2;
+        }
+        n = std::min(c, tc_num_sms() / 2);
+    }
+    return n;
+}
+
+int tc_variant_preferred(int kind) {
+    return kind == tc::KIND_TF32X2 ? tc::VAR_ZSTAGE : tc_prefetch_ok(kind) ? tc::VAR_PAIR : tc::VAR_GATHER;
+}
 
 bool tc_prefetch_ok(int kind) { return kind == tc::KIND_FP16X2 || kind == tc::KIND_BF16X2; }
 
@@ -1609,11 +2165,17 @@ bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs) {
 int tc_variant_resolve(int kind, int requested, bool zstage_grid) {
     if (requested == tc::VAR_ZSTAGE) return kind != tc::KIND_BF16X3 && zstage_grid ? tc::VAR_ZSTAGE : tc::VAR_GATHER;
     if (requested == tc::VAR_PREFETCH) return tc_prefetch_ok(kind) ? tc::VAR_PREFETCH : tc::VAR_GATHER;
+    if (requested == tc::VAR_PAIR) return tc_prefetch_ok(kind) ? tc::VAR_PAIR : tc::VAR_GATHER;
     return tc::VAR_GATHER;
 }
 
 int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs) {
-    return tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
+    // jobs laid out for pairs run the pair launch; others never do
+    bool pair = n_jobs > 0;
+    for (int j = 0; j < n_jobs; ++j) pair = pair && jobs[j].pair && !jobs[j].ylm;
+    if (pair) return tc::VAR_PAIR;
+    const int v = tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
+    return v == tc::VAR_PAIR ? tc::VAR_GATHER : v;
 }
 
 cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
@@ -1630,6 +2192,11 @@ cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, 
             if (variant == tc::VAR_ZSTAGE)
                 return persistent_t<KIND, tc::VAR_ZSTAGE>(d_jobs, d_items, n_items, drain_every, err, grid_ctas,
                                                           launches, st, progress, queue);
+        }
+        if constexpr (tc::Kind<KIND>::STAGE_KO && !tc::Kind<KIND>::TF32) {
+            if (variant == tc::VAR_PAIR)
+                return pair_t<KIND>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress,
+                                    queue);
         }
         if constexpr (tc::Kind<KIND>::STAGE_KO) {
             if (variant == tc::VAR_PREFETCH)
@@ -1679,22 +2246,31 @@ int tc_num_sms() {
 // With host outputs and bands, the tiles are ordered band by band, the launch
 // reports its progress, and each band's columns are copied to the host while
 // later bands compute (see TcArgs).
-cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream_t st) {
+cudaError_t launch_tc_form_factor(const TcArgs &args, int64_t *launches, cudaStream_t st) {
     using tc::BN;
+    const bool can_band =
+        args.f_host && args.copy_st && args.progress_dev && args.progress_host && args.ev_done && args.ev_copied;
+    TcArgs a = args;
+    a.pair = tc_variant_resolve(a.kind, a.zstage, false) == tc::VAR_PAIR ? 1 : 0;
     const size_t jb = tc_job_bytes(*a.ps, a.S, a.nx, a.ny, a.nz, a.kind);
     if (jb + 1024 + sizeof(TcJobDev) > a.ws_bytes) return cudaErrorInvalidValue;
     TcJobDev jd;
     memset(&jd, 0, sizeof(jd));
     cudaError_t e = tc_prep_job(a, a.ws, &jd, launches, st);
     if (e != cudaSuccess) return e;
-    const bool can_band = a.f_host && a.copy_st && a.progress_dev && a.progress_host && a.ev_done && a.ev_copied;
     // the job's tail split (job_desc_t) covers its last split_tiles tiles in any order
-    const int64_t n_tiles = (int64_t)jd.n_mt * jd.n_nt;
+    const int64_t n_tiles = (int64_t)(jd.pair ? jd.n_mt / 2 : jd.n_mt) * jd.n_nt;
     const int64_t first_split = jd.nsplit ? n_tiles - jd.split_tiles : n_tiles;
     const int64_t n_items_all = first_split + (n_tiles - first_split) * (jd.nsplit ? jd.nsplit : 1);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tc_num_sms(), n_items_all));
+    // units that take items in turn: CTAs, or CTA pairs (two CTAs per unit)
+    const int per = a.pair ? 2 : 1;
+    const int units = (int)std::max<int64_t>(1, std::min<int64_t>(a.pair ? tc_num_pairs() : tc_num_sms(), n_items_all));
+    const int grid = per * units;
+    const int n_rows = jd.n_mt / per;  // m-tiles, or m-tile pairs
     int bounds[kMaxBands + 1];
-    const int G = can_band ? band_bounds(jd, a.n_bands, grid, first_split, jd.nsplit, bounds) : 1;
+    const int G = can_band ? sched::band_bounds(n_rows, jd.n_nt, jd.mirror != 0, jd.N, BN, a.n_bands, units,
+                                                first_split, jd.nsplit, kMaxBands, bounds)
+                           : 1;
     std::vector<int4> items;
     int runs[kMaxBands][2][2], nruns[kMaxBands];
     int64_t band_end[kMaxBands];
@@ -1705,7 +2281,7 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
         std::vector<int2> tiles;
         for (int g = 0; g < G; ++g) {
             nruns[g] = band_runs(jd.n_nt, jd.mirror != 0, bounds[g], bounds[g + 1], runs[g]);
-            for (int mt = 0; mt < jd.n_mt; ++mt)
+            for (int mt = 0; mt < n_rows; ++mt)
                 for (int r = 0; r < nruns[g]; ++r)
                     for (int nt = runs[g][r][0]; nt < runs[g][r][1]; ++nt) tiles.push_back(make_int2(mt, nt));
             const int64_t t = (int64_t)tiles.size();
@@ -1731,19 +2307,23 @@ cudaError_t launch_tc_form_factor(const TcArgs &a, int64_t *launches, cudaStream
         for (int i = 0; i < grid * tc::GEN_WARPS; ++i) a.progress_host[i] = 0;
     }
     if (a.ev_mark) cudaEventRecord(a.ev_mark, st);
-    e = tc_launch_persistent(a.kind, tc_variant_for(a.kind, a.zstage, &jd, 1), d_job, d_items, n_items,
+    const int variant = tc_variant_for(a.kind, a.zstage, &jd, 1);
+    if (a.variant_used) *a.variant_used = variant;
+    e = tc_launch_persistent(a.kind, variant, d_job, d_items, n_items,
                              a.drain_every, a.err, grid, launches, st, G > 1 ? a.progress_dev : nullptr);
     if (a.bands_used) *a.bands_used = G;
     if (e != cudaSuccess || G == 1) return e;
     if ((e = cudaEventRecord(a.ev_done, st)) != cudaSuccess) return e;
-    // CTA b runs items b, b + grid, ...: items [0, E) are written once each of
-    // its generator warps has finished ceil((E - b) / grid) items (a split
-    // tile's last part writes the tile before it counts itself)
+    // unit b (a CTA, or the CTA pair 2b, 2b + 1) runs items b, b + units, ...:
+    // items [0, E) are written once each generator warp of the unit has
+    // finished ceil((E - b) / units) items (a split tile's last part writes
+    // the tile before it counts itself)
     auto written = [&](int64_t E) {
-        for (int b = 0; b < grid && b < E; ++b) {
-            const int need = (int)((E - b + grid - 1) / grid);
-            for (int w = 0; w < tc::GEN_WARPS; ++w)
-                if (a.progress_host[b * tc::GEN_WARPS + w] < need) return false;
+        for (int b = 0; b < units && b < E; ++b) {
+            const int need = (int)((E - b + units - 1) / units);
+            for (int c = per * b; c < per * (b + 1); ++c)
+                for (int w = 0; w < tc::GEN_WARPS; ++w)
+                    if (a.progress_host[c * tc::GEN_WARPS + w] < need) return false;
         }
         return true;
     };

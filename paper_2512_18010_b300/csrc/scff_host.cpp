@@ -131,7 +131,7 @@ extern "C" scff_status scff_last_path(scff_ctx *c, int32_t *out) {
 
 extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: NULL context");
-    if (mode < -1 || mode > 2) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
+    if (mode < -1 || mode > 3) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
     c->tc_zstage = mode;
     return SCFF_OK;
 }
@@ -775,11 +775,13 @@ static scff_status ff_run(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, sc
             ta.ev_copied = c->band_ev[1];
             ta.bands_used = &used;
         }
+        int variant_used = 0;
+        ta.variant_used = &variant_used;
         CUDA_TRY(launch_tc_form_factor(ta, &c->launches, st));
         if (ho) ho->done = used > 1;
         c->last_path[0] = 2;
         c->last_path[1] = precision;
-        c->last_path[2] = tc_variant_resolve(kind, ta.zstage, g->nz % 128 == 0);
+        c->last_path[2] = variant_used;
     } else {
         DirectArgs a;
         memset(&a, 0, sizeof(a));
@@ -850,7 +852,7 @@ static scff_status autotune(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, 
     // tensor cores with both W generator variants (bitwise the same results) unless the
     // context fixes one, then the FP32 direct path's state blocks
     const int kind = tc_kind_of_precision(precision);
-    for (int zs : {2, 1, 0})
+    for (int zs : {3, 2, 1, 0})
         if ((c->tc_zstage < 0 || c->tc_zstage == zs) && kind >= 0 && tc_variant_resolve(kind, zs, g->nz % 128 == 0) == zs)
             cand.push_back({1, 8, 8, zs});
     for (int sb : {8, 12, 16}) cand.push_back({0, 0, sb, 0});
@@ -1301,6 +1303,7 @@ struct scff_plan_s {
     std::vector<size_t> group_desc, group_items;  // offsets in dev
     std::vector<int> group_nitems;
     std::vector<char> group_zs;                   // W generator variant of each group's launch
+    int pair = 0;                                 // jobs laid out for the CTA-pair launch
     size_t off_queue = 0;                         // device int: the launches' work-queue counter
     void *dev = nullptr;
     size_t dev_bytes = 0;
@@ -1329,6 +1332,8 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     P->ctx = c;
     P->precision = precision;
     P->tc_kind = tc_kind_of_precision(precision);
+    // jobs laid out for the CTA-pair launch when that variant is asked for (it never changes a result)
+    P->pair = P->tc_kind >= 0 && tc_variant_resolve(P->tc_kind, zstage_mode(c, precision), false) == 3 ? 1 : 0;
     P->SB = fp64 ? 4 : 8;
     uint64_t budget = workspace_bytes ? workspace_bytes : std::min<uint64_t>(c->budget, 64ull << 30);
     size_t geom_max = 256, coef_max = 256, tab_max = 256;
@@ -1447,6 +1452,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
             ta.f2 = (float *)pj.job.f2_out;
             ta.kind = P->tc_kind;
             ta.half = pj.half;
+            ta.pair = P->pair;
             TcJobDev jd;
             memset(&jd, 0, sizeof(jd));
             tc_job_desc(ta, base + P->off_group + pj.region, &jd);
@@ -1507,6 +1513,7 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             ta.f2 = (float *)pj.job.f2_out;
             ta.kind = P->tc_kind;
             ta.half = pj.half;
+            ta.pair = P->pair;
             tc_axes_abs_max(pj.job.grid->hx.data(), ta.nx, pj.job.grid->hy.data(), ta.ny, pj.job.grid->hz.data(), ta.nz,
                             ta.qabs);
             CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));

@@ -138,6 +138,7 @@ struct Batch {
 struct scff_server_s {
     scff_ctx *ctx = nullptr;
     int precision = SCFF_TF32X3;
+    int variant = 0;                 // W generator variant requested (the context's mode when created)
     int slots = 2;
     int max_batch = 64;
     double cost_ratio = 0.0;         // batch members' work within this factor of the first one's (<= 0: any)
@@ -262,6 +263,7 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             ta.f2 = (float *)f2dev;
             ta.kind = tc_kind_of(sv->precision);
             ta.half = j->half;
+            ta.pair = tc_variant_resolve(ta.kind, sv->variant, false) == 3 ? 1 : 0;
             tc_axes_abs_max(j->ax[0].data(), j->req.nx, j->ax[1].data(), j->req.ny, j->ax[2].data(), j->req.nz,
                             ta.qabs);
             TcJobDev jd;
@@ -312,7 +314,7 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
         int64_t launches = 0;
         if (tc_launch_persistent(tc_kind_of(sv->precision),
-                                 tc_variant_for(tc_kind_of(sv->precision), zstage_mode(c, sv->precision), descs.data(),
+                                 tc_variant_for(tc_kind_of(sv->precision), sv->variant, descs.data(),
                                                 (int)descs.size()),
                                  reinterpret_cast<const TcJobDev *>(desc_dev),
                                  reinterpret_cast<const int4 *>(desc_dev + up1k(sizeof(TcJobDev) * descs.size())),
@@ -495,6 +497,7 @@ extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options
     scff_server_s *sv = new scff_server_s();
     sv->ctx = c;
     sv->precision = o.precision;
+    sv->variant = zstage_mode(c, o.precision);
     sv->slots = o.slots;
     sv->max_batch = o.max_batch_jobs;
     sv->cost_ratio = o.batch_cost_ratio;
@@ -524,7 +527,7 @@ extern "C" scff_status scff_server_create(scff_ctx *c, const scff_server_options
     }
     // tensor-core kernel attributes are set once, outside the server thread's launches
     if (tc_precision(sv->precision))
-        for (int v : {0, 1, 2})
+        for (int v : {0, 1, 2, 3})
             tc_launch_persistent(tc_kind_of(sv->precision), v, nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
     sv->th = std::thread(server_loop, sv);
     *out = sv;

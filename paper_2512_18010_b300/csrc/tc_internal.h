@@ -31,7 +31,10 @@ struct TcArgs {
     int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo, 3: FP16 hi/lo
     double qabs[3];            // largest |q| of each axis (bounds of the FP16 kind's scaling)
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
-    int zstage;                // W generator variant requested (tc_variant_resolve): 0 gather, 1 Z staging, 2 prefetch
+    int zstage;                // W generator variant requested (tc_variant_resolve): 0 gather, 1 Z staging, 2 prefetch, 3 CTA pairs
+    // 1: the job is laid out for the CTA-pair launch (m-tiles padded to an
+    // even count; set by the launchers from the resolved variant)
+    int pair;
     // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
     // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
     int half;
@@ -50,6 +53,7 @@ struct TcArgs {
     volatile int *progress_host;        // the same slots (host address)
     cudaEvent_t ev_done, ev_copied;     // end of the launch, end of the copies
     int *bands_used;
+    int *variant_used;         // optional: the W generator variant the launch ran
 };
 
 // Device descriptor of one prepared job (read by the persistent kernel).
@@ -81,6 +85,9 @@ struct TcJobDev {
     float2 *part;
     int *cnt;
     int nsplit, split_tiles;
+    // 1: laid out for the CTA-pair launch: n_mt is even and the work items'
+    // m field holds the m-tile pair (tiles (2 mp, nt) and (2 mp + 1, nt))
+    int pair;
     // FP16 kind: FP64 bits of the bound of the job's largest term, from which
     // the job exponent of the scaled A is derived (null for the other kinds)
     const unsigned long long *tmax;
@@ -129,18 +136,22 @@ cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, 
 // Whether every job of a launch can use the Z-staging variant (two-piece
 // kinds, product grids whose nz is a multiple of 128).
 bool tc_zstage_ok(int kind, const TcJobDev *jobs, int n_jobs);
-// Whether a kind has the prefetching variant (the kinds that stage their
-// k-offsets: FP16 hi/lo and BF16 hi/lo).
+// Whether a kind has the prefetching and CTA-pair variants (the kinds that
+// stage their k-offsets: FP16 hi/lo and BF16 hi/lo).
 bool tc_prefetch_ok(int kind);
+// Most CTA pairs (two-CTA clusters of the persistent kernel) resident at once.
+int tc_num_pairs();
 // The variant a launch runs for a requested one: 1 (Z staging) where the kind
-// and every job's grid allow it (zstage_grid: tc_zstage_ok), 2 (prefetch)
-// where the kind has it, else 0 (gather).  All three form bitwise the same W
+// and every job's grid allow it (zstage_grid: tc_zstage_ok), 2 (prefetch) and
+// 3 (CTA pairs: a two-CTA cluster shares each MMA and generates half of W per
+// SM) where the kind has them, else 0 (gather).  All three form bitwise the same W
 // and add the same partial sums in the same order, so the choice never
 // changes a result.
 int tc_variant_resolve(int kind, int requested, bool zstage_grid);
 int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs);
 // The automatic mode's variant for a kind (measured fastest on the
-// 10-heavy-atom job): Z staging for TF32 hi/lo, gather for the 16-bit kinds.
+// 10-heavy-atom job): Z staging for TF32 hi/lo, CTA pairs for FP16 hi/lo and
+// BF16 hi/lo, gather for BF16 hi/mid/lo.
 int tc_variant_preferred(int kind);
 int tc_num_sms();
 

@@ -19,7 +19,7 @@ from . import build as _build
 FP64, FP32, BF16X3, TF32X3, BF16X2, FP16X2 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3, "bf16x2": BF16X2, "fp16x2": FP16X2}
 # tensor-core W generator variants (scff_set_tc_zstage modes, scff_last_path's third entry)
-GEN_VARIANTS = {0: "gather", 1: "zstage", 2: "prefetch"}
+GEN_VARIANTS = {0: "gather", 1: "zstage", 2: "prefetch", 3: "pair"}
 RENORM_CONTRACTED = 1
 PURE_D = 2   # d shells are the 5 real solid harmonics
 PURE_F = 4   # f shells are the 7 real solid harmonics

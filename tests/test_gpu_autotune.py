@@ -44,7 +44,7 @@ def test_generator_variants_agree_bitwise(prec):
     # so the results are bitwise equal, and scff_last_path reports which one ran.
     base = W.config_f(n_heavy=2, n_states=5)
     job = W.Job(base.mol, base.T, W.axis(9, 12.0), W.axis(6, 9.0), W.axis(128, 14.0), 3520)
-    variants = (0, 1, 2) if prec in (scff.FP16X2, scff.BF16X2) else (0, 1)
+    variants = (0, 1, 2, 3) if prec in (scff.FP16X2, scff.BF16X2) else (0, 1)
     ctx = scff.Context(0)
     try:
         out = {}
@@ -77,11 +77,14 @@ def test_generator_variants_agree_bitwise(prec):
 
 @pytest.mark.parametrize("prec", [scff.FP16X2, scff.BF16X2])
 @pytest.mark.parametrize("drain", [2, 3, 8, 0])
-def test_prefetch_variant_regimes(prec, drain):
-    # The prefetching variant against the gather variant, bitwise, where its bookkeeping differs:
-    # drains of 2 and 3 chunks (odd groups, a last group shorter than the rest), the whole K in one
-    # TMEM run (0), items of a single k-chunk and tail-split parts (the small z = 128 grid has few
-    # tiles, so its last tiles run as parts), and the mirrored half on antisymmetric axes.
+@pytest.mark.parametrize("variant", [2, 3])
+def test_variant_regimes(prec, drain, variant):
+    # The prefetching and CTA-pair variants against the gather variant, bitwise, where their
+    # bookkeeping differs: drains of 2 and 3 chunks (odd groups, a last group shorter than the rest),
+    # the whole K in one TMEM run (0), items of a single k-chunk and tail-split parts (the small
+    # z = 128 grid has few tiles, so its last tiles run as parts), an odd number of m-tiles (the
+    # pair's second half all padding), ragged column tiles, and the mirrored half on antisymmetric
+    # axes.
     base = W.config_f(n_heavy=1, n_states=3)
     jobs = [W.Job(base.mol, base.T, W.axis(7, 10.0), W.axis(5, 8.0), W.axis(128, 12.0), 3521),
             W.Job(base.mol, base.T, W.axis(4, 10.0), W.axis(33, 8.0), W.axis(20, 12.0), 3522),
@@ -89,18 +92,19 @@ def test_prefetch_variant_regimes(prec, drain):
     ctx = scff.Context(0)
     try:
         ctx.set_tc_drain(drain)
-        for job in jobs:
+        for job, bands in zip(jobs, (0, 1, 2)):
+            ctx.set_download_bands(bands)   # overlapped download (automatic, off, two bands)
             out = {}
-            for z in (0, 2):
+            for z in (0, variant):
                 ctx.set_tc_zstage(z)
                 out[z] = scff.evaluate_job(ctx, job, precision=prec)
                 assert ctx.last_path()["variant"] == scff.GEN_VARIANTS[z]
-            assert np.array_equal(out[0][0], out[2][0]) and np.array_equal(out[0][1], out[2][1])
+            assert np.array_equal(out[0][0], out[variant][0]) and np.array_equal(out[0][1], out[variant][1])
             idx = W.subset_indices(job.nq, 300, 13)
             ref = oracle.grid_form_factor(job, idx)
             tol = 5e-5 if prec == scff.BF16X2 else 1e-5
             if drain != 0:
-                assert np.max(np.abs(out[2][0][:, idx] - ref)) / np.max(np.abs(ref)) < tol
+                assert np.max(np.abs(out[variant][0][:, idx] - ref)) / np.max(np.abs(ref)) < tol
     finally:
         ctx.close()
 
@@ -111,7 +115,7 @@ def test_last_path_reports_the_path_taken():
     try:
         assert ctx.last_path()["path"] is None
         scff.evaluate_job(ctx, job, precision=scff.FP16X2)
-        assert ctx.last_path() == {"path": "tensor_cores", "precision": "fp16x2", "variant": "gather"}
+        assert ctx.last_path() == {"path": "tensor_cores", "precision": "fp16x2", "variant": "pair"}
         # a tensor-core precision on an explicit q list runs the FP32 direct path
         scff.evaluate_job(ctx, job, precision=scff.BF16X3, q_list=np.array([[0.1, 0.2, 0.3], [1.0, 0.0, 0.0]]))
         assert ctx.last_path() == {"path": "direct_fp32", "precision": "fp32", "variant": None}
