@@ -55,6 +55,8 @@ TC_SOURCES = ["kernels_tc.cu", "tc_internal.h", "tc_schedule.h", "device_common.
 MEASURED_TRAFFIC = {
     ("cfg3", "fp16x2", 0): {"bytes": 640825344 + 334578944, "src": "934acd17cfd39fe8",
                             "profile": "profiles/tc_fp16x2_cfg3_full.md"},
+    ("cfg3", "fp16x2", 3): {"bytes": 841533440 + 400098304, "src": "a00774f4dc029de6",
+                            "profile": "profiles/tc_pair_fp16x2_cfg3_full.md"},
 }
 
 
@@ -818,7 +820,8 @@ def main():
         executed = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
         zs_used = {v: k for k, v in scff.GEN_VARIANTS.items()}.get(path_used["variant"], 0)
         trec = measured_traffic(args.workload, args.precision, zs_used)
-        roof = {"bound": "tensor", "kernel": "tc_persistent_kernel", "achieved": achieved, "peak": peak,
+        roof = {"bound": "tensor", "kernel": "tc_pair_kernel" if zs_used == 3 else "tc_persistent_kernel",
+                "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "work": f"{alg_flops} algorithmic flop per (q*state) = 2K + 8 n_pairs - 4 n_ss with K = {K} "
