@@ -18,6 +18,8 @@
 // the imaginary part of the polynomial.
 #include <math.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "scff_internal.h"
 
@@ -379,6 +381,91 @@ template <typename R, int SB> struct Acc {
     }
     __device__ __forceinline__ R re(int j) const { return sizeof(R) == 4 ? hr[j] + lr[j] : pr[j]; }
     __device__ __forceinline__ R im(int j) const { return sizeof(R) == 4 ? hi[j] + li[j] : pi[j]; }
+    // starts state j from the sum (r, i) of an earlier launch
+    __device__ __forceinline__ void set(int j, R r, R i) {
+        if constexpr (sizeof(R) == 4) {
+            hr[j] = r;
+            hi[j] = i;
+        } else {
+            pr[j] = r;
+            pi[j] = i;
+        }
+    }
+};
+
+// Packed FP32 pairs (Blackwell's f32x2 arithmetic): each instruction does two
+// independent FP32 operations, each rounded exactly as its scalar form, so
+// the packed kernels give bitwise the scalar results with half the issued
+// arithmetic instructions.
+using f2p = unsigned long long;  // two FP32 values in one 64-bit register pair (low word first)
+__device__ __forceinline__ f2p pk(float lo, float hi) {
+    f2p d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float pk_lo(f2p v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float pk_hi(f2p v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+    f2p d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+    f2p d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// The FP32 accumulators of Acc<float, SB> with states packed in pairs:
+// state 2j in the low word and 2j + 1 in the high word of element j.  The
+// same operations in the same order as Acc, so bitwise the same sums.
+template <int SB> struct AccP {
+    static_assert(SB % 2 == 0, "states in pairs");
+    static constexpr int H = SB / 2;
+    f2p pr[H], pi[H], hr[H], hi[H], lr[H], li[H];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int j = 0; j < H; ++j) pr[j] = pi[j] = hr[j] = hi[j] = lr[j] = li[j] = 0ull;
+    }
+    __device__ __forceinline__ static void two_sum(f2p &h, f2p &l, f2p x) {
+        const f2p s = add2(h, x);
+        const f2p bb = sub2(s, h);
+        const f2p err = add2(sub2(h, sub2(s, bb)), sub2(x, bb));
+        h = s;
+        l = add2(l, err);
+    }
+    __device__ __forceinline__ void flush() {
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            two_sum(hr[j], lr[j], pr[j]);
+            two_sum(hi[j], li[j], pi[j]);
+            pr[j] = pi[j] = 0ull;
+        }
+    }
+    __device__ __forceinline__ float re(int j) const {
+        return (j & 1) ? pk_hi(hr[j >> 1]) + pk_hi(lr[j >> 1]) : pk_lo(hr[j >> 1]) + pk_lo(lr[j >> 1]);
+    }
+    __device__ __forceinline__ float im(int j) const {
+        return (j & 1) ? pk_hi(hi[j >> 1]) + pk_hi(li[j >> 1]) : pk_lo(hi[j >> 1]) + pk_lo(li[j >> 1]);
+    }
+    __device__ __forceinline__ void set(int j, float r, float i) {
+        const int h = j >> 1;
+        hr[h] = (j & 1) ? pk(pk_lo(hr[h]), r) : pk(r, pk_hi(hr[h]));
+        hi[h] = (j & 1) ? pk(pk_lo(hi[h]), i) : pk(i, pk_hi(hi[h]));
+    }
 };
 
 // Slots of the collapsed sums of a pair of degree L (the VEC variant): for
@@ -397,13 +484,13 @@ __host__ __device__ constexpr bool collapse_odd(int L, int t) { return t < 2 * L
 // NOUNI: compiled for grids whose blocks do not share (ix, iy), without the
 // shared-row branches at all (the runtime test alone, although uniform across
 // the block, took the 64^3 FP32 job from 3.8 to 5.1 ms).
-template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI>
+template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI, typename AccT>
 __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__restrict__ cbuf,
                                               const R *__restrict__ bbuf,
                                               const typename Cplx<R>::T *__restrict__ gxy, int pr0,
                                               int np, const R (&px)[kMaxPairL + 1], const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1],
                                               int ix, int iy, int iz, double qx, double qy, double qz,
-                                              double q2, Acc<R, SB> &acc) {
+                                              double q2, AccT &acc) {
     constexpr int mL = mono_count(L);
     using V = typename Cplx<R>::T;
     for (int i = 0; i < np; ++i) {
@@ -416,35 +503,81 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
         } else {
             g = pair_factor<R, LIST>(p, pr0 + i, ix, iy, iz, qx, qy, qz, q2);
         }
-        R E[SB], O[SB];
-#pragma unroll
-        for (int j = 0; j < SB; ++j) E[j] = O[j] = R(0);
         if constexpr (VEC) {
             // the block's x and y powers are already folded into the chunk's
             // collapsed sums (see run_class): E and O are polynomials in q_z
-            // alone, 2L+1 terms per pair instead of (L+1)(L+2)(L+3)/6
+            // alone, 2L+1 terms per pair instead of (L+1)(L+2)(L+3)/6.  States
+            // are packed in pairs (AccP): every FMA below does two states.
             static_assert(sizeof(R) == 4 && SB % 4 == 0, "four FP32 sums per load");
-            constexpr int NS = 2 * L + 1;
+            constexpr int NS = 2 * L + 1, H = SB / 2;
+            f2p E[H], O[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) E[j] = O[j] = 0ull;
             const R *bb = bbuf + (size_t)i * NS * SB;
             static_for<NS>([&](auto T) {
                 constexpr int t = decltype(T)::value;
                 constexpr int w = collapse_w(L, t);
-                const R zw = pz[w];
+                const f2p zw = pk(pz[w], pz[w]);
                 const float4 *b4 = reinterpret_cast<const float4 *>(bb + t * SB);
 #pragma unroll
                 for (int jj = 0; jj < SB / 4; ++jj) {
                     const float4 cv = b4[jj];
-                    const R cc[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-                    for (int tt = 0; tt < 4; ++tt) {
-                        if constexpr (collapse_odd(L, t))
-                            O[4 * jj + tt] = fma(cc[tt], zw, O[4 * jj + tt]);
-                        else
-                            E[4 * jj + tt] = fma(cc[tt], zw, E[4 * jj + tt]);
+                    const f2p c01 = pk(cv.x, cv.y), c23 = pk(cv.z, cv.w);
+                    if constexpr (collapse_odd(L, t)) {
+                        O[2 * jj] = fma2(c01, zw, O[2 * jj]);
+                        O[2 * jj + 1] = fma2(c23, zw, O[2 * jj + 1]);
+                    } else {
+                        E[2 * jj] = fma2(c01, zw, E[2 * jj]);
+                        E[2 * jj + 1] = fma2(c23, zw, E[2 * jj + 1]);
                     }
                 }
             });
+            const f2p gx = pk(g.x, g.x), gy = pk(g.y, g.y), ngy = pk(-g.y, -g.y);
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                acc.pr[j] = fma2(gx, E[j], acc.pr[j]);
+                if constexpr (L != 0) {  // s-s pairs have no odd monomial
+                    acc.pr[j] = fma2(ngy, O[j], acc.pr[j]);
+                    acc.pi[j] = fma2(gx, O[j], acc.pi[j]);
+                }
+                acc.pi[j] = fma2(gy, E[j], acc.pi[j]);
+            }
+        } else if constexpr (sizeof(R) == 4) {
+            // every monomial of the pair, states packed in pairs (AccP)
+            constexpr int H = SB / 2;
+            f2p E[H], O[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) E[j] = O[j] = 0ull;
+            const R *c = cbuf + (size_t)i * mL * SB;
+            static_for<mL>([&](auto M) {
+                constexpr int m = decltype(M)::value;
+                constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
+                const R mono = px[u] * py[v] * pz[w];
+                const f2p mo = pk(mono, mono);
+                const float2 *c2 = reinterpret_cast<const float2 *>(c + m * SB);
+#pragma unroll
+                for (int j = 0; j < H; ++j) {
+                    const float2 cv = c2[j];
+                    if constexpr (((u + v + w) & 1) != 0)
+                        O[j] = fma2(pk(cv.x, cv.y), mo, O[j]);
+                    else
+                        E[j] = fma2(pk(cv.x, cv.y), mo, E[j]);
+                }
+            });
+            const f2p gx = pk(g.x, g.x), gy = pk(g.y, g.y), ngy = pk(-g.y, -g.y);
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                acc.pr[j] = fma2(gx, E[j], acc.pr[j]);
+                if constexpr (L != 0) {  // s-s pairs have no odd monomial
+                    acc.pr[j] = fma2(ngy, O[j], acc.pr[j]);
+                    acc.pi[j] = fma2(gx, O[j], acc.pi[j]);
+                }
+                acc.pi[j] = fma2(gy, E[j], acc.pi[j]);
+            }
         } else {
+            R E[SB], O[SB];
+#pragma unroll
+            for (int j = 0; j < SB; ++j) E[j] = O[j] = R(0);
             const R *c = cbuf + (size_t)i * mL * SB;
             static_for<mL>([&](auto M) {
                 constexpr int m = decltype(M)::value;
@@ -458,21 +591,21 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
                         E[j] = fma(c[m * SB + j], mono, E[j]);
                 }
             });
-        }
-        if constexpr (L == 0) {
-            // s-s pairs have no odd monomial: f += g E
+            if constexpr (L == 0) {
+                // s-s pairs have no odd monomial: f += g E
 #pragma unroll
-            for (int j = 0; j < SB; ++j) {
-                acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
-                acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
-            }
-        } else {
+                for (int j = 0; j < SB; ++j) {
+                    acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
+                    acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
+                }
+            } else {
 #pragma unroll
-            for (int j = 0; j < SB; ++j) {
-                acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
-                acc.pr[j] = fma(-g.y, O[j], acc.pr[j]);
-                acc.pi[j] = fma(g.x, O[j], acc.pi[j]);
-                acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
+                for (int j = 0; j < SB; ++j) {
+                    acc.pr[j] = fma(g.x, E[j], acc.pr[j]);
+                    acc.pr[j] = fma(-g.y, O[j], acc.pr[j]);
+                    acc.pi[j] = fma(g.x, O[j], acc.pi[j]);
+                    acc.pi[j] = fma(g.y, E[j], acc.pi[j]);
+                }
             }
         }
         if ((i % kFlushPairs) == kFlushPairs - 1) acc.flush();
@@ -482,12 +615,12 @@ __device__ __forceinline__ void consume_chunk(const DirectParams &p, const R *__
 
 // Runs one pair class through a double-buffered bulk-copy pipeline.  Returns
 // false (uniformly across the block) when a wait timed out.
-template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI>
+template <typename R, int SB, int L, bool LIST, bool VEC, bool NOUNI, typename AccT>
 __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf1, R *bbuf, typename Cplx<R>::T *gxy,
                                           int bx, int by, uint64_t *bars,
                                           uint32_t &phase, int sblk, const R (&px)[kMaxPairL + 1],
                                           const R (&py)[kMaxPairL + 1], const R (&pz)[kMaxPairL + 1], int ix, int iy, int iz, double qx, double qy,
-                                          double qz, double q2, Acc<R, SB> &acc) {
+                                          double qz, double q2, AccT &acc) {
     constexpr int mL = mono_count(L);
     constexpr int pair_bytes = mL * SB * (int)sizeof(R);
     static_assert(pair_bytes <= kChunkBytes, "one pair's coefficients must fit a staging buffer");
@@ -547,18 +680,23 @@ __device__ __forceinline__ bool run_class(const DirectParams &p, R *buf0, R *buf
                     bx_[k] = bx_[k - 1] * qxb;
                     by_[k] = by_[k - 1] * qyb;
                 }
+                // one thread per (pair, state): every slot's sum at once, each over
+                // its monomials in increasing order
                 const R *cb = bufs[b];
-                for (int e = threadIdx.x; e < n * NS * SB; e += blockDim.x) {
-                    const int js = e % SB, t = (e / SB) % NS, i = e / (SB * NS);
+                for (int e = threadIdx.x; e < n * SB; e += blockDim.x) {
+                    const int js = e % SB, i = e / SB;
                     const R *c = cb + (size_t)i * mL * SB + js;
-                    R sum = R(0);
+                    R sum[NS];
+#pragma unroll
+                    for (int t = 0; t < NS; ++t) sum[t] = R(0);
                     static_for<mL>([&](auto M) {
                         constexpr int m = decltype(M)::value;
                         constexpr int u = mono_u(m), v = mono_v(m), w = mono_w(m);
                         constexpr int tm = collapse_slot(L, w, (u + v + w) & 1);
-                        if (t == tm) sum = fma(c[m * SB], bx_[u] * by_[v], sum);
+                        sum[tm] = fma(c[m * SB], bx_[u] * by_[v], sum[tm]);
                     });
-                    bbuf[e] = sum;
+#pragma unroll
+                    for (int t = 0; t < NS; ++t) bbuf[((size_t)i * NS + t) * SB + js] = sum[t];
                 }
             }
             __syncthreads();
@@ -628,7 +766,8 @@ __global__ void __launch_bounds__(kDirectThreads, (direct_min_blocks<SB, VEC>())
     }
     using V = typename Cplx<R>::T;
     V *f = static_cast<V *>(p.f);
-    Acc<R, SB> acc;
+    // FP32 keeps its states packed in pairs (f32x2 arithmetic)
+    std::conditional_t<sizeof(R) == 4, AccP<SB>, Acc<R, SB>> acc;
     acc.zero();
     if ((p.part & kPartContinue) && valid) {
 #pragma unroll
@@ -636,13 +775,7 @@ __global__ void __launch_bounds__(kDirectThreads, (direct_min_blocks<SB, VEC>())
             const int s = sblk * SB + j;
             if (s < p.S) {
                 const V v = f[(size_t)s * p.nq_out + q];
-                if constexpr (sizeof(R) == 4) {
-                    acc.hr[j] = v.x;
-                    acc.hi[j] = v.y;
-                } else {
-                    acc.pr[j] = v.x;
-                    acc.pi[j] = v.y;
-                }
+                acc.set(j, v.x, v.y);
             }
         }
     }
