@@ -97,6 +97,7 @@ def parse():
     ap.add_argument("--drain", type=int, default=-1,
                     help="tensor-core k-chunks per TMEM accumulation group (-1 = library default, 8)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
+    ap.add_argument("--fp32-steps", type=int, default=3, help="timed steps of the FP32 direct path (0 = skip)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="q points of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -791,13 +792,39 @@ def main():
                 "speedup_of_value": value / (units / (fms / 1e3))}
         del f64
 
+    # the FP32 direct path on the same job (its own roofline: the FP32 FMA rate)
+    fp32 = None
+    if args.fp32_steps > 0 and prec != scff.FP32:
+        f32 = torch.empty((S, nq, 2), dtype=torch.float32, device=dev)
+        tms, qms = [], []
+        for k in range(args.fp32_steps + 1):  # the first call is a warm-up
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.form_factor(b, t, g, precision=scff.FP32, f_out=f32, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:
+                tms.append(e0.elapsed_time(e1))
+                qms.append(ctx.last_timing()[0])
+        fms = float(np.mean(tms))
+        fp32 = {"value": units / (fms / 1e3), "unit": UNIT, "ms_per_step": fms, "qeval_ms": float(np.mean(qms)),
+                "steps": args.fp32_steps, "kernel": "direct_kernel<float> (packed f32x2 FMAs, double-float sums)"}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            sel = torch.from_numpy(W.subset_indices(nq, args.cpu_sample, CPU_SEED)).to(dev)
+            fc = f32.index_select(1, sel).double().cpu().numpy()
+            fp32["_f"] = fc[..., 0] + 1j * fc[..., 1]
+        del f32
+
     # measured FMA-chain peaks (FP32, FP64) of this GPU, beside the derived ALU peaks
     alu = None
     if not args.no_alu_peaks:
         p32, _ = ctx.alu_peak(False, 65536)
+        p32x2, _ = ctx.alu_peak(False, 65536, packed=True)
         p64, _ = ctx.alu_peak(True, 4096)
-        alu = {"fp32_tflops": p32, "fp64_tflops": p64,
-               "how": "dependent FMA chains, 8 per thread, 64 warps per SM, best of 3 launches after a warm-up"}
+        alu = {"fp32_tflops": p32, "fp32x2_tflops": p32x2, "fp64_tflops": p64,
+               "how": "dependent FMA chains, 8 per thread, 64 warps per SM, best of 3 launches after a warm-up; "
+                      "fp32x2: the same chains on packed f32x2 pairs"}
 
     # roofline of the dominant kernel (the q-evaluation)
     n_pair, K, Kvw, n_ss = pair_stats(job.mol)
@@ -809,6 +836,16 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    if fp32 is not None:
+        ue = S * ((nq + 1) // 2 if half else nq)  # evaluated (q-point x state) units of the direct path
+        ach = alg_flops * ue / (fp32["qeval_ms"] / 1e3) / 1e12
+        fp32["algorithmic_tflops"] = ach
+        if alu is not None:
+            # the kernel issues packed f32x2 FMAs: its roofline is the higher of the two FP32 chain rates
+            pk32 = max(alu["fp32_tflops"], alu["fp32x2_tflops"])
+            fp32["alg_frac_of_measured_fp32"] = ach / pk32
+            fp32["peak_tflops"] = pk32
+            fp32["peak_source"] = "of measured: max of the FP32 and packed f32x2 FMA-chain peaks of this run (alu_peaks)"
     if used_tc:
         passes = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3, scff.FP16X2: 3}[prec]
         tc_flops = 8 * Kvw * passes              # executed tensor flops per (q, state)
@@ -976,6 +1013,9 @@ def main():
         if side is not None:
             side["parity_vs_oracle"] = sample_parity(job, W.subset_indices(nq, args.cpu_sample, CPU_SEED),
                                                      side.pop("_f"), side["precision"])
+        if fp32 is not None and "_f" in fp32:
+            fp32["parity_vs_oracle"] = sample_parity(job, W.subset_indices(nq, args.cpu_sample, CPU_SEED),
+                                                     fp32.pop("_f"), "fp32")
         if serving is not None:
             serving["served_parity_vs_oracle"] = [
                 {"job": int(i), "nbf": int(serving_jobs_keep[i].mol.nbf),
@@ -999,7 +1039,7 @@ def main():
                            "hermitian_half": bool(half),
                            "parallelism": f"dp{world} (one job per rank)"},
                 "roofline": roof, "cpu_baseline": cpu, "parity_vs_oracle": parity, "alu_peaks": alu, "e2e": e2e, "spherical": spherical, "fft_method": fftm, "no_symmetry": no_symmetry, "gpu_launches": int(launches),
-                "fp64_gpu_path": fp64, "side_precision": side, "screened": screened, "serving": serving,
+                "fp64_gpu_path": fp64, "fp32_direct": fp32, "side_precision": side, "screened": screened, "serving": serving,
                 "batch": batch, "clocks": clocks,
                 "step_ms": step_ms, "qeval_ms": qeval_ms}
         print(json.dumps(line), flush=True)

@@ -471,10 +471,12 @@ scff_status scff_wait_selftest(scff_ctx *ctx, int64_t tries);
 /*
  * ALU peak microbenchmark (measurement utility; no counterpart in the paper):
  * dependent fused multiply-add chains (8 per thread, 64 resident warps per SM)
- * on the context's device, FP64 when fp64 != 0 else FP32, `iters` rounds per
- * chain (1..2^24).  One warm-up launch, then the best of three timed launches:
- * *tflops = 2 x FMAs / time, *ms = that launch's time.  Synchronous; the
- * rooflines of the direct (CUDA-core) kernels are quoted against it.
+ * on the context's device: fp64 = 0 FP32, 1 FP64, 2 FP32 as packed pairs
+ * (f32x2, two FMAs per instruction); `iters` rounds per chain (1..2^24).  One
+ * warm-up launch, then the best of three timed launches: *tflops = 2 x FMAs /
+ * time, *ms = that launch's time.  Synchronous; the rooflines of the direct
+ * (CUDA-core) kernels are quoted against it.  Other fp64 values:
+ * SCFF_ERR_INVALID_ARG.
  */
 scff_status scff_alu_peak(scff_ctx *ctx, int fp64, int iters, double *tflops, double *ms);
 

@@ -31,8 +31,33 @@ __global__ void __launch_bounds__(kThreads) fma_chain_kernel(int iters, T a, T b
     if (s == (T)-1) sink[blockIdx.x] = s;
 }
 
+// The same chains on packed FP32 pairs (f32x2: two FMAs per instruction).
+__global__ void __launch_bounds__(kThreads) fma2_chain_kernel(int iters, float a, float b, float *__restrict__ sink) {
+    unsigned long long x[kChains], a2, b2;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(a2) : "f"(a));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(b2) : "f"(b));
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        const float v0 = (float)(threadIdx.x + c) * 1e-3f, v1 = (float)(threadIdx.x + 2 * c) * 1e-3f;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(v0), "f"(v1));
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(a2), "l"(b2));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[c]));
+        s += lo + hi;
+    }
+    if (s == -1.f) sink[blockIdx.x] = s;
+}
+
 }  // namespace
 
+// mode: 0 FP32 FMA chains, 1 FP64, 2 FP32 as packed f32x2 pairs.
 cudaError_t measure_alu_peak(int fp64, int iters, double *tflops, double *ms) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -46,8 +71,10 @@ cudaError_t measure_alu_peak(int fp64, int iters, double *tflops, double *ms) {
         float best = 0.f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms the clock up
             cudaEventRecord(e0, 0);
-            if (fp64)
+            if (fp64 == 1)
                 fma_chain_kernel<double><<<blocks, kThreads>>>(iters, 0.999999, 1e-6, (double *)sink);
+            else if (fp64 == 2)
+                fma2_chain_kernel<<<blocks, kThreads>>>(iters, 0.9999f, 1e-4f, (float *)sink);
             else
                 fma_chain_kernel<float><<<blocks, kThreads>>>(iters, 0.9999f, 1e-4f, (float *)sink);
             cudaEventRecord(e1, 0);
@@ -58,7 +85,7 @@ cudaError_t measure_alu_peak(int fp64, int iters, double *tflops, double *ms) {
         }
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) {
-            const double flops = 2.0 * kChains * (double)iters * kThreads * blocks;
+            const double flops = (fp64 == 2 ? 4.0 : 2.0) * kChains * (double)iters * kThreads * blocks;
             *ms = best;
             *tflops = flops / (best * 1e-3) / 1e12;
         }

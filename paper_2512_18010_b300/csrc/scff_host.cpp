@@ -1244,9 +1244,10 @@ extern "C" scff_status scff_separable_integral(scff_ctx *c, scff_basis_h b, scff
 extern "C" scff_status scff_alu_peak(scff_ctx *c, int fp64, int iters, double *tflops, double *ms) {
     if (!c || !tflops || !ms) return fail(SCFF_ERR_INVALID_ARG, "scff_alu_peak: NULL argument");
     if (iters < 1 || iters > (1 << 24)) return fail(SCFF_ERR_INVALID_ARG, "scff_alu_peak: iters must be 1..2^24");
+    if (fp64 < 0 || fp64 > 2) return fail(SCFF_ERR_INVALID_ARG, "scff_alu_peak: mode %d (0 FP32, 1 FP64, 2 f32x2)", fp64);
     cudaSetDevice(c->device);
     CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(measure_alu_peak(fp64 ? 1 : 0, iters, tflops, ms));
+    CUDA_TRY(measure_alu_peak(fp64, iters, tflops, ms));
     return SCFF_OK;
 }
 

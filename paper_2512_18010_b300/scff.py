@@ -581,11 +581,13 @@ class Context:
         downloads overlap the next band's compute (0 = automatic, 1 = off, 2..8)."""
         _check(self.lib.scff_set_download_bands(self.h, int(n_bands)))
 
-    def alu_peak(self, fp64: bool = False, iters: int = 65536):
-        """Measured FMA-chain rate of this device: (TFLOP/s, ms of the timed launch)."""
+    def alu_peak(self, fp64: bool = False, iters: int = 65536, packed: bool = False):
+        """Measured FMA-chain rate of this device: (TFLOP/s, ms of the timed launch).  FP64, FP32, or with
+        packed=True FP32 on packed f32x2 pairs."""
         t = np.zeros(1, dtype=np.float64)
         m = np.zeros(1, dtype=np.float64)
-        _check(self.lib.scff_alu_peak(self.h, 1 if fp64 else 0, int(iters), _p(t), _p(m)))
+        mode = 1 if fp64 else (2 if packed else 0)
+        _check(self.lib.scff_alu_peak(self.h, mode, int(iters), _p(t), _p(m)))
         return float(t[0]), float(m[0])
 
     def wait_selftest(self, tries: int = 4096):

@@ -319,6 +319,9 @@ def test_alu_peak_microbenchmark(ctx):
     assert 5.0 < p32 < 148 * 128 * 2 * 2.1e9 / 1e12
     assert 0.05 < p64 < p32
     assert ms32 > 0 and ms64 > 0
+    # packed f32x2 chains: at least the scalar rate's order, at most two FMAs per lane and clock
+    p32x2, ms32x2 = ctx.alu_peak(False, 16384, packed=True)
+    assert 0.5 * p32 < p32x2 < 2 * 148 * 128 * 2 * 2.1e9 / 1e12 and ms32x2 > 0
     for bad in (0, -5, 1 << 25):
         with pytest.raises(scff.ScffError) as e:
             ctx.alu_peak(False, bad)
