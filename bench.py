@@ -252,11 +252,65 @@ def fft_run(ctx, b, t, S, steps, stream, flush, job):
                                   "synthetic transition matrices weight the core s functions (exponents up to "
                                   "3000), whose densities are ~0.01 Bohr wide and whose transforms barely decay "
                                   "by |q| = 20, so no practical box resolves them and every q carries aliased "
-                                  "copies; the rate measures the FFT kernels only",
+                                  "copies; the rate measures the FFT kernels only (at_stated_accuracy: the "
+                                  "method where it converges, on a valence transition matrix)",
             "parseval_rel_diff": float(np.max(np.abs(par[:, 0] - par[:, 1]) / par[:, 0])),
             "fp32_vs_fp64_same_box_64": arith,
             "discretisation_err_vs_analytic": disc,
-            "fp64_path": {"value": S * n64 ** 3 / (ms64 / 1e3), "unit": UNIT, "ms_per_call": ms64, "box": "64^3"}}
+            "fp64_path": {"value": S * n64 ** 3 / (ms64 / 1e3), "unit": UNIT, "ms_per_call": ms64, "box": "64^3"},
+            "at_stated_accuracy": fft_valence_run(ctx, S, steps, stream, flush, job)}
+
+
+FFT_VAL_N, FFT_VAL_QMAX, FFT_VAL_CUT = 256, 40.0, 50.0
+
+
+def fft_valence_run(ctx, S, steps, stream, flush, job):
+    """The FFT method where it converges: the same molecule with a valence transition matrix (rows
+    and columns of the core functions, exponents above 50, set to zero), a 256^3 box centred on the
+    molecule with q in [-40, 40) (box side 20.1 Bohr), FP32; its rate and its discretisation error
+    against the analytic FP64 path at 512 sampled q of its grid."""
+    import torch
+    from paper_2512_18010_b300 import scff
+    Tv = W.valence_transitions(job.mol, job.T, FFT_VAL_CUT)
+    b = ctx.basis(job.mol)
+    t = ctx.transitions(b, Tv)
+    n, dq = FFT_VAL_N, 2 * FFT_VAL_QMAX / FFT_VAL_N
+    cen = tuple(float(c) for c in np.mean(job.mol.xyz, axis=0))
+
+    def call():
+        return ctx.fft_form_factor(b, t, n, dq, centre=cen, precision=scff.FP32, want=("f", "f2"), out="cuda",
+                                   stream=stream)
+
+    call()
+    ms = []
+    for k in range(max(1, min(steps, 3))):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    tms = float(np.mean(ms))
+    rng = np.random.default_rng(8)
+    idx = rng.integers(0, n, size=(512, 3))
+    q = dq * (idx - n // 2)
+    g = ctx.qgrid_list(q)
+    fa, _ = ctx.form_factor(b, t, g, precision=scff.FP64)
+    ctx.release(g)
+    fs = out["f"][:, idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    fs = fs[..., 0] + 1j * fs[..., 1]
+    err = float(np.max(np.max(np.abs(fs - fa), axis=1) / np.max(np.abs(fa), axis=1)))
+    del out
+    ctx.release(t)
+    ctx.release(b)
+    torch.cuda.empty_cache()
+    return {"workload": f"10-heavy-atom molecule, {S} states, valence transition matrix (core functions with "
+                        f"exponents above {FFT_VAL_CUT:g} removed), {n}^3 box centred on the molecule, side "
+                        f"{2 * np.pi / dq:.1f} Bohr, q in [-{FFT_VAL_QMAX:g}, {FFT_VAL_QMAX:g})",
+            "value": S * n ** 3 / (tms / 1e3), "unit": UNIT, "ms_per_call": tms, "precision": "fp32",
+            "discretisation_err_vs_analytic": err, "points": 512, "stated_accuracy": 1e-3,
+            "pass": bool(err <= 1e-3)}
 
 
 def pair_stats(mol):

@@ -145,6 +145,26 @@ def transition_matrices(seed: int, n_states: int, nbf: int) -> np.ndarray:
     return T
 
 
+def valence_transitions(mol: Molecule, T: np.ndarray, exponent_cut: float = 50.0) -> np.ndarray:
+    """T with the rows and columns of core functions set to zero: functions of shells whose largest
+    primitive exponent exceeds ``exponent_cut`` (the heavy atoms' tight s shells).  Transition
+    densities of valence excitations carry next to no core weight; this is the input on which a
+    real-space grid (the FFT method) can resolve the density."""
+    keep = []
+    off = 0
+    for sh in range(mol.n_shells):
+        l, npr = int(mol.shell_l[sh]), int(mol.shell_nprim[sh])
+        amax = float(np.max(mol.exponents[off:off + npr]))
+        off += npr
+        nf = 2 * l + 1 if (mol.pure & _PURE_BIT.get(l, 0)) else NFN[l]
+        keep += [amax <= exponent_cut] * nf
+    keep = np.asarray(keep)
+    Tv = np.array(T, dtype=np.float64, copy=True)
+    Tv[:, ~keep, :] = 0.0
+    Tv[:, :, ~keep] = 0.0
+    return Tv
+
+
 def subset_indices(n_total: int, n: int, seed: int) -> np.ndarray:
     """Seeded uniform sample of flat grid indices, sorted, without repeats."""
     rng = np.random.default_rng(seed)
