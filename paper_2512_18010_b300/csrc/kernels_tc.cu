@@ -576,7 +576,7 @@ static Layout make_layout_k(const PairSetDev &ps, int S, int nx, int ny, int nz)
 // phase q P is reduced to [-pi, pi] in FP64 (Cody-Waite with 2 pi split in
 // two doubles), so the FP32 sine and cosine of the remainder and the FP32
 // exponential are as accurate as the FP32 table entries; the powers of i q
-// are applied in FP64.
+// are applied in FP32 (row u carries at most u + 2 roundings of 2^-24).
 // With Q >= 0 (FP16 kind) every row u is multiplied by 2^(kRowExp - e_u),
 // e_u = axis_row_exp(u, 1/(4p), Q) with Q >= max |q_i| of the axis.
 __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict__ geom,
@@ -601,13 +601,16 @@ __global__ void axis_power_table_kernel(PairSetDev ps, const double *__restrict_
     const float r = (float)fma(-nk, kTwoPiLo, fma(-nk, kTwoPiHi, th));
     float sf, cf;
     sincosf(r, &sf, &cf);
-    const double g = (double)expf((float)(-q * q * inv4p));
-    double re = (double)cf * g, im = (double)sf * g;
+    const float g = expf((float)(-q * q * inv4p));
+    // powers of i q in FP32: each step adds one rounding of 2^-24, so row u
+    // carries at most u + 2 of them (the entries are stored in FP32 anyway)
+    const float qf = (float)q;
+    float re = cf * g, im = sf * g;
     for (int u = 0; u <= L; ++u) {
-        const double f = Q >= 0.0 ? ldexp(1.0, kRowExp - axis_row_exp(u, inv4p, Q)) : 1.0;
-        table[(row0 + u) * n + i] = make_float2((float)(re * f), (float)(im * f));
+        const int e = Q >= 0.0 ? kRowExp - axis_row_exp(u, inv4p, Q) : 0;  // exact power-of-two row scale
+        table[(row0 + u) * n + i] = make_float2(ldexpf(re, e), ldexpf(im, e));
         // times i q
-        const double nr = -q * im, ni = q * re;
+        const float nr = -qf * im, ni = qf * re;
         re = nr;
         im = ni;
     }
@@ -752,6 +755,101 @@ __global__ void abuild_kernel(PairSetDev ps, const float *__restrict__ coef32, i
     const int c0 = (int)((kv * V) % BK);
     uint8_t *base = Abuf + ((size_t)mt * nkc + kc) * KD::A_STAGE;
     const uint32_t off = sw64_offset<KIND>(r, c0);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        *reinterpret_cast<uint4 *>(base + q * A_ARR + off) = pr_[q];
+        *reinterpret_cast<uint4 *>(base + (NP + q) * A_ARR + off) = pi_[q];
+    }
+}
+
+// The same A image, one block of BM x (BK / PER_VEC) threads per (m-tile,
+// k-chunk): the chunk's k records are decoded once and the coefficients of
+// every state the tile's rows touch (states s0..s0 + ns - 1) are staged once
+// in shared memory, so each thread only reads its X entries; the sums run
+// over u in the same order as abuild_kernel's, so the image is bitwise the
+// same.  Dynamic shared memory: ns x BK x (kMaxPairL + 1) floats.
+template <int KIND>
+__global__ void __launch_bounds__(BM *Kind<KIND>::BK / Kind<KIND>::PER_VEC)
+    abuild_tile_kernel(PairSetDev ps, const float *__restrict__ coef32, int SB, int nxr, int nx,
+                       const float2 *__restrict__ X, const int4 *__restrict__ kinfo, int nkc, int M,
+                       uint8_t *__restrict__ Abuf, const int *__restrict__ kexp,
+                       const unsigned long long *__restrict__ tmax) {
+    using KD = Kind<KIND>;
+    constexpr int V = KD::PER_VEC, BK = KD::BK, NP = KD::NP, VPC = BK / V, NU = kMaxPairL + 1;
+    extern __shared__ float csm[];           // [ns][BK][NU] signed coefficients
+    __shared__ int4 kin[BK];                 // (pair or -1, v, w, axis row)
+    __shared__ int kun[BK];                  // u count of k (0 for padding)
+    __shared__ int ksh[BK];                  // FP16 kind: power-of-two scale of column k
+    const int kc = blockIdx.x, mt = blockIdx.y;
+    const int m0 = mt * BM;
+    const int s0 = min(m0, M - 1) / nxr;
+    const int ns = min(M - 1, m0 + BM - 1) / nxr - s0 + 1;
+    int G = 0;
+    if constexpr (KD::FP16) G = fp16_job_exp(tmax) - 2 * kRowExp;
+    if (threadIdx.x < BK) {
+        const int64_t k = (int64_t)kc * BK + threadIdx.x;
+        const int4 ki = kinfo[k];
+        int nu = 0;
+        if (ki.x >= 0) {
+            int L = 0;
+            while (L < kMaxPairL && ki.x >= ps.pair_off[L + 1]) ++L;
+            nu = L - ki.y - ki.z + 1;
+        }
+        kin[threadIdx.x] = ki;
+        kun[threadIdx.x] = nu;
+        if constexpr (KD::FP16) ksh[threadIdx.x] = kexp[k] + G;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ns * BK * NU; t += blockDim.x) {
+        const int u = t % NU, kl = (t / NU) % BK, si = t / (NU * BK);
+        const int4 ki = kin[kl];
+        float c = 0.f;
+        if (u < kun[kl]) {
+            int L = 0;
+            while (L < kMaxPairL && ki.x >= ps.pair_off[L + 1]) ++L;
+            const int64_t rowbase = ps.row_off[L] + (int64_t)(ki.x - ps.pair_off[L]) * mono_count(L);
+            const int s = s0 + si;
+            const int n = u + ki.y + ki.z;
+            c = coef32[((size_t)(s / SB) * ps.n_rows + rowbase + mono_index(u, ki.y, ki.z)) * SB + (s % SB)] *
+                ((n & 2) ? -1.f : 1.f);
+        }
+        csm[t] = c;
+    }
+    __syncthreads();
+    const int r = threadIdx.x / VPC, vv = threadIdx.x % VPC;
+    const int m = m0 + r;
+    const bool mvalid = m < M;
+    const int s = mvalid ? m / nxr : s0, ix = mvalid ? m % nxr : 0;
+    const float *cs = csm + (size_t)(s - s0) * BK * NU;
+    float re[V], im[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const int kl = vv * V + e;
+        const int4 ki = kin[kl];
+        const int nu = kun[kl];
+        float ar = 0.f, ai = 0.f;
+        if (mvalid) {
+            for (int u = 0; u < nu; ++u) {
+                const float c = cs[kl * NU + u];
+                const float2 x = X[(size_t)(ki.w + u) * nx + ix];
+                ar = fmaf(c, x.x, ar);
+                ai = fmaf(c, x.y, ai);
+            }
+            if constexpr (KD::FP16) {
+                if (nu > 0) {
+                    ar = pow2_scale(ar, ksh[kl]);
+                    ai = pow2_scale(ai, ksh[kl]);
+                }
+            }
+        }
+        re[e] = ar;
+        im[e] = ai;
+    }
+    uint4 pr_[NP], pi_[NP];
+    split_vec<KIND>(re, pr_);
+    split_vec<KIND>(im, pi_);
+    uint8_t *base = Abuf + ((size_t)mt * nkc + kc) * KD::A_STAGE;
+    const uint32_t off = sw64_offset<KIND>(r, vv * V);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         *reinterpret_cast<uint4 *>(base + q * A_ARR + off) = pr_[q];
@@ -1996,10 +2094,18 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
         if (launches) *launches += 1;
     }
     {
-        const int64_t tot = (int64_t)L.M_pad * (L.K_pad / KD::PER_VEC);
-        abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-            ps, a.coef32, a.SB, a.half ? (a.nx + 1) / 2 : a.nx, a.nx, X, kinfo, L.K_pad, L.nkc, L.M, L.M_pad, Abuf,
-            kexp, tmax);
+        const int nxr = a.half ? (a.nx + 1) / 2 : a.nx;
+        // states one m-tile's rows can touch, and their staged coefficients
+        const int ns_max = std::min(a.S, (BM + nxr - 1) / nxr + 1);
+        const size_t csm = sizeof(float) * (size_t)ns_max * KD::BK * (kMaxPairL + 1);
+        if (csm <= 48 * 1024 && L.M > 0) {
+            abuild_tile_kernel<KIND><<<dim3((unsigned)L.nkc, (unsigned)L.n_mt), BM * KD::BK / KD::PER_VEC, csm, st>>>(
+                ps, a.coef32, a.SB, nxr, a.nx, X, kinfo, L.nkc, L.M, Abuf, kexp, tmax);
+        } else {
+            const int64_t tot = (int64_t)L.M_pad * (L.K_pad / KD::PER_VEC);
+            abuild_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+                ps, a.coef32, a.SB, nxr, a.nx, X, kinfo, L.K_pad, L.nkc, L.M, L.M_pad, Abuf, kexp, tmax);
+        }
     }
     if (launches) *launches += 5;
     cudaError_t e = cudaMemsetAsync(w + L.off_cnt, 0, sizeof(int) * 8 * (size_t)L.part_tiles, st);
