@@ -18,6 +18,7 @@
 // the imaginary part of the polynomial.
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -113,19 +114,54 @@ cudaError_t launch_pair_geom(const PairSetDev &ps, double *pair_geom, cudaStream
 constexpr int kPrepThreads = 128;
 constexpr int kPrepStates = 8;  // states per register block
 
+// T entries staged per block and state block: the symmetrised T^s_ij (+ T^s_ji)
+// of every function pair of every pair the block's rows belong to.  A block
+// holds 128 consecutive rows; a pair of degree L has (L+1)(L+2)(L+3)/6 rows and
+// at most 1.6 times as many function pairs, so the block's pairs have at most
+// 1.6 x 128 + 2 x 100 (the two pairs cut by the block's ends) function pairs.
+constexpr int kPrepMaxFnPairs = 416;
+// dynamic shared memory: the staged T, then the function-pair offsets (kPrepThreads + 1 ints)
+constexpr int kPrepTsmBytes = kPrepMaxFnPairs * kPrepStates * (int)sizeof(double) + 1024;
+
 __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, const double *__restrict__ T,
                                                                 int S, int S_pad, int SB,
                                                                 double *__restrict__ coef64,
                                                                 float *__restrict__ coef32) {
     __shared__ double Csm[3 * 4 * 4][kPrepThreads];  // C[ax][a][a2] of this thread's row
-    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= ps.n_rows) return;
+    extern __shared__ double Tsm[];                  // [function pair of the block][kPrepStates], then foff
+    // first function pair of each of the block's pairs
+    int *foff = reinterpret_cast<int *>(Tsm + kPrepMaxFnPairs * kPrepStates);
+    const int64_t row0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t row = row0 + threadIdx.x;
+    const bool valid = row < ps.n_rows;
     const int tid = threadIdx.x;
+    auto pair_of = [&](int64_t r) {
+        int L = 0;
+        while (L < kMaxPairL && r >= ps.row_off[L + 1]) ++L;
+        return ps.pair_off[L] + (int)((r - ps.row_off[L]) / mono_count(L));
+    };
+    // the block's pairs p_lo..p_lo + np - 1 and their function-pair offsets
+    const int p_lo = pair_of(row0);
+    const int64_t row_last = row0 + (int64_t)blockDim.x <= ps.n_rows ? row0 + blockDim.x - 1 : ps.n_rows - 1;
+    const int np = pair_of(row_last) - p_lo + 1;
+    if (tid < np) {
+        const int2 rr = ps.pair_rec[p_lo + tid];
+        foff[tid + 1] = rec_nfn(ps.rec_type[rr.x]) * rec_nfn(ps.rec_type[rr.y]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        foff[0] = 0;
+        for (int t = 0; t < np; ++t) foff[t + 1] += foff[t];
+    }
+    __syncthreads();
+    const int nfp = foff[np];
+    const bool staged = nfp <= kPrepMaxFnPairs;  // else (never for s..f shells) read T from global memory
+
     int L = 0;
-    while (L < kMaxPairL && row >= ps.row_off[L + 1]) ++L;
+    while (L < kMaxPairL && valid && row >= ps.row_off[L + 1]) ++L;
     const int mL = mono_count(L);
-    const int64_t local = row - ps.row_off[L];
-    const int pr = ps.pair_off[L] + (int)(local / mL);
+    const int64_t local = valid ? row - ps.row_off[L] : 0;
+    const int pr = valid ? ps.pair_off[L] + (int)(local / mL) : p_lo;
     const int m = (int)(local % mL);
     const int2 rr = ps.pair_rec[pr];
     const double al = ps.rec_alpha[rr.x], be = ps.rec_alpha[rr.y];
@@ -152,16 +188,42 @@ __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, c
     const bool same = (rr.x == rr.y);
     const int n = e[0] + e[1] + e[2];
     const double sgn = K * ((n & 2) ? -1.0 : 1.0);  // i^n = +1, +i, -1, -i
+    const double *Tmine = Tsm + (size_t)foff[pr - p_lo] * kPrepStates;
     // states in register blocks of kPrepStates: the function-pair factor
     // w_i w_j D (state-independent) is formed once per block, and each state
     // adds T^s_ij (+ T^s_ji) times it
     const size_t nn = (size_t)nbf * nbf;
-    for (int s0 = 0; s0 < S_pad; s0 += kPrepStates) {
+    // blockIdx.y takes every gridDim.y-th block of states (more blocks in flight than rows alone give)
+    for (int s0 = blockIdx.y * kPrepStates; s0 < S_pad; s0 += gridDim.y * kPrepStates) {
         const int ns = min(kPrepStates, S - s0);
+        if (staged) {
+            // the symmetrised T of the block's function pairs for these states, once per block
+            __syncthreads();
+            for (int q = tid; q < nfp * kPrepStates; q += blockDim.x) {
+                const int u = q % kPrepStates, fp = q / kPrepStates;
+                int t = 0, hi = np - 1;  // the pair t with foff[t] <= fp < foff[t + 1]
+                while (t < hi) {
+                    const int mid = (t + hi + 1) >> 1;
+                    if (foff[mid] <= fp) t = mid;
+                    else hi = mid - 1;
+                }
+                const int2 qr = ps.pair_rec[p_lo + t];
+                const int m2 = rec_nfn(ps.rec_type[qr.y]);
+                const int i = (fp - foff[t]) / m2, j = (fp - foff[t]) % m2;
+                const int g1 = ps.rec_fn0[qr.x] + i, g2 = ps.rec_fn0[qr.y] + j;
+                double tw = 0.0;
+                if (u < ns) {
+                    tw = T[(size_t)(s0 + u) * nn + (size_t)g1 * nbf + g2];
+                    if (qr.x != qr.y) tw += T[(size_t)(s0 + u) * nn + (size_t)g2 * nbf + g1];
+                }
+                Tsm[q] = tw;
+            }
+            __syncthreads();
+        }
         double acc[kPrepStates];
 #pragma unroll
         for (int u = 0; u < kPrepStates; ++u) acc[u] = 0.0;
-        if (ns > 0) {
+        if (ns > 0 && valid) {
             for (int i = 0; i < n1; ++i) {
                 const double wi = ps.rec_w[kRecW * rr.x + i];
                 const int ai = fn_pow(t1, i, 0), bi = fn_pow(t1, i, 1), ci = fn_pow(t1, i, 2);
@@ -171,36 +233,52 @@ __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, c
                                      Csm[(2 * 4 + ci) * 4 + cj][tid];
                     if (D == 0.0) continue;
                     const double w = wi * ps.rec_w[kRecW * rr.y + j] * D;
-                    const double *Tij = T + (size_t)s0 * nn + (size_t)(f1 + i) * nbf + (f2 + j);
-                    const double *Tji = T + (size_t)s0 * nn + (size_t)(f2 + j) * nbf + (f1 + i);
+                    if (staged) {
+                        const double *ts = Tmine + (size_t)(i * n2 + j) * kPrepStates;
 #pragma unroll
-                    for (int u = 0; u < kPrepStates; ++u) {
-                        if (u < ns) {
-                            double tw = Tij[u * nn];
-                            if (!same) tw += Tji[u * nn];
-                            acc[u] = fma(tw, w, acc[u]);
+                        for (int u = 0; u < kPrepStates; ++u)
+                            if (u < ns) acc[u] = fma(ts[u], w, acc[u]);
+                    } else {
+                        const double *Tij = T + (size_t)s0 * nn + (size_t)(f1 + i) * nbf + (f2 + j);
+                        const double *Tji = T + (size_t)s0 * nn + (size_t)(f2 + j) * nbf + (f1 + i);
+#pragma unroll
+                        for (int u = 0; u < kPrepStates; ++u) {
+                            if (u < ns) {
+                                double tw = Tij[u * nn];
+                                if (!same) tw += Tji[u * nn];
+                                acc[u] = fma(tw, w, acc[u]);
+                            }
                         }
                     }
                 }
             }
         }
+        if (valid) {
 #pragma unroll
-        for (int u = 0; u < kPrepStates; ++u) {
-            const int s = s0 + u;
-            if (s >= S_pad) break;
-            const double val = sgn * acc[u];
-            const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
-            if (coef64) coef64[idx] = val;
-            if (coef32) coef32[idx] = (float)val;
+            for (int u = 0; u < kPrepStates; ++u) {
+                const int s = s0 + u;
+                if (s >= S_pad) break;
+                const double val = sgn * acc[u];
+                const size_t idx = ((size_t)(s / SB) * ps.n_rows + row) * SB + (s % SB);
+                if (coef64) coef64[idx] = val;
+                if (coef32) coef32[idx] = (float)val;
+            }
         }
     }
+}
+
+cudaError_t pairprep_init() {
+    // the staged T takes the block beyond 48 KB of shared memory; set on the
+    // current device when a context is created, before any stream capture
+    return cudaFuncSetAttribute(pairprep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrepTsmBytes);
 }
 
 cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB, int S_pad,
                             double *coef64, float *coef32, int64_t *launches, cudaStream_t st) {
     if (ps.n_rows == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((ps.n_rows + kPrepThreads - 1) / kPrepThreads);
-    pairprep_kernel<<<grid, kPrepThreads, 0, st>>>(ps, T, S, S_pad, SB, coef64, coef32);
+    const unsigned sblocks = (unsigned)std::max(1, (S_pad + kPrepStates - 1) / kPrepStates);
+    pairprep_kernel<<<dim3(grid, sblocks), kPrepThreads, kPrepTsmBytes, st>>>(ps, T, S, S_pad, SB, coef64, coef32);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

@@ -87,6 +87,7 @@ extern "C" scff_status scff_create(scff_ctx **out, int device, uint64_t hbm_budg
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(SCFF_ERR_INVALID_ARG, "scff_create: device %d of %d", device, ndev);
     CUDA_TRY(cudaSetDevice(device));
+    CUDA_TRY(pairprep_init());
     scff_ctx *c = new scff_ctx();
     c->device = device;
     size_t fr = 0, tot = 0;
