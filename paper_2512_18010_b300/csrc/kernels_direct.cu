@@ -268,14 +268,25 @@ __global__ void __launch_bounds__(kPrepThreads) pairprep_kernel(PairSetDev ps, c
 }
 
 cudaError_t pairprep_init() {
-    // the staged T takes the block beyond 48 KB of shared memory; set on the
-    // current device when a context is created, before any stream capture
-    return cudaFuncSetAttribute(pairprep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrepTsmBytes);
+    // the staged T takes the block beyond 48 KB of shared memory: the attribute
+    // is set once per device (when a context is created, or by the first launch
+    // on a device that has none, e.g. through the allocation-free entry)
+    constexpr int kDevs = 64;
+    static bool done[kDevs] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kDevs && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(pairprep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPrepTsmBytes);
+    if (e == cudaSuccess && dev >= 0 && dev < kDevs) done[dev] = true;
+    return e;
 }
 
 cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB, int S_pad,
                             double *coef64, float *coef32, int64_t *launches, cudaStream_t st) {
     if (ps.n_rows == 0) return cudaSuccess;
+    const cudaError_t ei = pairprep_init();
+    if (ei != cudaSuccess) return ei;
     const unsigned grid = (unsigned)((ps.n_rows + kPrepThreads - 1) / kPrepThreads);
     const unsigned sblocks = (unsigned)std::max(1, (S_pad + kPrepStates - 1) / kPrepStates);
     pairprep_kernel<<<dim3(grid, sblocks), kPrepThreads, kPrepTsmBytes, st>>>(ps, T, S, S_pad, SB, coef64, coef32);

@@ -151,7 +151,8 @@ cudaError_t launch_pair_geom(const PairSetDev &ps, double *pair_geom, cudaStream
 
 // coef[(s / SB * n_rows + row) * SB + s % SB] for s < S_pad (zero beyond S).
 // Kernel attributes of the pair-prep kernel on the current device (once per
-// device, before its first launch; scff_create calls it).
+// device; scff_create calls it before any capture, and launch_pairprep on a
+// device where it has not run yet).
 cudaError_t pairprep_init();
 cudaError_t launch_pairprep(const PairSetDev &ps, const double *T, int S, int SB, int S_pad,
                             double *coef64, float *coef32, int64_t *launches, cudaStream_t st);
