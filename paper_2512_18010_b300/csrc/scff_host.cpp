@@ -1311,6 +1311,13 @@ struct scff_plan_s {
     size_t dev_bytes = 0;
     size_t off_geom = 0, off_coef = 0, off_tab = 0, off_group = 0;
     size_t tab_stride = 0;
+    // Per-job prep of a tensor-core group runs on kLanes streams forked from
+    // the launch stream (job k of the group on lane k mod kLanes), each lane
+    // with its own pair-geometry and coefficient scratch at lane x lane_stride.
+    static constexpr int kLanes = 4;
+    size_t lane_stride = 0;
+    cudaStream_t lane[kLanes] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kLanes] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -1408,7 +1415,8 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     std::vector<std::vector<int4>> gitems(P->groups.size());
     P->off_geom = 0;
     P->off_coef = up1k(geom_max);
-    P->off_tab = P->off_coef + up1k(coef_max);
+    P->lane_stride = up1k(geom_max) + up1k(coef_max);
+    P->off_tab = (size_t)scff_plan_s::kLanes * P->lane_stride;
     P->tab_stride = up1k(tab_max);
     P->off_group = P->off_tab + 3 * P->tab_stride;
     const size_t off_desc = P->off_group + up1k(area_max);
@@ -1478,6 +1486,15 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     // Kernel attributes are set outside any later stream capture.
     for (size_t g = 0; g < P->groups.size(); ++g)
         tc_launch_persistent(P->tc_kind, P->group_zs[g], nullptr, nullptr, 0, 0, nullptr, 0, nullptr, 0);
+    // prep lanes (streams and events of the fork and join)
+    bool lanes_ok = cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l < scff_plan_s::kLanes && lanes_ok; ++l)
+        lanes_ok = cudaStreamCreateWithFlags(&P->lane[l], cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&P->join_ev[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!lanes_ok) {
+        free_plan_any(P);
+        return fail(SCFF_ERR_CUDA, "scff_plan_create: stream or event creation failed");
+    }
     c->plans.push_back(P);
     *out = P;
     return SCFF_OK;
@@ -1491,18 +1508,27 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
     const bool fp64 = P->precision == SCFF_FP64;
     CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     for (size_t g = 0; g < P->groups.size(); ++g) {
+        // the group's jobs are prepared on the lanes, after everything before on st
+        // (the previous group's launch still reads the shared group area)
+        CUDA_TRY(cudaEventRecord(P->fork_ev, st));
+        for (int l = 0; l < scff_plan_s::kLanes; ++l) CUDA_TRY(cudaStreamWaitEvent(P->lane[l], P->fork_ev, 0));
+        int k = 0;
         for (int i : P->groups[g]) {
             const PlanJob &pj = P->jobs[i];
             const PairSetDev &ps = pj.job.basis->dev;
-            CUDA_TRY(launch_pair_geom(ps, geom, st));
+            const int l = k++ % scff_plan_s::kLanes;
+            cudaStream_t ls = P->lane[l];
+            double *lgeom = reinterpret_cast<double *>(base + (size_t)l * P->lane_stride + P->off_geom);
+            void *lcoef = base + (size_t)l * P->lane_stride + P->off_coef;
+            CUDA_TRY(launch_pair_geom(ps, lgeom, ls));
             ++*launches;
-            CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, pj.SB, pj.S_pad, nullptr, (float *)coef, launches, st));
+            CUDA_TRY(launch_pairprep(ps, pj.job.trans->d_T, pj.S, pj.SB, pj.S_pad, nullptr, (float *)lcoef, launches, ls));
             TcArgs ta;
             memset(&ta, 0, sizeof(ta));
             ta.ps = &ps;
-            ta.coef32 = (const float *)coef;
+            ta.coef32 = (const float *)lcoef;
             ta.SB = pj.SB;
-            ta.pair_geom = geom;
+            ta.pair_geom = lgeom;
             ta.qx = pj.job.grid->d_qx;
             ta.qy = pj.job.grid->d_qy;
             ta.qz = pj.job.grid->d_qz;
@@ -1518,7 +1544,11 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             ta.pair = P->pair;
             tc_axes_abs_max(pj.job.grid->hx.data(), ta.nx, pj.job.grid->hy.data(), ta.ny, pj.job.grid->hz.data(), ta.nz,
                             ta.qabs);
-            CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, st));
+            CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, ls));
+        }
+        for (int l = 0; l < scff_plan_s::kLanes; ++l) {
+            CUDA_TRY(cudaEventRecord(P->join_ev[l], P->lane[l]));
+            CUDA_TRY(cudaStreamWaitEvent(st, P->join_ev[l], 0));
         }
         const int drain = c->drain_every >= 0 ? c->drain_every : 8;
         CUDA_TRY(tc_launch_persistent(P->tc_kind, P->group_zs[g],
@@ -1633,6 +1663,11 @@ extern "C" scff_status scff_plan_info(scff_ctx *c, scff_plan_h p, int64_t *info)
 static void free_plan(scff_plan_s *p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    for (int l = 0; l < scff_plan_s::kLanes; ++l) {
+        if (p->lane[l]) cudaStreamDestroy(p->lane[l]);
+        if (p->join_ev[l]) cudaEventDestroy(p->join_ev[l]);
+    }
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     cudaFree(p->dev);
     delete p;
 }
