@@ -2160,15 +2160,25 @@ void tc_build_items(const TcJobDev *jobs, int n_jobs, std::vector<int4> &items) 
 
 using sched::band_runs;
 
+// Per-device slots of the launchers' one-time set-up (kernel attributes, SM
+// and cluster counts): the current device's index, folded into the table.
+constexpr int kAttrDevices = 64;
+static int current_device_slot() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    return dev % kAttrDevices;
+}
+
 
 template <int KIND, int VAR>
 static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
                                 int grid_ctas, int64_t *launches, cudaStream_t st, int *progress, int *queue) {
     using namespace tc;
     using CF = Cfg<KIND, VAR>;
-    static bool attr_set = false;
+    static bool attr_set[kAttrDevices] = {};  // kernel attributes are per device
+    const int dev = current_device_slot();
     cudaError_t e;
-    if (!attr_set) {
+    if (!attr_set[dev]) {
         // The register split inside the kernel assumes exactly LAUNCH_REGS
         // registers per thread at launch; anything else could leave the
         // increasing warpgroups waiting, so refuse to launch.
@@ -2179,7 +2189,7 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
         e = cudaFuncSetAttribute(tc_persistent_kernel<KIND, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  CF::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[dev] = true;
     }
     if (n_items <= 0) return cudaSuccess;
     const int grid = std::max(1, std::min(grid_ctas, n_items));
@@ -2195,16 +2205,17 @@ static cudaError_t pair_t(const TcJobDev *d_jobs, const int4 *d_items, int n_ite
                           int grid_ctas, int64_t *launches, cudaStream_t st, int *progress, int *queue) {
     using namespace tc;
     using PC = PairCfg<KIND>;
-    static bool attr_set = false;
+    static bool attr_set[kAttrDevices] = {};  // kernel attributes are per device
+    const int dev = current_device_slot();
     cudaError_t e;
-    if (!attr_set) {
+    if (!attr_set[dev]) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, tc_pair_kernel<KIND>);
         if (e != cudaSuccess) return e;
         if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
         e = cudaFuncSetAttribute(tc_pair_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[dev] = true;
     }
     if (n_items <= 0) return cudaSuccess;
     const int pairs = std::max(1, std::min(std::min(grid_ctas / 2, tc_num_pairs()), n_items));
@@ -2227,7 +2238,9 @@ static cudaError_t pair_t(const TcJobDev *d_jobs, const int4 *d_items, int n_ite
 }
 
 int tc_num_pairs() {
-    static int n = 0;
+    static int cnt[kAttrDevices] = {};
+    const int slot = current_device_slot();
+    int &n = cnt[slot];
     if (!n) {
         // the pair kernels of both kinds have the same footprint (one CTA per SM)
         using PC = tc::PairCfg<tc::KIND_FP16X2>;
@@ -2337,14 +2350,15 @@ void tc_axes_abs_max(const double *qx, int nx, const double *qy, int ny, const d
 int64_t tc_max_items(int64_t tiles) { return tiles + 2 * (int64_t)tc_num_sms(); }
 
 int tc_num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static int cnt[kAttrDevices] = {};
+    const int slot = current_device_slot();
+    if (!cnt[slot]) {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
+        cnt[slot] = n > 0 ? n : 148;
     }
-    return n;
+    return cnt[slot];
 }
 
 // Single job: prepare it in the workspace, then one persistent launch over
