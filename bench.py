@@ -55,8 +55,8 @@ TC_SOURCES = ["kernels_tc.cu", "tc_internal.h", "tc_schedule.h", "device_common.
 MEASURED_TRAFFIC = {
     ("cfg3", "fp16x2", 0): {"bytes": 640825344 + 334578944, "src": "934acd17cfd39fe8",
                             "profile": "profiles/tc_fp16x2_cfg3_full.md"},
-    ("cfg3", "fp16x2", 3): {"bytes": 841533440 + 400098304, "src": "a00774f4dc029de6",
-                            "profile": "profiles/tc_pair_fp16x2_cfg3_full.md"},
+    ("cfg3", "fp16x2", 3): {"bytes": 844095744 + 401571072, "src": "5c9ae55e44314b10",
+                            "profile": "profiles/tc_pair_fp16x2_cfg3_launches.md"},
 }
 
 
