@@ -94,6 +94,20 @@ def test_ragged_grid_and_odd_state_count(ctx, prec):
     assert rel_err(f[:, idx], ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [scff.FP16X2, scff.BF16X3])
+def test_many_states_on_few_rows(ctx, prec):
+    # 60 states on a 3-point x axis (2 computed rows per state): a 128-row tile then spans 65
+    # states, more than the tiled A-image build stages in shared memory, so the image comes from the
+    # one-thread-per-vector build; the result must meet the same bar.
+    base = W.config1()
+    T = W.transition_matrices(78, 60, base.mol.nbf)
+    job = W.Job(base.mol, T, W.axis(3, 6.0), W.axis(5, 8.0), W.axis(24, 10.0))
+    f, _ = scff.evaluate_job(ctx, job, precision=prec)
+    idx = W.subset_indices(job.nq, 200, 6)
+    ref = oracle.grid_form_factor(job, idx)
+    assert rel_err(f[:, idx], ref) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", [scff.FP64, scff.FP32])
 def test_block_shared_rows_with_padded_states(ctx, prec):
     # z axis a multiple of the 128-point block (every block's points share (ix, iy), the FP32
