@@ -758,7 +758,7 @@ def main():
     ctx = scff.Context(local)
     if not args.no_autotune:
         ctx.set_autotune(True)
-    ctx.set_tc_zstage(args.zstage)
+    ctx.set_tc_variant(args.zstage)
     ctx.set_tc_drain(args.drain)
     b = ctx.basis(job.mol)
     t = ctx.transitions(b, job.T)

@@ -305,11 +305,12 @@ scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
  * when a tensor-core precision was asked for on an explicit q list, or when
  * the autotuner chose the FP32 direct path); out[2] = the W generator
  * variant the tensor-core kernel ran (0 gather, 1 Z staging, 2 prefetch, 3 CTA pairs; see
- * scff_set_tc_zstage), 0 off the tensor cores.  All -1 before the first
+ * scff_set_tc_variant), 0 off the tensor cores.  All -1 before the first
  * call. */
 scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
 
-/* Tensor-core W generator variant (no counterpart in the paper).
+/* Tensor-core launch shape and W generator variant (no counterpart in the
+ * paper); scff_set_tc_zstage is the same call under its earlier name.
  *   0 gather: each generator thread gathers its Y and Z table entries from
  *     global memory and keeps its share of the tile's running sums in
  *     registers.
@@ -331,6 +332,7 @@ scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
  * variants form bitwise the same W and add the same partial sums in the same
  * order, so results do not depend on the choice.  Applies to calls, plans and
  * servers created after it. */
+scff_status scff_set_tc_variant(scff_ctx *ctx, int mode);
 scff_status scff_set_tc_zstage(scff_ctx *ctx, int mode);
 
 /*
@@ -507,7 +509,7 @@ scff_status scff_screening_info(scff_ctx *ctx, scff_trans_h trans, scff_qgrid_h 
  * it, see scff_set_tc_drain).
  * scff_autotune_choice writes five values: out[0] = 1 tensor cores / 0 direct,
  * out[1] = drain, out[2] = state block, out[3] = best time in microseconds,
- * out[4] = the W generator variant chosen (scff_set_tc_zstage's modes 0-3). */
+ * out[4] = the W generator variant chosen (scff_set_tc_variant's modes 0-3). */
 scff_status scff_set_autotune(scff_ctx *ctx, int enable);
 scff_status scff_autotune_choice(scff_ctx *ctx, scff_basis_h basis, scff_trans_h trans,
                                  scff_qgrid_h grid, int precision, int32_t *out);

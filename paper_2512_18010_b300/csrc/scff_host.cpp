@@ -130,12 +130,14 @@ extern "C" scff_status scff_last_path(scff_ctx *c, int32_t *out) {
     return SCFF_OK;
 }
 
-extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) {
-    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: NULL context");
-    if (mode < -1 || mode > 3) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_zstage: %d", mode);
+extern "C" scff_status scff_set_tc_variant(scff_ctx *c, int mode) {
+    if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_variant: NULL context");
+    if (mode < -1 || mode > 3) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_variant: %d", mode);
     c->tc_zstage = mode;
     return SCFF_OK;
 }
+
+extern "C" scff_status scff_set_tc_zstage(scff_ctx *c, int mode) { return scff_set_tc_variant(c, mode); }
 
 extern "C" scff_status scff_set_timing(scff_ctx *c, int enable) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_timing: NULL context");

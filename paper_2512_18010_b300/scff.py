@@ -18,7 +18,7 @@ from . import build as _build
 
 FP64, FP32, BF16X3, TF32X3, BF16X2, FP16X2 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3, "bf16x2": BF16X2, "fp16x2": FP16X2}
-# tensor-core W generator variants (scff_set_tc_zstage modes, scff_last_path's third entry)
+# tensor-core W generator variants (scff_set_tc_variant modes, scff_last_path's third entry)
 GEN_VARIANTS = {0: "gather", 1: "zstage", 2: "prefetch", 3: "pair"}
 RENORM_CONTRACTED = 1
 PURE_D = 2   # d shells are the 5 real solid harmonics
@@ -35,7 +35,7 @@ _SYMBOLS = [
     "scff_create", "scff_destroy", "scff_last_error", "scff_basis", "scff_transitions",
     "scff_qgrid_product", "scff_qgrid_list", "scff_qgrid_size", "scff_form_factor", "scff_sync",
     "scff_kernel_launches", "scff_release_basis", "scff_release_transitions", "scff_release_qgrid",
-    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_set_tc_zstage", "scff_last_path", "scff_form_factor_static",
+    "scff_set_timing", "scff_last_timing", "scff_set_tc_drain", "scff_set_tc_variant", "scff_set_tc_zstage", "scff_last_path", "scff_form_factor_static",
     "scff_plan_create", "scff_plan_run", "scff_plan_run_graph", "scff_plan_info", "scff_release_plan",
     "scff_server_create", "scff_submit", "scff_wait", "scff_cancel", "scff_job_times", "scff_server_stats",
     "scff_server_destroy", "scff_set_autotune", "scff_autotune_choice", "scff_set_screening",
@@ -150,8 +150,9 @@ def load(build_if_missing: bool = True):
     lib.scff_autotune_choice.restype = I32
     lib.scff_set_timing.argtypes = [P, ctypes.c_int]
     lib.scff_set_tc_drain.argtypes = [P, ctypes.c_int]
-    lib.scff_set_tc_zstage.argtypes = [P, ctypes.c_int]
-    lib.scff_set_tc_zstage.restype = I32
+    for name in ("scff_set_tc_variant", "scff_set_tc_zstage"):
+        getattr(lib, name).argtypes = [P, ctypes.c_int]
+        getattr(lib, name).restype = I32
     lib.scff_last_path.argtypes = [P, P]
     lib.scff_last_path.restype = I32
     lib.scff_set_download_bands.argtypes = [P, ctypes.c_int]
@@ -453,11 +454,16 @@ class Context:
         return {"path": path, "precision": names.get(int(out[1])),
                 "variant": GEN_VARIANTS.get(int(out[2])) if path == "tensor_cores" else None}
 
+    def set_tc_variant(self, mode: int):
+        """Tensor-core launch shape and W generator variant: -1 automatic, 0 gather from global memory,
+        1 stage Z and Y in shared memory where the grid allows it, 2 prefetch the next chunk's table
+        entries with the running sums in TMEM, 3 CTA pairs (two SMs share each 256-row MMA and each
+        generates half of W); 2 and 3 where the split allows them (FP16 hi/lo, BF16 hi/lo).  All give
+        bitwise the same results (GEN_VARIANTS names them)."""
+        _check(self.lib.scff_set_tc_variant(self.h, int(mode)))
+
     def set_tc_zstage(self, mode: int):
-        """Tensor-core W generator variant: -1 automatic, 0 gather from global memory, 1 stage Z and Y
-        in shared memory where the grid allows it, 2 prefetch the next chunk's table entries with the
-        running sums in TMEM where the split kind allows it (FP16 hi/lo, BF16 hi/lo); all three give
-        bitwise the same results."""
+        """The same as set_tc_variant (its earlier name)."""
         _check(self.lib.scff_set_tc_zstage(self.h, int(mode)))
 
     def separable_integral(self, basis: Basis, trans: Transitions, qx, wx, qy, wy, qz, wz,
@@ -613,7 +619,7 @@ class Context:
         _check(self.lib.scff_autotune_choice(self.h, basis.handle, trans.handle, grid.handle, int(precision),
                                              _p(out)))
         return {"tensor_cores": bool(out[0]), "drain": int(out[1]), "state_block": int(out[2]),
-                "best_us": int(out[3]), "zstage": int(out[4])}
+                "best_us": int(out[3]), "zstage": int(out[4]), "variant": GEN_VARIANTS.get(int(out[4]))}
 
     def set_timing(self, enable: bool = True):
         _check(self.lib.scff_set_timing(self.h, 1 if enable else 0))

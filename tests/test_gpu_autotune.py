@@ -49,7 +49,7 @@ def test_generator_variants_agree_bitwise(prec):
     try:
         out = {}
         for z in variants:
-            ctx.set_tc_zstage(z)
+            ctx.set_tc_variant(z)
             f, f2 = scff.evaluate_job(ctx, job, precision=prec)
             p = ctx.last_path()
             assert p["path"] == "tensor_cores" and p["variant"] == scff.GEN_VARIANTS[z]
@@ -96,7 +96,7 @@ def test_variant_regimes(prec, drain, variant):
             ctx.set_download_bands(bands)   # overlapped download (automatic, off, two bands)
             out = {}
             for z in (0, variant):
-                ctx.set_tc_zstage(z)
+                ctx.set_tc_variant(z)
                 out[z] = scff.evaluate_job(ctx, job, precision=prec)
                 assert ctx.last_path()["variant"] == scff.GEN_VARIANTS[z]
             assert np.array_equal(out[0][0], out[variant][0]) and np.array_equal(out[0][1], out[variant][1])
