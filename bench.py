@@ -91,9 +91,9 @@ def parse():
     ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--precision", default="fp16x2", choices=["bf16x3", "tf32x3", "bf16x2", "fp16x2", "fp32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+    ap.add_argument("--zstage", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="tensor-core W generator variant: -1 automatic, 0 gather, 1 staged Z/Y, 2 prefetch, "
-                         "3 CTA pairs")
+                         "3 CTA pairs, 4 CTA pairs in the octant form")
     ap.add_argument("--drain", type=int, default=-1,
                     help="tensor-core k-chunks per TMEM accumulation group (-1 = library default, 8)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 path (0 = skip)")
@@ -495,17 +495,32 @@ def make_jobs(fn, n):
                 os.environ[k] = v
 
 
-def tc_useful(jobs, precision, seconds, scff):
-    """Tensor work of a set of jobs on the split-precision path per second: 8 flop per complex
-    multiply-add x (pair,v,w) rows x split products, over the rows (s, ix) of the evaluated
-    half of each antisymmetric grid, against the measured sustained BF16 rate."""
-    pieces = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3, scff.FP16X2: 3}.get(precision)
-    if pieces is None or seconds <= 0:
+def octant_form(precision, variant, scff):
+    """Whether the tensor-core launches of this precision run the octant form on antisymmetric grids
+    (the automatic mode and mode 4, for the kinds with CTA pairs)."""
+    return precision in (scff.FP16X2, scff.BF16X2) and variant in (-1, 4)
+
+
+def tc_flop_per_row(precision, octant):
+    """Executed tensor flop per (pair,v,w) row and evaluated (q*state) unit of the evaluated half:
+    8 per complex multiply-add, 4 in the octant form (eight real sums per octant point cover four
+    units), times the split's piece products."""
+    pieces = {"bf16x3": 6, "tf32x3": 3, "bf16x2": 3, "fp16x2": 3}.get(precision)
+    return None if pieces is None else (4 if octant else 8) * pieces
+
+
+def tc_useful(jobs, precision, seconds, scff, octant=False):
+    """Executed tensor work of a set of jobs on the split-precision path per second (tc_flop_per_row
+    x (pair,v,w) rows over the rows (s, ix) of the evaluated half of each antisymmetric grid), against
+    the measured sustained BF16 rate."""
+    names = {v: k for k, v in scff.PRECISIONS.items()}
+    per = tc_flop_per_row(names.get(precision), octant)
+    if per is None or seconds <= 0:
         return None
     flops = 0
     for j in jobs:
         kvw = pair_stats(j.mol)[2]
-        flops += 8 * pieces * kvw * j.n_states * ((len(j.qx) + 1) // 2) * len(j.qy) * len(j.qz)
+        flops += per * kvw * j.n_states * ((len(j.qx) + 1) // 2) * len(j.qy) * len(j.qz)
     tf = flops / seconds / 1e12
     out = {"tensor_tflops_useful": tf, "flop": float(flops)}
     try:
@@ -517,7 +532,7 @@ def tc_useful(jobs, precision, seconds, scff):
     return out
 
 
-def serving_run(scff, ctx, jobs, precision, fp64_jobs=8):
+def serving_run(scff, ctx, jobs, precision, fp64_jobs=8, variant=-1):
     """The serving stream on the split path and on the plain FP64 GPU path (both through the server).
 
     Split arm (all jobs): saturation throughput (every job submitted at t = 0), latency on an idle
@@ -528,6 +543,7 @@ def serving_run(scff, ctx, jobs, precision, fp64_jobs=8):
     large job shape's FP64 service time measured on one z slab of its grid (4 of 128 planes,
     scaled by the evaluated points); the FP64 rate on the whole stream is estimated from these two
     measured per-kind rates."""
+    octant = octant_form(precision, variant, scff)
     import torch
     handles, outs = [], []
     for job in jobs:
@@ -638,7 +654,7 @@ def serving_run(scff, ctx, jobs, precision, fp64_jobs=8):
         "split": {
             "saturation": {"value": u_all / wall_sat, "unit": UNIT, "wall_s": wall_sat, "capacity_jobs_per_s": cap,
                            "batches": st_sat["batches"], "max_inflight": st_sat["max_inflight"],
-                           "tensor": tc_useful(jobs, precision, wall_sat, scff)},
+                           "tensor": tc_useful(jobs, precision, wall_sat, scff, octant)},
             "idle_server": {"what": "each job submitted when the previous one finished: the latency at arrival "
                                     "rates far below capacity (0.7 x the FP64 path's capacity is "
                                     f"{100 * 0.7 * (est64['capacity_jobs_per_s'] if est64 else cap64) / cap:.2f}% "
@@ -661,9 +677,10 @@ def serving_run(scff, ctx, jobs, precision, fp64_jobs=8):
     }
 
 
-def batch_run(scff, ctx, jobs, precision, steps=3):
+def batch_run(scff, ctx, jobs, precision, steps=3, variant=-1):
     """The batched workload as one plan (persistent launches over a device work queue, one captured
     CUDA graph), replayed: ms per batch, rate, and the algorithmic and useful tensor work rates."""
+    octant = octant_form(precision, variant, scff)
     import torch
     t0 = time.perf_counter()
     specs = []
@@ -696,7 +713,7 @@ def batch_run(scff, ctx, jobs, precision, steps=3):
     alg_tf = alg / (ms / 1e3) / 1e12
     out = {"jobs": len(jobs), "precision": {v: k for k, v in scff.PRECISIONS.items()}[precision],
            "value": units / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "replays_timed": steps,
-           "algorithmic_tflops": alg_tf, "tensor": tc_useful(jobs, precision, ms / 1e3, scff),
+           "algorithmic_tflops": alg_tf, "tensor": tc_useful(jobs, precision, ms / 1e3, scff, octant),
            "setup_s": t_setup, "capture_and_first_replay_s": t_first,
            "graph": "one captured CUDA graph per plan, replayed", "schedule": "device work queue (atomic pull)"}
     try:
@@ -902,16 +919,17 @@ def main():
             fp32["peak_source"] = "of measured: max of the FP32 and packed f32x2 FMA-chain peaks of this run (alu_peaks)"
     if used_tc:
         passes = {scff.BF16X3: 6, scff.TF32X3: 3, scff.BF16X2: 3, scff.FP16X2: 3}[prec]
-        tc_flops = 8 * Kvw * passes              # executed tensor flops per (q, state)
+        zs_used = {v: k for k, v in scff.GEN_VARIANTS.items()}.get(path_used["variant"], 0)
+        per_row = tc_flop_per_row(args.precision, zs_used == 4)
+        tc_flops = per_row * Kvw                 # executed tensor flops per (q, state)
         measured_peak = "bf16_tflops" in peaks
         bf16 = float(peaks.get("bf16_tflops", 1800.0))  # fallback: one earlier B300 measurement
         peak = bf16 * (TF32_PER_BF16 if prec == scff.TF32X3 else 1.0)
         units_eval = S * nx_rows * len(job.qy) * len(job.qz)
         achieved = alg_flops * units_eval / (kern_ms / 1e3) / 1e12
         executed = tc_flops * units_eval / (kern_ms / 1e3) / 1e12
-        zs_used = {v: k for k, v in scff.GEN_VARIANTS.items()}.get(path_used["variant"], 0)
         trec = measured_traffic(args.workload, args.precision, zs_used)
-        roof = {"bound": "tensor", "kernel": "tc_pair_kernel" if zs_used == 3 else "tc_persistent_kernel",
+        roof = {"bound": "tensor", "kernel": "tc_pair_kernel" if zs_used in (3, 4) else "tc_persistent_kernel",
                 "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": trec["bytes"] if trec else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
@@ -919,8 +937,10 @@ def main():
                         f"monomial rows, {n_pair} pairs, {n_ss} s-s pairs (the work the method needs), times "
                         f"{units_eval} evaluated (q*state) units per launch",
                 "executed_tensor_tflops": executed, "executed_frac": executed / peak,
-                "executed_work": f"{tc_flops} tensor flop per (q*state) = 8 flop x {Kvw} (pair,v,w) rows x "
-                                 f"{passes} split products",
+                "executed_work": f"{tc_flops} tensor flop per (q*state) = {per_row // passes} flop x {Kvw} "
+                                 f"(pair,v,w) rows x {passes} split products"
+                                 + (" (octant form: real W, eight real sums per octant point cover four "
+                                    "evaluated units)" if zs_used == 4 else ""),
                 "peak_source": (("of measured: MEASURED_PEAKS.json bf16_tflops" if measured_peak
                                  else "of fallback: 1.8 PFLOP/s BF16 (MEASURED_PEAKS.json absent)")
                                 + (" x nominal TF32/BF16 ratio 0.5" if prec == scff.TF32X3 else "")
@@ -981,10 +1001,10 @@ def main():
             sms.append(e0.elapsed_time(e1))
         sm = float(np.mean(sms))
         kq = float(np.mean(qms))
-        passes_s = {scff.BF16X3: 6, scff.FP16X2: 3}[sp]
+        per_row_s = tc_flop_per_row(side_name, octant_form(sp, args.zstage, scff))
         side = {"precision": side_name, "value": units / (sm / 1e3), "unit": UNIT, "ms_per_step": sm,
                 "qeval_ms": kq, "alg_frac": alg_flops * units_eval / (kq / 1e3) / 1e12 / roof["peak"],
-                "executed_frac": 8 * Kvw * passes_s * units_eval / (kq / 1e3) / 1e12 / roof["peak"]}
+                "executed_frac": per_row_s * Kvw * units_eval / (kq / 1e3) / 1e12 / roof["peak"]}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             sel = torch.from_numpy(W.subset_indices(nq, args.cpu_sample, CPU_SEED)).to(dev)
             fc = f.index_select(1, sel).double().cpu().numpy()
@@ -1054,12 +1074,12 @@ def main():
     serving = None
     if serving_jobs:
         serving = serving_run(scff, ctx, serving_jobs, prec if prec in TC_PRECS else scff.FP16X2,
-                              fp64_jobs=args.serving_fp64_jobs)
+                              fp64_jobs=args.serving_fp64_jobs, variant=args.zstage)
         serving_jobs_keep = serving_jobs
         torch.cuda.empty_cache()
     batch = None
     if batch_jobs:
-        batch = batch_run(scff, ctx, batch_jobs, prec if prec in TC_PRECS else scff.FP16X2)
+        batch = batch_run(scff, ctx, batch_jobs, prec if prec in TC_PRECS else scff.FP16X2, variant=args.zstage)
 
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

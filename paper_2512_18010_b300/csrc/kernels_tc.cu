@@ -143,7 +143,13 @@ template <int KIND> struct Kind {
 //     latency overlaps the W work instead of preceding it.  The additions are
 //     the same, in the same order, as VAR_GATHER's, so both give bitwise the
 //     same tile.
-enum { VAR_GATHER = 0, VAR_ZSTAGE = 1, VAR_PREFETCH = 2, VAR_PAIR = 3 };
+//   VAR_OCT (the kinds with CTA pairs, antisymmetric grids): the CTA-pair
+//     launch with the jobs in the octant form (TcJobDev::oct), which the
+//     pair kernel runs per job.
+enum { VAR_GATHER = 0, VAR_ZSTAGE = 1, VAR_PREFETCH = 2, VAR_PAIR = 3, VAR_OCT = 4 };
+// Octant form: points per CTA-pair tile and per CTA.
+constexpr int OCT_PTS = 32;
+constexpr int OCT_PTH = OCT_PTS / 2;
 template <int KIND, int VAR> struct Cfg {
     using KD = Kind<KIND>;
     static constexpr bool ZS = VAR == VAR_ZSTAGE;
@@ -553,8 +559,10 @@ static Layout make_layout(const PairSetDev &ps, int S, int nx, int ny, int nz, i
     o = align_up(o + 256, 1024);
     L.off_A = o;
     o = align_up(o + (size_t)L.n_mt * L.nkc * a_stage, 1024);
-    // a split never needs more than 2P partial tiles (R * s <= 2P)
-    L.part_tiles = std::min<int64_t>(2 * (int64_t)tc_num_sms(), (int64_t)L.n_mt * L.n_nt * 16);
+    // a split never needs more than 2P partial tiles (R * s <= 2P); the
+    // octant form's column tiles are counted too
+    const int64_t n_oct_nt = ((int64_t)((ny + 1) / 2) * ((nz + 1) / 2) + OCT_PTS - 1) / OCT_PTS;
+    L.part_tiles = std::min<int64_t>(2 * (int64_t)tc_num_sms(), (int64_t)L.n_mt * std::max<int64_t>(L.n_nt, n_oct_nt) * 16);
     L.off_part = o;
     o = align_up(o + sizeof(float2) * (size_t)L.part_tiles * BM * BN, 1024);
     L.off_cnt = o;
@@ -999,6 +1007,59 @@ __device__ __forceinline__ bool drain_final(int gg, bool only, uint64_t *accFull
     return true;
 }
 
+// Octant form, one row m of a finished tile: this thread's 16 points
+// (iy, iz) (columns 32 nt + 16 hs + p of the octant grid) each hold the
+// eight real sums S_abc = sum_k A^a Y^b Z^c (a, b, c: real or imaginary
+// part; sr[16 c' + p] = S_r and si[16 c' + p] = S_i of the W row
+// c' = 2 [b = Im] + [c = Im]).  Y and Z at the mirrored axis points are the
+// complex conjugates (q_y[ny-1-iy] = -q_y[iy]), so with sy, sz = +-1
+//   Re f = S_rrr - sy sz S_rii - sz S_iri - sy S_iir
+//   Im f = S_irr - sy sz S_iii + sz S_rri + sy S_rir
+// at (ix, iy or ny-1-iy, iz or nz-1-iz), and f(-q) = conj(f(q)) at the
+// mirrored row.  Points that are their own mirror are written once.
+template <int CQ>
+__device__ __forceinline__ void oct_write(const TcJobDev &J, const int4 &item, int m, int hs, const float (&sr)[CQ],
+                                          const float (&si)[CQ]) {
+    const int sidx = m / J.nx, ix = m % J.nx;
+    const int ixm = J.nxf - 1 - ix;
+    const bool mir = ixm != ix;
+    float2 *frow = J.f + (size_t)sidx * J.nq + (size_t)ix * J.N;
+    float2 *mrow = J.f + (size_t)sidx * J.nq + (size_t)ixm * J.N;
+    float *f2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ix * J.N : nullptr;
+    float *m2row = J.f2 ? J.f2 + (size_t)sidx * J.nq + (size_t)ixm * J.N : nullptr;
+    const float sc = J.scale;
+    const int64_t n0 = (int64_t)item.z * OCT_PTS + hs * OCT_PTH;
+#pragma unroll
+    for (int p = 0; p < OCT_PTH; ++p) {
+        const int64_t no = n0 + p;
+        if (no >= J.Noct) continue;
+        const int iy = (int)(no / J.nzh), iz = (int)(no % J.nzh);
+        const int iy2 = J.ny - 1 - iy, iz2 = J.nz - 1 - iz;
+        const float P1 = sr[p], Q3 = sr[OCT_PTH + p], Q4 = sr[2 * OCT_PTH + p], P2 = sr[3 * OCT_PTH + p];
+        const float Q1 = si[p], P3 = si[OCT_PTH + p], P4 = si[2 * OCT_PTH + p], Q2 = si[3 * OCT_PTH + p];
+        const float a = P1 - P2, b = P1 + P2, c = P3 + P4, d = P3 - P4;
+        const float e = Q1 - Q2, g = Q1 + Q2, h = Q3 + Q4, l = Q3 - Q4;
+        float2 v[4];
+        v[0] = make_float2(sc * (a - c), sc * (e + h));  // (+qy, +qz)
+        v[1] = make_float2(sc * (b + d), sc * (g - l));  // (+qy, -qz)
+        v[2] = make_float2(sc * (b - d), sc * (g + l));  // (-qy, +qz)
+        v[3] = make_float2(sc * (a + c), sc * (e - h));  // (-qy, -qz)
+        const int ys[4] = {iy, iy, iy2, iy2}, zs[4] = {iz, iz2, iz, iz2};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (((r & 2) && iy2 == iy) || ((r & 1) && iz2 == iz)) continue;
+            const int64_t nn = (int64_t)ys[r] * J.nz + zs[r];
+            const float a2 = v[r].x * v[r].x + v[r].y * v[r].y;
+            frow[nn] = v[r];
+            if (f2row) f2row[nn] = a2;
+            if (mir) {
+                mrow[J.N - 1 - nn] = make_float2(v[r].x, -v[r].y);
+                if (m2row) m2row[J.N - 1 - nn] = a2;
+            }
+        }
+    }
+}
+
 // Writes one finished tile (this thread's row of the warp's region): a
 // part of a split tile stores its raw partial sums, and the last part of a
 // region to arrive sums all parts in part order; a whole tile (or the last
@@ -1055,6 +1116,12 @@ __device__ __forceinline__ void tile_epilogue(const TcJobDev &J, const int4 &ite
             for (int j = 0; j < CQ; ++j) {
                 acc_re[j] = pow2_scale(acc_re[j], -G);
                 acc_im[j] = pow2_scale(acc_im[j], -G);
+            }
+        }
+        if constexpr (CQ == 4 * OCT_PTH) {
+            if (J.oct) {
+                oct_write(J, item, m, colh / CQ, acc_re, acc_im);
+                return;
             }
         }
         const int sidx = m / J.nx, ix = m % J.nx;
@@ -1804,12 +1871,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         } else if (warp == 1 && lane == 0) {
             // ---------------- even CTA: MMA issuer for the pair
             constexpr uint32_t ID2 = idesc_mma<KD::FMT, 2 * BN, 2 * BM>(false);  // M = 256, N = 256
+            constexpr uint32_t IDO = idesc_mma<KD::FMT, BN, 2 * BM>(false);      // octant form: M = 256, N = 128
             int gc = 0, gbase = 0;
             for (int ic = 0;; ++ic) {
                 const int idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, 0);
                 if (idx == -2) *abort_flag = 1;
                 if (idx < 0) break;
-                const int nkc = items[idx].w;
+                const int4 itm = items[idx];
+                const int nkc = itm.w;
+                const bool oct = jobs[item_job(itm.x)].oct != 0;
                 const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
                 bool ok = true;
                 for (int it = 0; it < nkc; ++it, ++gc) {
@@ -1830,18 +1900,37 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint32_t t_d = tmem + set * (2 * BN);
                     const uint32_t a0 = smem_u32(smem + s * STAGE);
                     const uint32_t w0 = a0 + A_STAGE;
+                    if (oct) {
+                        // real W (NP arrays of 64 rows per CTA): S_r = Ar W in columns
+                        // [0, BN) of the set, S_i = Ai W in [BN, 2 BN)
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t ko = kk * 32;  // 32 bytes = one MMA K step
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t ko = kk * 32;
 #pragma unroll
-                        for (int pq = 0; pq < KD::NPROD; ++pq) {
-                            const int qa = prod_a(pq), qw = prod_w(pq);
-                            const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
-                            const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
-                            const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
-                            const uint32_t pb = w0 + qw * 3 * W_ARRH + ko;
-                            mma_issue_pair(t_d, ar, smem_desc_sw64(pb + W_ARRH), ID2, acc);  // += [Ar Wr | Ar Wi] per half
-                            mma_issue_pair(t_d, ai, smem_desc_sw64(pb), ID2, 1);             // += [-Ai Wi | Ai Wr]
+                            for (int pq = 0; pq < KD::NPROD; ++pq) {
+                                const int qa = prod_a(pq), qw = prod_w(pq);
+                                const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
+                                const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
+                                const uint64_t wb = smem_desc_sw64(w0 + qw * W_ARRH + ko);
+                                const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
+                                mma_issue_pair(t_d, ar, wb, IDO, acc);
+                                mma_issue_pair(t_d + BN, ai, wb, IDO, acc);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t ko = kk * 32;  // 32 bytes = one MMA K step
+#pragma unroll
+                            for (int pq = 0; pq < KD::NPROD; ++pq) {
+                                const int qa = prod_a(pq), qw = prod_w(pq);
+                                const uint64_t ar = smem_desc_sw64(a0 + qa * A_ARR + ko);
+                                const uint64_t ai = smem_desc_sw64(a0 + (NP + qa) * A_ARR + ko);
+                                const uint32_t acc = (first && kk == 0 && pq == 0) ? 0u : 1u;
+                                const uint32_t pb = w0 + qw * 3 * W_ARRH + ko;
+                                mma_issue_pair(t_d, ar, smem_desc_sw64(pb + W_ARRH), ID2, acc);  // += [Ar Wr | Ar Wi] per half
+                                mma_issue_pair(t_d, ai, smem_desc_sw64(pb), ID2, 1);             // += [-Ai Wi | Ai Wr]
+                            }
                         }
                     }
                     mma_commit_pair(&empty[s]);
@@ -1876,12 +1965,26 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int mp = item_mt(item.y), k0 = item_k0(item.y);
             const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
             const int ngroups = (nkc + G - 1) / G;
-            const int64_t n = (int64_t)item.z * BN + rank * BNH + wrow;
+            // octant form: this thread's point (16 per CTA) and W row product
+            // (Re or Im of Y) x (Re or Im of Z), W row 16 cmb + point
+            const bool oct = J.oct != 0;
+            const int opt = gt & (OCT_PTH - 1), cmb = (gt / OCT_PTH) & 3;
             int iy = 0, iz = 0;
-            if (n < J.N) {
-                iz = (int)(n % J.nz);
-                iy = (int)(n / J.nz);
+            if (oct) {
+                const int64_t no = (int64_t)item.z * OCT_PTS + rank * OCT_PTH + opt;
+                if (no < J.Noct) {
+                    iz = (int)(no % J.nzh);
+                    iy = (int)(no / J.nzh);
+                }
+            } else {
+                const int64_t n = (int64_t)item.z * BN + rank * BNH + wrow;
+                if (n < J.N) {
+                    iz = (int)(n % J.nz);
+                    iy = (int)(n / J.nz);
+                }
             }
+            // drains: columns of Re and Im (or of S_r and S_i) of this thread's half
+            const int dre0 = oct ? hsel * BNH : hsel * 2 * BNH, dim_off = oct ? BN : BNH;
             const float2 *Yc = J.Y + iy;
             const float2 *Zc = J.Z + iz;
             float acc_re[CQ], acc_im[CQ];
@@ -1913,7 +2016,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                     break;
                 }
                 uint8_t *wst = smem + s * STAGE + A_STAGE;
-                {
+                if (oct) {
+                    // real W: (Re or Im of Y) x (Re or Im of Z), one 64-row array per piece
+                    float v[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) v[e] = __fmul_rn((cmb & 2) ? y[e].y : y[e].x, (cmb & 1) ? z[e].y : z[e].x);
+                    uint4 pc_[NP];
+                    split_vec<KIND>(v, pc_);
+                    const uint32_t off = sw64_offset<KIND>(cmb * OCT_PTH + opt, kq * KQ);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) *reinterpret_cast<uint4 *>(wst + q * W_ARRH + off) = pc_[q];
+                } else {
                     float re[V], im[V];
 #pragma unroll
                     for (int e = 0; e < V; ++e) w_elem(y[e], z[e], re[e], im[e]);
@@ -1935,8 +2048,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&fullW[s]);  // the odd CTA's relay forwards it
                 while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
-                    if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, hsel * 2 * BNH,
-                                              BNH, acc_re, acc_im, abort_flag)) {
+                    if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, dre0, dim_off, acc_re,
+                                              acc_im, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -1946,8 +2059,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
             __syncwarp();
             while (ok && drained < ngroups) {
-                if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, hsel * 2 * BNH, BNH,
-                                          acc_re, acc_im, abort_flag))
+                if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, dre0, dim_off, acc_re,
+                                          acc_im, abort_flag))
                     ok = false;
                 ++drained;
             }
@@ -2002,10 +2115,12 @@ size_t tc_job_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kin
 
 size_t tc_workspace_bytes(const PairSetDev &ps, int S, int nx, int ny, int nz, int kind) {
     const tc::Layout L = layout_of(ps, S, nx, ny, nz, kind);
+    const int64_t n_oct_nt = ((int64_t)((ny + 1) / 2) * ((nz + 1) / 2) + tc::OCT_PTS - 1) / tc::OCT_PTS;
     // descriptors (one per band) and work items: the tiles plus at most 2P
     // parts of the tail split per band
     return L.total + 1024 + 256 + (sizeof(TcJobDev) * kMaxBands + 255) / 256 * 256 +
-           sizeof(int4) * (size_t)tc_max_items((int64_t)L.n_mt * L.n_nt + (int64_t)(kMaxBands - 1) * 2 * tc_num_sms());
+           sizeof(int4) * (size_t)tc_max_items((int64_t)L.n_mt * std::max<int64_t>(L.n_nt, n_oct_nt) +
+                                               (int64_t)(kMaxBands - 1) * 2 * tc_num_sms());
 }
 
 // Descriptor of one job whose tables and A image live in `ws`.
@@ -2020,6 +2135,7 @@ static tc::Layout job_layout(const TcArgs &a) {
     L.M = a.S * nxr;
     L.M_pad = (L.M + mq - 1) / mq * mq;
     L.n_mt = L.M_pad / BM;
+    if (a.oct) L.n_nt = (int)(((int64_t)((a.ny + 1) / 2) * ((a.nz + 1) / 2) + OCT_PTS - 1) / OCT_PTS);
     return L;
 }
 
@@ -2056,6 +2172,10 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->nsplit = sp;
     jd->split_tiles = sp ? R : 0;
     jd->tmax = Kind<KIND>::FP16 ? reinterpret_cast<const unsigned long long *>(w + L.off_tmax) : nullptr;
+    jd->oct = a.oct && a.pair && a.half ? 1 : 0;
+    jd->nyh = (a.ny + 1) / 2;
+    jd->nzh = (a.nz + 1) / 2;
+    jd->Noct = (int64_t)jd->nyh * jd->nzh;
 }
 
 // Tables, k-index and the A image of one job in `ws` (tc_job_bytes bytes).
@@ -2066,6 +2186,7 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
     const PairSetDev &ps = *a.ps;
     const Layout L = job_layout<KIND>(a);
     if (L.n_mt > (1 << 24)) return cudaErrorInvalidConfiguration;
+    if (a.oct && !(a.pair && a.half)) return cudaErrorInvalidValue;
     uint8_t *w = static_cast<uint8_t *>(ws);
     float2 *X = reinterpret_cast<float2 *>(w + L.off_X);
     float2 *Y = reinterpret_cast<float2 *>(w + L.off_Y);
@@ -2269,7 +2390,7 @@ int tc_num_pairs() {
 }
 
 int tc_variant_preferred(int kind) {
-    return kind == tc::KIND_TF32X2 ? tc::VAR_ZSTAGE : tc_prefetch_ok(kind) ? tc::VAR_PAIR : tc::VAR_GATHER;
+    return kind == tc::KIND_TF32X2 ? tc::VAR_ZSTAGE : tc_prefetch_ok(kind) ? tc::VAR_OCT : tc::VAR_GATHER;
 }
 
 bool tc_prefetch_ok(int kind) { return kind == tc::KIND_FP16X2 || kind == tc::KIND_BF16X2; }
@@ -2285,16 +2406,20 @@ int tc_variant_resolve(int kind, int requested, bool zstage_grid) {
     if (requested == tc::VAR_ZSTAGE) return kind != tc::KIND_BF16X3 && zstage_grid ? tc::VAR_ZSTAGE : tc::VAR_GATHER;
     if (requested == tc::VAR_PREFETCH) return tc_prefetch_ok(kind) ? tc::VAR_PREFETCH : tc::VAR_GATHER;
     if (requested == tc::VAR_PAIR) return tc_prefetch_ok(kind) ? tc::VAR_PAIR : tc::VAR_GATHER;
+    if (requested == tc::VAR_OCT) return tc_prefetch_ok(kind) ? tc::VAR_OCT : tc::VAR_GATHER;
     return tc::VAR_GATHER;
 }
 
 int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs) {
     // jobs laid out for pairs run the pair launch; others never do
-    bool pair = n_jobs > 0;
-    for (int j = 0; j < n_jobs; ++j) pair = pair && jobs[j].pair && !jobs[j].ylm;
-    if (pair) return tc::VAR_PAIR;
+    bool pair = n_jobs > 0, oct = false;
+    for (int j = 0; j < n_jobs; ++j) {
+        pair = pair && jobs[j].pair && !jobs[j].ylm;
+        oct = oct || jobs[j].oct;
+    }
+    if (pair) return oct ? tc::VAR_OCT : tc::VAR_PAIR;
     const int v = tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
-    return v == tc::VAR_PAIR ? tc::VAR_GATHER : v;
+    return v == tc::VAR_PAIR || v == tc::VAR_OCT ? tc::VAR_GATHER : v;
 }
 
 cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, const int4 *d_items, int n_items,
@@ -2313,7 +2438,7 @@ cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, 
                                                           launches, st, progress, queue);
         }
         if constexpr (tc::Kind<KIND>::STAGE_KO && !tc::Kind<KIND>::TF32) {
-            if (variant == tc::VAR_PAIR)
+            if (variant == tc::VAR_PAIR || variant == tc::VAR_OCT)
                 return pair_t<KIND>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress,
                                     queue);
         }
@@ -2371,7 +2496,11 @@ cudaError_t launch_tc_form_factor(const TcArgs &args, int64_t *launches, cudaStr
     const bool can_band =
         args.f_host && args.copy_st && args.progress_dev && args.progress_host && args.ev_done && args.ev_copied;
     TcArgs a = args;
-    a.pair = tc_variant_resolve(a.kind, a.zstage, false) == tc::VAR_PAIR ? 1 : 0;
+    {
+        const int v = tc_variant_resolve(a.kind, a.zstage, false);
+        a.pair = v == tc::VAR_PAIR || v == tc::VAR_OCT ? 1 : 0;
+        a.oct = v == tc::VAR_OCT && a.half ? 1 : 0;
+    }
     const size_t jb = tc_job_bytes(*a.ps, a.S, a.nx, a.ny, a.nz, a.kind);
     if (jb + 1024 + sizeof(TcJobDev) > a.ws_bytes) return cudaErrorInvalidValue;
     TcJobDev jd;
@@ -2388,9 +2517,20 @@ cudaError_t launch_tc_form_factor(const TcArgs &args, int64_t *launches, cudaStr
     const int grid = per * units;
     const int n_rows = jd.n_mt / per;  // m-tiles, or m-tile pairs
     int bounds[kMaxBands + 1];
-    const int G = can_band ? sched::band_bounds(n_rows, jd.n_nt, jd.mirror != 0, jd.N, BN, a.n_bands, units,
-                                                first_split, jd.nsplit, kMaxBands, bounds)
-                           : 1;
+    // Bands are ranges of column tiles (d = min(nt, n_nt-1-nt) with the
+    // mirror).  In the octant form they are ranges of octant y rows iy (each
+    // band also covers the mirrored rows ny-1-iy), banded only when a y row
+    // is a whole number of tiles.
+    const bool oct = jd.oct != 0;
+    const int oct_row_tiles = jd.nzh / tc::OCT_PTS;
+    int G = 1;
+    if (can_band && !oct)
+        G = sched::band_bounds(n_rows, jd.n_nt, jd.mirror != 0, jd.N, BN, a.n_bands, units, first_split, jd.nsplit,
+                               kMaxBands, bounds);
+    else if (can_band && oct && jd.nzh % tc::OCT_PTS == 0)
+        G = sched::band_bounds(n_rows, a.ny, true, jd.N, a.nz, a.n_bands, units, first_split, jd.nsplit, kMaxBands,
+                               bounds);
+    const int64_t unit_cols = oct ? a.nz : BN;  // output columns per band unit
     std::vector<int4> items;
     int runs[kMaxBands][2][2], nruns[kMaxBands];
     int64_t band_end[kMaxBands];
@@ -2400,10 +2540,18 @@ cudaError_t launch_tc_form_factor(const TcArgs &args, int64_t *launches, cudaStr
         // tiles band by band; band g ends after the items of its tiles
         std::vector<int2> tiles;
         for (int g = 0; g < G; ++g) {
-            nruns[g] = band_runs(jd.n_nt, jd.mirror != 0, bounds[g], bounds[g + 1], runs[g]);
-            for (int mt = 0; mt < n_rows; ++mt)
-                for (int r = 0; r < nruns[g]; ++r)
-                    for (int nt = runs[g][r][0]; nt < runs[g][r][1]; ++nt) tiles.push_back(make_int2(mt, nt));
+            if (oct) {
+                // octant y rows [b_g, b_g+1): their tiles, and the output rows they fill
+                nruns[g] = band_runs(a.ny, true, bounds[g], bounds[g + 1], runs[g]);
+                for (int mt = 0; mt < n_rows; ++mt)
+                    for (int iy = bounds[g]; iy < bounds[g + 1]; ++iy)
+                        for (int t = 0; t < oct_row_tiles; ++t) tiles.push_back(make_int2(mt, iy * oct_row_tiles + t));
+            } else {
+                nruns[g] = band_runs(jd.n_nt, jd.mirror != 0, bounds[g], bounds[g + 1], runs[g]);
+                for (int mt = 0; mt < n_rows; ++mt)
+                    for (int r = 0; r < nruns[g]; ++r)
+                        for (int nt = runs[g][r][0]; nt < runs[g][r][1]; ++nt) tiles.push_back(make_int2(mt, nt));
+            }
             const int64_t t = (int64_t)tiles.size();
             band_end[g] = t <= first_split ? t : first_split + (t - first_split) * jd.nsplit;
         }
@@ -2465,7 +2613,8 @@ cudaError_t launch_tc_form_factor(const TcArgs &args, int64_t *launches, cudaStr
             else std::this_thread::yield();
         }
         for (int r = 0; r < nruns[g]; ++r) {
-            const int64_t c0 = (int64_t)runs[g][r][0] * BN, c1 = std::min<int64_t>(jd.N, (int64_t)runs[g][r][1] * BN);
+            const int64_t c0 = (int64_t)runs[g][r][0] * unit_cols,
+                          c1 = std::min<int64_t>(jd.N, (int64_t)runs[g][r][1] * unit_cols);
             if (c1 <= c0) continue;
             e = cudaMemcpy2DAsync(a.f_host + 2 * c0, 8 * jd.N, a.f + 2 * c0, 8 * jd.N, 8 * (c1 - c0), rows,
                                   cudaMemcpyDeviceToHost, a.copy_st);

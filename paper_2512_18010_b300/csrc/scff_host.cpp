@@ -132,7 +132,7 @@ extern "C" scff_status scff_last_path(scff_ctx *c, int32_t *out) {
 
 extern "C" scff_status scff_set_tc_variant(scff_ctx *c, int mode) {
     if (!c) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_variant: NULL context");
-    if (mode < -1 || mode > 3) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_variant: %d", mode);
+    if (mode < -1 || mode > 4) return fail(SCFF_ERR_INVALID_ARG, "scff_set_tc_variant: %d", mode);
     c->tc_zstage = mode;
     return SCFF_OK;
 }
@@ -855,7 +855,7 @@ static scff_status autotune(scff_ctx *c, const PairSetDev &ps, scff_trans_s *t, 
     // tensor cores with both W generator variants (bitwise the same results) unless the
     // context fixes one, then the FP32 direct path's state blocks
     const int kind = tc_kind_of_precision(precision);
-    for (int zs : {3, 2, 1, 0})
+    for (int zs : {4, 3, 2, 1, 0})
         if ((c->tc_zstage < 0 || c->tc_zstage == zs) && kind >= 0 && tc_variant_resolve(kind, zs, g->nz % 128 == 0) == zs)
             cand.push_back({1, 8, 8, zs});
     for (int sb : {8, 12, 16}) cand.push_back({0, 0, sb, 0});
@@ -1308,6 +1308,7 @@ struct scff_plan_s {
     std::vector<int> group_nitems;
     std::vector<char> group_zs;                   // W generator variant of each group's launch
     int pair = 0;                                 // jobs laid out for the CTA-pair launch
+    int oct = 0;                                  // ... in the octant form (on antisymmetric grids)
     size_t off_queue = 0;                         // device int: the launches' work-queue counter
     void *dev = nullptr;
     size_t dev_bytes = 0;
@@ -1344,7 +1345,11 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     P->precision = precision;
     P->tc_kind = tc_kind_of_precision(precision);
     // jobs laid out for the CTA-pair launch when that variant is asked for (it never changes a result)
-    P->pair = P->tc_kind >= 0 && tc_variant_resolve(P->tc_kind, zstage_mode(c, precision), false) == 3 ? 1 : 0;
+    {
+        const int v = P->tc_kind >= 0 ? tc_variant_resolve(P->tc_kind, zstage_mode(c, precision), false) : 0;
+        P->pair = v == 3 || v == 4 ? 1 : 0;
+        P->oct = v == 4 ? 1 : 0;
+    }
     P->SB = fp64 ? 4 : 8;
     uint64_t budget = workspace_bytes ? workspace_bytes : std::min<uint64_t>(c->budget, 64ull << 30);
     size_t geom_max = 256, coef_max = 256, tab_max = 256;
@@ -1437,7 +1442,10 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
             const PlanJob &pj = P->jobs[i];
             const int64_t M = (int64_t)pj.S * pj.job.grid->nx;
             const int64_t N = (int64_t)pj.job.grid->ny * pj.job.grid->nz;
-            nitems_est[g] += (size_t)tc_max_items(((M + 127) / 128) * ((N + 127) / 128));
+            // column tiles: 128 columns, or 32 octant points in the octant form
+            const int64_t Noct = (int64_t)((pj.job.grid->ny + 1) / 2) * ((pj.job.grid->nz + 1) / 2);
+            const int64_t n_nt = std::max((N + 127) / 128, (Noct + 31) / 32);
+            nitems_est[g] += (size_t)tc_max_items(((M + 127) / 128) * n_nt);
         }
         items_bytes += up1k(sizeof(int4) * nitems_est[g]);
     }
@@ -1465,12 +1473,18 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
             ta.kind = P->tc_kind;
             ta.half = pj.half;
             ta.pair = P->pair;
+            ta.oct = P->oct && pj.half;
             TcJobDev jd;
             memset(&jd, 0, sizeof(jd));
             tc_job_desc(ta, base + P->off_group + pj.region, &jd);
             gdesc[g].push_back(jd);
         }
         tc_build_items(gdesc[g].data(), (int)gdesc[g].size(), gitems[g]);
+        if (gitems[g].size() > nitems_est[g]) {
+            cudaFree(P->dev);
+            delete P;
+            return fail(SCFF_ERR_INVALID_ARG, "scff_plan_create: work list larger than its reserved space");
+        }
         P->group_items[g] = ioff;
         P->group_nitems[g] = (int)gitems[g].size();
         P->group_zs[g] = (char)tc_variant_for(P->tc_kind, zstage_mode(c, precision), gdesc[g].data(), (int)gdesc[g].size());
@@ -1544,6 +1558,7 @@ static scff_status plan_launch(scff_plan_s *P, cudaStream_t st, int64_t *launche
             ta.kind = P->tc_kind;
             ta.half = pj.half;
             ta.pair = P->pair;
+            ta.oct = P->oct && pj.half;
             tc_axes_abs_max(pj.job.grid->hx.data(), ta.nx, pj.job.grid->hy.data(), ta.ny, pj.job.grid->hz.data(), ta.nz,
                             ta.qabs);
             CUDA_TRY(tc_prep_job(ta, base + P->off_group + pj.region, nullptr, launches, ls));

@@ -263,7 +263,11 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             ta.f2 = (float *)f2dev;
             ta.kind = tc_kind_of(sv->precision);
             ta.half = j->half;
-            ta.pair = tc_variant_resolve(ta.kind, sv->variant, false) == 3 ? 1 : 0;
+            {
+                const int v = tc_variant_resolve(ta.kind, sv->variant, false);
+                ta.pair = v == 3 || v == 4 ? 1 : 0;
+                ta.oct = v == 4 && j->half ? 1 : 0;
+            }
             tc_axes_abs_max(j->ax[0].data(), j->req.nx, j->ax[1].data(), j->req.ny, j->ax[2].data(), j->req.nz,
                             ta.qabs);
             TcJobDev jd;

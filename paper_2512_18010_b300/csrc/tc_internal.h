@@ -31,10 +31,13 @@ struct TcArgs {
     int kind;                  // 0: BF16 hi/lo, 1: BF16 hi/mid/lo, 2: TF32 hi/lo, 3: FP16 hi/lo
     double qabs[3];            // largest |q| of each axis (bounds of the FP16 kind's scaling)
     int drain_every;           // k-chunks per TMEM accumulation (0 = whole K)
-    int zstage;                // W generator variant requested (tc_variant_resolve): 0 gather, 1 Z staging, 2 prefetch, 3 CTA pairs
+    int zstage;                // W generator variant requested (tc_variant_resolve): 0 gather, 1 Z staging, 2 prefetch, 3 CTA pairs, 4 CTA pairs in the octant form
     // 1: the job is laid out for the CTA-pair launch (m-tiles padded to an
     // even count; set by the launchers from the resolved variant)
     int pair;
+    // 1 (with pair and half): the job runs in the octant form of the CTA-pair
+    // launch (see TcJobDev::oct); set by the launchers from the resolved variant
+    int oct;
     // 1: the three axes are antisymmetric (q[n-1-i] = -q[i]); only the rows
     // ix < ceil(nx/2) are computed and f(-q) = conj(f(q)) fills the rest
     int half;
@@ -91,6 +94,15 @@ struct TcJobDev {
     // FP16 kind: FP64 bits of the bound of the job's largest term, from which
     // the job exponent of the scaled A is derived (null for the other kinds)
     const unsigned long long *tmax;
+    // 1 (pair jobs on antisymmetric grids): octant form.  The columns are the
+    // Noct = nyh x nzh points (iy, iz) with iy < nyh = ceil(ny/2) and
+    // iz < nzh = ceil(nz/2), 32 per tile; W is real, one row per point and
+    // product (Re or Im of Y) x (Re or Im of Z), and Ar and Ai each multiply
+    // it into their own accumulator.  The eight real sums of a row and point
+    // give f at (ix, +-qy, +-qz) and, by f(-q) = conj(f(q)), at the mirrored
+    // row: half the tensor work and half the W values per output.
+    int oct, nyh, nzh;
+    int64_t Noct;
 };
 
 // Split kind of a tensor-core precision (scff_precision), -1 for the others.
