@@ -177,20 +177,26 @@ template <int KIND, int VAR> struct Cfg {
 // [Re | Im] of columns 0-63 followed by [Re | Im] of columns 64-127, for the
 // CTA's own rows.  Per SM the MMA work per chunk is that of the single-CTA
 // kernel, and the W generation half of it.
-template <int KIND> struct PairCfg {
+// OCTK: the build for launches whose jobs all run in the octant form (real
+// W: one 64-row array per piece and CTA), whose smaller stages leave room for
+// a fifth.
+template <int KIND, bool OCTK = false> struct PairCfg {
     using KD = Kind<KIND>;
     static constexpr int BNH = BN / 2;                     // W rows (complex columns) per CTA
     static constexpr int W_ARRH = BNH * ROW_BYTES;         // one 64-row W array
-    static constexpr int W_STAGE = 3 * KD::NP * W_ARRH;
+    static constexpr int W_STAGE = (OCTK ? 1 : 3) * KD::NP * W_ARRH;
     static constexpr int STAGE = KD::A_STAGE + W_STAGE;
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = OCTK ? 5 : 4;
     static constexpr int KQ = KD::BK / 4;                  // k per generator thread (four per W row)
     static constexpr int KO_BYTES = GEN_WARPS * 2 * KQ * 8;
     static constexpr int SMEM_BYTES = STAGES * STAGE + 1024 + BAR_BYTES + KO_BYTES;
     static_assert(KD::FUSE && KD::STAGE_KO && !KD::TF32, "pairs are built for the 16-bit two-piece kinds");
     static_assert(KQ == KD::PER_VEC, "one 16-byte vector per generator thread and chunk");
     static_assert(4 * BNH == GEN_WARPS * 32, "four generator threads per W row");
-    static_assert(STAGES <= 4 && SMEM_BYTES <= 232448, "shared memory budget");
+    static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+    // mbarrier and flag slots (8 bytes each) in the BAR_BYTES region
+    static constexpr int BO = 3 * STAGES;
+    static_assert((BO + 18) * 8 <= BAR_BYTES, "barrier region");
 };
 
 // Piece orders of the kept products (A piece, W piece).
@@ -1747,28 +1753,29 @@ __device__ __forceinline__ bool drain_group_pair(int gg, uint64_t *accFull, uint
 //     a set on the even CTA's accEmpty), then write the CTA's half tile.
 // The per-tile arithmetic (W elements, MMA order, drain groups, sums) is the
 // single-CTA kernel's, so the two launches give bitwise the same results.
-template <int KIND>
+template <int KIND, bool OCTK>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_pair_kernel(const TcJobDev *__restrict__ jobs, const int4 *__restrict__ items, int n_items, int drain_every,
                    int *err, int *progress, int *queue) {
     using KD = Kind<KIND>;
-    using PC = PairCfg<KIND>;
+    using PC = PairCfg<KIND, OCTK>;
     constexpr int BK = KD::BK, V = KD::PER_VEC, NP = KD::NP, STAGES = PC::STAGES, KQ = PC::KQ;
     constexpr int A_STAGE = KD::A_STAGE, STAGE = PC::STAGE, W_ARRH = PC::W_ARRH, BNH = PC::BNH;
     constexpr int CQ = BN / 2;  // accumulator columns (of Re and of Im) per drain thread
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
-    uint64_t *fullA = bars + 0;     // [STAGES] A stage landed (even CTA: both CTAs' stages)
-    uint64_t *fullW = bars + 4;     // [STAGES] (even CTA) W stage written by both CTAs' generators
-    uint64_t *empty = bars + 8;     // [STAGES] MMAs of the stage completed (both CTAs)
-    uint64_t *accFull = bars + 12;  // [2] accumulator set holds a finished group (both CTAs)
-    uint64_t *accEmpty = bars + 14; // [2] (even CTA) accumulator set drained in both CTAs
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 16);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 17);
-    uint64_t *ifull = bars + 20;    // [IRING] item published
-    uint64_t *iempty = bars + 24;   // [IRING] (even CTA) every role of both CTAs has read it
-    volatile int *iring = reinterpret_cast<volatile int *>(bars + 28);
+    constexpr int BO = PC::BO;
+    uint64_t *fullA = bars + 0;            // [STAGES] A stage landed (even CTA: both CTAs' stages)
+    uint64_t *fullW = bars + STAGES;       // [STAGES] (even CTA) W stage written by both CTAs' generators
+    uint64_t *empty = bars + 2 * STAGES;   // [STAGES] MMAs of the stage completed (both CTAs)
+    uint64_t *accFull = bars + BO;         // [2] accumulator set holds a finished group (both CTAs)
+    uint64_t *accEmpty = bars + BO + 2;    // [2] (even CTA) accumulator set drained in both CTAs
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + BO + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + BO + 5);
+    uint64_t *ifull = bars + BO + 8;       // [IRING] item published
+    uint64_t *iempty = bars + BO + 12;     // [IRING] (even CTA) every role of both CTAs has read it
+    volatile int *iring = reinterpret_cast<volatile int *>(bars + BO + 16);
     int2 *kobuf_all = reinterpret_cast<int2 *>(smem + STAGES * STAGE + BAR_BYTES);
 
     const uint32_t rank = cluster_rank();
@@ -1879,7 +1886,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (idx < 0) break;
                 const int4 itm = items[idx];
                 const int nkc = itm.w;
-                const bool oct = jobs[item_job(itm.x)].oct != 0;
+                const bool oct = OCTK || jobs[item_job(itm.x)].oct != 0;
                 const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
                 bool ok = true;
                 for (int it = 0; it < nkc; ++it, ++gc) {
@@ -1965,10 +1972,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int mp = item_mt(item.y), k0 = item_k0(item.y);
             const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
             const int ngroups = (nkc + G - 1) / G;
-            // octant form: this thread's point (16 per CTA) and W row product
-            // (Re or Im of Y) x (Re or Im of Z), W row 16 cmb + point
-            const bool oct = J.oct != 0;
-            const int opt = gt & (OCT_PTH - 1), cmb = (gt / OCT_PTH) & 3;
+            // octant form: this thread's point opt (16 per CTA) and pair of k (kp) in
+            // its warp's quarter of the chunk; it forms the four W rows of the point
+            // (16 c + opt for the product c = 2 [Im Y] + [Im Z]) at both k.  A warp
+            // covers 8 points x 4 k pairs, so its 4-byte shared stores hit 32
+            // distinct banks.
+            const bool oct = OCTK || J.oct != 0;
+            const int opt = ((gt >> 5) & 1) * 8 + (gt & 7), kp = (gt >> 3) & 3;
             int iy = 0, iz = 0;
             if (oct) {
                 const int64_t no = (int64_t)item.z * OCT_PTS + rank * OCT_PTH + opt;
@@ -1993,22 +2003,40 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int gc0 = gc;
             int drained = 0;
             const int2 *kofs = J.kofs + (size_t)k0 * BK + kq * KQ;
-            if (lane < KQ) cp_async8(kobuf + lane, kofs + lane);
-            cp_async_commit();
+            // octant form: each thread's two k-offsets (16 aligned bytes), read one
+            // chunk ahead into registers; the other form stages the warp's eight
+            // through shared memory
+            const int4 *kofs4 = reinterpret_cast<const int4 *>(kofs + 2 * kp);
+            int4 kn = make_int4(0, 0, 0, 0);
+            if (oct) {
+                kn = __ldg(kofs4);
+            } else {
+                if (lane < KQ) cp_async8(kobuf + lane, kofs + lane);
+                cp_async_commit();
+            }
             for (int it = 0; it < nkc && ok; ++it, ++gc) {
                 const int s = gc % STAGES;
-                if (it + 1 < nkc && lane < KQ)
-                    cp_async8(kobuf + ((it + 1) & 1) * KQ + lane, kofs + (size_t)(it + 1) * BK + lane);
-                cp_async_commit();
-                cp_async_wait<1>();  // this chunk's records have landed
-                __syncwarp();
                 const int2 *kb = kobuf + (it & 1) * KQ;
                 float2 y[KQ], z[KQ];
+                if (oct) {
+                    const int4 kc = kn;
+                    if (it + 1 < nkc) kn = __ldg(kofs4 + (size_t)(it + 1) * (BK / 2));
+                    y[0] = __ldg(Yc + kc.x);
+                    z[0] = __ldg(Zc + kc.y);
+                    y[1] = __ldg(Yc + kc.z);
+                    z[1] = __ldg(Zc + kc.w);
+                } else {
+                    if (it + 1 < nkc && lane < KQ)
+                        cp_async8(kobuf + ((it + 1) & 1) * KQ + lane, kofs + (size_t)(it + 1) * BK + lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();  // this chunk's records have landed
+                    __syncwarp();
 #pragma unroll
-                for (int e = 0; e < KQ; ++e) {
-                    const int2 k2 = kb[e];
-                    y[e] = __ldg(Yc + k2.x);
-                    z[e] = __ldg(Zc + k2.y);
+                    for (int e = 0; e < KQ; ++e) {
+                        const int2 k2 = kb[e];
+                        y[e] = __ldg(Yc + k2.x);
+                        z[e] = __ldg(Zc + k2.y);
+                    }
                 }
                 const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
                 if (__any_sync(0xffffffffu, !w) || *abort_flag) {
@@ -2017,15 +2045,22 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 uint8_t *wst = smem + s * STAGE + A_STAGE;
                 if (oct) {
-                    // real W: (Re or Im of Y) x (Re or Im of Z), one 64-row array per piece
-                    float v[V];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) v[e] = __fmul_rn((cmb & 2) ? y[e].y : y[e].x, (cmb & 1) ? z[e].y : z[e].x);
+                    // real W: (Re or Im of Y) x (Re or Im of Z) at the two k, one 64-row
+                    // array per piece; split word c holds row 16 c + opt at both k
+                    const float v[V] = {__fmul_rn(y[0].x, z[0].x), __fmul_rn(y[1].x, z[1].x),
+                                        __fmul_rn(y[0].x, z[0].y), __fmul_rn(y[1].x, z[1].y),
+                                        __fmul_rn(y[0].y, z[0].x), __fmul_rn(y[1].y, z[1].x),
+                                        __fmul_rn(y[0].y, z[0].y), __fmul_rn(y[1].y, z[1].y)};
                     uint4 pc_[NP];
                     split_vec<KIND>(v, pc_);
-                    const uint32_t off = sw64_offset<KIND>(cmb * OCT_PTH + opt, kq * KQ);
 #pragma unroll
-                    for (int q = 0; q < NP; ++q) *reinterpret_cast<uint4 *>(wst + q * W_ARRH + off) = pc_[q];
+                    for (int q = 0; q < NP; ++q) {
+                        const uint32_t wd[4] = {pc_[q].x, pc_[q].y, pc_[q].z, pc_[q].w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            *reinterpret_cast<uint32_t *>(wst + q * W_ARRH +
+                                                          sw64_offset<KIND>(c * OCT_PTH + opt, kq * KQ + 2 * kp)) = wd[c];
+                    }
                 } else {
                     float re[V], im[V];
 #pragma unroll
@@ -2320,21 +2355,23 @@ static cudaError_t persistent_t(const TcJobDev *d_jobs, const int4 *d_items, int
     return cudaGetLastError();
 }
 
-// CTA-pair launch: grid = 2 x pairs, clusters of two CTAs.
-template <int KIND>
+// CTA-pair launch: grid = 2 x pairs, clusters of two CTAs.  OCTK: the build
+// for launches whose jobs all run in the octant form.
+template <int KIND, bool OCTK>
 static cudaError_t pair_t(const TcJobDev *d_jobs, const int4 *d_items, int n_items, int drain_every, int *err,
                           int grid_ctas, int64_t *launches, cudaStream_t st, int *progress, int *queue) {
     using namespace tc;
-    using PC = PairCfg<KIND>;
+    using PC = PairCfg<KIND, OCTK>;
     static bool attr_set[kAttrDevices] = {};  // kernel attributes are per device
     const int dev = current_device_slot();
     cudaError_t e;
     if (!attr_set[dev]) {
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, tc_pair_kernel<KIND>);
+        e = cudaFuncGetAttributes(&fa, tc_pair_kernel<KIND, OCTK>);
         if (e != cudaSuccess) return e;
         if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidDeviceFunction;
-        e = cudaFuncSetAttribute(tc_pair_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC::SMEM_BYTES);
+        e = cudaFuncSetAttribute(tc_pair_kernel<KIND, OCTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 PC::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
@@ -2353,7 +2390,8 @@ static cudaError_t pair_t(const TcJobDev *d_jobs, const int4 *d_items, int n_ite
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, tc_pair_kernel<KIND>, d_jobs, d_items, n_items, drain_every, err, progress, queue);
+    e = cudaLaunchKernelEx(&cfg, tc_pair_kernel<KIND, OCTK>, d_jobs, d_items, n_items, drain_every, err, progress,
+                           queue);
     if (launches) ++*launches;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -2365,7 +2403,7 @@ int tc_num_pairs() {
     if (!n) {
         // the pair kernels of both kinds have the same footprint (one CTA per SM)
         using PC = tc::PairCfg<tc::KIND_FP16X2>;
-        cudaFuncSetAttribute(tc::tc_pair_kernel<tc::KIND_FP16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(tc::tc_pair_kernel<tc::KIND_FP16X2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              PC::SMEM_BYTES);
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof(cfg));
@@ -2380,7 +2418,8 @@ int tc_num_pairs() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int c = 0;
-        if (cudaOccupancyMaxActiveClusters(&c, tc::tc_pair_kernel<tc::KIND_FP16X2>, &cfg) != cudaSuccess || c <= 0) {
+        if (cudaOccupancyMaxActiveClusters(&c, tc::tc_pair_kernel<tc::KIND_FP16X2, false>, &cfg) != cudaSuccess ||
+            c <= 0) {
             cudaGetLastError();
             c = tc_num_sms() / 2;
         }
@@ -2412,10 +2451,12 @@ int tc_variant_resolve(int kind, int requested, bool zstage_grid) {
 
 int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs) {
     // jobs laid out for pairs run the pair launch; others never do
-    bool pair = n_jobs > 0, oct = false;
+    // (VAR_OCT: every job in the octant form, the five-stage build; jobs of both
+    // forms share the four-stage build, which takes the form per job)
+    bool pair = n_jobs > 0, oct = n_jobs > 0;
     for (int j = 0; j < n_jobs; ++j) {
         pair = pair && jobs[j].pair && !jobs[j].ylm;
-        oct = oct || jobs[j].oct;
+        oct = oct && jobs[j].oct;
     }
     if (pair) return oct ? tc::VAR_OCT : tc::VAR_PAIR;
     const int v = tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
@@ -2438,9 +2479,12 @@ cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, 
                                                           launches, st, progress, queue);
         }
         if constexpr (tc::Kind<KIND>::STAGE_KO && !tc::Kind<KIND>::TF32) {
-            if (variant == tc::VAR_PAIR || variant == tc::VAR_OCT)
-                return pair_t<KIND>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st, progress,
-                                    queue);
+            if (variant == tc::VAR_OCT)
+                return pair_t<KIND, true>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
+                                          progress, queue);
+            if (variant == tc::VAR_PAIR)
+                return pair_t<KIND, false>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
+                                           progress, queue);
         }
         if constexpr (tc::Kind<KIND>::STAGE_KO) {
             if (variant == tc::VAR_PREFETCH)

@@ -128,3 +128,41 @@ def test_octant_full_size_job():
         ctx.close()
     idx = W.subset_indices(job.nq, 256, 29)
     assert rel(f[:, idx], oracle.grid_form_factor(job, idx)) < 1e-5
+
+
+def test_mixed_plan_equals_alone():
+    # one plan holding a shifted grid (CTA pairs in the Re/Im form) and antisymmetric grids (octant
+    # form): the launch takes the form per job; alone, the antisymmetric jobs run the five-stage
+    # octant build.  Each job's result is bitwise the same in the batch and alone.
+    import torch
+    j1 = f_job(7, 5, 9, 3640)
+    j2 = f_job(6, 5, 20, 3641)
+    j2 = W.Job(j2.mol, j2.T, j2.qx + 0.25, j2.qy, j2.qz, 3641)
+    j3 = W.config1()
+    jobs = [j1, j2, j3]
+    ctx = scff.Context(0)
+    try:
+        ctx.set_tc_variant(4)
+        specs = []
+        for k, job in enumerate(jobs):
+            b = ctx.basis(job.mol)
+            t = ctx.transitions(b, job.T)
+            g = ctx.qgrid_product(job.qx, job.qy, job.qz)
+            specs.append((b, t, g, torch.full((job.n_states, job.nq, 2), float("nan"), device="cuda"),
+                          torch.full((job.n_states, job.nq), float("nan"), device="cuda"), 1.0 + 0.5 * k))
+        plan = ctx.plan(specs, precision=scff.FP16X2)
+        stream = torch.cuda.Stream()
+        plan.run_graph(stream)
+        stream.synchronize()
+        ctx.sync(stream)
+        for s, job in zip(specs, jobs):
+            fa, f2a = ctx.form_factor(s[0], s[1], s[2], precision=scff.FP16X2, scale=s[5], f_out="cuda")
+            ctx.sync()
+            assert torch.equal(fa, s[3]) and torch.equal(f2a, s[4])
+            idx = W.subset_indices(job.nq, 300, 31)
+            fc = s[3].cpu().numpy()
+            fc = fc[..., 0] + 1j * fc[..., 1]
+            assert rel(fc[:, idx], oracle.grid_form_factor(job, idx, scale=s[5])) < 1e-5
+        plan.release()
+    finally:
+        ctx.close()
