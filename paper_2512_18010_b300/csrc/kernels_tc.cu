@@ -1789,7 +1789,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&fullA[s], 1);
             // even CTA: its generator warps and the odd CTA's relay (A and W of the odd CTA landed)
-            mbar_init(&fullW[s], GEN_WARPS + (lead ? 1 : 0));
+            // (the octant-only build: the four generator warps of the chunk's parity)
+            mbar_init(&fullW[s], (OCTK ? GEN_WARPS / 2 : GEN_WARPS) + (lead ? 1 : 0));
             mbar_init(&empty[s], 1);
         }
         for (int j = 0; j < 2; ++j) {
@@ -2002,6 +2003,79 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int j = 0; j < CQ; ++j) acc_re[j] = acc_im[j] = 0.f;
             const int gc0 = gc;
             int drained = 0;
+            if constexpr (OCTK) {
+                // Octant-only build: warps 4-7 write the W stages of the item's even
+                // chunks and warps 8-11 those of its odd chunks, so the latency chains
+                // (k-offsets, gathers, stores, proxy fence) of two chunks run at once.
+                // Warp (4 + 4 grp + wq) covers quarter wq of its chunks' k; a thread
+                // forms points pl and pl + 8 of the CTA's 16 (four Re/Im products
+                // each, W rows 16 c + point) at the two k of its pair kpa.
+                const int grp = (warp - 4) >> 2, wq = (warp - 4) & 3, kpa = lane >> 3, pl = lane & 7;
+                const float2 *Yu[2], *Zu[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int64_t no = (int64_t)item.z * OCT_PTS + rank * OCT_PTH + u * 8 + pl;
+                    int ya = 0, za = 0;
+                    if (no < J.Noct) {
+                        za = (int)(no % J.nzh);
+                        ya = (int)(no / J.nzh);
+                    }
+                    Yu[u] = J.Y + ya;
+                    Zu[u] = J.Z + za;
+                }
+                const int4 *ko4 = reinterpret_cast<const int4 *>(J.kofs + (size_t)k0 * BK + wq * KQ + 2 * kpa);
+                int4 kn = make_int4(0, 0, 0, 0);
+                if (grp < nkc) kn = __ldg(ko4 + (size_t)grp * (BK / 2));
+                for (int it = grp; it < nkc && ok; it += 2) {
+                    const int g2 = gc0 + it, s = g2 % STAGES;
+                    const int4 kc = kn;
+                    if (it + 2 < nkc) kn = __ldg(ko4 + (size_t)(it + 2) * (BK / 2));
+                    float2 yy[2][2], zz[2][2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        yy[u][0] = __ldg(Yu[u] + kc.x);
+                        zz[u][0] = __ldg(Zu[u] + kc.y);
+                        yy[u][1] = __ldg(Yu[u] + kc.z);
+                        zz[u][1] = __ldg(Zu[u] + kc.w);
+                    }
+                    const bool w = g2 < STAGES || mbar_wait(&empty[s], ((g2 / STAGES) - 1) & 1);
+                    if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *wst = smem + s * STAGE + A_STAGE;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const float2 *y2 = yy[u], *z2 = zz[u];
+                        const float v[V] = {__fmul_rn(y2[0].x, z2[0].x), __fmul_rn(y2[1].x, z2[1].x),
+                                            __fmul_rn(y2[0].x, z2[0].y), __fmul_rn(y2[1].x, z2[1].y),
+                                            __fmul_rn(y2[0].y, z2[0].x), __fmul_rn(y2[1].y, z2[1].x),
+                                            __fmul_rn(y2[0].y, z2[0].y), __fmul_rn(y2[1].y, z2[1].y)};
+                        uint4 pc_[NP];
+                        split_vec<KIND>(v, pc_);
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            const uint32_t wd[4] = {pc_[q].x, pc_[q].y, pc_[q].z, pc_[q].w};
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                *reinterpret_cast<uint32_t *>(
+                                    wst + q * W_ARRH + sw64_offset<KIND>(c * OCT_PTH + u * 8 + pl, wq * KQ + 2 * kpa)) =
+                                    wd[c];
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&fullW[s]);  // the odd CTA's relay forwards it
+                    while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
+                        if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, dre0, dim_off,
+                                                  acc_re, acc_im, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        ++drained;
+                    }
+                }
+            } else {
             const int2 *kofs = J.kofs + (size_t)k0 * BK + kq * KQ;
             // octant form: each thread's two k-offsets (16 aligned bytes), read one
             // chunk ahead into registers; the other form stages the warp's eight
@@ -2090,6 +2164,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     ++drained;
                 }
+            }
             }
             cp_async_wait<0>();  // no copy into this warp's buffers outlives the item
             __syncwarp();
