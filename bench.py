@@ -57,6 +57,8 @@ MEASURED_TRAFFIC = {
                             "profile": "profiles/tc_fp16x2_cfg3_full.md"},
     ("cfg3", "fp16x2", 3): {"bytes": 844095744 + 401571072, "src": "5c9ae55e44314b10",
                             "profile": "profiles/tc_pair_fp16x2_cfg3_launches.md"},
+    ("cfg3", "fp16x2", 4): {"bytes": 922938112 + 518444544, "src": "a07f72c59d506350",
+                            "profile": "profiles/tc_pair_oct_fp16x2_cfg3_full.md"},
 }
 
 
