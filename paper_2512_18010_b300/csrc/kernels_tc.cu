@@ -1799,8 +1799,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int r = 0; r < IRING; ++r) {
             mbar_init(&ifull[r], 1);
-            // consumers: even CTA MMA thread + generators, odd CTA copier + relay + generators
-            mbar_init(&iempty[r], (1 + GEN_WARPS) + (2 + GEN_WARPS));
+            // consumers: even CTA MMA thread + generators, odd CTA copier + relay(s) + generators
+            mbar_init(&iempty[r], (1 + GEN_WARPS) + ((OCTK ? 3 : 2) + GEN_WARPS));
         }
         *abort_flag = 0;
         fence_mbarrier_init();
@@ -1854,9 +1854,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the copies of the last stages have landed before the CTA may exit
             for (int c = max(0, gc - STAGES); c < gc; ++c)
                 mbar_wait_n(&fullA[c % STAGES], (c / STAGES) & 1, kWaitLimit);
-        } else if (warp == 1 && lane == 0 && !lead) {
+        } else if ((warp == 1 || (OCTK && warp == 2)) && lane == 0 && !lead) {
             // ---------------- odd CTA: once a stage's A has landed and its W is
-            // written, one release arrival on the even CTA's fullW covers both
+            // written, one release arrival on the even CTA's fullW covers both.
+            // The octant-only build relays from two threads (warp 1 the even
+            // chunks, warp 2 the odd ones), so two release arrivals at cluster
+            // scope can be in flight at once.
+            const int rpar = warp - 1;
             int gc = 0;
             bool ok = true;
             for (int ic = 0; ok; ++ic) {
@@ -1865,6 +1869,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (idx < 0) break;
                 const int nkc = items[idx].w;
                 for (int it = 0; it < nkc; ++it, ++gc) {
+                    if (OCTK && (gc & 1) != rpar) continue;
                     const int s = gc % STAGES;
                     const uint32_t par = (gc / STAGES) & 1;
                     if (*abort_flag || !mbar_wait_abort(&fullA[s], par, abort_flag) ||
