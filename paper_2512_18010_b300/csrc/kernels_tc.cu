@@ -196,7 +196,7 @@ template <int KIND, bool OCTK = false> struct PairCfg {
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
     // mbarrier and flag slots (8 bytes each) in the BAR_BYTES region
     static constexpr int BO = 3 * STAGES;
-    static_assert((BO + 18) * 8 <= BAR_BYTES, "barrier region");
+    static_assert((BO + 20) * 8 <= BAR_BYTES, "barrier region");
 };
 
 // Piece orders of the kept products (A piece, W piece).
@@ -1707,10 +1707,14 @@ __device__ __forceinline__ int ring_take_pair(uint64_t *ifull, uint64_t *iempty,
 // Adds finished accumulator group gg (TMEM set gg & 1) into this thread's
 // register sums: row = TMEM lane, CQ columns of Re at column re0 of the set
 // and of Im at re0 + im_off; frees the set on the even CTA's accEmpty.
+// local (optional): the set's local barrier this warp arrives on instead
+// (the octant-only build: the even CTA's accEmpty, or the odd CTA's
+// accDrained, which one thread relays to the even CTA per group).
 template <int CQ>
 __device__ __forceinline__ bool drain_group_pair(int gg, uint64_t *accFull, uint64_t *accEmpty, uint32_t tmem,
                                                  int lg, int lane, int re0, int im_off, float (&acc_re)[CQ],
-                                                 float (&acc_im)[CQ], volatile int *abort_flag) {
+                                                 float (&acc_im)[CQ], volatile int *abort_flag,
+                                                 uint64_t *local = nullptr) {
     const int set = gg & 1;
     const bool got = mbar_wait_abort(&accFull[set], (gg >> 1) & 1, abort_flag);
     if (__any_sync(0xffffffffu, !got)) return false;
@@ -1734,7 +1738,10 @@ __device__ __forceinline__ bool drain_group_pair(int gg, uint64_t *accFull, uint
     }
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive_cluster(mapa_shared(&accEmpty[set], 0));
+    if (lane == 0) {
+        if (local) mbar_arrive(&local[set]);
+        else mbar_arrive_cluster(mapa_shared(&accEmpty[set], 0));
+    }
     return true;
 }
 
@@ -1776,6 +1783,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *ifull = bars + BO + 8;       // [IRING] item published
     uint64_t *iempty = bars + BO + 12;     // [IRING] (even CTA) every role of both CTAs has read it
     volatile int *iring = reinterpret_cast<volatile int *>(bars + BO + 16);
+    uint64_t *accDrained = bars + BO + 18;  // [2] (odd CTA, octant-only build) set drained by its warps
     int2 *kobuf_all = reinterpret_cast<int2 *>(smem + STAGES * STAGE + BAR_BYTES);
 
     const uint32_t rank = cluster_rank();
@@ -1795,12 +1803,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int j = 0; j < 2; ++j) {
             mbar_init(&accFull[j], 1);
-            mbar_init(&accEmpty[j], 2 * GEN_WARPS);
+            // octant-only build: the even CTA's warps arrive locally and one relay
+            // arrival covers the odd CTA's (accDrained)
+            mbar_init(&accEmpty[j], OCTK ? GEN_WARPS + 1 : 2 * GEN_WARPS);
+            mbar_init(&accDrained[j], GEN_WARPS);
         }
         for (int r = 0; r < IRING; ++r) {
             mbar_init(&ifull[r], 1);
             // consumers: even CTA MMA thread + generators, odd CTA copier + relay(s) + generators
-            mbar_init(&iempty[r], (1 + GEN_WARPS) + ((OCTK ? 3 : 2) + GEN_WARPS));
+            mbar_init(&iempty[r], (1 + GEN_WARPS) + ((OCTK ? 4 : 2) + GEN_WARPS));
         }
         *abort_flag = 0;
         fence_mbarrier_init();
@@ -1854,6 +1865,30 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the copies of the last stages have landed before the CTA may exit
             for (int c = max(0, gc - STAGES); c < gc; ++c)
                 mbar_wait_n(&fullA[c % STAGES], (c / STAGES) & 1, kWaitLimit);
+        } else if (OCTK && warp == 3 && lane == 0 && !lead) {
+            // ---------------- odd CTA (octant-only build): once all its generator
+            // warps have drained an accumulator group, one release arrival at
+            // cluster scope frees the set on the even CTA's accEmpty
+            int gbase = 0;
+            bool ok = true;
+            for (int ic = 0; ok; ++ic) {
+                const int idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, 0);
+                if (idx == -2) ok = false;
+                if (idx < 0) break;
+                const int nkc = items[idx].w;
+                const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
+                const int ngroups = (nkc + G - 1) / G;
+                for (int i = 0; i < ngroups; ++i) {
+                    const int gg = gbase + i;
+                    if (*abort_flag || !mbar_wait_abort(&accDrained[gg & 1], (gg >> 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(mapa_shared(&accEmpty[gg & 1], 0));
+                }
+                gbase += ngroups;
+            }
+            if (!ok) *abort_flag = 1;
         } else if ((warp == 1 || (OCTK && warp == 2)) && lane == 0 && !lead) {
             // ---------------- odd CTA: once a stage's A has landed and its W is
             // written, one release arrival on the even CTA's fullW covers both.
@@ -1968,6 +2003,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         int2 *kobuf = kobuf_all + (warp - 4) * 2 * KQ;
         int gc = 0, gbase = 0, done_items = 0;
         bool ok = true;
+        // where the drains arrive (the octant-only build: locally, see accDrained)
+        uint64_t *dloc = OCTK ? (lead ? accEmpty : accDrained) : nullptr;
         for (int ic = 0; ok; ++ic) {
             const int idx = ring_take_pair(ifull, iempty, iring, ic, abort_flag, lane);
             if (idx == -2) ok = false;
@@ -2073,7 +2110,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (lane == 0) mbar_arrive(&fullW[s]);  // the odd CTA's relay forwards it
                     while (drained < ngroups && (drained + 1) * G - 1 + STAGES <= it) {
                         if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, dre0, dim_off,
-                                                  acc_re, acc_im, abort_flag)) {
+                                                  acc_re, acc_im, abort_flag, dloc)) {
                             ok = false;
                             break;
                         }
@@ -2175,7 +2212,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             while (ok && drained < ngroups) {
                 if (!drain_group_pair<CQ>(gbase + drained, accFull, accEmpty, tmem, lg, lane, dre0, dim_off, acc_re,
-                                          acc_im, abort_flag))
+                                          acc_im, abort_flag, dloc))
                     ok = false;
                 ++drained;
             }
