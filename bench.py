@@ -57,7 +57,7 @@ MEASURED_TRAFFIC = {
                             "profile": "profiles/tc_fp16x2_cfg3_full.md"},
     ("cfg3", "fp16x2", 3): {"bytes": 844095744 + 401571072, "src": "5c9ae55e44314b10",
                             "profile": "profiles/tc_pair_fp16x2_cfg3_launches.md"},
-    ("cfg3", "fp16x2", 4): {"bytes": 922938112 + 518444544, "src": "a07f72c59d506350",
+    ("cfg3", "fp16x2", 4): {"bytes": 903161344 + 531844864, "src": "8d41f2876cb319dd",
                             "profile": "profiles/tc_pair_oct_fp16x2_cfg3_full.md"},
 }
 
