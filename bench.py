@@ -499,8 +499,8 @@ def make_jobs(fn, n):
 
 def octant_form(precision, variant, scff):
     """Whether the tensor-core launches of this precision run the octant form on antisymmetric grids
-    (the automatic mode and mode 4, for the kinds with CTA pairs)."""
-    return precision in (scff.FP16X2, scff.BF16X2) and variant in (-1, 4)
+    (the automatic mode and mode 4: CTA pairs for the two-piece splits, single CTAs for hi/mid/lo)."""
+    return precision in (scff.FP16X2, scff.BF16X2, scff.BF16X3) and variant in (-1, 4)
 
 
 def tc_flop_per_row(precision, octant):

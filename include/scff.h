@@ -305,7 +305,7 @@ scff_status scff_set_tc_drain(scff_ctx *ctx, int drain_every);
  * when a tensor-core precision was asked for on an explicit q list, or when
  * the autotuner chose the FP32 direct path); out[2] = the W generator
  * variant the tensor-core kernel ran (0 gather, 1 Z staging, 2 prefetch, 3 CTA pairs,
- * 4 CTA pairs in the octant form; see
+ * 4 the octant form; see
  * scff_set_tc_variant), 0 off the tensor cores.  All -1 before the first
  * call. */
 scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
@@ -326,15 +326,16 @@ scff_status scff_last_path(scff_ctx *ctx, int32_t *out);
  *     SMs (a cluster) share each 256-row MMA (cta_group::2); each CTA holds
  *     the A rows of its half and generates W for half of the tile's columns,
  *     so every SM forms half as much W per unit of tensor work.
- *   4 CTA pairs in the octant form (FP16 hi/lo and BF16 hi/lo): on grids
- *     whose three axes are antisymmetric (q[n-1-i] = -q[i]) the y and z
- *     factors at -q are the conjugates of those at +q, so W is formed real,
- *     one row per octant point and product of real or imaginary parts, and
- *     the eight real sums of a point give f at (qx, +-qy, +-qz) and, by
- *     f(-q) = conj(f(q)), at the mirrored points: half the tensor work and
- *     half the W values per output of mode 3.  On other grids it runs as 3.
+ *   4 the octant form (CTA pairs for FP16 hi/lo and BF16 hi/lo, single CTAs
+ *     of the gather variant for BF16 hi/mid/lo): on grids whose three axes
+ *     are antisymmetric (q[n-1-i] = -q[i]) the y and z factors at -q are the
+ *     conjugates of those at +q, so W is formed real, one row per octant
+ *     point and product of real or imaginary parts, and the eight real sums
+ *     of a point give f at (qx, +-qy, +-qz) and, by f(-q) = conj(f(q)), at
+ *     the mirrored points: half the tensor work and half the W values per
+ *     output.  On other grids it runs as 3 (two-piece kinds) or 0.
  * mode: -1 automatic (the default: Z staging for TF32 hi/lo, the octant form
- * of CTA pairs for FP16 hi/lo and BF16 hi/lo, gather for BF16 hi/mid/lo; with
+ * for FP16 hi/lo, BF16 hi/lo and BF16 hi/mid/lo; with
  * the autotuner on, tuned per job shape over the variants the grid and split
  * allow), 0 to 4 to request one (a variant the grid or split does not allow
  * runs as 0).  Variants 0 to 3 form bitwise the same W and add the same

@@ -1202,6 +1202,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr int A_STAGE = KD::A_STAGE, STAGE = KD::STAGE;
     constexpr int KH = BK / 2;        // k per generator thread (two threads per W row)
     constexpr int KSUB = 8;           // loads in flight per sub-batch
+    // octant form of the single-CTA gather variant (BF16 hi/mid/lo): jobs with
+    // TcJobDev::oct = 1 form a real W for 32 octant points x 4 Re/Im products
+    // (rows 64 h + 16 c + p for point 16 h + p) and Ar, Ai multiply it into
+    // their own accumulators (two MMAs per piece product instead of four)
+    constexpr bool OCTS = !KD::FUSE && !KD::TF32 && VAR == VAR_GATHER;
     constexpr int CQ = BN / 2;        // accumulator columns (of Re and of Im) per drain thread
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1344,6 +1349,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (idx == -2) *abort_flag = 1;
                 if (idx < 0) break;
                 const int nkc = items[idx].w;
+                const bool octj = OCTS && jobs[item_job(items[idx].x)].oct != 0;
                 const int G = drain_every >= 1 ? max(2, min(drain_every, nkc)) : nkc;
                 bool ok = true;
                 for (int it = 0; it < nkc; ++it, ++gc) {
@@ -1381,11 +1387,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 mma_issue<TF32>(t_re, ai, smem_desc_sw64(pb), ID2, 1);            // += [-Ai Wi | Ai Wr]
                             } else {
                                 const uint64_t wr = smem_desc_sw64(w0 + qw * W_ARR + ko);
-                                const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
-                                mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
-                                mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
-                                mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
-                                mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+                                if (octj) {
+                                    // real W: S_r = Ar W in the Re columns, S_i = Ai W in the Im columns
+                                    mma_issue<TF32>(t_re, ar, wr, ID, acc);
+                                    mma_issue<TF32>(t_im, ai, wr, ID, acc);
+                                } else {
+                                    const uint64_t wi = smem_desc_sw64(w0 + (NP + qw) * W_ARR + ko);
+                                    mma_issue<TF32>(t_re, ar, wr, ID, acc);   // Re += Ar Wr
+                                    mma_issue<TF32>(t_re, ai, wi, IDN, 1);    // Re -= Ai Wi
+                                    mma_issue<TF32>(t_im, ar, wi, ID, acc);   // Im += Ar Wi
+                                    mma_issue<TF32>(t_im, ai, wr, ID, 1);     // Im += Ai Wr
+                                }
                             }
                         }
                     }
@@ -1438,6 +1450,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                     while (l * l > iz) --l;
                     while ((l + 1) * (l + 1) <= iz) ++l;
                     iy = iy * J.ystride + l;
+                }
+            }
+            // octant form: thread point op (32 per tile) and k quad kq4 (4 k) of the chunk
+            const bool octj = OCTS && J.oct != 0;
+            const int op = gt & 31, kq4 = gt >> 5;
+            if (octj) {
+                const int64_t no = (int64_t)item.z * OCT_PTS + op;
+                iy = iz = 0;
+                if (no < J.Noct) {
+                    iz = (int)(no % J.nzh);
+                    iy = (int)(no / J.nzh);
                 }
             }
             const float2 *Yc = J.Y + iy;
@@ -1606,6 +1629,47 @@ __global__ void __launch_bounds__(THREADS, 1)
                         split_vec<KIND>(im, pi_);
                         const uint32_t off = sw64_offset<KIND>(wrow, khalf * KH + jv * V);
                         store_w<KIND>(wst, off, pr_, pi_);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&fullW[s]);
+                    } else if (octj) {
+                    // four Re/Im products of the point at four k from one gather each;
+                    // split word pairs hold a product at two k (8-byte stores)
+                    const int2 *ko4 = J.kofs + (size_t)(k0 + it) * BK + kq4 * 4;
+                    float2 y[4], z[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int2 k2 = __ldg(ko4 + e);
+                        y[e] = __ldg(Yc + k2.x);
+                        z[e] = __ldg(Zc + k2.y);
+                    }
+                    const bool w = gc < STAGES || mbar_wait(&empty[s], ((gc / STAGES) - 1) & 1);
+                    if (__any_sync(0xffffffffu, !w) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *wst = smem + s * STAGE + A_STAGE;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        // products 2h (Re or Im of Y by Re of Z) and 2h + 1 (by Im of Z)
+                        float v[8];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float yc = h ? y[e].y : y[e].x;
+                            v[e] = __fmul_rn(yc, z[e].x);
+                            v[4 + e] = __fmul_rn(yc, z[e].y);
+                        }
+                        uint4 pc_[NP];
+                        split_vec<KIND>(v, pc_);
+                        const int rbase = (op >> 4) * 64 + (op & 15);
+                        const uint32_t o0 = sw64_offset<KIND>(rbase + (2 * h) * OCT_PTH, kq4 * 4);
+                        const uint32_t o1 = sw64_offset<KIND>(rbase + (2 * h + 1) * OCT_PTH, kq4 * 4);
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            *reinterpret_cast<uint2 *>(wst + q * W_ARR + o0) = make_uint2(pc_[q].x, pc_[q].y);
+                            *reinterpret_cast<uint2 *>(wst + q * W_ARR + o1) = make_uint2(pc_[q].z, pc_[q].w);
+                        }
                     }
                     fence_proxy_async_smem();
                     __syncwarp();
@@ -2324,7 +2388,8 @@ static void job_desc_t(const TcArgs &a, void *ws, TcJobDev *jd) {
     jd->nsplit = sp;
     jd->split_tiles = sp ? R : 0;
     jd->tmax = Kind<KIND>::FP16 ? reinterpret_cast<const unsigned long long *>(w + L.off_tmax) : nullptr;
-    jd->oct = a.oct && a.pair && a.half ? 1 : 0;
+    // octant form: CTA pairs (two-piece kinds) or the single-CTA gather kernel (hi/mid/lo)
+    jd->oct = a.oct && a.half && (a.pair || !Kind<KIND>::FUSE) ? 1 : 0;
     jd->nyh = (a.ny + 1) / 2;
     jd->nzh = (a.nz + 1) / 2;
     jd->Noct = (int64_t)jd->nyh * jd->nzh;
@@ -2338,7 +2403,7 @@ static cudaError_t prep_job_t(const TcArgs &a, void *ws, TcJobDev *jd, int64_t *
     const PairSetDev &ps = *a.ps;
     const Layout L = job_layout<KIND>(a);
     if (L.n_mt > (1 << 24)) return cudaErrorInvalidConfiguration;
-    if (a.oct && !(a.pair && a.half)) return cudaErrorInvalidValue;
+    if (a.oct && !(a.half && (a.pair || !KD::FUSE))) return cudaErrorInvalidValue;
     uint8_t *w = static_cast<uint8_t *>(ws);
     float2 *X = reinterpret_cast<float2 *>(w + L.off_X);
     float2 *Y = reinterpret_cast<float2 *>(w + L.off_Y);
@@ -2546,7 +2611,7 @@ int tc_num_pairs() {
 }
 
 int tc_variant_preferred(int kind) {
-    return kind == tc::KIND_TF32X2 ? tc::VAR_ZSTAGE : tc_prefetch_ok(kind) ? tc::VAR_OCT : tc::VAR_GATHER;
+    return kind == tc::KIND_TF32X2 ? tc::VAR_ZSTAGE : tc::VAR_OCT;
 }
 
 bool tc_prefetch_ok(int kind) { return kind == tc::KIND_FP16X2 || kind == tc::KIND_BF16X2; }
@@ -2562,7 +2627,8 @@ int tc_variant_resolve(int kind, int requested, bool zstage_grid) {
     if (requested == tc::VAR_ZSTAGE) return kind != tc::KIND_BF16X3 && zstage_grid ? tc::VAR_ZSTAGE : tc::VAR_GATHER;
     if (requested == tc::VAR_PREFETCH) return tc_prefetch_ok(kind) ? tc::VAR_PREFETCH : tc::VAR_GATHER;
     if (requested == tc::VAR_PAIR) return tc_prefetch_ok(kind) ? tc::VAR_PAIR : tc::VAR_GATHER;
-    if (requested == tc::VAR_OCT) return tc_prefetch_ok(kind) ? tc::VAR_OCT : tc::VAR_GATHER;
+    if (requested == tc::VAR_OCT)
+        return tc_prefetch_ok(kind) || kind == tc::KIND_BF16X3 ? tc::VAR_OCT : tc::VAR_GATHER;
     return tc::VAR_GATHER;
 }
 
@@ -2576,6 +2642,9 @@ int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs) {
         oct = oct && jobs[j].oct;
     }
     if (pair) return oct ? tc::VAR_OCT : tc::VAR_PAIR;
+    // single CTAs: the octant form runs in the gather kernel (reported as VAR_OCT
+    // when every job takes it)
+    if (n_jobs > 0 && oct && kind == tc::KIND_BF16X3) return tc::VAR_OCT;
     const int v = tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
     return v == tc::VAR_PAIR || v == tc::VAR_OCT ? tc::VAR_GATHER : v;
 }
@@ -2659,7 +2728,7 @@ cudaError_t launch_tc_form_factor(const TcArgs &args, int64_t *launches, cudaStr
     TcArgs a = args;
     {
         const int v = tc_variant_resolve(a.kind, a.zstage, false);
-        a.pair = v == tc::VAR_PAIR || v == tc::VAR_OCT ? 1 : 0;
+        a.pair = tc_prefetch_ok(a.kind) && (v == tc::VAR_PAIR || v == tc::VAR_OCT) ? 1 : 0;
         a.oct = v == tc::VAR_OCT && a.half ? 1 : 0;
     }
     const size_t jb = tc_job_bytes(*a.ps, a.S, a.nx, a.ny, a.nz, a.kind);

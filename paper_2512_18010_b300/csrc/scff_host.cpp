@@ -1347,7 +1347,7 @@ extern "C" scff_status scff_plan_create(scff_ctx *c, int n_jobs, const scff_job 
     // jobs laid out for the CTA-pair launch when that variant is asked for (it never changes a result)
     {
         const int v = P->tc_kind >= 0 ? tc_variant_resolve(P->tc_kind, zstage_mode(c, precision), false) : 0;
-        P->pair = v == 3 || v == 4 ? 1 : 0;
+        P->pair = tc_prefetch_ok(P->tc_kind) && (v == 3 || v == 4) ? 1 : 0;
         P->oct = v == 4 ? 1 : 0;
     }
     P->SB = fp64 ? 4 : 8;

@@ -265,7 +265,7 @@ scff_status launch_batch(scff_server_s *sv, int k, Batch *B) {
             ta.half = j->half;
             {
                 const int v = tc_variant_resolve(ta.kind, sv->variant, false);
-                ta.pair = v == 3 || v == 4 ? 1 : 0;
+                ta.pair = tc_prefetch_ok(ta.kind) && (v == 3 || v == 4) ? 1 : 0;
                 ta.oct = v == 4 && j->half ? 1 : 0;
             }
             tc_axes_abs_max(j->ax[0].data(), j->req.nx, j->ax[1].data(), j->req.ny, j->ax[2].data(), j->req.nz,

@@ -19,7 +19,7 @@ from . import build as _build
 FP64, FP32, BF16X3, TF32X3, BF16X2, FP16X2 = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "tf32x3": TF32X3, "bf16x2": BF16X2, "fp16x2": FP16X2}
 # tensor-core W generator variants (scff_set_tc_variant modes, scff_last_path's third entry)
-GEN_VARIANTS = {0: "gather", 1: "zstage", 2: "prefetch", 3: "pair", 4: "pair_octant"}
+GEN_VARIANTS = {0: "gather", 1: "zstage", 2: "prefetch", 3: "pair", 4: "octant"}
 RENORM_CONTRACTED = 1
 PURE_D = 2   # d shells are the 5 real solid harmonics
 PURE_F = 4   # f shells are the 7 real solid harmonics
@@ -458,10 +458,10 @@ class Context:
         """Tensor-core launch shape and W generator variant: -1 automatic, 0 gather from global memory,
         1 stage Z and Y in shared memory where the grid allows it, 2 prefetch the next chunk's table
         entries with the running sums in TMEM, 3 CTA pairs (two SMs share each 256-row MMA and each
-        generates half of W), 4 CTA pairs in the octant form on antisymmetric grids (real W, half the
-        tensor work; 3 on other grids); 2 to 4 where the split allows them (FP16 hi/lo, BF16 hi/lo).
-        0 to 3 give bitwise the same results; 4 rounds differently within the same bar (GEN_VARIANTS
-        names them)."""
+        generates half of W), 4 the octant form on antisymmetric grids (real W, half the tensor work:
+        CTA pairs for FP16 hi/lo and BF16 hi/lo, single CTAs for BF16 hi/mid/lo; elsewhere 3 or 0);
+        2 and 3 where the split allows them (FP16 hi/lo, BF16 hi/lo).  0 to 3 give bitwise the same
+        results; 4 rounds differently within the same bar (GEN_VARIANTS names them)."""
         _check(self.lib.scff_set_tc_variant(self.h, int(mode)))
 
     def set_tc_zstage(self, mode: int):

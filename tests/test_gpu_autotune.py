@@ -119,7 +119,7 @@ def test_last_path_reports_the_path_taken():
         assert ctx.last_path()["path"] is None
         scff.evaluate_job(ctx, job, precision=scff.FP16X2)
         # the default for FP16 hi/lo on an antisymmetric grid: CTA pairs in the octant form
-        assert ctx.last_path() == {"path": "tensor_cores", "precision": "fp16x2", "variant": "pair_octant"}
+        assert ctx.last_path() == {"path": "tensor_cores", "precision": "fp16x2", "variant": "octant"}
         # a tensor-core precision on an explicit q list runs the FP32 direct path
         scff.evaluate_job(ctx, job, precision=scff.BF16X3, q_list=np.array([[0.1, 0.2, 0.3], [1.0, 0.0, 0.0]]))
         assert ctx.last_path() == {"path": "direct_fp32", "precision": "fp32", "variant": None}

@@ -34,18 +34,20 @@ def f_job(nx, ny, nz, seed, n_heavy=1, n_states=3, a=(10.0, 8.0, 12.0)):
 GRIDS = [(7, 5, 9), (4, 33, 20), (6, 8, 128), (9, 1, 64), (1, 3, 1), (16, 16, 16)]
 
 
-@pytest.mark.parametrize("prec", [scff.FP16X2, scff.BF16X2])
+@pytest.mark.parametrize("prec", [scff.FP16X2, scff.BF16X2, scff.BF16X3])
 @pytest.mark.parametrize("grid", GRIDS)
 def test_octant_matches_oracle_and_pair_form(prec, grid):
+    # mode 4 against the oracle and against mode 3 (CTA pairs in the Re/Im form for the two-piece
+    # splits; BF16 hi/mid/lo has no pairs and runs the single-CTA gather variant in both forms)
     job = f_job(*grid, seed=3600 + sum(grid))
     ctx = scff.Context(0)
     try:
         ctx.set_tc_variant(4)
         f4, f24 = scff.evaluate_job(ctx, job, precision=prec)
-        assert ctx.last_path()["variant"] == "pair_octant"
+        assert ctx.last_path()["variant"] == "octant"
         ctx.set_tc_variant(3)
         f3, _ = scff.evaluate_job(ctx, job, precision=prec)
-        assert ctx.last_path()["variant"] == "pair"
+        assert ctx.last_path()["variant"] == ("gather" if prec == scff.BF16X3 else "pair")
     finally:
         ctx.close()
     idx = W.subset_indices(job.nq, 400, 17)
@@ -58,8 +60,9 @@ def test_octant_matches_oracle_and_pair_form(prec, grid):
     assert np.array_equal(h, np.conj(h[:, ::-1, ::-1, ::-1]))  # every mirrored point written
 
 
+@pytest.mark.parametrize("prec", [scff.FP16X2, scff.BF16X3])
 @pytest.mark.parametrize("drain", [2, 3, 8])
-def test_octant_regimes(drain):
+def test_octant_regimes(drain, prec):
     # drains of 2 and 3 chunks, tail-split parts (few tiles on the z = 128 grid), an odd m-tile
     # count (the pair's second half all padding), overlapped download off / automatic / two bands
     jobs = [f_job(7, 5, 128, 3611), f_job(4, 33, 20, 3612), W.config1()]
@@ -69,7 +72,7 @@ def test_octant_regimes(drain):
         ctx.set_tc_variant(4)
         for job, bands in zip(jobs, (0, 1, 2)):
             ctx.set_download_bands(bands)
-            f, _ = scff.evaluate_job(ctx, job, precision=scff.FP16X2)
+            f, _ = scff.evaluate_job(ctx, job, precision=prec)
             idx = W.subset_indices(job.nq, 300, 19)
             assert rel(f[:, idx], oracle.grid_form_factor(job, idx)) < 1e-5
     finally:
@@ -123,7 +126,7 @@ def test_octant_full_size_job():
     ctx = scff.Context(0)
     try:
         f, _ = scff.evaluate_job(ctx, job, precision=scff.FP16X2)
-        assert ctx.last_path()["variant"] == "pair_octant"
+        assert ctx.last_path()["variant"] == "octant"
     finally:
         ctx.close()
     idx = W.subset_indices(job.nq, 256, 29)
