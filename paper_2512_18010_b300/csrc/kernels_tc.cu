@@ -1202,11 +1202,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr int A_STAGE = KD::A_STAGE, STAGE = KD::STAGE;
     constexpr int KH = BK / 2;        // k per generator thread (two threads per W row)
     constexpr int KSUB = 8;           // loads in flight per sub-batch
-    // octant form of the single-CTA gather variant (BF16 hi/mid/lo): jobs with
+    // octant form of the single-CTA gather kernel (BF16 hi/mid/lo, compiled as
+    // VAR_OCT so the plain gather kernel keeps its registers): jobs with
     // TcJobDev::oct = 1 form a real W for 32 octant points x 4 Re/Im products
     // (rows 64 h + 16 c + p for point 16 h + p) and Ar, Ai multiply it into
     // their own accumulators (two MMAs per piece product instead of four)
-    constexpr bool OCTS = !KD::FUSE && !KD::TF32 && VAR == VAR_GATHER;
+    constexpr bool OCTS = !KD::FUSE && !KD::TF32 && VAR == VAR_OCT;
     constexpr int CQ = BN / 2;        // accumulator columns (of Re and of Im) per drain thread
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -2642,9 +2643,11 @@ int tc_variant_for(int kind, int requested, const TcJobDev *jobs, int n_jobs) {
         oct = oct && jobs[j].oct;
     }
     if (pair) return oct ? tc::VAR_OCT : tc::VAR_PAIR;
-    // single CTAs: the octant form runs in the gather kernel (reported as VAR_OCT
-    // when every job takes it)
-    if (n_jobs > 0 && oct && kind == tc::KIND_BF16X3) return tc::VAR_OCT;
+    // single CTAs: jobs in the octant form run in the gather kernel's octant
+    // build, which also takes jobs in the Re/Im form
+    bool any_oct = false;
+    for (int j = 0; j < n_jobs; ++j) any_oct = any_oct || jobs[j].oct;
+    if (any_oct && kind == tc::KIND_BF16X3) return tc::VAR_OCT;
     const int v = tc_variant_resolve(kind, requested, tc_zstage_ok(kind, jobs, n_jobs));
     return v == tc::VAR_PAIR || v == tc::VAR_OCT ? tc::VAR_GATHER : v;
 }
@@ -2671,6 +2674,11 @@ cudaError_t tc_launch_persistent(int kind, int variant, const TcJobDev *d_jobs, 
             if (variant == tc::VAR_PAIR)
                 return pair_t<KIND, false>(d_jobs, d_items, n_items, drain_every, err, grid_ctas, launches, st,
                                            progress, queue);
+        }
+        if constexpr (!tc::Kind<KIND>::FUSE && !tc::Kind<KIND>::TF32) {
+            if (variant == tc::VAR_OCT)
+                return persistent_t<KIND, tc::VAR_OCT>(d_jobs, d_items, n_items, drain_every, err, grid_ctas,
+                                                       launches, st, progress, queue);
         }
         if constexpr (tc::Kind<KIND>::STAGE_KO) {
             if (variant == tc::VAR_PREFETCH)
