@@ -57,7 +57,7 @@ MEASURED_TRAFFIC = {
                             "profile": "profiles/tc_fp16x2_cfg3_full.md"},
     ("cfg3", "fp16x2", 3): {"bytes": 844095744 + 401571072, "src": "5c9ae55e44314b10",
                             "profile": "profiles/tc_pair_fp16x2_cfg3_launches.md"},
-    ("cfg3", "fp16x2", 4): {"bytes": 903161344 + 531844864, "src": "8d41f2876cb319dd",
+    ("cfg3", "fp16x2", 4): {"bytes": 885823232 + 522586880, "src": "c2fb967109756a08",
                             "profile": "profiles/tc_pair_oct_fp16x2_cfg3_full.md"},
 }
 
