@@ -1,4 +1,5 @@
-"""Octant form of the CTA-pair launch (scff_set_tc_variant mode 4).
+"""Octant form (scff_set_tc_variant mode 4): CTA pairs for FP16 hi/lo and BF16 hi/lo, single CTAs
+for BF16 hi/mid/lo.
 
 On a grid whose three axes are antisymmetric, the y and z factors of every
 pair term at -q are the complex conjugates of those at +q, so one real
